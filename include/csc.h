@@ -1,0 +1,147 @@
+/*
+ * csc.h - C ABI of the GB300 dual-domain convolutional sparse coding library (libcsc.so).
+ *
+ * Method: Affara, Ghanem & Wonka, "Fast Convolutional Sparse Coding in the Dual Domain"
+ * (arXiv 1709.09479). The problem (Eq. 1, summed over N images that share the dictionary):
+ *
+ *     min_{d,z}  1/2 sum_n || x_n - sum_k d_k * z_nk ||^2 + beta sum_{n,k} || z_nk ||_1
+ *     s.t.       || d_k ||_2^2 <= 1,
+ *
+ * with circular convolution on the image grid (Sec. 3). Higher-order CSC (Sec. 3.3): J channels per
+ * image share one code per filter; filter k has J channels.
+ *
+ * Layouts (all float32, C order, no padding):
+ *   x  images       [N][J][H][W]
+ *   d  filters      [K][J][fh][fw]  tap (a,b) sits at offset (a - (fh-1)/2, b - (fw-1)/2), wrapped
+ *   v  ADMM state   [N][K][H][W]    v = D^T lambda - z / rho; v = 0 means z = theta = 0
+ *   z  codes        [N][K][H][W]    z = rho (clamp(v, -beta, beta) - v)
+ *   mu multipliers  [K] float64     (Eq. Learning_Lagrangian)
+ *
+ * Pointers: every array argument may be host memory or device memory of the context's device;
+ * the library detects which (cudaPointerGetAttributes). Host arrays are staged through
+ * library-owned device buffers inside the call, and such calls return only after their host
+ * outputs are written. Calls whose arrays are all on the device are asynchronous on the
+ * context's stream, except csc_learn and csc_objective, which synchronise to return host values.
+ * The caller owns every array it passes; the library owns its workspace (allocated by csc_init
+ * and on first use of csc_learn, released by csc_destroy).
+ *
+ * Errors: every call returns a csc_status. Shape and argument errors are detected before any
+ * launch. A failed call leaves its output arrays unspecified but the context usable;
+ * csc_last_error gives a one-line description. No exception or exit() crosses the ABI.
+ */
+#ifndef CSC_H_
+#define CSC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct csc_ctx csc_ctx;
+
+typedef enum {
+  CSC_OK = 0,
+  CSC_ERR_ARG = 1,           /* null or inconsistent argument */
+  CSC_ERR_SHAPE = 2,         /* size outside what the kernels support */
+  CSC_ERR_WORKSPACE = 3,     /* device allocation failed */
+  CSC_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
+  CSC_ERR_NONFINITE = 5,     /* a non-finite value appeared */
+  CSC_ERR_NOT_CONVERGED = 6, /* reserved */
+  CSC_ERR_TIMEOUT = 7,       /* a bounded grid barrier gave up; results unspecified */
+  CSC_ERR_UNSUPPORTED = 8    /* valid request the library does not implement */
+} csc_status;
+
+typedef enum {
+  CSC_FP32 = 0,        /* everything in float32 */
+  CSC_MIXED_BF16 = 1   /* per-frequency contractions with bfloat16 operands, float32 accumulation */
+} csc_precision;
+
+typedef struct {
+  int J;          /* channels per image sharing one code (1 grey, 3 colour), 1..3 */
+  int K;          /* number of filters, >= 1 */
+  int fs[2];      /* filter support (fh, fw), odd, each <= the image side */
+  double beta;    /* l1 weight of Eq. 1, > 0 */
+  double rho;     /* ADMM step of Eq. Inference_solution, > 0 */
+  int cg_max;     /* CG iteration cap per learning step (csc_learn), >= 1 */
+  double cg_tol;  /* CG stop: ||r|| <= cg_tol ||b|| (relative residual), > 0 */
+  int precision;  /* csc_precision */
+} csc_params;
+
+/*
+ * Create a context for n_images images, all of size H x W (dims = {H, W}), on the current CUDA
+ * device, launching on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Supported sizes: W even; H, W >= 8; H and W/2 factoring into 2, 3, 5 and 7; one map plus 2*J
+ * half spectra in a CTA's shared memory: 8 * (H*P + 2*J*H*(W/2+1) + W + H + 1) <= 232448 bytes,
+ * P = W/2+1 rounded up to odd (128 x 128 fits at J = 1). Filter width fw <= 15.
+ * On success *out owns the workspace; release it with csc_destroy.
+ */
+csc_status csc_init(const csc_params* params, int n_images, const int* dims, void* stream,
+                    csc_ctx** out);
+
+/*
+ * Coding subproblem (Eq. 2) by `iters` iterations of the dual ADMM of Eq. Inference_solution
+ * (Sec. 3.2), in the Fourier domain, with the filters d fixed:
+ *     lambda = (D D^T + I/rho)^{-1} (D theta + D z / rho - x / rho)
+ *     theta  = Pi_C(D^T lambda - z / rho)
+ *     z      = z + rho (theta - D^T lambda)
+ * carried in the single state v (in/out, [N][K][H][W]); pass v = 0 for the start of Algorithm 1
+ * and the previous v to warm-start. If z is non-NULL it receives the codes of the final state.
+ * iters >= 0 (0 only computes z from v).
+ */
+csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters);
+
+/*
+ * Learning subproblem (Eq. 3, Sec. 3.2) for fixed codes z: `steps` rounds of
+ *     d(mu) = argmin_d 1/2 ||x - Z S^T d||^2 + sum_k mu_k ||d_k||^2   (Eqs. Learning_new..Solution)
+ *     mu_k <- max(mu_k ||d_k||_2, 1e-8)                                (Eq. mu_update)
+ * then d_k <- d_k / max(1, ||d_k||). d(mu) is the solution of the dual system of
+ * Eq. Learning_gamma; the library reaches the same d by solving the filter-space normal equations
+ * (S Z^T Z S^T + 2 diag(mu)) d = S Z^T x (strong duality) with CG warm-started from the current d.
+ * A filter whose codes are all zero keeps its d_k and mu_k. Channels are solved separately with
+ * one shared mu (Sec. 3.3). d is in/out [K][J][fh][fw]; mu is in/out [K] (float64).
+ * If cg_iters is non-NULL it receives `steps` ints (host memory): the CG iterations of each step
+ * (the maximum over channels). Synchronises the stream.
+ */
+csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, double* mu, int steps,
+                     int* cg_iters);
+
+/*
+ * Objective of Eq. 1 summed over images: *out (host) = 1/2 sum_n ||x_n - sum_k d_k * z_nk||^2
+ * + beta sum |z|. Reductions run in float64 in a fixed order. Synchronises the stream.
+ */
+csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const float* z, double* out);
+
+/*
+ * Benchmarking aid (no counterpart in the paper). While enabled, each coding sweep launch (one ADMM
+ * iteration over all N*K maps) and each csc_learn call are bracketed by CUDA events on the
+ * context's stream. kernel_launches counts every kernel the library launched (enabled or not).
+ */
+typedef struct {
+  double sweep_ms;           /* summed device time of the bracketed coding sweeps */
+  int sweep_launches;        /* number of bracketed coding sweeps */
+  double learn_ms;           /* summed device time of the bracketed csc_learn calls */
+  int learn_calls;
+  long long kernel_launches; /* kernels launched since the last csc_timing_read */
+} csc_timing;
+
+/* Turn event bracketing on (enable != 0) or off. */
+csc_status csc_timing_enable(csc_ctx* ctx, int enable);
+
+/* Read and reset the accumulated timing (synchronises the stream). */
+csc_status csc_timing_read(csc_ctx* ctx, csc_timing* out);
+
+/* Release the context and its workspace. NULL is ignored. */
+void csc_destroy(csc_ctx* ctx);
+
+/* One-line description of the last error on ctx (or of the last csc_init failure if ctx is NULL). */
+const char* csc_last_error(const csc_ctx* ctx);
+
+/* Library version string. */
+const char* csc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSC_H_ */

@@ -1,0 +1,197 @@
+"""Python binding of libcsc.so (include/csc.h): argument marshalling only.
+
+Every array argument may be a torch tensor (CUDA or CPU) or a numpy array; it must be contiguous
+and float32 (mu: float64). The library itself decides whether a pointer is host or device memory.
+All computation runs in the library's CUDA kernels; if libcsc.so is missing this module raises at
+import: there is no fallback.
+
+Functions carry the C names (csc_init, csc_code, csc_learn, csc_objective, csc_destroy,
+csc_last_error, csc_version); ``Solver`` wraps a context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsc.so")
+
+CSC_OK = 0
+STATUS_NAMES = {0: "CSC_OK", 1: "CSC_ERR_ARG", 2: "CSC_ERR_SHAPE", 3: "CSC_ERR_WORKSPACE", 4: "CSC_ERR_CUDA",
+                5: "CSC_ERR_NONFINITE", 6: "CSC_ERR_NOT_CONVERGED", 7: "CSC_ERR_TIMEOUT",
+                8: "CSC_ERR_UNSUPPORTED"}
+CSC_FP32 = 0
+CSC_MIXED_BF16 = 1
+
+
+class CscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class csc_params(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int), ("K", ctypes.c_int), ("fs", ctypes.c_int * 2),
+                ("beta", ctypes.c_double), ("rho", ctypes.c_double), ("cg_max", ctypes.c_int),
+                ("cg_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class csc_timing(ctypes.Structure):
+    _fields_ = [("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_int), ("learn_ms", ctypes.c_double),
+                ("learn_calls", ctypes.c_int), ("kernel_launches", ctypes.c_longlong)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built; run paper_1709_09479_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.csc_init.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, ctypes.POINTER(vp)]
+    lib.csc_init.restype = i
+    lib.csc_code.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.csc_code.restype = i
+    lib.csc_learn.argtypes = [vp, vp, vp, vp, vp, i, ctypes.POINTER(i)]
+    lib.csc_learn.restype = i
+    lib.csc_objective.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d)]
+    lib.csc_objective.restype = i
+    lib.csc_destroy.argtypes = [vp]
+    lib.csc_destroy.restype = None
+    lib.csc_last_error.argtypes = [vp]
+    lib.csc_last_error.restype = ctypes.c_char_p
+    lib.csc_timing_enable.argtypes = [vp, i]
+    lib.csc_timing_enable.restype = i
+    lib.csc_timing_read.argtypes = [vp, ctypes.POINTER(csc_timing)]
+    lib.csc_timing_read.restype = i
+    lib.csc_version.argtypes = []
+    lib.csc_version.restype = ctypes.c_char_p
+    return lib
+
+
+LIB = _load()
+
+
+def _ptr(a, dtype):
+    """Data pointer of a contiguous torch tensor / numpy array of the given dtype (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+        return a.ctypes.data
+    import torch
+    want = torch.float32 if dtype == np.float32 else torch.float64
+    if not isinstance(a, torch.Tensor) or a.dtype != want or not a.is_contiguous():
+        raise TypeError(f"expected a contiguous torch tensor of {want}")
+    return a.data_ptr()
+
+
+def _check(status, ctx=None):
+    if status != CSC_OK:
+        raise CscError(status, csc_last_error(ctx))
+
+
+def csc_version() -> str:
+    return LIB.csc_version().decode()
+
+
+def csc_last_error(ctx=None) -> str:
+    return LIB.csc_last_error(ctx).decode()
+
+
+def csc_init(J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6, precision=CSC_FP32,
+             stream=None):
+    """Create a context; returns an opaque handle (int). ``stream``: cudaStream_t as int or None."""
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, precision)
+    dims_arr = (ctypes.c_int * 2)(*dims)
+    out = ctypes.c_void_p()
+    _check(LIB.csc_init(ctypes.byref(p), n_images, dims_arr, stream, ctypes.byref(out)))
+    return out.value
+
+
+def csc_destroy(ctx):
+    LIB.csc_destroy(ctx)
+
+
+def csc_code(ctx, x, d, v, z=None, iters=1):
+    _check(LIB.csc_code(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _ptr(v, np.float32),
+                        _ptr(z, np.float32), iters), ctx)
+
+
+def csc_learn(ctx, x, z, d, mu, steps):
+    its = (ctypes.c_int * max(steps, 1))()
+    _check(LIB.csc_learn(ctx, _ptr(x, np.float32), _ptr(z, np.float32), _ptr(d, np.float32),
+                         _ptr(mu, np.float64), steps, its), ctx)
+    return list(its)[:steps]
+
+
+def csc_objective(ctx, x, d, z) -> float:
+    out = ctypes.c_double()
+    _check(LIB.csc_objective(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _ptr(z, np.float32),
+                             ctypes.byref(out)), ctx)
+    return out.value
+
+
+def csc_timing_enable(ctx, enable=True):
+    _check(LIB.csc_timing_enable(ctx, 1 if enable else 0), ctx)
+
+
+def csc_timing_read(ctx) -> dict:
+    t = csc_timing()
+    _check(LIB.csc_timing_read(ctx, ctypes.byref(t)), ctx)
+    return {"sweep_ms": t.sweep_ms, "sweep_launches": t.sweep_launches, "learn_ms": t.learn_ms,
+            "learn_calls": t.learn_calls, "kernel_launches": t.kernel_launches}
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class Solver:
+    """One context: N images of size dims = (H, W), K filters of support fs with J channels."""
+
+    def __init__(self, *, J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6,
+                 precision=CSC_FP32, stream=None):
+        self.J, self.K, self.fs, self.dims, self.N = J, K, tuple(fs), tuple(dims), n_images
+        self.beta, self.rho = beta, rho
+        if stream is None:
+            stream = _current_stream()
+        self.ctx = csc_init(J, K, fs, dims, n_images, beta, rho, cg_max, cg_tol, precision, stream)
+
+    def code(self, x, d, v, z=None, iters=1):
+        csc_code(self.ctx, x, d, v, z, iters)
+
+    def learn(self, x, z, d, mu, steps):
+        return csc_learn(self.ctx, x, z, d, mu, steps)
+
+    def objective(self, x, d, z):
+        return csc_objective(self.ctx, x, d, z)
+
+    def timing_enable(self, enable=True):
+        csc_timing_enable(self.ctx, enable)
+
+    def timing_read(self):
+        return csc_timing_read(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            csc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,395 @@
+// C ABI of libcsc.so (include/csc.h): argument checks, workspace, host/device staging, and the
+// order of launches for each entry point. All compute runs in the kernels of coding.cu and
+// learning.cu on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "csc_internal.cuh"
+
+using namespace csc;
+
+struct csc_ctx {
+  Ctx c;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+const char* kVersion = "csc-gb300 0.1 (sm_103a)";
+
+csc_status fail(Ctx* c, csc_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  else g_init_error = msg;
+  return s;
+}
+
+csc_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  return fail(c, CSC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CSC_CHECK_CUDA(ctx, call, where)               \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t ensure_alloc(T** p, size_t count) {
+  if (*p) return cudaSuccess;
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+bool radices_ok(const Radices& r) {
+  for (int i = 0; i < r.n_st; ++i)
+    if (!radix_supported_rt(r.r[i])) return false;
+  return true;
+}
+
+// Resolve an array argument to a device pointer, staging host memory into *stage.
+template <class T>
+csc_status stage_in(Ctx* c, const T* user, T** stage, size_t count, const T** dev, bool copy) {
+  if (is_device_ptr(user)) {
+    *dev = user;
+    return CSC_OK;
+  }
+  CSC_CHECK_CUDA(c, ensure_alloc(stage, count), "staging allocation");
+  if (copy)
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(*stage, user, count * sizeof(T), cudaMemcpyHostToDevice, c->stream),
+                   "host-to-device copy");
+  *dev = *stage;
+  return CSC_OK;
+}
+
+// benchmarking aid: open an event bracket (returns its index, or -1 when timing is off)
+int bracket_open(Ctx* c, int kind) {
+  if (!c->timing) return -1;
+  if (c->events_used == c->events.size()) {
+    Ctx::EventPair ep{nullptr, nullptr, kind};
+    if (cudaEventCreate(&ep.a) != cudaSuccess || cudaEventCreate(&ep.b) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    c->events.push_back(ep);
+  }
+  const int i = (int)c->events_used++;
+  c->events[i].kind = kind;
+  cudaEventRecord(c->events[i].a, c->stream);
+  return i;
+}
+
+void bracket_close(Ctx* c, int i) {
+  if (i >= 0) cudaEventRecord(c->events[i].b, c->stream);
+}
+
+void free_all(Ctx* c) {
+  for (auto& ep : c->events) {
+    cudaEventDestroy(ep.a);
+    cudaEventDestroy(ep.b);
+  }
+  c->events.clear();
+  void* ptrs[] = {c->tw, c->dhat, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+                  c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.b, c->L.vec, c->L.mu, c->L.dots, c->L.bar,
+                  c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* csc_version(void) { return kVersion; }
+
+const char* csc_last_error(const csc_ctx* ctx) {
+  return ctx ? ctx->c.last_error.c_str() : g_init_error.c_str();
+}
+
+csc_status csc_init(const csc_params* params, int n_images, const int* dims, void* stream, csc_ctx** out) {
+  if (!params || !dims || !out) return fail(nullptr, CSC_ERR_ARG, "csc_init: null argument");
+  *out = nullptr;
+  const csc_params& p = *params;
+  if (n_images < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init: n_images must be >= 1");
+  if (p.J < 1 || p.J > kMaxJ) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: J must be 1..3");
+  if (p.K < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init: K must be >= 1");
+  if (!(p.beta > 0) || !(p.rho > 0) || !std::isfinite(p.beta) || !std::isfinite(p.rho))
+    return fail(nullptr, CSC_ERR_ARG, "csc_init: beta and rho must be finite and > 0");
+  if (p.cg_max < 1 || !(p.cg_tol > 0)) return fail(nullptr, CSC_ERR_ARG, "csc_init: cg_max >= 1, cg_tol > 0");
+  if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16)
+    return fail(nullptr, CSC_ERR_ARG, "csc_init: unknown precision");
+  if (p.precision != CSC_FP32)
+    return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init: only CSC_FP32 is implemented in this build");
+  const int fh = p.fs[0], fw = p.fs[1];
+  if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter support must be odd and >= 1");
+  if (fw > 15) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter width must be <= 15");
+  const int H = dims[0], W = dims[1];
+  if (H < 8 || W < 8 || (W & 1)) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: need H, W >= 8 and W even");
+  if (fh > H || fw > W) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter larger than the image");
+
+  Ctx tmp;
+  tmp.p = p;
+  tmp.N = n_images; tmp.J = p.J; tmp.K = p.K; tmp.fh = fh; tmp.fw = fw; tmp.S2 = fh * fw;
+  Geometry& g = tmp.g;
+  g.H = H; g.W = W; g.Wh = W / 2; g.Wc = W / 2 + 1; g.P = odd_pitch(g.Wc);
+  g.Omega = H * g.Wc; g.D = H * W;
+  g.ct_id = (H == 128 && W == 128) ? 1 : (H == 100 && W == 100) ? 2 : (H == 64 && W == 64) ? 3 : 0;
+  g.rt.H = H; g.rt.W = W; g.rt.Wh = g.Wh; g.rt.Wc = g.Wc; g.rt.P = g.P; g.rt.Omega = g.Omega; g.rt.D = g.D;
+  g.rt.rrow = factorize(g.Wh);
+  g.rt.rcol = factorize(H);
+  if (!radices_ok(g.rt.rrow) || !radices_ok(g.rt.rcol))
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: H and W/2 must factor into 2, 3, 5 and 7");
+  if (sweep_smem_bytes(g, p.J, kIter) > kSmemLimit)
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: image too large for one map per CTA in shared memory");
+  const size_t cg_smem = ((size_t)p.K * p.J * tmp.S2 + (size_t)(kNT / fh) * fh * p.J * fw) * sizeof(float);
+  if (cg_smem > kSmemLimit)
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
+
+  tmp.stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&tmp.device) != cudaSuccess) return cuda_fail(nullptr, cudaGetLastError(), "cudaGetDevice");
+  cudaError_t e = cudaDeviceGetAttribute(&tmp.nsm, cudaDevAttrMultiProcessorCount, tmp.device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  const long long NK = (long long)tmp.N * tmp.K;
+  tmp.G = (int)std::min<long long>(tmp.nsm, NK);
+
+  csc_ctx* ctx = new (std::nothrow) csc_ctx;
+  if (!ctx) return fail(nullptr, CSC_ERR_WORKSPACE, "csc_init: out of host memory");
+  ctx->c = tmp;
+  Ctx* c = &ctx->c;
+  auto bail = [&](csc_status s) {
+    g_init_error = c->last_error;
+    free_all(c);
+    delete ctx;
+    return s;
+  };
+  const size_t Om = g.Omega;
+  std::vector<float2> tw(g.Wh + g.H + g.Wc);
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int t = 0; t < g.Wh; ++t) tw[t] = make_float2((float)cos(pi2 * t / g.Wh), (float)-sin(pi2 * t / g.Wh));
+  for (int t = 0; t < g.H; ++t)
+    tw[g.Wh + t] = make_float2((float)cos(pi2 * t / g.H), (float)-sin(pi2 * t / g.H));
+  for (int t = 0; t < g.Wc; ++t)
+    tw[g.Wh + g.H + t] = make_float2((float)cos(pi2 * t / g.W), (float)-sin(pi2 * t / g.W));
+  if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->dhat, (size_t)p.K * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->xhat, (size_t)tmp.N * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->pdiag, Om * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->pmat, Om * p.J * p.J * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->part[0], (size_t)(tmp.G + tmp.N) * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->part[1], (size_t)(tmp.G + tmp.N) * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->l1, tmp.G * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->objimg, tmp.N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->last_error = "csc_init: device workspace allocation failed";
+    return bail(CSC_ERR_WORKSPACE);
+  }
+  e = cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    c->last_error = std::string("csc_init: ") + cudaGetErrorString(e);
+    return bail(CSC_ERR_CUDA);
+  }
+  *out = ctx;
+  return CSC_OK;
+}
+
+void csc_destroy(csc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  free_all(&ctx->c);
+  delete ctx;
+}
+
+csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code: null context");
+  Ctx* c = &ctx->c;
+  if (!x || !d || !v) return fail(c, CSC_ERR_ARG, "csc_code: x, d and v must be non-null");
+  if (iters < 0) return fail(c, CSC_ERR_ARG, "csc_code: iters must be >= 0");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
+  const size_t nv = (size_t)c->N * c->K * c->g.D;
+  const float *xd = nullptr, *dd = nullptr, *vd_c = nullptr;
+  csc_status s;
+  if ((s = stage_in(c, v, &c->st_v, nv, &vd_c, true)) != CSC_OK) return s;
+  float* vd = const_cast<float*>(vd_c);
+  const bool v_host = (vd != v);
+  float* zd = nullptr;
+  bool z_host = false;
+  if (z) {
+    if (is_device_ptr(z)) zd = z;
+    else {
+      CSC_CHECK_CUDA(c, ensure_alloc(&c->st_z, nv), "staging allocation");
+      zd = c->st_z;
+      z_host = true;
+    }
+  }
+  if (iters == 0) {
+    if (zd) CSC_CHECK_CUDA(c, launch_codes_from_state(*c, vd, zd), "codes_from_state");
+    if (zd) c->launches += 1;
+  } else {
+    if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+    if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
+    CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
+    CSC_CHECK_CUDA(c, launch_solve_prep(*c), "per-frequency solve setup");
+    CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
+    CSC_CHECK_CUDA(c, launch_sweep(*c, kPrologue, nullptr, c->part[0], vd, nullptr), "coding prologue");
+    c->launches += 4;
+    for (int t = 0; t < iters; ++t) {
+      const int mode = (t == iters - 1) ? kLast : kIter;
+      const int br = (mode == kIter) ? bracket_open(c, 0) : -1;
+      CSC_CHECK_CUDA(c, launch_sweep(*c, mode, c->part[t & 1], c->part[(t + 1) & 1], vd, zd), "coding sweep");
+      bracket_close(c, br);
+      c->launches += 1;
+    }
+  }
+  if (v_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(v, vd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "v copy");
+  if (z_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(z, zd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "z copy");
+  if (v_host || z_host || (xd && xd != x) || (dd && dd != d))
+    CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  return CSC_OK;
+}
+
+csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const float* z, double* out) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_objective: null context");
+  Ctx* c = &ctx->c;
+  if (!x || !d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_objective: null argument");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
+  const size_t nz = (size_t)c->N * c->K * c->g.D;
+  const float *xd, *dd, *zd;
+  csc_status s;
+  if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
+  CSC_CHECK_CUDA(c, launch_sweep(*c, kObjective, nullptr, c->part[0], nullptr, const_cast<float*>(zd)),
+                 "objective sweep");
+  CSC_CHECK_CUDA(c, launch_objective_final(*c, c->part[0], c->objimg), "objective reduction");
+  c->launches += 4;
+  std::vector<double> img(c->N), l1(c->G);
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(img.data(), c->objimg, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "objective copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(l1.data(), c->l1, c->G * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "objective copy");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  double data = 0.0, reg = 0.0;
+  for (double v : img) data += v;
+  for (double v : l1) reg += v;
+  const double f = 0.5 * data + c->p.beta * reg;
+  if (!std::isfinite(f)) return fail(c, CSC_ERR_NONFINITE, "csc_objective: non-finite objective");
+  *out = f;
+  return CSC_OK;
+}
+
+csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, double* mu, int steps,
+                     int* cg_iters) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn: null context");
+  Ctx* c = &ctx->c;
+  if (!x || !z || !d || !mu) return fail(c, CSC_ERR_ARG, "csc_learn: null argument");
+  if (steps < 0) return fail(c, CSC_ERR_ARG, "csc_learn: steps must be >= 0");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const int K = c->K, J = c->J;
+  const size_t nx = (size_t)c->N * J * c->g.D, nd = (size_t)K * J * c->S2;
+  const size_t nz = (size_t)c->N * K * c->g.D, Om = c->g.Omega;
+  const size_t npairs = (size_t)K * (K + 1) / 2;
+  const int La = 2 * c->fh - 1, Lb = 2 * c->fw - 1;
+  LearnBuffers& L = c->L;
+  if (!L.ready) {
+    if (ensure_alloc(&L.zhat, (size_t)c->N * K * Om) != cudaSuccess ||
+        ensure_alloc(&L.gram, npairs * Om) != cudaSuccess ||
+        ensure_alloc(&L.lags, (size_t)K * K * La * Lb) != cudaSuccess ||
+        ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
+        ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
+        ensure_alloc(&L.dots, (size_t)K * 4 * kMaxJ) != cudaSuccess ||
+        ensure_alloc(&L.bar, (size_t)2) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CSC_ERR_WORKSPACE, "csc_learn: device workspace allocation failed");
+    }
+    L.ready = true;
+  }
+  if (steps > L.steps_cap) {
+    if (L.iters) cudaFree(L.iters);
+    L.iters = nullptr;
+    CSC_CHECK_CUDA(c, ensure_alloc(&L.iters, (size_t)steps), "iteration buffer");
+    L.steps_cap = steps;
+  }
+  const float *xd, *zd, *dd_c;
+  csc_status s;
+  if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, (const float*)d, &c->st_d, nd, &dd_c, true)) != CSC_OK) return s;
+  float* dd = const_cast<float*>(dd_c);
+  const bool mu_dev = is_device_ptr(mu);
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(L.mu, mu, K * sizeof(double),
+                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+                 "mu copy");
+  CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
+  const int br = bracket_open(c, 1);
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, zd, c->N * K, 0, L.zhat), "code spectra");
+  CSC_CHECK_CUDA(c, launch_learn_rhs(*c), "learning right-hand side");
+  CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
+  CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
+  CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
+  bracket_close(c, br);
+  c->launches += 6;
+  if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, nd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(mu, L.mu, K * sizeof(double),
+                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+                 "mu copy");
+  int herr = 0;
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
+  std::vector<int> its(std::max(steps, 1));
+  if (cg_iters && steps > 0)
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), L.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                   "iteration copy");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (herr) return fail(c, (csc_status)herr, "csc_learn: grid barrier timed out");
+  if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+  return CSC_OK;
+}
+
+csc_status csc_timing_enable(csc_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_timing_enable: null context");
+  ctx->c.timing = enable != 0;
+  return CSC_OK;
+}
+
+csc_status csc_timing_read(csc_ctx* ctx, csc_timing* out) {
+  if (!ctx || !out) return fail(ctx ? &ctx->c : nullptr, CSC_ERR_ARG, "csc_timing_read: null argument");
+  Ctx* c = &ctx->c;
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  csc_timing t{0.0, 0, 0.0, 0, c->launches};
+  for (size_t i = 0; i < c->events_used; ++i) {
+    float ms = 0.f;
+    CSC_CHECK_CUDA(c, cudaEventElapsedTime(&ms, c->events[i].a, c->events[i].b), "cudaEventElapsedTime");
+    if (c->events[i].kind == 0) { t.sweep_ms += ms; t.sweep_launches += 1; }
+    else { t.learn_ms += ms; t.learn_calls += 1; }
+  }
+  c->events_used = 0;
+  c->launches = 0;
+  *out = t;
+  return CSC_OK;
+}
+
+}  // extern "C"

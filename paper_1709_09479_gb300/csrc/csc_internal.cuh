@@ -1,0 +1,131 @@
+// Internal declarations shared by the translation units of libcsc.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/csc.h"
+#include "fft.cuh"
+
+namespace csc {
+
+constexpr int kNT = 512;              // threads of the per-map kernels
+constexpr int kMaxJ = 3;
+constexpr size_t kSmemLimit = 232448; // 227 KB opt-in shared memory per CTA
+constexpr double kMuFloor = 1e-8;
+
+enum SweepMode { kPrologue = 0, kIter = 1, kLast = 2, kObjective = 3 };
+
+// arguments of the coding sweep (one launch = one pass over all N*K maps)
+struct SweepArgs {
+  int N, K, J, G;        // images, filters, channels, CTAs in the launch
+  float beta, rho;
+  const float2* dhat;    // [K][J][Omega]
+  const float2* xhat;    // [N][J][Omega]
+  const float* pdiag;    // J == 1: [Omega] 1/(sum_k |dhat_k|^2 + 1/rho) / D
+  const float2* pmat;    // J > 1: [Omega][J][J] (A + I/rho)^{-1} / D
+  const float2* part_in; // [(G+N)][J][Omega] partial sums of the previous sweep
+  float2* part_out;      // [(G+N)][J][Omega]
+  float* v;              // [N][K][D] ADMM state
+  float* z;              // [N][K][D] codes: written by kLast (may be null), read by kObjective
+  double* l1;            // [G] per-CTA sum |z| (kObjective)
+  const float2* tw;      // twiddles [Wh | H | Wc]
+};
+
+struct Ctx;
+
+// geometry of the (uniform) batch, chosen at csc_init
+struct Geometry {
+  int H, W, Wh, Wc, P, Omega, D;
+  int ct_id;     // 0: run-time geometry; 1: 128x128; 2: 100x100; 3: 64x64
+  GeoRT rt;
+};
+
+struct LearnBuffers {
+  bool ready = false;
+  float2* zhat = nullptr;   // [N][K][Omega]
+  float2* gram = nullptr;   // [npairs][Omega], pairs k <= k'
+  float* lags = nullptr;    // [K][K][L*L]
+  float* b = nullptr;       // [K][J][S2]
+  float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
+  double* mu = nullptr;     // [K]
+  double* dots = nullptr;   // [G][J][4]
+  unsigned* bar = nullptr;  // grid barrier {count, generation}
+  int* iters = nullptr;     // [steps_cap]
+  int steps_cap = 0;
+};
+
+struct Ctx {
+  csc_params p;
+  int N, J, K, fh, fw, S2;
+  Geometry g;
+  cudaStream_t stream;
+  int device, nsm;
+  int G;                    // CTAs of the coding sweep
+  size_t sweep_smem;
+  // workspace
+  float2* tw = nullptr;
+  float2* dhat = nullptr;
+  float2* xhat = nullptr;
+  float* pdiag = nullptr;
+  float2* pmat = nullptr;
+  float2* part[2] = {nullptr, nullptr};
+  double* l1 = nullptr;
+  double* objimg = nullptr;
+  int* err = nullptr;
+  LearnBuffers L;
+  // staging of host arrays
+  float* st_x = nullptr;
+  float* st_d = nullptr;
+  float* st_v = nullptr;
+  float* st_z = nullptr;
+  double* st_mu = nullptr;
+  std::string last_error;
+  // benchmarking aid: event pairs around sweeps (kind 0) and learning calls (kind 1)
+  bool timing = false;
+  struct EventPair { cudaEvent_t a, b; int kind; };
+  std::vector<EventPair> events;
+  size_t events_used = 0;
+  mutable long long launches = 0;
+};
+
+// per-geometry launchers of the per-map kernels (geo_*.cu)
+struct GeoOps {
+  cudaError_t (*fft_maps)(const Ctx&, const float* in, int nmaps, int filter_mode, float2* out);
+  cudaError_t (*sweep)(const Ctx&, int mode, const SweepArgs&);
+  cudaError_t (*rhs)(const Ctx&);
+  cudaError_t (*lags)(const Ctx&);
+};
+const GeoOps& geo_ops_128();
+const GeoOps& geo_ops_100();
+const GeoOps& geo_ops_64();
+const GeoOps& geo_ops_rt();
+inline const GeoOps& geo_ops(const Ctx& c);
+
+// launchers (coding.cu)
+cudaError_t launch_fft_maps(const Ctx& c, const float* in, int nmaps, int filter_mode, float2* out);
+cudaError_t launch_solve_prep(const Ctx& c);
+cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
+                         float* z);
+cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z);
+cudaError_t launch_objective_final(const Ctx& c, const float2* part, double* out_img);
+size_t sweep_smem_bytes(const Geometry& g, int J, int mode);
+
+// launchers (learning.cu)
+cudaError_t launch_learn_rhs(const Ctx& c);
+cudaError_t launch_learn_gram(const Ctx& c);
+cudaError_t launch_learn_lags(const Ctx& c);
+cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
+
+inline const GeoOps& geo_ops(const Ctx& c) {
+  switch (c.g.ct_id) {
+    case 1: return geo_ops_128();
+    case 2: return geo_ops_100();
+    case 3: return geo_ops_64();
+    default: return geo_ops_rt();
+  }
+}
+
+}  // namespace csc

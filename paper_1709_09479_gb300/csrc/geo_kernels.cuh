@@ -1,0 +1,357 @@
+// Per-map kernels (one CTA transforms one H x W map in shared memory), templated on the image
+// geometry. Each geo_*.cu translation unit instantiates them for one geometry and exports the
+// launchers through a GeoOps table, so the fixed sizes compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "csc_internal.cuh"
+
+namespace csc {
+
+__device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
+
+// ---------------------------------------------------------------------------------------------
+// batched forward transforms of real maps or of filters placed on the grid
+// ---------------------------------------------------------------------------------------------
+struct FftMapsArgs {
+  const float* in;
+  int nmaps;
+  int filter_mode;   // 0: maps [m][H][W]; 1: filters [m][fh][fw] centred on the grid
+  int fh, fw;
+  float2* out;       // [m][Omega]
+  const float2* tw;
+};
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_fft_maps(FftMapsArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega();
+  float2* buf = sm;
+  Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  float* bf = reinterpret_cast<float*>(buf);
+  for (int m = blockIdx.x; m < a.nmaps; m += gridDim.x) {
+    __syncthreads();
+    if (a.filter_mode) {
+      for (int i = threadIdx.x; i < H * P; i += NT) buf[i] = make_float2(0.f, 0.f);
+      __syncthreads();
+      const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
+      const float* f = a.in + (size_t)m * a.fh * a.fw;
+      for (int t = threadIdx.x; t < a.fh * a.fw; t += NT) {
+        const int ta = t / a.fw, tb = t - ta * a.fw;
+        const int h = ((ta - ch) % H + H) % H, w = ((tb - cw) % W + W) % W;
+        bf[2 * P * h + w] = f[t];
+      }
+    } else {
+      const float* src = a.in + (size_t)m * H * W;
+      for (int p = threadIdx.x; p < H * W; p += NT) {
+        const int h = p / W, w = p - h * W;
+        bf[2 * P * h + w] = src[p];
+      }
+    }
+    __syncthreads();
+    rfft2<G, NT>(g, buf, tw);
+    float2* dst = a.out + (size_t)m * Om;
+    for (int o = threadIdx.x; o < Om; o += NT) {
+      const int h = o / Wc, c = o - h * Wc;
+      dst[o] = buf[h * P + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// the fused coding sweep
+// ---------------------------------------------------------------------------------------------
+template <class G, int MODE, int NT>
+__global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
+  extern __shared__ float2 sm[];
+  constexpr bool kLam = (MODE == kIter || MODE == kLast);
+  constexpr bool kAcc = (MODE != kLast);
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega(), D = g.d();
+  const int J = a.J;
+  float2* buf = sm;
+  float2* lam = buf + H * P;
+  float2* acc = lam + (kLam ? J * Om : 0);
+  float2* tws = acc + (kAcc ? J * Om : 0);
+  const Twiddles tw = stage_twiddles<G, NT>(g, tws, a.tw);
+  float* bf = reinterpret_cast<float*>(buf);
+  __syncthreads();
+
+  const long long NK = (long long)a.N * a.K;
+  const int cta = blockIdx.x;
+  const long long m0 = (long long)cta * NK / a.G, m1 = (long long)(cta + 1) * NK / a.G;
+  const float beta = a.beta;
+  double l1 = 0.0;
+
+  for (long long n = m0 / a.K; n * a.K < m1; ++n) {
+    const int kb = (int)(max(m0, n * a.K) - n * a.K);
+    const int ke = (int)(min(m1, (n + 1) * a.K) - n * a.K);
+    if (kLam) {
+      // lambda_hat / D for image n from the previous sweep's partial sums (slot = cta' + n)
+      const int c0 = (int)(((n * a.K + 1) * a.G - 1) / NK);
+      const int c1 = (int)((((n + 1) * a.K) * a.G - 1) / NK);
+      const float irho = 1.0f / a.rho;
+      const float2* xh = a.xhat + (size_t)n * J * Om;
+      for (int o = threadIdx.x; o < Om; o += NT) {
+        float2 r[kMaxJ];
+        for (int j = 0; j < J; ++j) {
+          const float2 x = xh[(size_t)j * Om + o];
+          float2 s = make_float2(-x.x * irho, -x.y * irho);
+          for (int c = c0; c <= c1; ++c) s = cadd(s, a.part_in[((size_t)(c + n) * J + j) * Om + o]);
+          r[j] = s;
+        }
+        if (J == 1) {
+          lam[o] = cscale(r[0], a.pdiag[o]);
+        } else {
+          const float2* pm = a.pmat + (size_t)o * J * J;
+          for (int i = 0; i < J; ++i) {
+            float2 s = make_float2(0.f, 0.f);
+            for (int j = 0; j < J; ++j) s = cfma(pm[i * J + j], r[j], s);
+            lam[(size_t)i * Om + o] = s;
+          }
+        }
+      }
+    }
+    if (kAcc)
+      for (int i = threadIdx.x; i < J * Om; i += NT) acc[i] = make_float2(0.f, 0.f);
+
+    for (int k = kb; k < ke; ++k) {
+      const size_t map = (size_t)n * a.K + k;
+      float* vk = a.v ? a.v + map * D : nullptr;
+      const float2* dk = a.dhat + (size_t)k * J * Om;
+      if (kLam) {
+        // w_hat_k = sum_j conj(d_hat_jk) lam_j
+        for (int o = threadIdx.x; o < Om; o += NT) {
+          float2 s = make_float2(0.f, 0.f);
+          for (int j = 0; j < J; ++j) s = cfmac(dk[(size_t)j * Om + o], lam[(size_t)j * Om + o], s);
+          const int h = o / Wc, c = o - h * Wc;
+          buf[h * P + c] = s;
+        }
+        __syncthreads();
+        irfft2<G, NT>(g, buf, tw);
+        float* zk = (MODE == kLast && a.z) ? a.z + map * D : nullptr;
+        for (int p = threadIdx.x; p < D; p += NT) {
+          const int h = p / W, x = p - h * W;
+          float* cell = bf + 2 * P * h + x;
+          const float vo = vk[p];
+          const float vn = *cell - (clampb(vo, beta) - vo);
+          vk[p] = vn;
+          const float cn = clampb(vn, beta);
+          if (MODE == kLast) {
+            if (zk) zk[p] = a.rho * (cn - vn);
+          } else {
+            *cell = 2.f * cn - vn;
+          }
+        }
+      } else if (MODE == kPrologue) {
+        for (int p = threadIdx.x; p < D; p += NT) {
+          const int h = p / W, x = p - h * W;
+          const float vo = vk[p];
+          bf[2 * P * h + x] = 2.f * clampb(vo, beta) - vo;
+        }
+      } else {  // kObjective: transform the codes themselves
+        const float* zk = a.z + map * D;
+        for (int p = threadIdx.x; p < D; p += NT) {
+          const int h = p / W, x = p - h * W;
+          const float zz = zk[p];
+          l1 += fabsf(zz);
+          bf[2 * P * h + x] = zz;
+        }
+      }
+      if (kAcc) {
+        __syncthreads();
+        rfft2<G, NT>(g, buf, tw);
+        for (int o = threadIdx.x; o < Om; o += NT) {
+          const int h = o / Wc, c = o - h * Wc;
+          const float2 u = buf[h * P + c];
+          for (int j = 0; j < J; ++j)
+            acc[(size_t)j * Om + o] = cfma(dk[(size_t)j * Om + o], u, acc[(size_t)j * Om + o]);
+        }
+      }
+      __syncthreads();
+    }
+    if (kAcc) {
+      float2* dst = a.part_out + (size_t)(cta + n) * J * Om;
+      for (int i = threadIdx.x; i < J * Om; i += NT) dst[i] = acc[i];
+    }
+  }
+  if (MODE == kObjective) {
+    __shared__ double red[NT / 32];
+    for (int off = 16; off > 0; off >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < NT / 32; ++i) s += red[i];
+      a.l1[cta] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// b_kj = S F^{-1}( sum_n conj(z_hat_nk) x_hat_nj ) / D: one CTA per (k, j)
+// ---------------------------------------------------------------------------------------------
+struct RhsArgs {
+  int N, K, J, fh, fw;
+  const float2* zhat;  // [N][K][Omega]
+  const float2* xhat;  // [N][J][Omega]
+  float* b;            // [K][J][fh*fw]
+  const float2* tw;
+};
+
+template <class G, int NT>
+__device__ __forceinline__ void crop_window(const G& g, const float* bf, int wa, int wb, int ca, int cb,
+                                            float scale, float* out) {
+  const int H = g.h(), W = g.w(), P = g.p();
+  for (int t = threadIdx.x; t < wa * wb; t += NT) {
+    const int ta = t / wb, tb = t - ta * wb;
+    const int h = ((ta - ca) % H + H) % H, w = ((tb - cb) % W + W) % W;
+    out[t] = bf[2 * P * h + w] * scale;
+  }
+}
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_learn_rhs(RhsArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), P = g.p(), Wc = g.wc(), Om = g.omega();
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  const int k = blockIdx.x / a.J, j = blockIdx.x % a.J;
+  for (int o = threadIdx.x; o < Om; o += NT) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int n = 0; n < a.N; ++n)
+      s = cfmac(a.zhat[((size_t)n * a.K + k) * Om + o], a.xhat[((size_t)n * a.J + j) * Om + o], s);
+    const int h = o / Wc, c = o - h * Wc;
+    buf[h * P + c] = s;
+  }
+  __syncthreads();
+  irfft2<G, NT>(g, buf, tw);
+  crop_window<G, NT>(g, reinterpret_cast<const float*>(buf), a.fh, a.fw, (a.fh - 1) / 2, (a.fw - 1) / 2,
+                     1.0f / (float)g.d(), a.b + ((size_t)k * a.J + j) * a.fh * a.fw);
+}
+
+// ---------------------------------------------------------------------------------------------
+// lags C_kk'(tau), tau in [-(fh-1), fh-1] x [-(fw-1), fw-1], one CTA per pair k <= k'
+// ---------------------------------------------------------------------------------------------
+struct LagsArgs {
+  int K, fh, fw;
+  const float2* gram;
+  float* lags;   // [K][K][La][Lb]
+  const float2* tw;
+};
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_learn_lags(LagsArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega();
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  // pair index -> (k, k')
+  int k = 0;
+  long long rem = blockIdx.x;
+  while (rem >= a.K - k) { rem -= a.K - k; ++k; }
+  const int kp = k + (int)rem;
+  const float2* src = a.gram + (size_t)blockIdx.x * Om;
+  for (int o = threadIdx.x; o < Om; o += NT) {
+    const int h = o / Wc, c = o - h * Wc;
+    buf[h * P + c] = src[o];
+  }
+  __syncthreads();
+  irfft2<G, NT>(g, buf, tw);
+  const float* bf = reinterpret_cast<const float*>(buf);
+  const int La = 2 * a.fh - 1, Lb = 2 * a.fw - 1;
+  const float scale = 1.0f / (float)g.d();
+  float* out = a.lags + ((size_t)k * a.K + kp) * La * Lb;
+  float* outT = a.lags + ((size_t)kp * a.K + k) * La * Lb;
+  for (int t = threadIdx.x; t < La * Lb; t += NT) {
+    const int ta = t / Lb, tb = t - ta * Lb;
+    const int h = ((ta - (a.fh - 1)) % H + H) % H, w = ((tb - (a.fw - 1)) % W + W) % W;
+    const float val = bf[2 * P * h + w] * scale;
+    if (k == kp) {
+      // autocorrelation: C_kk(tau) = C_kk(-tau); store the symmetrised value so the matrix of the
+      // normal equations is exactly symmetric (one writer per entry)
+      const int hm = ((-(ta - (a.fh - 1))) % H + H) % H, wm = ((-(tb - (a.fw - 1))) % W + W) % W;
+      out[t] = 0.5f * (val + bf[2 * P * hm + wm] * scale);
+    } else {
+      out[t] = val;
+      outT[(La - 1 - ta) * Lb + (Lb - 1 - tb)] = val;   // C_k'k(tau) = C_kk'(-tau)
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// launchers for one geometry
+// ---------------------------------------------------------------------------------------------
+inline size_t map_smem_bytes(const Geometry& g) {
+  return ((size_t)g.H * g.P + (size_t)(g.Wh + g.H + g.Wc)) * sizeof(float2);
+}
+
+template <class GEO>
+struct GeoLaunch {
+  static GEO geo(const Ctx& c) {
+    if constexpr (std::is_same<GEO, GeoRT>::value) return c.g.rt;
+    else return GEO{};
+  }
+
+  static cudaError_t fft_maps(const Ctx& c, const float* in, int nmaps, int filter_mode, float2* out) {
+    if (nmaps <= 0) return cudaSuccess;
+    FftMapsArgs a{in, nmaps, filter_mode, c.fh, c.fw, out, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    const int grid = std::min(nmaps, c.nsm * 4);
+    auto kern = k_fft_maps<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  template <int MODE>
+  static cudaError_t sweep_mode(const Ctx& c, const SweepArgs& a) {
+    auto kern = k_sweep<GEO, MODE, kNT>;
+    const size_t smem = sweep_smem_bytes(c.g, c.J, MODE);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<c.G, kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t sweep(const Ctx& c, int mode, const SweepArgs& a) {
+    switch (mode) {
+      case kPrologue: return sweep_mode<kPrologue>(c, a);
+      case kIter: return sweep_mode<kIter>(c, a);
+      case kLast: return sweep_mode<kLast>(c, a);
+      default: return sweep_mode<kObjective>(c, a);
+    }
+  }
+
+  static cudaError_t rhs(const Ctx& c) {
+    RhsArgs a{c.N, c.K, c.J, c.fh, c.fw, c.L.zhat, c.xhat, c.L.b, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    auto kern = k_learn_rhs<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<c.K * c.J, kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t lags(const Ctx& c) {
+    LagsArgs a{c.K, c.fh, c.fw, c.L.gram, c.L.lags, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    const int npairs = c.K * (c.K + 1) / 2;
+    auto kern = k_learn_lags<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<npairs, kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static const GeoOps& ops() {
+    static const GeoOps o{&fft_maps, &sweep, &rhs, &lags};
+    return o;
+  }
+};
+
+}  // namespace csc

@@ -1,0 +1,56 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/csc.h declares.
+Argument checks that fail before any CUDA call are exercised here without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1709_09479_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(csc_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"csc_init", "csc_code", "csc_learn", "csc_objective", "csc_destroy"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_argument_errors_without_gpu(lib):
+    from paper_1709_09479_gb300 import csc
+    assert "sm_103a" in csc.csc_version()
+    with pytest.raises(csc.CscError) as e:
+        csc.csc_init(J=4, K=2, fs=(3, 3), dims=(16, 16), n_images=1, beta=1.0, rho=1.0)
+    assert e.value.status == 2 and "J" in str(e.value)
+    with pytest.raises(csc.CscError) as e:
+        csc.csc_init(J=1, K=2, fs=(4, 3), dims=(16, 16), n_images=1, beta=1.0, rho=1.0)
+    assert e.value.status == 2
+    with pytest.raises(csc.CscError) as e:
+        csc.csc_init(J=1, K=2, fs=(3, 3), dims=(16, 15), n_images=1, beta=1.0, rho=1.0)
+    assert e.value.status == 2
+    with pytest.raises(csc.CscError) as e:
+        csc.csc_init(J=1, K=2, fs=(3, 3), dims=(22, 16), n_images=1, beta=1.0, rho=1.0)   # 11 | H
+    assert e.value.status == 2
+    with pytest.raises(csc.CscError) as e:
+        csc.csc_init(J=1, K=2, fs=(3, 3), dims=(16, 16), n_images=1, beta=-1.0, rho=1.0)
+    assert e.value.status == 1
+    assert lib.csc_code(None, None, None, None, None, 1) == 1
+
