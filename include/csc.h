@@ -131,6 +131,26 @@ csc_status csc_timing_enable(csc_ctx* ctx, int enable);
 /* Read and reset the accumulated timing (synchronises the stream). */
 csc_status csc_timing_read(csc_ctx* ctx, csc_timing* out);
 
+/*
+ * csc_code without a context and without allocating: the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory where they code images (code running while a CUDA
+ * graph is being captured, code inside a framework whose allocator owns the whole device pool, or
+ * plugins that are only handed a stream and device pointers).
+ * Same computation, arguments and layouts as csc_init(params, n_images, dims, stream) followed by
+ * csc_code(x, d, v, z, iters), except that x, d, v and z must be device pointers. The workspace is
+ * a fixed 64 MiB file-scope __device__ array that every GPU loading the library holds until the
+ * process exits; problems needing more return CSC_ERR_SHAPE with the byte count in
+ * csc_last_error(NULL) (e.g. N = 100, K = 100, 128 x 128 needs about 47 MB and fits).
+ * No cudaMalloc, cudaFree or other allocating call is made. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. Every call shares the one array and leaves its contents behind (each call
+ * rewrites everything it reads), so calls that may overlap on the GPU (different streams or
+ * devices sharing nothing else) race: serialise them on one stream. Asynchronous on `stream`.
+ * Errors are reported through the return value and csc_last_error(NULL).
+ */
+csc_status csc_code_noalloc(const csc_params* params, int n_images, const int* dims, void* stream,
+                            const float* x, const float* d, float* v, float* z, int iters);
+
 /* Release the context and its workspace. NULL is ignored. */
 void csc_destroy(csc_ctx* ctx);
 

@@ -63,6 +63,8 @@ def _load():
     lib.csc_timing_enable.restype = i
     lib.csc_timing_read.argtypes = [vp, ctypes.POINTER(csc_timing)]
     lib.csc_timing_read.restype = i
+    lib.csc_code_noalloc.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i]
+    lib.csc_code_noalloc.restype = i
     lib.csc_version.argtypes = []
     lib.csc_version.restype = ctypes.c_char_p
     return lib
@@ -130,6 +132,16 @@ def csc_objective(ctx, x, d, z) -> float:
     _check(LIB.csc_objective(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _ptr(z, np.float32),
                              ctypes.byref(out)), ctx)
     return out.value
+
+
+def csc_code_noalloc(J, K, fs, dims, n_images, beta, rho, x, d, v, z=None, iters=1, stream=None):
+    """The context-free, allocation-free coding call (device arrays only; see include/csc.h)."""
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, CSC_FP32)
+    dims_arr = (ctypes.c_int * 2)(*dims)
+    if stream is None:
+        stream = _current_stream()
+    _check(LIB.csc_code_noalloc(ctypes.byref(p), n_images, dims_arr, stream, _ptr(x, np.float32),
+                                _ptr(d, np.float32), _ptr(v, np.float32), _ptr(z, np.float32), iters))
 
 
 def csc_timing_enable(ctx, enable=True):

@@ -113,6 +113,10 @@ void free_all(Ctx* c) {
 
 }  // namespace
 
+namespace csc {
+void set_global_error(const char* msg) { g_init_error = msg; }
+}  // namespace csc
+
 extern "C" {
 
 const char* csc_version(void) { return kVersion; }

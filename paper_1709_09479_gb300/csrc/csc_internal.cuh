@@ -113,6 +113,9 @@ cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z);
 cudaError_t launch_objective_final(const Ctx& c, const float2* part, double* out_img);
 size_t sweep_smem_bytes(const Geometry& g, int J, int mode);
 
+// message returned by csc_last_error(NULL) (api.cu)
+void set_global_error(const char* msg);
+
 // launchers (learning.cu)
 cudaError_t launch_learn_rhs(const Ctx& c);
 cudaError_t launch_learn_gram(const Ctx& c);
