@@ -157,6 +157,8 @@ cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* 
   a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
   a.dhat = c.dhat; a.xhat = c.xhat; a.pdiag = c.pdiag; a.pmat = c.pmat;
   a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1; a.tw = c.tw;
+  const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0);
+  a.vec4 = (al && c.g.D % 16 == 0 && c.g.W % 4 == 0) ? 1 : 0;
   return geo_ops(c).sweep(c, mode, a);
 }
 

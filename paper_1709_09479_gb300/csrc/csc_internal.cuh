@@ -12,6 +12,7 @@
 namespace csc {
 
 constexpr int kNT = 512;              // threads of the per-map kernels
+constexpr int kNTSweep = 512;         // threads of the coding sweep
 constexpr int kMaxJ = 3;
 constexpr size_t kSmemLimit = 232448; // 227 KB opt-in shared memory per CTA
 constexpr double kMuFloor = 1e-8;
@@ -32,6 +33,7 @@ struct SweepArgs {
   float* z;              // [N][K][D] codes: written by kLast (may be null), read by kObjective
   double* l1;            // [G] per-CTA sum |z| (kObjective)
   const float2* tw;      // twiddles [Wh | H | Wc]
+  int vec4;              // v, z 16-byte aligned and D % 16 == 0: 4-pixel vector path + L2 prefetch
 };
 
 struct Ctx;

@@ -10,7 +10,8 @@
 //     on consecutive columns) hit 16 distinct 8-byte bank pairs per half-warp;
 //   * rows: a real row of W samples is read as W/2 complex values y[m] = x[2m] + i x[2m+1],
 //     transformed with a W/2-point complex FFT and split into the W/2+1 bins of the real DFT;
-//   * columns: Wc complex FFTs of length H;
+//   * columns: W/2 complex FFTs of length H: the row DC and Nyquist bins are real, so they travel
+//     together as one complex column and are separated after the transform;
 //   * 1-D FFTs: mixed-radix Stockham (radices 16, 8, 4, 2, 5, 3 hand-written, 7 by direct DFT),
 //     in place: every round reads its butterflies into registers, syncs, writes.
 //
@@ -141,9 +142,10 @@ template <bool INV> CSC_D void dft8(float2* a) {
   a[3] = cadd(e3, w3); a[7] = csub(e3, w3);
 }
 
-// 16 = 4 x 4: input n = 4 n1 + n2, output k = k1 + 4 k2
+// 16 = 4 x 4: input n = 4 n1 + n2, output k = k1 + 4 k2 left at a[4 k1 + k2] (transposed;
+// out_slot<16> gives the position of output k, resolved at compile time by the caller)
 template <bool INV> CSC_D void dft16(float2* a) {
-  // cos/sin(2 pi m / 16) for m = 1..3 (the twiddles w16^(n2 k1) with n2,k1 in 0..3 need m up to 9)
+  // cos/sin(2 pi m / 16), m = 1, 3 (the twiddles w16^(n2 k1) with n2, k1 in 0..3 need m up to 9)
   constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) dft4v<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
@@ -164,16 +166,12 @@ template <bool INV> CSC_D void dft16(float2* a) {
   a[13] = rot(a[13], s1, c1);
   a[14] = rot(a[14], -kSqrtHalf, kSqrtHalf);
   a[15] = rot(a[15], -c1, -s1);
-  float2 o[16];
 #pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    float2 b0 = a[4 * k1], b1 = a[4 * k1 + 1], b2 = a[4 * k1 + 2], b3 = a[4 * k1 + 3];
-    dft4v<INV>(b0, b1, b2, b3);
-    o[k1] = b0; o[k1 + 4] = b1; o[k1 + 8] = b2; o[k1 + 12] = b3;
-  }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = o[i];
+  for (int k1 = 0; k1 < 4; ++k1) dft4v<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
 }
+
+// register slot holding output k of dft<R> (identity except for the transposed radix 16)
+template <int R> CSC_HD constexpr int out_slot(int k) { return R == 16 ? 4 * (k % 4) + k / 4 : k; }
 
 template <bool INV> CSC_D void dft3(float2* a) {
   constexpr float h = 0.86602540378443864676f;  // sin(2 pi / 3)
@@ -235,12 +233,19 @@ template <int R, bool INV> CSC_D void dft(float2* a, const float2* tw, int n) {
 // one Stockham stage over a batch of lines, in place
 //   line L element e at buf[L*lstride + e*es]; Ns = product of earlier radices.
 // ---------------------------------------------------------------------------------------------
-template <int R> constexpr int items_per_thread() { return R >= 16 ? 2 : (32 / R > 0 ? 32 / R : 1); }
+// butterflies a thread holds per round: a register budget of 32 complex values (16 at 1024
+// threads); fixed-size plans ask for no more than one round needs (see stage_ipt)
+template <int R, int NT> constexpr int items_per_thread() {
+  return (NT >= 1024 ? 16 : 32) / R > 0 ? (NT >= 1024 ? 16 : 32) / R : 1;
+}
+CSC_HD constexpr int stage_ipt(int R, int NT, int n, int nlines, int cap) {
+  const int need = (nlines * (n / R) + NT - 1) / NT;
+  return need < cap ? (need > 0 ? need : 1) : cap;
+}
 
-template <int R, bool INV, int NT>
+template <int R, bool INV, int NT, int IPT = items_per_thread<R, NT>()>
 CSC_D void fft_stage(float2* __restrict__ buf, int nlines, int lstride, int es, int n, int Ns,
                      const float2* __restrict__ tw) {
-  constexpr int IPT = items_per_thread<R>();
   const int nb = n / R;
   int lpr = (NT * IPT) / nb;
   if (lpr > nlines) lpr = nlines;
@@ -275,22 +280,23 @@ CSC_D void fft_stage(float2* __restrict__ buf, int nlines, int lstride, int es, 
         const int k = j % Ns;
         float2* dst = buf + line * lstride + ((j - k) * R + k) * es;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[r * Ns * es] = v[it][r];
+        for (int r = 0; r < R; ++r) dst[r * Ns * es] = v[it][out_slot<R>(r)];
       }
     }
   }
   __syncthreads();
 }
 
-// all stages of a length-N transform, radices fixed at compile time
-template <int N, int S, bool INV, int NT>
-CSC_D void stages_ct(float2* buf, int nlines, int lstride, int es, const float2* tw) {
+// all stages of a length-N transform over NLINES lines, radices fixed at compile time
+template <int N, int S, bool INV, int NT, int NLINES>
+CSC_D void stages_ct(float2* buf, int lstride, int es, const float2* tw) {
   constexpr Radices rr = factorize(N);
   if constexpr (S < rr.n_st) {
     constexpr int R = rr.r[S];
     constexpr int NS = ns_before(rr, S);
-    fft_stage<R, INV, NT>(buf, nlines, lstride, es, N, NS, tw);
-    stages_ct<N, S + 1, INV, NT>(buf, nlines, lstride, es, tw);
+    constexpr int IPT = stage_ipt(R, NT, N, NLINES, items_per_thread<R, NT>());
+    fft_stage<R, INV, NT, IPT>(buf, NLINES, lstride, es, N, NS, tw);
+    stages_ct<N, S + 1, INV, NT, NLINES>(buf, lstride, es, tw);
   }
 }
 
@@ -335,10 +341,10 @@ struct GeoCT {
   CSC_D int omega() const { return Omega; }
   CSC_D int d() const { return D; }
   template <bool INV, int NT> CSC_D void rows(float2* buf, const float2* tw) const {
-    stages_ct<Wh, 0, INV, NT>(buf, H, P, 1, tw);
+    stages_ct<Wh, 0, INV, NT, H>(buf, P, 1, tw);
   }
   template <bool INV, int NT> CSC_D void cols(float2* buf, const float2* tw) const {
-    stages_ct<H, 0, INV, NT>(buf, Wc, 1, P, tw);
+    stages_ct<H, 0, INV, NT, Wh>(buf, 1, P, tw);
   }
 };
 
@@ -356,7 +362,7 @@ struct GeoRT {
     stages_rt<INV, NT>(buf, H, P, 1, Wh, rrow, tw);
   }
   template <bool INV, int NT> CSC_D void cols(float2* buf, const float2* tw) const {
-    stages_rt<INV, NT>(buf, Wc, 1, P, H, rcol, tw);
+    stages_rt<INV, NT>(buf, Wh, 1, P, H, rcol, tw);
   }
 };
 
@@ -381,9 +387,9 @@ CSC_D void split_rows_forward(const G& g, float2* buf, const float2* wsplit) {
     const int h = i % H, k = i / H;
     float2* row = buf + h * P;
     if (k == 0) {
+      // the real DC and Nyquist bins of the row share bin 0: X[0] + i X[Wh]
       const float2 y = row[0];
-      row[0] = make_float2(y.x + y.y, 0.f);
-      row[Wh] = make_float2(y.x - y.y, 0.f);
+      row[0] = make_float2(y.x + y.y, y.x - y.y);
     } else {
       const int k2 = Wh - k;
       const float2 ya = row[k], yb = row[k2];
@@ -413,7 +419,8 @@ CSC_D void split_rows_inverse(const G& g, float2* buf, const float2* wsplit) {
     const int h = i % H, k = i / H;
     float2* row = buf + h * P;
     if (k == 0) {
-      const float a = row[0].x, b = row[Wh].x;
+      // bin 0 carries the row's DC (real part) and Nyquist (imaginary part) values
+      const float a = row[0].x, b = row[0].y;
       row[0] = make_float2(a + b, a - b);
     } else {
       const int k2 = Wh - k;
@@ -438,16 +445,54 @@ CSC_D void split_rows_inverse(const G& g, float2* buf, const float2* wsplit) {
 
 // Forward: real map (float offset 2*P*h + w) -> half spectrum (complex offset h*P + c).
 // Caller syncs before (the map must be complete). Ends synced.
+// the 2-D transforms are calls, not inlined: each gets its own register allocation, which
+// measured faster than inlining them into the sweep (1.94 vs 2.17 ms per 128x128 sweep)
+#define CSC_FFT2_ATTR __device__ __noinline__
+// After the column FFT, column 0 holds Z = F(x_dc + i x_nyq) of two real columns:
+// X_dc(k) = (Z(k) + conj Z(-k))/2 stays in column 0, X_nyq(k) = (Z(k) - conj Z(-k))/(2i) goes to
+// column Wh. Pairs (k, H-k) are handled by one thread, so no other thread touches its bins.
 template <class G, int NT>
-CSC_D void rfft2(const G& g, float2* buf, const Twiddles& tw) {
+CSC_D void unpack_dc_nyquist(const G& g, float2* buf) {
+  const int H = g.h(), Wh = g.wh(), P = g.p();
+  for (int k = threadIdx.x; k <= H / 2; k += NT) {
+    const int k2 = (H - k) % H;
+    const float2 a = buf[k * P], b = buf[k2 * P];
+    // (a + conj b)/2 and (a - conj b)/(2i)
+    const float2 dc = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+    const float2 ny = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+    buf[k * P] = dc;
+    buf[k * P + Wh] = ny;
+    if (k2 != k) {
+      buf[k2 * P] = make_float2(dc.x, -dc.y);
+      buf[k2 * P + Wh] = make_float2(ny.x, -ny.y);
+    }
+  }
+  __syncthreads();
+}
+
+// Inverse of the above before the inverse column FFT: column 0 <- X_dc + i X_nyq.
+template <class G, int NT>
+CSC_D void pack_dc_nyquist(const G& g, float2* buf) {
+  const int H = g.h(), Wh = g.wh(), P = g.p();
+  for (int k = threadIdx.x; k < H; k += NT) {
+    const float2 dc = buf[k * P], ny = buf[k * P + Wh];
+    buf[k * P] = make_float2(dc.x - ny.y, dc.y + ny.x);
+  }
+  __syncthreads();
+}
+
+template <class G, int NT>
+CSC_FFT2_ATTR void rfft2(const G g, float2* buf, const Twiddles tw) {
   g.template rows<false, NT>(buf, tw.row);
   split_rows_forward<G, NT>(g, buf, tw.split);
   g.template cols<false, NT>(buf, tw.col);
+  unpack_dc_nyquist<G, NT>(g, buf);
 }
 
 // Inverse (unnormalised, result scaled by D = H*W): half spectrum -> real map.
 template <class G, int NT>
-CSC_D void irfft2(const G& g, float2* buf, const Twiddles& tw) {
+CSC_FFT2_ATTR void irfft2(const G g, float2* buf, const Twiddles tw) {
+  pack_dc_nyquist<G, NT>(g, buf);
   g.template cols<true, NT>(buf, tw.col);
   split_rows_inverse<G, NT>(g, buf, tw.split);
   g.template rows<true, NT>(buf, tw.row);

@@ -13,6 +13,11 @@ namespace csc {
 
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
+// bulk prefetch of a global range into L2 (address and size multiples of 16 bytes)
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------------------------------------
 // batched forward transforms of real maps or of filters placed on the grid
 // ---------------------------------------------------------------------------------------------
@@ -96,20 +101,28 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
       const float2* xh = a.xhat + (size_t)n * J * Om;
       for (int o = threadIdx.x; o < Om; o += NT) {
         float2 r[kMaxJ];
-        for (int j = 0; j < J; ++j) {
-          const float2 x = xh[(size_t)j * Om + o];
-          float2 s = make_float2(-x.x * irho, -x.y * irho);
-          for (int c = c0; c <= c1; ++c) s = cadd(s, a.part_in[((size_t)(c + n) * J + j) * Om + o]);
-          r[j] = s;
+#pragma unroll
+        for (int j = 0; j < kMaxJ; ++j) {
+          if (j < J) {
+            const float2 x = xh[(size_t)j * Om + o];
+            float2 s = make_float2(-x.x * irho, -x.y * irho);
+            for (int c = c0; c <= c1; ++c) s = cadd(s, a.part_in[((size_t)(c + n) * J + j) * Om + o]);
+            r[j] = s;
+          }
         }
         if (J == 1) {
           lam[o] = cscale(r[0], a.pdiag[o]);
         } else {
           const float2* pm = a.pmat + (size_t)o * J * J;
-          for (int i = 0; i < J; ++i) {
-            float2 s = make_float2(0.f, 0.f);
-            for (int j = 0; j < J; ++j) s = cfma(pm[i * J + j], r[j], s);
-            lam[(size_t)i * Om + o] = s;
+#pragma unroll
+          for (int i = 0; i < kMaxJ; ++i) {
+            if (i < J) {
+              float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int j = 0; j < kMaxJ; ++j)
+                if (j < J) s = cfma(pm[i * J + j], r[j], s);
+              lam[(size_t)i * Om + o] = s;
+            }
           }
         }
       }
@@ -121,53 +134,161 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
       const size_t map = (size_t)n * a.K + k;
       float* vk = a.v ? a.v + map * D : nullptr;
       const float2* dk = a.dhat + (size_t)k * J * Om;
+      // pull the next map's state (or codes) into L2 while this one is transformed
+      if (a.vec4 && threadIdx.x < 4 && (long long)map + 1 < m1) {
+        const float* nxt = (MODE == kObjective) ? a.z + (map + 1) * D : a.v + (map + 1) * D;
+        prefetch_l2(nxt + threadIdx.x * (D / 4), (unsigned)D);
+      }
       if (kLam) {
         // w_hat_k = sum_j conj(d_hat_jk) lam_j
-        for (int o = threadIdx.x; o < Om; o += NT) {
-          float2 s = make_float2(0.f, 0.f);
-          for (int j = 0; j < J; ++j) s = cfmac(dk[(size_t)j * Om + o], lam[(size_t)j * Om + o], s);
-          const int h = o / Wc, c = o - h * Wc;
-          buf[h * P + c] = s;
+        for (int o0 = threadIdx.x; o0 < Om; o0 += NT * 4) {
+          float2 dv[4][kMaxJ];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * NT;
+            if (o < Om)
+#pragma unroll
+              for (int j = 0; j < kMaxJ; ++j)
+                if (j < J) dv[u][j] = __ldg(dk + (size_t)j * Om + o);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * NT;
+            if (o < Om) {
+              float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int j = 0; j < kMaxJ; ++j)
+                if (j < J) s = cfmac(dv[u][j], lam[(size_t)j * Om + o], s);
+              const int h = o / Wc, c = o - h * Wc;
+              buf[h * P + c] = s;
+            }
+          }
         }
         __syncthreads();
         irfft2<G, NT>(g, buf, tw);
         float* zk = (MODE == kLast && a.z) ? a.z + map * D : nullptr;
-        for (int p = threadIdx.x; p < D; p += NT) {
-          const int h = p / W, x = p - h * W;
-          float* cell = bf + 2 * P * h + x;
-          const float vo = vk[p];
-          const float vn = *cell - (clampb(vo, beta) - vo);
-          vk[p] = vn;
-          const float cn = clampb(vn, beta);
-          if (MODE == kLast) {
-            if (zk) zk[p] = a.rho * (cn - vn);
-          } else {
-            *cell = 2.f * cn - vn;
+        if (a.vec4) {
+          // 4 pixels per thread and step, all loads of a thread issued before any use
+          constexpr int U = 8;
+          const int n4 = D / 4;
+          float4* v4 = reinterpret_cast<float4*>(vk);
+          float4* z4 = reinterpret_cast<float4*>(zk);
+          for (int q0 = threadIdx.x; q0 < n4; q0 += NT * U) {
+            float4 vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (q0 + u * NT < n4) vv[u] = __ldcs(v4 + q0 + u * NT);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int q = q0 + u * NT;
+              if (q < n4) {
+                const int p = 4 * q, h = p / W, x = p - h * W;
+                float2* cell = reinterpret_cast<float2*>(bf + 2 * P * h + x);
+                const float2 w01 = cell[0], w23 = cell[1];
+                float4 vn;
+                vn.x = w01.x - (clampb(vv[u].x, beta) - vv[u].x);
+                vn.y = w01.y - (clampb(vv[u].y, beta) - vv[u].y);
+                vn.z = w23.x - (clampb(vv[u].z, beta) - vv[u].z);
+                vn.w = w23.y - (clampb(vv[u].w, beta) - vv[u].w);
+                __stcs(v4 + q, vn);
+                if (MODE == kLast) {
+                  if (zk) {
+                    float4 zz;
+                    zz.x = a.rho * (clampb(vn.x, beta) - vn.x);
+                    zz.y = a.rho * (clampb(vn.y, beta) - vn.y);
+                    zz.z = a.rho * (clampb(vn.z, beta) - vn.z);
+                    zz.w = a.rho * (clampb(vn.w, beta) - vn.w);
+                    __stcs(z4 + q, zz);
+                  }
+                } else {
+                  cell[0] = make_float2(2.f * clampb(vn.x, beta) - vn.x, 2.f * clampb(vn.y, beta) - vn.y);
+                  cell[1] = make_float2(2.f * clampb(vn.z, beta) - vn.z, 2.f * clampb(vn.w, beta) - vn.w);
+                }
+              }
+            }
+          }
+        } else {
+          for (int p = threadIdx.x; p < D; p += NT) {
+            const int h = p / W, x = p - h * W;
+            float* cell = bf + 2 * P * h + x;
+            const float vo = vk[p];
+            const float vn = *cell - (clampb(vo, beta) - vo);
+            vk[p] = vn;
+            const float cn = clampb(vn, beta);
+            if (MODE == kLast) {
+              if (zk) zk[p] = a.rho * (cn - vn);
+            } else {
+              *cell = 2.f * cn - vn;
+            }
           }
         }
-      } else if (MODE == kPrologue) {
-        for (int p = threadIdx.x; p < D; p += NT) {
-          const int h = p / W, x = p - h * W;
-          const float vo = vk[p];
-          bf[2 * P * h + x] = 2.f * clampb(vo, beta) - vo;
-        }
-      } else {  // kObjective: transform the codes themselves
-        const float* zk = a.z + map * D;
-        for (int p = threadIdx.x; p < D; p += NT) {
-          const int h = p / W, x = p - h * W;
-          const float zz = zk[p];
-          l1 += fabsf(zz);
-          bf[2 * P * h + x] = zz;
+      } else {
+        // prologue: u = 2 clamp(v) - v of the given state; objective: the codes themselves
+        const float* src = (MODE == kPrologue) ? vk : a.z + map * D;
+        if (a.vec4) {
+          constexpr int U = 8;
+          const int n4 = D / 4;
+          const float4* s4 = reinterpret_cast<const float4*>(src);
+          for (int q0 = threadIdx.x; q0 < n4; q0 += NT * U) {
+            float4 vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (q0 + u * NT < n4) vv[u] = __ldg(s4 + q0 + u * NT);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int q = q0 + u * NT;
+              if (q < n4) {
+                const int p = 4 * q, h = p / W, x = p - h * W;
+                float2* cell = reinterpret_cast<float2*>(bf + 2 * P * h + x);
+                const float4 t = vv[u];
+                if (MODE == kPrologue) {
+                  cell[0] = make_float2(2.f * clampb(t.x, beta) - t.x, 2.f * clampb(t.y, beta) - t.y);
+                  cell[1] = make_float2(2.f * clampb(t.z, beta) - t.z, 2.f * clampb(t.w, beta) - t.w);
+                } else {
+                  l1 += (double)(fabsf(t.x) + fabsf(t.y)) + (double)(fabsf(t.z) + fabsf(t.w));
+                  cell[0] = make_float2(t.x, t.y);
+                  cell[1] = make_float2(t.z, t.w);
+                }
+              }
+            }
+          }
+        } else {
+          for (int p = threadIdx.x; p < D; p += NT) {
+            const int h = p / W, x = p - h * W;
+            const float t = src[p];
+            if (MODE == kPrologue) {
+              bf[2 * P * h + x] = 2.f * clampb(t, beta) - t;
+            } else {
+              l1 += fabsf(t);
+              bf[2 * P * h + x] = t;
+            }
+          }
         }
       }
       if (kAcc) {
         __syncthreads();
         rfft2<G, NT>(g, buf, tw);
-        for (int o = threadIdx.x; o < Om; o += NT) {
-          const int h = o / Wc, c = o - h * Wc;
-          const float2 u = buf[h * P + c];
-          for (int j = 0; j < J; ++j)
-            acc[(size_t)j * Om + o] = cfma(dk[(size_t)j * Om + o], u, acc[(size_t)j * Om + o]);
+        for (int o0 = threadIdx.x; o0 < Om; o0 += NT * 4) {
+          float2 dv[4][kMaxJ];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * NT;
+            if (o < Om)
+#pragma unroll
+              for (int j = 0; j < kMaxJ; ++j)
+                if (j < J) dv[u][j] = __ldg(dk + (size_t)j * Om + o);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = o0 + u * NT;
+            if (o < Om) {
+              const int h = o / Wc, c = o - h * Wc;
+              const float2 uh = buf[h * P + c];
+#pragma unroll
+              for (int j = 0; j < kMaxJ; ++j)
+                if (j < J) acc[(size_t)j * Om + o] = cfma(dv[u][j], uh, acc[(size_t)j * Om + o]);
+            }
+          }
         }
       }
       __syncthreads();
@@ -310,11 +431,11 @@ struct GeoLaunch {
 
   template <int MODE>
   static cudaError_t sweep_mode(const Ctx& c, const SweepArgs& a) {
-    auto kern = k_sweep<GEO, MODE, kNT>;
+    auto kern = k_sweep<GEO, MODE, kNTSweep>;
     const size_t smem = sweep_smem_bytes(c.g, c.J, MODE);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<c.G, kNT, smem, c.stream>>>(a, geo(c));
+    kern<<<c.G, kNTSweep, smem, c.stream>>>(a, geo(c));
     return cudaGetLastError();
   }
 
