@@ -1,7 +1,7 @@
 """Benchmark of the dual-domain CSC hot path (coding ADMM + filter update) on GB300.
 
 Workload (one step = one outer round of Algorithm 1): N=100 grey 128x128 images (1/f^2 Gaussian
-fields, contrast-normalised), K=100 filters 11x11, beta=1, rho=10; 20 coding iterations
+fields, contrast-normalised), K=100 filters 11x11, beta=1, rho=0.1; 20 coding iterations
 (csc_code) then 20 learning steps (csc_learn). The ADMM state (655 MB) is larger than L2, so no
 L2 flush is needed between iterations.
 
@@ -36,8 +36,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = {"workload": "powerlaw128: N=100 grey 128x128 1/f^2 fields, K=100 filters 11x11, beta=1, "
-                        "rho=10, one step = 20 coding iterations + 20 learning steps",
-            "N": 100, "H": 128, "W": 128, "K": 100, "s": 11, "J": 1, "beta": 1.0, "rho": 10.0,
+                        "rho=0.1, one step = 20 coding iterations + 20 learning steps",
+            "N": 100, "H": 128, "W": 128, "K": 100, "s": 11, "J": 1, "beta": 1.0, "rho": 0.1,
             "n_code": 20, "n_learn": 20, "image_seed": 2, "dict_seed": 21, "cg_max": 100, "cg_tol": 1e-6}
 METRIC = "coding ADMM iters/s"
 UNIT = "iters/s"

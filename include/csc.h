@@ -113,6 +113,36 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
 csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const float* z, double* out);
 
 /*
+ * Reverse mode through unrolled coding iterations (not in the paper; J = 1 in this build).
+ * csc_code_unrolled runs `iters` iterations of csc_code from the state v (in: v^0, out: v^T) and
+ * writes z = z_T (nullable) like csc_code, and records on `tape` (device memory of
+ * csc_tape_bytes(ctx, iters, every) bytes, owned by the caller): the state every `every`
+ * iterations (checkpoints), v^T, and lambda of every iteration.
+ * csc_code_backward then returns the vector-Jacobian products of z_T with respect to the images x
+ * and the filters d for the cotangent gz = dL/dz_T ([N][K][H][W]): gx [N][J][H][W], gd [K][J][fh][fw].
+ * It recomputes each segment's states from its checkpoint and runs the reverse recurrence
+ *   lambar = D vbar', rbar = P lambar, ubar = D^T rbar, xbar -= rbar / rho,
+ *   vbar = (1 - m) vbar' + (2m - 1) ubar,   m = 1[|v| < beta],
+ *   dbar_k += G(vbar'_k, lambda) + G(u_k, rbar) - G(w_k, rbar) - G(ubar_k, lambda),
+ * with G(a, b)(q) = sum_p b(p) a(p - q) on the filter support and the seed vbar^T = rho (m_T - 1) gz.
+ * All arrays must be device memory. Asynchronous on the context's stream.
+ */
+size_t csc_tape_bytes(const csc_ctx* ctx, int iters, int every);
+csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters,
+                             int every, void* tape);
+csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const void* tape, int iters,
+                             int every, const float* gz, float* gx, float* gd);
+
+/*
+ * Reconstruction (Eq. 1's model): out [N][J][H][W] = sum_k d_k * z_k. csc_synthesize_backward gives,
+ * for the cotangent gout of out, gz = D^T gout and gd_k = S sum_n z_nk ⋆ gout_n (J = 1 in this
+ * build). Device arrays only; asynchronous on the context's stream.
+ */
+csc_status csc_synthesize(csc_ctx* ctx, const float* d, const float* z, float* out);
+csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z, const float* gout, float* gz,
+                                   float* gd);
+
+/*
  * Benchmarking aid (no counterpart in the paper). While enabled, each coding sweep launch (one ADMM
  * iteration over all N*K maps) and each csc_learn call are bracketed by CUDA events on the
  * context's stream. kernel_launches counts every kernel the library launched (enabled or not).

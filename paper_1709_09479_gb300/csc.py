@@ -63,6 +63,16 @@ def _load():
     lib.csc_timing_enable.restype = i
     lib.csc_timing_read.argtypes = [vp, ctypes.POINTER(csc_timing)]
     lib.csc_timing_read.restype = i
+    lib.csc_tape_bytes.argtypes = [vp, i, i]
+    lib.csc_tape_bytes.restype = ctypes.c_size_t
+    lib.csc_code_unrolled.argtypes = [vp, vp, vp, vp, vp, i, i, vp]
+    lib.csc_code_unrolled.restype = i
+    lib.csc_code_backward.argtypes = [vp, vp, vp, vp, i, i, vp, vp, vp]
+    lib.csc_code_backward.restype = i
+    lib.csc_synthesize.argtypes = [vp, vp, vp, vp]
+    lib.csc_synthesize.restype = i
+    lib.csc_synthesize_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.csc_synthesize_backward.restype = i
     lib.csc_code_noalloc.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i]
     lib.csc_code_noalloc.restype = i
     lib.csc_version.argtypes = []
@@ -132,6 +142,34 @@ def csc_objective(ctx, x, d, z) -> float:
     _check(LIB.csc_objective(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _ptr(z, np.float32),
                              ctypes.byref(out)), ctx)
     return out.value
+
+
+def _raw_ptr(a):
+    """Data pointer of a device tensor of any dtype (the unrolled-coding tape)."""
+    return a.data_ptr()
+
+
+def csc_tape_bytes(ctx, iters, every) -> int:
+    return int(LIB.csc_tape_bytes(ctx, iters, every))
+
+
+def csc_code_unrolled(ctx, x, d, v, z, iters, every, tape):
+    _check(LIB.csc_code_unrolled(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _ptr(v, np.float32),
+                                 _ptr(z, np.float32), iters, every, _raw_ptr(tape)), ctx)
+
+
+def csc_code_backward(ctx, x, d, tape, iters, every, gz, gx, gd):
+    _check(LIB.csc_code_backward(ctx, _ptr(x, np.float32), _ptr(d, np.float32), _raw_ptr(tape), iters, every,
+                                 _ptr(gz, np.float32), _ptr(gx, np.float32), _ptr(gd, np.float32)), ctx)
+
+
+def csc_synthesize(ctx, d, z, out):
+    _check(LIB.csc_synthesize(ctx, _ptr(d, np.float32), _ptr(z, np.float32), _ptr(out, np.float32)), ctx)
+
+
+def csc_synthesize_backward(ctx, d, z, gout, gz, gd):
+    _check(LIB.csc_synthesize_backward(ctx, _ptr(d, np.float32), _ptr(z, np.float32), _ptr(gout, np.float32),
+                                       _ptr(gz, np.float32), _ptr(gd, np.float32)), ctx)
 
 
 def csc_code_noalloc(J, K, fs, dims, n_images, beta, rho, x, d, v, z=None, iters=1, stream=None):

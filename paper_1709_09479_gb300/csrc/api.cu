@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -106,7 +107,8 @@ void free_all(Ctx* c) {
   c->events.clear();
   void* ptrs[] = {c->tw, c->dhat, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.b, c->L.vec, c->L.mu, c->L.dots, c->L.bar,
-                  c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu};
+                  c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
+                  c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -369,6 +371,217 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
   if (herr) return fail(c, (csc_status)herr, "csc_learn: grid barrier timed out");
   if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+  return CSC_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// reverse mode through unrolled coding iterations, and the reconstruction D z
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+struct TapeLayout {
+  size_t ckpt, vT, lam, total;
+  int n_ckpt;
+};
+
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+TapeLayout tape_layout(const Ctx& c, int iters, int every) {
+  TapeLayout t;
+  const size_t state = (size_t)c.N * c.K * c.g.D * sizeof(float);
+  const size_t lam = (size_t)c.N * c.J * c.g.Omega * sizeof(float2);
+  t.n_ckpt = (iters + every - 1) / every;
+  t.ckpt = 0;
+  t.vT = up256((size_t)t.n_ckpt * state);
+  t.lam = t.vT + up256(state);
+  t.total = t.lam + up256((size_t)iters * lam);
+  return t;
+}
+
+csc_status check_device_arrays(Ctx* c, std::initializer_list<const void*> ptrs, const char* who) {
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p))
+      return fail(c, CSC_ERR_ARG, std::string(who) + ": arrays must be device memory");
+  return CSC_OK;
+}
+
+csc_status ensure_backward(Ctx* c, int seg) {
+  BackwardBuffers& B = c->B;
+  const size_t state = (size_t)c->N * c->K * c->g.D;
+  const size_t Om = c->g.Omega;
+  if (seg > B.seg_cap) {
+    if (B.seg) cudaFree(B.seg);
+    B.seg = nullptr;
+    B.seg_cap = 0;
+    CSC_CHECK_CUDA(c, cudaMalloc((void**)&B.seg, (size_t)seg * state * sizeof(float)), "backward workspace");
+    B.seg_cap = seg;
+  }
+  if (ensure_alloc(&B.vbar, state) != cudaSuccess || ensure_alloc(&B.gspec, (size_t)c->N * c->K * Om) != cudaSuccess ||
+      ensure_alloc(&B.S, (size_t)c->N * Om) != cudaSuccess || ensure_alloc(&B.Xb, (size_t)c->N * Om) != cudaSuccess ||
+      ensure_alloc(&B.part[0], (size_t)(c->G + c->N) * Om) != cudaSuccess ||
+      ensure_alloc(&B.part[1], (size_t)(c->G + c->N) * Om) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "backward workspace allocation failed");
+  }
+  return CSC_OK;
+}
+
+csc_status ensure_spec(Ctx* c) {
+  if (ensure_alloc(&c->B.spec, (size_t)c->N * c->J * c->g.Omega) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "spectrum workspace allocation failed");
+  }
+  return CSC_OK;
+}
+
+}  // namespace
+
+size_t csc_tape_bytes(const csc_ctx* ctx, int iters, int every) {
+  if (!ctx || iters < 1 || every < 1) return 0;
+  return tape_layout(ctx->c, iters, every).total;
+}
+
+csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters,
+                             int every, void* tape) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_unrolled: null context");
+  Ctx* c = &ctx->c;
+  if (!x || !d || !v || !tape || iters < 1 || every < 1)
+    return fail(c, CSC_ERR_ARG, "csc_code_unrolled: null array, iters < 1 or every < 1");
+  if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: J = 1 only");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s = check_device_arrays(c, {x, d, v, z, tape}, "csc_code_unrolled");
+  if (s != CSC_OK) return s;
+  const TapeLayout T = tape_layout(*c, iters, every);
+  unsigned char* tp = static_cast<unsigned char*>(tape);
+  const size_t state = (size_t)c->N * c->K * c->g.D;
+  float* ckpt = reinterpret_cast<float*>(tp + T.ckpt);
+  float* vT = reinterpret_cast<float*>(tp + T.vT);
+  float2* lam = reinterpret_cast<float2*>(tp + T.lam);
+  const size_t lam_n = (size_t)c->N * c->J * c->g.Omega;
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, d, c->K * c->J, 1, c->dhat), "filter spectra");
+  CSC_CHECK_CUDA(c, launch_solve_prep(*c), "per-frequency solve setup");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, x, c->N * c->J, 0, c->xhat), "image spectra");
+  CSC_CHECK_CUDA(c, launch_sweep(*c, kPrologue, nullptr, c->part[0], v, nullptr), "coding prologue");
+  c->launches += 4;
+  for (int t = 0; t < iters; ++t) {
+    if (t % every == 0)
+      CSC_CHECK_CUDA(c, cudaMemcpyAsync(ckpt + (size_t)(t / every) * state, v, state * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, c->stream), "checkpoint copy");
+    const int mode = (t == iters - 1) ? kLast : kIter;
+    CSC_CHECK_CUDA(c, launch_sweep_ex(*c, mode, c->part[t & 1], c->part[(t + 1) & 1], v, z, nullptr,
+                                      lam + (size_t)t * lam_n), "coding sweep");
+    c->launches += 1;
+  }
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(vT, v, state * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "state copy");
+  return CSC_OK;
+}
+
+csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const void* tape, int iters, int every,
+                             const float* gz, float* gx, float* gd) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_backward: null context");
+  Ctx* c = &ctx->c;
+  if (!x || !d || !tape || !gz || !gx || !gd || iters < 1 || every < 1)
+    return fail(c, CSC_ERR_ARG, "csc_code_backward: null array, iters < 1 or every < 1");
+  if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: J = 1 only");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s = check_device_arrays(c, {x, d, tape, gz, gx, gd}, "csc_code_backward");
+  if (s != CSC_OK) return s;
+  if ((s = ensure_backward(c, std::min(every, iters))) != CSC_OK) return s;
+  const TapeLayout T = tape_layout(*c, iters, every);
+  const unsigned char* tp = static_cast<const unsigned char*>(tape);
+  const size_t state = (size_t)c->N * c->K * c->g.D;
+  const float* ckpt = reinterpret_cast<const float*>(tp + T.ckpt);
+  const float* vT = reinterpret_cast<const float*>(tp + T.vT);
+  const float2* lam = reinterpret_cast<const float2*>(tp + T.lam);
+  const size_t lam_n = (size_t)c->N * c->g.Omega;
+  BackwardBuffers& B = c->B;
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, d, c->K, 1, c->dhat), "filter spectra");
+  CSC_CHECK_CUDA(c, launch_solve_prep(*c), "per-frequency solve setup");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, x, c->N, 0, c->xhat), "image spectra");
+  CSC_CHECK_CUDA(c, cudaMemsetAsync(B.S, 0, (size_t)c->N * c->g.Omega * sizeof(float), c->stream), "memset");
+  CSC_CHECK_CUDA(c, cudaMemsetAsync(B.Xb, 0, (size_t)c->N * c->g.Omega * sizeof(float2), c->stream), "memset");
+  c->launches += 3;
+  BwdArgs a;
+  a.N = c->N; a.K = c->K; a.G = c->G;
+  a.beta = (float)c->p.beta; a.rho = (float)c->p.rho; a.dsize = (float)c->g.D;
+  a.dhat = c->dhat; a.pdiag = c->pdiag; a.vbar = B.vbar; a.gz = gz; a.gspec = B.gspec; a.S = B.S; a.Xb = B.Xb;
+  a.tw = c->tw;
+  const GeoOps& ops = geo_ops(*c);
+  // seed: vbar^T = rho (m_T - 1) z_bar
+  a.part_in = nullptr; a.part_out = B.part[0]; a.vt = vT; a.lam_t = nullptr;
+  a.lam_prev = lam + (size_t)(iters - 1) * lam_n;
+  CSC_CHECK_CUDA(c, ops.bwd(*c, kBSeed, a), "backward seed");
+  c->launches += 1;
+  int cur = 0;
+  for (int sgm = T.n_ckpt - 1; sgm >= 0; --sgm) {
+    const int t0 = sgm * every, t1 = std::min(iters, t0 + every);
+    // recompute the forward states v^t0 .. v^(t1-1) of the segment from its checkpoint
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(B.seg, ckpt + (size_t)sgm * state, state * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, c->stream), "checkpoint restore");
+    if (t1 - t0 > 1) {
+      CSC_CHECK_CUDA(c, launch_sweep(*c, kPrologue, nullptr, c->part[0], B.seg, nullptr), "recompute prologue");
+      c->launches += 1;
+      for (int t = t0; t < t1 - 1; ++t) {
+        const int i = t - t0;
+        CSC_CHECK_CUDA(c, launch_sweep_ex(*c, kIter, c->part[i & 1], c->part[(i + 1) & 1], B.seg + (size_t)i * state,
+                                          nullptr, B.seg + (size_t)(i + 1) * state, nullptr), "recompute sweep");
+        c->launches += 1;
+      }
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      a.part_in = B.part[cur];
+      a.part_out = B.part[cur ^ 1];
+      a.vt = B.seg + (size_t)(t - t0) * state;
+      a.lam_t = lam + (size_t)t * lam_n;
+      a.lam_prev = t >= 1 ? lam + (size_t)(t - 1) * lam_n : nullptr;
+      CSC_CHECK_CUDA(c, ops.bwd(*c, t == 0 ? kBLast : kBIter, a), "backward sweep");
+      c->launches += 1;
+      cur ^= 1;
+    }
+  }
+  CSC_CHECK_CUDA(c, ops.spec_maps(*c, B.Xb, c->N, 1.0f, gx), "input gradient");
+  CSC_CHECK_CUDA(c, ops.dgrad(*c, B.gspec, B.S, gd), "filter gradient");
+  c->launches += 2;
+  return CSC_OK;
+}
+
+csc_status csc_synthesize(csc_ctx* ctx, const float* d, const float* z, float* out) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize: null context");
+  Ctx* c = &ctx->c;
+  if (!d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_synthesize: null argument");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s = check_device_arrays(c, {d, z, out}, "csc_synthesize");
+  if (s != CSC_OK) return s;
+  if ((s = ensure_spec(c)) != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, d, c->K * c->J, 1, c->dhat), "filter spectra");
+  CSC_CHECK_CUDA(c, launch_sweep(*c, kObjective, nullptr, c->part[0], nullptr, const_cast<float*>(z)), "synthesis");
+  CSC_CHECK_CUDA(c, launch_sum_slots(*c, c->part[0], c->B.spec), "synthesis sum");
+  CSC_CHECK_CUDA(c, geo_ops(*c).spec_maps(*c, c->B.spec, c->N * c->J, 1.0f / (float)c->g.D, out), "synthesis inverse");
+  c->launches += 4;
+  return CSC_OK;
+}
+
+csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z, const float* gout, float* gz,
+                                   float* gd) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize_backward: null context");
+  Ctx* c = &ctx->c;
+  if (!d || !z || !gout || !gz || !gd) return fail(c, CSC_ERR_ARG, "csc_synthesize_backward: null argument");
+  if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: J = 1 only");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s = check_device_arrays(c, {d, z, gout, gz, gd}, "csc_synthesize_backward");
+  if (s != CSC_OK) return s;
+  if ((s = ensure_spec(c)) != CSC_OK) return s;
+  if (ensure_alloc(&c->L.zhat, (size_t)c->N * c->K * c->g.Omega) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "csc_synthesize_backward: workspace allocation failed");
+  }
+  const GeoOps& ops = geo_ops(*c);
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, d, c->K, 1, c->dhat), "filter spectra");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, gout, c->N, 0, c->B.spec), "gradient spectra");
+  CSC_CHECK_CUDA(c, ops.expand(*c, c->B.spec, 1.0f / (float)c->g.D, gz), "code gradient");
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, z, c->N * c->K, 0, c->L.zhat), "code spectra");
+  CSC_CHECK_CUDA(c, ops.rhs_ex(*c, c->L.zhat, c->B.spec, gd), "filter gradient");
+  c->launches += 5;
   return CSC_OK;
 }
 

@@ -129,6 +129,26 @@ __global__ void k_objective_final(ObjFinalArgs a) {
   }
 }
 
+// per image: out_n = sum of the partial-sum slots of the CTAs covering image n (ascending order)
+struct SumSlotsArgs {
+  int N, K, J, G, Omega;
+  const float2* part;
+  float2* out;   // [N][J][Omega]
+};
+
+__global__ void k_sum_slots(SumSlotsArgs a) {
+  const int n = blockIdx.y;
+  const long long NK = (long long)a.N * a.K;
+  const int c0 = (int)((((long long)n * a.K + 1) * a.G - 1) / NK);
+  const int c1 = (int)((((long long)(n + 1) * a.K) * a.G - 1) / NK);
+  const int JO = a.J * a.Omega;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < JO; i += gridDim.x * blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int c = c0; c <= c1; ++c) s = cadd(s, a.part[(size_t)(c + n) * JO + i]);
+    a.out[(size_t)n * JO + i] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
@@ -152,14 +172,28 @@ cudaError_t launch_solve_prep(const Ctx& c) {
 
 cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                          float* z) {
+  return launch_sweep_ex(c, mode, part_in, part_out, v, z, nullptr, nullptr);
+}
+
+cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
+                            float* z, float* v_out, float2* lam_store) {
   SweepArgs a;
   a.N = c.N; a.K = c.K; a.J = c.J; a.G = c.G;
   a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
   a.dhat = c.dhat; a.xhat = c.xhat; a.pdiag = c.pdiag; a.pmat = c.pmat;
   a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1; a.tw = c.tw;
-  const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0);
+  a.v_out = v_out;
+  a.lam_store = lam_store;
+  const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0) && ((uintptr_t)v_out % 16 == 0);
   a.vec4 = (al && c.g.D % 16 == 0 && c.g.W % 4 == 0) ? 1 : 0;
   return geo_ops(c).sweep(c, mode, a);
+}
+
+cudaError_t launch_sum_slots(const Ctx& c, const float2* part, float2* out) {
+  SumSlotsArgs a{c.N, c.K, c.J, c.G, c.g.Omega, part, out};
+  dim3 grid((c.J * c.g.Omega + 255) / 256, c.N);
+  k_sum_slots<<<grid, 256, 0, c.stream>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z) {

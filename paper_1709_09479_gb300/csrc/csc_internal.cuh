@@ -34,6 +34,8 @@ struct SweepArgs {
   double* l1;            // [G] per-CTA sum |z| (kObjective)
   const float2* tw;      // twiddles [Wh | H | Wc]
   int vec4;              // v, z 16-byte aligned and D % 16 == 0: 4-pixel vector path + L2 prefetch
+  float* v_out;          // iterate/last: new state written here instead of over v (may be null)
+  float2* lam_store;     // iterate/last: lambda_hat / D of each image stored here [N][J][Omega] (may be null)
 };
 
 struct Ctx;
@@ -59,6 +61,17 @@ struct LearnBuffers {
   int steps_cap = 0;
 };
 
+struct BackwardBuffers {
+  int seg_cap = 0;          // states the segment buffer holds
+  float* seg = nullptr;     // [seg_cap][N][K][D] recomputed forward states
+  float* vbar = nullptr;    // [N][K][D]
+  float2* gspec = nullptr;  // [N][K][Omega]
+  float* S = nullptr;       // [N][Omega]
+  float2* Xb = nullptr;     // [N][Omega]
+  float2* part[2] = {nullptr, nullptr};
+  float2* spec = nullptr;   // [N][J][Omega] scratch spectra
+};
+
 struct Ctx {
   csc_params p;
   int N, J, K, fh, fw, S2;
@@ -78,6 +91,7 @@ struct Ctx {
   double* objimg = nullptr;
   int* err = nullptr;
   LearnBuffers L;
+  BackwardBuffers B;
   // staging of host arrays
   float* st_x = nullptr;
   float* st_d = nullptr;
@@ -94,11 +108,37 @@ struct Ctx {
 };
 
 // per-geometry launchers of the per-map kernels (geo_*.cu)
+enum BwdMode { kBSeed = 0, kBIter = 1, kBLast = 2 };
+
+// arguments of the reverse-mode sweep (geo_kernels.cuh, k_bwd_sweep)
+struct BwdArgs {
+  int N, K, G;
+  float beta, rho, dsize;
+  const float2* dhat;      // [K][Omega]
+  const float* pdiag;      // [Omega] P / D
+  const float2* part_in;   // [(G+N)][Omega]
+  float2* part_out;
+  float* vbar;             // [N][K][D] in/out
+  const float* vt;         // [N][K][D] forward state v^t (seed: v^T)
+  const float* gz;         // [N][K][D] dL/dz_T (seed)
+  const float2* lam_t;     // [N][Omega] lam_s^t (iterate, last)
+  const float2* lam_prev;  // [N][Omega] lam_s^{t-1} (seed, iterate)
+  float2* gspec;           // [N][K][Omega]
+  float* S;                // [N][Omega]
+  float2* Xb;              // [N][Omega]
+  const float2* tw;
+};
+
 struct GeoOps {
   cudaError_t (*fft_maps)(const Ctx&, const float* in, int nmaps, int filter_mode, float2* out);
   cudaError_t (*sweep)(const Ctx&, int mode, const SweepArgs&);
   cudaError_t (*rhs)(const Ctx&);
   cudaError_t (*lags)(const Ctx&);
+  cudaError_t (*bwd)(const Ctx&, int mode, const BwdArgs&);
+  cudaError_t (*spec_maps)(const Ctx&, const float2* spec, int nmaps, float scale, float* out);
+  cudaError_t (*dgrad)(const Ctx&, const float2* gspec, const float* S, float* gd);
+  cudaError_t (*rhs_ex)(const Ctx&, const float2* zhat, const float2* xhat, float* out);
+  cudaError_t (*expand)(const Ctx&, const float2* spec, float scale, float* out);
 };
 const GeoOps& geo_ops_128();
 const GeoOps& geo_ops_100();
@@ -113,7 +153,14 @@ cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* 
                          float* z);
 cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z);
 cudaError_t launch_objective_final(const Ctx& c, const float2* part, double* out_img);
+cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
+                            float* z, float* v_out, float2* lam_store);
+cudaError_t launch_sum_slots(const Ctx& c, const float2* part, float2* out);
 size_t sweep_smem_bytes(const Geometry& g, int J, int mode);
+inline size_t bwd_smem_bytes(const Geometry& g, bool rb, bool acc) {
+  return ((size_t)g.H * g.P + (rb ? (size_t)g.Omega : 0) + (acc ? (size_t)g.Omega : 0) +
+          (size_t)(g.Wh + g.H + g.Wc)) * sizeof(float2);
+}
 
 // message returned by csc_last_error(NULL) (api.cu)
 void set_global_error(const char* msg);

@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             r[j] = s;
           }
         }
+        float2* ls = (a.lam_store && cta == c0) ? a.lam_store + (size_t)n * J * Om : nullptr;
         if (J == 1) {
           lam[o] = cscale(r[0], a.pdiag[o]);
+          if (ls) ls[o] = lam[o];
         } else {
           const float2* pm = a.pmat + (size_t)o * J * J;
 #pragma unroll
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
               for (int j = 0; j < kMaxJ; ++j)
                 if (j < J) s = cfma(pm[i * J + j], r[j], s);
               lam[(size_t)i * Om + o] = s;
+              if (ls) ls[(size_t)i * Om + o] = s;
             }
           }
         }
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
     for (int k = kb; k < ke; ++k) {
       const size_t map = (size_t)n * a.K + k;
       float* vk = a.v ? a.v + map * D : nullptr;
+      float* vw = a.v_out ? a.v_out + map * D : vk;   // where the new state goes
       const float2* dk = a.dhat + (size_t)k * J * Om;
       // pull the next map's state (or codes) into L2 while this one is transformed
       if (a.vec4 && threadIdx.x < 4 && (long long)map + 1 < m1) {
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
           constexpr int U = 8;
           const int n4 = D / 4;
           float4* v4 = reinterpret_cast<float4*>(vk);
+          float4* vw4 = reinterpret_cast<float4*>(vw);
           float4* z4 = reinterpret_cast<float4*>(zk);
           for (int q0 = threadIdx.x; q0 < n4; q0 += NT * U) {
             float4 vv[U];
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
                 vn.y = w01.y - (clampb(vv[u].y, beta) - vv[u].y);
                 vn.z = w23.x - (clampb(vv[u].z, beta) - vv[u].z);
                 vn.w = w23.y - (clampb(vv[u].w, beta) - vv[u].w);
-                __stcs(v4 + q, vn);
+                __stcs(vw4 + q, vn);
                 if (MODE == kLast) {
                   if (zk) {
                     float4 zz;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             float* cell = bf + 2 * P * h + x;
             const float vo = vk[p];
             const float vn = *cell - (clampb(vo, beta) - vo);
-            vk[p] = vn;
+            vw[p] = vn;
             const float cn = clampb(vn, beta);
             if (MODE == kLast) {
               if (zk) zk[p] = a.rho * (cn - vn);
@@ -404,6 +409,243 @@ __global__ void __launch_bounds__(NT) k_learn_lags(LagsArgs a, G g) {
 
 
 // ---------------------------------------------------------------------------------------------
+// reverse mode through unrolled coding iterations (J = 1). With lam_s = lambda_hat / D stored by the
+// forward sweeps, one reverse step t (incoming vbar = dL/dv^{t+1}) is, per image and map:
+//   rbar_s = P/D * sum_k d_hat_k F(vbar_k)         (from the previous reverse sweep's partial sums)
+//   ubar_k = F^{-1}( conj(d_hat_k) rbar_s )
+//   vbar_k <- (1 - m) vbar_k + (2m - 1) ubar_k,     m = 1[|v^t_k| < beta]
+//   G_nk  += conj(F u^t_k) rbar_s + conj(F vbar^t_k) lam_s^{t-1}      (filter-gradient spectra)
+//   S_n   += D * 2 Re(conj(lam_s^t) rbar_s),  Xb_n -= rbar_s / rho       (once per image)
+// and the partial sums d_hat_k F(vbar^t_k) feed the next reverse step. The seed sweep sets
+// vbar^T = rho (m_T - 1) z_bar and G_nk = conj(F vbar^T_k) lam_s^{T-1}.
+// ---------------------------------------------------------------------------------------------
+template <class G, int MODE, int NT>
+__global__ void __launch_bounds__(NT, 1) k_bwd_sweep(BwdArgs a, G g) {
+  extern __shared__ float2 sm[];
+  constexpr bool kR = (MODE != kBSeed);    // needs rbar_s
+  constexpr bool kAcc = (MODE != kBLast);  // produces partial sums for the next reverse step
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega(), D = g.d();
+  float2* buf = sm;
+  float2* rb = buf + H * P;
+  float2* acc = rb + (kR ? Om : 0);
+  float2* tws = acc + (kAcc ? Om : 0);
+  const Twiddles tw = stage_twiddles<G, NT>(g, tws, a.tw);
+  float* bf = reinterpret_cast<float*>(buf);
+  __syncthreads();
+  const long long NK = (long long)a.N * a.K;
+  const int cta = blockIdx.x;
+  const long long m0 = (long long)cta * NK / a.G, m1 = (long long)(cta + 1) * NK / a.G;
+  const float beta = a.beta;
+  for (long long n = m0 / a.K; n * a.K < m1; ++n) {
+    const int kb = (int)(max(m0, n * a.K) - n * a.K);
+    const int ke = (int)(min(m1, (n + 1) * a.K) - n * a.K);
+    const int c0 = (int)(((n * a.K + 1) * a.G - 1) / NK);
+    const int c1 = (int)((((n + 1) * a.K) * a.G - 1) / NK);
+    if (kR) {
+      const bool owner = (cta == c0);
+      for (int o = threadIdx.x; o < Om; o += NT) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int c = c0; c <= c1; ++c) s = cadd(s, a.part_in[(size_t)(c + n) * Om + o]);
+        const float2 r = cscale(s, a.pdiag[o]);
+        rb[o] = r;
+        if (owner) {
+          const float2 l = a.lam_t[(size_t)n * Om + o];
+          a.S[(size_t)n * Om + o] += a.dsize * 2.f * (l.x * r.x + l.y * r.y);
+          float2 xb = a.Xb[(size_t)n * Om + o];
+          xb.x -= r.x / a.rho;
+          xb.y -= r.y / a.rho;
+          a.Xb[(size_t)n * Om + o] = xb;
+        }
+      }
+    }
+    if (kAcc)
+      for (int o = threadIdx.x; o < Om; o += NT) acc[o] = make_float2(0.f, 0.f);
+    const float2* lp = (MODE != kBLast) ? a.lam_prev + (size_t)n * Om : nullptr;
+    for (int k = kb; k < ke; ++k) {
+      const size_t map = (size_t)n * a.K + k;
+      const float2* dk = a.dhat + (size_t)k * Om;
+      float* vb = a.vbar + map * D;
+      const float* vtk = a.vt + map * D;
+      float2* gk = a.gspec + map * Om;
+      if (MODE == kBSeed) {
+        const float* gzk = a.gz + map * D;
+        for (int p = threadIdx.x; p < D; p += NT) {
+          const int h = p / W, x = p - h * W;
+          const float v = vtk[p];
+          const float m = (fabsf(v) < beta) ? 1.f : 0.f;
+          const float b = a.rho * (m - 1.f) * gzk[p];
+          vb[p] = b;
+          bf[2 * P * h + x] = b;
+        }
+      } else {
+        if (MODE == kBIter) {
+          // ubar_k = F^{-1}(conj(d_hat_k) rbar_s)
+          for (int o = threadIdx.x; o < Om; o += NT) {
+            const int h = o / Wc, c = o - h * Wc;
+            buf[h * P + c] = cfmac(__ldg(dk + o), rb[o], make_float2(0.f, 0.f));
+          }
+          __syncthreads();
+          irfft2<G, NT>(g, buf, tw);
+          // vbar update in HBM; then u^t into the buffer
+          for (int p = threadIdx.x; p < D; p += NT) {
+            const int h = p / W, x = p - h * W;
+            float* cell = bf + 2 * P * h + x;
+            const float v = vtk[p];
+            const float m = (fabsf(v) < beta) ? 1.f : 0.f;
+            vb[p] = (1.f - m) * vb[p] + (2.f * m - 1.f) * (*cell);
+            *cell = 2.f * clampb(v, beta) - v;
+          }
+        } else {
+          for (int p = threadIdx.x; p < D; p += NT) {
+            const int h = p / W, x = p - h * W;
+            const float v = vtk[p];
+            bf[2 * P * h + x] = 2.f * clampb(v, beta) - v;
+          }
+        }
+        __syncthreads();
+        rfft2<G, NT>(g, buf, tw);
+        // G_nk += conj(F u^t) rbar_s
+        for (int o = threadIdx.x; o < Om; o += NT) {
+          const int h = o / Wc, c = o - h * Wc;
+          gk[o] = cfmac(buf[h * P + c], rb[o], gk[o]);
+        }
+        __syncthreads();
+        if (MODE == kBIter) {
+          for (int p = threadIdx.x; p < D; p += NT) {
+            const int h = p / W, x = p - h * W;
+            bf[2 * P * h + x] = vb[p];
+          }
+        }
+      }
+      if (kAcc) {
+        __syncthreads();
+        rfft2<G, NT>(g, buf, tw);
+        // partial sums for the next reverse step, and G_nk (+)= conj(F vbar) lam_s^{t-1}
+        for (int o = threadIdx.x; o < Om; o += NT) {
+          const int h = o / Wc, c = o - h * Wc;
+          const float2 vh = buf[h * P + c];
+          acc[o] = cfma(__ldg(dk + o), vh, acc[o]);
+          const float2 base = (MODE == kBSeed) ? make_float2(0.f, 0.f) : gk[o];
+          gk[o] = cfmac(vh, lp[o], base);
+        }
+      }
+      __syncthreads();
+    }
+    if (kAcc) {
+      float2* dst = a.part_out + (size_t)(cta + n) * Om;
+      for (int o = threadIdx.x; o < Om; o += NT) dst[o] = acc[o];
+    }
+  }
+}
+
+// spectra [m][Omega] -> real maps [m][H][W] (scaled), one CTA per map; optional per-map source
+// sum: out = scale * F^{-1}(src[m]) (+ nothing else)
+struct SpecMapsArgs {
+  int nmaps;
+  const float2* spec;  // [m][Omega]
+  float* out;          // [m][D]
+  float scale;
+  const float2* tw;
+};
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_spec_to_maps(SpecMapsArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega();
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  const float* bf = reinterpret_cast<const float*>(buf);
+  for (int m = blockIdx.x; m < a.nmaps; m += gridDim.x) {
+    __syncthreads();
+    const float2* src = a.spec + (size_t)m * Om;
+    for (int o = threadIdx.x; o < Om; o += NT) {
+      const int h = o / Wc, c = o - h * Wc;
+      buf[h * P + c] = src[o];
+    }
+    __syncthreads();
+    irfft2<G, NT>(g, buf, tw);
+    float* dst = a.out + (size_t)m * H * W;
+    for (int p = threadIdx.x; p < H * W; p += NT) {
+      const int h = p / W, x = p - h * W;
+      dst[p] = bf[2 * P * h + x] * a.scale;
+    }
+  }
+}
+
+// filter gradient: gd_k = S F^{-1}( sum_n G_nk - d_hat_k sum_n S_n ), one CTA per filter
+struct DgradArgs {
+  int N, K, fh, fw;
+  const float2* gspec;  // [N][K][Omega]
+  const float* S;       // [N][Omega]
+  const float2* dhat;   // [K][Omega]
+  float* gd;            // [K][fh*fw]
+  const float2* tw;
+};
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_bwd_dgrad(DgradArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), P = g.p(), Wc = g.wc(), Om = g.omega();
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  const int k = blockIdx.x;
+  for (int o = threadIdx.x; o < Om; o += NT) {
+    float2 s = make_float2(0.f, 0.f);
+    float st = 0.f;
+    for (int n = 0; n < a.N; ++n) {
+      s = cadd(s, a.gspec[((size_t)n * a.K + k) * Om + o]);
+      st += a.S[(size_t)n * Om + o];
+    }
+    const float2 dk = a.dhat[(size_t)k * Om + o];
+    s.x -= dk.x * st;
+    s.y -= dk.y * st;
+    const int h = o / Wc, c = o - h * Wc;
+    buf[h * P + c] = s;
+  }
+  __syncthreads();
+  irfft2<G, NT>(g, buf, tw);
+  crop_window<G, NT>(g, reinterpret_cast<const float*>(buf), a.fh, a.fw, (a.fh - 1) / 2, (a.fw - 1) / 2,
+                     1.0f, a.gd + (size_t)k * a.fh * a.fw);
+}
+
+// out_nk = scale * F^{-1}( conj(d_hat_k) spec_n ) for every map (D^T applied to per-image spectra)
+struct ExpandArgs {
+  int N, K;
+  const float2* dhat;  // [K][Omega]
+  const float2* spec;  // [N][Omega]
+  float scale;
+  float* out;          // [N][K][D]
+  const float2* tw;
+};
+
+template <class G, int NT>
+__global__ void __launch_bounds__(NT) k_expand(ExpandArgs a, G g) {
+  extern __shared__ float2 sm[];
+  const int H = g.h(), W = g.w(), P = g.p(), Wc = g.wc(), Om = g.omega(), D = g.d();
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + H * P, a.tw);
+  const float* bf = reinterpret_cast<const float*>(buf);
+  const long long NK = (long long)a.N * a.K;
+  for (long long m = blockIdx.x; m < NK; m += gridDim.x) {
+    const int n = (int)(m / a.K), k = (int)(m % a.K);
+    __syncthreads();
+    const float2* dk = a.dhat + (size_t)k * Om;
+    const float2* sp = a.spec + (size_t)n * Om;
+    for (int o = threadIdx.x; o < Om; o += NT) {
+      const int h = o / Wc, c = o - h * Wc;
+      buf[h * P + c] = cscale(cfmac(__ldg(dk + o), sp[o], make_float2(0.f, 0.f)), a.scale);
+    }
+    __syncthreads();
+    irfft2<G, NT>(g, buf, tw);
+    float* dst = a.out + (size_t)m * D;
+    for (int p = threadIdx.x; p < D; p += NT) {
+      const int h = p / W, x = p - h * W;
+      dst[p] = bf[2 * P * h + x];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // launchers for one geometry
 // ---------------------------------------------------------------------------------------------
 inline size_t map_smem_bytes(const Geometry& g) {
@@ -448,8 +690,10 @@ struct GeoLaunch {
     }
   }
 
-  static cudaError_t rhs(const Ctx& c) {
-    RhsArgs a{c.N, c.K, c.J, c.fh, c.fw, c.L.zhat, c.xhat, c.L.b, c.tw};
+  static cudaError_t rhs(const Ctx& c) { return rhs_ex(c, c.L.zhat, c.xhat, c.L.b); }
+
+  static cudaError_t rhs_ex(const Ctx& c, const float2* zhat, const float2* xhat, float* out) {
+    RhsArgs a{c.N, c.K, c.J, c.fh, c.fw, zhat, xhat, out, c.tw};
     const size_t smem = map_smem_bytes(c.g);
     auto kern = k_learn_rhs<GEO, kNT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -469,8 +713,58 @@ struct GeoLaunch {
     return cudaGetLastError();
   }
 
+  template <int MODE>
+  static cudaError_t bwd_mode(const Ctx& c, const BwdArgs& a) {
+    auto kern = k_bwd_sweep<GEO, MODE, kNTSweep>;
+    const size_t smem = bwd_smem_bytes(c.g, MODE != kBSeed, MODE != kBLast);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<c.G, kNTSweep, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t bwd(const Ctx& c, int mode, const BwdArgs& a) {
+    switch (mode) {
+      case kBSeed: return bwd_mode<kBSeed>(c, a);
+      case kBIter: return bwd_mode<kBIter>(c, a);
+      default: return bwd_mode<kBLast>(c, a);
+    }
+  }
+
+  static cudaError_t spec_maps(const Ctx& c, const float2* spec, int nmaps, float scale, float* out) {
+    if (nmaps <= 0) return cudaSuccess;
+    SpecMapsArgs a{nmaps, spec, out, scale, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    auto kern = k_spec_to_maps<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(nmaps, c.nsm * 4), kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t dgrad(const Ctx& c, const float2* gspec, const float* S, float* gd) {
+    DgradArgs a{c.N, c.K, c.fh, c.fw, gspec, S, c.dhat, gd, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    auto kern = k_bwd_dgrad<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<c.K, kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t expand(const Ctx& c, const float2* spec, float scale, float* out) {
+    ExpandArgs a{c.N, c.K, c.dhat, spec, scale, out, c.tw};
+    const size_t smem = map_smem_bytes(c.g);
+    auto kern = k_expand<GEO, kNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long NK = (long long)c.N * c.K;
+    kern<<<(int)std::min<long long>(NK, (long long)c.nsm * 4), kNT, smem, c.stream>>>(a, geo(c));
+    return cudaGetLastError();
+  }
+
   static const GeoOps& ops() {
-    static const GeoOps o{&fft_maps, &sweep, &rhs, &lags};
+    static const GeoOps o{&fft_maps, &sweep, &rhs, &lags, &bwd, &spec_maps, &dgrad, &rhs_ex, &expand};
     return o;
   }
 };

@@ -31,7 +31,7 @@ def main():
     d = torch.from_numpy(inputs.unit_filters(21, a.K, 1, (a.s, a.s)).astype(np.float32)).cuda()
     v = torch.zeros((a.N, a.K, a.H, a.W), device="cuda")
     z = torch.empty_like(v)
-    with csc.Solver(J=1, K=a.K, fs=(a.s, a.s), dims=(a.H, a.W), n_images=a.N, beta=1.0, rho=10.0) as sv:
+    with csc.Solver(J=1, K=a.K, fs=(a.s, a.s), dims=(a.H, a.W), n_images=a.N, beta=1.0, rho=0.1) as sv:
         if a.what == "coding":
             sv.code(x, d, v, z, a.iters)
         else:
