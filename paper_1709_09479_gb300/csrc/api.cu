@@ -105,7 +105,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->tw, c->dhat, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.b, c->L.vec, c->L.mu, c->L.dots, c->L.bar,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
@@ -139,8 +139,11 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
   if (p.cg_max < 1 || !(p.cg_tol > 0)) return fail(nullptr, CSC_ERR_ARG, "csc_init: cg_max >= 1, cg_tol > 0");
   if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16)
     return fail(nullptr, CSC_ERR_ARG, "csc_init: unknown precision");
-  if (p.precision != CSC_FP32)
-    return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init: only CSC_FP32 is implemented in this build");
+  if (p.precision == CSC_MIXED_BF16) {
+    if (p.K > 128) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: CSC_MIXED_BF16 needs K <= 128");
+    if (tc_gram_smem_bytes(n_images) > kSmemLimit)
+      return fail(nullptr, CSC_ERR_SHAPE, "csc_init: CSC_MIXED_BF16 needs n_images <= 448");
+  }
   const int fh = p.fs[0], fw = p.fs[1];
   if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter support must be odd and >= 1");
@@ -194,6 +197,8 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
     tw[g.Wh + g.H + t] = make_float2((float)cos(pi2 * t / g.W), (float)-sin(pi2 * t / g.W));
   if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->dhat, (size_t)p.K * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      (p.precision == CSC_MIXED_BF16 &&
+       cudaMalloc((void**)&c->dhat16, (size_t)p.K * p.J * Om * sizeof(__nv_bfloat162)) != cudaSuccess) ||
       cudaMalloc((void**)&c->xhat, (size_t)tmp.N * p.J * Om * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->pdiag, Om * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&c->pmat, Om * p.J * p.J * sizeof(float2)) != cudaSuccess ||
@@ -256,6 +261,10 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
     CSC_CHECK_CUDA(c, launch_solve_prep(*c), "per-frequency solve setup");
     CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
+    if (c->p.precision == CSC_MIXED_BF16) {
+      CSC_CHECK_CUDA(c, launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->K * c->J * c->g.Omega), "bf16 spectra");
+      c->launches += 1;
+    }
     CSC_CHECK_CUDA(c, launch_sweep(*c, kPrologue, nullptr, c->part[0], vd, nullptr), "coding prologue");
     c->launches += 4;
     for (int t = 0; t < iters; ++t) {
@@ -353,7 +362,14 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, zd, c->N * K, 0, L.zhat), "code spectra");
   CSC_CHECK_CUDA(c, launch_learn_rhs(*c), "learning right-hand side");
-  CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
+  if (c->p.precision == CSC_MIXED_BF16) {
+    const size_t npad = (size_t)((c->N + 15) / 16 * 16);
+    CSC_CHECK_CUDA(c, ensure_alloc(reinterpret_cast<__nv_bfloat16**>(&L.zt), Om * K * 2 * npad), "bf16 workspace");
+    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, L.zt, c->err), "code Gram (tensor cores)");
+    c->launches += 1;
+  } else {
+    CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
+  }
   CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
   CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
   bracket_close(c, br);
@@ -448,6 +464,7 @@ csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float
   if (!x || !d || !v || !tape || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_unrolled: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: J = 1 only");
+  if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   csc_status s = check_device_arrays(c, {x, d, v, z, tape}, "csc_code_unrolled");
   if (s != CSC_OK) return s;
@@ -483,6 +500,7 @@ csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const
   if (!x || !d || !tape || !gz || !gx || !gd || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_backward: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: J = 1 only");
+  if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   csc_status s = check_device_arrays(c, {x, d, tape, gz, gx, gd}, "csc_code_backward");
   if (s != CSC_OK) return s;
@@ -549,6 +567,7 @@ csc_status csc_synthesize(csc_ctx* ctx, const float* d, const float* z, float* o
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize: null context");
   Ctx* c = &ctx->c;
   if (!d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_synthesize: null argument");
+  if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   csc_status s = check_device_arrays(c, {d, z, out}, "csc_synthesize");
   if (s != CSC_OK) return s;
@@ -567,6 +586,7 @@ csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z,
   Ctx* c = &ctx->c;
   if (!d || !z || !gout || !gz || !gd) return fail(c, CSC_ERR_ARG, "csc_synthesize_backward: null argument");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: J = 1 only");
+  if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   csc_status s = check_device_arrays(c, {d, z, gout, gz, gd}, "csc_synthesize_backward");
   if (s != CSC_OK) return s;

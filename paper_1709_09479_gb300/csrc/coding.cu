@@ -184,9 +184,22 @@ cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float
   a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1; a.tw = c.tw;
   a.v_out = v_out;
   a.lam_store = lam_store;
+  // the bf16 copy of d_hat is refreshed by csc_code only; the objective stays float32
+  a.dhat16 = (c.p.precision == CSC_MIXED_BF16 && mode != kObjective) ? c.dhat16 : nullptr;
   const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0) && ((uintptr_t)v_out % 16 == 0);
   a.vec4 = (al && c.g.D % 16 == 0 && c.g.W % 4 == 0) ? 1 : 0;
   return geo_ops(c).sweep(c, mode, a);
+}
+
+__global__ void k_to_bf16(const float2* __restrict__ in, __nv_bfloat162* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __floats2bfloat162_rn(in[i].x, in[i].y);
+}
+
+cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n) {
+  const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);
+  k_to_bf16<<<grid, 256, 0, c.stream>>>(in, out, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sum_slots(const Ctx& c, const float2* part, float2* out) {

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/csc.h"
 #include "fft.cuh"
 
@@ -35,6 +37,7 @@ struct SweepArgs {
   const float2* tw;      // twiddles [Wh | H | Wc]
   int vec4;              // v, z 16-byte aligned and D % 16 == 0: 4-pixel vector path + L2 prefetch
   float* v_out;          // iterate/last: new state written here instead of over v (may be null)
+  const __nv_bfloat162* dhat16;  // mixed precision: d_hat in bf16; contraction operands rounded to bf16
   float2* lam_store;     // iterate/last: lambda_hat / D of each image stored here [N][J][Omega] (may be null)
 };
 
@@ -59,6 +62,7 @@ struct LearnBuffers {
   unsigned* bar = nullptr;  // grid barrier {count, generation}
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
+  void* zt = nullptr;       // mixed precision: [Omega][K][2 npad] bf16 code spectra for the tensor-core Gram
 };
 
 struct BackwardBuffers {
@@ -83,6 +87,7 @@ struct Ctx {
   // workspace
   float2* tw = nullptr;
   float2* dhat = nullptr;
+  __nv_bfloat162* dhat16 = nullptr;   // mixed precision copy of dhat
   float2* xhat = nullptr;
   float* pdiag = nullptr;
   float2* pmat = nullptr;
@@ -170,6 +175,9 @@ cudaError_t launch_learn_rhs(const Ctx& c);
 cudaError_t launch_learn_gram(const Ctx& c);
 cudaError_t launch_learn_lags(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
+cudaError_t launch_learn_gram_tc(const Ctx& c, void* zt_buf, int* dev_err);
+size_t tc_gram_smem_bytes(int N);
+cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n);
 
 inline const GeoOps& geo_ops(const Ctx& c) {
   switch (c.g.ct_id) {

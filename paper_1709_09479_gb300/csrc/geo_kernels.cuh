@@ -13,6 +13,11 @@ namespace csc {
 
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
+// a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
+__device__ __forceinline__ float2 round_bf16(float2 v) {
+  return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y));
+}
+
 // bulk prefetch of a global range into L2 (address and size multiples of 16 bytes)
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -138,6 +143,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
       float* vk = a.v ? a.v + map * D : nullptr;
       float* vw = a.v_out ? a.v_out + map * D : vk;   // where the new state goes
       const float2* dk = a.dhat + (size_t)k * J * Om;
+      const __nv_bfloat162* dk16 = a.dhat16 ? a.dhat16 + (size_t)k * J * Om : nullptr;
       // pull the next map's state (or codes) into L2 while this one is transformed
       if (a.vec4 && threadIdx.x < 4 && (long long)map + 1 < m1) {
         const float* nxt = (MODE == kObjective) ? a.z + (map + 1) * D : a.v + (map + 1) * D;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             if (o < Om)
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
-                if (j < J) dv[u][j] = __ldg(dk + (size_t)j * Om + o);
+                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o]) : __ldg(dk + (size_t)j * Om + o);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -162,7 +168,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
               float2 s = make_float2(0.f, 0.f);
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
-                if (j < J) s = cfmac(dv[u][j], lam[(size_t)j * Om + o], s);
+                if (j < J) {
+                  const float2 l = lam[(size_t)j * Om + o];
+                  s = cfmac(dv[u][j], dk16 ? round_bf16(l) : l, s);
+                }
               const int h = o / Wc, c = o - h * Wc;
               buf[h * P + c] = s;
             }
@@ -281,14 +290,14 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             if (o < Om)
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
-                if (j < J) dv[u][j] = __ldg(dk + (size_t)j * Om + o);
+                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o]) : __ldg(dk + (size_t)j * Om + o);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int o = o0 + u * NT;
             if (o < Om) {
               const int h = o / Wc, c = o - h * Wc;
-              const float2 uh = buf[h * P + c];
+              const float2 uh = dk16 ? round_bf16(buf[h * P + c]) : buf[h * P + c];
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
                 if (j < J) acc[(size_t)j * Om + o] = cfma(dv[u][j], uh, acc[(size_t)j * Om + o]);
