@@ -18,6 +18,7 @@ constexpr int kNTSweep = 512;         // threads of the coding sweep
 constexpr int kMaxJ = 3;
 constexpr size_t kSmemLimit = 232448; // 227 KB opt-in shared memory per CTA
 constexpr double kMuFloor = 1e-8;
+constexpr int kMaxBlockJacobi = 128;  // filters with more taps use the scalar Jacobi preconditioner
 
 enum SweepMode { kPrologue = 0, kIter = 1, kLast = 2, kObjective = 3 };
 
@@ -58,7 +59,8 @@ struct LearnBuffers {
   float* b = nullptr;       // [K][J][S2]
   float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
   double* mu = nullptr;     // [K]
-  double* dots = nullptr;   // [G][J][4]
+  float* minv = nullptr;    // [K][S2][S2] block-Jacobi inverses (S2 <= kMaxBlockJacobi)
+  float* dots = nullptr;    // [G][4][kMaxJ] CG partial dot products
   unsigned* bar = nullptr;  // grid barrier {count, generation}
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;

@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
         }
       } else {
         // prologue: u = 2 clamp(v) - v of the given state; objective: the codes themselves
+        // (|z| summed in float32 per map, float64 across maps: the float64 rate is low)
         const float* src = (MODE == kPrologue) ? vk : a.z + map * D;
+        float l1f = 0.f;
         if (a.vec4) {
           constexpr int U = 8;
           const int n4 = D / 4;
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
                   cell[0] = make_float2(2.f * clampb(t.x, beta) - t.x, 2.f * clampb(t.y, beta) - t.y);
                   cell[1] = make_float2(2.f * clampb(t.z, beta) - t.z, 2.f * clampb(t.w, beta) - t.w);
                 } else {
-                  l1 += (double)(fabsf(t.x) + fabsf(t.y)) + (double)(fabsf(t.z) + fabsf(t.w));
+                  l1f += (fabsf(t.x) + fabsf(t.y)) + (fabsf(t.z) + fabsf(t.w));
                   cell[0] = make_float2(t.x, t.y);
                   cell[1] = make_float2(t.z, t.w);
                 }
@@ -273,11 +275,12 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             if (MODE == kPrologue) {
               bf[2 * P * h + x] = 2.f * clampb(t, beta) - t;
             } else {
-              l1 += fabsf(t);
+              l1f += fabsf(t);
               bf[2 * P * h + x] = t;
             }
           }
         }
+        l1 += (double)l1f;
       }
       if (kAcc) {
         __syncthreads();

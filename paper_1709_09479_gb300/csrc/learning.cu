@@ -111,11 +111,11 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
+      // one polling thread per CTA, no sleep between polls: sleeping added ~20 us per barrier
       const long long t0 = clock64();
       while (*vgen == gen) {
         if (*(volatile int*)err) { ok = 0; break; }
         if (clock64() - t0 > kSpinLimit) { atomicExch(err, (int)CSC_ERR_TIMEOUT); ok = 0; break; }
-        __nanosleep(100);
       }
     }
     __threadfence();
@@ -138,33 +138,73 @@ struct CgArgs {
   float* zv;          // [K][J][S2]  preconditioned residual
   float* Ap;          // [K][J][S2]
   double* mu;         // [K]
-  double* dots;       // [G][4][kMaxJ]
+  float* minv;        // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
+  float* dots;        // [G][4][kMaxJ] per-CTA partial dot products
   unsigned* bar;
   int* iters;         // [steps]
   int* err;
 };
 
-// y_k = (S Z^T Z S^T) p for filter k (+ 2 mu_k p_k), p in shared memory for all filters
+__device__ __forceinline__ uint32_t cg_smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// copy n floats of read-only global data into shared memory with asynchronous copies
+template <int NT>
+__device__ __forceinline__ void stage_async(float* dst, const float* src, int n) {
+  for (int i = threadIdx.x; i < n; i += NT)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cg_smem_addr(dst + i)), "l"(src + i) : "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+// dst[i] = src[i] + beta(i) * dst[i] over the whole vector, src written by other CTAs (read
+// through L2), loads batched 8 per thread
+template <int NT>
+__device__ __forceinline__ void axpy_from_l2(float* dst, const float* src, int n, int JS, int S2,
+                                             const float* beta, bool overwrite) {
+  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * NT) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (i0 + u * NT < n) ? __ldcg(src + i0 + u * NT) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * NT;
+      if (i < n) dst[i] = overwrite ? v[u] : fmaf(beta[(i % JS) / S2], dst[i], v[u]);
+    }
+  }
+  __syncthreads();
+}
+
+// y_k = (S Z^T Z S^T) p for filter k (+ 2 mu_k p_k), p in shared memory for all filters. The lag
+// blocks C_{k,k'} (La x LB each, contiguous in k') are staged through shared memory in chunks of
+// ngroups filters; thread (qa, grp) accumulates output row qa against filter k' = chunk + grp.
 template <int SI, int NT>
-__device__ void matvec_k(const CgArgs& a, int k, const float* pp, float* red, float two_mu, float* out) {
+__device__ void matvec_k(const CgArgs& a, int k, const float* pp, float* red, float* cbuf, float two_mu,
+                         float* out) {
   const int fh = a.fh, J = a.J, K = a.K, La = a.La, S2 = a.S2;
   constexpr int LB = 2 * SI - 1;
+  const int LL = La * LB;
   const int ngroups = NT / fh;
   const int t = threadIdx.x;
-  if (t < ngroups * fh) {
-    const int qa = t % fh, grp = t / fh;
-    float acc[kMaxJ][SI];
+  const bool worker = t < ngroups * fh;
+  const int qa = worker ? t % fh : 0, grp = worker ? t / fh : 0;
+  float acc[kMaxJ][SI];
 #pragma unroll
-    for (int j = 0; j < kMaxJ; ++j)
+  for (int j = 0; j < kMaxJ; ++j)
 #pragma unroll
-      for (int q = 0; q < SI; ++q) acc[j][q] = 0.f;
-    for (int kp = grp; kp < K; kp += ngroups) {
-      const float* C = a.lags + ((size_t)k * K + kp) * La * LB;
+    for (int q = 0; q < SI; ++q) acc[j][q] = 0.f;
+  for (int kp0 = 0; kp0 < K; kp0 += ngroups) {
+    const int nk = min(ngroups, K - kp0);
+    stage_async<NT>(cbuf, a.lags + ((size_t)k * K + kp0) * LL, nk * LL);
+    if (worker && grp < nk) {
+      const int kp = kp0 + grp;
+      const float* C = cbuf + (size_t)grp * LL;
       for (int qa2 = 0; qa2 < fh; ++qa2) {
         const float* crow = C + (qa - qa2 + fh - 1) * LB;
         float c[LB];
 #pragma unroll
-        for (int i = 0; i < LB; ++i) c[i] = __ldg(crow + i);
+        for (int i = 0; i < LB; ++i) c[i] = crow[i];
 #pragma unroll
         for (int j = 0; j < kMaxJ; ++j) {
           if (j < J) {
@@ -180,6 +220,9 @@ __device__ void matvec_k(const CgArgs& a, int k, const float* pp, float* red, fl
         }
       }
     }
+    __syncthreads();
+  }
+  if (worker) {
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j)
       if (j < J)
@@ -188,188 +231,292 @@ __device__ void matvec_k(const CgArgs& a, int k, const float* pp, float* red, fl
   }
   __syncthreads();
   for (int o = t; o < J * S2; o += NT) {
-    const int j = o / S2, q = o - j * S2, qa = q / SI, qb = q - qa * SI;
-    float s = 0.f;
-    for (int gidx = 0; gidx < ngroups; ++gidx) s += red[((gidx * fh + qa) * J + j) * SI + qb];
-    out[((size_t)k * J + j) * S2 + q] = s + two_mu * pp[((size_t)k * J + j) * S2 + q];
+    const int j = o / S2, q = o - j * S2, qa_ = q / SI, qb = q - qa_ * SI;
+    float sum = 0.f;
+    for (int gidx = 0; gidx < ngroups; ++gidx) sum += red[((gidx * fh + qa_) * J + j) * SI + qb];
+    out[((size_t)k * J + j) * S2 + q] = sum + two_mu * pp[((size_t)k * J + j) * S2 + q];
   }
   __syncthreads();
 }
 
+// Sums vals[0..n) over the block in float32 (the device's float64 rate is a few operations per
+// clock per SM, so per-thread float64 work is kept out of the CG loop); warp partials go to
+// scratch [NT/32][4 kMaxJ], warp 0 finishes, every thread gets the sums back in vals.
 template <int NT>
-__device__ void block_sum(double* vals, int n, double* scratch) {
-  // sums vals[0..n) across the block; result in vals (thread-local in, block-uniform out)
+__device__ void block_sum(float* vals, int n, float* scratch) {
   for (int i = 0; i < n; ++i) {
-    double v = vals[i];
+    float v = vals[i];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) scratch[(threadIdx.x >> 5) * 4 * kMaxJ + i] = v;
   }
   __syncthreads();
-  for (int i = 0; i < n; ++i) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += scratch[w * 4 * kMaxJ + i];
-    vals[i] = s;
+  if (threadIdx.x < 32) {
+    for (int i = 0; i < n; ++i) {
+      float v = (threadIdx.x < NT / 32) ? scratch[threadIdx.x * 4 * kMaxJ + i] : 0.f;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (threadIdx.x == 0) scratch[i] = v;
+    }
   }
   __syncthreads();
+  for (int i = 0; i < n; ++i) vals[i] = scratch[i];
+  __syncthreads();
+}
+
+// sum over the G CTAs of slot entries dots[gb][base + j], j < n (written by other CTAs: read
+// through L2), in a fixed order by warp 0 in float64, into bcast (shared memory)
+template <int NT>
+__device__ void grid_dots(const float* dots, int G, int base, int n, double* bcast) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int gb = lane; gb < G; gb += 32) s += (double)__ldcg(dots + (size_t)gb * 4 * kMaxJ + base + j);
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if (lane == 0) bcast[j] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// z_k = M_k^{-1} r_k for one filter, and the partial dot r_k . z_k. M_k is the filter's own block
+// of the normal-equation matrix (C_kk Toeplitz + 2 mu_k I, inverted at the start of the call), held
+// in shared memory (mloc) when the CTA owns this one filter, else read from a.minv; without
+// block inverses, the diagonal. rk is shared-memory scratch of J * S2 floats.
+template <int NT>
+__device__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc, float* rk,
+                               float* part) {
+  const int S2 = a.S2, JS = a.J * S2;
+  __syncthreads();   // r_k complete
+  for (int o = threadIdx.x; o < JS; o += NT) rk[o] = a.r[(size_t)k * JS + o];
+  __syncthreads();
+  const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
+  for (int o = threadIdx.x; o < JS; o += NT) {
+    const int j = o / S2, q = o - j * S2;
+    float zv = 0.f;
+    if (act) {
+      if (m) {
+        // M_k^{-1} is symmetric: column q, consecutive threads on consecutive addresses
+        const float* r = rk + (size_t)j * S2;
+        float sacc = 0.f;
+#pragma unroll 4
+        for (int q2 = 0; q2 < S2; ++q2) sacc = fmaf(m[(size_t)q2 * S2 + q], r[q2], sacc);
+        zv = sacc;
+      } else {
+        zv = rk[o] * sjac;
+      }
+    }
+    a.zv[(size_t)k * JS + o] = zv;
+    part[1 * kMaxJ + j] = fmaf(rk[o], zv, part[1 * kMaxJ + j]);
+  }
 }
 
 template <int SI, int NT>
 __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   extern __shared__ float smf[];
   __shared__ double scratch[(NT / 32) * 4 * kMaxJ];
+  __shared__ double bc[4 * kMaxJ];
+  // scalars of the iteration, kept by thread 0 (float64) and broadcast through shared memory
+  __shared__ double s_rz[kMaxJ], s_rr[kMaxJ], s_bb[kMaxJ];
+  __shared__ float s_alpha[kMaxJ], s_beta[kMaxJ], s_twomu, s_jac;
+  __shared__ int s_done[kMaxJ], s_all;
   const int K = a.K, J = a.J, S2 = a.S2, G = a.G;
   const int JS = J * S2;
-  float* pp = smf;                              // [K][J][S2]
-  float* red = pp + (size_t)K * JS;             // [ngroups][fh][J][SI]
+  const int ngroups = NT / a.fh;
+  float* pp = smf;                                            // [K][J][S2]
+  float* red = pp + (size_t)K * JS;                           // [ngroups][fh][J][SI]
+  float* cbuf = red + (size_t)ngroups * a.fh * J * SI;        // [ngroups][La][Lb]
+  float* rk = cbuf + (size_t)ngroups * a.La * a.Lb;           // [J][S2]
+  float* mloc = rk + JS;                                      // [S2][S2] (+ [S2] during the inversion)
+  const bool own_one = (G == K) && a.minv;                    // one filter per CTA: keep its inverse
   const int La = a.La, ctr = (a.fh - 1) * a.Lb + (a.fw - 1);   // lag tau = 0
 
   auto active = [&](int k) { return a.lags[((size_t)k * K + k) * La * a.Lb + ctr] > 0.f; };
-  auto precond = [&](int k) {
+  auto precond = [&](int k) {   // called by one thread
     const double m = (double)a.lags[((size_t)k * K + k) * La * a.Lb + ctr] + 2.0 * a.mu[k];
     return (float)(1.0 / m);
   };
 
-  for (int step = 0; step < a.steps; ++step) {
-    // ---- r = b - A x, z = M^{-1} r, p = z -----------------------------------------------
-    for (int i = threadIdx.x; i < K * JS; i += NT) pp[i] = a.x[i];
-    __syncthreads();
-    double part[4 * kMaxJ];
-    for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.0;
+  // ---- block-Jacobi preconditioner for this call: inverse of (C_kk Toeplitz + 2 mu_k I) -------
+  // (the mu at entry; the preconditioner need not track the later mu updates exactly)
+  if (a.minv) {
+    float* A = mloc;                    // [S2][S2]
+    float* colv = A + (size_t)S2 * S2;  // [S2]
+    const int fh = a.fh, fw = a.fw, Lb = a.Lb;
     for (int k = blockIdx.x; k < K; k += G) {
       const bool act = active(k);
-      const float two_mu = (float)(2.0 * a.mu[k]);
-      matvec_k<SI, NT>(a, k, pp, red, two_mu, a.Ap);
-      const float minv = act ? precond(k) : 0.f;
+      if (threadIdx.x == 0) s_twomu = (float)(2.0 * a.mu[k]);
+      __syncthreads();
+      const float tm = s_twomu;
+      const float* C = a.lags + ((size_t)k * K + k) * La * Lb;
+      for (int e = threadIdx.x; e < S2 * S2; e += NT) {
+        const int q = e / S2, q2 = e - q * S2;
+        const int qa = q / fw, qb = q - qa * fw, qa2 = q2 / fw, qb2 = q2 - qa2 * fw;
+        const float diag = (q == q2) ? 1.f : 0.f;
+        A[e] = act ? C[(qa - qa2 + fh - 1) * Lb + (qb - qb2 + fw - 1)] + tm * diag : diag;
+      }
+      __syncthreads();
+      // in-place Gauss-Jordan inversion (symmetric positive definite: no pivoting)
+      for (int pv = 0; pv < S2; ++pv) {
+        for (int i = threadIdx.x; i < S2; i += NT) colv[i] = A[(size_t)i * S2 + pv];
+        __syncthreads();
+        const float inv = 1.f / colv[pv];
+        for (int j = threadIdx.x; j < S2; j += NT)
+          if (j != pv) A[(size_t)pv * S2 + j] *= inv;
+        __syncthreads();
+        for (int i = threadIdx.x >> 5; i < S2; i += NT / 32) {
+          if (i == pv) continue;
+          const float ci = colv[i];
+          float* row = A + (size_t)i * S2;
+          const float* prow = A + (size_t)pv * S2;
+          for (int j = threadIdx.x & 31; j < S2; j += 32) row[j] = (j != pv) ? fmaf(-ci, prow[j], row[j]) : -ci * inv;
+        }
+        if (threadIdx.x == 0) A[(size_t)pv * S2 + pv] = inv;
+        __syncthreads();
+      }
+      if (!own_one) {
+        float* dst = a.minv + (size_t)k * S2 * S2;
+        for (int e = threadIdx.x; e < S2 * S2; e += NT) dst[e] = A[e];
+      }
+      __syncthreads();
+    }
+  }
+  const float* mk = own_one ? mloc : nullptr;
+  float* fscratch = reinterpret_cast<float*>(scratch);
+
+  for (int step = 0; step < a.steps; ++step) {
+    // ---- r = b - A x, z = M^{-1} r, p = z -----------------------------------------------
+    axpy_from_l2<NT>(pp, a.x, K * JS, JS, S2, nullptr, true);
+    float part[4 * kMaxJ];
+    for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
+    for (int k = blockIdx.x; k < K; k += G) {
+      const bool act = active(k);
+      if (threadIdx.x == 0) {
+        s_twomu = (float)(2.0 * a.mu[k]);
+        s_jac = act ? precond(k) : 0.f;
+      }
+      __syncthreads();
+      matvec_k<SI, NT>(a, k, pp, red, cbuf, s_twomu, a.Ap);
       for (int o = threadIdx.x; o < JS; o += NT) {
         const size_t idx = (size_t)k * JS + o;
         const int j = o / S2;
         const float bv = a.b[idx];
         const float rv = act ? bv - a.Ap[idx] : 0.f;
-        const float zv = rv * minv;
         a.r[idx] = rv;
-        a.zv[idx] = zv;
-        part[1 * kMaxJ + j] += (double)rv * zv;
-        part[2 * kMaxJ + j] += (double)rv * rv;
-        part[3 * kMaxJ + j] += act ? (double)bv * bv : 0.0;
+        part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
+        if (act) part[3 * kMaxJ + j] = fmaf(bv, bv, part[3 * kMaxJ + j]);
       }
+      precondition_k<NT>(a, k, act, s_jac, mk, rk, part);
     }
-    block_sum<NT>(part, 4 * kMaxJ, scratch);
+    block_sum<NT>(part, 4 * kMaxJ, fscratch);
     if (threadIdx.x == 0)
       for (int i = 0; i < 4 * kMaxJ; ++i) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + i] = part[i];
     if (!grid_sync(a.bar, G, a.err)) return;
-    double rz[kMaxJ], rr[kMaxJ], bb[kMaxJ];
-    for (int j = 0; j < J; ++j) {
-      rz[j] = rr[j] = bb[j] = 0.0;
-      for (int gb = 0; gb < G; ++gb) {
-        rz[j] += a.dots[(size_t)gb * 4 * kMaxJ + 1 * kMaxJ + j];
-        rr[j] += a.dots[(size_t)gb * 4 * kMaxJ + 2 * kMaxJ + j];
-        bb[j] += a.dots[(size_t)gb * 4 * kMaxJ + 3 * kMaxJ + j];
+    grid_dots<NT>(a.dots, G, kMaxJ, 3 * kMaxJ, bc);
+    if (threadIdx.x == 0)
+      for (int j = 0; j < kMaxJ; ++j) {
+        s_rz[j] = bc[j];
+        s_rr[j] = bc[kMaxJ + j];
+        s_bb[j] = bc[2 * kMaxJ + j];
+        s_done[j] = (j >= J);
       }
-    }
-    for (int i = threadIdx.x; i < K * JS; i += NT) pp[i] = a.zv[i];
-    __syncthreads();
+    axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, nullptr, true);
     int it = 0;
-    bool done[kMaxJ];
-    for (int j = 0; j < kMaxJ; ++j) done[j] = (j >= J);
     for (; it < a.cg_max; ++it) {
-      bool all = true;
-      for (int j = 0; j < J; ++j) {
-        done[j] = done[j] || !(rr[j] > a.tol2 * bb[j]) || !(rz[j] > 0.0);
-        all = all && done[j];
+      if (threadIdx.x == 0) {
+        int all = 1;
+        for (int j = 0; j < J; ++j) {
+          s_done[j] = s_done[j] || !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+          all = all && s_done[j];
+        }
+        s_all = all;
       }
-      if (all) break;
+      __syncthreads();
+      if (s_all) break;
       // ---- Ap, p.Ap --------------------------------------------------------------------
-      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.0;
+      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
       for (int k = blockIdx.x; k < K; k += G) {
         const bool act = active(k);
-        matvec_k<SI, NT>(a, k, pp, red, (float)(2.0 * a.mu[k]), a.Ap);
+        if (threadIdx.x == 0) s_twomu = (float)(2.0 * a.mu[k]);
+        __syncthreads();
+        matvec_k<SI, NT>(a, k, pp, red, cbuf, s_twomu, a.Ap);
         for (int o = threadIdx.x; o < JS; o += NT) {
           const size_t idx = (size_t)k * JS + o;
           const int j = o / S2;
-          if (act) part[j] += (double)pp[idx] * a.Ap[idx];
+          if (act) part[j] = fmaf(pp[idx], a.Ap[idx], part[j]);
         }
       }
-      block_sum<NT>(part, kMaxJ, scratch);
+      block_sum<NT>(part, kMaxJ, fscratch);
       if (threadIdx.x == 0)
         for (int j = 0; j < kMaxJ; ++j) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + j] = part[j];
       if (!grid_sync(a.bar, G, a.err)) return;
-      float alpha[kMaxJ];
-      for (int j = 0; j < kMaxJ; ++j) {
-        double pap = 0.0;
-        if (j < J)
-          for (int gb = 0; gb < G; ++gb) pap += a.dots[(size_t)gb * 4 * kMaxJ + j];
-        alpha[j] = (j < J && !done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
-      }
+      grid_dots<NT>(a.dots, G, 0, kMaxJ, bc);
+      if (threadIdx.x == 0)
+        for (int j = 0; j < kMaxJ; ++j) {
+          const double pap = bc[j];
+          s_alpha[j] = (j < J && !s_done[j] && pap > 0.0) ? (float)(s_rz[j] / pap) : 0.f;
+        }
+      __syncthreads();
       // ---- x += alpha p, r -= alpha Ap, z = M^{-1} r ---------------------------------------
-      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.0;
+      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
       for (int k = blockIdx.x; k < K; k += G) {
         if (!active(k)) continue;
-        const float minv = precond(k);
+        if (threadIdx.x == 0) s_jac = precond(k);
+        __syncthreads();
         for (int o = threadIdx.x; o < JS; o += NT) {
           const size_t idx = (size_t)k * JS + o;
           const int j = o / S2;
-          const float al = alpha[j];
+          const float al = s_alpha[j];
           a.x[idx] = fmaf(al, pp[idx], a.x[idx]);
           const float rv = fmaf(-al, a.Ap[idx], a.r[idx]);
-          const float zv = rv * minv;
           a.r[idx] = rv;
-          a.zv[idx] = zv;
-          part[1 * kMaxJ + j] += (double)rv * zv;
-          part[2 * kMaxJ + j] += (double)rv * rv;
+          part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
         }
+        precondition_k<NT>(a, k, true, s_jac, mk, rk, part);
       }
-      block_sum<NT>(part, 4 * kMaxJ, scratch);
+      block_sum<NT>(part, 4 * kMaxJ, fscratch);
       if (threadIdx.x == 0)
         for (int i = kMaxJ; i < 3 * kMaxJ; ++i) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + i] = part[i];
       if (!grid_sync(a.bar, G, a.err)) return;
-      float betav[kMaxJ];
-      for (int j = 0; j < kMaxJ; ++j) {
-        double rzn = 0.0, rrn = 0.0;
-        if (j < J)
-          for (int gb = 0; gb < G; ++gb) {
-            rzn += a.dots[(size_t)gb * 4 * kMaxJ + 1 * kMaxJ + j];
-            rrn += a.dots[(size_t)gb * 4 * kMaxJ + 2 * kMaxJ + j];
+      grid_dots<NT>(a.dots, G, kMaxJ, 2 * kMaxJ, bc);
+      if (threadIdx.x == 0) {
+        for (int j = 0; j < kMaxJ; ++j) {
+          if (j < J && !s_done[j]) {
+            s_beta[j] = s_rz[j] > 0.0 ? (float)(bc[j] / s_rz[j]) : 0.f;
+            s_rz[j] = bc[j];
+            s_rr[j] = bc[kMaxJ + j];
+          } else {
+            s_beta[j] = 0.f;
           }
-        if (j < J && !done[j]) {
-          betav[j] = rz[j] > 0.0 ? (float)(rzn / rz[j]) : 0.f;
-          rz[j] = rzn;
-          rr[j] = rrn;
-        } else {
-          betav[j] = 0.f;
         }
       }
-      // every CTA keeps the whole search direction: p = z + beta p
-      for (int i = threadIdx.x; i < K * JS; i += NT) {
-        const int j = (i % JS) / S2;
-        pp[i] = fmaf(betav[j], pp[i], a.zv[i]);
-      }
       __syncthreads();
+      // every CTA keeps the whole search direction: p = z + beta p
+      axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, s_beta, false);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.iters) a.iters[step] = it;
     // ---- mu_k <- max(mu_k ||d_k||, floor) for active filters (Eq. mu_update) ------------------
     for (int k = blockIdx.x; k < K; k += G) {
-      double s[4 * kMaxJ];
-      for (int i = 0; i < 4 * kMaxJ; ++i) s[i] = 0.0;
+      float sq[4 * kMaxJ];
+      for (int i = 0; i < 4 * kMaxJ; ++i) sq[i] = 0.f;
       for (int o = threadIdx.x; o < JS; o += NT) {
         const float xv = a.x[(size_t)k * JS + o];
-        s[0] += (double)xv * xv;
+        sq[0] = fmaf(xv, xv, sq[0]);
       }
-      block_sum<NT>(s, 1, scratch);
-      if (threadIdx.x == 0 && active(k)) a.mu[k] = fmax(a.mu[k] * sqrt(s[0]), a.mu_floor);
+      block_sum<NT>(sq, 1, fscratch);
+      if (threadIdx.x == 0 && active(k)) a.mu[k] = fmax(a.mu[k] * sqrt((double)sq[0]), a.mu_floor);
     }
     if (!grid_sync(a.bar, G, a.err)) return;
   }
   // ---- d_k <- d_k / max(1, ||d_k||) ---------------------------------------------------------
   for (int k = blockIdx.x; k < K; k += G) {
-    double s[4 * kMaxJ];
-    for (int i = 0; i < 4 * kMaxJ; ++i) s[i] = 0.0;
+    float sq[4 * kMaxJ];
+    for (int i = 0; i < 4 * kMaxJ; ++i) sq[i] = 0.f;
     for (int o = threadIdx.x; o < JS; o += NT) {
       const float xv = a.x[(size_t)k * JS + o];
-      s[0] += (double)xv * xv;
+      sq[0] = fmaf(xv, xv, sq[0]);
     }
-    block_sum<NT>(s, 1, scratch);
-    const double nrm = sqrt(s[0]);
-    const float sc = (float)(1.0 / fmax(1.0, nrm));
+    block_sum<NT>(sq, 1, fscratch);
+    const float sc = 1.0f / fmaxf(1.0f, sqrtf(sq[0]));
     for (int o = threadIdx.x; o < JS; o += NT) a.x[(size_t)k * JS + o] *= sc;
   }
 }
@@ -394,7 +541,9 @@ static cudaError_t launch_cg_si(const Ctx& c, CgArgs a) {
   constexpr int NT = kNT;
   auto kern = k_learn_cg<SI, NT>;
   const int ngroups = NT / c.fh;
-  const size_t smem = ((size_t)c.K * c.J * c.S2 + (size_t)ngroups * c.fh * c.J * SI) * sizeof(float);
+  size_t smem = ((size_t)c.K * c.J * c.S2 + (size_t)ngroups * c.fh * c.J * SI +
+                 (size_t)ngroups * (2 * c.fh - 1) * (2 * SI - 1) + (size_t)c.J * c.S2 +
+                 (a.minv ? (size_t)c.S2 * c.S2 + c.S2 : 0)) * sizeof(float);
   if (smem > kSmemLimit) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -415,7 +564,7 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   const size_t nvec = (size_t)c.K * c.J * c.S2;
   a.lags = c.L.lags; a.b = c.L.b; a.x = d;
   a.r = c.L.vec; a.zv = c.L.vec + nvec; a.Ap = c.L.vec + 2 * nvec;
-  a.mu = c.L.mu; a.dots = c.L.dots; a.bar = c.L.bar; a.iters = c.L.iters; a.err = dev_err;
+  a.mu = c.L.mu; a.minv = c.L.minv; a.dots = c.L.dots; a.bar = c.L.bar; a.iters = c.L.iters; a.err = dev_err;
   cudaError_t e = cudaMemsetAsync(c.L.bar, 0, 2 * sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
   switch (c.fw) {

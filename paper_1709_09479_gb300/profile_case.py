@@ -4,8 +4,8 @@
     python -m paper_1709_09479_gb300.profile_case learning [...]
 
 coding: csc_code with `iters` ADMM iterations (launch order: 2 spectra, solve setup, spectra,
-prologue sweep, then `iters` sweeps). learning: one csc_code of 2 iterations, then csc_learn with
-`steps` learning steps. Inputs are the seeded 1/f^2 fields and Gaussian dictionary of bench.py.
+prologue sweep, then `iters` sweeps). learning: one csc_code of `iters` iterations, then csc_learn
+with `steps` learning steps. Inputs are the seeded 1/f^2 fields and Gaussian dictionary of bench.py.
 """
 import argparse
 import sys
@@ -35,7 +35,7 @@ def main():
         if a.what == "coding":
             sv.code(x, d, v, z, a.iters)
         else:
-            sv.code(x, d, v, z, 2)
+            sv.code(x, d, v, z, a.iters)
             mu = torch.full((a.K,), 0.5, dtype=torch.float64, device="cuda")
             sv.learn(x, z, d, mu, a.steps)
     torch.cuda.synchronize()
