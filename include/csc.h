@@ -72,7 +72,13 @@ typedef struct {
   int cg_max;     /* CG iteration cap per learning step (csc_learn), >= 1 */
   double cg_tol;  /* CG stop: ||r|| <= cg_tol ||b|| (relative residual), > 0 */
   int precision;  /* csc_precision */
+  int flags;      /* CSC_FLAG_* bits */
 } csc_params;
+
+/* csc_code records its launch sequence in a CUDA graph the first time it is called with a given
+   (x, d, v, z, iters) on device memory, and replays the graph on later calls with the same
+   arguments (the arrays' contents may change between calls; their addresses may not). */
+#define CSC_FLAG_GRAPH 1
 
 /*
  * Create a context for n_images images, all of size H x W (dims = {H, W}), on the current CUDA
@@ -84,6 +90,22 @@ typedef struct {
  */
 csc_status csc_init(const csc_params* params, int n_images, const int* dims, void* stream,
                     csc_ctx** out);
+
+/*
+ * Like csc_init for a batch whose images have their own sizes: dims holds n_images (H, W) pairs.
+ * Arrays are the per-image arrays of csc_init concatenated in image order: x holds
+ * J*H_n*W_n floats for image n, v and z hold K*H_n*W_n. Each size must satisfy csc_init's
+ * conditions. Images of one size share one FFT plan, filter spectrum and per-frequency system;
+ * one launch per ADMM iteration codes every image, with the maps split over the CTAs by pixel
+ * count. On the first coding call the launch shape (threads per CTA, CTAs per SM) is chosen by
+ * timing the candidates on this batch. Supports csc_code and csc_objective (csc_learn and the
+ * reverse-mode calls return CSC_ERR_UNSUPPORTED on such a context).
+ */
+csc_status csc_init_uneven(const csc_params* params, int n_images, const int* dims, void* stream,
+                           csc_ctx** out);
+
+/* One-line JSON description of the context (sizes, size classes, launch shape) into buf (len bytes). */
+csc_status csc_describe(const csc_ctx* ctx, char* buf, int len);
 
 /*
  * Coding subproblem (Eq. 2) by `iters` iterations of the dual ADMM of Eq. Inference_solution

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "CSC_OK", 1: "CSC_ERR_ARG", 2: "CSC_ERR_SHAPE", 3: "CSC_ERR_W
                 8: "CSC_ERR_UNSUPPORTED"}
 CSC_FP32 = 0
 CSC_MIXED_BF16 = 1
+CSC_FLAG_GRAPH = 1
 
 
 class CscError(RuntimeError):
@@ -34,7 +35,7 @@ class CscError(RuntimeError):
 class csc_params(ctypes.Structure):
     _fields_ = [("J", ctypes.c_int), ("K", ctypes.c_int), ("fs", ctypes.c_int * 2),
                 ("beta", ctypes.c_double), ("rho", ctypes.c_double), ("cg_max", ctypes.c_int),
-                ("cg_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class csc_timing(ctypes.Structure):
@@ -63,6 +64,10 @@ def _load():
     lib.csc_timing_enable.restype = i
     lib.csc_timing_read.argtypes = [vp, ctypes.POINTER(csc_timing)]
     lib.csc_timing_read.restype = i
+    lib.csc_init_uneven.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, ctypes.POINTER(vp)]
+    lib.csc_init_uneven.restype = i
+    lib.csc_describe.argtypes = [vp, ctypes.c_char_p, i]
+    lib.csc_describe.restype = i
     lib.csc_tape_bytes.argtypes = [vp, i, i]
     lib.csc_tape_bytes.restype = ctypes.c_size_t
     lib.csc_code_unrolled.argtypes = [vp, vp, vp, vp, vp, i, i, vp]
@@ -112,13 +117,29 @@ def csc_last_error(ctx=None) -> str:
 
 
 def csc_init(J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6, precision=CSC_FP32,
-             stream=None):
+             stream=None, flags=0):
     """Create a context; returns an opaque handle (int). ``stream``: cudaStream_t as int or None."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, precision)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, precision, flags)
     dims_arr = (ctypes.c_int * 2)(*dims)
     out = ctypes.c_void_p()
     _check(LIB.csc_init(ctypes.byref(p), n_images, dims_arr, stream, ctypes.byref(out)))
     return out.value
+
+
+def csc_init_uneven(J, K, fs, dims_list, beta, rho, precision=CSC_FP32, stream=None, flags=0):
+    """Context for images of different sizes; dims_list = [(H, W), ...] in image order."""
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, precision, flags)
+    flat = [int(v) for hw in dims_list for v in hw]
+    arr = (ctypes.c_int * len(flat))(*flat)
+    out = ctypes.c_void_p()
+    _check(LIB.csc_init_uneven(ctypes.byref(p), len(dims_list), arr, stream, ctypes.byref(out)))
+    return out.value
+
+
+def csc_describe(ctx) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(LIB.csc_describe(ctx, buf, 512), ctx)
+    return buf.value.decode()
 
 
 def csc_destroy(ctx):
@@ -206,13 +227,20 @@ def _current_stream():
 class Solver:
     """One context: N images of size dims = (H, W), K filters of support fs with J channels."""
 
-    def __init__(self, *, J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6,
-                 precision=CSC_FP32, stream=None):
-        self.J, self.K, self.fs, self.dims, self.N = J, K, tuple(fs), tuple(dims), n_images
+    def __init__(self, *, J, K, fs, dims=None, n_images=None, beta, rho, cg_max=100, cg_tol=1e-6,
+                 precision=CSC_FP32, stream=None, flags=0, dims_list=None):
+        """dims + n_images: a batch of equal sizes; dims_list: one (H, W) per image (uneven batch)."""
+        self.J, self.K, self.fs = J, K, tuple(fs)
         self.beta, self.rho = beta, rho
         if stream is None:
             stream = _current_stream()
-        self.ctx = csc_init(J, K, fs, dims, n_images, beta, rho, cg_max, cg_tol, precision, stream)
+        if dims_list is not None:
+            self.dims_list = [tuple(hw) for hw in dims_list]
+            self.N, self.dims = len(self.dims_list), None
+            self.ctx = csc_init_uneven(J, K, fs, self.dims_list, beta, rho, precision, stream, flags)
+        else:
+            self.dims, self.N = tuple(dims), n_images
+            self.ctx = csc_init(J, K, fs, dims, n_images, beta, rho, cg_max, cg_tol, precision, stream, flags)
 
     def code(self, x, d, v, z=None, iters=1):
         csc_code(self.ctx, x, d, v, z, iters)
@@ -222,6 +250,9 @@ class Solver:
 
     def objective(self, x, d, z):
         return csc_objective(self.ctx, x, d, z)
+
+    def describe(self):
+        return csc_describe(self.ctx)
 
     def timing_enable(self, enable=True):
         csc_timing_enable(self.ctx, enable)

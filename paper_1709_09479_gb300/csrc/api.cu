@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <vector>
@@ -100,6 +101,13 @@ void bracket_close(Ctx* c, int i) {
 }
 
 void free_all(Ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
+  void* uptrs[] = {c->U.d_cls, c->U.d_img, c->U.d_mstart, c->U.d_slot};
+  for (void* p : uptrs)
+    if (p) cudaFree(p);
   for (auto& ep : c->events) {
     cudaEventDestroy(ep.a);
     cudaEventDestroy(ep.b);
@@ -111,6 +119,229 @@ void free_all(Ctx* c) {
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+}
+
+
+// checks one image size against what the per-map kernels support; fills the geometry
+csc_status check_size(const csc_params& p, int H, int W, Geometry& g, const char* who) {
+  const int fh = p.fs[0], fw = p.fs[1];
+  char msg[160];
+  if (H < 8 || W < 8 || (W & 1)) {
+    std::snprintf(msg, sizeof(msg), "%s: image %dx%d: need H, W >= 8 and W even", who, H, W);
+    return fail(nullptr, CSC_ERR_SHAPE, msg);
+  }
+  if (fh > H || fw > W) {
+    std::snprintf(msg, sizeof(msg), "%s: filter larger than the %dx%d image", who, H, W);
+    return fail(nullptr, CSC_ERR_SHAPE, msg);
+  }
+  g.H = H; g.W = W; g.Wh = W / 2; g.Wc = W / 2 + 1; g.P = odd_pitch(g.Wc);
+  g.Omega = H * g.Wc; g.D = H * W;
+  g.ct_id = (H == 128 && W == 128) ? 1 : (H == 100 && W == 100) ? 2 : (H == 64 && W == 64) ? 3 : 0;
+  g.rt.H = H; g.rt.W = W; g.rt.Wh = g.Wh; g.rt.Wc = g.Wc; g.rt.P = g.P; g.rt.Omega = g.Omega; g.rt.D = g.D;
+  g.rt.rrow = factorize(g.Wh);
+  g.rt.rcol = factorize(H);
+  if (!radices_ok(g.rt.rrow) || !radices_ok(g.rt.rcol)) {
+    std::snprintf(msg, sizeof(msg), "%s: image %dx%d: H and W/2 must factor into 2, 3, 5 and 7", who, H, W);
+    return fail(nullptr, CSC_ERR_SHAPE, msg);
+  }
+  if (sweep_smem_bytes(g, p.J, kIter) > kSmemLimit) {
+    std::snprintf(msg, sizeof(msg), "%s: image %dx%d too large for one map per CTA in shared memory", who, H, W);
+    return fail(nullptr, CSC_ERR_SHAPE, msg);
+  }
+  return CSC_OK;
+}
+
+// a context view on one size class of an uneven batch, for the per-map setup launchers
+void class_view(const Ctx& c, int ci, Ctx& v) {
+  const UClass& uc = c.U.cls[ci];
+  v.p = c.p; v.N = c.N; v.J = c.J; v.K = c.K; v.fh = c.fh; v.fw = c.fw; v.S2 = c.S2;
+  v.stream = c.stream; v.device = c.device; v.nsm = c.nsm; v.G = c.G;
+  Geometry g;
+  check_size(c.p, c.U.cls_H[ci], c.U.cls_W[ci], g, "class");
+  g.ct_id = 0;
+  v.g = g;
+  v.tw = c.tw + uc.tw;
+  v.dhat = c.dhat + uc.dhat;
+  v.pdiag = c.pdiag + uc.pd;
+  v.pmat = c.pmat + uc.pm;
+}
+
+// cost-balanced CTA map ranges and partial-sum slots for G CTAs
+void uneven_partition(Ctx* c, int G) {
+  UnevenLayout& U = c->U;
+  const int N = c->N, K = c->K, J = c->J;
+  std::vector<double> cost(N);
+  double total = 0.0;
+  for (int n = 0; n < N; ++n) {
+    const UClass& uc = U.cls[U.img[n].cls];
+    cost[n] = (double)uc.g.D;
+    total += cost[n] * K;
+  }
+  const long long NK = (long long)N * K;
+  U.mstart.assign(G + 1, 0);
+  long long m = 0;
+  double acc = 0.0;
+  for (int cta = 1; cta < G; ++cta) {
+    const double target = total * cta / G;
+    while (m < NK && acc + cost[m / K] * 0.5 < target) { acc += cost[m / K]; ++m; }
+    long long lo = U.mstart[cta - 1] + 1, hi = NK - (G - cta);
+    U.mstart[cta] = std::min(std::max(m, lo), hi);
+    if (U.mstart[cta] != m) {   // keep acc consistent with the clamped boundary
+      acc = 0.0;
+      for (long long q = 0; q < U.mstart[cta]; ++q) acc += cost[q / K];
+      m = U.mstart[cta];
+    }
+  }
+  U.mstart[G] = NK;
+  auto cta_of = [&](long long map) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (U.mstart[mid] <= map) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  U.slot.assign(G + N, 0);
+  long long off = 0;
+  for (int n = 0; n < N; ++n) {
+    UImage& im = U.img[n];
+    im.c0 = cta_of((long long)n * K);
+    im.c1 = cta_of((long long)(n + 1) * K - 1);
+    const long long om = U.cls[im.cls].g.Omega;
+    for (int cc = im.c0; cc <= im.c1; ++cc) {
+      U.slot[cc + n] = off;
+      off += (long long)J * om;
+    }
+  }
+  U.n_slot = off;
+  c->G = G;
+}
+
+csc_status upload_uneven(Ctx* c) {
+  UnevenLayout& U = c->U;
+  auto put = [&](auto** dptr, const auto& vec) {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    if (*dptr) cudaFree(*dptr);
+    *dptr = nullptr;
+    if (cudaMalloc((void**)dptr, std::max<size_t>(vec.size(), 1) * sizeof(T)) != cudaSuccess) return false;
+    return cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!put(&U.d_cls, U.cls) || !put(&U.d_img, U.img) || !put(&U.d_mstart, U.mstart) || !put(&U.d_slot, U.slot)) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "uneven batch: descriptor upload failed");
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (c->part[i]) cudaFree(c->part[i]);
+    c->part[i] = nullptr;
+    if (cudaMalloc((void**)&c->part[i], std::max<long long>(U.n_slot, 1) * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CSC_ERR_WORKSPACE, "uneven batch: partial-sum allocation failed");
+    }
+  }
+  if (c->l1) cudaFree(c->l1);
+  c->l1 = nullptr;
+  if (cudaMalloc((void**)&c->l1, c->G * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "uneven batch: allocation failed");
+  }
+  return CSC_OK;
+}
+
+UnevenArgs uneven_args(const Ctx& c, const float2* part_in, float2* part_out, float* v, float* z) {
+  UnevenArgs a;
+  a.N = c.N; a.K = c.K; a.J = c.J; a.G = c.G;
+  a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
+  a.buf_elems = c.U.buf_elems; a.max_omega = c.U.max_omega;
+  a.cls = c.U.d_cls; a.img = c.U.d_img; a.mstart = c.U.d_mstart; a.slot = c.U.d_slot;
+  a.tw = c.tw; a.dhat = c.dhat; a.pdiag = c.pdiag; a.pmat = c.pmat; a.xhat = c.xhat;
+  a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1;
+  return a;
+}
+
+// spectra of the filters (per class) and of the images (per image) of an uneven batch
+cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
+  for (int ci = 0; ci < (int)c->U.cls.size(); ++ci) {
+    Ctx v;
+    class_view(*c, ci, v);
+    cudaError_t e = launch_fft_maps(v, d, c->K * c->J, 1, v.dhat);
+    if (e == cudaSuccess && solve) e = launch_solve_prep(v);
+    if (e != cudaSuccess) return e;
+    c->launches += solve ? 2 : 1;
+  }
+  for (int n = 0; n < c->N; ++n) {
+    const UImage& im = c->U.img[n];
+    Ctx v;
+    class_view(*c, im.cls, v);
+    cudaError_t e = launch_fft_maps(v, x + im.x, c->J, 0, c->xhat + im.xh);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+  }
+  return cudaSuccess;
+}
+
+// the sweeps of one coding call on an uneven batch
+cudaError_t uneven_sweeps(Ctx* c, float* v, float* z, int iters) {
+  const size_t smem_max = uneven_smem_bytes(c->U, c->J, kPrologue);
+  cudaError_t e = launch_sweep_uneven(uneven_args(*c, nullptr, c->part[0], v, nullptr), kPrologue, c->G, c->U.nt,
+                                      uneven_smem_bytes(c->U, c->J, kPrologue), c->stream);
+  (void)smem_max;
+  c->launches += 1;
+  for (int t = 0; t < iters && e == cudaSuccess; ++t) {
+    const int mode = (t == iters - 1) ? kLast : kIter;
+    const int br = (mode == kIter) ? bracket_open(c, 0) : -1;
+    e = launch_sweep_uneven(uneven_args(*c, c->part[t & 1], c->part[(t + 1) & 1], v, z), mode, c->G, c->U.nt,
+                            uneven_smem_bytes(c->U, c->J, mode), c->stream);
+    bracket_close(c, br);
+    c->launches += 1;
+  }
+  return e;
+}
+
+// pick threads per CTA and CTAs per SM for this batch by timing two sweeps of each candidate
+csc_status uneven_autotune(Ctx* c, float* v) {
+  struct Cand { int nt, per_sm; };
+  const Cand cands[] = {{512, 1}, {256, 1}, {256, 2}, {512, 2}};
+  const size_t smem = uneven_smem_bytes(c->U, c->J, kIter);
+  float best = 1e30f;
+  Cand pick{512, 1};
+  float* vs = nullptr;
+  const size_t nv = (size_t)c->U.n_v;
+  CSC_CHECK_CUDA(c, cudaMalloc((void**)&vs, nv * sizeof(float)), "autotune scratch");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(vs, v, nv * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "copy");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (const Cand& cd : cands) {
+    if (cd.per_sm * (smem + 1024) > (size_t)228 * 1024) continue;
+    const int G = (int)std::min<long long>((long long)c->nsm * cd.per_sm, (long long)c->N * c->K);
+    uneven_partition(c, G);
+    csc_status st = upload_uneven(c);
+    if (st != CSC_OK) { cudaFree(vs); return st; }
+    c->U.nt = cd.nt;
+    cudaError_t e = launch_sweep_uneven(uneven_args(*c, nullptr, c->part[0], vs, nullptr), kPrologue, G, cd.nt,
+                                        uneven_smem_bytes(c->U, c->J, kPrologue), c->stream);
+    e = (e == cudaSuccess) ? launch_sweep_uneven(uneven_args(*c, c->part[0], c->part[1], vs, nullptr), kIter, G,
+                                                 cd.nt, smem, c->stream) : e;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+      e = launch_sweep_uneven(uneven_args(*c, c->part[(r + 1) & 1], c->part[r & 1], vs, nullptr), kIter, G, cd.nt,
+                              smem, c->stream);
+    cudaEventRecord(e1, c->stream);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; pick = cd; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(vs);
+  const int G = (int)std::min<long long>((long long)c->nsm * pick.per_sm, (long long)c->N * c->K);
+  uneven_partition(c, G);
+  csc_status st = upload_uneven(c);
+  if (st != CSC_OK) return st;
+  c->U.nt = pick.nt;
+  c->U.tuned = true;
+  return CSC_OK;
 }
 
 }  // namespace
@@ -223,6 +454,120 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
   return CSC_OK;
 }
 
+csc_status csc_init_uneven(const csc_params* params, int n_images, const int* dims, void* stream,
+                           csc_ctx** out) {
+  if (!params || !dims || !out) return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: null argument");
+  *out = nullptr;
+  const csc_params& p = *params;
+  if (n_images < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: n_images must be >= 1");
+  if (p.J < 1 || p.J > kMaxJ) return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: J must be 1..3");
+  if (p.K < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: K must be >= 1");
+  if (!(p.beta > 0) || !(p.rho > 0) || !std::isfinite(p.beta) || !std::isfinite(p.rho))
+    return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: beta and rho must be finite and > 0");
+  if (p.precision != CSC_FP32) return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: CSC_FP32 only");
+  const int fh = p.fs[0], fw = p.fs[1];
+  if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: filter support must be odd and >= 1");
+  csc_ctx* ctx = new (std::nothrow) csc_ctx;
+  if (!ctx) return fail(nullptr, CSC_ERR_WORKSPACE, "csc_init_uneven: out of host memory");
+  Ctx* c = &ctx->c;
+  c->p = p;
+  c->N = n_images; c->J = p.J; c->K = p.K; c->fh = fh; c->fw = fw; c->S2 = fh * fw;
+  c->uneven = true;
+  c->stream = (cudaStream_t)stream;
+  auto bail = [&](csc_status st) {
+    if (c->last_error.size()) g_init_error = c->last_error;
+    free_all(c);
+    delete ctx;
+    return st;
+  };
+  UnevenLayout& U = c->U;
+  std::vector<Geometry> geos;
+  std::vector<float2> tw;
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int n = 0; n < n_images; ++n) {
+    const int H = dims[2 * n], W = dims[2 * n + 1];
+    int ci = -1;
+    for (int q = 0; q < (int)U.cls.size(); ++q)
+      if (U.cls_H[q] == H && U.cls_W[q] == W) { ci = q; break; }
+    if (ci < 0) {
+      Geometry g;
+      csc_status st = check_size(p, H, W, g, "csc_init_uneven");
+      if (st != CSC_OK) { delete ctx; return st; }
+      UClass uc;
+      uc.g = g.rt;
+      uc.tw = U.n_tw; uc.dhat = U.n_dhat; uc.pd = U.n_pd; uc.pm = U.n_pm;
+      U.n_tw += g.Wh + g.H + g.Wc;
+      U.n_dhat += (long long)p.K * p.J * g.Omega;
+      U.n_pd += g.Omega;
+      U.n_pm += (long long)g.Omega * p.J * p.J;
+      for (int t = 0; t < g.Wh; ++t) tw.push_back(make_float2((float)cos(pi2 * t / g.Wh), (float)-sin(pi2 * t / g.Wh)));
+      for (int t = 0; t < g.H; ++t) tw.push_back(make_float2((float)cos(pi2 * t / g.H), (float)-sin(pi2 * t / g.H)));
+      for (int t = 0; t < g.Wc; ++t) tw.push_back(make_float2((float)cos(pi2 * t / g.W), (float)-sin(pi2 * t / g.W)));
+      U.buf_elems = std::max(U.buf_elems, g.H * g.P);
+      U.max_omega = std::max(U.max_omega, g.Omega);
+      U.max_tw = std::max(U.max_tw, g.Wh + g.H + g.Wc);
+      U.cls.push_back(uc);
+      U.cls_H.push_back(H);
+      U.cls_W.push_back(W);
+      geos.push_back(g);
+      ci = (int)U.cls.size() - 1;
+    }
+    UImage im;
+    im.cls = ci; im.c0 = im.c1 = 0;
+    im.x = U.n_x; im.v = U.n_v; im.xh = U.n_xh;
+    U.n_x += (long long)p.J * geos[ci].D;
+    U.n_v += (long long)p.K * geos[ci].D;
+    U.n_xh += (long long)p.J * geos[ci].Omega;
+    U.img.push_back(im);
+  }
+  if (uneven_smem_bytes(U, p.J, kIter) > kSmemLimit) {
+    delete ctx;
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: the largest image and the largest spectrum do not fit one CTA");
+  }
+  c->g = geos[0];
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    c->last_error = "csc_init_uneven: no CUDA device";
+    return bail(CSC_ERR_CUDA);
+  }
+  uneven_partition(c, (int)std::min<long long>(c->nsm, (long long)n_images * p.K));
+  if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->dhat, U.n_dhat * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->pdiag, U.n_pd * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->pmat, U.n_pm * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->xhat, U.n_xh * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->objimg, n_images * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->last_error = "csc_init_uneven: device workspace allocation failed";
+    return bail(CSC_ERR_WORKSPACE);
+  }
+  if (cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->last_error = "csc_init_uneven: upload failed";
+    return bail(CSC_ERR_CUDA);
+  }
+  if (upload_uneven(c) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
+  *out = ctx;
+  return CSC_OK;
+}
+
+csc_status csc_describe(const csc_ctx* ctx, char* buf, int len) {
+  if (!ctx || !buf || len < 1) return fail(nullptr, CSC_ERR_ARG, "csc_describe: null argument");
+  const Ctx& c = ctx->c;
+  const int n_cls = c.uneven ? (int)c.U.cls.size() : 1;
+  std::snprintf(buf, (size_t)len,
+                "{\"N\": %d, \"K\": %d, \"J\": %d, \"uneven\": %s, \"size_classes\": %d, \"ctas\": %d, "
+                "\"threads_per_cta\": %d, \"autotuned\": %s, \"graph\": %s, \"graph_recorded\": %s}",
+                c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, c.G, c.uneven ? c.U.nt : (int)kNTSweep,
+                (c.uneven && c.U.tuned) ? "true" : "false", (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
+                c.graph ? "true" : "false");
+  return CSC_OK;
+}
+
 void csc_destroy(csc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->c.device);
@@ -237,8 +582,9 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
   if (!x || !d || !v) return fail(c, CSC_ERR_ARG, "csc_code: x, d and v must be non-null");
   if (iters < 0) return fail(c, CSC_ERR_ARG, "csc_code: iters must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
-  const size_t nv = (size_t)c->N * c->K * c->g.D;
+  const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
+  const size_t nd = (size_t)c->K * c->J * c->S2;
+  const size_t nv = c->uneven ? (size_t)c->U.n_v : (size_t)c->N * c->K * c->g.D;
   const float *xd = nullptr, *dd = nullptr, *vd_c = nullptr;
   csc_status s;
   if ((s = stage_in(c, v, &c->st_v, nv, &vd_c, true)) != CSC_OK) return s;
@@ -254,27 +600,80 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
       z_host = true;
     }
   }
-  if (iters == 0) {
-    if (zd) CSC_CHECK_CUDA(c, launch_codes_from_state(*c, vd, zd), "codes_from_state");
-    if (zd) c->launches += 1;
-  } else {
+  if (iters > 0) {
     if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
     if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
-    CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
-    CSC_CHECK_CUDA(c, launch_solve_prep(*c), "per-frequency solve setup");
-    CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
-    if (c->p.precision == CSC_MIXED_BF16) {
-      CSC_CHECK_CUDA(c, launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->K * c->J * c->g.Omega), "bf16 spectra");
+  }
+  if (c->uneven && iters > 0 && !c->U.tuned) {
+    CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, true), "uneven setup");
+    if ((s = uneven_autotune(c, vd)) != CSC_OK) return s;
+  }
+  // the launch sequence of this call
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (iters == 0) {
+      if (!zd) return cudaSuccess;
+      c->launches += 1;
+      return launch_codes_from_state(*c, vd, zd);
+    }
+    if (c->uneven) {
+      e = uneven_setup(c, dd, xd, true);
+      if (e == cudaSuccess) e = uneven_sweeps(c, vd, zd, iters);
+      return e;
+    }
+    e = launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat);
+    if (e == cudaSuccess) e = launch_solve_prep(*c);
+    if (e == cudaSuccess) e = launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat);
+    if (e == cudaSuccess && c->p.precision == CSC_MIXED_BF16) {
+      e = launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->K * c->J * c->g.Omega);
       c->launches += 1;
     }
-    CSC_CHECK_CUDA(c, launch_sweep(*c, kPrologue, nullptr, c->part[0], vd, nullptr), "coding prologue");
+    if (e == cudaSuccess) e = launch_sweep(*c, kPrologue, nullptr, c->part[0], vd, nullptr);
     c->launches += 4;
-    for (int t = 0; t < iters; ++t) {
+    for (int t = 0; t < iters && e == cudaSuccess; ++t) {
       const int mode = (t == iters - 1) ? kLast : kIter;
       const int br = (mode == kIter) ? bracket_open(c, 0) : -1;
-      CSC_CHECK_CUDA(c, launch_sweep(*c, mode, c->part[t & 1], c->part[(t + 1) & 1], vd, zd), "coding sweep");
+      e = launch_sweep(*c, mode, c->part[t & 1], c->part[(t + 1) & 1], vd, zd);
       bracket_close(c, br);
       c->launches += 1;
+    }
+    return e;
+  };
+  const bool all_dev = !v_host && !z_host && (iters == 0 || (xd == x && dd == d));
+  const void* key[5] = {x, d, v, z, nullptr};
+  const bool same = c->graph && c->graph_iters == iters && key[0] == c->graph_key[0] && key[1] == c->graph_key[1] &&
+                    key[2] == c->graph_key[2] && key[3] == c->graph_key[3];
+  if ((c->p.flags & CSC_FLAG_GRAPH) && all_dev && same) {
+    CSC_CHECK_CUDA(c, cudaGraphLaunch(c->graph, c->stream), "graph launch");
+  } else {
+    CSC_CHECK_CUDA(c, enqueue(), "coding launch");
+    if ((c->p.flags & CSC_FLAG_GRAPH) && all_dev) {
+      // record the sequence for later calls with the same arrays
+      if (c->graph) cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+      if (!c->cap_stream) CSC_CHECK_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream");
+      cudaStream_t user = c->stream;
+      const bool timing = c->timing;
+      const long long launches = c->launches;
+      c->timing = false;
+      c->stream = c->cap_stream;
+      cudaGraph_t gr = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t e2 = (e == cudaSuccess) ? enqueue() : e;
+      cudaError_t e3 = (e == cudaSuccess) ? cudaStreamEndCapture(c->cap_stream, &gr) : e;
+      c->stream = user;
+      c->timing = timing;
+      c->launches = launches;
+      if (e2 == cudaSuccess && e3 == cudaSuccess && gr) {
+        if (cudaGraphInstantiate(&c->graph, gr, 0) == cudaSuccess) {
+          for (int i = 0; i < 4; ++i) c->graph_key[i] = key[i];
+          c->graph_iters = iters;
+        } else {
+          c->graph = nullptr;
+        }
+      }
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
     }
   }
   if (v_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(v, vd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "v copy");
@@ -289,19 +688,30 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   Ctx* c = &ctx->c;
   if (!x || !d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_objective: null argument");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
-  const size_t nz = (size_t)c->N * c->K * c->g.D;
+  const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
+  const size_t nd = (size_t)c->K * c->J * c->S2;
+  const size_t nz = c->uneven ? (size_t)c->U.n_v : (size_t)c->N * c->K * c->g.D;
   const float *xd, *dd, *zd;
   csc_status s;
   if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
-  CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
-  CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
-  CSC_CHECK_CUDA(c, launch_sweep(*c, kObjective, nullptr, c->part[0], nullptr, const_cast<float*>(zd)),
-                 "objective sweep");
-  CSC_CHECK_CUDA(c, launch_objective_final(*c, c->part[0], c->objimg), "objective reduction");
-  c->launches += 4;
+  if (c->uneven) {
+    CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, false), "uneven setup");
+    const UnevenArgs ua = uneven_args(*c, nullptr, c->part[0], nullptr, const_cast<float*>(zd));
+    CSC_CHECK_CUDA(c, launch_sweep_uneven(ua, kObjective, c->G, c->U.nt, uneven_smem_bytes(c->U, c->J, kObjective),
+                                          c->stream), "objective sweep");
+    CSC_CHECK_CUDA(c, launch_objective_final_uneven(uneven_args(*c, c->part[0], nullptr, nullptr, nullptr), c->objimg,
+                                                    c->stream), "objective reduction");
+    c->launches += 2;
+  } else {
+    CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
+    CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
+    CSC_CHECK_CUDA(c, launch_sweep(*c, kObjective, nullptr, c->part[0], nullptr, const_cast<float*>(zd)),
+                   "objective sweep");
+    CSC_CHECK_CUDA(c, launch_objective_final(*c, c->part[0], c->objimg), "objective reduction");
+    c->launches += 4;
+  }
   std::vector<double> img(c->N), l1(c->G);
   CSC_CHECK_CUDA(c, cudaMemcpyAsync(img.data(), c->objimg, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                  "objective copy");
@@ -321,6 +731,7 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
                      int* cg_iters) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn: null context");
   Ctx* c = &ctx->c;
+  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn: not available on an uneven-batch context");
   if (!x || !z || !d || !mu) return fail(c, CSC_ERR_ARG, "csc_learn: null argument");
   if (steps < 0) return fail(c, CSC_ERR_ARG, "csc_learn: steps must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -464,6 +875,7 @@ csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float
                              int every, void* tape) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_unrolled: null context");
   Ctx* c = &ctx->c;
+  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on an uneven-batch context");
   if (!x || !d || !v || !tape || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_unrolled: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: J = 1 only");
@@ -500,6 +912,7 @@ csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const
                              const float* gz, float* gx, float* gd) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_backward: null context");
   Ctx* c = &ctx->c;
+  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on an uneven-batch context");
   if (!x || !d || !tape || !gz || !gx || !gd || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_backward: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: J = 1 only");
@@ -569,6 +982,7 @@ csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const
 csc_status csc_synthesize(csc_ctx* ctx, const float* d, const float* z, float* out) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize: null context");
   Ctx* c = &ctx->c;
+  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: not available on an uneven-batch context");
   if (!d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_synthesize: null argument");
   if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -587,6 +1001,7 @@ csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z,
                                    float* gd) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize_backward: null context");
   Ctx* c = &ctx->c;
+  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: not available on an uneven-batch context");
   if (!d || !z || !gout || !gz || !gd) return fail(c, CSC_ERR_ARG, "csc_synthesize_backward: null argument");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: J = 1 only");
   if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: CSC_FP32 only");

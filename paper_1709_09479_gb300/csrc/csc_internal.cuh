@@ -44,6 +44,52 @@ struct SweepArgs {
 
 struct Ctx;
 
+// ---- batches of images of different sizes (uneven.cu) ------------------------------------------
+struct UClass {            // one image size: run-time FFT plan and offsets of its per-class data
+  GeoRT g;
+  long long tw, dhat, pd, pm;   // element offsets into the twiddle, d_hat, P (diag / J x J) buffers
+};
+struct UImage {
+  int cls, c0, c1;         // size class; first and last CTA whose map range covers the image
+  long long x, v, xh;      // element offsets of its images (x), maps (v, z) and image spectra
+};
+struct UnevenArgs {
+  int N, K, J, G;
+  float beta, rho;
+  int buf_elems, max_omega;
+  const UClass* cls;
+  const UImage* img;
+  const long long* mstart;  // [G+1] map range of each CTA (global map index n*K + k)
+  const long long* slot;    // [G+N] partial-sum slot offset (float2) of (cta, image), indexed by cta + n
+  const float2* tw;
+  const float2* dhat;
+  const float* pdiag;
+  const float2* pmat;
+  const float2* xhat;
+  const float2* part_in;
+  float2* part_out;
+  float* v;
+  float* z;
+  double* l1;
+};
+struct UnevenLayout {
+  std::vector<UClass> cls;
+  std::vector<UImage> img;
+  std::vector<int> cls_H, cls_W;
+  std::vector<long long> mstart, slot;
+  int buf_elems = 0, max_omega = 0, max_tw = 0;
+  long long n_tw = 0, n_dhat = 0, n_pd = 0, n_pm = 0, n_x = 0, n_v = 0, n_xh = 0, n_slot = 0;
+  UClass* d_cls = nullptr;
+  UImage* d_img = nullptr;
+  long long* d_mstart = nullptr;
+  long long* d_slot = nullptr;
+  int nt = 512;             // threads per CTA of the sweep (autotuned)
+  bool tuned = false;
+};
+size_t uneven_smem_bytes(const UnevenLayout& L, int J, int mode);
+cudaError_t launch_sweep_uneven(const UnevenArgs& a, int mode, int G, int nt, size_t smem, cudaStream_t st);
+cudaError_t launch_objective_final_uneven(const UnevenArgs& a, double* out, cudaStream_t st);
+
 // geometry of the (uniform) batch, chosen at csc_init
 struct Geometry {
   int H, W, Wh, Wc, P, Omega, D;
@@ -99,6 +145,13 @@ struct Ctx {
   int* err = nullptr;
   LearnBuffers L;
   BackwardBuffers B;
+  bool uneven = false;
+  UnevenLayout U;
+  // CUDA graph of the last csc_code launch sequence (flag CSC_FLAG_GRAPH)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int graph_iters = -1;
   // staging of host arrays
   float* st_x = nullptr;
   float* st_d = nullptr;

@@ -1,0 +1,112 @@
+"""GPU parity of batched coding over images of different sizes (one persistent launch per ADMM
+iteration, per-size FFT plans, cost-balanced CTA ranges, autotuned launch shape), of the CUDA-graph
+replay of csc_code, and of the uneven objective, against the float64 oracle run image by image."""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import csc_oracle as O
+from tests.gpu_common import REL_TOL, f32, maxrel, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def csc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1709_09479_gb300 import csc as lib
+    return lib
+
+
+def batch(seed, sizes, K, J, s):
+    from paper_1709_09479_gb300 import inputs
+    xs = [f32(inputs.powerlaw_field(seed + i, 1, J, hw)).astype(np.float64) for i, hw in enumerate(sizes)]
+    d = f32(inputs.unit_filters(seed + 99, K, J, (s, s))).astype(np.float64)
+    return xs, d
+
+
+def flat(arrs):
+    import torch
+    return torch.from_numpy(np.concatenate([a.reshape(-1) for a in arrs]).astype(np.float32)).cuda()
+
+
+def split(t, sizes, per):
+    out, off = [], 0
+    a = t.detach().cpu().numpy().astype(np.float64)
+    for (H, W) in sizes:
+        n = per * H * W
+        out.append(a[off:off + n].reshape((1, per, H, W)))
+        off += n
+    return out
+
+
+SIZES = [(64, 64), (48, 40), (100, 100), (24, 32), (64, 64), (128, 128), (40, 48), (96, 70)]
+
+
+@pytest.mark.parametrize("J,K,s,iters", [(1, 5, 5, 5), (1, 40, 3, 3), (3, 4, 3, 4)])
+def test_uneven_coding_matches_oracle_per_image(csc, J, K, s, iters):
+    import torch
+    # three channels need 3x the spectrum space per CTA: sizes up to 64 x 64 fit
+    sizes = SIZES if J == 1 else [(64, 64), (48, 40), (24, 32), (40, 48)]
+    beta, rho = 0.3, 1.0
+    xs, d = batch(200 + K, sizes, K, J, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    with csc.Solver(J=J, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho) as sv:
+        v = torch.zeros(n_v, device="cuda")
+        z = torch.empty_like(v)
+        sv.code(flat(xs), flat([d]), v, z, iters)
+        torch.cuda.synchronize()
+        info = json.loads(sv.describe())
+    assert info["uneven"] and info["autotuned"] and info["size_classes"] == len(set(sizes))
+    for xo, vg, zg in zip(xs, split(v, sizes, K), split(z, sizes, K)):
+        vo, zo = O.code_admm(xo, d, beta, rho, iters)
+        assert rel(vg, vo) <= REL_TOL and maxrel(vg, vo) <= REL_TOL
+        if np.any(zo != 0):
+            assert rel(zg, zo) <= REL_TOL
+
+
+def test_uneven_equals_uniform_and_graph_replay(csc):
+    """A batch of equal sizes through the uneven path gives the uniform path's state; repeated
+    calls under CSC_FLAG_GRAPH (graph replay) give the eager calls' state."""
+    import torch
+    N, K, s, beta, rho = 4, 6, 5, 0.3, 1.0
+    dims = (64, 64)
+    xs, d = batch(300, [dims] * N, K, 1, s)
+    x, dv = flat(xs), flat([d])
+    states = {}
+    for mode in ("uniform", "uneven", "graph"):
+        flags = csc.CSC_FLAG_GRAPH if mode == "graph" else 0
+        kw = dict(dims=dims, n_images=N) if mode != "uneven" else dict(dims_list=[dims] * N)
+        with csc.Solver(J=1, K=K, fs=(s, s), beta=beta, rho=rho, flags=flags, **kw) as sv:
+            v = torch.zeros(N * K * 64 * 64, device="cuda")
+            z = torch.empty_like(v)
+            for _ in range(3):          # the graph is recorded on the first call, replayed after
+                sv.code(x, dv, v, z, 4)
+            torch.cuda.synchronize()
+            if mode == "graph":
+                assert json.loads(sv.describe())["graph_recorded"]
+            states[mode] = v.cpu().numpy().astype(np.float64)
+    assert maxrel(states["uneven"], states["uniform"]) <= 1e-5
+    np.testing.assert_array_equal(states["graph"], states["uniform"])
+    vo = np.concatenate([O.code_admm(xo, d, beta, rho, 12)[0].reshape(-1) for xo in xs])
+    assert rel(states["uniform"], vo) <= REL_TOL
+
+
+def test_uneven_objective_matches_oracle(csc):
+    K, s = 5, 5
+    xs, d = batch(400, SIZES, K, 1, s)
+    rng = np.random.default_rng(1)
+    zs = [f32(np.where(rng.random((1, K) + hw) < 0.05, rng.standard_normal((1, K) + hw), 0.0)).astype(np.float64)
+          for hw in SIZES]
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=SIZES, beta=0.6, rho=1.0) as sv:
+        f = sv.objective(flat(xs), flat([d]), flat(zs))
+    fo = sum(O.objective(xo, d, zo, 0.6) for xo, zo in zip(xs, zs))
+    assert abs(f - fo) <= 1e-5 * fo
+
+
+def test_uneven_rejects_unsupported_sizes_and_calls(csc):
+    with pytest.raises(csc.CscError) as e:
+        csc.Solver(J=1, K=2, fs=(3, 3), dims_list=[(64, 64), (22, 16)], beta=1.0, rho=1.0)
+    assert e.value.status == 2 and "22x16" in str(e.value)
