@@ -236,6 +236,118 @@ def time_to_target(csc, torch, dev):
     return out
 
 
+UNEVEN_SIDES = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
+
+
+def measure_extensions(csc, torch, dev, hbm_peak):
+    """The spec extensions, each on its own workload, device-timed with CUDA events:
+    uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
+    replay), unroll32 (reverse mode through 20 unrolled iterations), mixed128 (the benchmark step in
+    the mixed-precision mode, tensor-core Gram)."""
+    from paper_1709_09479_gb300 import autograd as ag
+    from paper_1709_09479_gb300 import inputs
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # --- uneven256: sides drawn independently from the even 7-smooth sizes in [64, 128] ----------
+    rng = np.random.default_rng(3)
+    sizes = [(int(rng.choice(UNEVEN_SIDES)), int(rng.choice(UNEVEN_SIDES))) for _ in range(256)]
+    K, s, iters = 64, 11, 10
+    xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
+    x = torch.from_numpy(xs.astype(np.float32)).to(dev)
+    d = torch.from_numpy(inputs.unit_filters(30, K, 1, (s, s)).astype(np.float32)).to(dev)
+    npx = sum(H * W for H, W in sizes)
+    nom = sum(H * (W // 2 + 1) for H, W in sizes)
+    v = torch.zeros(K * npx, device=dev)
+    z = torch.empty_like(v)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1, flags=csc.CSC_FLAG_GRAPH) as sv:
+        sv.code(x, d, v, z, iters)       # autotune + record the graph
+        sv.code(x, d, v, z, iters)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(3):
+            sv.code(x, d, v, z, iters)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        desc = json.loads(sv.describe())
+    # per-sweep time from an eager call with event brackets (graph replays are not bracketed)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1) as sv2:
+        sv2.code(x, d, v, z, 3)
+        sv2.timing_read()
+        sv2.timing_enable(True)
+        sv2.code(x, d, v, z, iters)
+        tm = sv2.timing_read()
+    sweep_s = tm["sweep_ms"] / max(tm["sweep_launches"], 1) / 1e3
+    alg = 8.0 * K * npx + 8.0 * nom
+    out["uneven256"] = {"workload": "256 grey images, H and W drawn independently from the even 7-smooth sizes in "
+                                    "[64, 128] (seed 3), K=64 filters 11x11, beta=1, rho=0.1, float32",
+                        "pixels": npx, "size_classes": desc["size_classes"], "launch": desc,
+                        "coding_iters_per_s": iters / (ms / 1e3), "ms_per_call_of_10_iters": ms,
+                        "sweep_us": sweep_s * 1e6, "sweep_hbm_frac": alg / sweep_s / 1e9 / hbm_peak}
+    del x, v, z
+
+    # --- unroll32: batch 32, 128x128, K=64, T=20, checkpoints every 5 --------------------------
+    N, K, H, W, T, every = 32, 64, 128, 128, 20, 5
+    xu = torch.from_numpy(inputs.powerlaw_field(5, N, 1, (H, W)).astype(np.float32)).to(dev).requires_grad_(True)
+    yu = torch.from_numpy(inputs.powerlaw_field(50, N, 1, (H, W)).astype(np.float32)).to(dev)
+    du = torch.from_numpy(inputs.unit_filters(51, K, 1, (s, s)).astype(np.float32)).to(dev).requires_grad_(True)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims=(H, W), n_images=N, beta=1.0, rho=0.1) as sv:
+        def fwd():
+            zT = ag.UnrolledCode.apply(sv, xu, du, T, every)
+            r = ag.Synthesize.apply(sv, du, zT) - yu
+            return (r * r).mean()
+        for _ in range(2):
+            fwd().backward()
+        torch.cuda.synchronize()
+        e0, e1, e2 = ev(), ev(), ev()
+        fms = tms = 0.0
+        for _ in range(3):
+            xu.grad = None
+            du.grad = None
+            e0.record()
+            loss = fwd()
+            e1.record()
+            loss.backward()
+            e2.record()
+            torch.cuda.synchronize()
+            fms += e0.elapsed_time(e1)
+            tms += e0.elapsed_time(e2)
+    out["unroll32"] = {"workload": "batch 32 grey 128x128, K=64 filters 11x11, T=20 unrolled iterations, "
+                                   "checkpoints every 5, loss mean((D z_T - y)^2)",
+                       "forward_ms": fms / 3, "forward_backward_ms": tms / 3, "loss": float(loss.detach())}
+    del xu, yu, du
+
+    # --- mixed128: the benchmark step with bf16 contractions and the tensor-core Gram ---------------
+    w = WORKLOAD
+    x_np, d_np = make_inputs(w)
+    x = torch.from_numpy(x_np).to(dev)
+    d = torch.from_numpy(d_np).to(dev)
+    v = torch.zeros((w["N"], w["K"], w["H"], w["W"]), device=dev)
+    z = torch.empty_like(v)
+    mu = torch.full((w["K"],), 0.5, dtype=torch.float64, device=dev)
+    with csc.Solver(J=1, K=w["K"], fs=(w["s"], w["s"]), dims=(w["H"], w["W"]), n_images=w["N"], beta=w["beta"],
+                    rho=w["rho"], cg_max=w["cg_max"], cg_tol=w["cg_tol"], precision=csc.CSC_MIXED_BF16) as sv:
+        for _ in range(2):
+            sv.code(x, d, v, z, w["n_code"])
+            sv.learn(x, z, d, mu, w["n_learn"])
+        sv.timing_read()
+        sv.timing_enable(True)
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(2):
+            sv.code(x, d, v, z, w["n_code"])
+            sv.learn(x, z, d, mu, w["n_learn"])
+        e1.record()
+        torch.cuda.synchronize()
+        tm = sv.timing_read()
+    out["mixed128"] = {"workload": "the benchmark step in CSC_MIXED_BF16", "ms_per_step": e0.elapsed_time(e1) / 2,
+                       "coding_sweep_us": tm["sweep_ms"] / max(tm["sweep_launches"], 1) * 1e3,
+                       "learn_ms_per_step": tm["learn_ms"] / max(tm["learn_calls"], 1)}
+    return out
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -319,6 +431,8 @@ def run_ours(args):
 
     ttt = time_to_target(csc, torch, dev) if rank == 0 else None
     sv.close()
+    del v, z
+    ext = measure_extensions(csc, torch, dev, peaks()[0]) if (rank == 0 and not args.no_extensions) else None
 
     line = None
     if rank == 0:
@@ -342,6 +456,7 @@ def run_ours(args):
                           "learn_ms_per_step": tm["learn_ms"] / args.steps,
                           "coding_only_iters_per_s": 1e3 / (tm["sweep_ms"] / max(tm["sweep_launches"], 1))},
             "time_to_1e-4": ttt,
+            "extensions": ext,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": cpu_sample},
             "clocks": clk.summary(),
@@ -359,6 +474,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extensions", action="store_true", help="skip the extension workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
