@@ -113,7 +113,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.dots, c->L.bar,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
@@ -430,6 +430,8 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
     tw[g.Wh + g.H + t] = make_float2((float)cos(pi2 * t / g.W), (float)-sin(pi2 * t / g.W));
   if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->dhat, (size_t)p.K * p.J * Om * sizeof(float2)) != cudaSuccess ||
+      (g.ct_id == 1 && p.J == 1 &&
+       cudaMalloc((void**)&c->dhatp, (size_t)p.K * Om * sizeof(float2)) != cudaSuccess) ||
       (p.precision == CSC_MIXED_BF16 &&
        cudaMalloc((void**)&c->dhat16, (size_t)p.K * p.J * Om * sizeof(__nv_bfloat162)) != cudaSuccess) ||
       cudaMalloc((void**)&c->xhat, (size_t)tmp.N * p.J * Om * sizeof(float2)) != cudaSuccess ||

@@ -161,7 +161,10 @@ size_t sweep_smem_bytes(const Geometry& g, int J, int mode) {
 }
 
 cudaError_t launch_fft_maps(const Ctx& c, const float* in, int nmaps, int filter_mode, float2* out) {
-  return geo_ops(c).fft_maps(c, in, nmaps, filter_mode, out);
+  cudaError_t e = geo_ops(c).fft_maps(c, in, nmaps, filter_mode, out);
+  // the fused 128 x 128 sweep reads the filter spectra in its own thread order
+  if (e == cudaSuccess && filter_mode == 1 && out == c.dhat && c.dhatp) e = launch_permute_dhat128(c);
+  return e;
 }
 
 cudaError_t launch_solve_prep(const Ctx& c) {
@@ -188,6 +191,7 @@ cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float
   a.dhat16 = (c.p.precision == CSC_MIXED_BF16 && mode != kObjective) ? c.dhat16 : nullptr;
   const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0) && ((uintptr_t)v_out % 16 == 0);
   a.vec4 = (al && c.g.D % 16 == 0 && c.g.W % 4 == 0) ? 1 : 0;
+  if (fused128_applies(c, a)) return launch_sweep_fused128(c, mode, a);
   return geo_ops(c).sweep(c, mode, a);
 }
 

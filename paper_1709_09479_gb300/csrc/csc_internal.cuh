@@ -135,6 +135,7 @@ struct Ctx {
   // workspace
   float2* tw = nullptr;
   float2* dhat = nullptr;
+  float2* dhatp = nullptr;            // 128 x 128, J = 1: d_hat in the thread order of the fused sweep
   __nv_bfloat162* dhat16 = nullptr;   // mixed precision copy of dhat
   float2* xhat = nullptr;
   float* pdiag = nullptr;
@@ -208,6 +209,10 @@ inline const GeoOps& geo_ops(const Ctx& c);
 
 // launchers (coding.cu)
 cudaError_t launch_fft_maps(const Ctx& c, const float* in, int nmaps, int filter_mode, float2* out);
+// the fused 128 x 128 sweep (sweep128.cu)
+bool fused128_applies(const Ctx& c, const SweepArgs& a);
+cudaError_t launch_sweep_fused128(const Ctx& c, int mode, const SweepArgs& a);
+cudaError_t launch_permute_dhat128(const Ctx& c);
 cudaError_t launch_solve_prep(const Ctx& c);
 cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                          float* z);
