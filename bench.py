@@ -53,7 +53,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "geo_kernels.cuh"):
+    for f in ("fft.cuh", "sweep128.cu"):
         h.update(open(os.path.join(ROOT, "paper_1709_09479_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -61,7 +61,7 @@ def kernel_source_hash():
 def profiled_traffic():
     """dram bytes per launch of the coding sweep from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "k_sweep_128x128_N100_K100.md")
+    p = os.path.join(ROOT, "profiles", "k_sweep_f128_iterate_N100_K100.md")
     if not os.path.exists(p):
         return None
     src, traffic = None, None
@@ -448,7 +448,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
                     "d2h_bytes_per_step": int(d_np.nbytes)},
             "gpu_launches": int(tm["kernel_launches"]),
-            "roofline": {"bound": "hbm", "kernel": "k_sweep<128x128, iterate>", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": "k_sweep_f128<iterate>", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                          "avg_launch_us": sweep_avg_s * 1e6, "launches": tm["sweep_launches"]},

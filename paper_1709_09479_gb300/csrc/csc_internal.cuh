@@ -102,12 +102,13 @@ struct LearnBuffers {
   float2* zhat = nullptr;   // [N][K][Omega]
   float2* gram = nullptr;   // [npairs][Omega], pairs k <= k'
   float* lags = nullptr;    // [K][K][L*L]
+  float2* chat = nullptr;   // [NF][K(K+1)/2] lag spectra / (La Lb), NF = La * fw
+  float2* yhat = nullptr;   // [K][J][NF] half spectrum of the CG product
   float* b = nullptr;       // [K][J][S2]
   float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
   double* mu = nullptr;     // [K]
   float* minv = nullptr;    // [K][S2][S2] block-Jacobi inverses (S2 <= kMaxBlockJacobi)
-  float* dots = nullptr;    // [G][4][kMaxJ] CG partial dot products
-  unsigned* bar = nullptr;  // grid barrier {count, generation}
+  unsigned long long* slots = nullptr;   // [2][G][4 kMaxJ] CG exchange words (sum | epoch)
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
   void* zt = nullptr;       // mixed precision: [Omega][K][2 npad] bf16 code spectra for the tensor-core Gram
@@ -235,6 +236,7 @@ cudaError_t launch_learn_rhs(const Ctx& c);
 cudaError_t launch_learn_gram(const Ctx& c);
 cudaError_t launch_learn_lags(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
+size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem);
 cudaError_t launch_learn_gram_tc(const Ctx& c, void* zt_buf, int* dev_err);
 size_t tc_gram_smem_bytes(int N);
 cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n);

@@ -92,261 +92,461 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// bounded grid barrier for the cooperative CG launch
-// ---------------------------------------------------------------------------------------------
-constexpr long long kSpinLimit = 2000000000LL;   // ~1 s of SM clocks
+// bound of every spin-wait of the CG launch (~1 s of SM clocks)
+constexpr long long kSpinLimit = 2000000000LL;
 
-__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
-  __shared__ int s_ok;
+// ---------------------------------------------------------------------------------------------
+// lag spectra: the normal-equation product in the Fourier domain of the (2fh-1) x (2fw-1) lag grid
+//
+// For taps q, q' of an fh x fw filter the lags q - q' stay inside the La x Lb = (2fh-1) x (2fw-1)
+// window, so the block Toeplitz product [S Z^T Z S^T p]_k(q) = sum_k' sum_q' C_kk'(q - q') p_k'(q')
+// equals the circular correlation on the La x Lb grid, cropped to the taps:
+//     y_k = crop( F^-1( sum_k' C_hat_kk' . F(p_k') ) ),   C_hat_kk' = F(C_kk') on the lag grid.
+// C is real, so only the half spectrum w2 < fw is kept (NF = La * fw bins); C_hat_k'k = conj C_hat_kk'.
+// chat[f][pair(k, k')] holds C_hat_kk'(f) / (La Lb) for k <= k' (pair_index order), f = w1 * fw + w2.
+// ---------------------------------------------------------------------------------------------
+struct LagSpecArgs {
+  int K, fh, fw, La, Lb, NF;
+  const float* lags;   // [K][K][La][Lb], lag (ta, tb) at ((ta + fh - 1) * Lb + tb + fw - 1)
+  float2* chat;        // [NF][K(K+1)/2]
+};
+
+__device__ __forceinline__ float2 unit_root(int m, int L) {   // exp(-2 pi i m / L), 0 <= m < L
+  float s, c;
+  sincospif(2.0f * (float)m / (float)L, &s, &c);
+  return make_float2(c, -s);
+}
+
+constexpr int kLagSpecNT = 256;
+
+__global__ void __launch_bounds__(kLagSpecNT) k_lag_spectra(LagSpecArgs a) {
+  extern __shared__ float2 ls2[];
+  const int La = a.La, Lb = a.Lb, fw = a.fw, fh = a.fh, NF = a.NF, K = a.K;
+  float2* R = ls2;                          // [La][fw] row transforms
+  float2* twa = R + La * fw;                // [La]
+  float2* twb = twa + La;                   // [Lb]
+  float* C = reinterpret_cast<float*>(twb + Lb);   // [La][Lb]
+  // pair (k <= kp) of this CTA
+  int k = 0, rem = blockIdx.x;
+  while (rem >= K - k) { rem -= K - k; ++k; }
+  const int kp = k + rem;
+  for (int i = threadIdx.x; i < La; i += kLagSpecNT) twa[i] = unit_root(i, La);
+  for (int i = threadIdx.x; i < Lb; i += kLagSpecNT) twb[i] = unit_root(i, Lb);
+  const float* src = a.lags + ((size_t)k * K + kp) * La * Lb;
+  for (int i = threadIdx.x; i < La * Lb; i += kLagSpecNT) C[i] = src[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    int ok = 1;
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      // one polling thread per CTA, no sleep between polls: sleeping added ~20 us per barrier
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*(volatile int*)err) { ok = 0; break; }
-        if (clock64() - t0 > kSpinLimit) { atomicExch(err, (int)CSC_ERR_TIMEOUT); ok = 0; break; }
-      }
+  // over tb: R[ta][w2] = sum_tb C[ta][tb] exp(-2 pi i w2 (tb - fw + 1) / Lb)
+  for (int e = threadIdx.x; e < La * fw; e += kLagSpecNT) {
+    const int ta = e / fw, w2 = e - ta * fw;
+    float2 s = make_float2(0.f, 0.f);
+    for (int tb = 0; tb < Lb; ++tb) {
+      const int m = ((w2 * (tb - fw + 1)) % Lb + Lb) % Lb;
+      const float cv = C[ta * Lb + tb];
+      s.x = fmaf(cv, twb[m].x, s.x);
+      s.y = fmaf(cv, twb[m].y, s.y);
     }
-    __threadfence();
-    s_ok = ok;
+    R[e] = s;
   }
   __syncthreads();
-  return s_ok != 0;
+  // over ta, scaled by 1/(La Lb)
+  const float sc = 1.0f / (float)(La * Lb);
+  for (int f = threadIdx.x; f < NF; f += kLagSpecNT) {
+    const int w1 = f / fw, w2 = f - w1 * fw;
+    float2 s = make_float2(0.f, 0.f);
+    for (int ta = 0; ta < La; ++ta) {
+      const int m = ((w1 * (ta - fh + 1)) % La + La) % La;
+      s = cfma(R[ta * fw + w2], twa[m], s);
+    }
+    s = cscale(s, sc);
+    a.chat[(size_t)f * (K * (K + 1) / 2) + pair_index(k, kp, K)] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
 // persistent CG over all learning steps
+//
+// One cooperative launch; CTA b owns the lag-grid bins [f0, f1) for the product and the filters
+// k = b, b + G, ... for everything else. An iteration has two grid-wide exchanges:
+//   A: after the product at its bins (y_hat to global) a CTA publishes its partial p . A p;
+//   B: after x, r and z = M^-1 r of its filters (z to global) it publishes partial r . z, r . r.
+// Exchanges carry no atomics: each CTA writes its partial sums into its own slot as 64-bit words
+// (float bits | epoch << 32) after a fence, and every CTA's warp 0 polls all slots until they
+// carry the current epoch, then sums them in CTA order (so every CTA gets the same totals).
+// Slots alternate between two banks by epoch parity, so a CTA that is one exchange ahead never
+// overwrites words a slower CTA is still reading.
 // ---------------------------------------------------------------------------------------------
+constexpr int kSlotWords = 4 * kMaxJ;
+
 struct CgArgs {
-  int K, J, fh, fw, S2, La, Lb, G, steps, cg_max;
+  int K, J, fh, fw, S2, La, Lb, NF, G, steps, cg_max;
   double tol2, mu_floor;
-  const float* lags;  // [K][K][La*Lb]
-  const float* b;     // [K][J][S2]
-  float* x;           // [K][J][S2]  d (in/out)
-  float* r;           // [K][J][S2]
-  float* zv;          // [K][J][S2]  preconditioned residual
-  float* Ap;          // [K][J][S2]
-  double* mu;         // [K]
-  float* minv;        // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
-  float* dots;        // [G][4][kMaxJ] per-CTA partial dot products
-  unsigned* bar;
-  int* iters;         // [steps]
+  const float* lags;   // [K][K][La*Lb]: the zero lag of C_kk (activity) and the preconditioner blocks
+  const float2* chat;  // [NF][K(K+1)/2] lag spectra / (La Lb), pairs k <= k'
+  int chat_smem;       // the CTA's bins of chat are staged in shared memory
+  float2* yhat;        // [K][J][NF] half spectrum of the product being formed
+  const float* b;      // [K][J][S2]
+  float* x;            // [K][J][S2]  d (in/out)
+  float* zv;           // [K][J][S2]  preconditioned residual
+  double* mu;          // [K]
+  float* minv;         // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
+  unsigned long long* slots;   // [2][G][kSlotWords], zeroed before the launch
+  int* iters;          // [steps]
   int* err;
 };
 
-__device__ __forceinline__ uint32_t cg_smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// copy n floats of read-only global data into shared memory with asynchronous copies
-template <int NT>
-__device__ __forceinline__ void stage_async(float* dst, const float* src, int n) {
-  for (int i = threadIdx.x; i < n; i += NT)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(cg_smem_addr(dst + i)), "l"(src + i) : "memory");
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
+// shared-memory layout of the CG kernel (float2 arrays first, then floats)
+struct CgSmem {
+  size_t ew, phat, red, yh, sc, twa, twb, cch, pp, own, mloc, total_floats;
+  int nb, nown;
+};
+CSC_HD CgSmem cg_smem_layout(int K, int J, int S2, int NF, int fh, int fw, int La, int Lb, int NT, int G,
+                             bool minv, bool chat_smem) {
+  CgSmem L;
+  L.nb = (NF + G - 1) / G;        // bins per CTA (at most)
+  L.nown = (K + G - 1) / G;       // filters per CTA (at most)
+  const int red_items = L.nb * K < NT ? NT : L.nb * K;
+  size_t o = 0;   // in floats
+  L.ew = o;   o += 2 * (size_t)L.nb * S2;
+  L.phat = o; o += 2 * (size_t)L.nb * K * J;
+  L.red = o;  o += 2 * (size_t)red_items * J;
+  L.yh = o;   o += 2 * (size_t)J * NF;
+  L.sc = o;   o += 2 * (size_t)J * fw * fh;
+  L.twa = o;  o += 2 * (size_t)La;
+  L.twb = o;  o += 2 * (size_t)Lb;
+  L.cch = o;  o += chat_smem ? 2 * (size_t)L.nb * (K * (K + 1) / 2) : 0;
+  L.pp = o;   o += (size_t)K * J * S2;
+  L.own = o;  o += 4 * (size_t)L.nown * J * S2;   // x, r, b, z of the CTA's filters
+  L.mloc = o; o += minv ? (size_t)S2 * S2 + S2 : 0;
+  L.total_floats = o;
+  return L;
 }
 
 // dst[i] = src[i] + beta(i) * dst[i] over the whole vector, src written by other CTAs (read
-// through L2), loads batched 8 per thread
+// through L2); up to 24 loads per thread in flight before their use
 template <int NT>
 __device__ __forceinline__ void axpy_from_l2(float* dst, const float* src, int n, int JS, int S2,
-                                             const float* beta, bool overwrite) {
-  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * NT) {
-    float v[8];
+                                             const double* beta, bool overwrite) {
+  constexpr int U = 24;
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * NT) {
+    float v[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (i0 + u * NT < n) ? __ldcg(src + i0 + u * NT) : 0.f;
+    for (int u = 0; u < U; ++u) v[u] = (i0 + u * NT < n) ? __ldcg(src + i0 + u * NT) : 0.f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = i0 + u * NT;
-      if (i < n) dst[i] = overwrite ? v[u] : fmaf(beta[(i % JS) / S2], dst[i], v[u]);
+      if (i < n) dst[i] = overwrite ? v[u] : fmaf((float)beta[(i % JS) / S2], dst[i], v[u]);
     }
   }
-  __syncthreads();
-}
-
-// y_k = (S Z^T Z S^T) p for filter k (+ 2 mu_k p_k), p in shared memory for all filters. The lag
-// blocks C_{k,k'} (La x LB each, contiguous in k') are staged through shared memory in chunks of
-// ngroups filters; thread (qa, grp) accumulates output row qa against filter k' = chunk + grp.
-template <int SI, int NT>
-__device__ void matvec_k(const CgArgs& a, int k, const float* pp, float* red, float* cbuf, float two_mu,
-                         float* out) {
-  const int fh = a.fh, J = a.J, K = a.K, La = a.La, S2 = a.S2;
-  constexpr int LB = 2 * SI - 1;
-  const int LL = La * LB;
-  const int ngroups = NT / fh;
-  const int t = threadIdx.x;
-  const bool worker = t < ngroups * fh;
-  const int qa = worker ? t % fh : 0, grp = worker ? t / fh : 0;
-  float acc[kMaxJ][SI];
-#pragma unroll
-  for (int j = 0; j < kMaxJ; ++j)
-#pragma unroll
-    for (int q = 0; q < SI; ++q) acc[j][q] = 0.f;
-  for (int kp0 = 0; kp0 < K; kp0 += ngroups) {
-    const int nk = min(ngroups, K - kp0);
-    stage_async<NT>(cbuf, a.lags + ((size_t)k * K + kp0) * LL, nk * LL);
-    if (worker && grp < nk) {
-      const int kp = kp0 + grp;
-      const float* C = cbuf + (size_t)grp * LL;
-      for (int qa2 = 0; qa2 < fh; ++qa2) {
-        const float* crow = C + (qa - qa2 + fh - 1) * LB;
-        float c[LB];
-#pragma unroll
-        for (int i = 0; i < LB; ++i) c[i] = crow[i];
-#pragma unroll
-        for (int j = 0; j < kMaxJ; ++j) {
-          if (j < J) {
-            const float* prow = pp + ((size_t)kp * J + j) * S2 + qa2 * SI;
-            float pv[SI];
-#pragma unroll
-            for (int i = 0; i < SI; ++i) pv[i] = prow[i];
-#pragma unroll
-            for (int qb = 0; qb < SI; ++qb)
-#pragma unroll
-              for (int qb2 = 0; qb2 < SI; ++qb2) acc[j][qb] = fmaf(c[qb - qb2 + SI - 1], pv[qb2], acc[j][qb]);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (worker) {
-#pragma unroll
-    for (int j = 0; j < kMaxJ; ++j)
-      if (j < J)
-#pragma unroll
-        for (int qb = 0; qb < SI; ++qb) red[((grp * fh + qa) * J + j) * SI + qb] = acc[j][qb];
-  }
-  __syncthreads();
-  for (int o = t; o < J * S2; o += NT) {
-    const int j = o / S2, q = o - j * S2, qa_ = q / SI, qb = q - qa_ * SI;
-    float sum = 0.f;
-    for (int gidx = 0; gidx < ngroups; ++gidx) sum += red[((gidx * fh + qa_) * J + j) * SI + qb];
-    out[((size_t)k * J + j) * S2 + q] = sum + two_mu * pp[((size_t)k * J + j) * S2 + q];
-  }
-  __syncthreads();
 }
 
 // Sums vals[0..n) over the block in float32 (the device's float64 rate is a few operations per
-// clock per SM, so per-thread float64 work is kept out of the CG loop); warp partials go to
-// scratch [NT/32][4 kMaxJ], warp 0 finishes, every thread gets the sums back in vals.
+// clock per SM, so per-thread float64 work is kept out of the CG loop); the totals are valid in
+// thread 0 only. scratch: [NT/32][kSlotWords] floats, free on entry.
 template <int NT>
-__device__ void block_sum(float* vals, int n, float* scratch) {
+__device__ __forceinline__ void block_reduce_to0(float* vals, int n, float* scratch) {
   for (int i = 0; i < n; ++i) {
     float v = vals[i];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) scratch[(threadIdx.x >> 5) * 4 * kMaxJ + i] = v;
+    if ((threadIdx.x & 31) == 0) scratch[(threadIdx.x >> 5) * kSlotWords + i] = v;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
     for (int i = 0; i < n; ++i) {
-      float v = (threadIdx.x < NT / 32) ? scratch[threadIdx.x * 4 * kMaxJ + i] : 0.f;
+      float v = (threadIdx.x < NT / 32) ? scratch[threadIdx.x * kSlotWords + i] : 0.f;
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (threadIdx.x == 0) scratch[i] = v;
+      vals[i] = v;
     }
   }
-  __syncthreads();
-  for (int i = 0; i < n; ++i) vals[i] = scratch[i];
-  __syncthreads();
 }
 
-// sum over the G CTAs of slot entries dots[gb][base + j], j < n (written by other CTAs: read
-// through L2), in a fixed order by warp 0 in float64, into bcast (shared memory)
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0: make the CTA's earlier global writes visible, then publish vals[0..n) with epoch ep.
+// The caller has synchronised the block since those writes.
+__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, int n, unsigned ep) {
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  unsigned long long* s = slots + ((size_t)(ep & 1) * G + blockIdx.x) * kSlotWords;
+  // at least one word: an exchange without sums still carries the epoch
+  for (int i = 0; i < (n > 0 ? n : 1); ++i)
+    st_volatile_u64(s + i, ((unsigned long long)ep << 32) | __float_as_uint(n > 0 ? vals[i] : 0.f));
+}
+
+// every thread: totals[i] = sum over CTAs (in CTA order) of word i of epoch ep, i < n. The G * n
+// words are polled by all threads of the block at once (a few independent loads each, repeated
+// until they carry the epoch), parked in vals ([G][n] floats of shared memory) and summed by warp 0
+// in a fixed order. false on a device error or when the wait runs out (error flag set).
 template <int NT>
-__device__ void grid_dots(const float* dots, int G, int base, int n, double* bcast) {
+__device__ bool gather(const unsigned long long* slots, int G, int n, unsigned ep, double* totals, float* vals,
+                       int* err) {
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  const int nw = n > 0 ? n : 1;
+  const unsigned long long* base = slots + (size_t)(ep & 1) * G * kSlotWords;
+  constexpr int kPer = 4;   // words per thread: G * nw <= kPer * NT
+  int idx[kPer];
+  bool ready[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    idx[u] = threadIdx.x + u * NT;
+    ready[u] = idx[u] >= G * nw;
+  }
+  const long long t0 = clock64();
+  bool fail = false;
+  while (true) {
+    unsigned long long w[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+      if (!ready[u]) w[u] = ld_volatile_u64(base + (size_t)(idx[u] / nw) * kSlotWords + idx[u] % nw);
+    bool all = true;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      if (!ready[u]) {
+        if ((unsigned)(w[u] >> 32) == ep) {
+          ready[u] = true;
+          vals[idx[u]] = __uint_as_float((unsigned)w[u]);
+        } else {
+          all = false;
+        }
+      }
+    }
+    if (all) break;
+    if (*(volatile int*)err) { fail = true; break; }
+    if (clock64() - t0 > kSpinLimit) { atomicExch(err, (int)CSC_ERR_TIMEOUT); fail = true; break; }
+  }
+  if (fail) s_fail = 1;
+  __threadfence();
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    for (int j = 0; j < n; ++j) {
-      double s = 0.0;
-      for (int gb = lane; gb < G; gb += 32) s += (double)__ldcg(dots + (size_t)gb * 4 * kMaxJ + base + j);
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if (lane == 0) bcast[j] = s;
+    for (int i = 0; i < n; ++i) {
+      double v = 0.0;
+      for (int b = lane; b < G; b += 32) v += (double)vals[b * nw + i];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) totals[i] = v;
     }
   }
   __syncthreads();
+  return s_fail == 0;
 }
 
-// z_k = M_k^{-1} r_k for one filter, and the partial dot r_k . z_k. M_k is the filter's own block
-// of the normal-equation matrix (C_kk Toeplitz + 2 mu_k I, inverted at the start of the call), held
-// in shared memory (mloc) when the CTA owns this one filter, else read from a.minv; without
-// block inverses, the diagonal. rk is shared-memory scratch of J * S2 floats.
+// Lag-grid half spectrum of S Z^T Z S^T p at this CTA's bins, p (all filters) in shared memory:
+// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yhat (C_hat_kk' = conj C_hat_k'k for k > k'),
+// and the partial Parseval sums of p . S Z^T Z S^T p over these bins (weight 2 for w2 > 0) into
+// part[j]. ew[i][q] holds the tap twiddles of the CTA's bin f0 + i, cch the CTA's bins of chat (or
+// null: read from global). Ends synchronised.
 template <int NT>
-__device__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc, float* rk,
-                               float* part) {
-  const int S2 = a.S2, JS = a.J * S2;
-  __syncthreads();   // r_k complete
-  for (int o = threadIdx.x; o < JS; o += NT) rk[o] = a.r[(size_t)k * JS + o];
+__device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, const float2* ew, float2* phat,
+                             float2* red, const float2* cch, float* part) {
+  const int K = a.K, J = a.J, S2 = a.S2, fw = a.fw, NF = a.NF;
+  const int KJ = K * J;
+  const int np = K * (K + 1) / 2;
+  // p_hat of every filter at the CTA's bins (four partial sums per item)
+  for (int e = threadIdx.x; e < nbc * KJ; e += NT) {
+    const int bi = e / KJ, i = e - bi * KJ;
+    const float* pr = pp + (size_t)i * S2;
+    const float2* w = ew + (size_t)bi * S2;
+    float2 s4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s4[u] = make_float2(0.f, 0.f);
+    int q = 0;
+    for (; q + 4 <= S2; q += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float pv = pr[q + u];
+        s4[u].x = fmaf(pv, w[q + u].x, s4[u].x);
+        s4[u].y = fmaf(pv, w[q + u].y, s4[u].y);
+      }
+    }
+    for (; q < S2; ++q) {
+      const float pv = pr[q];
+      s4[0].x = fmaf(pv, w[q].x, s4[0].x);
+      s4[0].y = fmaf(pv, w[q].y, s4[0].y);
+    }
+    phat[e] = cadd(cadd(s4[0], s4[1]), cadd(s4[2], s4[3]));
+  }
   __syncthreads();
+  // partial products over k' ranges: item (bin, part, k)
+  const int PS = (nbc * K < NT) ? NT / (nbc * K) : 1;
+  const int kchunk = (K + PS - 1) / PS;
+  for (int e = threadIdx.x; e < nbc * PS * K; e += NT) {
+    const int k = e % K, rest = e / K, pi = rest % PS, bi = rest / PS;
+    const float2* cf = cch ? cch + (size_t)bi * np : a.chat + (size_t)(f0 + bi) * np;
+    const float2* ph = phat + (size_t)bi * KJ;
+    const int kp0 = pi * kchunk, kp1 = min(K, kp0 + kchunk);
+    float2 acc[kMaxJ];
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int kp = kp0; kp < kp1; ++kp) {
+      float2 c;
+      if (kp >= k) {
+        c = cf[pair_index(k, kp, K)];
+      } else {
+        c = cf[pair_index(kp, k, K)];
+        c.y = -c.y;
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j)
+        if (j < J) acc[j] = cfma(c, ph[kp * J + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j)
+      if (j < J) red[(size_t)e * J + j] = acc[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nbc * KJ; e += NT) {
+    const int bi = e / KJ, i = e - bi * KJ, k = i / J, j = i - k * J;
+    const int f = f0 + bi, w2 = f % fw;
+    float2 s = make_float2(0.f, 0.f);
+    for (int pi = 0; pi < PS; ++pi) s = cadd(s, red[(((size_t)bi * PS + pi) * K + k) * J + j]);
+    a.yhat[(size_t)i * NF + f] = s;
+    const float2 p = phat[e];
+    part[j] = fmaf(w2 == 0 ? 1.f : 2.f, p.x * s.x + p.y * s.y, part[j]);
+  }
+}
+
+// y_k = crop(F^-1 y_hat_k) on the taps, for one filter (y_hat written by other CTAs before the
+// last exchange: read through L2). Thread t gets y at taps o = t, t + NT, ... in out[o].
+template <int NT>
+__device__ void product_taps(const CgArgs& a, int k, float2* yh, float2* sc, const float2* twa, const float2* twb,
+                             float* out) {
+  const int J = a.J, NF = a.NF, fw = a.fw, fh = a.fh, La = a.La, Lb = a.Lb, S2 = a.S2;
+  for (int i = threadIdx.x; i < J * NF; i += NT) yh[i] = __ldcg(a.yhat + (size_t)k * J * NF + i);
+  __syncthreads();
+  // over w1: sc[j][w2][qa] = sum_w1 y_hat[j][w1][w2] exp(+2 pi i w1 qa / La)
+  for (int e = threadIdx.x; e < J * fw * fh; e += NT) {
+    const int j = e / (fw * fh), rem = e - j * fw * fh, w2 = rem / fh, qa = rem - w2 * fh;
+    float2 s = make_float2(0.f, 0.f);
+    for (int w1 = 0; w1 < La; ++w1) s = cfmac(twa[(w1 * qa) % La], yh[(size_t)j * NF + w1 * fw + w2], s);
+    sc[e] = s;
+  }
+  __syncthreads();
+  // over w2: y[j][qa][qb] = sum_w2 wt(w2) Re(sc[j][w2][qa] exp(+2 pi i w2 qb / Lb))
+  for (int o = threadIdx.x; o < J * S2; o += NT) {
+    const int j = o / S2, q = o - j * S2, qa = q / fw, qb = q - qa * fw;
+    float s = 0.f;
+    for (int w2 = 0; w2 < fw; ++w2) {
+      const float2 v = sc[((size_t)j * fw + w2) * fh + qa];
+      const float2 e = twb[(w2 * qb) % Lb];   // exp(-i .); Re(v conj(e))
+      s = fmaf(w2 == 0 ? 1.f : 2.f, v.x * e.x + v.y * e.y, s);
+    }
+    out[o] = s;
+  }
+}
+
+// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zv; the
+// partial r . z into part[kMaxJ + j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the
+// CTA owns one filter, else global), else the diagonal. Four lanes of a warp share one tap.
+template <int NT>
+__device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc,
+                                               const float* r, float* zo, float* part) {
+  const int S2 = a.S2, JS = a.J * S2;
   const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
-  for (int o = threadIdx.x; o < JS; o += NT) {
+  const int sub = threadIdx.x & 3;
+  for (int o0 = threadIdx.x >> 2; o0 < ((JS + 7) / 8) * 8; o0 += NT / 4) {
+    const int o = o0 < JS ? o0 : JS - 1;
     const int j = o / S2, q = o - j * S2;
     float zv = 0.f;
     if (act) {
       if (m) {
-        // M_k^{-1} is symmetric: column q, consecutive threads on consecutive addresses
-        const float* r = rk + (size_t)j * S2;
+        // M_k^{-1} is symmetric: column q
+        const float* rj = r + (size_t)j * S2;
         float sacc = 0.f;
-#pragma unroll 4
-        for (int q2 = 0; q2 < S2; ++q2) sacc = fmaf(m[(size_t)q2 * S2 + q], r[q2], sacc);
+        for (int q2 = sub; q2 < S2; q2 += 4) sacc = fmaf(m[(size_t)q2 * S2 + q], rj[q2], sacc);
         zv = sacc;
-      } else {
-        zv = rk[o] * sjac;
+      } else if (sub == 0) {
+        zv = r[o] * sjac;
       }
     }
-    a.zv[(size_t)k * JS + o] = zv;
-    part[1 * kMaxJ + j] = fmaf(rk[o], zv, part[1 * kMaxJ + j]);
+    zv += __shfl_xor_sync(0xffffffffu, zv, 1);
+    zv += __shfl_xor_sync(0xffffffffu, zv, 2);
+    if (sub == 0 && o0 < JS) {
+      zo[o] = zv;
+      a.zv[(size_t)k * JS + o] = zv;
+      part[kMaxJ + j] = fmaf(r[o], zv, part[kMaxJ + j]);
+    }
   }
 }
 
-template <int SI, int NT>
+template <int NT>
 __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   extern __shared__ float smf[];
-  __shared__ double scratch[(NT / 32) * 4 * kMaxJ];
-  __shared__ double bc[4 * kMaxJ];
-  // scalars of the iteration, kept by thread 0 (float64) and broadcast through shared memory
-  __shared__ double s_rz[kMaxJ], s_rr[kMaxJ], s_bb[kMaxJ];
-  __shared__ float s_alpha[kMaxJ], s_beta[kMaxJ], s_twomu, s_jac;
-  __shared__ int s_done[kMaxJ], s_all;
+  __shared__ float scratch[(NT / 32) * kSlotWords];
+  __shared__ double tot[kSlotWords];
+  __shared__ float gvals[4 * NT];   // gathered words [G][n]
+  __shared__ float s_twomu[8], s_jac[8];
+  __shared__ int s_act[8];
   const int K = a.K, J = a.J, S2 = a.S2, G = a.G;
   const int JS = J * S2;
-  const int ngroups = NT / a.fh;
-  float* pp = smf;                                            // [K][J][S2]
-  float* red = pp + (size_t)K * JS;                           // [ngroups][fh][J][SI]
-  float* cbuf = red + (size_t)ngroups * a.fh * J * SI;        // [ngroups][La][Lb]
-  float* rk = cbuf + (size_t)ngroups * a.La * a.Lb;           // [J][S2]
-  float* mloc = rk + JS;                                      // [S2][S2] (+ [S2] during the inversion)
-  const bool own_one = (G == K) && a.minv;                    // one filter per CTA: keep its inverse
-  const int La = a.La, ctr = (a.fh - 1) * a.Lb + (a.fw - 1);   // lag tau = 0
+  const CgSmem Ls = cg_smem_layout(K, J, S2, a.NF, a.fh, a.fw, a.La, a.Lb, NT, G, a.minv != nullptr, a.chat_smem);
+  float2* ew = reinterpret_cast<float2*>(smf + Ls.ew);
+  float2* phat = reinterpret_cast<float2*>(smf + Ls.phat);
+  float2* red = reinterpret_cast<float2*>(smf + Ls.red);
+  float2* yh = reinterpret_cast<float2*>(smf + Ls.yh);
+  float2* sc = reinterpret_cast<float2*>(smf + Ls.sc);
+  float2* twa = reinterpret_cast<float2*>(smf + Ls.twa);
+  float2* twb = reinterpret_cast<float2*>(smf + Ls.twb);
+  float2* cch = a.chat_smem ? reinterpret_cast<float2*>(smf + Ls.cch) : nullptr;   // [nb][K(K+1)/2]
+  float* pp = smf + Ls.pp;                       // [K][J][S2] the whole search direction
+  float* ox = smf + Ls.own;                      // [nown][J][S2] x, r, b, z of the CTA's filters
+  float* orr = ox + (size_t)Ls.nown * JS;
+  float* ob = orr + (size_t)Ls.nown * JS;
+  float* oz = ob + (size_t)Ls.nown * JS;
+  float* mloc = smf + Ls.mloc;                   // [S2][S2] (+ [S2] during the inversion)
+  const int nown = (blockIdx.x < K) ? (K - 1 - blockIdx.x) / G + 1 : 0;
+  const bool own_one = (G >= K) && a.minv;       // at most one filter per CTA: keep its inverse
+  const int La = a.La, Lb = a.Lb, ctr = (a.fh - 1) * Lb + (a.fw - 1);   // lag tau = 0
+  const int f0 = (int)((long long)blockIdx.x * a.NF / G), f1 = (int)((long long)(blockIdx.x + 1) * a.NF / G);
+  const int nbc = f1 - f0;
+  unsigned ep = 0;
 
-  auto active = [&](int k) { return a.lags[((size_t)k * K + k) * La * a.Lb + ctr] > 0.f; };
-  auto precond = [&](int k) {   // called by one thread
-    const double m = (double)a.lags[((size_t)k * K + k) * La * a.Lb + ctr] + 2.0 * a.mu[k];
-    return (float)(1.0 / m);
-  };
+  for (int i = threadIdx.x; i < La; i += NT) twa[i] = unit_root(i, La);
+  for (int i = threadIdx.x; i < Lb; i += NT) twb[i] = unit_root(i, Lb);
+  __syncthreads();
+  // tap twiddles of the CTA's bins: exp(-2 pi i (w1 qa / La + w2 qb / Lb))
+  for (int e = threadIdx.x; e < nbc * S2; e += NT) {
+    const int bi = e / S2, q = e - bi * S2, f = f0 + bi;
+    const int w1 = f / a.fw, w2 = f - w1 * a.fw, qa = q / a.fw, qb = q - qa * a.fw;
+    ew[e] = cmul(twa[(w1 * qa) % La], twb[(w2 * qb) % Lb]);
+  }
+  // the CTA's bins of the lag spectra
+  if (cch) {
+    const size_t n = (size_t)nbc * (K * (K + 1) / 2);
+    const float2* src = a.chat + (size_t)f0 * (K * (K + 1) / 2);
+    for (size_t i = threadIdx.x; i < n; i += NT) cch[i] = __ldg(src + i);
+  }
+  // the CTA's filters: activity, x, b
+  if (threadIdx.x < nown) {
+    const int k = blockIdx.x + threadIdx.x * G;
+    s_act[threadIdx.x] = a.lags[((size_t)k * K + k) * La * Lb + ctr] > 0.f;
+  }
+  for (int i = 0; i < nown; ++i) {
+    const int k = blockIdx.x + i * G;
+    for (int o = threadIdx.x; o < JS; o += NT) {
+      ox[(size_t)i * JS + o] = a.x[(size_t)k * JS + o];
+      ob[(size_t)i * JS + o] = a.b[(size_t)k * JS + o];
+    }
+  }
+  __syncthreads();
 
   // ---- block-Jacobi preconditioner for this call: inverse of (C_kk Toeplitz + 2 mu_k I) -------
   // (the mu at entry; the preconditioner need not track the later mu updates exactly)
   if (a.minv) {
     float* A = mloc;                    // [S2][S2]
     float* colv = A + (size_t)S2 * S2;  // [S2]
-    const int fh = a.fh, fw = a.fw, Lb = a.Lb;
-    for (int k = blockIdx.x; k < K; k += G) {
-      const bool act = active(k);
-      if (threadIdx.x == 0) s_twomu = (float)(2.0 * a.mu[k]);
-      __syncthreads();
-      const float tm = s_twomu;
+    const int fh = a.fh, fw = a.fw;
+    for (int i = 0; i < nown; ++i) {
+      const int k = blockIdx.x + i * G;
+      const bool act = s_act[i];
+      const float tm = (float)(2.0 * a.mu[k]);
       const float* C = a.lags + ((size_t)k * K + k) * La * Lb;
       for (int e = threadIdx.x; e < S2 * S2; e += NT) {
         const int q = e / S2, q2 = e - q * S2;
@@ -357,16 +557,16 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       __syncthreads();
       // in-place Gauss-Jordan inversion (symmetric positive definite: no pivoting)
       for (int pv = 0; pv < S2; ++pv) {
-        for (int i = threadIdx.x; i < S2; i += NT) colv[i] = A[(size_t)i * S2 + pv];
+        for (int r = threadIdx.x; r < S2; r += NT) colv[r] = A[(size_t)r * S2 + pv];
         __syncthreads();
         const float inv = 1.f / colv[pv];
         for (int j = threadIdx.x; j < S2; j += NT)
           if (j != pv) A[(size_t)pv * S2 + j] *= inv;
         __syncthreads();
-        for (int i = threadIdx.x >> 5; i < S2; i += NT / 32) {
-          if (i == pv) continue;
-          const float ci = colv[i];
-          float* row = A + (size_t)i * S2;
+        for (int r = threadIdx.x >> 5; r < S2; r += NT / 32) {
+          if (r == pv) continue;
+          const float ci = colv[r];
+          float* row = A + (size_t)r * S2;
           const float* prow = A + (size_t)pv * S2;
           for (int j = threadIdx.x & 31; j < S2; j += 32) row[j] = (j != pv) ? fmaf(-ci, prow[j], row[j]) : -ci * inv;
         }
@@ -381,143 +581,187 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     }
   }
   const float* mk = own_one ? mloc : nullptr;
-  float* fscratch = reinterpret_cast<float*>(scratch);
 
   for (int step = 0; step < a.steps; ++step) {
+    if (threadIdx.x < nown) {
+      const int k = blockIdx.x + threadIdx.x * G;
+      const double m2 = 2.0 * a.mu[k];
+      s_twomu[threadIdx.x] = (float)m2;
+      s_jac[threadIdx.x] = s_act[threadIdx.x] ? (float)(1.0 / ((double)a.lags[((size_t)k * K + k) * La * Lb + ctr] + m2)) : 0.f;
+    }
     // ---- r = b - A x, z = M^{-1} r, p = z -----------------------------------------------
     axpy_from_l2<NT>(pp, a.x, K * JS, JS, S2, nullptr, true);
-    float part[4 * kMaxJ];
-    for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
-    for (int k = blockIdx.x; k < K; k += G) {
-      const bool act = active(k);
-      if (threadIdx.x == 0) {
-        s_twomu = (float)(2.0 * a.mu[k]);
-        s_jac = act ? precond(k) : 0.f;
-      }
-      __syncthreads();
-      matvec_k<SI, NT>(a, k, pp, red, cbuf, s_twomu, a.Ap);
+    __syncthreads();
+    float part[kSlotWords];
+#pragma unroll
+    for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
+    product_bins<NT>(a, f0, nbc, pp, ew, phat, red, cch, part);
+    __syncthreads();
+    publish(a.slots, G, part, 0, ++ep);   // no sums: an exchange of y_hat only
+    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
+#pragma unroll
+    for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
+    for (int i = 0; i < nown; ++i) {
+      const int k = blockIdx.x + i * G;
+      float* r = orr + (size_t)i * JS;
+      product_taps<NT>(a, k, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
+      const bool act = s_act[i];
       for (int o = threadIdx.x; o < JS; o += NT) {
-        const size_t idx = (size_t)k * JS + o;
         const int j = o / S2;
-        const float bv = a.b[idx];
-        const float rv = act ? bv - a.Ap[idx] : 0.f;
-        a.r[idx] = rv;
+        const float bv = ob[(size_t)i * JS + o];
+        const float rv = act ? bv - fmaf(s_twomu[i], ox[(size_t)i * JS + o], r[o]) : 0.f;
+        r[o] = rv;
         part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
         if (act) part[3 * kMaxJ + j] = fmaf(bv, bv, part[3 * kMaxJ + j]);
       }
-      precondition_k<NT>(a, k, act, s_jac, mk, rk, part);
+      __syncthreads();
+      precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, part);
     }
-    block_sum<NT>(part, 4 * kMaxJ, fscratch);
-    if (threadIdx.x == 0)
-      for (int i = 0; i < 4 * kMaxJ; ++i) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + i] = part[i];
-    if (!grid_sync(a.bar, G, a.err)) return;
-    grid_dots<NT>(a.dots, G, kMaxJ, 3 * kMaxJ, bc);
-    if (threadIdx.x == 0)
+    {
+      float w3[kSlotWords];
+#pragma unroll
       for (int j = 0; j < kMaxJ; ++j) {
-        s_rz[j] = bc[j];
-        s_rr[j] = bc[kMaxJ + j];
-        s_bb[j] = bc[2 * kMaxJ + j];
-        s_done[j] = (j >= J);
+        w3[j] = part[kMaxJ + j];
+        w3[kMaxJ + j] = part[2 * kMaxJ + j];
+        w3[2 * kMaxJ + j] = part[3 * kMaxJ + j];
       }
+      float packed[kSlotWords];
+      for (int j = 0; j < J; ++j) {
+        packed[j] = w3[j];
+        packed[J + j] = w3[kMaxJ + j];
+        packed[2 * J + j] = w3[2 * kMaxJ + j];
+      }
+      block_reduce_to0<NT>(packed, 3 * J, scratch);
+      __syncthreads();
+      publish(a.slots, G, packed, 3 * J, ++ep);
+    }
+    if (!gather<NT>(a.slots, G, 3 * J, ep, tot, gvals, a.err)) return;
+    double rz[kMaxJ], rr[kMaxJ], bb[kMaxJ];
+    bool done[kMaxJ];
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      rz[j] = j < J ? tot[j] : 0.0;
+      rr[j] = j < J ? tot[J + j] : 0.0;
+      bb[j] = j < J ? tot[2 * J + j] : 0.0;
+      done[j] = (j >= J);
+    }
     axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, nullptr, true);
+    __syncthreads();
     int it = 0;
     for (; it < a.cg_max; ++it) {
-      if (threadIdx.x == 0) {
-        int all = 1;
-        for (int j = 0; j < J; ++j) {
-          s_done[j] = s_done[j] || !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
-          all = all && s_done[j];
-        }
-        s_all = all;
+      bool all = true;
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j) {
+        done[j] = done[j] || !(rr[j] > a.tol2 * bb[j]) || !(rz[j] > 0.0);
+        all = all && done[j];
       }
-      __syncthreads();
-      if (s_all) break;
-      // ---- Ap, p.Ap --------------------------------------------------------------------
-      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
-      for (int k = blockIdx.x; k < K; k += G) {
-        const bool act = active(k);
-        if (threadIdx.x == 0) s_twomu = (float)(2.0 * a.mu[k]);
-        __syncthreads();
-        matvec_k<SI, NT>(a, k, pp, red, cbuf, s_twomu, a.Ap);
+      if (all) break;   // the same totals on every thread of every CTA
+      // ---- A p at this CTA's bins, p . A p (exchange A) -----------------------------------
+#pragma unroll
+      for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
+      product_bins<NT>(a, f0, nbc, pp, ew, phat, red, cch, part);
+      for (int i = 0; i < nown; ++i) {
+        if (!s_act[i]) continue;
+        const int k = blockIdx.x + i * G;
         for (int o = threadIdx.x; o < JS; o += NT) {
-          const size_t idx = (size_t)k * JS + o;
-          const int j = o / S2;
-          if (act) part[j] = fmaf(pp[idx], a.Ap[idx], part[j]);
+          const float pv = pp[(size_t)k * JS + o];
+          part[o / S2] = fmaf(s_twomu[i] * pv, pv, part[o / S2]);
         }
       }
-      block_sum<NT>(part, kMaxJ, fscratch);
-      if (threadIdx.x == 0)
-        for (int j = 0; j < kMaxJ; ++j) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + j] = part[j];
-      if (!grid_sync(a.bar, G, a.err)) return;
-      grid_dots<NT>(a.dots, G, 0, kMaxJ, bc);
-      if (threadIdx.x == 0)
-        for (int j = 0; j < kMaxJ; ++j) {
-          const double pap = bc[j];
-          s_alpha[j] = (j < J && !s_done[j] && pap > 0.0) ? (float)(s_rz[j] / pap) : 0.f;
-        }
+      block_reduce_to0<NT>(part, J, scratch);
       __syncthreads();
-      // ---- x += alpha p, r -= alpha Ap, z = M^{-1} r ---------------------------------------
-      for (int i = 0; i < 4 * kMaxJ; ++i) part[i] = 0.f;
-      for (int k = blockIdx.x; k < K; k += G) {
-        if (!active(k)) continue;
-        if (threadIdx.x == 0) s_jac = precond(k);
-        __syncthreads();
+      publish(a.slots, G, part, J, ++ep);
+      if (!gather<NT>(a.slots, G, J, ep, tot, gvals, a.err)) return;
+      float alpha[kMaxJ];
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j) {
+        const double pap = j < J ? tot[j] : 0.0;
+        alpha[j] = (j < J && !done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
+      }
+      // ---- x += alpha p, r -= alpha A p, z = M^{-1} r (exchange B) ---------------------------
+#pragma unroll
+      for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
+      for (int i = 0; i < nown; ++i) {
+        if (!s_act[i]) continue;
+        const int k = blockIdx.x + i * G;
+        float* r = orr + (size_t)i * JS;
+        float* yk = oz + (size_t)i * JS;   // A p of the filter, then z
+        product_taps<NT>(a, k, yh, sc, twa, twb, yk);
         for (int o = threadIdx.x; o < JS; o += NT) {
-          const size_t idx = (size_t)k * JS + o;
           const int j = o / S2;
-          const float al = s_alpha[j];
-          a.x[idx] = fmaf(al, pp[idx], a.x[idx]);
-          const float rv = fmaf(-al, a.Ap[idx], a.r[idx]);
-          a.r[idx] = rv;
+          const float al = alpha[j];
+          const float pv = pp[(size_t)k * JS + o];
+          const float apv = fmaf(s_twomu[i], pv, yk[o]);
+          ox[(size_t)i * JS + o] = fmaf(al, pv, ox[(size_t)i * JS + o]);
+          const float rv = fmaf(-al, apv, r[o]);
+          r[o] = rv;
           part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
         }
-        precondition_k<NT>(a, k, true, s_jac, mk, rk, part);
+        __syncthreads();
+        precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, part);
       }
-      block_sum<NT>(part, 4 * kMaxJ, fscratch);
-      if (threadIdx.x == 0)
-        for (int i = kMaxJ; i < 3 * kMaxJ; ++i) a.dots[(size_t)blockIdx.x * 4 * kMaxJ + i] = part[i];
-      if (!grid_sync(a.bar, G, a.err)) return;
-      grid_dots<NT>(a.dots, G, kMaxJ, 2 * kMaxJ, bc);
-      if (threadIdx.x == 0) {
-        for (int j = 0; j < kMaxJ; ++j) {
-          if (j < J && !s_done[j]) {
-            s_beta[j] = s_rz[j] > 0.0 ? (float)(bc[j] / s_rz[j]) : 0.f;
-            s_rz[j] = bc[j];
-            s_rr[j] = bc[kMaxJ + j];
-          } else {
-            s_beta[j] = 0.f;
-          }
+      {
+        float packed[kSlotWords];
+        for (int j = 0; j < J; ++j) {
+          packed[j] = part[kMaxJ + j];
+          packed[J + j] = part[2 * kMaxJ + j];
+        }
+        block_reduce_to0<NT>(packed, 2 * J, scratch);
+        __syncthreads();
+        publish(a.slots, G, packed, 2 * J, ++ep);
+      }
+      if (!gather<NT>(a.slots, G, 2 * J, ep, tot, gvals, a.err)) return;
+      double beta[kMaxJ];
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j) {
+        if (j < J && !done[j]) {
+          beta[j] = rz[j] > 0.0 ? tot[j] / rz[j] : 0.0;
+          rz[j] = tot[j];
+          rr[j] = tot[J + j];
+        } else {
+          beta[j] = 0.0;
         }
       }
-      __syncthreads();
       // every CTA keeps the whole search direction: p = z + beta p
-      axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, s_beta, false);
+      axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, beta, false);
+      __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.iters) a.iters[step] = it;
-    // ---- mu_k <- max(mu_k ||d_k||, floor) for active filters (Eq. mu_update) ------------------
-    for (int k = blockIdx.x; k < K; k += G) {
-      float sq[4 * kMaxJ];
-      for (int i = 0; i < 4 * kMaxJ; ++i) sq[i] = 0.f;
+    // ---- mu_k <- max(mu_k ||d_k||, floor) for active filters (Eq. mu_update); x to global -------
+    for (int i = 0; i < nown; ++i) {
+      const int k = blockIdx.x + i * G;
+      float sq[kSlotWords];
+#pragma unroll
+      for (int u = 0; u < kSlotWords; ++u) sq[u] = 0.f;
       for (int o = threadIdx.x; o < JS; o += NT) {
-        const float xv = a.x[(size_t)k * JS + o];
+        const float xv = ox[(size_t)i * JS + o];
         sq[0] = fmaf(xv, xv, sq[0]);
+        a.x[(size_t)k * JS + o] = xv;
       }
-      block_sum<NT>(sq, 1, fscratch);
-      if (threadIdx.x == 0 && active(k)) a.mu[k] = fmax(a.mu[k] * sqrt((double)sq[0]), a.mu_floor);
+      block_reduce_to0<NT>(sq, 1, scratch);
+      if (threadIdx.x == 0 && s_act[i]) a.mu[k] = fmax(a.mu[k] * sqrt((double)sq[0]), a.mu_floor);
+      __syncthreads();
     }
-    if (!grid_sync(a.bar, G, a.err)) return;
+    __syncthreads();
+    publish(a.slots, G, part, 0, ++ep);   // x complete everywhere before the next step
+    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
   }
   // ---- d_k <- d_k / max(1, ||d_k||) ---------------------------------------------------------
-  for (int k = blockIdx.x; k < K; k += G) {
-    float sq[4 * kMaxJ];
-    for (int i = 0; i < 4 * kMaxJ; ++i) sq[i] = 0.f;
+  for (int i = 0; i < nown; ++i) {
+    const int k = blockIdx.x + i * G;
+    float sq[kSlotWords];
+#pragma unroll
+    for (int u = 0; u < kSlotWords; ++u) sq[u] = 0.f;
     for (int o = threadIdx.x; o < JS; o += NT) {
-      const float xv = a.x[(size_t)k * JS + o];
+      const float xv = ox[(size_t)i * JS + o];
       sq[0] = fmaf(xv, xv, sq[0]);
     }
-    block_sum<NT>(sq, 1, fscratch);
-    const float sc = 1.0f / fmaxf(1.0f, sqrtf(sq[0]));
-    for (int o = threadIdx.x; o < JS; o += NT) a.x[(size_t)k * JS + o] *= sc;
+    block_reduce_to0<NT>(sq, 1, scratch);
+    if (threadIdx.x == 0) scratch[0] = 1.0f / fmaxf(1.0f, sqrtf(sq[0]));
+    __syncthreads();
+    const float sc2 = scratch[0];
+    for (int o = threadIdx.x; o < JS; o += NT) a.x[(size_t)k * JS + o] = ox[(size_t)i * JS + o] * sc2;
+    __syncthreads();
   }
 }
 
@@ -534,50 +778,61 @@ cudaError_t launch_learn_gram(const Ctx& c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_learn_lags(const Ctx& c) { return geo_ops(c).lags(c); }
+cudaError_t launch_learn_lags(const Ctx& c) {
+  cudaError_t e = geo_ops(c).lags(c);
+  if (e != cudaSuccess) return e;
+  const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
+  LagSpecArgs a{c.K, c.fh, c.fw, La, Lb, La * c.fw, c.L.lags, c.L.chat};
+  const size_t smem = (size_t)(La * c.fw + La + Lb) * sizeof(float2) + (size_t)La * Lb * sizeof(float);
+  const int npairs = c.K * (c.K + 1) / 2;
+  k_lag_spectra<<<npairs, kLagSpecNT, smem, c.stream>>>(a);
+  c.launches += 1;
+  return cudaGetLastError();
+}
 
-template <int SI>
-static cudaError_t launch_cg_si(const Ctx& c, CgArgs a) {
+int learn_cg_ctas(const Ctx& c) {
+  const int La = 2 * c.fh - 1;
+  return std::max(1, std::min(c.nsm, std::max(c.K, La * c.fw)));
+}
+
+size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem) {
+  const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
+  // at least as many bins and filters per CTA as any launch of this context will have
+  const int G = std::max(1, std::min(c.nsm > 0 ? c.nsm : 1, std::max(c.K, La * c.fw)));
+  return cg_smem_layout(c.K, c.J, c.S2, La * c.fw, c.fh, c.fw, La, Lb, kNT, G, minv, chat_smem).total_floats *
+         sizeof(float);
+}
+
+cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   constexpr int NT = kNT;
-  auto kern = k_learn_cg<SI, NT>;
-  const int ngroups = NT / c.fh;
-  size_t smem = ((size_t)c.K * c.J * c.S2 + (size_t)ngroups * c.fh * c.J * SI +
-                 (size_t)ngroups * (2 * c.fh - 1) * (2 * SI - 1) + (size_t)c.J * c.S2 +
-                 (a.minv ? (size_t)c.S2 * c.S2 + c.S2 : 0)) * sizeof(float);
+  CgArgs a;
+  a.K = c.K; a.J = c.J; a.fh = c.fh; a.fw = c.fw; a.S2 = c.S2;
+  a.La = 2 * c.fh - 1; a.Lb = 2 * c.fw - 1; a.NF = a.La * c.fw;
+  a.G = 0; a.steps = steps; a.cg_max = c.p.cg_max;
+  a.tol2 = c.p.cg_tol * c.p.cg_tol; a.mu_floor = kMuFloor;
+  const size_t nvec = (size_t)c.K * c.J * c.S2;
+  a.lags = c.L.lags; a.chat = c.L.chat; a.yhat = c.L.yhat; a.b = c.L.b; a.x = d;
+  a.zv = c.L.vec + nvec;
+  a.mu = c.L.mu; a.minv = c.L.minv; a.slots = c.L.slots; a.iters = c.L.iters; a.err = dev_err;
+  // the grid: one CTA per SM at most (every CTA must be resident: the exchanges wait on all)
+  a.G = learn_cg_ctas(c);
+  cudaError_t e = cudaMemsetAsync(c.L.slots, 0, (size_t)2 * a.G * kSlotWords * sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  auto kern = k_learn_cg<NT>;
+  // the CTA's bins of the lag spectra stay in shared memory when they fit
+  a.chat_smem = learn_cg_smem_bytes(c, a.minv != nullptr, true) <= kSmemLimit ? 1 : 0;
+  const size_t smem = learn_cg_smem_bytes(c, a.minv != nullptr, a.chat_smem != 0);
   if (smem > kSmemLimit) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  a.G = std::min(c.K, per_sm * c.nsm);
+  if ((c.K + a.G - 1) / a.G > 8) return cudaErrorInvalidValue;   // filters per CTA
+  if (a.G * 3 * c.J > 4 * NT) return cudaErrorInvalidValue;       // gathered words per exchange
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(a.G), dim3(NT), args, smem, c.stream);
-}
-
-cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
-  CgArgs a;
-  a.K = c.K; a.J = c.J; a.fh = c.fh; a.fw = c.fw; a.S2 = c.S2;
-  a.La = 2 * c.fh - 1; a.Lb = 2 * c.fw - 1; a.G = 0; a.steps = steps; a.cg_max = c.p.cg_max;
-  a.tol2 = c.p.cg_tol * c.p.cg_tol; a.mu_floor = kMuFloor;
-  const size_t nvec = (size_t)c.K * c.J * c.S2;
-  a.lags = c.L.lags; a.b = c.L.b; a.x = d;
-  a.r = c.L.vec; a.zv = c.L.vec + nvec; a.Ap = c.L.vec + 2 * nvec;
-  a.mu = c.L.mu; a.minv = c.L.minv; a.dots = c.L.dots; a.bar = c.L.bar; a.iters = c.L.iters; a.err = dev_err;
-  cudaError_t e = cudaMemsetAsync(c.L.bar, 0, 2 * sizeof(unsigned), c.stream);
-  if (e != cudaSuccess) return e;
-  switch (c.fw) {
-    case 1: return launch_cg_si<1>(c, a);
-    case 3: return launch_cg_si<3>(c, a);
-    case 5: return launch_cg_si<5>(c, a);
-    case 7: return launch_cg_si<7>(c, a);
-    case 9: return launch_cg_si<9>(c, a);
-    case 11: return launch_cg_si<11>(c, a);
-    case 13: return launch_cg_si<13>(c, a);
-    case 15: return launch_cg_si<15>(c, a);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace csc
