@@ -234,29 +234,39 @@ __device__ __forceinline__ void axpy_from_l2(float* dst, const float* src, int n
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * NT;
-      if (i < n) dst[i] = overwrite ? v[u] : fmaf((float)beta[(i % JS) / S2], dst[i], v[u]);
+      if (i < n) dst[i] = overwrite ? v[u] : fmaf((float)beta[JS == S2 ? 0 : (i % JS) / S2], dst[i], v[u]);
     }
   }
 }
 
-// Sums vals[0..n) over the block in float32 (the device's float64 rate is a few operations per
+// Sums vals[0..N) over the block in float32 (the device's float64 rate is a few operations per
 // clock per SM, so per-thread float64 work is kept out of the CG loop); the totals are valid in
 // thread 0 only. scratch: [NT/32][kSlotWords] floats, free on entry.
-template <int NT>
-__device__ __forceinline__ void block_reduce_to0(float* vals, int n, float* scratch) {
-  for (int i = 0; i < n; ++i) {
+template <int NT, int N>
+__device__ __forceinline__ void block_reduce_to0(float (&vals)[N], float* scratch) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
     float v = vals[i];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) scratch[(threadIdx.x >> 5) * kSlotWords + i] = v;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    for (int i = 0; i < n; ++i) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
       float v = (threadIdx.x < NT / 32) ? scratch[threadIdx.x * kSlotWords + i] : 0.f;
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       vals[i] = v;
     }
   }
+}
+
+// vals[idx] += v for a run-time idx with every slot kept in registers
+template <int N>
+__device__ __forceinline__ void add_at(float (&vals)[N], int idx, float v) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i == idx) vals[i] += v;
 }
 
 __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
@@ -268,15 +278,16 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return v;
 }
 
-// thread 0: make the CTA's earlier global writes visible, then publish vals[0..n) with epoch ep.
-// The caller has synchronised the block since those writes.
-__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, int n, unsigned ep) {
+// thread 0: make the CTA's earlier global writes visible, then publish vals[0..N) with epoch ep.
+// The caller has synchronised the block since those writes. N == 0: one word without a sum.
+template <int N>
+__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, unsigned ep) {
   if (threadIdx.x != 0) return;
-  __threadfence();
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release: the CTA's stores before the words
   unsigned long long* s = slots + ((size_t)(ep & 1) * G + blockIdx.x) * kSlotWords;
-  // at least one word: an exchange without sums still carries the epoch
-  for (int i = 0; i < (n > 0 ? n : 1); ++i)
-    st_volatile_u64(s + i, ((unsigned long long)ep << 32) | __float_as_uint(n > 0 ? vals[i] : 0.f));
+#pragma unroll
+  for (int i = 0; i < (N > 0 ? N : 1); ++i)
+    st_volatile_u64(s + i, ((unsigned long long)ep << 32) | __float_as_uint(N > 0 ? vals[i] : 0.f));
 }
 
 // every thread: totals[i] = sum over CTAs (in CTA order) of word i of epoch ep, i < n. The G * n
@@ -322,7 +333,7 @@ __device__ bool gather(const unsigned long long* slots, int G, int n, unsigned e
     if (clock64() - t0 > kSpinLimit) { atomicExch(err, (int)CSC_ERR_TIMEOUT); fail = true; break; }
   }
   if (fail) s_fail = 1;
-  __threadfence();
+  if (threadIdx.x < G * nw) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire: words before data
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -341,39 +352,40 @@ __device__ bool gather(const unsigned long long* slots, int G, int n, unsigned e
 // y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yhat (C_hat_kk' = conj C_hat_k'k for k > k'),
 // and the partial Parseval sums of p . S Z^T Z S^T p over these bins (weight 2 for w2 > 0) into
 // part[j]. ew[i][q] holds the tap twiddles of the CTA's bin f0 + i, cch the CTA's bins of chat (or
-// null: read from global). Ends synchronised.
-template <int NT>
+// null: read from global), both in pair_index order. Does not end synchronised.
+template <int NT, int JT>
 __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, const float2* ew, float2* phat,
-                             float2* red, const float2* cch, float* part) {
-  const int K = a.K, J = a.J, S2 = a.S2, fw = a.fw, NF = a.NF;
+                             float2* red, const float2* cch, float (&part)[JT]) {
+  constexpr int J = JT;
+  const int K = a.K, S2 = a.S2, fw = a.fw, NF = a.NF;
   const int KJ = K * J;
   const int np = K * (K + 1) / 2;
-  // p_hat of every filter at the CTA's bins (four partial sums per item)
-  for (int e = threadIdx.x; e < nbc * KJ; e += NT) {
-    const int bi = e / KJ, i = e - bi * KJ;
-    const float* pr = pp + (size_t)i * S2;
-    const float2* w = ew + (size_t)bi * S2;
-    float2 s4[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s4[u] = make_float2(0.f, 0.f);
-    int q = 0;
-    for (; q + 4 <= S2; q += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float pv = pr[q + u];
-        s4[u].x = fmaf(pv, w[q + u].x, s4[u].x);
-        s4[u].y = fmaf(pv, w[q + u].y, s4[u].y);
+  // p_hat of every filter at the CTA's bins: four lanes per (bin, filter, channel)
+  {
+    const int sub = threadIdx.x & 3;
+    const int nit = nbc * KJ;
+    for (int e0 = threadIdx.x >> 2; e0 < ((nit + 7) / 8) * 8; e0 += NT / 4) {
+      const int e = e0 < nit ? e0 : nit - 1;
+      const int bi = e / KJ, i = e - bi * KJ;
+      const float* pr = pp + (size_t)i * S2;
+      const float2* w = ew + (size_t)bi * S2;
+      float2 s = make_float2(0.f, 0.f);
+      for (int q = sub; q < S2; q += 4) {
+        const float pv = pr[q];
+        s.x = fmaf(pv, w[q].x, s.x);
+        s.y = fmaf(pv, w[q].y, s.y);
       }
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
+      if (sub == 0 && e0 < nit) phat[e] = s;
     }
-    for (; q < S2; ++q) {
-      const float pv = pr[q];
-      s4[0].x = fmaf(pv, w[q].x, s4[0].x);
-      s4[0].y = fmaf(pv, w[q].y, s4[0].y);
-    }
-    phat[e] = cadd(cadd(s4[0], s4[1]), cadd(s4[2], s4[3]));
   }
   __syncthreads();
-  // partial products over k' ranges: item (bin, part, k)
+  // partial products over k' ranges: item (bin, part, k). In pair_index order the entries
+  // C_hat_k'k (k' < k, column k of the upper triangle) are K - k' - 1 apart, C_hat_kk' (k' >= k,
+  // row k) are contiguous.
   const int PS = (nbc * K < NT) ? NT / (nbc * K) : 1;
   const int kchunk = (K + PS - 1) / PS;
   for (int e = threadIdx.x; e < nbc * PS * K; e += NT) {
@@ -384,18 +396,29 @@ __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, 
     float2 acc[kMaxJ];
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j) acc[j] = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int kp = kp0; kp < kp1; ++kp) {
-      float2 c;
-      if (kp >= k) {
-        c = cf[pair_index(k, kp, K)];
-      } else {
-        c = cf[pair_index(kp, k, K)];
-        c.y = -c.y;
-      }
+    // k' < k: conj of the stored C_hat_k'k
+    const int ce = min(kp1, k);
+    if (kp0 < ce) {
+      int idx = kp0 * K - kp0 * (kp0 - 1) / 2 + (k - kp0);
+      for (int kp = kp0; kp < ce; ++kp) {
+        const float2 c = cf[idx];
+        idx += K - kp - 1;
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j)
-        if (j < J) acc[j] = cfma(c, ph[kp * J + j], acc[j]);
+        for (int j = 0; j < kMaxJ; ++j)
+          if (j < J) acc[j] = cfmac(c, ph[kp * J + j], acc[j]);
+      }
+    }
+    // k' >= k: the stored C_hat_kk'
+    const int rs = max(kp0, k);
+    if (rs < kp1) {
+      const float2* row = cf + (k * K - k * (k - 1) / 2 - k);
+#pragma unroll 4
+      for (int kp = rs; kp < kp1; ++kp) {
+        const float2 c = row[kp];
+#pragma unroll
+        for (int j = 0; j < kMaxJ; ++j)
+          if (j < J) acc[j] = cfma(c, ph[kp * J + j], acc[j]);
+      }
     }
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j)
@@ -409,7 +432,7 @@ __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, 
     for (int pi = 0; pi < PS; ++pi) s = cadd(s, red[(((size_t)bi * PS + pi) * K + k) * J + j]);
     a.yhat[(size_t)i * NF + f] = s;
     const float2 p = phat[e];
-    part[j] = fmaf(w2 == 0 ? 1.f : 2.f, p.x * s.x + p.y * s.y, part[j]);
+    add_at(part, j, (w2 == 0 ? 1.f : 2.f) * (p.x * s.x + p.y * s.y));
   }
 }
 
@@ -421,33 +444,51 @@ __device__ void product_taps(const CgArgs& a, int k, float2* yh, float2* sc, con
   const int J = a.J, NF = a.NF, fw = a.fw, fh = a.fh, La = a.La, Lb = a.Lb, S2 = a.S2;
   for (int i = threadIdx.x; i < J * NF; i += NT) yh[i] = __ldcg(a.yhat + (size_t)k * J * NF + i);
   __syncthreads();
-  // over w1: sc[j][w2][qa] = sum_w1 y_hat[j][w1][w2] exp(+2 pi i w1 qa / La)
-  for (int e = threadIdx.x; e < J * fw * fh; e += NT) {
-    const int j = e / (fw * fh), rem = e - j * fw * fh, w2 = rem / fh, qa = rem - w2 * fh;
-    float2 s = make_float2(0.f, 0.f);
-    for (int w1 = 0; w1 < La; ++w1) s = cfmac(twa[(w1 * qa) % La], yh[(size_t)j * NF + w1 * fw + w2], s);
-    sc[e] = s;
+  // over w1: sc[j][w2][qa] = sum_w1 y_hat[j][w1][w2] exp(+2 pi i w1 qa / La), four lanes per item
+  {
+    const int sub = threadIdx.x & 3;
+    const int nit = J * fw * fh;
+    for (int e0 = threadIdx.x >> 2; e0 < ((nit + 7) / 8) * 8; e0 += NT / 4) {
+      const int e = e0 < nit ? e0 : nit - 1;
+      const int j = e / (fw * fh), rem = e - j * fw * fh, w2 = rem / fh, qa = rem - w2 * fh;
+      float2 s = make_float2(0.f, 0.f);
+      int m = (sub * qa) % La;
+      const int step = (4 * qa) % La;
+      for (int w1 = sub; w1 < La; w1 += 4) {
+        s = cfmac(twa[m], yh[(size_t)j * NF + w1 * fw + w2], s);
+        m += step;
+        if (m >= La) m -= La;
+      }
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
+      if (sub == 0 && e0 < nit) sc[e] = s;
+    }
   }
   __syncthreads();
   // over w2: y[j][qa][qb] = sum_w2 wt(w2) Re(sc[j][w2][qa] exp(+2 pi i w2 qb / Lb))
   for (int o = threadIdx.x; o < J * S2; o += NT) {
     const int j = o / S2, q = o - j * S2, qa = q / fw, qb = q - qa * fw;
     float s = 0.f;
+    int m = 0;
     for (int w2 = 0; w2 < fw; ++w2) {
       const float2 v = sc[((size_t)j * fw + w2) * fh + qa];
-      const float2 e = twb[(w2 * qb) % Lb];   // exp(-i .); Re(v conj(e))
+      const float2 e = twb[m];   // exp(-i .); Re(v conj(e))
       s = fmaf(w2 == 0 ? 1.f : 2.f, v.x * e.x + v.y * e.y, s);
+      m += qb;
+      if (m >= Lb) m -= Lb;
     }
     out[o] = s;
   }
 }
 
 // z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zv; the
-// partial r . z into part[kMaxJ + j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the
-// CTA owns one filter, else global), else the diagonal. Four lanes of a warp share one tap.
-template <int NT>
+// partial r . z into part[j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the CTA owns
+// one filter, else global), else the diagonal. Four lanes of a warp share one tap.
+template <int NT, int N>
 __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc,
-                                               const float* r, float* zo, float* part) {
+                                               const float* r, float* zo, float (&part)[N]) {
   const int S2 = a.S2, JS = a.J * S2;
   const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
   const int sub = threadIdx.x & 3;
@@ -471,12 +512,12 @@ __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act,
     if (sub == 0 && o0 < JS) {
       zo[o] = zv;
       a.zv[(size_t)k * JS + o] = zv;
-      part[kMaxJ + j] = fmaf(r[o], zv, part[kMaxJ + j]);
+      add_at(part, j, r[o] * zv);
     }
   }
 }
 
-template <int NT>
+template <int NT, int JT>
 __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   extern __shared__ float smf[];
   __shared__ float scratch[(NT / 32) * kSlotWords];
@@ -484,7 +525,8 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   __shared__ float gvals[4 * NT];   // gathered words [G][n]
   __shared__ float s_twomu[8], s_jac[8];
   __shared__ int s_act[8];
-  const int K = a.K, J = a.J, S2 = a.S2, G = a.G;
+  constexpr int J = JT;
+  const int K = a.K, S2 = a.S2, G = a.G;
   const int JS = J * S2;
   const CgSmem Ls = cg_smem_layout(K, J, S2, a.NF, a.fh, a.fw, a.La, a.Lb, NT, G, a.minv != nullptr, a.chat_smem);
   float2* ew = reinterpret_cast<float2*>(smf + Ls.ew);
@@ -592,58 +634,47 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     // ---- r = b - A x, z = M^{-1} r, p = z -----------------------------------------------
     axpy_from_l2<NT>(pp, a.x, K * JS, JS, S2, nullptr, true);
     __syncthreads();
-    float part[kSlotWords];
-#pragma unroll
-    for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
-    product_bins<NT>(a, f0, nbc, pp, ew, phat, red, cch, part);
-    __syncthreads();
-    publish(a.slots, G, part, 0, ++ep);   // no sums: an exchange of y_hat only
-    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
-#pragma unroll
-    for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
-    for (int i = 0; i < nown; ++i) {
-      const int k = blockIdx.x + i * G;
-      float* r = orr + (size_t)i * JS;
-      product_taps<NT>(a, k, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
-      const bool act = s_act[i];
-      for (int o = threadIdx.x; o < JS; o += NT) {
-        const int j = o / S2;
-        const float bv = ob[(size_t)i * JS + o];
-        const float rv = act ? bv - fmaf(s_twomu[i], ox[(size_t)i * JS + o], r[o]) : 0.f;
-        r[o] = rv;
-        part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
-        if (act) part[3 * kMaxJ + j] = fmaf(bv, bv, part[3 * kMaxJ + j]);
-      }
-      __syncthreads();
-      precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, part);
-    }
     {
-      float w3[kSlotWords];
+      float pa[J];
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        w3[j] = part[kMaxJ + j];
-        w3[kMaxJ + j] = part[2 * kMaxJ + j];
-        w3[2 * kMaxJ + j] = part[3 * kMaxJ + j];
+      for (int j = 0; j < J; ++j) pa[j] = 0.f;
+      product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
+    }
+    __syncthreads();
+    publish<0>(a.slots, G, nullptr, ++ep);   // no sums: an exchange of y_hat only
+    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
+    {
+      float w3[3 * J];   // r . z, r . r, b . b
+#pragma unroll
+      for (int u = 0; u < 3 * J; ++u) w3[u] = 0.f;
+      for (int i = 0; i < nown; ++i) {
+        const int k = blockIdx.x + i * G;
+        float* r = orr + (size_t)i * JS;
+        product_taps<NT>(a, k, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
+        const bool act = s_act[i];
+        for (int o = threadIdx.x; o < JS; o += NT) {
+          const int j = J == 1 ? 0 : o / S2;
+          const float bv = ob[(size_t)i * JS + o];
+          const float rv = act ? bv - fmaf(s_twomu[i], ox[(size_t)i * JS + o], r[o]) : 0.f;
+          r[o] = rv;
+          add_at(w3, J + j, rv * rv);
+          if (act) add_at(w3, 2 * J + j, bv * bv);
+        }
+        __syncthreads();
+        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3);
       }
-      float packed[kSlotWords];
-      for (int j = 0; j < J; ++j) {
-        packed[j] = w3[j];
-        packed[J + j] = w3[kMaxJ + j];
-        packed[2 * J + j] = w3[2 * kMaxJ + j];
-      }
-      block_reduce_to0<NT>(packed, 3 * J, scratch);
-      __syncthreads();
-      publish(a.slots, G, packed, 3 * J, ++ep);
+      block_reduce_to0<NT>(w3, scratch);
+      publish<3 * J>(a.slots, G, w3, ++ep);
     }
     if (!gather<NT>(a.slots, G, 3 * J, ep, tot, gvals, a.err)) return;
-    double rz[kMaxJ], rr[kMaxJ], bb[kMaxJ];
-    bool done[kMaxJ];
+    double rz[J], rr[J], bb[J];
+    bool done[J];
 #pragma unroll
-    for (int j = 0; j < kMaxJ; ++j) {
-      rz[j] = j < J ? tot[j] : 0.0;
-      rr[j] = j < J ? tot[J + j] : 0.0;
-      bb[j] = j < J ? tot[2 * J + j] : 0.0;
-      done[j] = (j >= J);
+    for (int j = 0; j < J; ++j) {
+      rz[j] = tot[j];
+      rr[j] = tot[J + j];
+      bb[j] = tot[2 * J + j];
+      done[j] = false;
     }
     axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, nullptr, true);
     __syncthreads();
@@ -651,70 +682,70 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     for (; it < a.cg_max; ++it) {
       bool all = true;
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
+      for (int j = 0; j < J; ++j) {
         done[j] = done[j] || !(rr[j] > a.tol2 * bb[j]) || !(rz[j] > 0.0);
         all = all && done[j];
       }
       if (all) break;   // the same totals on every thread of every CTA
       // ---- A p at this CTA's bins, p . A p (exchange A) -----------------------------------
+      {
+        float pa[J];
 #pragma unroll
-      for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
-      product_bins<NT>(a, f0, nbc, pp, ew, phat, red, cch, part);
-      for (int i = 0; i < nown; ++i) {
-        if (!s_act[i]) continue;
-        const int k = blockIdx.x + i * G;
-        for (int o = threadIdx.x; o < JS; o += NT) {
-          const float pv = pp[(size_t)k * JS + o];
-          part[o / S2] = fmaf(s_twomu[i] * pv, pv, part[o / S2]);
+        for (int j = 0; j < J; ++j) pa[j] = 0.f;
+        product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
+        for (int i = 0; i < nown; ++i) {
+          if (!s_act[i]) continue;
+          const int k = blockIdx.x + i * G;
+          for (int o = threadIdx.x; o < JS; o += NT) {
+            const float pv = pp[(size_t)k * JS + o];
+            add_at(pa, J == 1 ? 0 : o / S2, s_twomu[i] * pv * pv);
+          }
         }
+        block_reduce_to0<NT>(pa, scratch);   // its barrier orders the y_hat stores before the publish
+        publish<J>(a.slots, G, pa, ++ep);
       }
-      block_reduce_to0<NT>(part, J, scratch);
-      __syncthreads();
-      publish(a.slots, G, part, J, ++ep);
       if (!gather<NT>(a.slots, G, J, ep, tot, gvals, a.err)) return;
-      float alpha[kMaxJ];
+      float alpha[J];
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        const double pap = j < J ? tot[j] : 0.0;
-        alpha[j] = (j < J && !done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
+      for (int j = 0; j < J; ++j) {
+        const double pap = tot[j];
+        alpha[j] = (!done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
       }
       // ---- x += alpha p, r -= alpha A p, z = M^{-1} r (exchange B) ---------------------------
-#pragma unroll
-      for (int i = 0; i < kSlotWords; ++i) part[i] = 0.f;
-      for (int i = 0; i < nown; ++i) {
-        if (!s_act[i]) continue;
-        const int k = blockIdx.x + i * G;
-        float* r = orr + (size_t)i * JS;
-        float* yk = oz + (size_t)i * JS;   // A p of the filter, then z
-        product_taps<NT>(a, k, yh, sc, twa, twb, yk);
-        for (int o = threadIdx.x; o < JS; o += NT) {
-          const int j = o / S2;
-          const float al = alpha[j];
-          const float pv = pp[(size_t)k * JS + o];
-          const float apv = fmaf(s_twomu[i], pv, yk[o]);
-          ox[(size_t)i * JS + o] = fmaf(al, pv, ox[(size_t)i * JS + o]);
-          const float rv = fmaf(-al, apv, r[o]);
-          r[o] = rv;
-          part[2 * kMaxJ + j] = fmaf(rv, rv, part[2 * kMaxJ + j]);
-        }
-        __syncthreads();
-        precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, part);
-      }
       {
-        float packed[kSlotWords];
-        for (int j = 0; j < J; ++j) {
-          packed[j] = part[kMaxJ + j];
-          packed[J + j] = part[2 * kMaxJ + j];
+        float w2[2 * J];   // r . z, r . r
+#pragma unroll
+        for (int u = 0; u < 2 * J; ++u) w2[u] = 0.f;
+        for (int i = 0; i < nown; ++i) {
+          if (!s_act[i]) continue;
+          const int k = blockIdx.x + i * G;
+          float* r = orr + (size_t)i * JS;
+          float* yk = oz + (size_t)i * JS;   // A p of the filter, then z
+          product_taps<NT>(a, k, yh, sc, twa, twb, yk);
+          for (int o = threadIdx.x; o < JS; o += NT) {
+            const int j = J == 1 ? 0 : o / S2;
+            float al = alpha[0];
+#pragma unroll
+            for (int jj = 1; jj < J; ++jj)
+              if (jj == j) al = alpha[jj];
+            const float pv = pp[(size_t)k * JS + o];
+            const float apv = fmaf(s_twomu[i], pv, yk[o]);
+            ox[(size_t)i * JS + o] = fmaf(al, pv, ox[(size_t)i * JS + o]);
+            const float rv = fmaf(-al, apv, r[o]);
+            r[o] = rv;
+            add_at(w2, J + j, rv * rv);
+          }
+          __syncthreads();
+          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2);
         }
-        block_reduce_to0<NT>(packed, 2 * J, scratch);
-        __syncthreads();
-        publish(a.slots, G, packed, 2 * J, ++ep);
+        block_reduce_to0<NT>(w2, scratch);   // its barrier orders the z stores before the publish
+        publish<2 * J>(a.slots, G, w2, ++ep);
       }
       if (!gather<NT>(a.slots, G, 2 * J, ep, tot, gvals, a.err)) return;
-      double beta[kMaxJ];
+      double beta[J];
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        if (j < J && !done[j]) {
+      for (int j = 0; j < J; ++j) {
+        if (!done[j]) {
           beta[j] = rz[j] > 0.0 ? tot[j] / rz[j] : 0.0;
           rz[j] = tot[j];
           rr[j] = tot[J + j];
@@ -730,33 +761,29 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     // ---- mu_k <- max(mu_k ||d_k||, floor) for active filters (Eq. mu_update); x to global -------
     for (int i = 0; i < nown; ++i) {
       const int k = blockIdx.x + i * G;
-      float sq[kSlotWords];
-#pragma unroll
-      for (int u = 0; u < kSlotWords; ++u) sq[u] = 0.f;
+      float sq[1] = {0.f};
       for (int o = threadIdx.x; o < JS; o += NT) {
         const float xv = ox[(size_t)i * JS + o];
         sq[0] = fmaf(xv, xv, sq[0]);
         a.x[(size_t)k * JS + o] = xv;
       }
-      block_reduce_to0<NT>(sq, 1, scratch);
+      block_reduce_to0<NT>(sq, scratch);
       if (threadIdx.x == 0 && s_act[i]) a.mu[k] = fmax(a.mu[k] * sqrt((double)sq[0]), a.mu_floor);
       __syncthreads();
     }
     __syncthreads();
-    publish(a.slots, G, part, 0, ++ep);   // x complete everywhere before the next step
+    publish<0>(a.slots, G, nullptr, ++ep);   // x complete everywhere before the next step
     if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
   }
   // ---- d_k <- d_k / max(1, ||d_k||) ---------------------------------------------------------
   for (int i = 0; i < nown; ++i) {
     const int k = blockIdx.x + i * G;
-    float sq[kSlotWords];
-#pragma unroll
-    for (int u = 0; u < kSlotWords; ++u) sq[u] = 0.f;
+    float sq[1] = {0.f};
     for (int o = threadIdx.x; o < JS; o += NT) {
       const float xv = ox[(size_t)i * JS + o];
       sq[0] = fmaf(xv, xv, sq[0]);
     }
-    block_reduce_to0<NT>(sq, 1, scratch);
+    block_reduce_to0<NT>(sq, scratch);
     if (threadIdx.x == 0) scratch[0] = 1.0f / fmaxf(1.0f, sqrtf(sq[0]));
     __syncthreads();
     const float sc2 = scratch[0];
@@ -818,7 +845,7 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   a.G = learn_cg_ctas(c);
   cudaError_t e = cudaMemsetAsync(c.L.slots, 0, (size_t)2 * a.G * kSlotWords * sizeof(unsigned long long), c.stream);
   if (e != cudaSuccess) return e;
-  auto kern = k_learn_cg<NT>;
+  auto kern = c.J == 1 ? k_learn_cg<NT, 1> : c.J == 2 ? k_learn_cg<NT, 2> : k_learn_cg<NT, 3>;
   // the CTA's bins of the lag spectra stay in shared memory when they fit
   a.chat_smem = learn_cg_smem_bytes(c, a.minv != nullptr, true) <= kSmemLimit ? 1 : 0;
   const size_t smem = learn_cg_smem_bytes(c, a.minv != nullptr, a.chat_smem != 0);
