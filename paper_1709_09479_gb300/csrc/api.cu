@@ -114,7 +114,7 @@ void free_all(Ctx* c) {
   }
   c->events.clear();
   void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
-                  c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yhat, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
+                  c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
   for (void* p : ptrs)
@@ -397,14 +397,13 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: H and W/2 must factor into 2, 3, 5 and 7");
   if (sweep_smem_bytes(g, p.J, kIter) > kSmemLimit)
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: image too large for one map per CTA in shared memory");
-  const size_t cg_smem = learn_cg_smem_bytes(tmp, tmp.S2 <= kMaxBlockJacobi, false);
-  if (cg_smem > kSmemLimit)
-    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
-
   tmp.stream = (cudaStream_t)stream;
   if (cudaGetDevice(&tmp.device) != cudaSuccess) return cuda_fail(nullptr, cudaGetLastError(), "cudaGetDevice");
   cudaError_t e = cudaDeviceGetAttribute(&tmp.nsm, cudaDevAttrMultiProcessorCount, tmp.device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  const size_t cg_smem = learn_cg_smem_bytes(tmp, tmp.S2 <= kMaxBlockJacobi, false);
+  if (cg_smem > kSmemLimit)
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
   const long long NK = (long long)tmp.N * tmp.K;
   tmp.G = (int)std::min<long long>(tmp.nsm, NK);
 
@@ -746,7 +745,8 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
         ensure_alloc(&L.gram, npairs * Om) != cudaSuccess ||
         ensure_alloc(&L.lags, (size_t)K * K * La * Lb) != cudaSuccess ||
         ensure_alloc(&L.chat, (size_t)La * c->fw * K * (K + 1) / 2) != cudaSuccess ||
-        ensure_alloc(&L.yhat, (size_t)K * J * La * c->fw) != cudaSuccess ||
+        ensure_alloc(&L.yw, (size_t)2 * K * J * La * c->fw) != cudaSuccess ||
+        ensure_alloc(&L.zw, nd) != cudaSuccess ||
         ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
         ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
         (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||

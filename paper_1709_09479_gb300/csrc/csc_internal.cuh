@@ -103,7 +103,8 @@ struct LearnBuffers {
   float2* gram = nullptr;   // [npairs][Omega], pairs k <= k'
   float* lags = nullptr;    // [K][K][L*L]
   float2* chat = nullptr;   // [NF][K(K+1)/2] lag spectra / (La Lb), NF = La * fw
-  float2* yhat = nullptr;   // [K][J][NF] half spectrum of the CG product
+  unsigned long long* yw = nullptr;   // [K][J][NF][2] epoch-tagged words of the CG product spectrum
+  unsigned long long* zw = nullptr;   // [K][J][S2] epoch-tagged words of z = M^-1 r
   float* b = nullptr;       // [K][J][S2]
   float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
   double* mu = nullptr;     // [K]
@@ -130,7 +131,7 @@ struct Ctx {
   int N, J, K, fh, fw, S2;
   Geometry g;
   cudaStream_t stream;
-  int device, nsm;
+  int device = 0, nsm = 0;
   int G;                    // CTAs of the coding sweep
   size_t sweep_smem;
   // workspace

@@ -169,11 +169,12 @@ __global__ void __launch_bounds__(kLagSpecNT) k_lag_spectra(LagSpecArgs a) {
 // k = b, b + G, ... for everything else. An iteration has two grid-wide exchanges:
 //   A: after the product at its bins (y_hat to global) a CTA publishes its partial p . A p;
 //   B: after x, r and z = M^-1 r of its filters (z to global) it publishes partial r . z, r . r.
-// Exchanges carry no atomics: each CTA writes its partial sums into its own slot as 64-bit words
-// (float bits | epoch << 32) after a fence, and every CTA's warp 0 polls all slots until they
-// carry the current epoch, then sums them in CTA order (so every CTA gets the same totals).
-// Slots alternate between two banks by epoch parity, so a CTA that is one exchange ahead never
-// overwrites words a slower CTA is still reading.
+// Exchanges carry no atomics and, but for the one at the end of a learning step, no fences: every
+// value that crosses CTAs (partial sums, y_hat, z) is stored as a 64-bit word (float bits |
+// epoch << 32), so a reader polls exactly the words it needs until they carry the current epoch:
+// one round trip to L2 per exchange. Partial sums go to per-CTA slots that alternate between two
+// banks by epoch parity (a CTA one exchange ahead never overwrites words a slower CTA still
+// reads) and are summed in CTA order, so every CTA gets the same totals.
 // ---------------------------------------------------------------------------------------------
 constexpr int kSlotWords = 4 * kMaxJ;
 
@@ -183,10 +184,10 @@ struct CgArgs {
   const float* lags;   // [K][K][La*Lb]: the zero lag of C_kk (activity) and the preconditioner blocks
   const float2* chat;  // [NF][K(K+1)/2] lag spectra / (La Lb), pairs k <= k'
   int chat_smem;       // the CTA's bins of chat are staged in shared memory
-  float2* yhat;        // [K][J][NF] half spectrum of the product being formed
+  unsigned long long* yw;   // [K][J][NF][2] words of y_hat (re, im), the product being formed
+  unsigned long long* zw;   // [K][J][S2] words of z = M^-1 r
   const float* b;      // [K][J][S2]
   float* x;            // [K][J][S2]  d (in/out)
-  float* zv;           // [K][J][S2]  preconditioned residual
   double* mu;          // [K]
   float* minv;         // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
   unsigned long long* slots;   // [2][G][kSlotWords], zeroed before the launch
@@ -278,12 +279,17 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return v;
 }
 
+__device__ __forceinline__ unsigned long long tag(float v, unsigned ep) {
+  return ((unsigned long long)ep << 32) | __float_as_uint(v);
+}
+
 // thread 0: make the CTA's earlier global writes visible, then publish vals[0..N) with epoch ep.
 // The caller has synchronised the block since those writes. N == 0: one word without a sum.
 template <int N>
-__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, unsigned ep) {
+__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, unsigned ep,
+                                        bool fence = false) {
   if (threadIdx.x != 0) return;
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release: the CTA's stores before the words
+  if (fence) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release: plain stores before the words
   unsigned long long* s = slots + ((size_t)(ep & 1) * G + blockIdx.x) * kSlotWords;
 #pragma unroll
   for (int i = 0; i < (N > 0 ? N : 1); ++i)
@@ -348,14 +354,79 @@ __device__ bool gather(const unsigned long long* slots, int G, int n, unsigned e
   return s_fail == 0;
 }
 
+// Waits until this thread's words carry epoch ep: the exchange's slot words (G CTAs x nw, thread t
+// polls words t and t + NT; values parked in vals, [G][nw] floats of shared memory) when slots
+// is not null, and the data words t + u NT < ndata (left in wd[u]; the value is the low half).
+// All pending words are loaded together on every pass. false when a CTA flagged an error or the
+// wait ran out (flag set).
+template <int NT, int U>
+__device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsigned ep, float* vals,
+                           const unsigned long long* data, int ndata, unsigned long long (&wd)[U], int* err) {
+  const unsigned long long* sb = slots ? slots + (size_t)(ep & 1) * G * kSlotWords : nullptr;
+  const int nsw = slots ? G * nw : 0;
+  unsigned pend = 0;   // bit u: data word u pending; bits 30, 31: slot words
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if ((int)threadIdx.x + u * NT < ndata) pend |= 1u << u;
+  if ((int)threadIdx.x < nsw) pend |= 1u << 30;
+  if ((int)threadIdx.x + NT < nsw) pend |= 1u << 31;
+  const long long t0 = clock64();
+  while (true) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (pend & (1u << u)) wd[u] = ld_volatile_u64(data + threadIdx.x + u * NT);
+    unsigned long long ws0 = 0, ws1 = 0;
+    if (pend & (1u << 30)) ws0 = ld_volatile_u64(sb + (size_t)(threadIdx.x / nw) * kSlotWords + threadIdx.x % nw);
+    if (pend & (1u << 31)) {
+      const int i = threadIdx.x + NT;
+      ws1 = ld_volatile_u64(sb + (size_t)(i / nw) * kSlotWords + i % nw);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if ((pend & (1u << u)) && (unsigned)(wd[u] >> 32) == ep) pend &= ~(1u << u);
+    if ((pend & (1u << 30)) && (unsigned)(ws0 >> 32) == ep) {
+      vals[threadIdx.x] = __uint_as_float((unsigned)ws0);
+      pend &= ~(1u << 30);
+    }
+    if ((pend & (1u << 31)) && (unsigned)(ws1 >> 32) == ep) {
+      vals[threadIdx.x + NT] = __uint_as_float((unsigned)ws1);
+      pend &= ~(1u << 31);
+    }
+    if (!pend) return true;
+    if (*(volatile int*)err) return false;
+    if (clock64() - t0 > kSpinLimit) {
+      atomicExch(err, (int)CSC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ float word_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
+// totals[i] = sum over CTAs in CTA order of vals[b * nw + i], i < n (warp 0, float64). Call after a
+// barrier that follows wait_words; ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, double* totals) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = 0; i < n; ++i) {
+      double v = 0.0;
+      for (int b = lane; b < G; b += 32) v += (double)vals[b * nw + i];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) totals[i] = v;
+    }
+  }
+  __syncthreads();
+}
+
 // Lag-grid half spectrum of S Z^T Z S^T p at this CTA's bins, p (all filters) in shared memory:
-// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yhat (C_hat_kk' = conj C_hat_k'k for k > k'),
+// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yw with epoch ep (C_hat_kk' = conj C_hat_k'k for k > k'),
 // and the partial Parseval sums of p . S Z^T Z S^T p over these bins (weight 2 for w2 > 0) into
 // part[j]. ew[i][q] holds the tap twiddles of the CTA's bin f0 + i, cch the CTA's bins of chat (or
 // null: read from global), both in pair_index order. Does not end synchronised.
 template <int NT, int JT>
 __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, const float2* ew, float2* phat,
-                             float2* red, const float2* cch, float (&part)[JT]) {
+                             float2* red, const float2* cch, float (&part)[JT], unsigned ep) {
   constexpr int J = JT;
   const int K = a.K, S2 = a.S2, fw = a.fw, NF = a.NF;
   const int KJ = K * J;
@@ -430,20 +501,20 @@ __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, 
     const int f = f0 + bi, w2 = f % fw;
     float2 s = make_float2(0.f, 0.f);
     for (int pi = 0; pi < PS; ++pi) s = cadd(s, red[(((size_t)bi * PS + pi) * K + k) * J + j]);
-    a.yhat[(size_t)i * NF + f] = s;
+    unsigned long long* w = a.yw + 2 * ((size_t)i * NF + f);
+    st_volatile_u64(w, tag(s.x, ep));
+    st_volatile_u64(w + 1, tag(s.y, ep));
     const float2 p = phat[e];
     add_at(part, j, (w2 == 0 ? 1.f : 2.f) * (p.x * s.x + p.y * s.y));
   }
 }
 
-// y_k = crop(F^-1 y_hat_k) on the taps, for one filter (y_hat written by other CTAs before the
-// last exchange: read through L2). Thread t gets y at taps o = t, t + NT, ... in out[o].
+// y = crop(F^-1 y_hat) on the taps for one filter, y_hat ([J][NF]) in shared memory and complete.
+// Thread t gets y at taps o = t, t + NT, ... in out[o].
 template <int NT>
-__device__ void product_taps(const CgArgs& a, int k, float2* yh, float2* sc, const float2* twa, const float2* twb,
+__device__ void product_taps(const CgArgs& a, const float2* yh, float2* sc, const float2* twa, const float2* twb,
                              float* out) {
   const int J = a.J, NF = a.NF, fw = a.fw, fh = a.fh, La = a.La, Lb = a.Lb, S2 = a.S2;
-  for (int i = threadIdx.x; i < J * NF; i += NT) yh[i] = __ldcg(a.yhat + (size_t)k * J * NF + i);
-  __syncthreads();
   // over w1: sc[j][w2][qa] = sum_w1 y_hat[j][w1][w2] exp(+2 pi i w1 qa / La), four lanes per item
   {
     const int sub = threadIdx.x & 3;
@@ -483,12 +554,12 @@ __device__ void product_taps(const CgArgs& a, int k, float2* yh, float2* sc, con
   }
 }
 
-// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zv; the
+// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zw (epoch ep); the
 // partial r . z into part[j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the CTA owns
 // one filter, else global), else the diagonal. Four lanes of a warp share one tap.
 template <int NT, int N>
 __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc,
-                                               const float* r, float* zo, float (&part)[N]) {
+                                               const float* r, float* zo, float (&part)[N], unsigned ep) {
   const int S2 = a.S2, JS = a.J * S2;
   const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
   const int sub = threadIdx.x & 3;
@@ -511,7 +582,7 @@ __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act,
     zv += __shfl_xor_sync(0xffffffffu, zv, 2);
     if (sub == 0 && o0 < JS) {
       zo[o] = zv;
-      a.zv[(size_t)k * JS + o] = zv;
+      st_volatile_u64(a.zw + (size_t)k * JS + o, tag(zv, ep));
       add_at(part, j, r[o] * zv);
     }
   }
@@ -522,7 +593,9 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   extern __shared__ float smf[];
   __shared__ float scratch[(NT / 32) * kSlotWords];
   __shared__ double tot[kSlotWords];
-  __shared__ float gvals[4 * NT];   // gathered words [G][n]
+  __shared__ float gvals[2 * NT];   // slot words of the current exchange [G][nw]
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
   __shared__ float s_twomu[8], s_jac[8];
   __shared__ int s_act[8];
   constexpr int J = JT;
@@ -624,6 +697,9 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   }
   const float* mk = own_one ? mloc : nullptr;
 
+  constexpr int UY = 6;    // y_hat words per thread: 2 J NF <= UY NT
+  constexpr int UZ = 12;   // z words per thread and pass
+  const int nyw = 2 * J * a.NF, nz = K * JS;
   for (int step = 0; step < a.steps; ++step) {
     if (threadIdx.x < nown) {
       const int k = blockIdx.x + threadIdx.x * G;
@@ -638,19 +714,26 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       float pa[J];
 #pragma unroll
       for (int j = 0; j < J; ++j) pa[j] = 0.f;
-      product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
+      product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa, ep + 1);
     }
-    __syncthreads();
     publish<0>(a.slots, G, nullptr, ++ep);   // no sums: an exchange of y_hat only
-    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
     {
       float w3[3 * J];   // r . z, r . r, b . b
 #pragma unroll
       for (int u = 0; u < 3 * J; ++u) w3[u] = 0.f;
       for (int i = 0; i < nown; ++i) {
         const int k = blockIdx.x + i * G;
+        unsigned long long yv[UY];
+        if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, 1, ep, gvals, a.yw + (size_t)k * nyw, nyw, yv, a.err))
+          s_fail = 1;
+        float* yhf = reinterpret_cast<float*>(yh);
+#pragma unroll
+        for (int u = 0; u < UY; ++u)
+          if ((int)threadIdx.x + u * NT < nyw) yhf[threadIdx.x + u * NT] = word_value(yv[u]);
+        __syncthreads();
+        if (s_fail) return;
         float* r = orr + (size_t)i * JS;
-        product_taps<NT>(a, k, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
+        product_taps<NT>(a, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
         const bool act = s_act[i];
         for (int o = threadIdx.x; o < JS; o += NT) {
           const int j = J == 1 ? 0 : o / S2;
@@ -661,14 +744,32 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           if (act) add_at(w3, 2 * J + j, bv * bv);
         }
         __syncthreads();
-        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3);
+        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3, ep + 1);
+      }
+      if (nown == 0) {   // the exchange's slot words still have to be seen
+        unsigned long long none[1];
+        if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) return;
       }
       block_reduce_to0<NT>(w3, scratch);
       publish<3 * J>(a.slots, G, w3, ++ep);
     }
-    if (!gather<NT>(a.slots, G, 3 * J, ep, tot, gvals, a.err)) return;
     double rz[J], rr[J], bb[J];
     bool done[J];
+    // all z (and the sums) of exchange ep: p = z
+    for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
+      unsigned long long zv[UZ];
+      if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 3 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT), zv,
+                              a.err))
+        s_fail = 1;
+      __syncthreads();
+      if (s_fail) return;
+#pragma unroll
+      for (int u = 0; u < UZ; ++u)
+        if (c0 + (int)threadIdx.x + u * NT < nz) pp[c0 + threadIdx.x + u * NT] = word_value(zv[u]);
+    }
+    sum_slots<NT>(gvals, G, 3 * J, 3 * J, tot);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       rz[j] = tot[j];
@@ -676,8 +777,6 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       bb[j] = tot[2 * J + j];
       done[j] = false;
     }
-    axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, nullptr, true);
-    __syncthreads();
     int it = 0;
     for (; it < a.cg_max; ++it) {
       bool all = true;
@@ -692,7 +791,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         float pa[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) pa[j] = 0.f;
-        product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
+        product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa, ep + 1);
         for (int i = 0; i < nown; ++i) {
           if (!s_act[i]) continue;
           const int k = blockIdx.x + i * G;
@@ -701,27 +800,44 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             add_at(pa, J == 1 ? 0 : o / S2, s_twomu[i] * pv * pv);
           }
         }
-        block_reduce_to0<NT>(pa, scratch);   // its barrier orders the y_hat stores before the publish
+        block_reduce_to0<NT>(pa, scratch);
         publish<J>(a.slots, G, pa, ++ep);
-      }
-      if (!gather<NT>(a.slots, G, J, ep, tot, gvals, a.err)) return;
-      float alpha[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const double pap = tot[j];
-        alpha[j] = (!done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
       }
       // ---- x += alpha p, r -= alpha A p, z = M^{-1} r (exchange B) ---------------------------
       {
         float w2[2 * J];   // r . z, r . r
 #pragma unroll
         for (int u = 0; u < 2 * J; ++u) w2[u] = 0.f;
-        for (int i = 0; i < nown; ++i) {
-          if (!s_act[i]) continue;
+        float alpha[J];
+        for (int i = 0; i < nown + (nown == 0 ? 1 : 0); ++i) {
           const int k = blockIdx.x + i * G;
+          const bool has = i < nown;
+          unsigned long long yv[UY];
+          if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, J, ep, gvals, has ? a.yw + (size_t)k * nyw : nullptr,
+                                  has ? nyw : 0, yv, a.err))
+            s_fail = 1;
+          float* yhf = reinterpret_cast<float*>(yh);
+#pragma unroll
+          for (int u = 0; u < UY; ++u)
+            if (has && (int)threadIdx.x + u * NT < nyw) yhf[threadIdx.x + u * NT] = word_value(yv[u]);
+          __syncthreads();
+          if (s_fail) return;
+          if (i == 0) {
+            sum_slots<NT>(gvals, G, J, J, tot);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              const double pap = tot[j];
+              alpha[j] = (!done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
+            }
+          }
+          if (!has) continue;
+          if (!s_act[i]) {   // z_k stays 0, but its words carry every exchange's epoch
+            for (int o = threadIdx.x; o < JS; o += NT) st_volatile_u64(a.zw + (size_t)k * JS + o, tag(0.f, ep + 1));
+            continue;
+          }
           float* r = orr + (size_t)i * JS;
           float* yk = oz + (size_t)i * JS;   // A p of the filter, then z
-          product_taps<NT>(a, k, yh, sc, twa, twb, yk);
+          product_taps<NT>(a, yh, sc, twa, twb, yk);
           for (int o = threadIdx.x; o < JS; o += NT) {
             const int j = J == 1 ? 0 : o / S2;
             float al = alpha[0];
@@ -736,25 +852,45 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             add_at(w2, J + j, rv * rv);
           }
           __syncthreads();
-          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2);
+          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2, ep + 1);
         }
-        block_reduce_to0<NT>(w2, scratch);   // its barrier orders the z stores before the publish
+        block_reduce_to0<NT>(w2, scratch);
         publish<2 * J>(a.slots, G, w2, ++ep);
       }
-      if (!gather<NT>(a.slots, G, 2 * J, ep, tot, gvals, a.err)) return;
+      // ---- p = z + beta p: every CTA keeps the whole search direction ------------------------
       double beta[J];
+      for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
+        unsigned long long zv[UZ];
+        if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 2 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT),
+                                zv, a.err))
+          s_fail = 1;
+        __syncthreads();
+        if (s_fail) return;
+        if (c0 == 0) {
+          sum_slots<NT>(gvals, G, 2 * J, 2 * J, tot);
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        if (!done[j]) {
-          beta[j] = rz[j] > 0.0 ? tot[j] / rz[j] : 0.0;
-          rz[j] = tot[j];
-          rr[j] = tot[J + j];
-        } else {
-          beta[j] = 0.0;
+          for (int j = 0; j < J; ++j) {
+            if (!done[j]) {
+              beta[j] = rz[j] > 0.0 ? tot[j] / rz[j] : 0.0;
+              rz[j] = tot[j];
+              rr[j] = tot[J + j];
+            } else {
+              beta[j] = 0.0;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < UZ; ++u) {
+          const int idx = c0 + threadIdx.x + u * NT;
+          if (idx < nz) {
+            float bt = (float)beta[0];
+#pragma unroll
+            for (int jj = 1; jj < J; ++jj)
+              if (jj == (idx % JS) / S2) bt = (float)beta[jj];
+            pp[idx] = fmaf(bt, pp[idx], word_value(zv[u]));
+          }
         }
       }
-      // every CTA keeps the whole search direction: p = z + beta p
-      axpy_from_l2<NT>(pp, a.zv, K * JS, JS, S2, beta, false);
       __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.iters) a.iters[step] = it;
@@ -772,8 +908,14 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       __syncthreads();
     }
     __syncthreads();
-    publish<0>(a.slots, G, nullptr, ++ep);   // x complete everywhere before the next step
-    if (!gather<NT>(a.slots, G, 0, ep, tot, gvals, a.err)) return;
+    publish<0>(a.slots, G, nullptr, ++ep, true);   // x (plain stores) complete everywhere before the next step
+    {
+      unsigned long long none[1];
+      if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err)) s_fail = 1;
+      if (threadIdx.x < G) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire before reading x
+      __syncthreads();
+      if (s_fail) return;
+    }
   }
   // ---- d_k <- d_k / max(1, ||d_k||) ---------------------------------------------------------
   for (int i = 0; i < nown; ++i) {
@@ -838,12 +980,14 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   a.G = 0; a.steps = steps; a.cg_max = c.p.cg_max;
   a.tol2 = c.p.cg_tol * c.p.cg_tol; a.mu_floor = kMuFloor;
   const size_t nvec = (size_t)c.K * c.J * c.S2;
-  a.lags = c.L.lags; a.chat = c.L.chat; a.yhat = c.L.yhat; a.b = c.L.b; a.x = d;
-  a.zv = c.L.vec + nvec;
+  a.lags = c.L.lags; a.chat = c.L.chat; a.yw = c.L.yw; a.zw = c.L.zw; a.b = c.L.b; a.x = d;
   a.mu = c.L.mu; a.minv = c.L.minv; a.slots = c.L.slots; a.iters = c.L.iters; a.err = dev_err;
   // the grid: one CTA per SM at most (every CTA must be resident: the exchanges wait on all)
   a.G = learn_cg_ctas(c);
+  // epochs restart at 1 every launch: clear every word that carries one
   cudaError_t e = cudaMemsetAsync(c.L.slots, 0, (size_t)2 * a.G * kSlotWords * sizeof(unsigned long long), c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.L.yw, 0, (size_t)2 * c.K * c.J * a.NF * sizeof(unsigned long long), c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.L.zw, 0, nvec * sizeof(unsigned long long), c.stream);
   if (e != cudaSuccess) return e;
   auto kern = c.J == 1 ? k_learn_cg<NT, 1> : c.J == 2 ? k_learn_cg<NT, 2> : k_learn_cg<NT, 3>;
   // the CTA's bins of the lag spectra stay in shared memory when they fit
@@ -857,7 +1001,8 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if ((c.K + a.G - 1) / a.G > 8) return cudaErrorInvalidValue;   // filters per CTA
-  if (a.G * 3 * c.J > 4 * NT) return cudaErrorInvalidValue;       // gathered words per exchange
+  if (a.G * 3 * c.J > 2 * NT) return cudaErrorInvalidValue;       // slot words per exchange
+  if (2 * c.J * a.NF > 6 * NT) return cudaErrorInvalidValue;      // y_hat words per filter
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(a.G), dim3(NT), args, smem, c.stream);
 }
