@@ -104,6 +104,18 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
 csc_status csc_init_uneven(const csc_params* params, int n_images, const int* dims, void* stream,
                            csc_ctx** out);
 
+/*
+ * Like csc_init for videos: n_videos tensors of J channels x T frames x H x W (dims = {T, H, W}),
+ * coded with K filters of support ft x fh x fw per channel (params->fs = {fh, fw}; ft odd, taps at
+ * time offsets -(ft-1)/2 .. (ft-1)/2, circular like the spatial ones), 3-D DFTs: the higher-order
+ * extension of Sec. 3.3 with a time axis. Arrays: x [N][J][T][H][W], d [K][J][ft][fh][fw],
+ * v and z [N][K][T][H][W]. Supported: H = W = 128, 1 <= T <= 64, ft <= 7 and <= T, CSC_FP32.
+ * Supports csc_code, csc_objective, csc_describe and csc_destroy; the learning and reverse-mode
+ * calls return CSC_ERR_UNSUPPORTED on such a context.
+ */
+csc_status csc_init_video(const csc_params* params, int ft, int n_videos, const int* dims, void* stream,
+                          csc_ctx** out);
+
 /* One-line JSON description of the context (sizes, size classes, launch shape) into buf (len bytes). */
 csc_status csc_describe(const csc_ctx* ctx, char* buf, int len);
 

@@ -66,6 +66,8 @@ def _load():
     lib.csc_timing_read.restype = i
     lib.csc_init_uneven.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, ctypes.POINTER(vp)]
     lib.csc_init_uneven.restype = i
+    lib.csc_init_video.argtypes = [ctypes.POINTER(csc_params), i, i, ctypes.POINTER(i), vp, ctypes.POINTER(vp)]
+    lib.csc_init_video.restype = i
     lib.csc_describe.argtypes = [vp, ctypes.c_char_p, i]
     lib.csc_describe.restype = i
     lib.csc_tape_bytes.argtypes = [vp, i, i]
@@ -133,6 +135,15 @@ def csc_init_uneven(J, K, fs, dims_list, beta, rho, precision=CSC_FP32, stream=N
     arr = (ctypes.c_int * len(flat))(*flat)
     out = ctypes.c_void_p()
     _check(LIB.csc_init_uneven(ctypes.byref(p), len(dims_list), arr, stream, ctypes.byref(out)))
+    return out.value
+
+
+def csc_init_video(J, K, fs, ft, dims, n_videos, beta, rho, stream=None):
+    """Context for n_videos tensors J x T x H x W (dims = (T, H, W)), filters ft x fh x fw (fs = (fh, fw))."""
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, CSC_FP32, 0)
+    dims_arr = (ctypes.c_int * 3)(*dims)
+    out = ctypes.c_void_p()
+    _check(LIB.csc_init_video(ctypes.byref(p), ft, n_videos, dims_arr, stream, ctypes.byref(out)))
     return out.value
 
 
@@ -228,13 +239,17 @@ class Solver:
     """One context: N images of size dims = (H, W), K filters of support fs with J channels."""
 
     def __init__(self, *, J, K, fs, dims=None, n_images=None, beta, rho, cg_max=100, cg_tol=1e-6,
-                 precision=CSC_FP32, stream=None, flags=0, dims_list=None):
-        """dims + n_images: a batch of equal sizes; dims_list: one (H, W) per image (uneven batch)."""
+                 precision=CSC_FP32, stream=None, flags=0, dims_list=None, ft=None):
+        """dims + n_images: a batch of equal sizes; dims_list: one (H, W) per image (uneven batch);
+        ft + dims = (T, H, W): n_images videos with filters of ft time taps (3-D transforms)."""
         self.J, self.K, self.fs = J, K, tuple(fs)
         self.beta, self.rho = beta, rho
         if stream is None:
             stream = _current_stream()
-        if dims_list is not None:
+        if ft is not None:
+            self.dims, self.N, self.ft = tuple(dims), n_images, ft
+            self.ctx = csc_init_video(J, K, fs, ft, dims, n_images, beta, rho, stream)
+        elif dims_list is not None:
             self.dims_list = [tuple(hw) for hw in dims_list]
             self.N, self.dims = len(self.dims_list), None
             self.ctx = csc_init_uneven(J, K, fs, self.dims_list, beta, rho, precision, stream, flags)

@@ -116,7 +116,8 @@ void free_all(Ctx* c) {
   void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
-                  c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec};
+                  c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
+                  c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -358,7 +359,16 @@ const char* csc_last_error(const csc_ctx* ctx) {
   return ctx ? ctx->c.last_error.c_str() : g_init_error.c_str();
 }
 
+static csc_status init_ctx(const csc_params* params, int n_images, const int* dims, void* stream, csc_ctx** out,
+                           bool video);
+
 csc_status csc_init(const csc_params* params, int n_images, const int* dims, void* stream, csc_ctx** out) {
+  return init_ctx(params, n_images, dims, stream, out, false);
+}
+
+// video contexts run their own frame and bin kernels: the 2-D sweep and learning limits do not apply
+static csc_status init_ctx(const csc_params* params, int n_images, const int* dims, void* stream, csc_ctx** out,
+                           bool video) {
   if (!params || !dims || !out) return fail(nullptr, CSC_ERR_ARG, "csc_init: null argument");
   *out = nullptr;
   const csc_params& p = *params;
@@ -395,14 +405,14 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
   g.rt.rcol = factorize(H);
   if (!radices_ok(g.rt.rrow) || !radices_ok(g.rt.rcol))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: H and W/2 must factor into 2, 3, 5 and 7");
-  if (sweep_smem_bytes(g, p.J, kIter) > kSmemLimit)
+  if (!video && sweep_smem_bytes(g, p.J, kIter) > kSmemLimit)
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: image too large for one map per CTA in shared memory");
   tmp.stream = (cudaStream_t)stream;
   if (cudaGetDevice(&tmp.device) != cudaSuccess) return cuda_fail(nullptr, cudaGetLastError(), "cudaGetDevice");
   cudaError_t e = cudaDeviceGetAttribute(&tmp.nsm, cudaDevAttrMultiProcessorCount, tmp.device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
   const size_t cg_smem = learn_cg_smem_bytes(tmp, tmp.S2 <= kMaxBlockJacobi, false);
-  if (cg_smem > kSmemLimit)
+  if (!video && cg_smem > kSmemLimit)
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
   const long long NK = (long long)tmp.N * tmp.K;
   tmp.G = (int)std::min<long long>(tmp.nsm, NK);
@@ -554,16 +564,148 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   return CSC_OK;
 }
 
+// ---- video tensors --------------------------------------------------------------------------
+
+csc_status csc_init_video(const csc_params* params, int ft, int n_videos, const int* dims, void* stream,
+                          csc_ctx** out) {
+  if (!params || !dims || !out) return fail(nullptr, CSC_ERR_ARG, "csc_init_video: null argument");
+  *out = nullptr;
+  const int T = dims[0], H = dims[1], W = dims[2];
+  if (H != 128 || W != 128) return fail(nullptr, CSC_ERR_SHAPE, "csc_init_video: frames must be 128 x 128");
+  if (T < 1 || T > video_max_T()) return fail(nullptr, CSC_ERR_SHAPE, "csc_init_video: T must be 1..64");
+  if (ft < 1 || !(ft & 1) || ft > 7 || ft > T)
+    return fail(nullptr, CSC_ERR_SHAPE, "csc_init_video: time support must be odd, <= 7 and <= T");
+  if (params->precision != CSC_FP32) return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_video: CSC_FP32 only");
+  const int hw[2] = {H, W};
+  csc_status s = init_ctx(params, n_videos, hw, stream, out, true);
+  if (s != CSC_OK) return s;
+  Ctx* c = &(*out)->c;
+  c->video = true;
+  c->T = T;
+  c->ft = ft;
+  const size_t OM = (size_t)c->g.Omega;
+  const size_t nmaps = std::max((size_t)c->K * c->J * ft, (size_t)c->N * c->J * T);
+  if (cudaMalloc((void**)&c->vS, (size_t)c->N * c->K * T * OM * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vd2, (size_t)c->K * c->J * ft * OM * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vx3, (size_t)c->N * c->J * T * OM * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vp3, (size_t)T * OM * c->J * c->J * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vtmp, nmaps * OM * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vobj, (size_t)c->N * video_bin_blocks() * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->vl1, (size_t)c->nsm * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    csc_destroy(*out);
+    *out = nullptr;
+    return fail(nullptr, CSC_ERR_WORKSPACE, "csc_init_video: device workspace allocation failed");
+  }
+  return CSC_OK;
+}
+
+static VideoArgs video_args(const Ctx* c, float* v, float* z) {
+  VideoArgs a;
+  a.N = c->N; a.K = c->K; a.J = c->J; a.T = c->T; a.ft = c->ft;
+  a.beta = (float)c->p.beta; a.rho = (float)c->p.rho;
+  a.tw = c->tw; a.S = c->vS; a.v = v; a.z = z; a.l1 = c->vl1;
+  a.d2 = c->vd2; a.xh3 = c->vx3; a.p3 = c->vp3; a.objpart = c->vobj;
+  return a;
+}
+
+// filter tap spectra, x_hat at the 3-D frequencies and the per-frequency systems
+static cudaError_t video_setup(Ctx* c, const VideoArgs& a, const float* dd, const float* xd) {
+  cudaError_t e = launch_fft_maps(*c, dd, c->K * c->J * c->ft, 1, c->vtmp);
+  if (e == cudaSuccess) e = launch_permute_f128(c->vtmp, c->vd2, c->K * c->J * c->ft, *c);
+  if (e == cudaSuccess) e = launch_fft_maps(*c, xd, c->N * c->J * c->T, 0, c->vtmp);
+  if (e == cudaSuccess) e = launch_video_setup(a, c->vtmp, c->stream);
+  c->launches += 4;
+  return e;
+}
+
+static csc_status video_code(Ctx* c, const float* x, const float* d, float* v, float* z, int iters) {
+  const size_t D = (size_t)c->g.D;
+  const size_t nx = (size_t)c->N * c->J * c->T * D, nd = (size_t)c->K * c->J * c->ft * c->S2;
+  const size_t nv = (size_t)c->N * c->K * c->T * D;
+  const float *xd = nullptr, *dd = nullptr, *vd_c = nullptr;
+  csc_status s;
+  if ((s = stage_in(c, v, &c->st_v, nv, &vd_c, true)) != CSC_OK) return s;
+  float* vd = const_cast<float*>(vd_c);
+  const bool v_host = (vd != v);
+  float* zd = nullptr;
+  bool z_host = false;
+  if (z) {
+    if (is_device_ptr(z)) zd = z;
+    else {
+      CSC_CHECK_CUDA(c, ensure_alloc(&c->st_z, nv), "staging allocation");
+      zd = c->st_z;
+      z_host = true;
+    }
+  }
+  if (iters == 0) {
+    if (zd) {
+      CSC_CHECK_CUDA(c, launch_codes_from_state_n(*c, vd, zd, nv), "codes");
+      c->launches += 1;
+    }
+  } else {
+    if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+    if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
+    const VideoArgs a = video_args(c, vd, zd);
+    const int G = c->nsm;
+    CSC_CHECK_CUDA(c, video_setup(c, a, dd, xd), "video setup");
+    CSC_CHECK_CUDA(c, launch_video_frames(a, kPrologue, G, c->stream), "video prologue");
+    c->launches += 1;
+    for (int t = 0; t < iters; ++t) {
+      const int br = (t < iters - 1) ? bracket_open(c, 0) : -1;
+      CSC_CHECK_CUDA(c, launch_video_bins(a, kIter, c->stream), "video bins");
+      CSC_CHECK_CUDA(c, launch_video_frames(a, t == iters - 1 ? kLast : kIter, G, c->stream), "video frames");
+      bracket_close(c, br);
+      c->launches += 2;
+    }
+  }
+  if (v_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(v, vd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "v copy");
+  if (z_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(z, zd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "z copy");
+  if (v_host || z_host || (xd && xd != x) || (dd && dd != d))
+    CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  return CSC_OK;
+}
+
+static csc_status video_objective(Ctx* c, const float* x, const float* d, const float* z, double* out) {
+  const size_t D = (size_t)c->g.D;
+  const size_t nx = (size_t)c->N * c->J * c->T * D, nd = (size_t)c->K * c->J * c->ft * c->S2;
+  const size_t nz = (size_t)c->N * c->K * c->T * D;
+  const float *xd, *dd, *zd;
+  csc_status s;
+  if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
+  const VideoArgs a = video_args(c, nullptr, const_cast<float*>(zd));
+  const int G = c->nsm;
+  CSC_CHECK_CUDA(c, video_setup(c, a, dd, xd), "video setup");
+  CSC_CHECK_CUDA(c, launch_video_frames(a, kObjective, G, c->stream), "video codes spectra");
+  CSC_CHECK_CUDA(c, launch_video_bins(a, kObjective, c->stream), "video residual");
+  c->launches += 2;
+  const int nb = c->N * video_bin_blocks();
+  std::vector<double> parts(nb), l1(G);
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(parts.data(), c->vobj, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "objective copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(l1.data(), c->vl1, G * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "objective copy");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  double e2 = 0.0, a1 = 0.0;
+  for (double p : parts) e2 += p;
+  for (double p : l1) a1 += p;
+  *out = 0.5 * e2 + c->p.beta * a1;
+  return CSC_OK;
+}
+
 csc_status csc_describe(const csc_ctx* ctx, char* buf, int len) {
   if (!ctx || !buf || len < 1) return fail(nullptr, CSC_ERR_ARG, "csc_describe: null argument");
   const Ctx& c = ctx->c;
   const int n_cls = c.uneven ? (int)c.U.cls.size() : 1;
   std::snprintf(buf, (size_t)len,
                 "{\"N\": %d, \"K\": %d, \"J\": %d, \"uneven\": %s, \"size_classes\": %d, \"ctas\": %d, "
-                "\"threads_per_cta\": %d, \"autotuned\": %s, \"graph\": %s, \"graph_recorded\": %s}",
+                "\"threads_per_cta\": %d, \"autotuned\": %s, \"graph\": %s, \"graph_recorded\": %s, "
+                "\"video\": %s, \"T\": %d, \"ft\": %d}",
                 c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, c.G, c.uneven ? c.U.nt : (int)kNTSweep,
                 (c.uneven && c.U.tuned) ? "true" : "false", (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
-                c.graph ? "true" : "false");
+                c.graph ? "true" : "false", c.video ? "true" : "false", c.T, c.ft);
   return CSC_OK;
 }
 
@@ -581,6 +723,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
   if (!x || !d || !v) return fail(c, CSC_ERR_ARG, "csc_code: x, d and v must be non-null");
   if (iters < 0) return fail(c, CSC_ERR_ARG, "csc_code: iters must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->video) return video_code(c, x, d, v, z, iters);
   const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
   const size_t nd = (size_t)c->K * c->J * c->S2;
   const size_t nv = c->uneven ? (size_t)c->U.n_v : (size_t)c->N * c->K * c->g.D;
@@ -687,6 +830,7 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   Ctx* c = &ctx->c;
   if (!x || !d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_objective: null argument");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->video) return video_objective(c, x, d, z, out);
   const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
   const size_t nd = (size_t)c->K * c->J * c->S2;
   const size_t nz = c->uneven ? (size_t)c->U.n_v : (size_t)c->N * c->K * c->g.D;
@@ -731,6 +875,7 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn: not available on an uneven-batch context");
+  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn: not available on a video context");
   if (!x || !z || !d || !mu) return fail(c, CSC_ERR_ARG, "csc_learn: null argument");
   if (steps < 0) return fail(c, CSC_ERR_ARG, "csc_learn: steps must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -877,6 +1022,7 @@ csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_unrolled: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on an uneven-batch context");
+  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on a video context");
   if (!x || !d || !v || !tape || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_unrolled: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: J = 1 only");
@@ -914,6 +1060,7 @@ csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_backward: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on an uneven-batch context");
+  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on a video context");
   if (!x || !d || !tape || !gz || !gx || !gd || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_backward: null array, iters < 1 or every < 1");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: J = 1 only");
@@ -984,6 +1131,7 @@ csc_status csc_synthesize(csc_ctx* ctx, const float* d, const float* z, float* o
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: not available on an uneven-batch context");
+  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: not available on a video context");
   if (!d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_synthesize: null argument");
   if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize: CSC_FP32 only");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -1003,6 +1151,7 @@ csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z,
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_synthesize_backward: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: not available on an uneven-batch context");
+  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: not available on a video context");
   if (!d || !z || !gout || !gz || !gd) return fail(c, CSC_ERR_ARG, "csc_synthesize_backward: null argument");
   if (c->J != 1) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: J = 1 only");
   if (c->p.precision != CSC_FP32) return fail(c, CSC_ERR_UNSUPPORTED, "csc_synthesize_backward: CSC_FP32 only");

@@ -213,6 +213,12 @@ cudaError_t launch_sum_slots(const Ctx& c, const float2* part, float2* out) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_codes_from_state_n(const Ctx& c, const float* v, float* z, size_t n) {
+  const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);
+  k_codes_from_state<<<grid, 256, 0, c.stream>>>(v, z, n, (float)c.p.beta, (float)c.p.rho);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z) {
   const size_t n = (size_t)c.N * c.K * c.g.D;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);

@@ -44,6 +44,28 @@ struct SweepArgs {
 
 struct Ctx;
 
+// ---- video tensors (video.cu): J x T x 128 x 128, filters ft x fh x fw ---------------------------
+struct VideoArgs {
+  int N, K, J, T, ft;
+  float beta, rho;
+  const float2* tw;    // the context's twiddles [Wh | H | Wc]
+  float2* S;           // [N][K][T][8320] per-frame 2-D spectra, thread-major bins
+  float* v;            // [N][K][T][128][128]
+  float* z;            // [N][K][T][128][128]
+  double* l1;          // [grid] per-CTA sum |z| (objective)
+  const float2* d2;    // [K][J][ft][8320] 2-D spectra of the filters' time taps
+  float2* xh3;         // [N][J][T][8320] x_hat at the 3-D frequencies (time frequency tau)
+  float2* p3;          // [T][8320][J][J] (A + I/rho)^{-1} / (128 * 128)
+  double* objpart;     // [N][bin blocks] residual energy (objective)
+};
+size_t video_frames_smem_bytes();
+int video_max_T();
+int video_bin_blocks();
+cudaError_t launch_video_frames(const VideoArgs& a, int mode, int G, cudaStream_t st);
+cudaError_t launch_video_bins(const VideoArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_video_setup(const VideoArgs& a, const float2* x2, cudaStream_t st);
+cudaError_t launch_permute_f128(const float2* in, float2* out, int nmaps, const Ctx& c);
+
 // ---- batches of images of different sizes (uneven.cu) ------------------------------------------
 struct UClass {            // one image size: run-time FFT plan and offsets of its per-class data
   GeoRT g;
@@ -150,6 +172,16 @@ struct Ctx {
   BackwardBuffers B;
   bool uneven = false;
   UnevenLayout U;
+  // video tensors (csc_init_video)
+  bool video = false;
+  int T = 1, ft = 1;
+  float2* vS = nullptr;     // [N][K][T][8320]
+  float2* vd2 = nullptr;    // [K][J][ft][8320]
+  float2* vx3 = nullptr;    // [N][J][T][8320]
+  float2* vp3 = nullptr;    // [T][8320][J][J]
+  float2* vtmp = nullptr;   // canonical 2-D spectra scratch [max(K J ft, N J T)][Omega]
+  double* vobj = nullptr;   // [N][bin blocks]
+  double* vl1 = nullptr;    // [frame CTAs]
   // CUDA graph of the last csc_code launch sequence (flag CSC_FLAG_GRAPH)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -219,6 +251,7 @@ cudaError_t launch_solve_prep(const Ctx& c);
 cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                          float* z);
 cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z);
+cudaError_t launch_codes_from_state_n(const Ctx& c, const float* v, float* z, size_t n);
 cudaError_t launch_objective_final(const Ctx& c, const float2* part, double* out_img);
 cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                             float* z, float* v_out, float2* lam_store);
