@@ -26,7 +26,7 @@ namespace csc {
 namespace f128 {
 
 constexpr int kVidMaxT = 64;
-constexpr int kBinTile = 8;    // 2-D bins per CTA of k_video_bins
+constexpr int kBinTile = 32;   // 2-D bins per CTA of k_video_bins (one warp's lanes)
 constexpr int kBinNT = 256;
 
 // ---------------------------------------------------------------------------------------------
@@ -132,157 +132,199 @@ __global__ void __launch_bounds__(NT, 1) k_video_frames(VideoArgs a) {
 // per block of 2-D bins: the contraction over filters, the per-frequency solve and the products
 // with conj(d_hat), all along time; or (objective) the residual's energy by Parseval
 // ---------------------------------------------------------------------------------------------
-template <int MODE, int JT>
+// Thread layout: lane = bin of a 32-bin tile (every load and store of S, D2, x_hat and P moves
+// 256 contiguous bytes per warp), warp = row of work. The two convolutions along time are register
+// blocked over four consecutive frames (and, for r, over all channels), so a staged S or lambda
+// value is loaded once per four outputs. Shared memory (dynamic, sized by T): S tiles of KS
+// filters, their time taps, and two J x T x 32 work arrays.
+constexpr int kKS = 4;
+constexpr int kTB = 4;   // frames per register block
+template <int J>
+__host__ __device__ constexpr size_t bins_smem_floats(int T) {
+  return 2 * ((size_t)kKS * T * kBinTile + (size_t)kKS * J * 8 * kBinTile + 2 * (size_t)J * T * kBinTile + T);
+}
+
+template <int MODE, int JT, int FT>
 __global__ void __launch_bounds__(kBinNT) k_video_bins(VideoArgs a) {
   constexpr int J = JT;
-  __shared__ float2 sS[4][kVidMaxT][kBinTile];        // S_k tiles of 4 filters
-  __shared__ float2 sD[4][J][8][kBinTile];            // their time taps (ft <= 8)
-  __shared__ float2 sr[J][kVidMaxT][kBinTile];         // r, then lambda
-  __shared__ float2 sx[J][kVidMaxT][kBinTile];         // r_hat, lambda_hat
-  __shared__ float2 tw[kVidMaxT];                      // exp(-2 pi i m / T)
-  __shared__ double red[kBinNT / 32];
-  const int T = a.T, K = a.K, ft = a.ft, oc = (a.ft - 1) / 2;
+  constexpr int KS = kKS;
+  constexpr int B = kBinTile;                          // 32 bins = one warp's lanes
+  constexpr int NW = kBinNT / 32;                      // 8 warps
+  constexpr int OC = (FT - 1) / 2;
+  constexpr int WIN = kTB + FT - 1;                    // frames a block of four outputs reads
+  extern __shared__ float2 vsm[];
+  const int T = a.T, K = a.K;
+  float2* sS = vsm;                                    // [KS][T][B]
+  float2* sD = sS + (size_t)KS * T * B;                // [KS][J][8][B]
+  float2* sr = sD + (size_t)KS * J * 8 * B;            // [J][T][B]: r, then lambda_hat
+  float2* sx = sr + (size_t)J * T * B;                 // [J][T][B]: r_hat, then lambda
+  float2* tw = sx + (size_t)J * T * B;                 // [T] exp(-2 pi i m / T)
+  __shared__ double red[NW];
   const int n = blockIdx.y;
-  const int p0 = blockIdx.x * kBinTile;
+  const int p0 = blockIdx.x * B;
   const int tid = threadIdx.x;
-  const int pp = tid % kBinTile;                       // bin of the tile
+  const int b = tid & 31, w = tid >> 5;
   for (int i = tid; i < T; i += kBinNT) {
     float s, c;
     sincospif(2.0f * (float)i / (float)T, &s, &c);
     tw[i] = make_float2(c, -s);
   }
-  // ---- r_j(t) = sum_k sum_t' D2_jk(t') S_k(t - o(t')) -------------------------------------
-  // thread e = (j, t, pp) accumulates outputs e, e + 256, ... (J * T * 8 <= 3 * 64 * 8)
-  constexpr int kOut = (J * kVidMaxT * kBinTile + kBinNT - 1) / kBinNT;
-  float2 acc[kOut];
+  const int nblk = (T + kTB - 1) / kTB;                // frame blocks (T <= 64: <= 16)
+  const int nout = J * T;
+  const size_t fbase = (size_t)n * K * T;
+  auto wrap = [T](int t) {   // t mod T for any t (windows may extend more than T past the ends when T < 4)
+    t %= T;
+    return t < 0 ? t + T : t;
+  };
+  // ---- r_j(t) = sum_k sum_t' D2_jk(t') S_k(t - o(t')): warp w, frame blocks w and w + 8 -------
+  float2 acc[2][J][kTB];
 #pragma unroll
-  for (int u = 0; u < kOut; ++u) acc[u] = make_float2(0.f, 0.f);
-  const int nout = J * T * kBinTile;
-  for (int k0 = 0; k0 < K; k0 += 4) {
-    const int nk = min(4, K - k0);
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int i = 0; i < kTB; ++i) acc[h][j][i] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += KS) {
+    const int nk = min(KS, K - k0);
     __syncthreads();
-    for (int i = tid; i < nk * T * kBinTile; i += kBinNT) {
-      const int kk = i / (T * kBinTile), rem = i - kk * T * kBinTile, tt = rem / kBinTile, b = rem - tt * kBinTile;
-      const size_t fr = ((size_t)n * K + k0 + kk) * T + tt;
-      sS[kk][tt][b] = __ldcs(a.S + fr * OM + p0 + b);
+    for (int e = w; e < nk * T; e += NW) {
+      const int kk = e / T, tt = e - kk * T;
+      sS[((size_t)kk * T + tt) * B + b] = __ldcs(a.S + (fbase + (size_t)(k0 + kk) * T + tt) * OM + p0 + b);
     }
-    for (int i = tid; i < nk * J * ft * kBinTile; i += kBinNT) {
-      const int kk = i / (J * ft * kBinTile), rem = i - kk * J * ft * kBinTile;
-      const int j = rem / (ft * kBinTile), rem2 = rem - j * ft * kBinTile, tp = rem2 / kBinTile, b = rem2 - tp * kBinTile;
-      sD[kk][j][tp][b] = __ldg(a.d2 + (((size_t)(k0 + kk) * J + j) * ft + tp) * OM + p0 + b);
+    for (int e = w; e < nk * J * FT; e += NW) {
+      const int kk = e / (J * FT), rem = e - kk * J * FT, j = rem / FT, tp = rem - j * FT;
+      sD[(((size_t)kk * J + j) * 8 + tp) * B + b] = __ldg(a.d2 + (((size_t)(k0 + kk) * J + j) * FT + tp) * OM + p0 + b);
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < kOut; ++u) {
-      const int e = tid + u * kBinNT;
-      if (e < nout) {
-        const int j = e / (T * kBinTile), rem = e - j * T * kBinTile, tt = rem / kBinTile, b = rem - tt * kBinTile;
-        float2 s = acc[u];
-        for (int kk = 0; kk < nk; ++kk)
-          for (int tp = 0; tp < ft; ++tp) {
-            int ts = tt - (tp - oc);
-            ts = ts < 0 ? ts + T : (ts >= T ? ts - T : ts);
-            s = cfma(sD[kk][j][tp][b], sS[kk][ts][b], s);
+    for (int h = 0; h < 2; ++h) {
+      const int blk = w + NW * h;
+      if (blk < nblk) {
+        const int t0 = kTB * blk;
+        for (int kk = 0; kk < nk; ++kk) {
+          // S_k(t0 + i - tp + OC) for i < 4, tp < FT: window index wi = i - tp + FT - 1
+          float2 win[WIN];
+#pragma unroll
+          for (int wi = 0; wi < WIN; ++wi) win[wi] = sS[((size_t)kk * T + wrap(t0 + wi - (FT - 1) + OC)) * B + b];
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            float2 dv[FT];
+#pragma unroll
+            for (int tp = 0; tp < FT; ++tp) dv[tp] = sD[(((size_t)kk * J + j) * 8 + tp) * B + b];
+#pragma unroll
+            for (int i = 0; i < kTB; ++i)
+#pragma unroll
+              for (int tp = 0; tp < FT; ++tp) acc[h][j][i] = cfma(dv[tp], win[i - tp + FT - 1], acc[h][j][i]);
           }
-        acc[u] = s;
+        }
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < kOut; ++u) {
-    const int e = tid + u * kBinNT;
-    if (e < nout) {
-      const int j = e / (T * kBinTile), rem = e - j * T * kBinTile, tt = rem / kBinTile, b = rem - tt * kBinTile;
-      sr[j][tt][b] = acc[u];
-    }
+  for (int h = 0; h < 2; ++h) {
+    const int blk = w + NW * h;
+    if (blk < nblk)
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int i = 0; i < kTB; ++i)
+          if (kTB * blk + i < T) sr[((size_t)j * T + kTB * blk + i) * B + b] = acc[h][j][i];
   }
   __syncthreads();
   // ---- r_hat = F_t r - x_hat / rho (iterate) or - x_hat (objective) ------------------------
   const float xs = (MODE == kObjective) ? 1.f : 1.f / a.rho;
-  for (int e = tid; e < nout; e += kBinNT) {
-    const int j = e / (T * kBinTile), rem = e - j * T * kBinTile, tau = rem / kBinTile, b = rem - tau * kBinTile;
+  for (int e = w; e < nout; e += NW) {
+    const int j = e / T, tau = e - j * T;
+    const float2* rj = sr + (size_t)j * T * B + b;
     float2 s = make_float2(0.f, 0.f);
     int m = 0;
     for (int tt = 0; tt < T; ++tt) {
-      s = cfma(sr[j][tt][b], tw[m], s);
+      s = cfma(rj[tt * B], tw[m], s);
       m += tau;
       if (m >= T) m -= T;
     }
     const float2 xh = a.xh3[(((size_t)n * J + j) * T + tau) * OM + p0 + b];
-    sx[j][tau][b] = make_float2(s.x - xs * xh.x, s.y - xs * xh.y);
+    sx[(size_t)e * B + b] = make_float2(s.x - xs * xh.x, s.y - xs * xh.y);
   }
   __syncthreads();
   if (MODE == kObjective) {
     // sum_{tau, bins} wt |r_hat|^2 / (T H W), wt = 1 on the kw = 0 and kw = 64 columns, else 2
+    const int kw = canonical_of(p0 + b) % 65;
+    const float wt = (kw == 0 || kw == 64) ? 1.f : 2.f;
     double e2 = 0.0;
-    for (int e = tid; e < nout; e += kBinNT) {
-      const int j = e / (T * kBinTile), rem = e - j * T * kBinTile, tau = rem / kBinTile, b = rem - tau * kBinTile;
-      const int kw = canonical_of(p0 + b) % 65;
-      const float wt = (kw == 0 || kw == 64) ? 1.f : 2.f;
-      const float2 v = sx[j][tau][b];
+    for (int e = w; e < nout; e += NW) {
+      const float2 v = sx[(size_t)e * B + b];
       e2 += (double)(wt * (v.x * v.x + v.y * v.y));
     }
     for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
-    if ((tid & 31) == 0) red[tid >> 5] = e2;
+    if (b == 0) red[w] = e2;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int i = 0; i < kBinNT / 32; ++i) s += red[i];
+      for (int i = 0; i < NW; ++i) s += red[i];
       a.objpart[(size_t)n * gridDim.x + blockIdx.x] = s / ((double)T * D);
     }
     return;
   }
-  // ---- lambda_hat = P r_hat; lambda = F_t^-1 lambda_hat (P carries 1/(H W)) -----------------
-  for (int e = tid; e < T * kBinTile; e += kBinNT) {
-    const int tau = e / kBinTile, b = e - tau * kBinTile;
+  // ---- lambda_hat = P r_hat (P carries 1/(H W)) ---------------------------------------------
+  for (int tau = w; tau < T; tau += NW) {
     const float2* Pm = a.p3 + ((size_t)tau * OM + p0 + b) * J * J;
     float2 rv[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) rv[j] = sx[j][tau][b];
+    for (int j = 0; j < J; ++j) rv[j] = sx[((size_t)j * T + tau) * B + b];
 #pragma unroll
     for (int i = 0; i < J; ++i) {
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < J; ++j) s = cfma(__ldg(Pm + i * J + j), rv[j], s);
-      sr[i][tau][b] = s;   // lambda_hat
+      sr[((size_t)i * T + tau) * B + b] = s;
     }
   }
   __syncthreads();
+  // ---- lambda = F_t^-1 lambda_hat ------------------------------------------------------------
   const float iT = 1.f / (float)T;
-  for (int e = tid; e < nout; e += kBinNT) {
-    const int j = e / (T * kBinTile), rem = e - j * T * kBinTile, tt = rem / kBinTile, b = rem - tt * kBinTile;
+  for (int e = w; e < nout; e += NW) {
+    const int j = e / T, tt = e - j * T;
+    const float2* lj = sr + (size_t)j * T * B + b;
     float2 s = make_float2(0.f, 0.f);
     int m = 0;
     for (int tau = 0; tau < T; ++tau) {
-      s = cfmac(tw[m], sr[j][tau][b], s);   // exp(+2 pi i tau t / T) lambda_hat
+      s = cfmac(tw[m], lj[tau * B], s);   // exp(+2 pi i tau t / T) lambda_hat
       m += tt;
       if (m >= T) m -= T;
     }
-    sx[j][tt][b] = cscale(s, iT);   // lambda
+    sx[(size_t)e * B + b] = cscale(s, iT);
   }
-  __syncthreads();
-  // ---- S_k(t) <- sum_j sum_t' conj(D2_jk(t')) lambda_j(t + o(t')) ---------------------------
-  for (int k0 = 0; k0 < K; k0 += 4) {
-    const int nk = min(4, K - k0);
+  // ---- S_k(t) <- sum_j sum_t' conj(D2_jk(t')) lambda_j(t + o(t')): (filter, frame block) rows --
+  for (int k0 = 0; k0 < K; k0 += KS) {
+    const int nk = min(KS, K - k0);
     __syncthreads();
-    for (int i = tid; i < nk * J * ft * kBinTile; i += kBinNT) {
-      const int kk = i / (J * ft * kBinTile), rem = i - kk * J * ft * kBinTile;
-      const int j = rem / (ft * kBinTile), rem2 = rem - j * ft * kBinTile, tp = rem2 / kBinTile, b = rem2 - tp * kBinTile;
-      sD[kk][j][tp][b] = __ldg(a.d2 + (((size_t)(k0 + kk) * J + j) * ft + tp) * OM + p0 + b);
+    for (int e = w; e < nk * J * FT; e += NW) {
+      const int kk = e / (J * FT), rem = e - kk * J * FT, j = rem / FT, tp = rem - j * FT;
+      sD[(((size_t)kk * J + j) * 8 + tp) * B + b] = __ldg(a.d2 + (((size_t)(k0 + kk) * J + j) * FT + tp) * OM + p0 + b);
     }
     __syncthreads();
-    for (int i = tid; i < nk * T * kBinTile; i += kBinNT) {
-      const int kk = i / (T * kBinTile), rem = i - kk * T * kBinTile, tt = rem / kBinTile, b = rem - tt * kBinTile;
-      float2 s = make_float2(0.f, 0.f);
+    for (int e = w; e < nk * nblk; e += NW) {
+      const int kk = e / nblk, blk = e - kk * nblk, t0 = kTB * blk;
+      float2 o4[kTB];
 #pragma unroll
-      for (int j = 0; j < J; ++j)
-        for (int tp = 0; tp < ft; ++tp) {
-          int ts = tt + (tp - oc);
-          ts = ts < 0 ? ts + T : (ts >= T ? ts - T : ts);
-          s = cfmac(sD[kk][j][tp][b], sx[j][ts][b], s);
+      for (int i = 0; i < kTB; ++i) o4[i] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        // lambda_j(t0 + i + tp - OC): window index wi = i + tp
+        float2 win[WIN];
+#pragma unroll
+        for (int wi = 0; wi < WIN; ++wi) win[wi] = sx[((size_t)j * T + wrap(t0 + wi - OC)) * B + b];
+#pragma unroll
+        for (int tp = 0; tp < FT; ++tp) {
+          const float2 dv = sD[(((size_t)kk * J + j) * 8 + tp) * B + b];
+#pragma unroll
+          for (int i = 0; i < kTB; ++i) o4[i] = cfmac(dv, win[i + tp], o4[i]);
         }
-      const size_t fr = ((size_t)n * K + k0 + kk) * T + tt;
-      __stcs(a.S + fr * OM + p0 + b, s);
+      }
+#pragma unroll
+      for (int i = 0; i < kTB; ++i)
+        if (t0 + i < T) __stcs(a.S + (fbase + (size_t)(k0 + kk) * T + t0 + i) * OM + p0 + b, o4[i]);
     }
   }
 }
@@ -304,7 +346,8 @@ __global__ void k_video_xhat(VideoArgs a, const float2* __restrict__ x2) {
 }
 
 // P(tau, p) = (A + I / rho)^{-1} / (H W), A_ij = sum_k d_hat_ik conj(d_hat_jk) at the 3-D frequency,
-// d_hat_jk(tau, p) = sum_t' exp(-2 pi i tau o(t') / T) D2_jk(t', p); float64, Gauss-Jordan
+// d_hat_jk(tau, p) = sum_t' exp(-2 pi i tau o(t') / T) D2_jk(t', p) (float32, ft terms); A is summed
+// over filters in float32 with Kahan-Babuska compensation and inverted (Gauss-Jordan) in float64
 template <int JT>
 __global__ void k_video_prep(VideoArgs a) {
   constexpr int J = JT;
@@ -312,34 +355,53 @@ __global__ void k_video_prep(VideoArgs a) {
   const int tau = blockIdx.y;
   if (p >= OM) return;
   const int T = a.T, ft = a.ft, oc = (a.ft - 1) / 2;
-  double re[J][2 * J], im[J][2 * J];
+  float2 ph[8];   // exp(-2 pi i tau o(t') / T), t' < ft <= 7
+#pragma unroll
+  for (int tp = 0; tp < 8; ++tp) {
+    const int m = ((tau * (tp - oc)) % T + T) % T;
+    float sn, cs;
+    sincospif(2.0f * (float)m / (float)T, &sn, &cs);
+    ph[tp] = make_float2(cs, -sn);
+  }
+  // A summed over filters in float32 with compensation (the float64 rate is low), inverted in float64
+  float ar[J][J], ai[J][J], cr[J][J], ci[J][J];
 #pragma unroll
   for (int i = 0; i < J; ++i)
 #pragma unroll
-    for (int j = 0; j < 2 * J; ++j) { re[i][j] = 0.0; im[i][j] = 0.0; }
+    for (int j = 0; j < J; ++j) { ar[i][j] = ai[i][j] = cr[i][j] = ci[i][j] = 0.f; }
+  auto kadd = [](float& s, float& c, float v) {   // Kahan-Babuska step
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  };
   for (int k = 0; k < a.K; ++k) {
-    double dr[J], di[J];
+    float2 dk[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      dr[j] = 0.0;
-      di[j] = 0.0;
-      for (int tp = 0; tp < ft; ++tp) {
-        const int m = ((tau * (tp - oc)) % T + T) % T;
-        double sn, cs;
-        sincospi(2.0 * (double)m / (double)T, &sn, &cs);
-        const float2 v = a.d2[(((size_t)k * J + j) * ft + tp) * OM + p];
-        dr[j] += (double)v.x * cs + (double)v.y * sn;    // v * exp(-i phi)
-        di[j] += (double)v.y * cs - (double)v.x * sn;
-      }
+      float2 sacc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int tp = 0; tp < 8; ++tp)
+        if (tp < ft) sacc = cfma(a.d2[(((size_t)k * J + j) * ft + tp) * OM + p], ph[tp], sacc);
+      dk[j] = sacc;
     }
 #pragma unroll
     for (int i = 0; i < J; ++i)
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        re[i][j] += dr[i] * dr[j] + di[i] * di[j];
-        im[i][j] += di[i] * dr[j] - dr[i] * di[j];
+        kadd(ar[i][j], cr[i][j], dk[i].x * dk[j].x + dk[i].y * dk[j].y);
+        kadd(ai[i][j], ci[i][j], dk[i].y * dk[j].x - dk[i].x * dk[j].y);
       }
   }
+  double re[J][2 * J], im[J][2 * J];
+#pragma unroll
+  for (int i = 0; i < J; ++i)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      re[i][j] = (double)ar[i][j] + (double)cr[i][j];
+      im[i][j] = (double)ai[i][j] + (double)ci[i][j];
+      re[i][J + j] = 0.0;
+      im[i][J + j] = 0.0;
+    }
 #pragma unroll
   for (int i = 0; i < J; ++i) { re[i][i] += 1.0 / a.rho; re[i][J + i] = 1.0; }
 #pragma unroll
@@ -382,15 +444,34 @@ cudaError_t launch_frames_mode(const VideoArgs& a, int G, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int MODE, int J, int FT>
+cudaError_t launch_bins_mjf(const VideoArgs& a, cudaStream_t st) {
+  auto kern = k_video_bins<MODE, J, FT>;
+  const size_t smem = bins_smem_floats<J>(a.T) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(OM / kBinTile, a.N);
+  kern<<<grid, kBinNT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int J>
+cudaError_t launch_bins_mj(const VideoArgs& a, cudaStream_t st) {
+  switch (a.ft) {
+    case 1: return launch_bins_mjf<MODE, J, 1>(a, st);
+    case 3: return launch_bins_mjf<MODE, J, 3>(a, st);
+    case 5: return launch_bins_mjf<MODE, J, 5>(a, st);
+    default: return launch_bins_mjf<MODE, J, 7>(a, st);
+  }
+}
+
 template <int MODE>
 cudaError_t launch_bins_mode(const VideoArgs& a, cudaStream_t st) {
-  dim3 grid(OM / kBinTile, a.N);
   switch (a.J) {
-    case 1: k_video_bins<MODE, 1><<<grid, kBinNT, 0, st>>>(a); break;
-    case 2: k_video_bins<MODE, 2><<<grid, kBinNT, 0, st>>>(a); break;
-    default: k_video_bins<MODE, 3><<<grid, kBinNT, 0, st>>>(a); break;
+    case 1: return launch_bins_mj<MODE, 1>(a, st);
+    case 2: return launch_bins_mj<MODE, 2>(a, st);
+    default: return launch_bins_mj<MODE, 3>(a, st);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace f128
@@ -398,6 +479,9 @@ cudaError_t launch_bins_mode(const VideoArgs& a, cudaStream_t st) {
 size_t video_frames_smem_bytes() { return ((size_t)f128::H * f128::P + f128::H) * sizeof(float2); }
 int video_max_T() { return f128::kVidMaxT; }
 int video_bin_blocks() { return f128::OM / f128::kBinTile; }
+size_t video_bins_smem_bytes(int J, int T) {
+  return (J == 1 ? f128::bins_smem_floats<1>(T) : J == 2 ? f128::bins_smem_floats<2>(T) : f128::bins_smem_floats<3>(T)) * sizeof(float);
+}
 
 cudaError_t launch_video_frames(const VideoArgs& a, int mode, int G, cudaStream_t st) {
   switch (mode) {
