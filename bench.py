@@ -242,8 +242,9 @@ UNEVEN_SIDES = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
 def measure_extensions(csc, torch, dev, hbm_peak):
     """The spec extensions, each on its own workload, device-timed with CUDA events:
     uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
-    replay), unroll32 (reverse mode through 20 unrolled iterations), mixed128 (the benchmark step in
-    the mixed-precision mode, tensor-core Gram)."""
+    replay), unroll32 (reverse mode through 20 unrolled iterations), video3d (higher-order coding of an
+    RGB video with 3-D transforms), mixed128 (the benchmark step in the mixed-precision mode,
+    tensor-core Gram)."""
     from paper_1709_09479_gb300 import autograd as ag
     from paper_1709_09479_gb300 import inputs
     out = {}
@@ -318,6 +319,32 @@ def measure_extensions(csc, torch, dev, hbm_peak):
                                    "checkpoints every 5, loss mean((D z_T - y)^2)",
                        "forward_ms": fms / 3, "forward_backward_ms": tms / 3, "loss": float(loss.detach())}
     del xu, yu, du
+
+    # --- video3d: RGB video, 3 x 32 frames x 128x128, K=64 colour filters 5x11x11, 3-D transforms ----
+    Jv, Tv, Kv, ftv, sv_ = 3, 32, 64, 5, 11
+    xv = torch.from_numpy(inputs.powerlaw_field(4, 1, Jv, (Tv, 128, 128)).astype(np.float32)).to(dev)
+    dvv = torch.from_numpy(inputs.unit_filters(40, Kv, Jv, (ftv, sv_, sv_)).astype(np.float32)).to(dev)
+    vv = torch.zeros((1, Kv, Tv, 128, 128), device=dev)
+    zv = torch.empty_like(vv)
+    with csc.Solver(J=Jv, K=Kv, fs=(sv_, sv_), ft=ftv, dims=(Tv, 128, 128), n_images=1, beta=0.5, rho=0.1) as sv:
+        sv.code(xv, dvv, vv, zv, 3)
+        torch.cuda.synchronize()
+        sv.timing_read()
+        sv.timing_enable(True)
+        e0, e1 = ev(), ev()
+        e0.record()
+        sv.code(xv, dvv, vv, zv, 20)
+        e1.record()
+        torch.cuda.synchronize()
+        tm = sv.timing_read()
+    it_s = tm["sweep_ms"] / max(tm["sweep_launches"], 1) / 1e3
+    alg = 8.0 * Kv * Tv * 128 * 128 + 8.0 * Jv * Tv * 128 * 65
+    out["video3d"] = {"workload": "1 RGB video 3 x 32 x 128x128 (1/f^2 over space and time, seed 4), K=64 colour "
+                                  "filters 5x11x11 (seed 40), beta=0.5, rho=0.1, 3-D transforms, float32",
+                      "coding_iters_per_s": 1.0 / it_s, "iter_us": it_s * 1e6,
+                      "ms_per_call_of_20_iters": e0.elapsed_time(e1), "algorithmic_bytes_per_iter": alg,
+                      "hbm_frac": alg / it_s / 1e9 / hbm_peak}
+    del xv, dvv, vv, zv
 
     # --- mixed128: the benchmark step with bf16 contractions and the tensor-core Gram ---------------
     w = WORKLOAD

@@ -102,3 +102,15 @@ def test_video_rejects_unsupported_shapes(csc):
                  np.zeros((2, 1, 3, 3, 3), np.float32), np.full(2, 0.5), 1)
     assert e.value.status == 8
     sv.close()
+
+
+def test_video_full_size_matches_oracle(csc):
+    """The RGB video workload's full size (3 x 32 x 128 x 128, K = 64 filters 5 x 11 x 11), two ADMM
+    iterations, element by element against the oracle."""
+    N, K, J, T, ft, s, beta, rho = 1, 64, 3, 32, 5, 11, 0.5, 0.1
+    x, d = problem(4, N, K, J, T, ft, s)
+    v_o, z_o = O.code_admm(x, d, beta, rho, 2)
+    v_g, z_g = run_gpu(csc, x, d, beta, rho, 2)
+    assert np.count_nonzero(z_o) > 0
+    assert rel(v_g, v_o) <= REL_TOL
+    assert rel(z_g, z_o) <= REL_TOL
