@@ -42,8 +42,9 @@ __device__ __forceinline__ long long pair_index(int k, int kp, int K) {
 }
 
 __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
-  __shared__ float2 As[kGramT][kGramF];
-  __shared__ float2 Bs[kGramT][kGramF];
+  // double-buffered: the next image's tiles are loaded into registers while this image's are used
+  __shared__ float2 As[2][kGramT][kGramF];
+  __shared__ float2 Bs[2][kGramT][kGramF];
   // tile pair (ti <= tj) from blockIdx.x
   int ti = 0, rem = blockIdx.x;
   while (rem >= a.ntile - ti) { rem -= a.ntile - ti; ++ti; }
@@ -52,33 +53,53 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
   const int f = threadIdx.x % kGramF;
   const int grp = threadIdx.x / kGramF;   // 0..7
   const int kq = grp % 4, kpq = grp / 4;  // k rows 4kq..4kq+3, k' rows 8kpq..8kpq+7
+  // this thread's share of a tile pair: elements e = threadIdx.x + 256 u of 16 x 32
+  constexpr int kLd = kGramT * kGramF / kGramNT;   // 2
+  int lr[kLd], lf[kLd];
+  bool la[kLd], lb[kLd];
+#pragma unroll
+  for (int u = 0; u < kLd; ++u) {
+    const int e = threadIdx.x + u * kGramNT;
+    lr[u] = e / kGramF;
+    lf[u] = e % kGramF;
+    const int oo = o0 + lf[u];
+    la[u] = (ti * kGramT + lr[u] < a.K) && oo < a.Omega;
+    lb[u] = (tj * kGramT + lr[u] < a.K) && oo < a.Omega;
+  }
+  auto load = [&](int n, float2 (&ra)[kLd], float2 (&rb)[kLd]) {
+#pragma unroll
+    for (int u = 0; u < kLd; ++u) {
+      const size_t base = (size_t)n * a.K;
+      ra[u] = la[u] ? __ldg(a.zhat + (base + ti * kGramT + lr[u]) * a.Omega + o0 + lf[u]) : make_float2(0.f, 0.f);
+      rb[u] = lb[u] ? __ldg(a.zhat + (base + tj * kGramT + lr[u]) * a.Omega + o0 + lf[u]) : make_float2(0.f, 0.f);
+    }
+  };
   float2 acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
   const int o = o0 + f;
+  float2 ra[kLd], rb[kLd];
+  load(0, ra, rb);
   for (int n = 0; n < a.N; ++n) {
-    for (int e = threadIdx.x; e < kGramT * kGramF; e += kGramNT) {
-      const int r = e / kGramF, ff = e % kGramF;
-      const int oo = o0 + ff;
-      const int ka = ti * kGramT + r, kb = tj * kGramT + r;
-      As[r][ff] = (ka < a.K && oo < a.Omega) ? a.zhat[((size_t)n * a.K + ka) * a.Omega + oo]
-                                              : make_float2(0.f, 0.f);
-      Bs[r][ff] = (kb < a.K && oo < a.Omega) ? a.zhat[((size_t)n * a.K + kb) * a.Omega + oo]
-                                              : make_float2(0.f, 0.f);
+    const int bf = n & 1;
+#pragma unroll
+    for (int u = 0; u < kLd; ++u) {
+      As[bf][lr[u]][lf[u]] = ra[u];
+      Bs[bf][lr[u]][lf[u]] = rb[u];
     }
     __syncthreads();
+    if (n + 1 < a.N) load(n + 1, ra, rb);
     float2 av[4], bv[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) av[i] = As[4 * kq + i][f];
+    for (int i = 0; i < 4; ++i) av[i] = As[bf][4 * kq + i][f];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) bv[jj] = Bs[8 * kpq + jj][f];
+    for (int jj = 0; jj < 8; ++jj) bv[jj] = Bs[bf][8 * kpq + jj][f];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) acc[i][jj] = cfmac(av[i], bv[jj], acc[i][jj]);
-    __syncthreads();
   }
   if (o >= a.Omega) return;
 #pragma unroll
@@ -217,7 +238,7 @@ CSC_HD CgSmem cg_smem_layout(int K, int J, int S2, int NF, int fh, int fw, int L
   L.cch = o;  o += chat_smem ? 2 * (size_t)L.nb * (K * (K + 1) / 2) : 0;
   L.pp = o;   o += (size_t)K * J * S2;
   L.own = o;  o += 4 * (size_t)L.nown * J * S2;   // x, r, b, z of the CTA's filters
-  L.mloc = o; o += minv ? (size_t)S2 * S2 + S2 : 0;
+  L.mloc = o; o += minv ? (size_t)S2 * S2 + 2 * S2 : 0;
   L.total_floats = o;
   return L;
 }
@@ -615,7 +636,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   float* orr = ox + (size_t)Ls.nown * JS;
   float* ob = orr + (size_t)Ls.nown * JS;
   float* oz = ob + (size_t)Ls.nown * JS;
-  float* mloc = smf + Ls.mloc;                   // [S2][S2] (+ [S2] during the inversion)
+  float* mloc = smf + Ls.mloc;                   // [S2][S2] (+ 2 [S2] during the inversion)
   const int nown = (blockIdx.x < K) ? (K - 1 - blockIdx.x) / G + 1 : 0;
   const bool own_one = (G >= K) && a.minv;       // at most one filter per CTA: keep its inverse
   const int La = a.La, Lb = a.Lb, ctr = (a.fh - 1) * Lb + (a.fw - 1);   // lag tau = 0
@@ -656,7 +677,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   // (the mu at entry; the preconditioner need not track the later mu updates exactly)
   if (a.minv) {
     float* A = mloc;                    // [S2][S2]
-    float* colv = A + (size_t)S2 * S2;  // [S2]
+    float* colv = A + (size_t)S2 * S2;  // [S2] pivot column, then [S2] pivot row
     const int fh = a.fh, fw = a.fw;
     for (int i = 0; i < nown; ++i) {
       const int k = blockIdx.x + i * G;
@@ -670,22 +691,26 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         A[e] = act ? C[(qa - qa2 + fh - 1) * Lb + (qb - qb2 + fw - 1)] + tm * diag : diag;
       }
       __syncthreads();
-      // in-place Gauss-Jordan inversion (symmetric positive definite: no pivoting)
+      // in-place Gauss-Jordan inversion (symmetric positive definite: no pivoting); per pivot the
+      // pivot column and row are copied out, then every thread updates its elements
+      float* prow = colv + S2;
       for (int pv = 0; pv < S2; ++pv) {
-        for (int r = threadIdx.x; r < S2; r += NT) colv[r] = A[(size_t)r * S2 + pv];
+        for (int r = threadIdx.x; r < S2; r += NT) {
+          colv[r] = A[(size_t)r * S2 + pv];
+          prow[r] = A[(size_t)pv * S2 + r];
+        }
         __syncthreads();
         const float inv = 1.f / colv[pv];
-        for (int j = threadIdx.x; j < S2; j += NT)
-          if (j != pv) A[(size_t)pv * S2 + j] *= inv;
-        __syncthreads();
-        for (int r = threadIdx.x >> 5; r < S2; r += NT / 32) {
-          if (r == pv) continue;
-          const float ci = colv[r];
-          float* row = A + (size_t)r * S2;
-          const float* prow = A + (size_t)pv * S2;
-          for (int j = threadIdx.x & 31; j < S2; j += 32) row[j] = (j != pv) ? fmaf(-ci, prow[j], row[j]) : -ci * inv;
+        int i = threadIdx.x / S2, j = threadIdx.x - (threadIdx.x / S2) * S2;
+        const int di = NT / S2, dj = NT - (NT / S2) * S2;
+        for (int e = threadIdx.x; e < S2 * S2; e += NT) {
+          float* el = A + (size_t)i * S2 + j;
+          if (i == pv) *el = (j == pv) ? inv : prow[j] * inv;
+          else *el = (j == pv) ? -colv[i] * inv : fmaf(-colv[i] * inv, prow[j], *el);
+          i += di;
+          j += dj;
+          if (j >= S2) { j -= S2; ++i; }
         }
-        if (threadIdx.x == 0) A[(size_t)pv * S2 + pv] = inv;
         __syncthreads();
       }
       if (!own_one) {
