@@ -113,7 +113,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
@@ -441,6 +441,8 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
        cudaMalloc((void**)&c->dhatp, (size_t)p.K * Om * sizeof(float2)) != cudaSuccess) ||
       (p.precision == CSC_MIXED_BF16 &&
        cudaMalloc((void**)&c->dhat16, (size_t)p.K * p.J * Om * sizeof(__nv_bfloat162)) != cudaSuccess) ||
+      (p.precision == CSC_MIXED_BF16 && g.ct_id == 1 && p.J == 1 &&
+       cudaMalloc((void**)&c->dhatp16, (size_t)p.K * Om * sizeof(__nv_bfloat162)) != cudaSuccess) ||
       cudaMalloc((void**)&c->xhat, (size_t)tmp.N * p.J * Om * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->pdiag, Om * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&c->pmat, Om * p.J * p.J * sizeof(float2)) != cudaSuccess ||
@@ -768,6 +770,11 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     if (e == cudaSuccess) e = launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat);
     if (e == cudaSuccess && c->p.precision == CSC_MIXED_BF16) {
       e = launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->K * c->J * c->g.Omega);
+      // and the copy in the thread order of the fused 128 x 128 sweep
+      if (e == cudaSuccess && c->dhatp16) {
+        e = launch_to_bf16(*c, c->dhatp, c->dhatp16, (size_t)c->K * c->g.Omega);
+        c->launches += 1;
+      }
       c->launches += 1;
     }
     if (e == cudaSuccess) e = launch_sweep(*c, kPrologue, nullptr, c->part[0], vd, nullptr);

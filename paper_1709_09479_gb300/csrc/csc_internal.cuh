@@ -160,6 +160,7 @@ struct Ctx {
   float2* tw = nullptr;
   float2* dhat = nullptr;
   float2* dhatp = nullptr;            // 128 x 128, J = 1: d_hat in the thread order of the fused sweep
+  __nv_bfloat162* dhatp16 = nullptr;  // its bf16 copy (mixed precision)
   __nv_bfloat162* dhat16 = nullptr;   // mixed precision copy of dhat
   float2* xhat = nullptr;
   float* pdiag = nullptr;

@@ -21,8 +21,14 @@
 namespace csc {
 namespace f128 {
 
-template <int MODE>
-__global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2* __restrict__ dhatp) {
+// a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
+__device__ __forceinline__ float2 to_bf16(float2 v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
+
+// BF: mixed precision. d_hat comes in bfloat16 (dhatp16, thread-major) and both operands of every
+// complex product of the contractions are bfloat16 values, accumulated in float32.
+template <int MODE, bool BF>
+__global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2* __restrict__ dhatp,
+                                                      const __nv_bfloat162* __restrict__ dhatp16) {
   extern __shared__ float2 sm[];
   constexpr bool kLam = (MODE == kIter || MODE == kLast);
   constexpr bool kAcc = (MODE != kLast);
@@ -79,6 +85,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
     for (int k = kb; k < ke; ++k) {
       const size_t map = (size_t)n * a.K + k;
       const float2* dk = dhatp + (size_t)k * OM;
+      const __nv_bfloat162* dk16 = BF ? dhatp16 + (size_t)k * OM : nullptr;
+      auto dval = [&](int p) { return BF ? __bfloat1622float2(dk16[p]) : __ldg(dk + p); };
       if (threadIdx.x < 4 && (long long)map + 1 < m1) {
         const float* nxt = (MODE == kObjective) ? a.z + (map + 1) * D : a.v + (map + 1) * D;
         prefetch_l2_f128(nxt + threadIdx.x * (D / 4), (unsigned)D);
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         // w_hat = conj(d_hat_k) lambda_hat at this thread's bins, inverse split, first row pass
         inv_rows1(buf, T, R, [&](int s) {
           const int p = slot_pos(s, t);
-          return cmulc(lam[p], dk[p]);
+          return cmulc(BF ? to_bf16(lam[p]) : lam[p], dval(p));
         });
         __syncthreads();
         inv_rows2(buf, R);
@@ -157,15 +165,15 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         // second forward row pass, split, accumulate d_hat_k u_hat (d_hat loads issued first)
         float2 dv[18];
 #pragma unroll
-        for (int s = 0; s < 16; ++s) dv[s] = __ldg(dk + s * NT + t);
+        for (int s = 0; s < 16; ++s) dv[s] = dval(s * NT + t);
         dv[16] = dv[17] = make_float2(0.f, 0.f);
         if (nyq) {
-          dv[16] = __ldg(dk + 16 * NT + t);
-          dv[17] = __ldg(dk + 16 * NT + NQ + t);
+          dv[16] = dval(16 * NT + t);
+          dv[17] = dval(16 * NT + NQ + t);
         }
         fwd_rows2_split(buf, T, R, [&](int s, float2 x) {
           const int p = slot_pos(s, t);
-          acc[p] = cfma(dv[s], x, acc[p]);
+          acc[p] = cfma(dv[s], BF ? to_bf16(x) : x, acc[p]);
         });
       }
     }
@@ -207,28 +215,30 @@ size_t smem_bytes(int mode) {
   return ((size_t)H * P + (lam ? OM : 0) + (acc ? OM : 0) + H) * sizeof(float2);
 }
 
-template <int MODE>
+template <int MODE, bool BF>
 cudaError_t launch_mode(const Ctx& c, const SweepArgs& a) {
-  auto kern = k_sweep_f128<MODE>;
+  auto kern = k_sweep_f128<MODE, BF>;
   const size_t smem = smem_bytes(MODE);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<c.G, NT, smem, c.stream>>>(a, c.dhatp);
+  kern<<<c.G, NT, smem, c.stream>>>(a, c.dhatp, c.dhatp16);
   return cudaGetLastError();
 }
 
 }  // namespace f128
 
 bool fused128_applies(const Ctx& c, const SweepArgs& a) {
-  return c.dhatp && c.g.ct_id == 1 && c.J == 1 && a.dhat16 == nullptr && a.vec4;
+  return c.dhatp && c.g.ct_id == 1 && c.J == 1 && a.vec4 && (a.dhat16 == nullptr || c.dhatp16 != nullptr);
 }
 
+// a.dhat16 set: mixed precision, with the context's thread-major bf16 copy of d_hat
 cudaError_t launch_sweep_fused128(const Ctx& c, int mode, const SweepArgs& a) {
+  const bool bf = a.dhat16 != nullptr && c.dhatp16 != nullptr;
   switch (mode) {
-    case kPrologue: return f128::launch_mode<kPrologue>(c, a);
-    case kIter: return f128::launch_mode<kIter>(c, a);
-    case kLast: return f128::launch_mode<kLast>(c, a);
-    default: return f128::launch_mode<kObjective>(c, a);
+    case kPrologue: return bf ? f128::launch_mode<kPrologue, true>(c, a) : f128::launch_mode<kPrologue, false>(c, a);
+    case kIter: return bf ? f128::launch_mode<kIter, true>(c, a) : f128::launch_mode<kIter, false>(c, a);
+    case kLast: return bf ? f128::launch_mode<kLast, true>(c, a) : f128::launch_mode<kLast, false>(c, a);
+    default: return f128::launch_mode<kObjective, false>(c, a);
   }
 }
 
