@@ -291,12 +291,13 @@ __device__ __forceinline__ void add_at(float (&vals)[N], int idx, float v) {
     if (i == idx) vals[i] += v;
 }
 
+// 64-bit words exchanged between CTAs: relaxed, GPU scope (single-copy atomic; no fences implied)
 __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -375,59 +376,71 @@ __device__ bool gather(const unsigned long long* slots, int G, int n, unsigned e
   return s_fail == 0;
 }
 
-// Waits until this thread's words carry epoch ep: the exchange's slot words (G CTAs x nw, thread t
-// polls words t and t + NT; values parked in vals, [G][nw] floats of shared memory) when slots
-// is not null, and the data words t + u NT < ndata (left in wd[u]; the value is the low half).
-// All pending words are loaded together on every pass. false when a CTA flagged an error or the
-// wait ran out (flag set).
+// Waits until this block's words carry epoch ep, in two phases: first the exchange's slot words
+// (G CTAs x nw; thread t polls words t and t + NT, values parked in vals, [G][nw] floats of shared
+// memory), when slots is not null; after a block barrier the data words t + u NT < ndata (left in
+// wd[u]; the value is the low half), which the publishers wrote before their slot words and so are
+// almost always complete by then (any that are not are polled again). Must be called by the whole
+// block. false when a CTA flagged an error or the wait ran out (flag set).
 template <int NT, int U>
 __device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsigned ep, float* vals,
                            const unsigned long long* data, int ndata, unsigned long long (&wd)[U], int* err) {
-  const unsigned long long* sb = slots ? slots + (size_t)(ep & 1) * G * kSlotWords : nullptr;
-  const int nsw = slots ? G * nw : 0;
-  unsigned pend = 0;   // bit u: data word u pending; bits 30, 31: slot words
+  __shared__ int s_bad;
+  const long long t0 = clock64();
+  bool ok = true;
+  if (slots) {
+    if (threadIdx.x == 0) s_bad = 0;
+    const unsigned long long* sb = slots + (size_t)(ep & 1) * G * kSlotWords;
+    const int nsw = G * nw;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = threadIdx.x + u * NT;
+      if (i < nsw) {
+        const unsigned long long* wp = sb + (size_t)(i / nw) * kSlotWords + i % nw;
+        unsigned long long w = ld_volatile_u64(wp);
+        while ((unsigned)(w >> 32) != ep) {
+          if (*(volatile int*)err || clock64() - t0 > kSpinLimit) { ok = false; break; }
+          w = ld_volatile_u64(wp);
+        }
+        vals[i] = __uint_as_float((unsigned)w);
+      }
+    }
+    if (!ok) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {
+      if (!*(volatile int*)err) atomicExch(err, (int)CSC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  unsigned pend = 0;
 #pragma unroll
   for (int u = 0; u < U; ++u)
     if ((int)threadIdx.x + u * NT < ndata) pend |= 1u << u;
-  if ((int)threadIdx.x < nsw) pend |= 1u << 30;
-  if ((int)threadIdx.x + NT < nsw) pend |= 1u << 31;
-  const long long t0 = clock64();
-  while (true) {
+  while (pend) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (pend & (1u << u)) wd[u] = ld_volatile_u64(data + threadIdx.x + u * NT);
-    unsigned long long ws0 = 0, ws1 = 0;
-    if (pend & (1u << 30)) ws0 = ld_volatile_u64(sb + (size_t)(threadIdx.x / nw) * kSlotWords + threadIdx.x % nw);
-    if (pend & (1u << 31)) {
-      const int i = threadIdx.x + NT;
-      ws1 = ld_volatile_u64(sb + (size_t)(i / nw) * kSlotWords + i % nw);
-    }
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if ((pend & (1u << u)) && (unsigned)(wd[u] >> 32) == ep) pend &= ~(1u << u);
-    if ((pend & (1u << 30)) && (unsigned)(ws0 >> 32) == ep) {
-      vals[threadIdx.x] = __uint_as_float((unsigned)ws0);
-      pend &= ~(1u << 30);
-    }
-    if ((pend & (1u << 31)) && (unsigned)(ws1 >> 32) == ep) {
-      vals[threadIdx.x + NT] = __uint_as_float((unsigned)ws1);
-      pend &= ~(1u << 31);
-    }
-    if (!pend) return true;
+    if (!pend) break;
     if (*(volatile int*)err) return false;
     if (clock64() - t0 > kSpinLimit) {
       atomicExch(err, (int)CSC_ERR_TIMEOUT);
       return false;
     }
   }
+  return true;
 }
 
 __device__ __forceinline__ float word_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
 
 // totals[i] = sum over CTAs in CTA order of vals[b * nw + i], i < n (warp 0, float64). Call after a
-// barrier that follows wait_words; ends with a barrier.
-template <int NT>
-__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, double* totals) {
+// barrier that follows wait_words; ends with a barrier. then() runs on thread 0 once the totals are
+// known: the scalars of the iteration are formed there, in float64, and broadcast through shared
+// memory (the device's float64 rate is low).
+template <int NT, class F>
+__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, double* totals, F then) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = 0; i < n; ++i) {
@@ -436,6 +449,7 @@ __device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int 
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       if (lane == 0) totals[i] = v;
     }
+    if (lane == 0) then();
   }
   __syncthreads();
 }
@@ -618,6 +632,10 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   __shared__ int s_fail;
   if (threadIdx.x == 0) s_fail = 0;
   __shared__ float s_twomu[8], s_jac[8];
+  // scalars of the CG iteration, formed by thread 0 in float64
+  __shared__ double s_rz[kMaxJ], s_rr[kMaxJ], s_bb[kMaxJ];
+  __shared__ float s_alpha[kMaxJ], s_beta[kMaxJ];
+  __shared__ int s_done[kMaxJ], s_all;
   __shared__ int s_act[8];
   constexpr int J = JT;
   const int K = a.K, S2 = a.S2, G = a.G;
@@ -780,8 +798,6 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       block_reduce_to0<NT>(w3, scratch);
       publish<3 * J>(a.slots, G, w3, ++ep);
     }
-    double rz[J], rr[J], bb[J];
-    bool done[J];
     // all z (and the sums) of exchange ep: p = z
     for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
       unsigned long long zv[UZ];
@@ -794,23 +810,20 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       for (int u = 0; u < UZ; ++u)
         if (c0 + (int)threadIdx.x + u * NT < nz) pp[c0 + threadIdx.x + u * NT] = word_value(zv[u]);
     }
-    sum_slots<NT>(gvals, G, 3 * J, 3 * J, tot);
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      rz[j] = tot[j];
-      rr[j] = tot[J + j];
-      bb[j] = tot[2 * J + j];
-      done[j] = false;
-    }
+    sum_slots<NT>(gvals, G, 3 * J, 3 * J, tot, [&]() {
+      int all = 1;
+      for (int j = 0; j < J; ++j) {
+        s_rz[j] = tot[j];
+        s_rr[j] = tot[J + j];
+        s_bb[j] = tot[2 * J + j];
+        s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+        all = all && s_done[j];
+      }
+      s_all = all;
+    });
     int it = 0;
     for (; it < a.cg_max; ++it) {
-      bool all = true;
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        done[j] = done[j] || !(rr[j] > a.tol2 * bb[j]) || !(rz[j] > 0.0);
-        all = all && done[j];
-      }
-      if (all) break;   // the same totals on every thread of every CTA
+      if (s_all) break;   // the same totals in every CTA
       // ---- A p at this CTA's bins, p . A p (exchange A) -----------------------------------
       {
         float pa[J];
@@ -833,7 +846,6 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         float w2[2 * J];   // r . z, r . r
 #pragma unroll
         for (int u = 0; u < 2 * J; ++u) w2[u] = 0.f;
-        float alpha[J];
         for (int i = 0; i < nown + (nown == 0 ? 1 : 0); ++i) {
           const int k = blockIdx.x + i * G;
           const bool has = i < nown;
@@ -847,14 +859,13 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             if (has && (int)threadIdx.x + u * NT < nyw) yhf[threadIdx.x + u * NT] = word_value(yv[u]);
           __syncthreads();
           if (s_fail) return;
-          if (i == 0) {
-            sum_slots<NT>(gvals, G, J, J, tot);
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-              const double pap = tot[j];
-              alpha[j] = (!done[j] && pap > 0.0) ? (float)(rz[j] / pap) : 0.f;
-            }
-          }
+          if (i == 0)
+            sum_slots<NT>(gvals, G, J, J, tot, [&]() {
+              for (int j = 0; j < J; ++j) {
+                const double pap = tot[j];
+                s_alpha[j] = (!s_done[j] && pap > 0.0) ? (float)(s_rz[j] / pap) : 0.f;
+              }
+            });
           if (!has) continue;
           if (!s_act[i]) {   // z_k stays 0, but its words carry every exchange's epoch
             for (int o = threadIdx.x; o < JS; o += NT) st_volatile_u64(a.zw + (size_t)k * JS + o, tag(0.f, ep + 1));
@@ -865,10 +876,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           product_taps<NT>(a, yh, sc, twa, twb, yk);
           for (int o = threadIdx.x; o < JS; o += NT) {
             const int j = J == 1 ? 0 : o / S2;
-            float al = alpha[0];
-#pragma unroll
-            for (int jj = 1; jj < J; ++jj)
-              if (jj == j) al = alpha[jj];
+            const float al = s_alpha[j];
             const float pv = pp[(size_t)k * JS + o];
             const float apv = fmaf(s_twomu[i], pv, yk[o]);
             ox[(size_t)i * JS + o] = fmaf(al, pv, ox[(size_t)i * JS + o]);
@@ -883,7 +891,6 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         publish<2 * J>(a.slots, G, w2, ++ep);
       }
       // ---- p = z + beta p: every CTA keeps the whole search direction ------------------------
-      double beta[J];
       for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
         unsigned long long zv[UZ];
         if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 2 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT),
@@ -891,27 +898,27 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           s_fail = 1;
         __syncthreads();
         if (s_fail) return;
-        if (c0 == 0) {
-          sum_slots<NT>(gvals, G, 2 * J, 2 * J, tot);
-#pragma unroll
-          for (int j = 0; j < J; ++j) {
-            if (!done[j]) {
-              beta[j] = rz[j] > 0.0 ? tot[j] / rz[j] : 0.0;
-              rz[j] = tot[j];
-              rr[j] = tot[J + j];
-            } else {
-              beta[j] = 0.0;
+        if (c0 == 0)
+          sum_slots<NT>(gvals, G, 2 * J, 2 * J, tot, [&]() {
+            int all = 1;
+            for (int j = 0; j < J; ++j) {
+              if (!s_done[j]) {
+                s_beta[j] = s_rz[j] > 0.0 ? (float)(tot[j] / s_rz[j]) : 0.f;
+                s_rz[j] = tot[j];
+                s_rr[j] = tot[J + j];
+                s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+              } else {
+                s_beta[j] = 0.f;
+              }
+              all = all && s_done[j];
             }
-          }
-        }
+            s_all = all;
+          });
 #pragma unroll
         for (int u = 0; u < UZ; ++u) {
           const int idx = c0 + threadIdx.x + u * NT;
           if (idx < nz) {
-            float bt = (float)beta[0];
-#pragma unroll
-            for (int jj = 1; jj < J; ++jj)
-              if (jj == (idx % JS) / S2) bt = (float)beta[jj];
+            const float bt = s_beta[J == 1 ? 0 : (idx % JS) / S2];
             pp[idx] = fmaf(bt, pp[idx], word_value(zv[u]));
           }
         }
