@@ -300,7 +300,16 @@ CSC_D void stages_ct(float2* buf, int lstride, int es, const float2* tw) {
   }
 }
 
-// run-time radices (sizes without a fixed-size instantiation): dispatch each stage to its radix
+// one run-time stage as a call of its own: each radix gets its own register allocation (inlined
+// together behind a switch they share one, and spill)
+template <int R, bool INV, int NT, int IPT>
+__device__ __noinline__ void fft_stage_rt(float2* buf, int nlines, int lstride, int es, int n, int Ns,
+                                          const float2* tw) {
+  fft_stage<R, INV, NT, IPT>(buf, nlines, lstride, es, n, Ns, tw);
+}
+
+// run-time radices (sizes without a fixed-size instantiation): dispatch each stage to its radix,
+// at most 16 complex values per thread and round
 template <bool INV, int NT>
 __device__ __noinline__ void stages_rt(float2* buf, int nlines, int lstride, int es, int n,
                                        const Radices& rr, const float2* tw) {
@@ -308,13 +317,13 @@ __device__ __noinline__ void stages_rt(float2* buf, int nlines, int lstride, int
   for (int s = 0; s < rr.n_st; ++s) {
     const int R = rr.r[s];
     switch (R) {
-      case 2: fft_stage<2, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 3: fft_stage<3, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 4: fft_stage<4, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 5: fft_stage<5, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 7: fft_stage<7, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 8: fft_stage<8, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
-      case 16: fft_stage<16, INV, NT>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 2: fft_stage_rt<2, INV, NT, 8>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 3: fft_stage_rt<3, INV, NT, 5>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 4: fft_stage_rt<4, INV, NT, 4>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 5: fft_stage_rt<5, INV, NT, 3>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 7: fft_stage_rt<7, INV, NT, 2>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 8: fft_stage_rt<8, INV, NT, 2>(buf, nlines, lstride, es, n, ns, tw); break;
+      case 16: fft_stage_rt<16, INV, NT, 1>(buf, nlines, lstride, es, n, ns, tw); break;
       default: break;   // host planning rejects other radices
     }
     ns *= R;
@@ -482,7 +491,7 @@ CSC_D void pack_dc_nyquist(const G& g, float2* buf) {
 }
 
 template <class G, int NT>
-CSC_FFT2_ATTR void rfft2(const G g, float2* buf, const Twiddles tw) {
+CSC_FFT2_ATTR void rfft2(const G& g, float2* buf, const Twiddles tw) {
   g.template rows<false, NT>(buf, tw.row);
   split_rows_forward<G, NT>(g, buf, tw.split);
   g.template cols<false, NT>(buf, tw.col);
@@ -491,7 +500,7 @@ CSC_FFT2_ATTR void rfft2(const G g, float2* buf, const Twiddles tw) {
 
 // Inverse (unnormalised, result scaled by D = H*W): half spectrum -> real map.
 template <class G, int NT>
-CSC_FFT2_ATTR void irfft2(const G g, float2* buf, const Twiddles tw) {
+CSC_FFT2_ATTR void irfft2(const G& g, float2* buf, const Twiddles tw) {
   pack_dc_nyquist<G, NT>(g, buf);
   g.template cols<true, NT>(buf, tw.col);
   split_rows_inverse<G, NT>(g, buf, tw.split);

@@ -33,14 +33,16 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_uneven(UnevenArgs a) {
   const float beta = a.beta;
   double l1 = 0.0;
   int cur_cls = -1;
-  GeoRT g;
+  // the current size class's plan lives in shared memory: the transforms read it by reference
+  __shared__ GeoRT g;
   Twiddles tw;
 
   for (long long n = m0 / a.K; n * a.K < m1; ++n) {
     const UImage im = a.img[n];
     if (im.cls != cur_cls) {
       __syncthreads();
-      g = a.cls[im.cls].g;
+      if (threadIdx.x == 0) g = a.cls[im.cls].g;
+      __syncthreads();
       tw = stage_twiddles<GeoRT, NT>(g, tws, a.tw + a.cls[im.cls].tw);
       cur_cls = im.cls;
       __syncthreads();
