@@ -188,9 +188,10 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def time_to_target(csc, torch, dev):
+def time_to_target(csc, torch, dev, precision=None, graph=False):
     """Rounds of Algorithm 1 on the 10-image sparse workload until the objective is within 1e-4
-    relative of the float64 oracle's final objective; then the wall time of that many rounds."""
+    relative of the float64 oracle's final objective; then the wall time of that many rounds
+    (precision: CSC_FP32 or CSC_MIXED_BF16; graph: CUDA-graph replay of the coding calls)."""
     ref_path = os.path.join(ROOT, "tests", "golden", "sparse10_oracle.json")
     if not os.path.exists(ref_path):
         return None
@@ -203,7 +204,9 @@ def time_to_target(csc, torch, dev):
     x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
     d0 = torch.from_numpy(inputs.unit_filters(c["dict_seed"], c["K"], 1, (c["s"], c["s"])).astype(np.float32)).to(dev)
     sv = csc.Solver(J=1, K=c["K"], fs=(c["s"], c["s"]), dims=(c["H"], c["W"]), n_images=c["N"], beta=c["beta"],
-                    rho=c["rho"], cg_max=400, cg_tol=1e-6)
+                    rho=c["rho"], cg_max=400, cg_tol=1e-6,
+                    precision=csc.CSC_FP32 if precision is None else precision,
+                    flags=csc.CSC_FLAG_GRAPH if graph else 0)
 
     def rounds(n, log):
         d = d0.clone()
@@ -457,6 +460,10 @@ def run_ours(args):
     traffic = profiled_traffic()
 
     ttt = time_to_target(csc, torch, dev) if rank == 0 else None
+    if ttt is not None:
+        # the mixed-precision form (bf16 contractions, tensor-core Gram, CUDA-graph replay of coding)
+        mixed = time_to_target(csc, torch, dev, precision=csc.CSC_MIXED_BF16, graph=True)
+        ttt["mixed_graph"] = {k: mixed[k] for k in ("f_gpu_final", "rel_gap_final", "rounds", "seconds")}
     sv.close()
     del v, z
     ext = measure_extensions(csc, torch, dev, peaks()[0]) if (rank == 0 and not args.no_extensions) else None
