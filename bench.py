@@ -53,7 +53,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "sweep128.cu"):
+    for f in ("fft.cuh", "f128_common.cuh", "sweep128.cu"):
         h.update(open(os.path.join(ROOT, "paper_1709_09479_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
