@@ -34,8 +34,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
   constexpr bool kAcc = (MODE != kLast);
   float2* buf = sm;                                   // [128][P]
   float2* lam = buf + H * P;                          // [OM] thread-major
-  float2* acc = lam + (kLam ? OM : 0);                // [OM] thread-major
-  float2* T = acc + (kAcc ? OM : 0);                  // [128] exp(-2 pi i m / 128)
+  float2* T = lam + (kLam ? OM : 0);                  // [128] exp(-2 pi i m / 128)
   const int t = threadIdx.x;
   for (int i = t; i < H; i += NT) T[i] = a.tw[W / 2 + i];
 
@@ -73,14 +72,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         if (ls) ls[o] = l;
       }
     }
-    if (kAcc) {
+    // sum_k d_hat_k u_hat_k of this image at the thread's 16 (+2) bins, in registers
+    float2 acc[18];
 #pragma unroll
-      for (int s = 0; s < 16; ++s) acc[s * NT + t] = make_float2(0.f, 0.f);
-      if (nyq) {
-        acc[16 * NT + t] = make_float2(0.f, 0.f);
-        acc[16 * NT + NQ + t] = make_float2(0.f, 0.f);
-      }
-    }
+    for (int s = 0; s < 18; ++s) acc[s] = make_float2(0.f, 0.f);
 
     for (int k = kb; k < ke; ++k) {
       const size_t map = (size_t)n * a.K + k;
@@ -113,7 +108,6 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         // zc[out_slot<16>(j)] is w at rows h = g + 8 j: state update (and codes on the last sweep)
         float* vw = (a.v_out ? a.v_out : a.v) + map * D;
         float* zk = (MODE == kLast && a.z) ? a.z + map * D : nullptr;
-        float2 u[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 w = zc[out_slot<16>(j)];
@@ -127,12 +121,12 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
               __stcs(reinterpret_cast<float2*>(zk + (g + 8 * j) * W + 2 * wc),
                      make_float2(a.rho * (clampb(vn.x, beta) - vn.x), a.rho * (clampb(vn.y, beta) - vn.y)));
           } else {
-            u[j] = make_float2(2.f * clampb(vn.x, beta) - vn.x, 2.f * clampb(vn.y, beta) - vn.y);
+            vv[j] = make_float2(2.f * clampb(vn.x, beta) - vn.x, 2.f * clampb(vn.y, beta) - vn.y);   // u
           }
         }
         if (kAcc) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) zc[j] = u[j];
+          for (int j = 0; j < 16; ++j) zc[j] = vv[j];
         }
       } else {
         // prologue: u = 2 clamp(v) - v; objective: the codes themselves. The previous map's row
@@ -171,20 +165,14 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
           dv[16] = dval(16 * NT + t);
           dv[17] = dval(16 * NT + NQ + t);
         }
-        fwd_rows2_split(buf, T, R, [&](int s, float2 x) {
-          const int p = slot_pos(s, t);
-          acc[p] = cfma(dv[s], BF ? to_bf16(x) : x, acc[p]);
-        });
+        fwd_rows2_split(buf, T, R, [&](int s, float2 x) { acc[s] = cfma(dv[s], BF ? to_bf16(x) : x, acc[s]); });
       }
     }
     if (kAcc) {
       float2* dst = a.part_out + (size_t)(cta + n) * OM;
-#pragma unroll 2
-      for (int s = 0; s < 18; ++s) {
-        if (s >= 16 && !nyq) break;
-        const int p = s < 16 ? s * NT + t : 16 * NT + (s - 16) * NQ + t;
-        dst[canonical_of(p)] = acc[p];
-      }
+#pragma unroll
+      for (int s = 0; s < 18; ++s)
+        if (s < 16 || nyq) dst[canonical_of(slot_pos(s, t))] = acc[s];
     }
   }
   if (MODE == kObjective) {
@@ -211,8 +199,7 @@ __global__ void k_permute_dhat(const float2* __restrict__ in, float2* __restrict
 
 size_t smem_bytes(int mode) {
   const bool lam = (mode == kIter || mode == kLast);
-  const bool acc = (mode != kLast);
-  return ((size_t)H * P + (lam ? OM : 0) + (acc ? OM : 0) + H) * sizeof(float2);
+  return ((size_t)H * P + (lam ? OM : 0) + H) * sizeof(float2);
 }
 
 template <int MODE, bool BF>
