@@ -15,7 +15,8 @@
 //   * 128 = 16 x 8 (columns) and 64 = 8 x 8 (rows) Cooley-Tukey passes; every pass writes its outputs
 //     over the shared-memory cells it read, so the callers need a block barrier between passes only.
 // Forward transforms are unnormalised with exp(-2 pi i / n); the inverse is unnormalised (result
-// scaled by 128 * 128). T[m] = exp(-2 pi i m / 128) in shared memory.
+// scaled by 128 * 128). Twiddles w^m = exp(-2 pi i m / 128) come from two shared-memory tables laid
+// out so that a pass reads the two twiddles of consecutive butterfly outputs in one 16-byte load.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -89,6 +90,34 @@ __device__ __forceinline__ Roles roles_of(int t) {
   return R;
 }
 
+// twiddle tables: q[16 a + m] = w^(a m mod 128) (a, m < 16: the pass twiddles), s[8 k + j] = w^(k + 8 j)
+// (k, j < 8: the real split of residue class k)
+constexpr int kTwQ = 256, kTwS = 64, kTwEntries = kTwQ + kTwS;
+struct Tw {
+  const float2* q;
+  const float2* s;
+};
+// fill the tables at tab (kTwEntries float2, 16-byte aligned) from w^m, m < 128, in global memory
+template <int NTH>
+__device__ __forceinline__ Tw build_tw(float2* tab, const float2* __restrict__ w128) {
+  for (int i = threadIdx.x; i < kTwEntries; i += NTH) {
+    const int m = i < kTwQ ? ((i >> 4) * (i & 15)) & 127 : ((i - kTwQ) >> 3) + 8 * ((i - kTwQ) & 7);
+    tab[i] = w128[m];
+  }
+  return Tw{tab, tab + kTwQ};
+}
+// entries 2 i and 2 i + 1 of a table row
+__device__ __forceinline__ void tw_pair(const float2* row, int i, float2& w0, float2& w1) {
+  const float4 v = reinterpret_cast<const float4*>(row)[i];
+  w0 = make_float2(v.x, v.y);
+  w1 = make_float2(v.z, v.w);
+}
+// the 8 entries of a table row into registers (four 16-byte loads)
+__device__ __forceinline__ void tw_row8(const float2* row, float2 (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tw_pair(row, i, w[2 * i], w[2 * i + 1]);
+}
+
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
 // pull `bytes` of the next map into L2 while this one is transformed
@@ -127,7 +156,7 @@ __device__ __forceinline__ float2 partner_y(const float2 (&p)[8], bool cls0) {
 // inverse split of the thread's bins (get(slot) -> X) and the first inverse row pass (8-point over
 // kw = class + 8 n1, twiddle conj w64^(class k1)), stored over the item's cells
 template <class GET>
-__device__ __forceinline__ void inv_rows1(float2* buf, const float2* T, const Roles& R, GET get) {
+__device__ __forceinline__ void inv_rows1(float2* buf, const Tw& T, const Roles& R, GET get) {
   const Items& it = R.it;
   float2 xa[8], xb[8], na = make_float2(0.f, 0.f), nb = make_float2(0.f, 0.f);
 #pragma unroll
@@ -139,14 +168,16 @@ __device__ __forceinline__ void inv_rows1(float2* buf, const float2* T, const Ro
     na = get(16);
     nb = get(17);
   }
-  float2 za[8], zb[8];
+  float2 za[8], zb[8], wa[8], wb[8];
+  tw_row8(T.s + 8 * it.kA, wa);
+  tw_row8(T.s + 8 * it.kB, wb);
   const bool sf = it.self, cls0 = R.cls0;
 #define CSC_F128_UNSPLIT(J)                                                                       \
   {                                                                                               \
     const float2 pa = sf ? partner<J>(xa, na, cls0) : partner<J>(xb, nb, cls0);                   \
     const float2 pb = sf ? partner<J>(xb, nb, cls0) : partner<J>(xa, na, cls0);                   \
-    za[J] = split_inv(xa[J], pa, T[it.kA + 8 * J]);                                               \
-    zb[J] = split_inv(xb[J], pb, T[it.kB + 8 * J]);                                               \
+    za[J] = split_inv(xa[J], pa, wa[J]);                                                          \
+    zb[J] = split_inv(xb[J], pb, wb[J]);                                                          \
   }
   CSC_F128_UNSPLIT(0) CSC_F128_UNSPLIT(1) CSC_F128_UNSPLIT(2) CSC_F128_UNSPLIT(3)
   CSC_F128_UNSPLIT(4) CSC_F128_UNSPLIT(5) CSC_F128_UNSPLIT(6) CSC_F128_UNSPLIT(7)
@@ -155,12 +186,14 @@ __device__ __forceinline__ void inv_rows1(float2* buf, const float2* T, const Ro
   dft8<true>(zb);
   float2* ra = buf + it.rowA * P + 8 * it.kA;
   float2* rb = buf + it.rowB * P + 8 * it.kB;
+  tw_row8(T.q + 16 * (2 * it.kA), wa);
+  tw_row8(T.q + 16 * (2 * it.kB), wb);
   ra[0] = za[0];
   rb[0] = zb[0];
 #pragma unroll
   for (int q = 1; q < 8; ++q) {
-    ra[q] = cmulc(za[q], T[(2 * it.kA * q) & 127]);
-    rb[q] = cmulc(zb[q], T[(2 * it.kB * q) & 127]);
+    ra[q] = cmulc(za[q], wa[q]);
+    rb[q] = cmulc(zb[q], wb[q]);
   }
 }
 
@@ -180,17 +213,18 @@ __device__ __forceinline__ void inv_rows2(float2* buf, const Roles& R) {
 }
 
 // first inverse column pass: column wc, kh = 16 n1 + n2 for n2 = g, g + 8
-__device__ __forceinline__ void inv_cols1(float2* buf, const float2* T, const Roles& R) {
+__device__ __forceinline__ void inv_cols1(float2* buf, const Tw& T, const Roles& R) {
 #pragma unroll
   for (int h2 = 0; h2 < 2; ++h2) {
     const int n2 = R.g + 8 * h2;
-    float2 y[8];
+    float2 y[8], w[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = buf[(16 * q + n2) * P + R.wc];
+    tw_row8(T.q + 16 * n2, w);
     dft8<true>(y);
     buf[n2 * P + R.wc] = y[0];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) buf[(16 * q + n2) * P + R.wc] = cmulc(y[q], T[(n2 * q) & 127]);
+    for (int q = 1; q < 8; ++q) buf[(16 * q + n2) * P + R.wc] = cmulc(y[q], w[q]);
   }
 }
 
@@ -203,11 +237,16 @@ __device__ __forceinline__ void inv_cols2(const float2* buf, const Roles& R, flo
 
 // first forward column pass from zc[j] = the map at rows 8 j + g (natural order): 16-point, twiddle
 // w128^(g k1), stored over the cells the second inverse column pass reads
-__device__ __forceinline__ void fwd_cols1(float2* buf, const float2* T, const Roles& R, float2 (&zc)[16]) {
+__device__ __forceinline__ void fwd_cols1(float2* buf, const Tw& T, const Roles& R, float2 (&zc)[16]) {
   dft16<false>(zc);
   buf[(16 * R.g) * P + R.wc] = zc[out_slot<16>(0)];
 #pragma unroll
-  for (int k1 = 1; k1 < 16; ++k1) buf[(16 * R.g + k1) * P + R.wc] = cmul(zc[out_slot<16>(k1)], T[(R.g * k1) & 127]);
+  for (int i = 0; i < 8; ++i) {
+    float2 w0, w1;
+    tw_pair(T.q + 16 * R.g, i, w0, w1);
+    if (i > 0) buf[(16 * R.g + 2 * i) * P + R.wc] = cmul(zc[out_slot<16>(2 * i)], w0);
+    buf[(16 * R.g + 2 * i + 1) * P + R.wc] = cmul(zc[out_slot<16>(2 * i + 1)], w1);
+  }
 }
 
 // second forward column pass: k1 = g, g + 8 -> canonical rows kh = k1 + 16 k2
@@ -225,24 +264,25 @@ __device__ __forceinline__ void fwd_cols2(float2* buf, const Roles& R) {
 }
 
 // first forward row pass: row r, n2 = c, c + 4; twiddle w64^(n2 k1)
-__device__ __forceinline__ void fwd_rows1(float2* buf, const float2* T, const Roles& R) {
+__device__ __forceinline__ void fwd_rows1(float2* buf, const Tw& T, const Roles& R) {
 #pragma unroll
   for (int h2 = 0; h2 < 2; ++h2) {
     const int n2 = R.c + 4 * h2;
     float2* row = buf + R.r * P;
-    float2 y[8];
+    float2 y[8], w[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = row[8 * q + n2];
+    tw_row8(T.q + 16 * (2 * n2), w);
     dft8<false>(y);
     row[n2] = y[0];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) row[8 * q + n2] = cmul(y[q], T[(2 * n2 * q) & 127]);
+    for (int q = 1; q < 8; ++q) row[8 * q + n2] = cmul(y[q], w[q]);
   }
 }
 
 // second forward row pass of items A and B and the split: put(slot, X) for each of the thread's bins
 template <class PUT>
-__device__ __forceinline__ void fwd_rows2_split(const float2* buf, const float2* T, const Roles& R, PUT put) {
+__device__ __forceinline__ void fwd_rows2_split(const float2* buf, const Tw& T, const Roles& R, PUT put) {
   const Items& it = R.it;
   float2 ya[8], yb[8];
   const float2* ra = buf + it.rowA * P + 8 * it.kA;
@@ -254,13 +294,16 @@ __device__ __forceinline__ void fwd_rows2_split(const float2* buf, const float2*
   }
   dft8<false>(ya);
   dft8<false>(yb);
+  float2 wa[8], wb[8];
+  tw_row8(T.s + 8 * it.kA, wa);
+  tw_row8(T.s + 8 * it.kB, wb);
   const bool sf = it.self, cls0 = R.cls0;
 #define CSC_F128_SPLIT(J)                                                                         \
   {                                                                                               \
     const float2 pa = sf ? partner_y<J>(ya, cls0) : partner_y<J>(yb, cls0);                       \
     const float2 pb = sf ? partner_y<J>(yb, cls0) : partner_y<J>(ya, cls0);                       \
-    put(J, split_fwd(ya[J], pa, T[it.kA + 8 * J]));                                               \
-    put(8 + J, split_fwd(yb[J], pb, T[it.kB + 8 * J]));                                           \
+    put(J, split_fwd(ya[J], pa, wa[J]));                                                          \
+    put(8 + J, split_fwd(yb[J], pb, wb[J]));                                                      \
   }
   CSC_F128_SPLIT(0) CSC_F128_SPLIT(1) CSC_F128_SPLIT(2) CSC_F128_SPLIT(3)
   CSC_F128_SPLIT(4) CSC_F128_SPLIT(5) CSC_F128_SPLIT(6) CSC_F128_SPLIT(7)

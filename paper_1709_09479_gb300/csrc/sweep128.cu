@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
   constexpr bool kAcc = (MODE != kLast);
   float2* buf = sm;                                   // [128][P]
   float2* lam = buf + H * P;                          // [OM] thread-major
-  float2* T = lam + (kLam ? OM : 0);                  // [128] exp(-2 pi i m / 128)
+  float2* twt = lam + (kLam ? OM : 0);                // twiddle tables (kTwEntries)
   const int t = threadIdx.x;
-  for (int i = t; i < H; i += NT) T[i] = a.tw[W / 2 + i];
+  const Tw T = build_tw<NT>(twt, a.tw + W / 2);
 
   const Roles R = roles_of(t);
   const int wc = R.wc, g = R.g;
@@ -199,7 +199,7 @@ __global__ void k_permute_dhat(const float2* __restrict__ in, float2* __restrict
 
 size_t smem_bytes(int mode) {
   const bool lam = (mode == kIter || mode == kLast);
-  return ((size_t)H * P + (lam ? OM : 0) + H) * sizeof(float2);
+  return ((size_t)H * P + (lam ? OM : 0) + kTwEntries) * sizeof(float2);
 }
 
 template <int MODE, bool BF>

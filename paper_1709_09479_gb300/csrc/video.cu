@@ -38,9 +38,8 @@ __global__ void __launch_bounds__(NT, 1) k_video_frames(VideoArgs a) {
   constexpr bool kInv = (MODE == kIter || MODE == kLast);
   constexpr bool kFwd = (MODE != kLast);
   float2* buf = sm;            // [128][P]
-  float2* T = buf + H * P;     // [128]
   const int t = threadIdx.x;
-  for (int i = t; i < H; i += NT) T[i] = a.tw[W / 2 + i];
+  const Tw T = build_tw<NT>(buf + H * P, a.tw + W / 2);
   const Roles R = roles_of(t);
   const int wc = R.wc, g = R.g;
   const long long nf = (long long)a.N * a.K * a.T;
@@ -437,7 +436,7 @@ __global__ void k_video_prep(VideoArgs a) {
 template <int MODE>
 cudaError_t launch_frames_mode(const VideoArgs& a, int G, cudaStream_t st) {
   auto kern = k_video_frames<MODE>;
-  const size_t smem = ((size_t)H * P + H) * sizeof(float2);
+  const size_t smem = ((size_t)H * P + kTwEntries) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<G, NT, smem, st>>>(a);
@@ -476,7 +475,7 @@ cudaError_t launch_bins_mode(const VideoArgs& a, cudaStream_t st) {
 
 }  // namespace f128
 
-size_t video_frames_smem_bytes() { return ((size_t)f128::H * f128::P + f128::H) * sizeof(float2); }
+size_t video_frames_smem_bytes() { return ((size_t)f128::H * f128::P + f128::kTwEntries) * sizeof(float2); }
 int video_max_T() { return f128::kVidMaxT; }
 int video_bin_blocks() { return f128::OM / f128::kBinTile; }
 size_t video_bins_smem_bytes(int J, int T) {
