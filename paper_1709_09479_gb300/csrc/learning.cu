@@ -41,10 +41,16 @@ __device__ __forceinline__ long long pair_index(int k, int kp, int K) {
   return (long long)k * K - (long long)k * (k - 1) / 2 + (kp - k);
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+
 __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
-  // double-buffered: the next image's tiles are loaded into registers while this image's are used
-  __shared__ float2 As[2][kGramT][kGramF];
-  __shared__ float2 Bs[2][kGramT][kGramF];
+  // three-stage pipeline: the tiles of image n + 2 are copied (cp.async) while image n is used
+  constexpr int kSt = 3;
+  __shared__ __align__(16) float2 As[kSt][kGramT][kGramF];
+  __shared__ __align__(16) float2 Bs[kSt][kGramT][kGramF];
   // tile pair (ti <= tj) from blockIdx.x
   int ti = 0, rem = blockIdx.x;
   while (rem >= a.ntile - ti) { rem -= a.ntile - ti; ++ti; }
@@ -66,13 +72,17 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
     la[u] = (ti * kGramT + lr[u] < a.K) && oo < a.Omega;
     lb[u] = (tj * kGramT + lr[u] < a.K) && oo < a.Omega;
   }
-  auto load = [&](int n, float2 (&ra)[kLd], float2 (&rb)[kLd]) {
+  auto stage = [&](int n) {   // issue the copies of image n into buffer n % kSt (zero fill outside)
+    const int bf = n % kSt;
 #pragma unroll
     for (int u = 0; u < kLd; ++u) {
       const size_t base = (size_t)n * a.K;
-      ra[u] = la[u] ? __ldg(a.zhat + (base + ti * kGramT + lr[u]) * a.Omega + o0 + lf[u]) : make_float2(0.f, 0.f);
-      rb[u] = lb[u] ? __ldg(a.zhat + (base + tj * kGramT + lr[u]) * a.Omega + o0 + lf[u]) : make_float2(0.f, 0.f);
+      const float2* sa = la[u] ? a.zhat + (base + ti * kGramT + lr[u]) * a.Omega + o0 + lf[u] : a.zhat;
+      const float2* sb = lb[u] ? a.zhat + (base + tj * kGramT + lr[u]) * a.Omega + o0 + lf[u] : a.zhat;
+      cp_async8(&As[bf][lr[u]][lf[u]], sa, la[u]);
+      cp_async8(&Bs[bf][lr[u]][lf[u]], sb, lb[u]);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
   float2 acc[4][8];
 #pragma unroll
@@ -80,17 +90,15 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
   const int o = o0 + f;
-  float2 ra[kLd], rb[kLd];
-  load(0, ra, rb);
+  stage(0);
+  if (a.N > 1) stage(1);
+  else asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int n = 0; n < a.N; ++n) {
-    const int bf = n & 1;
-#pragma unroll
-    for (int u = 0; u < kLd; ++u) {
-      As[bf][lr[u]][lf[u]] = ra[u];
-      Bs[bf][lr[u]][lf[u]] = rb[u];
-    }
-    __syncthreads();
-    if (n + 1 < a.N) load(n + 1, ra, rb);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // image n has landed
+    __syncthreads();                                          // ... for every thread; image n-1 is done
+    if (n + 2 < a.N) stage(n + 2);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int bf = n % kSt;
     float2 av[4], bv[8];
 #pragma unroll
     for (int i = 0; i < 4; ++i) av[i] = As[bf][4 * kq + i][f];
@@ -101,6 +109,7 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) acc[i][jj] = cfmac(av[i], bv[jj], acc[i][jj]);
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (o >= a.Omega) return;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
