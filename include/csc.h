@@ -57,10 +57,12 @@ typedef enum {
   CSC_MIXED_BF16 = 1   /* FFTs, shrinkage and CG in float32; the per-frequency contractions with
                           bfloat16 operands and float32 accumulation: sum_k d_hat_k u_hat_k and
                           conj(d_hat_k) lambda_hat in the coding sweep (CUDA cores), and the code Gram
-                          Z(w)^H Z(w) of csc_learn on the tensor cores (tcgen05). The per-frequency
-                          system (A(w) + I/rho)^{-1} is built in float64 in both modes. Needs K <= 128
-                          and n_images <= 448; csc_code_unrolled, csc_code_backward and the
-                          synthesis calls accept CSC_FP32 only. */
+                          Z(w)^H Z(w) of csc_learn on the tensor cores (tcgen05 kind::f16). In
+                          CSC_FP32 the Gram also runs on the tensor cores when K <= 128, as three
+                          TF32 products of a hi + lo operand split (float32-accurate). The
+                          per-frequency system (A(w) + I/rho)^{-1} is built in float64 in both modes.
+                          Needs K <= 128; csc_code_unrolled, csc_code_backward and the synthesis
+                          calls accept CSC_FP32 only. */
 } csc_precision;
 
 typedef struct {

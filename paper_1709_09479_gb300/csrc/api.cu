@@ -113,7 +113,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.zt, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
@@ -382,8 +382,6 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
     return fail(nullptr, CSC_ERR_ARG, "csc_init: unknown precision");
   if (p.precision == CSC_MIXED_BF16) {
     if (p.K > 128) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: CSC_MIXED_BF16 needs K <= 128");
-    if (tc_gram_smem_bytes(n_images) > kSmemLimit)
-      return fail(nullptr, CSC_ERR_SHAPE, "csc_init: CSC_MIXED_BF16 needs n_images <= 448");
   }
   const int fh = p.fs[0], fw = p.fs[1];
   if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
@@ -901,6 +899,7 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
         ensure_alloc(&L.zw, nd) != cudaSuccess ||
         ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
         ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
+        (gram_tc_fuses_rhs(*c) && ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess) ||
         (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||
         ensure_alloc(&L.slots, (size_t)2 * c->nsm * 4 * kMaxJ) != cudaSuccess) {
       cudaGetLastError();
@@ -928,19 +927,21 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   const int br = bracket_open(c, 1);
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, zd, c->N * K, 0, L.zhat), "code spectra");
-  CSC_CHECK_CUDA(c, launch_learn_rhs(*c), "learning right-hand side");
-  if (c->p.precision == CSC_MIXED_BF16) {
-    const size_t npad = (size_t)((c->N + 15) / 16 * 16);
-    CSC_CHECK_CUDA(c, ensure_alloc(reinterpret_cast<__nv_bfloat16**>(&L.zt), Om * K * 2 * npad), "bf16 workspace");
-    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, L.zt, c->err), "code Gram (tensor cores)");
-    c->launches += 1;
+  // the per-frequency Gram on the tensor cores (3xTF32 in float32, BF16 in the mixed mode) also
+  // forms the right-hand-side spectra when K + J <= 128; otherwise the CUDA-core Gram
+  const bool mixed = c->p.precision == CSC_MIXED_BF16;
+  if (gram_tc_applies(*c)) {
+    float2* rspec = gram_tc_fuses_rhs(*c) ? L.rspec : nullptr;
+    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, mixed, rspec, c->err), "code Gram (tensor cores)");
+    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, rspec), "learning right-hand side");
   } else {
     CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
+    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, nullptr), "learning right-hand side");
   }
   CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
   CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
   bracket_close(c, br);
-  c->launches += 6;
+  c->launches += 7;   // two spectra, Gram, right-hand side, lags, lag spectra, CG
   if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, nd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
   CSC_CHECK_CUDA(c, cudaMemcpyAsync(mu, L.mu, K * sizeof(double),
                                     mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),

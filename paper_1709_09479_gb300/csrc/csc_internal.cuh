@@ -134,7 +134,7 @@ struct LearnBuffers {
   unsigned long long* slots = nullptr;   // [2][G][4 kMaxJ] CG exchange words (sum | epoch)
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
-  void* zt = nullptr;       // mixed precision: [Omega][K][2 npad] bf16 code spectra for the tensor-core Gram
+  float2* rspec = nullptr;  // [K][J][Omega] right-hand-side spectra from the tensor-core Gram
 };
 
 struct BackwardBuffers {
@@ -228,7 +228,7 @@ struct BwdArgs {
 struct GeoOps {
   cudaError_t (*fft_maps)(const Ctx&, const float* in, int nmaps, int filter_mode, float2* out);
   cudaError_t (*sweep)(const Ctx&, int mode, const SweepArgs&);
-  cudaError_t (*rhs)(const Ctx&);
+  cudaError_t (*rhs)(const Ctx&, const float2* spec);
   cudaError_t (*lags)(const Ctx&);
   cudaError_t (*bwd)(const Ctx&, int mode, const BwdArgs&);
   cudaError_t (*spec_maps)(const Ctx&, const float2* spec, int nmaps, float scale, float* out);
@@ -267,13 +267,16 @@ inline size_t bwd_smem_bytes(const Geometry& g, bool rb, bool acc) {
 void set_global_error(const char* msg);
 
 // launchers (learning.cu)
-cudaError_t launch_learn_rhs(const Ctx& c);
+cudaError_t launch_learn_rhs(const Ctx& c, const float2* spec);
 cudaError_t launch_learn_gram(const Ctx& c);
 cudaError_t launch_learn_lags(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
 size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem);
-cudaError_t launch_learn_gram_tc(const Ctx& c, void* zt_buf, int* dev_err);
-size_t tc_gram_smem_bytes(int N);
+// tensor-core Gram (K <= 128): 3xTF32 (float32-accurate) or BF16 operands; with rspec non-null
+// (K + J <= 128) it also writes the right-hand-side spectra [K][J][Omega]
+cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err);
+bool gram_tc_applies(const Ctx& c);
+bool gram_tc_fuses_rhs(const Ctx& c);
 cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n);
 
 inline const GeoOps& geo_ops(const Ctx& c) {

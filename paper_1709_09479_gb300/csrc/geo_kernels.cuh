@@ -337,6 +337,7 @@ struct RhsArgs {
   const float2* xhat;  // [N][J][Omega]
   float* b;            // [K][J][fh*fw]
   const float2* tw;
+  const float2* spec;  // [K][J][Omega] precomputed sum_n conj(z_hat_nk) x_hat_nj, or null
 };
 
 template <class G, int NT>
@@ -359,8 +360,10 @@ __global__ void __launch_bounds__(NT) k_learn_rhs(RhsArgs a, G g) {
   const int k = blockIdx.x / a.J, j = blockIdx.x % a.J;
   for (int o = threadIdx.x; o < Om; o += NT) {
     float2 s = make_float2(0.f, 0.f);
-    for (int n = 0; n < a.N; ++n)
-      s = cfmac(a.zhat[((size_t)n * a.K + k) * Om + o], a.xhat[((size_t)n * a.J + j) * Om + o], s);
+    if (a.spec) s = a.spec[((size_t)k * a.J + j) * Om + o];
+    else
+      for (int n = 0; n < a.N; ++n)
+        s = cfmac(a.zhat[((size_t)n * a.K + k) * Om + o], a.xhat[((size_t)n * a.J + j) * Om + o], s);
     const int h = o / Wc, c = o - h * Wc;
     buf[h * P + c] = s;
   }
@@ -702,10 +705,14 @@ struct GeoLaunch {
     }
   }
 
-  static cudaError_t rhs(const Ctx& c) { return rhs_ex(c, c.L.zhat, c.xhat, c.L.b); }
+  static cudaError_t rhs(const Ctx& c, const float2* spec) { return rhs_run(c, c.L.zhat, c.xhat, c.L.b, spec); }
 
   static cudaError_t rhs_ex(const Ctx& c, const float2* zhat, const float2* xhat, float* out) {
-    RhsArgs a{c.N, c.K, c.J, c.fh, c.fw, zhat, xhat, out, c.tw};
+    return rhs_run(c, zhat, xhat, out, nullptr);
+  }
+
+  static cudaError_t rhs_run(const Ctx& c, const float2* zhat, const float2* xhat, float* out, const float2* spec) {
+    RhsArgs a{c.N, c.K, c.J, c.fh, c.fw, zhat, xhat, out, c.tw, spec};
     const size_t smem = map_smem_bytes(c.g);
     auto kern = k_learn_rhs<GEO, kNT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

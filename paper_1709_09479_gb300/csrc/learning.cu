@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
-cudaError_t launch_learn_rhs(const Ctx& c) { return geo_ops(c).rhs(c); }
+cudaError_t launch_learn_rhs(const Ctx& c, const float2* spec) { return geo_ops(c).rhs(c, spec); }
 
 cudaError_t launch_learn_gram(const Ctx& c) {
   const int ntile = (c.K + kGramT - 1) / kGramT;

@@ -1,22 +1,39 @@
-// Per-frequency code Gram on the 5th-generation tensor cores (mixed-precision learning).
+// Per-frequency code Gram on the 5th-generation tensor cores.
 //
 // The learning step needs, for every frequency w, the K x K Hermitian matrix
 //     G(w) = Z(w)^H Z(w),   Z(w) in C^{N x K} (the code spectra of N images),
-// which is the only dense contraction on the path (a K x N by N x K product per frequency).
+// which is the only dense contraction on the path (a K x N by N x K product per frequency), and the
+// right-hand-side spectra R_kj(w) = sum_n conj(z_hat_nk(w)) x_hat_nj(w), which are the same product
+// with the J image spectra appended to Z as extra columns.
 // With C1 = [Re Z ; Im Z] (2N x K) and C2 = [Im Z ; -Re Z]:
 //     Re G = C1^T C1,   Im G = C1^T C2.
-// One CTA per frequency (persistent over frequencies) stages C1^T (K rows of 2N bfloat16, K-major)
-// in shared memory in the canonical no-swizzle core-matrix layout, and one thread issues
-// tcgen05.mma kind::f16 (M = 128 rows = filters, N = K rounded up to 16, K-step 16 = images):
-// the Re G accumulator pairs K-step s with itself; the Im G accumulator pairs the Re half of C1^T
+//
+// One CTA owns one frequency at a time (persistent over frequencies, two CTAs per SM so that one's
+// epilogue overlaps the other's MMAs). The images are taken in chunks of NC: all 128 threads load
+// z_hat_nk(w) for the chunk straight from the [N][K][Omega] spectra (rows k >= K + J and images
+// n >= N are zero), split them into tensor-core operands and store them as C1^T rows (filters) of
+// [Re over the chunk's images | Im over them] in the canonical no-swizzle K-major core-matrix layout.
+// One thread then issues tcgen05.mma (M = 128 rows = filters, N = K + J rounded up to 16): the Re G
+// accumulator pairs each K-step with itself, the Im G accumulator pairs the Re half of a chunk row
 // with its Im half and the Im half with the Re half under the descriptor's negate-B bit, so C2 is
-// never materialised. Both accumulators sit in the same TMEM lanes (row k), so the epilogue thread
-// of row k reads its Re and Im rows with tcgen05.ld and writes G_kk'(w) for k' >= k.
-// Waits on the MMA-completion mbarrier are bounded; on timeout the CTA records an error flag, frees
-// its TMEM and returns.
+// never materialised. A ring of STAGES chunk buffers lets the loads of chunk i + 1 and the stores of
+// later chunks run while the MMAs of chunk i execute; each buffer is released by a tcgen05.commit.
+//
+// Two operand precisions:
+//   X3 = true   float32-accurate 3xTF32: v = hi + lo with hi, lo rounded to TF32 (10 explicit mantissa
+//               bits); G accumulates hi.hi + hi.lo + lo.hi in FP32 (kind::tf32). The dropped lo.lo term
+//               and the rounding of lo are below 2^-21 relative per product.
+//   X3 = false  BF16 operands, FP32 accumulation (kind::f16), the mixed-precision mode.
+//
+// The epilogue thread of TMEM lane k reads its Re and Im rows with tcgen05.ld and writes G_kk'(w)
+// for k <= k' < K and R_kj(w) for the appended columns. Every wait on an mbarrier is bounded; on
+// timeout the CTA records CSC_ERR_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "csc_internal.cuh"
 
@@ -24,6 +41,21 @@ namespace csc {
 
 constexpr int kTcThreads = 128;
 constexpr long long kTcSpinLimit = 2000000000LL;
+constexpr int kTcRowBytes = 128;                       // one chunk row: [Re | Im] of the chunk's images
+constexpr int kTcPieceBytes = 128 * kTcRowBytes;       // 128 rows
+constexpr int kTcKSteps = kTcRowBytes / 32;            // 32 bytes (2 core matrices) per MMA K-step
+constexpr uint32_t kTcLbo = 128;                       // next core matrix along K
+constexpr uint32_t kTcSbo = kTcRowBytes / 16 * 128;    // next group of 8 rows
+constexpr int kTcCols = 256;                           // TMEM columns: Re G at 0, Im G at 128
+
+template <bool X3>
+struct TcCfg {
+  static constexpr int NC = X3 ? 16 : 32;              // images per chunk (element 4 or 2 bytes)
+  static constexpr int PIECES = X3 ? 2 : 1;            // hi, lo
+  static constexpr int STAGES = X3 ? 3 : 4;
+  static constexpr int STAGE_BYTES = PIECES * kTcPieceBytes;
+  static constexpr int SMEM = STAGES * STAGE_BYTES;
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -31,27 +63,60 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 
 // shared-memory matrix descriptor (tcgen05): start, leading (K-direction core-matrix) byte offset,
 // stride (8-row-group) byte offset, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)((kTcLbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((kTcSbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
 
-// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool negate_b) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | ((uint32_t)(n >> 3) << 17) |
+// instruction descriptor: D f32 (bits 4-5 = 1), A and B of format fmt (bits 7-9, 10-12; BF16 = 1,
+// TF32 = 2), negate-B bit 14, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28 (M = 128)
+__host__ __device__ constexpr uint32_t idesc_mma(uint32_t fmt, int n, bool negate_b) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (negate_b ? (1u << 14) : 0u) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+template <bool X3>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (X3) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// bounded wait for the completion of phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kTcSpinLimit) return false;
+  }
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -66,95 +131,143 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// round to the nearest TF32 value (10 explicit mantissa bits; ties away from zero), kept in a
+// float32 container with the 13 low bits clear
+__device__ __forceinline__ float round_tf32(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+
 struct TcGramArgs {
-  int N, K, Omega;
-  int npad;              // N rounded up to 16: each C1^T row holds 2 * npad bf16
-  int ntile;             // K rounded up to 16 (MMA N)
-  const __nv_bfloat16* zt;  // [Omega][K][2 * npad]  (Re over images, then Im), zero padded
-  float2* gram;          // [npairs][Omega]
+  int N, K, J, Omega;
+  int ntile;                // B rows (MMA N): K + J (or K) rounded up to 16, <= 128
+  int rows;                 // loaded rows: K + J when the right-hand side is fused, else K
+  const float2* zhat;       // [N][K][Omega]
+  const float2* xhat;       // [N][J][Omega]
+  float2* gram;             // [npairs][Omega], pairs k <= k'
+  float2* rspec;            // [K][J][Omega] or null (no fused right-hand side)
   int* err;
 };
 
+template <bool X3>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
+  using C = TcCfg<X3>;
+  constexpr int NC = C::NC;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row_bytes = 4 * a.npad;               // 2 * npad bf16
-  const int chunks = row_bytes / 16;              // 16-byte chunks per row (core-matrix columns)
-  const uint32_t lbo = 128u;                      // next core matrix along K
-  const uint32_t sbo = (uint32_t)chunks * 128u;   // next group of 8 rows
+  const int r8 = lane & 7, q4 = lane >> 3;
   const uint32_t tile = smem_addr(smem);
-  constexpr uint32_t kCols = 256;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
-                 "r"(kCols));
+                 "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+    for (int s = 0; s < C::STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&empty_bar[s])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&acc_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&drain_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t acc_re = tmem, acc_im = tmem + (uint32_t)a.ntile;
-  const int ksteps = a.npad / 8;                  // 16 bf16 (two core matrices) per K-step
-  const int half = ksteps / 2;
-  const uint32_t id_pos = idesc_bf16(a.ntile, false), id_neg = idesc_bf16(a.ntile, true);
-  uint32_t phase = 0;
-  bool ok = true;
+  const uint32_t acc_re = tmem, acc_im = tmem + 128u;
+  constexpr uint32_t fmt = X3 ? 2u : 1u;
+  const uint32_t id_pos = idesc_mma(fmt, a.ntile, false), id_neg = idesc_mma(fmt, a.ntile, true);
+  const int nchunks = (a.N + NC - 1) / NC;
 
+  // element u of this thread's share of a chunk: image 4 (u % (NC/4)) + q4, row 8 kg + r8 with
+  // kg = 4 (u / (NC/4)) + warp; a warp's 32 lanes write 32 distinct banks of one core-matrix column
+  auto load_chunk = [&](int o, int ch, float2* vals) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int n = ch * NC + 4 * (u % (NC / 4)) + q4;
+      const int k = 8 * (4 * (u / (NC / 4)) + warp) + r8;
+      float2 v = make_float2(0.f, 0.f);
+      if (n < a.N) {
+        if (k < a.K) v = a.zhat[((size_t)n * a.K + k) * a.Omega + o];
+        else if (k < a.rows) v = a.xhat[((size_t)n * a.J + (k - a.K)) * a.Omega + o];
+      }
+      vals[u] = v;
+    }
+  };
+  auto store_chunk = [&](int s, const float2* vals) {
+    uint8_t* st = smem + s * C::STAGE_BYTES;
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int nl = 4 * (u % (NC / 4)) + q4;
+      const int k = 8 * (4 * (u / (NC / 4)) + warp) + r8;
+      const int row = (k >> 3) * (int)kTcSbo + (k & 7) * 16;
+      if constexpr (X3) {
+        const int cre = nl * 4, cim = (NC + nl) * 4;   // byte columns
+        const float hr = round_tf32(vals[u].x), hi = round_tf32(vals[u].y);
+        const float lr = round_tf32(vals[u].x - hr), li = round_tf32(vals[u].y - hi);
+        uint8_t* p0 = st + row;
+        uint8_t* p1 = st + kTcPieceBytes + row;
+        *reinterpret_cast<float*>(p0 + (cre >> 4) * kTcLbo + (cre & 15)) = hr;
+        *reinterpret_cast<float*>(p0 + (cim >> 4) * kTcLbo + (cim & 15)) = hi;
+        *reinterpret_cast<float*>(p1 + (cre >> 4) * kTcLbo + (cre & 15)) = lr;
+        *reinterpret_cast<float*>(p1 + (cim >> 4) * kTcLbo + (cim & 15)) = li;
+      } else {
+        const int cre = nl * 2, cim = (NC + nl) * 2;
+        uint8_t* p0 = st + row;
+        *reinterpret_cast<__nv_bfloat16*>(p0 + (cre >> 4) * kTcLbo + (cre & 15)) = __float2bfloat16_rn(vals[u].x);
+        *reinterpret_cast<__nv_bfloat16*>(p0 + (cim >> 4) * kTcLbo + (cim & 15)) = __float2bfloat16_rn(vals[u].y);
+      }
+    }
+  };
+
+  bool ok = true;
+  int it = 0;           // chunks produced by this CTA
+  int nfreq = 0;        // frequencies finished by this CTA
+  float2 vals[NC];
+  if (blockIdx.x < a.Omega) load_chunk(blockIdx.x, 0, vals);
   for (int o = blockIdx.x; o < a.Omega && ok; o += gridDim.x) {
-    // stage C1^T rows (filters) of frequency o; rows >= K are zero
-    const uint4* src = reinterpret_cast<const uint4*>(a.zt + (size_t)o * a.K * 2 * a.npad);
-    for (int i = threadIdx.x; i < 128 * chunks; i += kTcThreads) {
-      const int m = i / chunks, c = i - m * chunks;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (m < a.K) val = src[(size_t)m * chunks + c];
-      const uint32_t off = (uint32_t)(m >> 3) * sbo + (uint32_t)c * lbo + (uint32_t)(m & 7) * 16u;
-      *reinterpret_cast<uint4*>(smem + off) = val;
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int s = 0; s < ksteps; ++s) {
-        const uint64_t ad = smem_desc(tile + (uint32_t)s * 2u * lbo, lbo, sbo);
-        mma_bf16(acc_re, ad, ad, id_pos, s > 0 ? 1u : 0u);
-        const int sb = s < half ? s + half : s - half;
-        const uint64_t bd = smem_desc(tile + (uint32_t)sb * 2u * lbo, lbo, sbo);
-        mma_bf16(acc_im, ad, bd, s < half ? id_pos : id_neg, s > 0 ? 1u : 0u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       smem_addr(&mbar))
-                   : "memory");
-    }
-    // bounded wait for the MMAs of this frequency
-    {
-      const long long t0 = clock64();
-      uint32_t done = 0;
-      while (!done) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_addr(&mbar)), "r"(phase)
-            : "memory");
-        if (!done && clock64() - t0 > kTcSpinLimit) {
-          atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
-          ok = false;
-          break;
+    for (int ch = 0; ch < nchunks; ++ch, ++it) {
+      const int s = it % C::STAGES;
+      if (it >= C::STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((it / C::STAGES - 1) & 1))) ok = false;
+      if (ok) store_chunk(s, vals);
+      // prefetch the next chunk (of this frequency or the next one) while the MMAs run
+      if (ch + 1 < nchunks) load_chunk(o, ch + 1, vals);
+      else if (o + (int)gridDim.x < a.Omega) load_chunk(o + gridDim.x, 0, vals);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      if (__syncthreads_and(ok ? 1 : 0) == 0) { ok = false; break; }
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t base = tile + (uint32_t)(s * C::STAGE_BYTES);
+#pragma unroll
+        for (int ks = 0; ks < kTcKSteps; ++ks) {
+          const int kb = ks < kTcKSteps / 2 ? ks + kTcKSteps / 2 : ks - kTcKSteps / 2;
+          const uint32_t idi = ks < kTcKSteps / 2 ? id_pos : id_neg;
+#pragma unroll
+          for (int c = 0; c < (X3 ? 3 : 1); ++c) {
+            const uint32_t pa = (c == 2) ? kTcPieceBytes : 0u;   // hi.hi, hi.lo, lo.hi
+            const uint32_t pb = (c == 1) ? kTcPieceBytes : 0u;
+            const uint64_t ad = smem_desc(base + pa + (uint32_t)ks * 2u * kTcLbo);
+            const uint64_t bre = smem_desc(base + pb + (uint32_t)ks * 2u * kTcLbo);
+            const uint64_t bim = smem_desc(base + pb + (uint32_t)kb * 2u * kTcLbo);
+            const uint32_t accum = (ch > 0 || ks > 0 || c > 0) ? 1u : 0u;
+            mma<X3>(acc_re, ad, bre, id_pos, accum);
+            mma<X3>(acc_im, ad, bim, idi, accum);
+          }
         }
+        mma_commit(&empty_bar[s]);
+        if (ch + 1 == nchunks) mma_commit(&acc_bar);
       }
     }
-    phase ^= 1u;
+    if (!ok) break;
+    // epilogue: the frequency's accumulators are complete
+    if (!mbar_wait(&acc_bar, (uint32_t)(nfreq & 1))) ok = false;
+    ++nfreq;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (__syncthreads_and(ok ? 1 : 0) == 0) { ok = false; break; }
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (filter k), 16 columns at a time
     const int k = 32 * warp + lane;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     for (int c0 = 0; c0 < a.ntile; c0 += 16) {
@@ -168,73 +281,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
           if (kp >= k && kp < a.K) {
             const long long p = (long long)k * a.K - (long long)k * (k - 1) / 2 + (kp - k);
             a.gram[p * a.Omega + o] = make_float2(gr[i], gi[i]);
+          } else if (kp >= a.K && kp < a.rows && a.rspec) {
+            a.rspec[((size_t)k * a.J + (kp - a.K)) * a.Omega + o] = make_float2(gr[i], gi[i]);
           }
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
   }
+  if (!ok && threadIdx.x == 0) atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
+  // drain: every MMA this CTA issued has completed before its TMEM is released
+  if (threadIdx.x == 0) mma_commit(&drain_bar);
+  if (!mbar_wait(&drain_bar, 0u)) {
+    if (threadIdx.x == 0) atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols));
 }
 
-// z_hat [N][K][Omega] float32 -> zt [Omega][K][2*npad] bf16 (Re over images, then Im, zero padded):
-// a CTA transposes one filter's 32-frequency slab through shared memory
-struct ZtArgs {
-  int N, K, Omega, npad;
-  const float2* zhat;
-  __nv_bfloat16* zt;
-};
+bool gram_tc_applies(const Ctx& c) { return c.K <= 128; }
 
-__global__ void __launch_bounds__(256) k_zt_transpose(ZtArgs a) {
-  extern __shared__ float2 slab[];   // [N][32]
-  const int k = blockIdx.y;
-  const int o0 = blockIdx.x * 32;
-  for (int i = threadIdx.x; i < a.N * 32; i += blockDim.x) {
-    const int n = i / 32, f = i % 32;
-    const int o = o0 + f;
-    slab[i] = (o < a.Omega) ? a.zhat[((size_t)n * a.K + k) * a.Omega + o] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int row = 2 * a.npad;
-  for (int i = threadIdx.x; i < 32 * row; i += blockDim.x) {
-    const int f = i / row, e = i - f * row;
-    const int o = o0 + f;
-    if (o >= a.Omega) continue;
-    const int n = e < a.npad ? e : e - a.npad;
-    float v = 0.f;
-    if (n < a.N) v = e < a.npad ? slab[n * 32 + f].x : slab[n * 32 + f].y;
-    a.zt[((size_t)o * a.K + k) * row + e] = __float2bfloat16_rn(v);
-  }
-}
+bool gram_tc_fuses_rhs(const Ctx& c) { return c.K + c.J <= 128; }
 
-size_t tc_gram_smem_bytes(int N) {
-  const int npad = (N + 15) / 16 * 16;
-  return (size_t)128 * 4 * npad;
-}
-
-cudaError_t launch_learn_gram_tc(const Ctx& c, void* zt_buf, int* dev_err) {
-  const int npad = (c.N + 15) / 16 * 16;
-  const int ntile = (c.K + 15) / 16 * 16;
-  __nv_bfloat16* zt = static_cast<__nv_bfloat16*>(zt_buf);
-  ZtArgs za{c.N, c.K, c.g.Omega, npad, c.L.zhat, zt};
-  dim3 tg((c.g.Omega + 31) / 32, c.K);
-  const size_t tsm = (size_t)c.N * 32 * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_zt_transpose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+template <bool X3>
+static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err) {
+  const int rows = rspec ? c.K + c.J : c.K;
+  const int ntile = (rows + 15) / 16 * 16;
+  TcGramArgs a{c.N, c.K, c.J, c.g.Omega, ntile, rows, c.L.zhat, c.xhat, c.L.gram, rspec, dev_err};
+  // at least 80 KB per CTA keeps at most two CTAs (2 x 256 TMEM columns) per SM
+  const int smem = std::max(TcCfg<X3>::SMEM, 80 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_zt_transpose<<<tg, 256, tsm, c.stream>>>(za);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  TcGramArgs a{c.N, c.K, c.g.Omega, npad, ntile, zt, c.L.gram, dev_err};
-  // at least 80 KB per CTA keeps two CTAs (2 x 256 TMEM columns) per SM
-  size_t smem = tc_gram_smem_bytes(c.N);
-  if (smem < 80 * 1024) smem = 80 * 1024;
-  if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
   const int grid = std::min(c.g.Omega, 2 * c.nsm);
-  k_gram_tc<<<grid, kTcThreads, smem, c.stream>>>(a);
+  k_gram_tc<X3><<<grid, kTcThreads, smem, c.stream>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err) {
+  if (!gram_tc_applies(c)) return cudaErrorInvalidValue;
+  if (rspec && !gram_tc_fuses_rhs(c)) return cudaErrorInvalidValue;
+  return bf16 ? launch_gram_tc_t<false>(c, rspec, dev_err) : launch_gram_tc_t<true>(c, rspec, dev_err);
 }
 
 }  // namespace csc

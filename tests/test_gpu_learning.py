@@ -54,6 +54,13 @@ LEARN_CASES = [
     (3, 6, 1, (64, 64), 5, 0.3, 4),
     (2, 3, 3, (24, 32), 3, 0.2, 3),
     (4, 8, 1, (100, 100), 11, 0.5, 2),
+    # tensor-core Gram coverage: 3 image chunks with a ragged tail (fused right-hand side), colour
+    # with 3 chunks, K = 128 (Gram on the tensor cores, right-hand side separate) and K = 130 (the
+    # CUDA-core Gram)
+    (37, 20, 1, (32, 32), 5, 0.3, 2),
+    (40, 12, 3, (24, 24), 3, 0.3, 2),
+    (3, 128, 1, (16, 16), 3, 0.3, 2),
+    (2, 130, 1, (16, 16), 3, 0.3, 2),
 ]
 
 

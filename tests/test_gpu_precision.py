@@ -45,7 +45,8 @@ def test_bf16_coding_error_against_oracle(csc, case):
     assert e16 <= CODE_BF16_TOL
 
 
-@pytest.mark.parametrize("case", [(3, 6, (64, 64), 5, 0.3), (16, 100, (64, 64), 5, 0.3), (4, 8, (100, 100), 11, 0.5)])
+@pytest.mark.parametrize("case", [(3, 6, (64, 64), 5, 0.3), (16, 100, (64, 64), 5, 0.3), (4, 8, (100, 100), 11, 0.5),
+                                  (45, 20, (32, 32), 5, 0.3)])
 def test_tensor_core_gram_learning_against_oracle(csc, case):
     import torch
     N, K, dims, s, beta = case
