@@ -113,7 +113,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->L.zt, c->L.lagT, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
@@ -410,7 +410,7 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
   cudaError_t e = cudaDeviceGetAttribute(&tmp.nsm, cudaDevAttrMultiProcessorCount, tmp.device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
   const size_t cg_smem = learn_cg_smem_bytes(tmp, tmp.S2 <= kMaxBlockJacobi, false);
-  if (!video && cg_smem > kSmemLimit)
+  if (!video && (cg_smem > kSmemLimit || !learn_cg_shape_ok(tmp)))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
   const long long NK = (long long)tmp.N * tmp.K;
   tmp.G = (int)std::min<long long>(tmp.nsm, NK);
@@ -899,7 +899,9 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
         ensure_alloc(&L.zw, nd) != cudaSuccess ||
         ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
         ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
-        (gram_tc_fuses_rhs(*c) && ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess) ||
+        (gram_tc_applies(*c) && (ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess ||
+                                 ensure_alloc(&L.zt, (size_t)c->N * K * Om) != cudaSuccess ||
+                                 ensure_alloc(&L.lagT, lag_sep_T_count(*c)) != cudaSuccess)) ||
         (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||
         ensure_alloc(&L.slots, (size_t)2 * c->nsm * 4 * kMaxJ) != cudaSuccess) {
       cudaGetLastError();
@@ -926,22 +928,26 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
   const int br = bracket_open(c, 1);
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
-  CSC_CHECK_CUDA(c, launch_fft_maps(*c, zd, c->N * K, 0, L.zhat), "code spectra");
-  // the per-frequency Gram on the tensor cores (3xTF32 in float32, BF16 in the mixed mode) also
-  // forms the right-hand-side spectra when K + J <= 128; otherwise the CUDA-core Gram
-  const bool mixed = c->p.precision == CSC_MIXED_BF16;
+  // the per-frequency Gram on the tensor cores (3xTF32 in float32, BF16 in the mixed mode), with the
+  // right-hand-side spectra as J extra columns, when K + J <= 128; otherwise on the CUDA cores
   if (gram_tc_applies(*c)) {
-    float2* rspec = gram_tc_fuses_rhs(*c) ? L.rspec : nullptr;
-    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, mixed, rspec, c->err), "code Gram (tensor cores)");
-    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, rspec), "learning right-hand side");
+    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
+    CSC_CHECK_CUDA(c, launch_spectra_transpose(*c, L.zhat, c->N * K, L.zt), "code spectra transpose");
+    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, c->p.precision == CSC_MIXED_BF16, L.rspec, c->err),
+                   "code Gram (tensor cores)");
+    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, L.rspec), "learning right-hand side");
+    CSC_CHECK_CUDA(c, launch_learn_lags_sep(*c), "code lags");
+    c->launches += 4;
   } else {
+    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
     CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
     CSC_CHECK_CUDA(c, launch_learn_rhs(*c, nullptr), "learning right-hand side");
+    CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
+    c->launches += 3;
   }
-  CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
   CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
   bracket_close(c, br);
-  c->launches += 7;   // two spectra, Gram, right-hand side, lags, lag spectra, CG
+  c->launches += 2;   // image spectra, CG (the lag kernels count themselves)
   if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, nd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
   CSC_CHECK_CUDA(c, cudaMemcpyAsync(mu, L.mu, K * sizeof(double),
                                     mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
@@ -1175,7 +1181,7 @@ csc_status csc_synthesize_backward(csc_ctx* ctx, const float* d, const float* z,
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, d, c->K, 1, c->dhat), "filter spectra");
   CSC_CHECK_CUDA(c, launch_fft_maps(*c, gout, c->N, 0, c->B.spec), "gradient spectra");
   CSC_CHECK_CUDA(c, ops.expand(*c, c->B.spec, 1.0f / (float)c->g.D, gz), "code gradient");
-  CSC_CHECK_CUDA(c, launch_fft_maps(*c, z, c->N * c->K, 0, c->L.zhat), "code spectra");
+  CSC_CHECK_CUDA(c, launch_code_spectra(*c, z, c->N * c->K, c->L.zhat), "code spectra");
   CSC_CHECK_CUDA(c, ops.rhs_ex(*c, c->L.zhat, c->B.spec, gd), "filter gradient");
   c->launches += 5;
   return CSC_OK;

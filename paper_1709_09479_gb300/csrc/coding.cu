@@ -167,6 +167,11 @@ cudaError_t launch_fft_maps(const Ctx& c, const float* in, int nmaps, int filter
   return e;
 }
 
+cudaError_t launch_code_spectra(const Ctx& c, const float* in, int nmaps, float2* out) {
+  if (c.g.ct_id == 1) return launch_spectra_f128(c, in, nmaps, out);
+  return geo_ops(c).fft_maps(c, in, nmaps, 0, out);
+}
+
 cudaError_t launch_solve_prep(const Ctx& c) {
   PrepArgs a{c.K, c.J, c.g.Omega, c.p.rho, 1.0 / ((double)c.g.D), c.dhat, c.pdiag, c.pmat};
   k_solve_prep<<<(c.g.Omega + 255) / 256, 256, 0, c.stream>>>(a);

@@ -122,7 +122,8 @@ struct Geometry {
 struct LearnBuffers {
   bool ready = false;
   float2* zhat = nullptr;   // [N][K][Omega]
-  float2* gram = nullptr;   // [npairs][Omega], pairs k <= k'
+  float2* gram = nullptr;   // [npairs][Omega], pairs k <= k' (CUDA-core Gram), or [Omega][npairs] in
+                            // column order k'(k'+1)/2 + k (tensor-core Gram)
   float* lags = nullptr;    // [K][K][L*L]
   float2* chat = nullptr;   // [NF][K(K+1)/2] lag spectra / (La Lb), NF = La * fw
   unsigned long long* yw = nullptr;   // [K][J][NF][2] epoch-tagged words of the CG product spectrum
@@ -135,6 +136,8 @@ struct LearnBuffers {
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
   float2* rspec = nullptr;  // [K][J][Omega] right-hand-side spectra from the tensor-core Gram
+  float2* zt = nullptr;     // [Omega][N K] frequency-major code spectra for the tensor-core Gram
+  float2* lagT = nullptr;   // [H][2 fw - 1][npairs] row sums of the separable lag transform
 };
 
 struct BackwardBuffers {
@@ -269,14 +272,22 @@ void set_global_error(const char* msg);
 // launchers (learning.cu)
 cudaError_t launch_learn_rhs(const Ctx& c, const float2* spec);
 cudaError_t launch_learn_gram(const Ctx& c);
-cudaError_t launch_learn_lags(const Ctx& c);
+cudaError_t launch_learn_lags(const Ctx& c);       // from gram [npairs][Omega] (CUDA-core Gram)
+cudaError_t launch_learn_lags_sep(const Ctx& c);   // from the tensor-core Gram's gramT [Omega][npairs]
+size_t lag_sep_T_count(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
+bool learn_cg_shape_ok(const Ctx& c);   // filters per CTA <= 8 and 2 J NF <= 6 NT
 size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem);
-// tensor-core Gram (K <= 128): 3xTF32 (float32-accurate) or BF16 operands; with rspec non-null
-// (K + J <= 128) it also writes the right-hand-side spectra [K][J][Omega]
+// spectra of nmaps real maps (codes), out[m][Omega]: the fused-sweep passes for 128 x 128 maps,
+// else the generic FFT
+cudaError_t launch_code_spectra(const Ctx& c, const float* in, int nmaps, float2* out);
+cudaError_t launch_spectra_f128(const Ctx& c, const float* in, long long nmaps, float2* out);
+// out[o][m] = in[m][o] for nmaps spectra (frequency-major copy for the tensor-core Gram)
+cudaError_t launch_spectra_transpose(const Ctx& c, const float2* in, int nmaps, float2* out);
+// tensor-core Gram (K + J <= 128): 3xTF32 (float32-accurate) or BF16 operands, reading the
+// frequency-major code spectra L.zt; also writes the right-hand-side spectra [K][J][Omega]
 cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err);
 bool gram_tc_applies(const Ctx& c);
-bool gram_tc_fuses_rhs(const Ctx& c);
 cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n);
 
 inline const GeoOps& geo_ops(const Ctx& c) {

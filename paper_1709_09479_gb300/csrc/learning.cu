@@ -988,9 +988,302 @@ cudaError_t launch_learn_gram(const Ctx& c) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// lags from the frequency-major Gram of the tensor-core path, gramT[o][p], pairs in column order
+// p = k'(k'+1)/2 + k (k <= k'), o = kh * Wc + kw. Only the La x Lb window of C_kk' = F^-1 G_kk' / D is
+// needed, so the inverse transform is two direct partial sums (G is Hermitian: C is real):
+//   T(kh, w) = sum_{kw < Wc} c(kw) G(kh, kw) e^{+2 pi i kw w / W},  c = 1 at kw = 0 and kw = W/2, else 2
+//   C(h, w)  = (1/D) sum_kh Re[T(kh, w) e^{+2 pi i kh h / H}],        |h| < fh, |w| < fw
+// with one thread per pair in both (coalesced over p), twiddles from exact integer phases.
+// ---------------------------------------------------------------------------------------------
+struct LagSepArgs {
+  int K, H, W, Wc, fh, fw, La, Lb, np;
+  const float2* gramT;   // [Omega][np]
+  float2* T;             // [H][Lb][np]
+  float* lags;           // [K][K][La][Lb]
+  float invD;
+};
+
+constexpr int kLagSepNT = 128, kLagSepU = 24, kLagSepB = 4;
+
+__device__ __forceinline__ float2 root_pos(long long m, int L) {   // exp(+2 pi i m / L)
+  int r = (int)(m % L);
+  if (r < 0) r += L;
+  float s, c;
+  sincospif(2.0f * (float)r / (float)L, &s, &c);
+  return make_float2(c, s);
+}
+
+// one thread per (pair, row kh): up to kLagSepU values of w per pass over the row (one pass when
+// 2 fw - 1 <= 24), the row's Gram values loaded kLagSepB at a time ahead of their use
+__global__ void __launch_bounds__(kLagSepNT) k_lags_rows(LagSepArgs a) {
+  extern __shared__ float2 e1[];   // [Wc][Lb]: c(kw) e^{2 pi i kw w / W}
+  const int kh = blockIdx.y;
+  for (int i = threadIdx.x; i < a.Wc * a.Lb; i += kLagSepNT) {
+    const int kw = i / a.Lb, wi = i - kw * a.Lb;
+    const float2 r = root_pos((long long)kw * (wi - (a.fw - 1)), a.W);
+    const float wt = (kw == 0 || 2 * kw == a.W) ? 1.f : 2.f;
+    e1[i] = make_float2(wt * r.x, wt * r.y);
+  }
+  __syncthreads();
+  const int p = blockIdx.x * kLagSepNT + threadIdx.x;
+  if (p >= a.np) return;
+  const float2* g = a.gramT + (size_t)kh * a.Wc * a.np + p;
+  for (int w0 = 0; w0 < a.Lb; w0 += kLagSepU) {
+    float2 acc[kLagSepU];
+#pragma unroll
+    for (int j = 0; j < kLagSepU; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int kw0 = 0; kw0 < a.Wc; kw0 += kLagSepB) {
+      float2 gv[kLagSepB];
+#pragma unroll
+      for (int b = 0; b < kLagSepB; ++b)
+        gv[b] = kw0 + b < a.Wc ? __ldg(g + (size_t)(kw0 + b) * a.np) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < kLagSepB; ++b) {
+        if (kw0 + b >= a.Wc) break;
+        const float2* e = e1 + (kw0 + b) * a.Lb + w0;
+#pragma unroll
+        for (int j = 0; j < kLagSepU; ++j)
+          if (w0 + j < a.Lb) acc[j] = cfma(gv[b], e[j], acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kLagSepU; ++j)
+      if (w0 + j < a.Lb) a.T[((size_t)kh * a.Lb + w0 + j) * a.np + p] = acc[j];
+  }
+}
+
+// acc[j] = C(h, w) for ta = h + fh - 1 = h0 + j (REV: ta = La - 1 - (h0 + j)) and the w of T column
+// wt. Both orders form each value with the same operations in the same order, so C(tau) comes out
+// bitwise the same whichever thread forms it.
+template <bool REV>
+__device__ __forceinline__ void lag_column(const LagSepArgs& a, const float2* e2, int p, int wt, int h0, float* acc) {
+  const float2* t = a.T + (size_t)wt * a.np + p;
+#pragma unroll
+  for (int j = 0; j < kLagSepU; ++j) acc[j] = 0.f;
+  for (int kh0 = 0; kh0 < a.H; kh0 += kLagSepB) {
+    float2 tv[kLagSepB];
+#pragma unroll
+    for (int b = 0; b < kLagSepB; ++b)
+      tv[b] = kh0 + b < a.H ? __ldg(t + (size_t)(kh0 + b) * a.Lb * a.np) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < kLagSepB; ++b) {
+      if (kh0 + b >= a.H) break;
+      const float2* e = e2 + (kh0 + b) * a.La;
+#pragma unroll
+      for (int j = 0; j < kLagSepU; ++j)
+        if (h0 + j < a.La) {
+          const float2 ev = e[REV ? a.La - 1 - (h0 + j) : h0 + j];
+          acc[j] = fmaf(tv[b].x, ev.x, fmaf(-tv[b].y, ev.y, acc[j]));
+        }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kLagSepNT) k_lags_cols(LagSepArgs a) {
+  extern __shared__ float2 e2[];   // [H][La]: e^{2 pi i kh h / H} / D
+  const int wi = blockIdx.y;
+  for (int i = threadIdx.x; i < a.H * a.La; i += kLagSepNT) {
+    const int kh = i / a.La, hi = i - kh * a.La;
+    const float2 r = root_pos((long long)kh * (hi - (a.fh - 1)), a.H);
+    e2[i] = make_float2(r.x * a.invD, r.y * a.invD);
+  }
+  __syncthreads();
+  const int p = blockIdx.x * kLagSepNT + threadIdx.x;
+  if (p >= a.np) return;
+  // column-order pair p = k'(k'+1)/2 + k
+  int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+  while (kp * (kp + 1) / 2 > p) --kp;
+  while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
+  const int k = p - kp * (kp + 1) / 2;
+  const int LL = a.La * a.Lb;
+  float* out = a.lags + ((size_t)k * a.K + kp) * LL;
+  float* outT = a.lags + ((size_t)kp * a.K + k) * LL;
+  for (int h0 = 0; h0 < a.La; h0 += kLagSepU) {
+    float acc[kLagSepU];
+    lag_column<false>(a, e2, p, wi, h0, acc);
+    if (k == kp) {
+      // autocorrelation: C_kk(tau) = C_kk(-tau); store the symmetrised value so the matrix of the
+      // normal equations is exactly symmetric (the writers of tau and -tau add the same two values)
+      float m[kLagSepU];
+      lag_column<true>(a, e2, p, a.Lb - 1 - wi, h0, m);
+#pragma unroll
+      for (int j = 0; j < kLagSepU; ++j) {
+        const int hi = h0 + j;
+        if (hi >= a.La) break;
+        out[hi * a.Lb + wi] = 0.5f * (acc[j] + m[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kLagSepU; ++j) {
+        const int hi = h0 + j;
+        if (hi >= a.La) break;
+        out[hi * a.Lb + wi] = acc[j];
+        outT[(a.La - 1 - hi) * a.Lb + (a.Lb - 1 - wi)] = acc[j];   // C_k'k(tau) = C_kk'(-tau)
+      }
+    }
+  }
+}
+
+// Both partial sums in one kernel for windows up to 24 x 24 (filters up to 12 x 12): a CTA owns 16
+// pairs (8 threads per pair, each with the w columns sub, sub + 8, sub + 16), walks the H rows of
+// the Gram with a four-deep cp.async ring of row tiles [Wc][16 pairs], forms T(kh, w) for its
+// columns and adds Re[T e^{2 pi i kh h / H}] / D into its C(h, w) registers. No T buffer.
+constexpr int kLfPairs = 16, kLfSub = 8, kLfNT = kLfPairs * kLfSub, kLfNW = 3, kLfNH = 24, kLfStages = 4;
+
+__device__ __forceinline__ void cp_async8_lag(void* dst, const void* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+
+size_t lags_fused_smem(const Ctx& c) {
+  const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
+  return ((size_t)c.g.Wc * Lb + (size_t)c.g.H * La + (size_t)kLfStages * c.g.Wc * kLfPairs) * sizeof(float2);
+}
+
+bool lags_fused_applies(const Ctx& c) {
+  const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
+  return La <= kLfNH && Lb <= kLfNW * kLfSub && lags_fused_smem(c) <= kSmemLimit &&
+         (size_t)kLfPairs * La * Lb * sizeof(float) <= (size_t)kLfStages * c.g.Wc * kLfPairs * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(kLfNT) k_lags_fused(LagSepArgs a) {
+  extern __shared__ float2 lsm[];
+  float2* e1 = lsm;                          // [Wc][Lb]: c(kw) e^{2 pi i kw w / W}
+  float2* e2 = e1 + a.Wc * a.Lb;             // [H][La]: e^{2 pi i kh h / H} / D
+  float2* gs = e2 + a.H * a.La;              // [kLfStages][Wc][kLfPairs]
+  for (int i = threadIdx.x; i < a.Wc * a.Lb; i += kLfNT) {
+    const int kw = i / a.Lb, wi = i - kw * a.Lb;
+    const float2 r = root_pos((long long)kw * (wi - (a.fw - 1)), a.W);
+    const float wt = (kw == 0 || 2 * kw == a.W) ? 1.f : 2.f;
+    e1[i] = make_float2(wt * r.x, wt * r.y);
+  }
+  for (int i = threadIdx.x; i < a.H * a.La; i += kLfNT) {
+    const int kh = i / a.La, hi = i - kh * a.La;
+    const float2 r = root_pos((long long)kh * (hi - (a.fh - 1)), a.H);
+    e2[i] = make_float2(r.x * a.invD, r.y * a.invD);
+  }
+  const int p0 = blockIdx.x * kLfPairs;
+  const int q = threadIdx.x / kLfSub, sub = threadIdx.x % kLfSub;
+  const int tile = a.Wc * kLfPairs;
+  auto issue_row = [&](int kh) {
+    float2* dst = gs + (kh % kLfStages) * tile;
+    const float2* src = a.gramT + (size_t)kh * a.Wc * a.np + p0;
+    for (int i = threadIdx.x; i < tile; i += kLfNT) {
+      const int kw = i / kLfPairs, qq = i - kw * kLfPairs;
+      const bool v = p0 + qq < a.np;
+      cp_async8_lag(dst + i, src + (size_t)kw * a.np + (v ? qq : 0), v);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  for (int r = 0; r < kLfStages - 1; ++r) {
+    if (r < a.H) issue_row(r);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  float acc[kLfNW][kLfNH];
+#pragma unroll
+  for (int w = 0; w < kLfNW; ++w)
+#pragma unroll
+    for (int h = 0; h < kLfNH; ++h) acc[w][h] = 0.f;
+  for (int kh = 0; kh < a.H; ++kh) {
+    if (kh + kLfStages - 1 < a.H) issue_row(kh + kLfStages - 1);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kLfStages - 1) : "memory");
+    __syncthreads();   // row kh (and, on the first pass, the twiddle tables) visible to all
+    const float2* g = gs + (kh % kLfStages) * tile + q;
+    float2 t[kLfNW];
+#pragma unroll
+    for (int w = 0; w < kLfNW; ++w) t[w] = make_float2(0.f, 0.f);
+    for (int kw = 0; kw < a.Wc; ++kw) {
+      const float2 gv = g[kw * kLfPairs];
+      const float2* e = e1 + kw * a.Lb + sub;
+#pragma unroll
+      for (int w = 0; w < kLfNW; ++w)
+        if (sub + kLfSub * w < a.Lb) t[w] = cfma(gv, e[kLfSub * w], t[w]);
+    }
+    const float2* e = e2 + kh * a.La;
+#pragma unroll
+    for (int w = 0; w < kLfNW; ++w)
+#pragma unroll
+      for (int h = 0; h < kLfNH; ++h)
+        if (h < a.La) acc[w][h] = fmaf(t[w].x, e[h].x, fmaf(-t[w].y, e[h].y, acc[w][h]));
+    __syncthreads();   // every read of row kh's slot precedes its refill
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  // C of the CTA's pairs through shared memory (the ring is free), for the mirrored diagonal values
+  float* xs = reinterpret_cast<float*>(gs);   // [kLfPairs][La][Lb]
+  const int LL = a.La * a.Lb;
+#pragma unroll
+  for (int w = 0; w < kLfNW; ++w) {
+    const int wi = sub + kLfSub * w;
+    if (wi >= a.Lb) continue;
+#pragma unroll
+    for (int h = 0; h < kLfNH; ++h)
+      if (h < a.La) xs[q * LL + h * a.Lb + wi] = acc[w][h];
+  }
+  __syncthreads();
+  const int p = p0 + q;
+  if (p >= a.np) return;
+  int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+  while (kp * (kp + 1) / 2 > p) --kp;
+  while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
+  const int k = p - kp * (kp + 1) / 2;
+  float* out = a.lags + ((size_t)k * a.K + kp) * LL;
+  float* outT = a.lags + ((size_t)kp * a.K + k) * LL;
+  for (int i = sub; i < LL; i += kLfSub) {
+    const float v = xs[q * LL + i];
+    if (k == kp) {
+      // autocorrelation: C_kk(tau) = C_kk(-tau); the writers of tau and -tau add the same two
+      // values, so the normal-equation matrix is exactly symmetric
+      out[i] = 0.5f * (v + xs[q * LL + (LL - 1 - i)]);
+    } else {
+      out[i] = v;
+      outT[LL - 1 - i] = v;   // C_k'k(tau) = C_kk'(-tau)
+    }
+  }
+}
+
+size_t lag_sep_T_count(const Ctx& c) {
+  if (lags_fused_applies(c)) return 1;   // the fused kernel keeps T in registers
+  return (size_t)c.g.H * (2 * c.fw - 1) * ((size_t)c.K * (c.K + 1) / 2);
+}
+
+static cudaError_t launch_lag_spectra(const Ctx& c);
+
+cudaError_t launch_learn_lags_sep(const Ctx& c) {
+  const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
+  const int np = c.K * (c.K + 1) / 2;
+  LagSepArgs a{c.K, c.g.H, c.g.W, c.g.Wc, c.fh, c.fw, La, Lb, np, c.L.gram, c.L.lagT, c.L.lags,
+               1.0f / (float)c.g.D};
+  const size_t s1 = (size_t)c.g.Wc * Lb * sizeof(float2), s2 = (size_t)c.g.H * La * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_lags_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lags_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+  if (e != cudaSuccess) return e;
+  if (lags_fused_applies(c)) {
+    const size_t sf = lags_fused_smem(c);
+    if ((e = cudaFuncSetAttribute(k_lags_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf)) != cudaSuccess)
+      return e;
+    k_lags_fused<<<(np + kLfPairs - 1) / kLfPairs, kLfNT, sf, c.stream>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    c.launches += 1;
+    return launch_lag_spectra(c);
+  }
+  const int tiles = (np + kLagSepNT - 1) / kLagSepNT;
+  k_lags_rows<<<dim3(tiles, c.g.H), kLagSepNT, s1, c.stream>>>(a);
+  k_lags_cols<<<dim3(tiles, Lb), kLagSepNT, s2, c.stream>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  c.launches += 2;
+  return launch_lag_spectra(c);
+}
+
 cudaError_t launch_learn_lags(const Ctx& c) {
   cudaError_t e = geo_ops(c).lags(c);
   if (e != cudaSuccess) return e;
+  c.launches += 1;
+  return launch_lag_spectra(c);
+}
+
+static cudaError_t launch_lag_spectra(const Ctx& c) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
   LagSpecArgs a{c.K, c.fh, c.fw, La, Lb, La * c.fw, c.L.lags, c.L.chat};
   const size_t smem = (size_t)(La * c.fw + La + Lb) * sizeof(float2) + (size_t)La * Lb * sizeof(float);
@@ -1000,15 +1293,22 @@ cudaError_t launch_learn_lags(const Ctx& c) {
   return cudaGetLastError();
 }
 
+// one CTA per SM at most, and no more than the 2 NT slot words of an exchange hold (3 J per CTA)
 int learn_cg_ctas(const Ctx& c) {
   const int La = 2 * c.fh - 1;
-  return std::max(1, std::min(c.nsm, std::max(c.K, La * c.fw)));
+  const int nsm = c.nsm > 0 ? c.nsm : 1;
+  return std::max(1, std::min(std::min(nsm, 2 * kNT / (3 * c.J)), std::max(c.K, La * c.fw)));
+}
+
+bool learn_cg_shape_ok(const Ctx& c) {
+  const int G = learn_cg_ctas(c);
+  const int NF = (2 * c.fh - 1) * c.fw;
+  return (c.K + G - 1) / G <= 8 && 2 * c.J * NF <= 6 * kNT;
 }
 
 size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
-  // at least as many bins and filters per CTA as any launch of this context will have
-  const int G = std::max(1, std::min(c.nsm > 0 ? c.nsm : 1, std::max(c.K, La * c.fw)));
+  const int G = learn_cg_ctas(c);
   return cg_smem_layout(c.K, c.J, c.S2, La * c.fw, c.fh, c.fw, La, Lb, kNT, G, minv, chat_smem).total_floats *
          sizeof(float);
 }

@@ -8,11 +8,13 @@
 // With C1 = [Re Z ; Im Z] (2N x K) and C2 = [Im Z ; -Re Z]:
 //     Re G = C1^T C1,   Im G = C1^T C2.
 //
-// One CTA owns one frequency at a time (persistent over frequencies, two CTAs per SM so that one's
-// epilogue overlaps the other's MMAs). The images are taken in chunks of NC: all 128 threads load
-// z_hat_nk(w) for the chunk straight from the [N][K][Omega] spectra (rows k >= K + J and images
-// n >= N are zero), split them into tensor-core operands and store them as C1^T rows (filters) of
-// [Re over the chunk's images | Im over them] in the canonical no-swizzle K-major core-matrix layout.
+// The code spectra come frequency-major, zt[w][n K + k], so the N x K values of one frequency are
+// one contiguous run. One CTA owns one frequency at a time (persistent over frequencies, two CTAs
+// per SM so that one's epilogue overlaps the other's MMAs). The images are taken in chunks of NC:
+// all 128 threads load z_hat_nk(w) for the chunk (rows K..K+J-1 from the image spectra x_hat_nj(w);
+// rows k >= K + J and images n >= N are zero), split them into tensor-core operands and store them as
+// C1^T rows (filters) of [Re over the chunk's images | Im over them] in the canonical no-swizzle
+// K-major core-matrix layout.
 // One thread then issues tcgen05.mma (M = 128 rows = filters, N = K + J rounded up to 16): the Re G
 // accumulator pairs each K-step with itself, the Im G accumulator pairs the Re half of a chunk row
 // with its Im half and the Im half with the Re half under the descriptor's negate-B bit, so C2 is
@@ -26,9 +28,10 @@
 //   X3 = false  BF16 operands, FP32 accumulation (kind::f16), the mixed-precision mode.
 //
 // The epilogue thread of TMEM lane k reads its Re and Im rows with tcgen05.ld and writes G_kk'(w)
-// for k <= k' < K and R_kj(w) for the appended columns. Every wait on an mbarrier is bounded; on
-// timeout the CTA records CSC_ERR_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
-// returns.
+// for k <= k' < K, frequency-major with the pairs in column order (gram[w][k'(k'+1)/2 + k], so the
+// lanes of a warp store one contiguous run per column k'), and R_kj(w) for the appended columns.
+// Every wait on an mbarrier is bounded; on timeout the CTA records CSC_ERR_TIMEOUT, waits (bounded)
+// for its own MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,7 +42,7 @@
 
 namespace csc {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // warps w and w + 4 share TMEM lane quarter w & 3
 constexpr long long kTcSpinLimit = 2000000000LL;
 constexpr int kTcRowBytes = 128;                       // one chunk row: [Re | Im] of the chunk's images
 constexpr int kTcPieceBytes = 128 * kTcRowBytes;       // 128 rows
@@ -52,10 +55,25 @@ template <bool X3>
 struct TcCfg {
   static constexpr int NC = X3 ? 16 : 32;              // images per chunk (element 4 or 2 bytes)
   static constexpr int PIECES = X3 ? 2 : 1;            // hi, lo
-  static constexpr int STAGES = X3 ? 3 : 4;
+  static constexpr int STAGES = 2;                     // operand stages
+  static constexpr int RAW = X3 ? 3 : 2;               // raw (float2) chunk stages in flight
   static constexpr int STAGE_BYTES = PIECES * kTcPieceBytes;
-  static constexpr int SMEM = STAGES * STAGE_BYTES;
 };
+
+// raw chunk row stride (float2) for R = K + J rows: >= R and = 8 (mod 16), so that the two
+// images of a half-warp's conversion reads fall in opposite halves of the banks
+__host__ __device__ constexpr int raw_pitch(int R) { return (R + 7) / 16 * 16 + 8; }
+
+template <bool X3>
+size_t gram_tc_smem(int R) {
+  using C = TcCfg<X3>;
+  return (size_t)C::STAGES * C::STAGE_BYTES + (size_t)C::RAW * C::NC * raw_pitch(R) * sizeof(float2);
+}
+
+__device__ __forceinline__ void cp_async8z(void* dst, const void* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -139,12 +157,13 @@ __device__ __forceinline__ float round_tf32(float v) {
 
 struct TcGramArgs {
   int N, K, J, Omega;
-  int ntile;                // B rows (MMA N): K + J (or K) rounded up to 16, <= 128
-  int rows;                 // loaded rows: K + J when the right-hand side is fused, else K
-  const float2* zhat;       // [N][K][Omega]
+  int ntile;                // B rows (MMA N): K + J rounded up to 16, <= 128
+  int rows;                 // loaded rows: K + J
+  const float2* zt;         // [Omega][N K] frequency-major code spectra
   const float2* xhat;       // [N][J][Omega]
-  float2* gram;             // [npairs][Omega], pairs k <= k'
-  float2* rspec;            // [K][J][Omega] or null (no fused right-hand side)
+  float2* gram;             // [Omega][np], pair (k <= k') at k'(k'+1)/2 + k
+  int np;                   // K (K + 1) / 2
+  float2* rspec;            // [K][J][Omega]
   int* err;
 };
 
@@ -158,6 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wq = warp & 3, wh = warp >> 2;
   const int r8 = lane & 7, q4 = lane >> 3;
   const uint32_t tile = smem_addr(smem);
 
@@ -182,32 +202,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
   const uint32_t id_pos = idesc_mma(fmt, a.ntile, false), id_neg = idesc_mma(fmt, a.ntile, true);
   const int nchunks = (a.N + NC - 1) / NC;
 
-  // element u of this thread's share of a chunk: image 4 (u % (NC/4)) + q4, row 8 kg + r8 with
-  // kg = 4 (u / (NC/4)) + warp; a warp's 32 lanes write 32 distinct banks of one core-matrix column
-  auto load_chunk = [&](int o, int ch, float2* vals) {
-#pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      const int n = ch * NC + 4 * (u % (NC / 4)) + q4;
-      const int k = 8 * (4 * (u / (NC / 4)) + warp) + r8;
-      float2 v = make_float2(0.f, 0.f);
-      if (n < a.N) {
-        if (k < a.K) v = a.zhat[((size_t)n * a.K + k) * a.Omega + o];
-        else if (k < a.rows) v = a.xhat[((size_t)n * a.J + (k - a.K)) * a.Omega + o];
+  // raw chunks: [NC images][RP rows] float2, rows 0..K-1 the codes' spectra, K..K+J-1 the images'
+  const int R = a.rows, RP = raw_pitch(R);
+  float2* raw = reinterpret_cast<float2*>(smem + C::STAGES * C::STAGE_BYTES);
+  const size_t NK = (size_t)a.N * a.K;
+  // copies of chunk ch of frequency o into raw stage rs: thread t < R copies row t of every image
+  // (one contiguous run of K values per image for the codes); images n >= N are zero-filled
+  auto issue_chunk = [&](int o, int ch, int rs) {
+    const int k = threadIdx.x & 127;
+    if (k < R) {
+      float2* dst = raw + (size_t)rs * NC * RP + k;
+      const float2* zo = a.zt + (size_t)o * NK + k;
+#pragma unroll 4
+      for (int nl = threadIdx.x >> 7; nl < NC; nl += 2) {
+        const int n = ch * NC + nl;
+        const bool v = n < a.N;
+        const float2* src = k < a.K ? zo + (size_t)(v ? n : 0) * a.K
+                                    : a.xhat + ((size_t)(v ? n : 0) * a.J + (k - a.K)) * a.Omega + o;
+        cp_async8z(dst + nl * RP, src, v);
       }
-      vals[u] = v;
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  auto store_chunk = [&](int s, const float2* vals) {
+  // element u = 2 uu + wh of this thread's share of a chunk: image 4 (u % (NC/4)) + q4, row
+  // 8 kg + r8 with kg = 4 (u / (NC/4)) + wq; a warp's 32 lanes write 32 distinct banks of one
+  // core-matrix column
+  auto convert_chunk = [&](int rs, int s) {
+    const float2* rw = raw + (size_t)rs * NC * RP;
     uint8_t* st = smem + s * C::STAGE_BYTES;
 #pragma unroll
-    for (int u = 0; u < NC; ++u) {
+    for (int uu = 0; uu < NC / 2; ++uu) {
+      const int u = 2 * uu + wh;
       const int nl = 4 * (u % (NC / 4)) + q4;
-      const int k = 8 * (4 * (u / (NC / 4)) + warp) + r8;
+      const int k = 8 * (4 * (u / (NC / 4)) + wq) + r8;
+      const float2 v = k < R ? rw[nl * RP + k] : make_float2(0.f, 0.f);
       const int row = (k >> 3) * (int)kTcSbo + (k & 7) * 16;
       if constexpr (X3) {
         const int cre = nl * 4, cim = (NC + nl) * 4;   // byte columns
-        const float hr = round_tf32(vals[u].x), hi = round_tf32(vals[u].y);
-        const float lr = round_tf32(vals[u].x - hr), li = round_tf32(vals[u].y - hi);
+        const float hr = round_tf32(v.x), hi = round_tf32(v.y);
+        const float lr = round_tf32(v.x - hr), li = round_tf32(v.y - hi);
         uint8_t* p0 = st + row;
         uint8_t* p1 = st + kTcPieceBytes + row;
         *reinterpret_cast<float*>(p0 + (cre >> 4) * kTcLbo + (cre & 15)) = hr;
@@ -217,79 +250,93 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
       } else {
         const int cre = nl * 2, cim = (NC + nl) * 2;
         uint8_t* p0 = st + row;
-        *reinterpret_cast<__nv_bfloat16*>(p0 + (cre >> 4) * kTcLbo + (cre & 15)) = __float2bfloat16_rn(vals[u].x);
-        *reinterpret_cast<__nv_bfloat16*>(p0 + (cim >> 4) * kTcLbo + (cim & 15)) = __float2bfloat16_rn(vals[u].y);
+        *reinterpret_cast<__nv_bfloat16*>(p0 + (cre >> 4) * kTcLbo + (cre & 15)) = __float2bfloat16_rn(v.x);
+        *reinterpret_cast<__nv_bfloat16*>(p0 + (cim >> 4) * kTcLbo + (cim & 15)) = __float2bfloat16_rn(v.y);
       }
     }
   };
 
   bool ok = true;
-  int it = 0;           // chunks produced by this CTA
   int nfreq = 0;        // frequencies finished by this CTA
-  float2 vals[NC];
-  if (blockIdx.x < a.Omega) load_chunk(blockIdx.x, 0, vals);
-  for (int o = blockIdx.x; o < a.Omega && ok; o += gridDim.x) {
-    for (int ch = 0; ch < nchunks; ++ch, ++it) {
-      const int s = it % C::STAGES;
-      if (it >= C::STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((it / C::STAGES - 1) & 1))) ok = false;
-      if (ok) store_chunk(s, vals);
-      // prefetch the next chunk (of this frequency or the next one) while the MMAs run
-      if (ch + 1 < nchunks) load_chunk(o, ch + 1, vals);
-      else if (o + (int)gridDim.x < a.Omega) load_chunk(o + gridDim.x, 0, vals);
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      if (__syncthreads_and(ok ? 1 : 0) == 0) { ok = false; break; }
-      if (threadIdx.x == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t base = tile + (uint32_t)(s * C::STAGE_BYTES);
+  // this CTA's chunk sequence: (o, ch) for o = blockIdx.x, blockIdx.x + gridDim.x, ..., ch < nchunks
+  const int nmine = blockIdx.x < a.Omega ? ((a.Omega - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) : 0;
+  const int total = nmine * nchunks;
+  auto chunk_o = [&](int i) { return (int)blockIdx.x + (i / nchunks) * (int)gridDim.x; };
+  for (int i = 0; i < C::RAW - 1; ++i) {
+    if (i < total) issue_chunk(chunk_o(i), i % nchunks, i % C::RAW);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int it = 0; it < total && ok; ++it) {
+    const int o = chunk_o(it), ch = it % nchunks;
+    // copies of chunk it + RAW - 1 go into the raw stage that chunk it - 1 used (converted before
+    // the last block barrier)
+    const int ahead = it + C::RAW - 1;
+    if (ahead < total) issue_chunk(chunk_o(ahead), ahead % nchunks, ahead % C::RAW);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(C::RAW - 1) : "memory");   // chunk it has landed
+    __syncthreads();
+    const int s = it % C::STAGES;
+    if (it >= C::STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((it / C::STAGES - 1) & 1))) ok = false;
+    if (ok) convert_chunk(it % C::RAW, s);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    if (__syncthreads_and(ok ? 1 : 0) == 0) { ok = false; break; }
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = tile + (uint32_t)(s * C::STAGE_BYTES);
 #pragma unroll
-        for (int ks = 0; ks < kTcKSteps; ++ks) {
-          const int kb = ks < kTcKSteps / 2 ? ks + kTcKSteps / 2 : ks - kTcKSteps / 2;
-          const uint32_t idi = ks < kTcKSteps / 2 ? id_pos : id_neg;
+      for (int ks = 0; ks < kTcKSteps; ++ks) {
+        const int kb = ks < kTcKSteps / 2 ? ks + kTcKSteps / 2 : ks - kTcKSteps / 2;
+        const uint32_t idi = ks < kTcKSteps / 2 ? id_pos : id_neg;
 #pragma unroll
-          for (int c = 0; c < (X3 ? 3 : 1); ++c) {
-            const uint32_t pa = (c == 2) ? kTcPieceBytes : 0u;   // hi.hi, hi.lo, lo.hi
-            const uint32_t pb = (c == 1) ? kTcPieceBytes : 0u;
-            const uint64_t ad = smem_desc(base + pa + (uint32_t)ks * 2u * kTcLbo);
-            const uint64_t bre = smem_desc(base + pb + (uint32_t)ks * 2u * kTcLbo);
-            const uint64_t bim = smem_desc(base + pb + (uint32_t)kb * 2u * kTcLbo);
-            const uint32_t accum = (ch > 0 || ks > 0 || c > 0) ? 1u : 0u;
-            mma<X3>(acc_re, ad, bre, id_pos, accum);
-            mma<X3>(acc_im, ad, bim, idi, accum);
-          }
+        for (int c = 0; c < (X3 ? 3 : 1); ++c) {
+          const uint32_t pa = (c == 2) ? kTcPieceBytes : 0u;   // hi.hi, hi.lo, lo.hi
+          const uint32_t pb = (c == 1) ? kTcPieceBytes : 0u;
+          const uint64_t ad = smem_desc(base + pa + (uint32_t)ks * 2u * kTcLbo);
+          const uint64_t bre = smem_desc(base + pb + (uint32_t)ks * 2u * kTcLbo);
+          const uint64_t bim = smem_desc(base + pb + (uint32_t)kb * 2u * kTcLbo);
+          const uint32_t accum = (ch > 0 || ks > 0 || c > 0) ? 1u : 0u;
+          mma<X3>(acc_re, ad, bre, id_pos, accum);
+          mma<X3>(acc_im, ad, bim, idi, accum);
         }
-        mma_commit(&empty_bar[s]);
-        if (ch + 1 == nchunks) mma_commit(&acc_bar);
       }
+      mma_commit(&empty_bar[s]);
+      if (ch + 1 == nchunks) mma_commit(&acc_bar);
     }
+    if (ch + 1 < nchunks) continue;
     if (!ok) break;
     // epilogue: the frequency's accumulators are complete
     if (!mbar_wait(&acc_bar, (uint32_t)(nfreq & 1))) ok = false;
     ++nfreq;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (__syncthreads_and(ok ? 1 : 0) == 0) { ok = false; break; }
-    const int k = 32 * warp + lane;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    for (int c0 = 0; c0 < a.ntile; c0 += 16) {
-      float gr[16], gi[16];
+    // warp w reads TMEM lanes 32 (w & 3) .. + 31 (filter k); warps w < 4 take the first half of the
+    // 16-column groups, warps w >= 4 the rest
+    const int k = 32 * wq + lane;
+    const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+    const int ngroups = a.ntile / 16, gsplit = (ngroups + 1) / 2;
+    // G_kk'(w) at gram[w][k'(k'+1)/2 + k]: for one column k' the lanes' k are consecutive, so a
+    // warp's store is one contiguous run
+    float2* gcol = a.gram + (size_t)o * a.np + k;
+    float2* rrow = a.rspec + ((long long)k * a.J - a.K) * a.Omega + o;
+    for (int gi0 = wh ? gsplit : 0; gi0 < (wh ? ngroups : gsplit); ++gi0) {
+      const int c0 = 16 * gi0;
+      float gr[16], gim[16];
       tmem_ld16(acc_re + lane_off + (uint32_t)c0, gr);
-      tmem_ld16(acc_im + lane_off + (uint32_t)c0, gi);
+      tmem_ld16(acc_im + lane_off + (uint32_t)c0, gim);
       if (k < a.K) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int kp = c0 + i;
-          if (kp >= k && kp < a.K) {
-            const long long p = (long long)k * a.K - (long long)k * (k - 1) / 2 + (kp - k);
-            a.gram[p * a.Omega + o] = make_float2(gr[i], gi[i]);
-          } else if (kp >= a.K && kp < a.rows && a.rspec) {
-            a.rspec[((size_t)k * a.J + (kp - a.K)) * a.Omega + o] = make_float2(gr[i], gi[i]);
-          }
+          if (kp >= k && kp < a.K) gcol[kp * (kp + 1) / 2] = make_float2(gr[i], gim[i]);
+          else if (kp >= a.K && kp < a.rows) rrow[(long long)kp * a.Omega] = make_float2(gr[i], gim[i]);
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   }
   if (!ok && threadIdx.x == 0) atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   // drain: every MMA this CTA issued has completed before its TMEM is released
   if (threadIdx.x == 0) mma_commit(&drain_bar);
   if (!mbar_wait(&drain_bar, 0u)) {
@@ -301,17 +348,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols));
 }
 
-bool gram_tc_applies(const Ctx& c) { return c.K <= 128; }
+// out[o][m] = in[m][o]: 32 x 32 tiles through shared memory (both sides in 256-byte coalesced rows)
+constexpr int kTrTile = 32;
 
-bool gram_tc_fuses_rhs(const Ctx& c) { return c.K + c.J <= 128; }
+__global__ void __launch_bounds__(256) k_spectra_transpose(const float2* __restrict__ in, int nmaps, int Omega,
+                                                           float2* __restrict__ out) {
+  __shared__ float2 tile[kTrTile][kTrTile + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int tiles_o = (Omega + kTrTile - 1) / kTrTile;
+  const long long ntiles = (long long)tiles_o * ((nmaps + kTrTile - 1) / kTrTile);
+  for (long long tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
+    const int to = (int)(tid % tiles_o), tm = (int)(tid / tiles_o);
+    const int o0 = to * kTrTile, m0 = tm * kTrTile;
+    __syncthreads();   // the previous tile's reads precede these writes
+#pragma unroll
+    for (int r = ty; r < kTrTile; r += 8) {
+      const int m = m0 + r, o = o0 + tx;
+      if (m < nmaps && o < Omega) tile[r][tx] = __ldcs(in + (size_t)m * Omega + o);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < kTrTile; r += 8) {
+      const int o = o0 + r, m = m0 + tx;
+      if (m < nmaps && o < Omega) out[(size_t)o * nmaps + m] = tile[tx][r];
+    }
+  }
+}
+
+cudaError_t launch_spectra_transpose(const Ctx& c, const float2* in, int nmaps, float2* out) {
+  if (nmaps <= 0) return cudaSuccess;
+  const long long ntiles = (long long)((c.g.Omega + kTrTile - 1) / kTrTile) * ((nmaps + kTrTile - 1) / kTrTile);
+  const int grid = (int)std::min<long long>(ntiles, (long long)c.nsm * 8);
+  k_spectra_transpose<<<grid, 256, 0, c.stream>>>(in, nmaps, c.g.Omega, out);
+  return cudaGetLastError();
+}
+
+bool gram_tc_applies(const Ctx& c) { return c.K + c.J <= 128; }
 
 template <bool X3>
 static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err) {
-  const int rows = rspec ? c.K + c.J : c.K;
+  const int rows = c.K + c.J;
   const int ntile = (rows + 15) / 16 * 16;
-  TcGramArgs a{c.N, c.K, c.J, c.g.Omega, ntile, rows, c.L.zhat, c.xhat, c.L.gram, rspec, dev_err};
+  TcGramArgs a{c.N, c.K, c.J, c.g.Omega, ntile, rows, c.L.zt, c.xhat, c.L.gram, c.K * (c.K + 1) / 2, rspec, dev_err};
   // at least 80 KB per CTA keeps at most two CTAs (2 x 256 TMEM columns) per SM
-  const int smem = std::max(TcCfg<X3>::SMEM, 80 * 1024);
+  const int smem = (int)std::max<size_t>(gram_tc_smem<X3>(rows), 80 * 1024);
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min(c.g.Omega, 2 * c.nsm);
@@ -320,8 +400,7 @@ static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err) {
 }
 
 cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err) {
-  if (!gram_tc_applies(c)) return cudaErrorInvalidValue;
-  if (rspec && !gram_tc_fuses_rhs(c)) return cudaErrorInvalidValue;
+  if (!gram_tc_applies(c) || !rspec) return cudaErrorInvalidValue;
   return bf16 ? launch_gram_tc_t<false>(c, rspec, dev_err) : launch_gram_tc_t<true>(c, rspec, dev_err);
 }
 
