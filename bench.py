@@ -378,6 +378,17 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     return out
 
 
+def max_over_ranks(value, dist, dev=None):
+    """The largest of every rank's value (the job's time is its slowest replica's); a no-op without a
+    process group. dev: the device of the collective's tensor (None: host, for gloo)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -428,9 +439,7 @@ def run_ours(args):
     tm = sv.timing_read()
     sv.timing_enable(False)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     iters_total = w["n_code"] * args.steps * world
     value = iters_total / (ms / 1e3)
 
