@@ -2,10 +2,14 @@
 
     python -m paper_1709_09479_gb300.profile_case coding [--N 100 --K 100 --H 128 --W 128 --iters 3]
     python -m paper_1709_09479_gb300.profile_case learning [...]
+    python -m paper_1709_09479_gb300.profile_case uneven [--iters 3]
 
 coding: csc_code with `iters` ADMM iterations (launch order: 2 spectra, solve setup, spectra,
 prologue sweep, then `iters` sweeps). learning: one csc_code of `iters` iterations, then csc_learn
-with `steps` learning steps. Inputs are the seeded 1/f^2 fields and Gaussian dictionary of bench.py.
+with `steps` learning steps. uneven: the 256-image batch of bench.py's uneven256 workload (sides from
+the even 7-smooth sizes in [64, 128], K = 64), one csc_code of `iters` iterations (launch order: the
+autotuner's two sweeps per candidate configuration, then the call's prologue and sweeps). Inputs are
+the seeded 1/f^2 fields and Gaussian dictionaries of bench.py.
 """
 import argparse
 import sys
@@ -15,7 +19,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["coding", "learning"])
+    ap.add_argument("what", choices=["coding", "learning", "uneven"])
     ap.add_argument("--N", type=int, default=100)
     ap.add_argument("--K", type=int, default=100)
     ap.add_argument("--H", type=int, default=128)
@@ -27,6 +31,22 @@ def main():
     import torch
 
     from paper_1709_09479_gb300 import csc, inputs
+    if a.what == "uneven":
+        sides = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
+        rng = np.random.default_rng(3)
+        sizes = [(int(rng.choice(sides)), int(rng.choice(sides))) for _ in range(256)]
+        K = 64
+        xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
+        x = torch.from_numpy(xs.astype(np.float32)).cuda()
+        d = torch.from_numpy(inputs.unit_filters(30, K, 1, (a.s, a.s)).astype(np.float32)).cuda()
+        npx = sum(H * W for H, W in sizes)
+        v = torch.zeros(K * npx, device="cuda")
+        z = torch.empty_like(v)
+        with csc.Solver(J=1, K=K, fs=(a.s, a.s), dims_list=sizes, beta=1.0, rho=0.1) as sv:
+            sv.code(x, d, v, z, a.iters)
+        torch.cuda.synchronize()
+        print("ok", float(v.abs().sum()))
+        return 0
     x = torch.from_numpy(inputs.powerlaw_field(2, a.N, 1, (a.H, a.W)).astype(np.float32)).cuda()
     d = torch.from_numpy(inputs.unit_filters(21, a.K, 1, (a.s, a.s)).astype(np.float32)).cuda()
     v = torch.zeros((a.N, a.K, a.H, a.W), device="cuda")
