@@ -1125,33 +1125,40 @@ __global__ void __launch_bounds__(kLagSepNT) k_lags_cols(LagSepArgs a) {
   }
 }
 
-// Both partial sums in one kernel for windows up to 24 x 24 (filters up to 12 x 12): a CTA owns 16
-// pairs (8 threads per pair, each with the w columns sub, sub + 8, sub + 16), walks the H rows of
-// the Gram with a four-deep cp.async ring of row tiles [Wc][16 pairs], forms T(kh, w) for its
-// columns and adds Re[T e^{2 pi i kh h / H}] / D into its C(h, w) registers. No T buffer.
-constexpr int kLfPairs = 16, kLfSub = 8, kLfNT = kLfPairs * kLfSub, kLfNW = 3, kLfNH = 24, kLfStages = 4;
+// Both partial sums in one kernel for windows up to 24 x 24 (filters up to 12 x 12): a CTA owns 8
+// pairs; for each pair 8 threads own the w columns sub, sub + 8, sub + 16 and 4 thread groups split
+// the H rows of the Gram (group g takes rows g, g + 4, ...), each group with a four-deep cp.async
+// ring of its row tiles [Wc][8 pairs]. A thread forms T(kh, w) for its columns and adds
+// Re[T e^{2 pi i kh h / H}] / D into its C(h, w) registers; the four groups' partial windows are
+// then added in group order through shared memory. No T buffer.
+constexpr int kLfPairs = 8, kLfSub = 8, kLfGroups = 4, kLfNT = kLfPairs * kLfSub * kLfGroups, kLfNW = 3, kLfNH = 24,
+              kLfStages = 4;
 
 __device__ __forceinline__ void cp_async8_lag(void* dst, const void* src, bool valid) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
 }
 
+static size_t lags_fused_ring(const Ctx& c) {
+  return (size_t)kLfGroups * kLfStages * c.g.Wc * kLfPairs * sizeof(float2);
+}
+
 size_t lags_fused_smem(const Ctx& c) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
-  return ((size_t)c.g.Wc * Lb + (size_t)c.g.H * La + (size_t)kLfStages * c.g.Wc * kLfPairs) * sizeof(float2);
+  return ((size_t)c.g.Wc * Lb + (size_t)c.g.H * La) * sizeof(float2) + lags_fused_ring(c);
 }
 
 bool lags_fused_applies(const Ctx& c) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
   return La <= kLfNH && Lb <= kLfNW * kLfSub && lags_fused_smem(c) <= kSmemLimit &&
-         (size_t)kLfPairs * La * Lb * sizeof(float) <= (size_t)kLfStages * c.g.Wc * kLfPairs * sizeof(float2);
+         (size_t)kLfGroups * kLfPairs * La * Lb * sizeof(float) <= lags_fused_ring(c);
 }
 
 __global__ void __launch_bounds__(kLfNT) k_lags_fused(LagSepArgs a) {
   extern __shared__ float2 lsm[];
   float2* e1 = lsm;                          // [Wc][Lb]: c(kw) e^{2 pi i kw w / W}
   float2* e2 = e1 + a.Wc * a.Lb;             // [H][La]: e^{2 pi i kh h / H} / D
-  float2* gs = e2 + a.H * a.La;              // [kLfStages][Wc][kLfPairs]
+  float2* gs = e2 + a.H * a.La;              // [kLfGroups][kLfStages][Wc][kLfPairs]
   for (int i = threadIdx.x; i < a.Wc * a.Lb; i += kLfNT) {
     const int kw = i / a.Lb, wi = i - kw * a.Lb;
     const float2 r = root_pos((long long)kw * (wi - (a.fw - 1)), a.W);
@@ -1164,54 +1171,61 @@ __global__ void __launch_bounds__(kLfNT) k_lags_fused(LagSepArgs a) {
     e2[i] = make_float2(r.x * a.invD, r.y * a.invD);
   }
   const int p0 = blockIdx.x * kLfPairs;
-  const int q = threadIdx.x / kLfSub, sub = threadIdx.x % kLfSub;
+  const int grp = threadIdx.x / (kLfPairs * kLfSub);        // row group
+  const int gt = threadIdx.x % (kLfPairs * kLfSub);         // thread within the group
+  const int q = gt / kLfSub, sub = gt % kLfSub;
   const int tile = a.Wc * kLfPairs;
-  auto issue_row = [&](int kh) {
-    float2* dst = gs + (kh % kLfStages) * tile;
-    const float2* src = a.gramT + (size_t)kh * a.Wc * a.np + p0;
-    for (int i = threadIdx.x; i < tile; i += kLfNT) {
-      const int kw = i / kLfPairs, qq = i - kw * kLfPairs;
-      const bool v = p0 + qq < a.np;
-      cp_async8_lag(dst + i, src + (size_t)kw * a.np + (v ? qq : 0), v);
+  float2* ring = gs + (size_t)grp * kLfStages * tile;
+  const int nrounds = (a.H + kLfGroups - 1) / kLfGroups;
+  auto issue_row = [&](int r) {   // row kh = grp + kLfGroups r of this group into slot r % kLfStages
+    const int kh = grp + kLfGroups * r;
+    if (kh < a.H) {
+      float2* dst = ring + (r % kLfStages) * tile;
+      const float2* src = a.gramT + (size_t)kh * a.Wc * a.np + p0;
+      for (int i = gt; i < tile; i += kLfPairs * kLfSub) {
+        const int kw = i / kLfPairs, qq = i - kw * kLfPairs;
+        const bool v = p0 + qq < a.np;
+        cp_async8_lag(dst + i, src + (size_t)kw * a.np + (v ? qq : 0), v);
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  for (int r = 0; r < kLfStages - 1; ++r) {
-    if (r < a.H) issue_row(r);
-    else asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
+  for (int r = 0; r < kLfStages - 1; ++r) issue_row(r);
   float acc[kLfNW][kLfNH];
 #pragma unroll
   for (int w = 0; w < kLfNW; ++w)
 #pragma unroll
     for (int h = 0; h < kLfNH; ++h) acc[w][h] = 0.f;
-  for (int kh = 0; kh < a.H; ++kh) {
-    if (kh + kLfStages - 1 < a.H) issue_row(kh + kLfStages - 1);
-    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int r = 0; r < nrounds; ++r) {
+    issue_row(r + kLfStages - 1);
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kLfStages - 1) : "memory");
-    __syncthreads();   // row kh (and, on the first pass, the twiddle tables) visible to all
-    const float2* g = gs + (kh % kLfStages) * tile + q;
-    float2 t[kLfNW];
+    __syncthreads();   // row r of every group (and, on the first pass, the twiddle tables) visible
+    const int kh = grp + kLfGroups * r;
+    if (kh < a.H) {
+      const float2* g = ring + (r % kLfStages) * tile + q;
+      float2 t[kLfNW];
 #pragma unroll
-    for (int w = 0; w < kLfNW; ++w) t[w] = make_float2(0.f, 0.f);
-    for (int kw = 0; kw < a.Wc; ++kw) {
-      const float2 gv = g[kw * kLfPairs];
-      const float2* e = e1 + kw * a.Lb + sub;
+      for (int w = 0; w < kLfNW; ++w) t[w] = make_float2(0.f, 0.f);
+      for (int kw = 0; kw < a.Wc; ++kw) {
+        const float2 gv = g[kw * kLfPairs];
+        const float2* e = e1 + kw * a.Lb + sub;
+#pragma unroll
+        for (int w = 0; w < kLfNW; ++w)
+          if (sub + kLfSub * w < a.Lb) t[w] = cfma(gv, e[kLfSub * w], t[w]);
+      }
+      const float2* e = e2 + kh * a.La;
 #pragma unroll
       for (int w = 0; w < kLfNW; ++w)
-        if (sub + kLfSub * w < a.Lb) t[w] = cfma(gv, e[kLfSub * w], t[w]);
+#pragma unroll
+        for (int h = 0; h < kLfNH; ++h)
+          if (h < a.La) acc[w][h] = fmaf(t[w].x, e[h].x, fmaf(-t[w].y, e[h].y, acc[w][h]));
     }
-    const float2* e = e2 + kh * a.La;
-#pragma unroll
-    for (int w = 0; w < kLfNW; ++w)
-#pragma unroll
-      for (int h = 0; h < kLfNH; ++h)
-        if (h < a.La) acc[w][h] = fmaf(t[w].x, e[h].x, fmaf(-t[w].y, e[h].y, acc[w][h]));
-    __syncthreads();   // every read of row kh's slot precedes its refill
+    __syncthreads();   // every read of round r's slots precedes their refill
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  // C of the CTA's pairs through shared memory (the ring is free), for the mirrored diagonal values
-  float* xs = reinterpret_cast<float*>(gs);   // [kLfPairs][La][Lb]
+  __syncthreads();
+  // the groups' partial windows through shared memory (the rings are free): [group][pair][La][Lb]
+  float* xs = reinterpret_cast<float*>(gs);
   const int LL = a.La * a.Lb;
 #pragma unroll
   for (int w = 0; w < kLfNW; ++w) {
@@ -1219,26 +1233,31 @@ __global__ void __launch_bounds__(kLfNT) k_lags_fused(LagSepArgs a) {
     if (wi >= a.Lb) continue;
 #pragma unroll
     for (int h = 0; h < kLfNH; ++h)
-      if (h < a.La) xs[q * LL + h * a.Lb + wi] = acc[w][h];
+      if (h < a.La) xs[(grp * kLfPairs + q) * LL + h * a.Lb + wi] = acc[w][h];
   }
   __syncthreads();
-  const int p = p0 + q;
-  if (p >= a.np) return;
-  int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
-  while (kp * (kp + 1) / 2 > p) --kp;
-  while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
-  const int k = p - kp * (kp + 1) / 2;
-  float* out = a.lags + ((size_t)k * a.K + kp) * LL;
-  float* outT = a.lags + ((size_t)kp * a.K + k) * LL;
-  for (int i = sub; i < LL; i += kLfSub) {
-    const float v = xs[q * LL + i];
+  auto total = [&](int qq, int i) {   // the four groups' sum, always in group order
+    float v = 0.f;
+#pragma unroll
+    for (int gg = 0; gg < kLfGroups; ++gg) v += xs[(gg * kLfPairs + qq) * LL + i];
+    return v;
+  };
+  for (int e = threadIdx.x; e < kLfPairs * LL; e += kLfNT) {
+    const int qq = e / LL, i = e - qq * LL;
+    const int p = p0 + qq;
+    if (p >= a.np) continue;
+    int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    while (kp * (kp + 1) / 2 > p) --kp;
+    while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
+    const int k = p - kp * (kp + 1) / 2;
+    const float v = total(qq, i);
     if (k == kp) {
       // autocorrelation: C_kk(tau) = C_kk(-tau); the writers of tau and -tau add the same two
       // values, so the normal-equation matrix is exactly symmetric
-      out[i] = 0.5f * (v + xs[q * LL + (LL - 1 - i)]);
+      a.lags[((size_t)k * a.K + kp) * LL + i] = 0.5f * (v + total(qq, LL - 1 - i));
     } else {
-      out[i] = v;
-      outT[LL - 1 - i] = v;   // C_k'k(tau) = C_kk'(-tau)
+      a.lags[((size_t)k * a.K + kp) * LL + i] = v;
+      a.lags[((size_t)kp * a.K + k) * LL + (LL - 1 - i)] = v;   // C_k'k(tau) = C_kk'(-tau)
     }
   }
 }
