@@ -290,6 +290,18 @@ def measure_extensions(csc, torch, dev, hbm_peak):
                         "pixels": npx, "size_classes": desc["size_classes"], "launch": desc,
                         "coding_iters_per_s": iters / (ms / 1e3), "ms_per_call_of_10_iters": ms,
                         "sweep_us": sweep_s * 1e6, "sweep_hbm_frac": alg / sweep_s / 1e9 / hbm_peak}
+    # the same batch with the per-frequency contractions in bfloat16 (float32 accumulation)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1,
+                    precision=csc.CSC_MIXED_BF16) as sv3:
+        v.zero_()
+        sv3.code(x, d, v, z, 3)
+        sv3.timing_read()
+        sv3.timing_enable(True)
+        sv3.code(x, d, v, z, iters)
+        tm3 = sv3.timing_read()
+    sweep3 = tm3["sweep_ms"] / max(tm3["sweep_launches"], 1) / 1e3
+    out["uneven256"]["bf16"] = {"sweep_us": sweep3 * 1e6, "sweep_hbm_frac": alg / sweep3 / 1e9 / hbm_peak,
+                                "coding_iters_per_s_sweeps_only": 1.0 / sweep3}
     del x, v, z
 
     # --- unroll32: batch 32, 128x128, K=64, T=20, checkpoints every 5 --------------------------

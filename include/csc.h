@@ -61,8 +61,10 @@ typedef enum {
                           CSC_FP32 the Gram also runs on the tensor cores when K <= 128, as three
                           TF32 products of a hi + lo operand split (float32-accurate). The
                           per-frequency system (A(w) + I/rho)^{-1} is built in float64 in both modes.
-                          Needs K <= 128; csc_code_unrolled, csc_code_backward and the synthesis
-                          calls accept CSC_FP32 only. */
+                          csc_init needs K <= 128 in this mode. Uniform and uneven batches accept
+                          it; video contexts,
+                          csc_code_unrolled, csc_code_backward and the synthesis calls accept
+                          CSC_FP32 only. */
 } csc_precision;
 
 typedef struct {

@@ -255,6 +255,7 @@ UnevenArgs uneven_args(const Ctx& c, const float2* part_in, float2* part_out, fl
   a.buf_elems = c.U.buf_elems; a.max_omega = c.U.max_omega;
   a.cls = c.U.d_cls; a.img = c.U.d_img; a.mstart = c.U.d_mstart; a.slot = c.U.d_slot;
   a.tw = c.tw; a.dhat = c.dhat; a.pdiag = c.pdiag; a.pmat = c.pmat; a.xhat = c.xhat;
+  a.dhat16 = c.p.precision == CSC_MIXED_BF16 ? c.dhat16 : nullptr;
   a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1;
   return a;
 }
@@ -274,6 +275,11 @@ cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
     Ctx v;
     class_view(*c, im.cls, v);
     cudaError_t e = launch_fft_maps(v, x + im.x, c->J, 0, c->xhat + im.xh);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+  }
+  if (c->dhat16) {
+    cudaError_t e = launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->U.n_dhat);
     if (e != cudaSuccess) return e;
     c->launches += 1;
   }
@@ -473,7 +479,8 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   if (p.K < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: K must be >= 1");
   if (!(p.beta > 0) || !(p.rho > 0) || !std::isfinite(p.beta) || !std::isfinite(p.rho))
     return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: beta and rho must be finite and > 0");
-  if (p.precision != CSC_FP32) return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: CSC_FP32 only");
+  if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16)
+    return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: unknown precision");
   const int fh = p.fs[0], fw = p.fs[1];
   if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: filter support must be odd and >= 1");
@@ -544,6 +551,8 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   uneven_partition(c, (int)std::min<long long>(c->nsm, (long long)n_images * p.K));
   if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->dhat, U.n_dhat * sizeof(float2)) != cudaSuccess ||
+      (p.precision == CSC_MIXED_BF16 &&
+       cudaMalloc((void**)&c->dhat16, U.n_dhat * sizeof(__nv_bfloat162)) != cudaSuccess) ||
       cudaMalloc((void**)&c->pdiag, U.n_pd * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&c->pmat, U.n_pm * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->xhat, U.n_xh * sizeof(float2)) != cudaSuccess ||
@@ -846,7 +855,8 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
   if (c->uneven) {
     CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, false), "uneven setup");
-    const UnevenArgs ua = uneven_args(*c, nullptr, c->part[0], nullptr, const_cast<float*>(zd));
+    UnevenArgs ua = uneven_args(*c, nullptr, c->part[0], nullptr, const_cast<float*>(zd));
+    ua.dhat16 = nullptr;   // the objective stays float32 in every mode
     CSC_CHECK_CUDA(c, launch_sweep_uneven(ua, kObjective, c->G, c->U.nt, uneven_smem_bytes(c->U, c->J, kObjective),
                                           c->stream), "objective sweep");
     CSC_CHECK_CUDA(c, launch_objective_final_uneven(uneven_args(*c, c->part[0], nullptr, nullptr, nullptr), c->objimg,

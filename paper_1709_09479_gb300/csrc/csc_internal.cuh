@@ -85,6 +85,7 @@ struct UnevenArgs {
   const long long* slot;    // [G+N] partial-sum slot offset (float2) of (cta, image), indexed by cta + n
   const float2* tw;
   const float2* dhat;
+  const __nv_bfloat162* dhat16;   // mixed precision: bf16 copy of dhat (contraction operands), else null
   const float* pdiag;
   const float2* pmat;
   const float2* xhat;

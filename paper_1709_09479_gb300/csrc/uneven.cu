@@ -7,6 +7,7 @@
 // each image of its range once, builds that image's lambda from the previous sweep's partial sums
 // (slots of the covering CTAs in ascending order: deterministic), and streams the image's maps
 // through shared memory with the run-time FFT plan of the image's class.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,9 @@
 namespace csc {
 
 __device__ __forceinline__ float uclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
+
+// a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
+__device__ __forceinline__ float2 ubf16(float2 v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, 1) k_sweep_uneven(UnevenArgs a) {
@@ -92,12 +96,18 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_uneven(UnevenArgs a) {
       const size_t moff = (size_t)im.v + (size_t)k * D;
       float* vk = a.v ? a.v + moff : nullptr;
       const float2* dk = dhat_c + (size_t)k * J * Om;
+      // mixed precision: both operands of every complex product of the contractions in bfloat16
+      const __nv_bfloat162* dk16 = a.dhat16 ? a.dhat16 + uc.dhat + (size_t)k * J * Om : nullptr;
+      auto dval = [&](size_t i) { return dk16 ? __bfloat1622float2(dk16[i]) : __ldg(dk + i); };
       if (kLam) {
         for (int o = threadIdx.x; o < Om; o += NT) {
           float2 s = make_float2(0.f, 0.f);
 #pragma unroll
           for (int j = 0; j < kMaxJ; ++j)
-            if (j < J) s = cfmac(__ldg(dk + (size_t)j * Om + o), lam[(size_t)j * Om + o], s);
+            if (j < J) {
+              const float2 l = lam[(size_t)j * Om + o];
+              s = cfmac(dval((size_t)j * Om + o), dk16 ? ubf16(l) : l, s);
+            }
           const int h = o / Wc, c = o - h * Wc;
           buf[h * P + c] = s;
         }
@@ -159,10 +169,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_uneven(UnevenArgs a) {
         rfft2<GeoRT, NT>(g, buf, tw);
         for (int o = threadIdx.x; o < Om; o += NT) {
           const int h = o / Wc, c = o - h * Wc;
-          const float2 uh = buf[h * P + c];
+          const float2 uh = dk16 ? ubf16(buf[h * P + c]) : buf[h * P + c];
 #pragma unroll
           for (int j = 0; j < kMaxJ; ++j)
-            if (j < J) acc[(size_t)j * Om + o] = cfma(__ldg(dk + (size_t)j * Om + o), uh, acc[(size_t)j * Om + o]);
+            if (j < J) acc[(size_t)j * Om + o] = cfma(dval((size_t)j * Om + o), uh, acc[(size_t)j * Om + o]);
         }
       }
       __syncthreads();

@@ -110,3 +110,35 @@ def test_uneven_rejects_unsupported_sizes_and_calls(csc):
     with pytest.raises(csc.CscError) as e:
         csc.Solver(J=1, K=2, fs=(3, 3), dims_list=[(64, 64), (22, 16)], beta=1.0, rho=1.0)
     assert e.value.status == 2 and "22x16" in str(e.value)
+
+
+def test_uneven_bf16_contractions_against_oracle(csc):
+    """The uneven batch in CSC_MIXED_BF16 (bfloat16 operands of the per-frequency contractions,
+    float32 accumulation): a stated error bound against the float64 oracle, the float32 run on the
+    same batch within the float32 bar, and the objective float32 in both modes."""
+    import torch
+    from tests.test_gpu_precision import CODE_BF16_TOL
+    K, s, iters, beta, rho = 6, 5, 6, 0.3, 1.0
+    sizes = SIZES
+    xs, d = batch(400, sizes, K, 1, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    out = {}
+    for prec in (csc.CSC_FP32, csc.CSC_MIXED_BF16):
+        with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho, precision=prec) as sv:
+            v = torch.zeros(n_v, device="cuda")
+            z = torch.empty_like(v)
+            sv.code(flat(xs), flat([d]), v, z, iters)
+            torch.cuda.synchronize()
+            f = sv.objective(flat(xs), flat([d]), z)
+            out[prec] = (split(z, sizes, K), f)
+    zo = [O.code_admm(xo, d, beta, rho, iters)[1] for xo in xs]
+    ref = np.concatenate([a.reshape(-1) for a in zo])
+    e32 = rel(np.concatenate([a.reshape(-1) for a in out[csc.CSC_FP32][0]]), ref)
+    e16 = rel(np.concatenate([a.reshape(-1) for a in out[csc.CSC_MIXED_BF16][0]]), ref)
+    print(f"uneven coding rel err vs oracle: fp32 {e32:.2e}  bf16 {e16:.2e}")
+    assert e32 <= REL_TOL
+    assert 0 < e16 <= CODE_BF16_TOL
+    # the objective of the bf16 codes, evaluated in float32, against the oracle on the same codes
+    z16 = out[csc.CSC_MIXED_BF16][0]
+    fo = sum(O.objective(xo, d, zz, beta) for xo, zz in zip(xs, z16))
+    assert abs(out[csc.CSC_MIXED_BF16][1] - fo) <= 1e-5 * fo
