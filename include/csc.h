@@ -114,8 +114,10 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
  * time offsets -(ft-1)/2 .. (ft-1)/2, circular like the spatial ones), 3-D DFTs: the higher-order
  * extension of Sec. 3.3 with a time axis. Arrays: x [N][J][T][H][W], d [K][J][ft][fh][fw],
  * v and z [N][K][T][H][W]. Supported: H = W = 128, 1 <= T <= 64, ft <= 7 and <= T, CSC_FP32.
- * Supports csc_code, csc_objective, csc_describe and csc_destroy; the learning and reverse-mode
- * calls return CSC_ERR_UNSUPPORTED on such a context.
+ * Supports csc_code, csc_objective, csc_learn (fh <= 12, fw <= 16, K + J <= 128; the 3-D lag window
+ * (2ft-1) x (2fh-1) x (2fw-1), Jacobi-preconditioned CG driven from the host, params->cg_max and
+ * cg_tol as for csc_init), csc_describe and csc_destroy; the reverse-mode calls return
+ * CSC_ERR_UNSUPPORTED on such a context.
  */
 csc_status csc_init_video(const csc_params* params, int ft, int n_videos, const int* dims, void* stream,
                           csc_ctx** out);
@@ -143,7 +145,8 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
  * Eq. Learning_gamma; the library reaches the same d by solving the filter-space normal equations
  * (S Z^T Z S^T + 2 diag(mu)) d = S Z^T x (strong duality) with CG warm-started from the current d.
  * A filter whose codes are all zero keeps its d_k and mu_k. Channels are solved separately with
- * one shared mu (Sec. 3.3). d is in/out [K][J][fh][fw]; mu is in/out [K] (float64).
+ * one shared mu (Sec. 3.3). d is in/out [K][J][fh][fw] ([K][J][ft][fh][fw] on a video context);
+ * mu is in/out [K] (float64).
  * If cg_iters is non-NULL it receives `steps` ints (host memory): the CG iterations of each step
  * (the maximum over channels). Synchronises the stream.
  */

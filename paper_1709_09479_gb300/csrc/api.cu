@@ -117,7 +117,9 @@ void free_all(Ctx* c) {
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
-                  c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1};
+                  c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1,
+                  c->VL.z3, c->VL.zt, c->VL.x2, c->VL.x3, c->VL.gram, c->VL.rspec, c->VL.rspecT, c->VL.U, c->VL.lags,
+                  c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.st, c->VL.iters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -890,10 +892,37 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn: null context");
   Ctx* c = &ctx->c;
   if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn: not available on an uneven-batch context");
-  if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn: not available on a video context");
   if (!x || !z || !d || !mu) return fail(c, CSC_ERR_ARG, "csc_learn: null argument");
   if (steps < 0) return fail(c, CSC_ERR_ARG, "csc_learn: steps must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->video) {
+    if (!video_learn_shape_ok(*c))
+      return fail(c, CSC_ERR_SHAPE, "csc_learn: video learning needs fh, fw <= 12, K + J <= 128, T <= 64");
+    const size_t D3 = (size_t)c->T * c->g.D;
+    const size_t vx = (size_t)c->N * c->J * D3, vz = (size_t)c->N * c->K * D3;
+    const size_t vd = (size_t)c->K * c->J * c->ft * c->fh * c->fw;
+    const float *xd, *zd, *dd_c;
+    csc_status s;
+    if ((s = stage_in(c, x, &c->st_x, vx, &xd, true)) != CSC_OK) return s;
+    if ((s = stage_in(c, z, &c->st_z, vz, &zd, true)) != CSC_OK) return s;
+    if ((s = stage_in(c, (const float*)d, &c->st_d, vd, &dd_c, true)) != CSC_OK) return s;
+    float* dd = const_cast<float*>(dd_c);
+    CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
+    const int br = bracket_open(c, 1);
+    if ((s = video_learn(c, xd, zd, dd, mu, steps)) != CSC_OK) return s;
+    bracket_close(c, br);
+    if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, vd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
+    int herr = 0;
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
+    std::vector<int> its(std::max(steps, 1));
+    if (cg_iters && steps > 0)
+      CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), c->VL.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                     "iteration copy");
+    CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (herr) return fail(c, (csc_status)herr, "csc_learn: tensor-core Gram wait timed out");
+    if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+    return CSC_OK;
+  }
   const int K = c->K, J = c->J;
   const size_t nx = (size_t)c->N * J * c->g.D, nd = (size_t)K * J * c->S2;
   const size_t nz = (size_t)c->N * K * c->g.D, Om = c->g.Omega;

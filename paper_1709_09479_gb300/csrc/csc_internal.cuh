@@ -141,6 +141,28 @@ struct LearnBuffers {
   float2* lagT = nullptr;   // [H][2 fw - 1][npairs] row sums of the separable lag transform
 };
 
+// video learning workspace (video_learn.cu), allocated on the first csc_learn of a video context
+struct VideoLearnBuffers {
+  float2* z3 = nullptr;      // [N K][T][Omega] codes' 3-D spectra
+  float2* zt = nullptr;      // [T Omega][N K] frequency-major
+  float2* x2 = nullptr;      // [N J T][Omega] images' per-frame spectra
+  float2* x3 = nullptr;      // [N J][T][Omega]
+  float2* gram = nullptr;    // [T Omega][K(K+1)/2] (column pair order)
+  float2* rspec = nullptr;   // [K J][T Omega]
+  float2* rspecT = nullptr;  // [T Omega][K J]
+  float2* U = nullptr;       // [T][items][window] partial inverse DFTs
+  float* lags = nullptr;     // [K][K][2ft-1][2fh-1][2fw-1]
+  float2* chat = nullptr;    // [(2ft-1)(2fh-1) fw][K(K+1)/2]
+  float* vec = nullptr;      // b, r, z, p, y: 5 x [K][J][ft fh fw]
+  float2* phat = nullptr;    // [K J][bins]
+  float2* yhat = nullptr;
+  double* mu = nullptr;
+  int* active = nullptr;
+  void* st = nullptr;        // CG scalars and flags
+  int* iters = nullptr;
+  int iters_cap = 0;
+};
+
 struct BackwardBuffers {
   int seg_cap = 0;          // states the segment buffer holds
   float* seg = nullptr;     // [seg_cap][N][K][D] recomputed forward states
@@ -175,6 +197,7 @@ struct Ctx {
   int* err = nullptr;
   LearnBuffers L;
   BackwardBuffers B;
+  VideoLearnBuffers VL;
   bool uneven = false;
   UnevenLayout U;
   // video tensors (csc_init_video)
@@ -273,6 +296,10 @@ void set_global_error(const char* msg);
 // launchers (learning.cu)
 cudaError_t launch_learn_rhs(const Ctx& c, const float2* spec);
 cudaError_t launch_learn_gram(const Ctx& c);
+// learning on a video context (video_learn.cu): x, z, d device arrays; mu host or device; the
+// steps' CG iteration counts in c->VL.iters
+csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double* mu, int steps);
+bool video_learn_shape_ok(const Ctx& c);
 cudaError_t launch_learn_lags(const Ctx& c);       // from gram [npairs][Omega] (CUDA-core Gram)
 cudaError_t launch_learn_lags_sep(const Ctx& c);   // from the tensor-core Gram's gramT [Omega][npairs]
 size_t lag_sep_T_count(const Ctx& c);

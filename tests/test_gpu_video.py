@@ -1,6 +1,7 @@
-"""GPU parity of video coding (the higher-order extension of Sec. 3.3 with a time axis, 3-D DFTs):
-the CUDA path through csc_init_video / csc_code / csc_objective against the float64 oracle, which
-runs the same dual ADMM (Eq. Inference_solution) with n-dimensional transforms.
+"""GPU parity of video coding and learning (the higher-order extension of Sec. 3.3 with a time axis,
+3-D DFTs): the CUDA path through csc_init_video / csc_code / csc_objective / csc_learn against the
+float64 oracle, which runs the same dual ADMM (Eq. Inference_solution) and learning (Sec. 3.2) with
+n-dimensional transforms.
 
 Cases: grey and colour (J = 1, 3), odd and even frame counts, time supports 1, 3 and 5, a warm
 start, host-pointer arguments, and the objective of Eq. 1.
@@ -96,12 +97,84 @@ def test_video_rejects_unsupported_shapes(csc):
         csc.Solver(J=1, K=2, fs=(3, 3), ft=3, dims=(8, 64, 64), n_images=1, beta=0.5, rho=1.0)
     with pytest.raises(csc.CscError):
         csc.Solver(J=1, K=2, fs=(3, 3), ft=4, dims=(8, 128, 128), n_images=1, beta=0.5, rho=1.0)
-    sv = csc.Solver(J=1, K=2, fs=(3, 3), ft=3, dims=(8, 128, 128), n_images=1, beta=0.5, rho=1.0)
-    with pytest.raises(csc.CscError) as e:
+    sv = csc.Solver(J=1, K=2, fs=(13, 13), ft=3, dims=(8, 128, 128), n_images=1, beta=0.5, rho=1.0)
+    with pytest.raises(csc.CscError) as e:   # a 25-tap lag window per axis: beyond the learning kernels
         sv.learn(np.zeros((1, 1, 8, 128, 128), np.float32), np.zeros((1, 2, 8, 128, 128), np.float32),
-                 np.zeros((2, 1, 3, 3, 3), np.float32), np.full(2, 0.5), 1)
-    assert e.value.status == 8
+                 np.zeros((2, 1, 3, 13, 13), np.float32), np.full(2, 0.5), 1)
+    assert e.value.status == 2
     sv.close()
+
+
+LEARN_CASES = [
+    # (N, K, J, T, ft, s, steps)
+    (1, 3, 1, 6, 3, 5, 2),
+    (1, 4, 3, 4, 3, 5, 2),
+]
+
+
+@pytest.mark.parametrize("N,K,J,T,ft,s,steps", LEARN_CASES)
+def test_video_learning_matches_oracle(csc, N, K, J, T, ft, s, steps):
+    """Learning on video tensors (Sec. 3.2 with 3-D DFTs, Sec. 3.3's channels): the GPU's
+    filter-space normal equations against the oracle's dual gamma route, element by element."""
+    import torch
+    from paper_1709_09479_gb300 import inputs
+    x = f32(inputs.powerlaw_field(80 + T, N, J, (T, 128, 128))).astype(np.float64)
+    d = f32(inputs.unit_filters(81 + T, K, J, (ft, s, s))).astype(np.float64)
+    _, z = O.code_admm(x, d, 0.3, 1.0, 20)
+    z = f32(z).astype(np.float64)
+    mu0 = np.full(K, 0.5)
+    d_o, mu_o, _, _ = O.learn_paper(x, z, d, mu0, np.zeros_like(x), steps)
+    sv = csc.Solver(J=J, K=K, fs=(s, s), ft=ft, dims=(T, 128, 128), n_images=N, beta=0.3, rho=1.0,
+                    cg_tol=1e-7, cg_max=400)
+    dv = to_cuda(d)
+    mu = torch.tensor(mu0, device="cuda")
+    its = sv.learn(to_cuda(x), to_cuda(z), dv, mu, steps)
+    sv.close()
+    d_g, mu_g = to_np(dv), mu.cpu().numpy()
+    print(f"video learning: CG iterations {its}, filters rel err {rel(d_g, d_o):.2e}")
+    assert len(its) == steps and all(0 < i <= 400 for i in its)
+    assert rel(d_g, d_o) <= REL_TOL
+    assert maxrel(d_g, d_o) <= 3 * REL_TOL
+    np.testing.assert_allclose(mu_g, mu_o, rtol=REL_TOL)
+
+
+def test_video_learning_full_size_normal_equations(csc):
+    """The RGB video workload's full size (3 x 32 x 128 x 128, K = 64 colour filters 5 x 11 x 11): one
+    learning step's filters against the normal equations (S Z^T Z S^T + 2 diag mu) d_j = S Z^T x_j, with
+    Z and Z^T applied by the oracle's float64 3-D operators; the codes are the GPU's own."""
+    import torch
+    N, K, J, T, ft, s, beta, rho = 1, 64, 3, 32, 5, 11, 0.5, 0.1
+    x, d = problem(4, N, K, J, T, ft, s)
+    sv = csc.Solver(J=J, K=K, fs=(s, s), ft=ft, dims=(T, 128, 128), n_images=N, beta=beta, rho=rho,
+                    cg_tol=1e-6, cg_max=400)
+    v = torch.zeros((N, K, T, 128, 128), device="cuda")
+    zt = torch.empty_like(v)
+    sv.code(to_cuda(x), to_cuda(d), v, zt, 10)
+    mu0 = np.full(K, 0.5)
+    dv = to_cuda(d)
+    mu = torch.tensor(mu0, device="cuda")
+    its = sv.learn(to_cuda(x), zt, dv, mu, 1)
+    sv.close()
+    z = to_np(zt)
+    d_out, mu1 = to_np(dv), mu.cpu().numpy()
+    assert 0 < its[0] <= 400
+    active = np.array([np.any(z[:, k] != 0) for k in range(K)])
+    ok = active & (mu1 > 10 * O.MU_FLOOR)
+    assert ok.sum() >= K // 2
+    d_pre = d_out * np.maximum(1.0, mu1 / mu0)[:, None, None, None, None]
+    ops = O.LearningOperators(z)
+    fs = (ft, s, s)
+    res_num = res_den = 0.0
+    for j in range(J):
+        lhs = O.crop_support(ops.ZT(ops.Z(O.pad_support(d_pre[:, j], ops.dims))), fs) \
+            + 2.0 * mu0[:, None, None, None] * d_pre[:, j]
+        rhs = O.crop_support(ops.ZT(x[:, j]), fs)
+        res_num += np.sum((lhs - rhs)[ok] ** 2)
+        res_den += np.sum(rhs[ok] ** 2)
+    res = np.sqrt(res_num / res_den)
+    print(f"full-size video learning: CG iterations {its[0]}, normal-equation residual {res:.2e}")
+    assert res <= 1e-4
+    assert np.all(np.sqrt((d_out.reshape(K, -1) ** 2).sum(1)) <= 1 + 1e-5)
 
 
 def test_video_full_size_matches_oracle(csc):
