@@ -246,7 +246,7 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     """The spec extensions, each on its own workload, device-timed with CUDA events:
     uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
     replay), unroll32 (reverse mode through 20 unrolled iterations), video3d (higher-order coding of an
-    RGB video with 3-D transforms), mixed128 (the benchmark step in the mixed-precision mode,
+    RGB video with 3-D transforms, and one outer iteration of coding and learning), mixed128 (the benchmark step in the mixed-precision mode,
     tensor-core Gram)."""
     from paper_1709_09479_gb300 import autograd as ag
     from paper_1709_09479_gb300 import inputs
@@ -359,6 +359,22 @@ def measure_extensions(csc, torch, dev, hbm_peak):
                       "coding_iters_per_s": 1.0 / it_s, "iter_us": it_s * 1e6,
                       "ms_per_call_of_20_iters": e0.elapsed_time(e1), "algorithmic_bytes_per_iter": alg,
                       "hbm_frac": alg / it_s / 1e9 / hbm_peak}
+    # one outer iteration of Algorithm 1 on the video: 20 coding iterations + 20 learning steps
+    muv = torch.full((Kv,), 0.5, dtype=torch.float64, device=dev)
+    with csc.Solver(J=Jv, K=Kv, fs=(sv_, sv_), ft=ftv, dims=(Tv, 128, 128), n_images=1, beta=0.5, rho=0.1,
+                    cg_max=100, cg_tol=1e-6) as sv:
+        sv.code(xv, dvv, vv, zv, 20)
+        its = sv.learn(xv, zv, dvv, muv, 20)    # warm-up: workspace, first solves
+        torch.cuda.synchronize()
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        sv.code(xv, dvv, vv, zv, 20)
+        e1.record()
+        its = sv.learn(xv, zv, dvv, muv, 20)
+        e2.record()
+        torch.cuda.synchronize()
+    out["video3d"]["outer_iteration"] = {"coding_ms": e0.elapsed_time(e1), "learning_ms": e1.elapsed_time(e2),
+                                         "learning_cg_iterations": int(sum(its))}
     del xv, dvv, vv, zv
 
     # --- mixed128: the benchmark step with bf16 contractions and the tensor-core Gram ---------------

@@ -118,8 +118,8 @@ void free_all(Ctx* c) {
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
                   c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1,
-                  c->VL.z3, c->VL.zt, c->VL.x2, c->VL.x3, c->VL.gram, c->VL.rspec, c->VL.rspecT, c->VL.U, c->VL.lags,
-                  c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.st, c->VL.iters};
+                  c->VL.z3, c->VL.zt, c->VL.x2, c->VL.x3, c->VL.gram, c->VL.rspec, c->VL.rspecT, c->VL.U, c->VL.tab, c->VL.lags,
+                  c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.fscal, c->VL.part, c->VL.st, c->VL.iters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

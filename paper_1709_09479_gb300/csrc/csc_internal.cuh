@@ -151,6 +151,7 @@ struct VideoLearnBuffers {
   float2* rspec = nullptr;   // [K J][T Omega]
   float2* rspecT = nullptr;  // [T Omega][K J]
   float2* U = nullptr;       // [T][items][window] partial inverse DFTs
+  float2* tab = nullptr;     // twiddle tables of the partial inverse DFTs
   float* lags = nullptr;     // [K][K][2ft-1][2fh-1][2fw-1]
   float2* chat = nullptr;    // [(2ft-1)(2fh-1) fw][K(K+1)/2]
   float* vec = nullptr;      // b, r, z, p, y: 5 x [K][J][ft fh fw]
@@ -158,6 +159,8 @@ struct VideoLearnBuffers {
   float2* yhat = nullptr;
   double* mu = nullptr;
   int* active = nullptr;
+  float* fscal = nullptr;    // [2][K] per-step float scalars of the CG
+  double* part = nullptr;    // per-block partial sums of the CG iterations
   void* st = nullptr;        // CG scalars and flags
   int* iters = nullptr;
   int iters_cap = 0;

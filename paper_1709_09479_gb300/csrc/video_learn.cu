@@ -16,7 +16,7 @@
 //   4. lag spectra C_hat on the window grid (k_vl_lagspec), separable DFTs;
 //   5. preconditioned CG per learning step, the operator in the Fourier domain of the lag grid:
 //      taps -> bins (k_vl_t2b), y_hat_k = sum_k' C_hat_kk' p_hat_k' (k_vl_prod), bins -> taps
-//      (k_vl_b2t), and the vector updates and float64 dot products in one block (k_vl_cg); Jacobi
+//      (k_vl_b2t), and the vector updates with float64 dot products over all SMs (k_vl_it_*); Jacobi
 //      preconditioner 1 / (C_kk(0) + 2 mu_k); then mu_k <- max(mu_k ||d_k||, floor) (k_vl_step_end),
 //      and after the last step d_k <- d_k / max(1, ||d_k||).
 // Filters whose codes are all zero keep d_k and mu_k. The host drives the CG iterations in batches
@@ -42,6 +42,16 @@ __device__ __forceinline__ float2 root(long long m, int L, float sign) {   // ex
   float s, c;
   sincospif(2.0f * (float)r / (float)L, &s, &c);
   return make_float2(c, sign * s);
+}
+
+__device__ __forceinline__ int imod(int m, int L) {
+  const int r = m % L;
+  return r < 0 ? r + L : r;
+}
+
+// tab[m] = exp(sign 2 pi i m / L), m < L, built by the whole block (no barrier inside)
+__device__ __forceinline__ void build_roots(float2* tab, int L, float sign) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tab[i] = root(i, L, sign);
 }
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
@@ -76,24 +86,30 @@ __global__ void k_dft_time(const float2* __restrict__ in, float2* __restrict__ o
 struct RowsArgs {
   const float2* gT;
   int np, T, La, Lb, offa, offb;
-  float2* U;   // [T][np][La * Lb]
+  float2* U;           // [T][np][La * Lb]
+  const float2* tab;   // [Wc][Lb] c(kw) e^{2 pi i kw (wb - offb) / W}, then [H][La] e^{2 pi i kh (ha - offa) / H}
 };
+
+__global__ void k_vl_tables(RowsArgs a, float2* tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Wc * a.Lb) {
+    const int kw = i / a.Lb, wi = i - kw * a.Lb;
+    const float2 r = root((long long)kw * (wi - a.offb), W, 1.f);
+    const float wt = (kw == 0 || 2 * kw == W) ? 1.f : 2.f;
+    tab[i] = make_float2(wt * r.x, wt * r.y);
+  } else if (i < Wc * a.Lb + H * a.La) {
+    const int j = i - Wc * a.Lb;
+    const int kh = j / a.La, hi = j - kh * a.La;
+    tab[i] = root((long long)kh * (hi - a.offa), H, 1.f);
+  }
+}
 
 __global__ void __launch_bounds__(kRowsNT) k_vl_rows(RowsArgs a) {
   extern __shared__ float2 sm[];
   float2* e1 = sm;                       // [Wc][Lb]
   float2* e2 = e1 + Wc * a.Lb;           // [H][La]
   float2* ring = e2 + H * a.La;          // [kRowsStages][Wc][kRowsPairs]
-  for (int i = threadIdx.x; i < Wc * a.Lb; i += kRowsNT) {
-    const int kw = i / a.Lb, wi = i - kw * a.Lb;
-    const float2 r = root((long long)kw * (wi - a.offb), W, 1.f);
-    const float wt = (kw == 0 || 2 * kw == W) ? 1.f : 2.f;
-    e1[i] = make_float2(wt * r.x, wt * r.y);
-  }
-  for (int i = threadIdx.x; i < H * a.La; i += kRowsNT) {
-    const int kh = i / a.La, hi = i - kh * a.La;
-    e2[i] = root((long long)kh * (hi - a.offa), H, 1.f);
-  }
+  for (int i = threadIdx.x; i < Wc * a.Lb + H * a.La; i += kRowsNT) e1[i] = a.tab[i];   // e1 then e2
   const int tau = blockIdx.y;
   const int p0 = blockIdx.x * kRowsPairs;
   const int q = threadIdx.x / kRowsSub, sub = threadIdx.x % kRowsSub;
@@ -154,13 +170,17 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows(RowsArgs a) {
 
 // C(ti, i) = (1/D) sum_tau Re(U[tau][p][i] e^{2 pi i tau (ti - offt) / T}); the same operations in the
 // same order for every (p, ti, i), so C(tau) is bitwise the same whichever thread forms it
-__device__ __forceinline__ float time_sum(const float2* U, int np, int LL, int T, int p, int i, int ti, int offt,
-                                          float invD) {
+__device__ __forceinline__ float time_sum(const float2* U, const float2* twT, int np, int LL, int T, int p, int i,
+                                          int ti, int offt, float invD) {
   float s = 0.f;
+  const int step = imod(ti - offt, T);
+  int m = 0;
   for (int tau = 0; tau < T; ++tau) {
     const float2 u = U[((size_t)tau * np + p) * LL + i];
-    const float2 e = root((long long)tau * (ti - offt), T, 1.f);
+    const float2 e = twT[m];
     s = fmaf(u.x, e.x, fmaf(-u.y, e.y, s));
+    m += step;
+    if (m >= T) m -= T;
   }
   return s * invD;
 }
@@ -174,13 +194,16 @@ struct TimeArgs {
 };
 
 __global__ void k_vl_time(TimeArgs a) {
+  __shared__ float2 twT[64];   // exp(+2 pi i m / T)
+  build_roots(twT, a.T, 1.f);
+  __syncthreads();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)a.np * a.LL) return;
   const int p = (int)(e / a.LL), i = (int)(e - (long long)p * a.LL);
   const int LLL = a.Lt * a.LL;
   if (!a.lags) {
     for (int ti = 0; ti < a.Lt; ++ti)
-      a.out[(size_t)p * LLL + ti * a.LL + i] = time_sum(a.U, a.np, a.LL, a.T, p, i, ti, a.offt, a.invD);
+      a.out[(size_t)p * LLL + ti * a.LL + i] = time_sum(a.U, twT, a.np, a.LL, a.T, p, i, ti, a.offt, a.invD);
     return;
   }
   int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
@@ -190,11 +213,11 @@ __global__ void k_vl_time(TimeArgs a) {
   float* outp = a.out + ((size_t)k * a.K + kp) * LLL;
   float* outT = a.out + ((size_t)kp * a.K + k) * LLL;
   for (int ti = 0; ti < a.Lt; ++ti) {
-    const float v = time_sum(a.U, a.np, a.LL, a.T, p, i, ti, a.offt, a.invD);
+    const float v = time_sum(a.U, twT, a.np, a.LL, a.T, p, i, ti, a.offt, a.invD);
     const int idx = ti * a.LL + i;
     if (k == kp) {
       // C_kk(tau) = C_kk(-tau): the writers of tau and -tau add the same two values
-      const float m = time_sum(a.U, a.np, a.LL, a.T, p, a.LL - 1 - i, a.Lt - 1 - ti, a.offt, a.invD);
+      const float m = time_sum(a.U, twT, a.np, a.LL, a.T, p, a.LL - 1 - i, a.Lt - 1 - ti, a.offt, a.invD);
       outp[idx] = 0.5f * (v + m);
     } else {
       outp[idx] = v;
@@ -217,6 +240,12 @@ __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
   float* C = reinterpret_cast<float*>(ss);                 // [Lt][La][Lb]
   float2* R1 = ss + (Lt * La * Lb + 1) / 2;                // [Lt][La][fw]
   float2* R2 = R1 + Lt * La * fw;                          // [Lt][La][fw]
+  float2* tb_ = R2 + Lt * La * fw;                         // exp(-2 pi i m / Lb), / La, / Lt
+  float2* ta_ = tb_ + Lb;
+  float2* tt_ = ta_ + La;
+  build_roots(tb_, Lb, -1.f);
+  build_roots(ta_, La, -1.f);
+  build_roots(tt_, Lt, -1.f);
   int k = 0, rem = blockIdx.x;
   while (rem >= a.K - k) { rem -= a.K - k; ++k; }
   const int kp = k + rem;
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
     const int w2 = e % fw, row = e / fw;
     float2 s = make_float2(0.f, 0.f);
     for (int tb = 0; tb < Lb; ++tb) {
-      const float2 r = root((long long)w2 * (tb - (a.fw - 1)), Lb, -1.f);
+      const float2 r = tb_[imod(w2 * (tb - (a.fw - 1)), Lb)];
       const float cv = C[row * Lb + tb];
       s.x = fmaf(cv, r.x, s.x);
       s.y = fmaf(cv, r.y, s.y);
@@ -238,7 +267,7 @@ __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
   for (int e = threadIdx.x; e < Lt * La * fw; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, tt = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
-    for (int ta = 0; ta < La; ++ta) s = cfma(R1[(tt * La + ta) * fw + w2], root((long long)w1 * (ta - (a.fh - 1)), La, -1.f), s);
+    for (int ta = 0; ta < La; ++ta) s = cfma(R1[(tt * La + ta) * fw + w2], ta_[imod(w1 * (ta - (a.fh - 1)), La)], s);
     R2[e] = s;
   }
   __syncthreads();
@@ -248,7 +277,7 @@ __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
   for (int e = threadIdx.x; e < Lt * La * fw; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, w0 = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
-    for (int tt = 0; tt < Lt; ++tt) s = cfma(R2[(tt * La + w1) * fw + w2], root((long long)w0 * (tt - (a.ft - 1)), Lt, -1.f), s);
+    for (int tt = 0; tt < Lt; ++tt) s = cfma(R2[(tt * La + w1) * fw + w2], tt_[imod(w0 * (tt - (a.ft - 1)), Lt)], s);
     a.chat[(size_t)e * np + pidx] = cscale(s, sc);
   }
 }
@@ -272,6 +301,12 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
   float* P = reinterpret_cast<float*>(so);           // [ft][fh][fw]
   float2* Q1 = so + (a.S3 + 1) / 2;                  // [ft][fh][fw']  (w2 < fw)
   float2* Q2 = Q1 + ft * fh * fw;                    // [ft][La][fw]
+  float2* tb_ = Q2 + ft * La * fw;                   // exp(-2 pi i m / Lb), / La, / Lt
+  float2* ta_ = tb_ + a.Lb;
+  float2* tt_ = ta_ + La;
+  build_roots(tb_, a.Lb, -1.f);
+  build_roots(ta_, La, -1.f);
+  build_roots(tt_, Lt, -1.f);
   const size_t kj = blockIdx.x;
   for (int i = threadIdx.x; i < a.S3; i += blockDim.x) P[i] = a.p[kj * a.S3 + i];
   __syncthreads();
@@ -279,7 +314,7 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
     const int w2 = e % fw, row = e / fw;
     float2 s = make_float2(0.f, 0.f);
     for (int qb = 0; qb < fw; ++qb) {
-      const float2 r = root((long long)w2 * qb, a.Lb, -1.f);
+      const float2 r = tb_[(w2 * qb) % a.Lb];
       const float pv = P[row * fw + qb];
       s.x = fmaf(pv, r.x, s.x);
       s.y = fmaf(pv, r.y, s.y);
@@ -290,14 +325,14 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
   for (int e = threadIdx.x; e < ft * La * fw; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, qt = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
-    for (int qa = 0; qa < fh; ++qa) s = cfma(Q1[(qt * fh + qa) * fw + w2], root((long long)w1 * qa, La, -1.f), s);
+    for (int qa = 0; qa < fh; ++qa) s = cfma(Q1[(qt * fh + qa) * fw + w2], ta_[(w1 * qa) % La], s);
     Q2[e] = s;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < a.NF; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, w0 = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
-    for (int qt = 0; qt < ft; ++qt) s = cfma(Q2[(qt * La + w1) * fw + w2], root((long long)w0 * qt, Lt, -1.f), s);
+    for (int qt = 0; qt < ft; ++qt) s = cfma(Q2[(qt * La + w1) * fw + w2], tt_[(w0 * qt) % Lt], s);
     a.phat[kj * a.NF + e] = s;
   }
 }
@@ -337,20 +372,26 @@ __global__ void __launch_bounds__(256) k_vl_b2t(OpArgs a) {
   float2* Y = so;                        // [Lt][La][fw]
   float2* Q2 = Y + a.NF;                 // [ft][La][fw]
   float2* Q1 = Q2 + ft * La * fw;        // [ft][fh][fw]
+  float2* tb_ = Q1 + ft * fh * fw;       // exp(+2 pi i m / Lb), / La, / Lt
+  float2* ta_ = tb_ + a.Lb;
+  float2* tt_ = ta_ + La;
+  build_roots(tb_, a.Lb, 1.f);
+  build_roots(ta_, La, 1.f);
+  build_roots(tt_, Lt, 1.f);
   const size_t kj = blockIdx.x;
   for (int i = threadIdx.x; i < a.NF; i += blockDim.x) Y[i] = a.yhat[kj * a.NF + i];
   __syncthreads();
   for (int e = threadIdx.x; e < ft * La * fw; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, qt = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
-    for (int w0 = 0; w0 < Lt; ++w0) s = cfma(Y[(w0 * La + w1) * fw + w2], root((long long)w0 * qt, Lt, 1.f), s);
+    for (int w0 = 0; w0 < Lt; ++w0) s = cfma(Y[(w0 * La + w1) * fw + w2], tt_[(w0 * qt) % Lt], s);
     Q2[e] = s;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < ft * fh * fw; e += blockDim.x) {
     const int w2 = e % fw, qa = (e / fw) % fh, qt = e / (fw * fh);
     float2 s = make_float2(0.f, 0.f);
-    for (int w1 = 0; w1 < La; ++w1) s = cfma(Q2[(qt * La + w1) * fw + w2], root((long long)w1 * qa, La, 1.f), s);
+    for (int w1 = 0; w1 < La; ++w1) s = cfma(Q2[(qt * La + w1) * fw + w2], ta_[(w1 * qa) % La], s);
     Q1[e] = s;
   }
   __syncthreads();
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(256) k_vl_b2t(OpArgs a) {
     float s = 0.f;
     for (int w2 = 0; w2 < fw; ++w2) {
       const float2 v = Q1[row * fw + w2];
-      const float2 r = root((long long)w2 * qb, a.Lb, 1.f);
+      const float2 r = tb_[(w2 * qb) % a.Lb];
       s = fmaf(w2 == 0 ? 1.f : 2.f, v.x * r.x - v.y * r.y, s);
     }
     a.y[kj * a.S3 + e] = s;
@@ -388,6 +429,7 @@ struct VecArgs {
   int zero_lag;        // index of the zero lag in a [Lt][La][Lb] window
   int LLL;
   const int* active;   // [K]
+  float* fscal;        // [2][K]: 2 mu_k and the Jacobi inverse 1 / (C_kk(0) + 2 mu_k) (0 if inactive), float
   CgState* st;
   int* iters_out;      // [steps]
   int step;
@@ -411,22 +453,25 @@ __device__ void block_sum(double (&v)[N], double* red) {
   __syncthreads();
 }
 
-__device__ __forceinline__ float inv_diag(const VecArgs& a, int k) {
-  if (!a.active[k]) return 0.f;
-  const double c0 = (double)a.lags[((size_t)k * a.K + k) * a.LLL + a.zero_lag];
-  return (float)(1.0 / (c0 + 2.0 * a.mu[k]));
-}
-
-// phase 0: r = b - (y + 2 mu x) with y = C x, z = M^-1 r, p = z; rz, rr, bb
+// (the per-filter float scalars of a step are formed once per filter in float64 and stored as floats:
+// the device's float64 rate is low, so no element of the vector loops touches float64 arithmetic)
+// phase 0: the step's scalars; r = b - (y + 2 mu x) with y = C x, z = M^-1 r, p = z; rz, rr, bb
 __global__ void __launch_bounds__(kCgNT) k_vl_cg_init(VecArgs a) {
   __shared__ double red[(kCgNT / 32 + 1) * 3 * kMaxJ];
+  __shared__ float s2mu[128], sinv[128];
+  for (int k = threadIdx.x; k < a.K; k += kCgNT) {
+    const double c0 = (double)a.lags[((size_t)k * a.K + k) * a.LLL + a.zero_lag];
+    s2mu[k] = a.fscal[k] = (float)(2.0 * a.mu[k]);
+    sinv[k] = a.fscal[a.K + k] = a.active[k] ? (float)(1.0 / (c0 + 2.0 * a.mu[k])) : 0.f;
+  }
+  __syncthreads();
   const int JS = a.J * a.S3, n = a.K * JS;
   double s[3 * kMaxJ] = {};
   for (int i = threadIdx.x; i < n; i += kCgNT) {
     const int k = i / JS, j = (i - k * JS) / a.S3;
     if (!a.active[k]) { a.r[i] = a.z[i] = a.p[i] = 0.f; continue; }
-    const float rv = a.b[i] - (a.y[i] + (float)(2.0 * a.mu[k]) * a.x[i]);
-    const float zv = rv * inv_diag(a, k);
+    const float rv = a.b[i] - (a.y[i] + s2mu[k] * a.x[i]);
+    const float zv = rv * sinv[k];
     a.r[i] = rv; a.z[i] = zv; a.p[i] = zv;
     s[j] += (double)rv * zv;
     s[kMaxJ + j] += (double)rv * rv;
@@ -447,63 +492,127 @@ __global__ void __launch_bounds__(kCgNT) k_vl_cg_init(VecArgs a) {
   }
 }
 
-// one iteration after y = C p: Ap = y + 2 mu p; alpha = rz / p.Ap; x += alpha p; r -= alpha Ap;
-// z = M^-1 r; beta = rz' / rz; p = z + beta p; convergence of each channel
-__global__ void __launch_bounds__(kCgNT) k_vl_cg_iter(VecArgs a) {
-  if (a.st->done) return;
-  __shared__ double red[(kCgNT / 32 + 1) * 2 * kMaxJ];
-  __shared__ float s_alpha[kMaxJ], s_beta[kMaxJ];
-  const int JS = a.J * a.S3, n = a.K * JS;
-  double pap[kMaxJ] = {};
-  for (int i = threadIdx.x; i < n; i += kCgNT) {
-    const int k = i / JS, j = (i - k * JS) / a.S3;
-    if (!a.active[k]) continue;
-    const float apv = a.y[i] + (float)(2.0 * a.mu[k]) * a.p[i];
-    pap[j] += (double)a.p[i] * apv;
-  }
-  block_sum<kMaxJ>(pap, red);
-  if (threadIdx.x < kMaxJ) {
-    const int j = threadIdx.x;
-    s_alpha[j] = (j < a.J && !a.st->done_j[j] && pap[j] > 0.0) ? (float)(a.st->rz[j] / pap[j]) : 0.f;
+// one iteration over G blocks (after y = C p), four launches: partial p . Ap per block; alpha from
+// the partials (summed in block order) and the updates of x, r, z with partial r . z, r . r; the
+// scalars (one block: beta, convergence, the iteration count); p = z + beta p
+constexpr int kVecNT = 256;
+struct IterArgs {
+  VecArgs v;
+  int G;
+  double* part;    // [G][kMaxJ]: p . Ap
+  double* part2;   // [G][2 kMaxJ]: r . z, r . r
+  float* beta;     // [kMaxJ]
+};
+
+template <int N>
+__device__ void block_sum_small(double (&v)[N], double* red) {   // kVecNT threads; result in thread 0
+  for (int i = 0; i < N; ++i) {
+    double s = v[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[(threadIdx.x >> 5) * N + i] = s;
   }
   __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < kVecNT / 32; ++w) s += red[w * N + i];
+      v[i] = s;
+    }
+}
+
+__device__ __forceinline__ void block_range(int n, int G, int& i0, int& i1) {
+  i0 = (int)((long long)blockIdx.x * n / G);
+  i1 = (int)((long long)(blockIdx.x + 1) * n / G);
+}
+
+__global__ void __launch_bounds__(kVecNT) k_vl_it_pap(IterArgs a) {
+  const VecArgs& v = a.v;
+  if (v.st->done) return;
+  __shared__ double red[(kVecNT / 32) * kMaxJ];
+  const int JS = v.J * v.S3, n = v.K * JS;
+  int i0, i1;
+  block_range(n, a.G, i0, i1);
+  double pap[kMaxJ] = {};
+  for (int i = i0 + threadIdx.x; i < i1; i += kVecNT) {
+    const int k = i / JS, j = (i - k * JS) / v.S3;
+    if (!v.active[k]) continue;
+    const float apv = v.y[i] + v.fscal[k] * v.p[i];
+    pap[j] += (double)v.p[i] * apv;
+  }
+  block_sum_small<kMaxJ>(pap, red);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kMaxJ; ++j) a.part[blockIdx.x * kMaxJ + j] = pap[j];
+}
+
+__global__ void __launch_bounds__(kVecNT) k_vl_it_upd(IterArgs a) {
+  const VecArgs& v = a.v;
+  if (v.st->done) return;
+  __shared__ double red[(kVecNT / 32) * 2 * kMaxJ];
+  __shared__ float s_alpha[kMaxJ];
+  if (threadIdx.x < kMaxJ) {
+    const int j = threadIdx.x;
+    double pap = 0.0;
+    for (int g = 0; g < a.G; ++g) pap += a.part[g * kMaxJ + j];
+    s_alpha[j] = (j < v.J && !v.st->done_j[j] && pap > 0.0) ? (float)(v.st->rz[j] / pap) : 0.f;
+  }
+  __syncthreads();
+  const int JS = v.J * v.S3, n = v.K * JS;
+  int i0, i1;
+  block_range(n, a.G, i0, i1);
   double s[2 * kMaxJ] = {};
-  for (int i = threadIdx.x; i < n; i += kCgNT) {
-    const int k = i / JS, j = (i - k * JS) / a.S3;
-    if (!a.active[k]) continue;
+  for (int i = i0 + threadIdx.x; i < i1; i += kVecNT) {
+    const int k = i / JS, j = (i - k * JS) / v.S3;
+    if (!v.active[k]) continue;
     const float al = s_alpha[j];
-    const float pv = a.p[i];
-    const float apv = a.y[i] + (float)(2.0 * a.mu[k]) * pv;
-    a.x[i] = fmaf(al, pv, a.x[i]);
-    const float rv = fmaf(-al, apv, a.r[i]);
-    a.r[i] = rv;
-    const float zv = rv * inv_diag(a, k);
-    a.z[i] = zv;
+    const float pv = v.p[i];
+    const float apv = v.y[i] + v.fscal[k] * pv;
+    v.x[i] = fmaf(al, pv, v.x[i]);
+    const float rv = fmaf(-al, apv, v.r[i]);
+    v.r[i] = rv;
+    const float zv = rv * v.fscal[v.K + k];
+    v.z[i] = zv;
     s[j] += (double)rv * zv;
     s[kMaxJ + j] += (double)rv * rv;
   }
-  block_sum<2 * kMaxJ>(s, red);
-  if (threadIdx.x == 0) {
-    int all = 1;
-    for (int j = 0; j < a.J; ++j) {
-      if (!a.st->done_j[j]) {
-        s_beta[j] = a.st->rz[j] > 0.0 ? (float)(s[j] / a.st->rz[j]) : 0.f;
-        a.st->rz[j] = s[j];
-        a.st->rr[j] = s[kMaxJ + j];
-        a.st->done_j[j] = !(a.st->rr[j] > a.tol2 * a.st->bb[j]) || !(a.st->rz[j] > 0.0);
-      } else {
-        s_beta[j] = 0.f;
-      }
-      all = all && a.st->done_j[j];
+  block_sum_small<2 * kMaxJ>(s, red);
+  if (threadIdx.x == 0)
+    for (int u = 0; u < 2 * kMaxJ; ++u) a.part2[blockIdx.x * 2 * kMaxJ + u] = s[u];
+}
+
+__global__ void k_vl_it_scal(IterArgs a) {
+  const VecArgs& v = a.v;
+  if (threadIdx.x != 0 || v.st->done) return;
+  int all = 1;
+  for (int j = 0; j < v.J; ++j) {
+    double rz = 0.0, rr = 0.0;
+    for (int g = 0; g < a.G; ++g) {
+      rz += a.part2[g * 2 * kMaxJ + j];
+      rr += a.part2[g * 2 * kMaxJ + kMaxJ + j];
     }
-    a.st->iters += 1;
-    a.st->done = all || a.st->iters >= a.cg_max;
+    if (!v.st->done_j[j]) {
+      a.beta[j] = v.st->rz[j] > 0.0 ? (float)(rz / v.st->rz[j]) : 0.f;
+      v.st->rz[j] = rz;
+      v.st->rr[j] = rr;
+      v.st->done_j[j] = !(rr > v.tol2 * v.st->bb[j]) || !(rz > 0.0);
+    } else {
+      a.beta[j] = 0.f;
+    }
+    all = all && v.st->done_j[j];
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kCgNT) {
-    const int k = i / JS, j = (i - k * JS) / a.S3;
-    if (!a.active[k]) continue;
-    a.p[i] = fmaf(s_beta[j], a.p[i], a.z[i]);
+  v.st->iters += 1;
+  v.st->done = all || v.st->iters >= v.cg_max;
+}
+
+__global__ void __launch_bounds__(kVecNT) k_vl_it_p(IterArgs a) {
+  const VecArgs& v = a.v;
+  if (v.st->done) return;
+  const int JS = v.J * v.S3, n = v.K * JS;
+  int i0, i1;
+  block_range(n, a.G, i0, i1);
+  for (int i = i0 + threadIdx.x; i < i1; i += kVecNT) {
+    const int k = i / JS, j = (i - k * JS) / v.S3;
+    if (!v.active[k]) continue;
+    v.p[i] = fmaf(a.beta[j], v.p[i], v.z[i]);
   }
 }
 
@@ -608,8 +717,11 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   A((void**)&V.yhat, (size_t)KJ * NF * sizeof(float2));
   A((void**)&V.mu, (size_t)K * sizeof(double));
   A((void**)&V.active, (size_t)K * sizeof(int));
+  A((void**)&V.fscal, (size_t)2 * K * sizeof(float));
+  A((void**)&V.part, (size_t)3 * kMaxJ * c->nsm * sizeof(double) + kMaxJ * sizeof(float));
   A((void**)&V.st, sizeof(CgState));
   A((void**)&V.x2, (size_t)N * J * O3 * sizeof(float2));
+  A((void**)&V.tab, ((size_t)Wc * 32 + (size_t)H * kMaxL) * sizeof(float2));
   if (e == cudaSuccess && steps > V.iters_cap) {
     if (V.iters) cudaFree(V.iters);
     V.iters = nullptr;
@@ -657,7 +769,8 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   VL_CHECK(cudaFuncSetAttribute(k_vl_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm), "attribute");
   const float invD = 1.0f / (float)(O3 / Wc * W);   // 1 / (T H W)
   {
-    RowsArgs ra{V.gram, np, T, La, Lb, fh - 1, fw - 1, V.U};
+    RowsArgs ra{V.gram, np, T, La, Lb, fh - 1, fw - 1, V.U, V.tab};
+    k_vl_tables<<<(Wc * Lb + H * La + 255) / 256, 256, 0, st>>>(ra, V.tab);
     k_vl_rows<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
     VL_CHECK(cudaGetLastError(), "lag window rows");
     TimeArgs ta{V.U, np, T, Lt, La * Lb, ft - 1, K, J, invD, 1, V.lags};
@@ -666,7 +779,8 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     VL_CHECK(cudaGetLastError(), "lag window time");
   }
   {
-    RowsArgs ra{V.rspecT, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, V.U};
+    RowsArgs ra{V.rspecT, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, V.U, V.tab};
+    k_vl_tables<<<(Wc * fw + H * fh + 255) / 256, 256, 0, st>>>(ra, V.tab);
     k_vl_rows<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
     VL_CHECK(cudaGetLastError(), "right-hand side rows");
     TimeArgs ta{V.U, KJ, T, ft, fh * fw, (ft - 1) / 2, K, J, invD, 0, b};
@@ -677,7 +791,7 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   // 4. lag spectra
   {
     SpecArgs sa{V.lags, K, Lt, La, Lb, fw, ft, fh, V.chat};
-    const size_t ssm = ((size_t)(Lt * La * Lb + 1) / 2 + 2 * (size_t)Lt * La * fw) * sizeof(float2);
+    const size_t ssm = ((size_t)(Lt * La * Lb + 1) / 2 + 2 * (size_t)Lt * La * fw + Lt + La + Lb) * sizeof(float2);
     VL_CHECK(cudaFuncSetAttribute(k_vl_lagspec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm), "attribute");
     k_vl_lagspec<<<np, 256, ssm, st>>>(sa);
     VL_CHECK(cudaGetLastError(), "lag spectra");
@@ -689,8 +803,8 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   VL_CHECK(cudaGetLastError(), "activity");
   float* xdev = d;   // staged by the caller: device filters [K][J][ft][fh][fw]
   OpArgs oa{K, J, ft, fh, fw, Lt, La, Lb, S3, NF, nullptr, V.phat, V.yhat, y, V.chat, nullptr};
-  const size_t t2b_sm = ((size_t)(S3 + 1) / 2 + (size_t)ft * fh * fw + (size_t)ft * La * fw) * sizeof(float2);
-  const size_t b2t_sm = ((size_t)NF + (size_t)ft * La * fw + (size_t)ft * fh * fw) * sizeof(float2);
+  const size_t t2b_sm = ((size_t)(S3 + 1) / 2 + (size_t)ft * fh * fw + (size_t)ft * La * fw + Lt + La + Lb) * sizeof(float2);
+  const size_t b2t_sm = ((size_t)NF + (size_t)ft * La * fw + (size_t)ft * fh * fw + Lt + La + Lb) * sizeof(float2);
   VL_CHECK(cudaFuncSetAttribute(k_vl_t2b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2b_sm), "attribute");
   VL_CHECK(cudaFuncSetAttribute(k_vl_b2t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2t_sm), "attribute");
   auto apply = [&](const float* pv, const int* done) -> cudaError_t {
@@ -703,11 +817,18 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     return cudaGetLastError();
   };
   VecArgs va{K, J, S3, c->p.cg_max, c->p.cg_tol * c->p.cg_tol, kMuFloor, b, xdev, r, zz, pvec, y, V.mu, V.lags,
-             ((ft - 1) * La + (fh - 1)) * Lb + (fw - 1), Lt * La * Lb, V.active, reinterpret_cast<CgState*>(V.st),
-             V.iters, 0};
+             ((ft - 1) * La + (fh - 1)) * Lb + (fw - 1), Lt * La * Lb, V.active, V.fscal,
+             reinterpret_cast<CgState*>(V.st), V.iters, 0};
   int* done_dev = &reinterpret_cast<CgState*>(V.st)->done;
+  IterArgs ia;
+  ia.v = va;
+  ia.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nsm, (nvec + kVecNT - 1) / kVecNT));
+  ia.part = V.part;
+  ia.part2 = V.part + (size_t)kMaxJ * c->nsm;
+  ia.beta = reinterpret_cast<float*>(V.part + (size_t)3 * kMaxJ * c->nsm);
   for (int s = 0; s < steps; ++s) {
     va.step = s;
+    ia.v = va;
     VL_CHECK(apply(xdev, nullptr), "operator");
     k_vl_cg_init<<<1, kCgNT, 0, st>>>(va);
     VL_CHECK(cudaGetLastError(), "CG init");
@@ -715,7 +836,10 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
       const int batch = std::min(8, c->p.cg_max - it);
       for (int u = 0; u < batch; ++u) {
         VL_CHECK(apply(pvec, done_dev), "operator");
-        k_vl_cg_iter<<<1, kCgNT, 0, st>>>(va);
+        k_vl_it_pap<<<ia.G, kVecNT, 0, st>>>(ia);
+        k_vl_it_upd<<<ia.G, kVecNT, 0, st>>>(ia);
+        k_vl_it_scal<<<1, 32, 0, st>>>(ia);
+        k_vl_it_p<<<ia.G, kVecNT, 0, st>>>(ia);
       }
       VL_CHECK(cudaGetLastError(), "CG iteration");
       it += batch;
