@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
   }
 }
 
-// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f), C_hat_kk' = conj C_hat_k'k for k > k'
+// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f), C_hat_kk' = conj C_hat_k'k for k > k'; the lanes of a
+// warp share the bin (p_hat loads are broadcasts) and take consecutive filters
 __global__ void k_vl_prod(OpArgs a) {
   if (a.done && *a.done) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -549,11 +550,15 @@ __global__ void __launch_bounds__(kVecNT) k_vl_it_upd(IterArgs a) {
   if (v.st->done) return;
   __shared__ double red[(kVecNT / 32) * 2 * kMaxJ];
   __shared__ float s_alpha[kMaxJ];
-  if (threadIdx.x < kMaxJ) {
-    const int j = threadIdx.x;
-    double pap = 0.0;
-    for (int g = 0; g < a.G; ++g) pap += a.part[g * kMaxJ + j];
-    s_alpha[j] = (j < v.J && !v.st->done_j[j] && pap > 0.0) ? (float)(v.st->rz[j] / pap) : 0.f;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      double t = 0.0;
+      for (int g = threadIdx.x; g < a.G; g += 32) t += a.part[g * kMaxJ + j];
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      if (threadIdx.x == 0)
+        s_alpha[j] = (j < v.J && !v.st->done_j[j] && t > 0.0) ? (float)(v.st->rz[j] / t) : 0.f;
+    }
   }
   __syncthreads();
   const int JS = v.J * v.S3, n = v.K * JS;
@@ -579,16 +584,21 @@ __global__ void __launch_bounds__(kVecNT) k_vl_it_upd(IterArgs a) {
     for (int u = 0; u < 2 * kMaxJ; ++u) a.part2[blockIdx.x * 2 * kMaxJ + u] = s[u];
 }
 
-__global__ void k_vl_it_scal(IterArgs a) {
+__global__ void k_vl_it_scal(IterArgs a) {   // one warp
   const VecArgs& v = a.v;
-  if (threadIdx.x != 0 || v.st->done) return;
+  if (v.st->done) return;
+  double sums[2 * kMaxJ];
+#pragma unroll
+  for (int u = 0; u < 2 * kMaxJ; ++u) {
+    double t = 0.0;
+    for (int g = threadIdx.x; g < a.G; g += 32) t += a.part2[g * 2 * kMaxJ + u];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    sums[u] = t;
+  }
+  if (threadIdx.x != 0) return;
   int all = 1;
   for (int j = 0; j < v.J; ++j) {
-    double rz = 0.0, rr = 0.0;
-    for (int g = 0; g < a.G; ++g) {
-      rz += a.part2[g * 2 * kMaxJ + j];
-      rr += a.part2[g * 2 * kMaxJ + kMaxJ + j];
-    }
+    const double rz = sums[j], rr = sums[kMaxJ + j];
     if (!v.st->done_j[j]) {
       a.beta[j] = v.st->rz[j] > 0.0 ? (float)(rz / v.st->rz[j]) : 0.f;
       v.st->rz[j] = rz;
