@@ -105,7 +105,9 @@ void free_all(Ctx* c) {
   c->graph = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
-  void* uptrs[] = {c->U.d_cls, c->U.d_img, c->U.d_mstart, c->U.d_slot};
+  void* uptrs[] = {c->U.d_cls, c->U.d_img, c->U.d_mstart, c->U.d_slot, c->U.d_bcls, c->U.d_bimg, c->U.d_bcol,
+                   c->U.d_brow, c->U.d_bfreq, c->U.d_btabs, c->U.d_by, c->U.d_blam, c->U.d_be, c->U.d_bl1,
+                   c->U.d_bsetup};
   for (void* p : uptrs)
     if (p) cudaFree(p);
   for (auto& ep : c->events) {
@@ -172,7 +174,7 @@ void class_view(const Ctx& c, int ci, Ctx& v) {
 // cost-balanced CTA map ranges and partial-sum slots for G CTAs
 void uneven_partition(Ctx* c, int G) {
   UnevenLayout& U = c->U;
-  const int N = c->N, K = c->K, J = c->J;
+  const int N = U.n_small, K = c->K, J = c->J;
   std::vector<double> cost(N);
   double total = 0.0;
   for (int n = 0; n < N; ++n) {
@@ -252,7 +254,7 @@ csc_status upload_uneven(Ctx* c) {
 
 UnevenArgs uneven_args(const Ctx& c, const float2* part_in, float2* part_out, float* v, float* z) {
   UnevenArgs a;
-  a.N = c.N; a.K = c.K; a.J = c.J; a.G = c.G;
+  a.N = c.U.n_small; a.K = c.K; a.J = c.J; a.G = c.G;
   a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
   a.buf_elems = c.U.buf_elems; a.max_omega = c.U.max_omega;
   a.cls = c.U.d_cls; a.img = c.U.d_img; a.mstart = c.U.d_mstart; a.slot = c.U.d_slot;
@@ -260,6 +262,42 @@ UnevenArgs uneven_args(const Ctx& c, const float2* part_in, float2* part_out, fl
   a.dhat16 = c.p.precision == CSC_MIXED_BF16 ? c.dhat16 : nullptr;
   a.part_in = part_in; a.part_out = part_out; a.v = v; a.z = z; a.l1 = c.l1;
   return a;
+}
+
+BigArgs big_args(const Ctx& c, float* v, float* z) {
+  const UnevenLayout& U = c.U;
+  BigArgs a{};
+  a.K = c.K; a.J = c.J;
+  a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
+  a.cls = U.d_bcls; a.img = U.d_bimg;
+  a.col_items = U.d_bcol; a.row_items = U.d_brow; a.freq_items = U.d_bfreq;
+  a.n_col_items = (int)U.bcol.size(); a.n_row_items = (int)U.brow.size(); a.n_freq_items = (int)U.bfreq.size();
+  a.col_smem = U.bcol_smem; a.row_smem = U.brow_smem;
+  a.tabs = U.d_btabs; a.dhat = c.dhat; a.pdiag = c.pdiag; a.pmat = c.pmat; a.xhat = c.xhat;
+  a.Y = U.d_by; a.lam = U.d_blam; a.v = v; a.z = z; a.e_items = U.d_be; a.l1_items = U.d_bl1;
+  return a;
+}
+
+// kernel launches of one launch_big_sweep call
+int big_launches(int mode) { return mode == kPrologue ? 3 : mode == kLast ? 2 : mode == kIter ? 4 : 3; }
+
+csc_status upload_big(Ctx* c, const std::vector<BigSetupItem>& setup) {
+  UnevenLayout& U = c->U;
+  auto put = [&](auto** dptr, const auto& vec) {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    if (cudaMalloc((void**)dptr, std::max<size_t>(vec.size(), 1) * sizeof(T)) != cudaSuccess) return false;
+    return cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!put(&U.d_bcls, U.bcls) || !put(&U.d_bimg, U.bimg) || !put(&U.d_bcol, U.bcol) || !put(&U.d_brow, U.brow) ||
+      !put(&U.d_bfreq, U.bfreq) || !put(&U.d_btabs, U.btabs) || !put(&U.d_bsetup, setup) ||
+      cudaMalloc((void**)&U.d_by, std::max<long long>(U.n_by, 1) * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&U.d_blam, std::max<long long>(U.n_blam, 1) * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&U.d_be, std::max<size_t>(U.bfreq.size(), 1) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&U.d_bl1, std::max<size_t>(U.brow.size(), 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "uneven batch: allocation of the large-image workspace failed");
+  }
+  return CSC_OK;
 }
 
 // spectra of the filters (per class) and of the images (per image) of an uneven batch
@@ -272,13 +310,30 @@ cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
     if (e != cudaSuccess) return e;
     c->launches += solve ? 2 : 1;
   }
-  for (int n = 0; n < c->N; ++n) {
+  for (int n = 0; n < c->U.n_small; ++n) {
     const UImage& im = c->U.img[n];
     Ctx v;
     class_view(*c, im.cls, v);
     cudaError_t e = launch_fft_maps(v, x + im.x, c->J, 0, c->xhat + im.xh);
     if (e != cudaSuccess) return e;
     c->launches += 1;
+  }
+  if (!c->U.bimg.empty()) {
+    const UnevenLayout& U = c->U;
+    cudaError_t e = launch_big_setup(big_args(*c, nullptr, nullptr), U.d_bsetup, U.n_bsetup_rows,
+                                     U.d_bsetup + U.n_bsetup_rows, U.n_bsetup_cols, d, x, c->dhat, c->xhat, c->fh,
+                                     c->fw, c->stream);
+    c->launches += 2;
+    for (int ci = 0; ci < (int)U.bcls.size() && solve && e == cudaSuccess; ++ci) {
+      const BigCls& bc = U.bcls[ci];
+      Ctx v;
+      v.p = c->p; v.K = c->K; v.J = c->J; v.stream = c->stream;
+      v.g.Omega = bc.H * bc.Wc; v.g.D = bc.H * bc.W;
+      v.dhat = c->dhat + bc.dhat; v.pdiag = c->pdiag + bc.pd; v.pmat = c->pmat + bc.pm;
+      e = launch_solve_prep(v);
+      c->launches += 1;
+    }
+    if (e != cudaSuccess) return e;
   }
   if (c->dhat16) {
     cudaError_t e = launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->U.n_dhat);
@@ -290,24 +345,41 @@ cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
 
 // the sweeps of one coding call on an uneven batch
 cudaError_t uneven_sweeps(Ctx* c, float* v, float* z, int iters) {
-  const size_t smem_max = uneven_smem_bytes(c->U, c->J, kPrologue);
-  cudaError_t e = launch_sweep_uneven(uneven_args(*c, nullptr, c->part[0], v, nullptr), kPrologue, c->G, c->U.nt,
-                                      uneven_smem_bytes(c->U, c->J, kPrologue), c->stream);
-  (void)smem_max;
-  c->launches += 1;
+  const bool small = c->U.n_small > 0, big = !c->U.bimg.empty();
+  const BigArgs ba = big_args(*c, v, z);
+  cudaError_t e = cudaSuccess;
+  if (small) {
+    e = launch_sweep_uneven(uneven_args(*c, nullptr, c->part[0], v, nullptr), kPrologue, c->G, c->U.nt,
+                            uneven_smem_bytes(c->U, c->J, kPrologue), c->stream);
+    c->launches += 1;
+  }
+  if (big && e == cudaSuccess) {
+    e = launch_big_sweep(ba, kPrologue, c->stream);
+    c->launches += big_launches(kPrologue);
+  }
   for (int t = 0; t < iters && e == cudaSuccess; ++t) {
     const int mode = (t == iters - 1) ? kLast : kIter;
     const int br = (mode == kIter) ? bracket_open(c, 0) : -1;
-    e = launch_sweep_uneven(uneven_args(*c, c->part[t & 1], c->part[(t + 1) & 1], v, z), mode, c->G, c->U.nt,
-                            uneven_smem_bytes(c->U, c->J, mode), c->stream);
+    if (small) {
+      e = launch_sweep_uneven(uneven_args(*c, c->part[t & 1], c->part[(t + 1) & 1], v, z), mode, c->G, c->U.nt,
+                              uneven_smem_bytes(c->U, c->J, mode), c->stream);
+      c->launches += 1;
+    }
+    if (big && e == cudaSuccess) {
+      e = launch_big_sweep(ba, mode, c->stream);
+      c->launches += big_launches(mode);
+    }
     bracket_close(c, br);
-    c->launches += 1;
   }
   return e;
 }
 
 // pick threads per CTA and CTAs per SM for this batch by timing two sweeps of each candidate
 csc_status uneven_autotune(Ctx* c, float* v) {
+  if (c->U.n_small == 0) {
+    c->U.tuned = true;
+    return CSC_OK;
+  }
   struct Cand { int nt, per_sm; };
   const Cand cands[] = {{512, 1}, {256, 1}, {256, 2}, {512, 2}};
   const size_t smem = uneven_smem_bytes(c->U, c->J, kIter);
@@ -322,7 +394,7 @@ csc_status uneven_autotune(Ctx* c, float* v) {
   cudaEventCreate(&e1);
   for (const Cand& cd : cands) {
     if (cd.per_sm * (smem + 1024) > (size_t)228 * 1024) continue;
-    const int G = (int)std::min<long long>((long long)c->nsm * cd.per_sm, (long long)c->N * c->K);
+    const int G = (int)std::min<long long>((long long)c->nsm * cd.per_sm, (long long)c->U.n_small * c->K);
     uneven_partition(c, G);
     csc_status st = upload_uneven(c);
     if (st != CSC_OK) { cudaFree(vs); return st; }
@@ -344,7 +416,7 @@ csc_status uneven_autotune(Ctx* c, float* v) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(vs);
-  const int G = (int)std::min<long long>((long long)c->nsm * pick.per_sm, (long long)c->N * c->K);
+  const int G = (int)std::min<long long>((long long)c->nsm * pick.per_sm, (long long)c->U.n_small * c->K);
   uneven_partition(c, G);
   csc_status st = upload_uneven(c);
   if (st != CSC_OK) return st;
@@ -505,13 +577,46 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   const double pi2 = 6.283185307179586476925286766559;
   for (int n = 0; n < n_images; ++n) {
     const int H = dims[2 * n], W = dims[2 * n + 1];
-    int ci = -1;
+    int ci = -1, bi = -1;
     for (int q = 0; q < (int)U.cls.size(); ++q)
       if (U.cls_H[q] == H && U.cls_W[q] == W) { ci = q; break; }
+    for (int q = 0; ci < 0 && q < (int)U.bcls.size(); ++q)
+      if (U.bcls_H[q] == H && U.bcls_W[q] == W) { bi = q; break; }
+    Geometry g;
+    if (ci < 0 && bi < 0 && check_size(p, H, W, g, "csc_init_uneven") != CSC_OK) {
+      // not one map per CTA: the multi-pass engine (any side up to kBigMaxSide, any factorisation)
+      if (H < 8 || W < 8 || fh > H || fw > W || !big_add_class(U, H, W)) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg), "csc_init_uneven: image %dx%d: need 8 <= H, W <= %d and the filter inside",
+                      H, W, kBigMaxSide);
+        delete ctx;
+        return fail(nullptr, CSC_ERR_SHAPE, msg);
+      }
+      g_init_error.clear();
+      bi = (int)U.bcls.size() - 1;
+      BigCls& bc = U.bcls[bi];
+      const long long Om = (long long)H * bc.Wc;
+      bc.dhat = U.n_dhat; bc.pd = U.n_pd; bc.pm = U.n_pm;
+      U.n_dhat += (long long)p.K * p.J * Om;
+      U.n_pd += Om;
+      U.n_pm += Om * p.J * p.J;
+    }
+    if (bi >= 0) {
+      const BigCls& bc = U.bcls[bi];
+      const long long Om = (long long)H * bc.Wc;
+      BigImg im;
+      im.cls = bi;
+      im.x = U.n_x; im.v = U.n_v; im.xh = U.n_xh;
+      im.y = U.n_by; im.lam = U.n_blam;
+      U.n_x += (long long)p.J * H * W;
+      U.n_v += (long long)p.K * H * W;
+      U.n_xh += (long long)p.J * Om;
+      U.n_by += (long long)p.K * Om;
+      U.n_blam += (long long)p.J * Om;
+      U.bimg.push_back(im);
+      continue;
+    }
     if (ci < 0) {
-      Geometry g;
-      csc_status st = check_size(p, H, W, g, "csc_init_uneven");
-      if (st != CSC_OK) { delete ctx; return st; }
       UClass uc;
       uc.g = g.rt;
       uc.tw = U.n_tw; uc.dhat = U.n_dhat; uc.pd = U.n_pd; uc.pm = U.n_pm;
@@ -539,19 +644,22 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
     U.n_xh += (long long)p.J * geos[ci].Omega;
     U.img.push_back(im);
   }
+  U.n_small = (int)U.img.size();
+  std::vector<BigSetupItem> bsetup;
+  if (!U.bimg.empty()) big_build_items(U, p.K, p.J, fh, fw, bsetup);
   if (uneven_smem_bytes(U, p.J, kIter) > kSmemLimit) {
     delete ctx;
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: the largest image and the largest spectrum do not fit one CTA");
   }
-  c->g = geos[0];
+  if (!geos.empty()) c->g = geos[0];
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
     c->last_error = "csc_init_uneven: no CUDA device";
     return bail(CSC_ERR_CUDA);
   }
-  uneven_partition(c, (int)std::min<long long>(c->nsm, (long long)n_images * p.K));
-  if (cudaMalloc((void**)&c->tw, tw.size() * sizeof(float2)) != cudaSuccess ||
+  uneven_partition(c, (int)std::min<long long>(c->nsm, (long long)U.n_small * p.K));
+  if (cudaMalloc((void**)&c->tw, std::max<size_t>(tw.size(), 1) * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->dhat, U.n_dhat * sizeof(float2)) != cudaSuccess ||
       (p.precision == CSC_MIXED_BF16 &&
        cudaMalloc((void**)&c->dhat16, U.n_dhat * sizeof(__nv_bfloat162)) != cudaSuccess) ||
@@ -571,6 +679,7 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
     return bail(CSC_ERR_CUDA);
   }
   if (upload_uneven(c) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
+  if (!U.bimg.empty() && upload_big(c, bsetup) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
   *out = ctx;
   return CSC_OK;
 }
@@ -710,11 +819,14 @@ csc_status csc_describe(const csc_ctx* ctx, char* buf, int len) {
   if (!ctx || !buf || len < 1) return fail(nullptr, CSC_ERR_ARG, "csc_describe: null argument");
   const Ctx& c = ctx->c;
   const int n_cls = c.uneven ? (int)c.U.cls.size() : 1;
+  const int n_big = c.uneven ? (int)c.U.bcls.size() : 0;
   std::snprintf(buf, (size_t)len,
-                "{\"N\": %d, \"K\": %d, \"J\": %d, \"uneven\": %s, \"size_classes\": %d, \"ctas\": %d, "
+                "{\"N\": %d, \"K\": %d, \"J\": %d, \"uneven\": %s, \"size_classes\": %d, "
+                "\"large_size_classes\": %d, \"large_images\": %d, \"ctas\": %d, "
                 "\"threads_per_cta\": %d, \"autotuned\": %s, \"graph\": %s, \"graph_recorded\": %s, "
                 "\"video\": %s, \"T\": %d, \"ft\": %d}",
-                c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, c.G, c.uneven ? c.U.nt : (int)kNTSweep,
+                c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, n_big, c.uneven ? (int)c.U.bimg.size() : 0, c.G,
+                c.uneven ? c.U.nt : (int)kNTSweep,
                 (c.uneven && c.U.tuned) ? "true" : "false", (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
                 c.graph ? "true" : "false", c.video ? "true" : "false", c.T, c.ft);
   return CSC_OK;
@@ -855,15 +967,29 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
+  std::vector<double> big_e, big_l1;
   if (c->uneven) {
     CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, false), "uneven setup");
-    UnevenArgs ua = uneven_args(*c, nullptr, c->part[0], nullptr, const_cast<float*>(zd));
-    ua.dhat16 = nullptr;   // the objective stays float32 in every mode
-    CSC_CHECK_CUDA(c, launch_sweep_uneven(ua, kObjective, c->G, c->U.nt, uneven_smem_bytes(c->U, c->J, kObjective),
-                                          c->stream), "objective sweep");
-    CSC_CHECK_CUDA(c, launch_objective_final_uneven(uneven_args(*c, c->part[0], nullptr, nullptr, nullptr), c->objimg,
-                                                    c->stream), "objective reduction");
-    c->launches += 2;
+    if (c->U.n_small > 0) {
+      UnevenArgs ua = uneven_args(*c, nullptr, c->part[0], nullptr, const_cast<float*>(zd));
+      ua.dhat16 = nullptr;   // the objective stays float32 in every mode
+      CSC_CHECK_CUDA(c, launch_sweep_uneven(ua, kObjective, c->G, c->U.nt,
+                                            uneven_smem_bytes(c->U, c->J, kObjective), c->stream), "objective sweep");
+      CSC_CHECK_CUDA(c, launch_objective_final_uneven(uneven_args(*c, c->part[0], nullptr, nullptr, nullptr),
+                                                      c->objimg, c->stream), "objective reduction");
+      c->launches += 2;
+    }
+    if (!c->U.bimg.empty()) {
+      CSC_CHECK_CUDA(c, launch_big_sweep(big_args(*c, nullptr, const_cast<float*>(zd)), kObjective, c->stream),
+                     "objective sweep (large images)");
+      c->launches += big_launches(kObjective);
+      big_e.resize(c->U.bfreq.size());
+      big_l1.resize(c->U.brow.size());
+      CSC_CHECK_CUDA(c, cudaMemcpyAsync(big_e.data(), c->U.d_be, big_e.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                        c->stream), "objective copy");
+      CSC_CHECK_CUDA(c, cudaMemcpyAsync(big_l1.data(), c->U.d_bl1, big_l1.size() * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream), "objective copy");
+    }
   } else {
     CSC_CHECK_CUDA(c, launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat), "filter spectra");
     CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat), "image spectra");
@@ -872,15 +998,20 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
     CSC_CHECK_CUDA(c, launch_objective_final(*c, c->part[0], c->objimg), "objective reduction");
     c->launches += 4;
   }
-  std::vector<double> img(c->N), l1(c->G);
-  CSC_CHECK_CUDA(c, cudaMemcpyAsync(img.data(), c->objimg, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                 "objective copy");
-  CSC_CHECK_CUDA(c, cudaMemcpyAsync(l1.data(), c->l1, c->G * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                 "objective copy");
+  const int n_img = c->uneven ? c->U.n_small : c->N;
+  std::vector<double> img(n_img), l1(c->G);
+  if (n_img > 0) {
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(img.data(), c->objimg, n_img * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream), "objective copy");
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(l1.data(), c->l1, c->G * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                   "objective copy");
+  }
   CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
   double data = 0.0, reg = 0.0;
   for (double v : img) data += v;
   for (double v : l1) reg += v;
+  for (double v : big_e) data += v;
+  for (double v : big_l1) reg += v;
   const double f = 0.5 * data + c->p.beta * reg;
   if (!std::isfinite(f)) return fail(c, CSC_ERR_NONFINITE, "csc_objective: non-finite objective");
   *out = f;

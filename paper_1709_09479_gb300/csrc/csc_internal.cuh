@@ -95,12 +95,94 @@ struct UnevenArgs {
   float* z;
   double* l1;
 };
+// ---- uneven-batch images beyond the one-map-per-CTA sweep (uneven_big.cu) -------------------------
+struct BigPlan {          // a length-n complex DFT
+  int n;
+  int M;                  // 0: Stockham plan of n (7-smooth); else Bluestein length M >= 2n - 1 (7-smooth)
+  Radices rad;            // radices of n, or of M
+  long long tw;           // twiddles exp(-2 pi i t / L), L = n or M: element offset into the tables
+  long long chirp, bhat;  // Bluestein: w_j = exp(-pi i j^2 / n) (n), FFT_M of the conjugate chirp / M (M)
+};
+struct BigCls {
+  int H, W, Wc;           // Wc = W/2 + 1 stored columns (both parities)
+  int col_ls, row_ls;     // line pitch of the column / row passes in shared memory (>= n and >= M)
+  BigPlan pcol, prow;     // lengths H and W
+  long long dhat, pd, pm; // offsets of the class's d_hat, P diagonal, P blocks (the uneven buffers)
+};
+struct BigImg {
+  int cls;
+  long long x, v, xh;     // offsets in the uneven batch's arrays (user order)
+  long long y, lam;       // offsets of its K map spectra and its J lambda_hat in the big workspaces
+};
+struct BigItem {          // an image's map (or, for frequency items, the image) and a range
+  int img, map, first, count;
+};
+struct BigSetupItem {      // rows or columns [first, first + count) of one map of the setup transforms
+  int cls, first, count, filter;
+  long long src;          // filter: element offset of its [fh][fw] taps in d; image: of its [H][W] plane in x
+  long long dst;          // element offset of its half spectrum [H][Wc] in d_hat (filter) or x_hat (image)
+};
+struct BigArgs {
+  int K, J;
+  float beta, rho;
+  const BigCls* cls;
+  const BigImg* img;
+  const BigItem* col_items;
+  const BigItem* row_items;
+  const BigItem* freq_items;
+  int n_col_items, n_row_items, n_freq_items;
+  size_t col_smem, row_smem;
+  const float2* tabs;
+  const float2* dhat;
+  const float* pdiag;
+  const float2* pmat;
+  const float2* xhat;
+  float2* Y;
+  float2* lam;
+  float* v;
+  float* z;
+  double* e_items;        // [n_freq_items] residual energy (objective)
+  double* l1_items;       // [n_row_items] sum |z| (objective)
+};
+constexpr int kBigMaxSide = 1024;
+cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_big_setup(const BigArgs& a, const BigSetupItem* row_items, int n_rows,
+                             const BigSetupItem* col_items, int n_cols, const float* d, const float* x,
+                             float2* dhat, float2* xhat, int fh, int fw, cudaStream_t st);
+struct UnevenLayout;
+// plans (and their tables, appended to L.btabs) of a new H x W class; false if a side is out of range
+bool big_add_class(UnevenLayout& L, int H, int W);
+// the work-item lists of the sweeps and of the setup, from L.bcls / L.bimg
+void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<BigSetupItem>& setup);
+
 struct UnevenLayout {
   std::vector<UClass> cls;
   std::vector<UImage> img;
   std::vector<int> cls_H, cls_W;
   std::vector<long long> mstart, slot;
   int buf_elems = 0, max_omega = 0, max_tw = 0;
+  int n_small = 0;          // images coded by the one-map-per-CTA sweep (U.img); the rest are in bimg
+  // images the one-map-per-CTA sweep cannot hold, coded by uneven_big.cu
+  std::vector<BigCls> bcls;
+  std::vector<BigImg> bimg;
+  std::vector<int> bcls_H, bcls_W;
+  std::vector<float2> btabs;
+  std::vector<BigPlan> bplans;   // one per transform length, shared by the classes
+  std::vector<BigItem> bcol, brow, bfreq;
+  size_t bcol_smem = 0, brow_smem = 0;
+  long long n_by = 0, n_blam = 0;
+  BigCls* d_bcls = nullptr;
+  BigImg* d_bimg = nullptr;
+  BigItem* d_bcol = nullptr;
+  BigItem* d_brow = nullptr;
+  BigItem* d_bfreq = nullptr;
+  float2* d_btabs = nullptr;
+  float2* d_by = nullptr;
+  float2* d_blam = nullptr;
+  double* d_be = nullptr;
+  double* d_bl1 = nullptr;
+  BigSetupItem* d_bsetup = nullptr;
+  int n_bsetup_rows = 0, n_bsetup_cols = 0;
   long long n_tw = 0, n_dhat = 0, n_pd = 0, n_pm = 0, n_x = 0, n_v = 0, n_xh = 0, n_slot = 0;
   UClass* d_cls = nullptr;
   UImage* d_img = nullptr;

@@ -1,0 +1,525 @@
+// Coding of the images of an uneven batch whose maps do not fit the one-map-per-CTA sweep: any side
+// up to 512, odd widths, and lengths with prime factors above 7 (the dual ADMM of
+// Eq. Inference_solution, the same arithmetic as uneven.cu).
+//
+// The map spectra live in HBM ([map][H][W/2+1], the half-spectrum layout of d_hat and x_hat) and each
+// 2-D transform is two batched passes of 1-D transforms through shared memory:
+//   columns (length H, complex) on the W/2+1 stored columns, and
+//   rows (length W, complex on the real row, then the first W/2+1 bins kept; the inverse first
+//   completes the row by Hermitian symmetry, X[W-k] = conj X[k]).
+// A 1-D transform of a 7-smooth length is the run-time Stockham plan of fft.cuh; any other length n
+// goes through Bluestein's chirp z-transform: with w_j = e^{-pi i j^2/n},
+//     X_k = w_k sum_j (x_j w_j) conj(w_{k-j}),
+// a circular convolution of length M >= 2n - 1 (M 7-smooth) done with two length-M transforms; the
+// inverse transform is conj(DFT(conj x)).
+// One ADMM iteration over all such images is four launches: the inverse column pass (building
+// w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j as it loads), the row pass (inverse row transform, the
+// state update v <- w - (clamp(v) - v), u = 2 clamp(v) - v, forward row transform), the forward
+// column pass, and the per-frequency pass that forms r_hat = sum_k d_hat_k u_hat_k - x_hat / rho and
+// lambda_hat = P r_hat (P includes 1/D, so the transforms stay unnormalised). Work items are listed
+// on the host; every sum is formed in a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "csc_internal.cuh"
+
+namespace csc {
+namespace big {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ float bclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
+
+// nlines lines of length pl.n at buf + line * ls; the Bluestein path needs ls >= pl.M. Ends synchronised.
+template <bool INV>
+__device__ void fft1(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs) {
+  if (pl.M == 0) {
+    stages_rt<INV, NT>(buf, nlines, ls, 1, pl.n, pl.rad, tabs + pl.tw);
+    return;
+  }
+  const int n = pl.n, M = pl.M;
+  const float2* w = tabs + pl.chirp;
+  const float2* bh = tabs + pl.bhat;
+  for (int i = threadIdx.x; i < nlines * M; i += NT) {
+    const int line = i / M, j = i - line * M;
+    float2* p = buf + (size_t)line * ls + j;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < n) {
+      v = *p;
+      if (INV) v.y = -v.y;
+      v = cmul(v, w[j]);
+    }
+    *p = v;
+  }
+  __syncthreads();
+  stages_rt<false, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
+  for (int i = threadIdx.x; i < nlines * M; i += NT) {
+    const int line = i / M, j = i - line * M;
+    float2* p = buf + (size_t)line * ls + j;
+    *p = cmul(*p, bh[j]);
+  }
+  __syncthreads();
+  stages_rt<true, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
+  for (int i = threadIdx.x; i < nlines * n; i += NT) {
+    const int line = i / n, j = i - line * n;
+    float2* p = buf + (size_t)line * ls + j;
+    float2 v = cmul(*p, w[j]);
+    if (INV) v.y = -v.y;
+    *p = v;
+  }
+  __syncthreads();
+}
+
+// ---- column pass: item = (image, map, first column, columns) ------------------------------------
+// BUILD: the inverse transform of w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j; else the forward
+// transform of the stored row spectra
+template <bool BUILD>
+__global__ void __launch_bounds__(NT) k_big_cols(BigArgs a) {
+  extern __shared__ float2 sm[];
+  __shared__ BigPlan pl;
+  const BigItem it = a.col_items[blockIdx.x];
+  const BigImg im = a.img[it.img];
+  const BigCls& bc = a.cls[im.cls];
+  if (threadIdx.x == 0) pl = bc.pcol;
+  __syncthreads();
+  const int H = bc.H, Wc = bc.Wc, Om = H * Wc, nc = it.count, kw0 = it.first;
+  const int ls = bc.col_ls;
+  float2* Y = a.Y + im.y + (size_t)it.map * Om;
+  if (BUILD) {
+    const float2* lam = a.lam + im.lam;
+    const float2* dk = a.dhat + bc.dhat + (size_t)it.map * a.J * Om;
+    for (int i = threadIdx.x; i < nc * H; i += NT) {
+      const int c = i % nc, h = i / nc;
+      const int o = h * Wc + kw0 + c;
+      float2 s = make_float2(0.f, 0.f);
+      for (int j = 0; j < a.J; ++j) s = cfmac(dk[(size_t)j * Om + o], lam[(size_t)j * Om + o], s);
+      sm[(size_t)c * ls + h] = s;
+    }
+  } else {
+    for (int i = threadIdx.x; i < nc * H; i += NT) {
+      const int c = i % nc, h = i / nc;
+      sm[(size_t)c * ls + h] = Y[(size_t)h * Wc + kw0 + c];
+    }
+  }
+  __syncthreads();
+  fft1<BUILD>(sm, nc, ls, pl, a.tabs);
+  for (int i = threadIdx.x; i < nc * H; i += NT) {
+    const int c = i % nc, h = i / nc;
+    Y[(size_t)h * Wc + kw0 + c] = sm[(size_t)c * ls + h];
+  }
+}
+
+// ---- row pass: item = (image, map, first row, rows) ----------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_big_rows(BigArgs a) {
+  extern __shared__ float2 sm[];
+  __shared__ BigPlan pl;
+  __shared__ double red[NT / 32];
+  const BigItem it = a.row_items[blockIdx.x];
+  const BigImg im = a.img[it.img];
+  const BigCls& bc = a.cls[im.cls];
+  if (threadIdx.x == 0) pl = bc.prow;
+  __syncthreads();
+  const int H = bc.H, W = bc.W, Wc = bc.Wc, Om = H * Wc, nr = it.count, h0 = it.first;
+  const int ls = bc.row_ls;
+  const size_t moff = im.v + (size_t)it.map * H * W;
+  float2* Y = a.Y + im.y + (size_t)it.map * Om;
+  const float beta = a.beta;
+  double l1 = 0.0;
+  if (MODE == kIter || MODE == kLast) {
+    // the row spectra of w, completed by Hermitian symmetry, to the rows of w
+    for (int i = threadIdx.x; i < nr * W; i += NT) {
+      const int r = i / W, kw = i - r * W;
+      const float2* src = Y + (size_t)(h0 + r) * Wc;
+      float2 v = kw < Wc ? src[kw] : src[W - kw];
+      if (kw >= Wc) v.y = -v.y;
+      sm[(size_t)r * ls + kw] = v;
+    }
+    __syncthreads();
+    fft1<true>(sm, nr, ls, pl, a.tabs);
+    for (int i = threadIdx.x; i < nr * W; i += NT) {
+      const int r = i / W, x = i - r * W;
+      const size_t p = moff + (size_t)(h0 + r) * W + x;
+      const float vo = a.v[p];
+      const float vn = sm[(size_t)r * ls + x].x - (bclamp(vo, beta) - vo);
+      a.v[p] = vn;
+      const float cn = bclamp(vn, beta);
+      if (MODE == kLast) {
+        if (a.z) a.z[p] = a.rho * (cn - vn);
+      } else {
+        sm[(size_t)r * ls + x] = make_float2(2.f * cn - vn, 0.f);
+      }
+    }
+  } else {
+    const float* src = (MODE == kPrologue) ? a.v : a.z;
+    for (int i = threadIdx.x; i < nr * W; i += NT) {
+      const int r = i / W, x = i - r * W;
+      const float t = src[moff + (size_t)(h0 + r) * W + x];
+      if (MODE == kPrologue) {
+        sm[(size_t)r * ls + x] = make_float2(2.f * bclamp(t, beta) - t, 0.f);
+      } else {
+        l1 += fabs((double)t);
+        sm[(size_t)r * ls + x] = make_float2(t, 0.f);
+      }
+    }
+  }
+  if (MODE != kLast) {
+    __syncthreads();
+    fft1<false>(sm, nr, ls, pl, a.tabs);
+    for (int i = threadIdx.x; i < nr * Wc; i += NT) {
+      const int r = i / Wc, kw = i - r * Wc;
+      Y[(size_t)(h0 + r) * Wc + kw] = sm[(size_t)r * ls + kw];
+    }
+  }
+  if (MODE == kObjective) {
+    for (int off = 16; off > 0; off >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      a.l1_items[blockIdx.x] = s;
+    }
+  }
+}
+
+// ---- per frequency: r_hat = sum_k d_hat_k u_hat_k - x_hat / rho; lambda_hat = P r_hat, or (objective)
+// the residual energy (1/D) sum_w wt(w) |sum_k d_hat_k z_hat_k - x_hat|^2 -------------------------
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_big_freq(BigArgs a) {
+  __shared__ double red[NT / 32];
+  const BigItem it = a.freq_items[blockIdx.x];
+  const BigImg im = a.img[it.img];
+  const BigCls& bc = a.cls[im.cls];
+  const int H = bc.H, W = bc.W, Wc = bc.Wc, Om = H * Wc, J = a.J, K = a.K;
+  const float irho = 1.0f / a.rho;
+  double e = 0.0;
+  const int o = it.first + threadIdx.x;
+  if (threadIdx.x < it.count) {
+    float2 r[kMaxJ];
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      if (j < J) {
+        const float2 x = a.xhat[im.xh + (size_t)j * Om + o];
+        r[j] = MODE == kObjective ? make_float2(-x.x, -x.y) : make_float2(-x.x * irho, -x.y * irho);
+      }
+    }
+    const float2* Yb = a.Y + im.y;
+    const float2* db = a.dhat + bc.dhat;
+    for (int k = 0; k < K; ++k) {
+      const float2 u = Yb[(size_t)k * Om + o];
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j)
+        if (j < J) r[j] = cfma(db[((size_t)k * J + j) * Om + o], u, r[j]);
+    }
+    if (MODE == kObjective) {
+      const int kw = o % Wc;
+      const double wt = (kw == 0 || 2 * kw == W) ? 1.0 : 2.0;
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j)
+        if (j < J) e += wt * ((double)r[j].x * r[j].x + (double)r[j].y * r[j].y);
+    } else if (J == 1) {
+      a.lam[im.lam + o] = cscale(r[0], a.pdiag[bc.pd + o]);
+    } else {
+      const float2* pm = a.pmat + bc.pm + (size_t)o * J * J;
+#pragma unroll
+      for (int i = 0; i < kMaxJ; ++i) {
+        if (i < J) {
+          float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < kMaxJ; ++j)
+            if (j < J) s = cfma(pm[i * J + j], r[j], s);
+          a.lam[im.lam + (size_t)i * Om + o] = s;
+        }
+      }
+    }
+  }
+  if (MODE == kObjective) {
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      a.e_items[blockIdx.x] = s / (double)(H * W);
+    }
+  }
+}
+
+// ---- spectra for the setup: the forward row transform of real maps (images, or filters placed with
+// their taps centred: tap (ta, tb) at ((ta - (fh-1)/2) mod H, (tb - (fw-1)/2) mod W)) -----------------
+__global__ void __launch_bounds__(NT) k_big_setup_rows(BigArgs a, const BigSetupItem* items, const float* d,
+                                                       const float* x, float2* dhat, float2* xhat, int fh, int fw) {
+  extern __shared__ float2 sm[];
+  __shared__ BigPlan pl;
+  const BigSetupItem it = items[blockIdx.x];
+  const BigCls& bc = a.cls[it.cls];
+  if (threadIdx.x == 0) pl = bc.prow;
+  __syncthreads();
+  const int H = bc.H, W = bc.W, Wc = bc.Wc, nr = it.count, h0 = it.first;
+  const int ls = bc.row_ls;
+  const float* src = (it.filter ? d : x) + it.src;
+  float2* dst = (it.filter ? dhat : xhat) + it.dst;
+  const int ch = (fh - 1) / 2, cw = (fw - 1) / 2;
+  for (int i = threadIdx.x; i < nr * W; i += NT) {
+    const int r = i / W, col = i - r * W, h = h0 + r;
+    float v = 0.f;
+    if (it.filter) {
+      const int ta = (h + ch) % H, tb = (col + cw) % W;
+      if (ta < fh && tb < fw) v = src[ta * fw + tb];
+    } else {
+      v = src[(size_t)h * W + col];
+    }
+    sm[(size_t)r * ls + col] = make_float2(v, 0.f);
+  }
+  __syncthreads();
+  fft1<false>(sm, nr, ls, pl, a.tabs);
+  for (int i = threadIdx.x; i < nr * Wc; i += NT) {
+    const int r = i / Wc, kw = i - r * Wc;
+    dst[(size_t)(h0 + r) * Wc + kw] = sm[(size_t)r * ls + kw];
+  }
+}
+
+// the forward column transform of the setup's row spectra, in place
+__global__ void __launch_bounds__(NT) k_big_setup_cols(BigArgs a, const BigSetupItem* items, float2* dhat,
+                                                       float2* xhat) {
+  extern __shared__ float2 sm[];
+  __shared__ BigPlan pl;
+  const BigSetupItem it = items[blockIdx.x];
+  const BigCls& bc = a.cls[it.cls];
+  if (threadIdx.x == 0) pl = bc.pcol;
+  __syncthreads();
+  const int H = bc.H, Wc = bc.Wc, nc = it.count, kw0 = it.first;
+  const int ls = bc.col_ls;
+  float2* dst = (it.filter ? dhat : xhat) + it.dst;
+  for (int i = threadIdx.x; i < nc * H; i += NT) {
+    const int c = i % nc, h = i / nc;
+    sm[(size_t)c * ls + h] = dst[(size_t)h * Wc + kw0 + c];
+  }
+  __syncthreads();
+  fft1<false>(sm, nc, ls, pl, a.tabs);
+  for (int i = threadIdx.x; i < nc * H; i += NT) {
+    const int c = i % nc, h = i / nc;
+    dst[(size_t)h * Wc + kw0 + c] = sm[(size_t)c * ls + h];
+  }
+}
+
+}  // namespace big
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+static cudaError_t big_attr(const void* f, size_t smem) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st) {
+  using namespace big;
+  cudaError_t e = cudaSuccess;
+  const size_t csm = a.col_smem, rsm = a.row_smem;
+  if (mode == kIter || mode == kLast) {
+    if ((e = big_attr((const void*)k_big_cols<true>, csm)) != cudaSuccess) return e;
+    k_big_cols<true><<<a.n_col_items, NT, csm, st>>>(a);
+  }
+  switch (mode) {
+    case kPrologue:
+      if ((e = big_attr((const void*)k_big_rows<kPrologue>, rsm)) != cudaSuccess) return e;
+      k_big_rows<kPrologue><<<a.n_row_items, NT, rsm, st>>>(a);
+      break;
+    case kIter:
+      if ((e = big_attr((const void*)k_big_rows<kIter>, rsm)) != cudaSuccess) return e;
+      k_big_rows<kIter><<<a.n_row_items, NT, rsm, st>>>(a);
+      break;
+    case kLast:
+      if ((e = big_attr((const void*)k_big_rows<kLast>, rsm)) != cudaSuccess) return e;
+      k_big_rows<kLast><<<a.n_row_items, NT, rsm, st>>>(a);
+      break;
+    default:
+      if ((e = big_attr((const void*)k_big_rows<kObjective>, rsm)) != cudaSuccess) return e;
+      k_big_rows<kObjective><<<a.n_row_items, NT, rsm, st>>>(a);
+      break;
+  }
+  if (mode == kLast) return cudaGetLastError();
+  if ((e = big_attr((const void*)k_big_cols<false>, csm)) != cudaSuccess) return e;
+  k_big_cols<false><<<a.n_col_items, NT, csm, st>>>(a);
+  if (mode == kObjective) k_big_freq<kObjective><<<a.n_freq_items, NT, 0, st>>>(a);
+  else k_big_freq<kIter><<<a.n_freq_items, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_big_setup(const BigArgs& a, const BigSetupItem* row_items, int n_rows,
+                             const BigSetupItem* col_items, int n_cols, const float* d, const float* x,
+                             float2* dhat, float2* xhat, int fh, int fw, cudaStream_t st) {
+  using namespace big;
+  cudaError_t e;
+  if ((e = big_attr((const void*)k_big_setup_rows, a.row_smem)) != cudaSuccess) return e;
+  if ((e = big_attr((const void*)k_big_setup_cols, a.col_smem)) != cudaSuccess) return e;
+  if (n_rows > 0) k_big_setup_rows<<<n_rows, NT, a.row_smem, st>>>(a, row_items, d, x, dhat, xhat, fh, fw);
+  if (n_cols > 0) k_big_setup_cols<<<n_cols, NT, a.col_smem, st>>>(a, col_items, dhat, xhat);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// host planning
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+bool smooth7(int n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+// the DFT of x (length n, any factorisation) in double: recursive decimation in time on the smallest
+// prime factor
+void host_dft(const double* xr, const double* xi, int n, int stride, double* yr, double* yi) {
+  if (n == 1) { yr[0] = xr[0]; yi[0] = xi[0]; return; }
+  int p = 2;
+  while (n % p) ++p;
+  const int m = n / p;
+  std::vector<double> sr(n), si(n);
+  for (int r = 0; r < p; ++r) host_dft(xr + r * stride, xi + r * stride, m, stride * p, &sr[r * m], &si[r * m]);
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int k = 0; k < n; ++k) {
+    double ar = 0.0, ai = 0.0;
+    for (int r = 0; r < p; ++r) {
+      const double t = -pi2 * (double)(((long long)r * k) % n) / n;
+      const double c = std::cos(t), s = std::sin(t);
+      const double ur = sr[r * m + k % m], ui = si[r * m + k % m];
+      ar += ur * c - ui * s;
+      ai += ur * s + ui * c;
+    }
+    yr[k] = ar;
+    yi[k] = ai;
+  }
+}
+
+void push_twiddles(std::vector<float2>& tabs, int L) {
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int t = 0; t < L; ++t) tabs.push_back(make_float2((float)std::cos(pi2 * t / L), (float)-std::sin(pi2 * t / L)));
+}
+
+const BigPlan& plan_of(UnevenLayout& L, int n) {
+  for (const BigPlan& p : L.bplans)
+    if (p.n == n) return p;
+  BigPlan p{};
+  p.n = n;
+  if (smooth7(n)) {
+    p.M = 0;
+    p.rad = factorize(n);
+    p.tw = (long long)L.btabs.size();
+    push_twiddles(L.btabs, n);
+  } else {
+    int M = 2 * n - 1;
+    while (!smooth7(M)) ++M;
+    p.M = M;
+    p.rad = factorize(M);
+    p.tw = (long long)L.btabs.size();
+    push_twiddles(L.btabs, M);
+    // chirp w_j = exp(-pi i j^2 / n), the phase reduced mod 2n in integers
+    const double pi = 3.14159265358979323846264338328;
+    std::vector<double> wr(n), wi(n);
+    p.chirp = (long long)L.btabs.size();
+    for (int j = 0; j < n; ++j) {
+      const double t = -pi * (double)(((long long)j * j) % (2LL * n)) / n;
+      wr[j] = std::cos(t);
+      wi[j] = std::sin(t);
+      L.btabs.push_back(make_float2((float)wr[j], (float)wi[j]));
+    }
+    // b_m = conj(w_|m|) on the circle of length M, its DFT divided by M
+    std::vector<double> br(M, 0.0), bi(M, 0.0), hr(M), hi(M);
+    for (int j = 0; j < n; ++j) {
+      br[j] = wr[j]; bi[j] = -wi[j];
+      if (j > 0) { br[M - j] = wr[j]; bi[M - j] = -wi[j]; }
+    }
+    host_dft(br.data(), bi.data(), M, 1, hr.data(), hi.data());
+    p.bhat = (long long)L.btabs.size();
+    for (int k = 0; k < M; ++k) L.btabs.push_back(make_float2((float)(hr[k] / M), (float)(hi[k] / M)));
+  }
+  L.bplans.push_back(p);
+  return L.bplans.back();
+}
+
+int odd_at_least(int n) { return n | 1; }
+
+constexpr size_t kBigLineBudget = 64 * 1024;   // shared memory per work item (bytes)
+
+int lines_per_item(int ls, int total) {
+  const int l = (int)(kBigLineBudget / ((size_t)ls * sizeof(float2)));
+  return std::max(1, std::min(l, total));
+}
+
+}  // namespace
+
+bool big_add_class(UnevenLayout& L, int H, int W) {
+  if (H < 1 || W < 1 || H > kBigMaxSide || W > kBigMaxSide) return false;
+  BigCls bc{};
+  bc.H = H; bc.W = W; bc.Wc = W / 2 + 1;
+  bc.pcol = plan_of(L, H);
+  bc.prow = plan_of(L, W);
+  bc.col_ls = odd_at_least(std::max(H, bc.pcol.M));
+  bc.row_ls = odd_at_least(std::max(W, bc.prow.M));
+  L.bcls.push_back(bc);
+  L.bcls_H.push_back(H);
+  L.bcls_W.push_back(W);
+  return true;
+}
+
+void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<BigSetupItem>& setup) {
+  (void)fh; (void)fw;
+  L.bcol.clear(); L.brow.clear(); L.bfreq.clear(); setup.clear();
+  L.bcol_smem = L.brow_smem = 0;
+  std::vector<int> nc(L.bcls.size()), nr(L.bcls.size());
+  for (size_t ci = 0; ci < L.bcls.size(); ++ci) {
+    const BigCls& bc = L.bcls[ci];
+    nc[ci] = lines_per_item(bc.col_ls, bc.Wc);
+    nr[ci] = lines_per_item(bc.row_ls, bc.H);
+    L.bcol_smem = std::max(L.bcol_smem, (size_t)nc[ci] * bc.col_ls * sizeof(float2));
+    L.brow_smem = std::max(L.brow_smem, (size_t)nr[ci] * bc.row_ls * sizeof(float2));
+  }
+  for (int i = 0; i < (int)L.bimg.size(); ++i) {
+    const int ci = L.bimg[i].cls;
+    const BigCls& bc = L.bcls[ci];
+    const int Om = bc.H * bc.Wc;
+    for (int k = 0; k < K; ++k) {
+      for (int c0 = 0; c0 < bc.Wc; c0 += nc[ci]) L.bcol.push_back({i, k, c0, std::min(nc[ci], bc.Wc - c0)});
+      for (int h0 = 0; h0 < bc.H; h0 += nr[ci]) L.brow.push_back({i, k, h0, std::min(nr[ci], bc.H - h0)});
+    }
+    for (int o0 = 0; o0 < Om; o0 += big::NT) L.bfreq.push_back({i, 0, o0, std::min(big::NT, Om - o0)});
+  }
+  // setup: rows of every filter of every class and of every image, then their columns
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int ci = 0; ci < (int)L.bcls.size(); ++ci) {
+      const BigCls& bc = L.bcls[ci];
+      const int Om = bc.H * bc.Wc;
+      for (int m = 0; m < K * J; ++m) {
+        const long long src = (long long)m * fh * fw, dst = bc.dhat + (long long)m * Om;
+        if (pass == 0)
+          for (int h0 = 0; h0 < bc.H; h0 += nr[ci]) setup.push_back({ci, h0, std::min(nr[ci], bc.H - h0), 1, src, dst});
+        else
+          for (int c0 = 0; c0 < bc.Wc; c0 += nc[ci]) setup.push_back({ci, c0, std::min(nc[ci], bc.Wc - c0), 1, src, dst});
+      }
+    }
+    for (int i = 0; i < (int)L.bimg.size(); ++i) {
+      const BigImg& im = L.bimg[i];
+      const BigCls& bc = L.bcls[im.cls];
+      const int Om = bc.H * bc.Wc;
+      for (int j = 0; j < J; ++j) {
+        const long long src = im.x + (long long)j * bc.H * bc.W, dst = im.xh + (long long)j * Om;
+        if (pass == 0)
+          for (int h0 = 0; h0 < bc.H; h0 += nr[im.cls])
+            setup.push_back({im.cls, h0, std::min(nr[im.cls], bc.H - h0), 0, src, dst});
+        else
+          for (int c0 = 0; c0 < bc.Wc; c0 += nc[im.cls])
+            setup.push_back({im.cls, c0, std::min(nc[im.cls], bc.Wc - c0), 0, src, dst});
+      }
+    }
+    if (pass == 0) L.n_bsetup_rows = (int)setup.size();
+  }
+  L.n_bsetup_cols = (int)setup.size() - L.n_bsetup_rows;
+}
+
+}  // namespace csc

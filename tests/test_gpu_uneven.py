@@ -107,9 +107,66 @@ def test_uneven_objective_matches_oracle(csc):
 
 
 def test_uneven_rejects_unsupported_sizes_and_calls(csc):
-    with pytest.raises(csc.CscError) as e:
-        csc.Solver(J=1, K=2, fs=(3, 3), dims_list=[(64, 64), (22, 16)], beta=1.0, rho=1.0)
-    assert e.value.status == 2 and "22x16" in str(e.value)
+    for bad in [(2000, 64), (64, 6), (9, 4)]:
+        with pytest.raises(csc.CscError) as e:
+            csc.Solver(J=1, K=2, fs=(5, 5), dims_list=[(64, 64), bad], beta=1.0, rho=1.0)
+        assert e.value.status == 2 and f"{bad[0]}x{bad[1]}" in str(e.value)
+
+
+# sides the one-map-per-CTA sweep cannot hold: odd widths, prime sides (Bluestein), sides above 128
+LARGE = [(67, 131), (64, 64), (200, 181), (256, 300), (9, 8), (130, 97), (509, 64), (100, 100), (67, 131)]
+
+
+@pytest.mark.parametrize("J,K,s,iters,sizes", [
+    (1, 4, 5, 4, LARGE),
+    (3, 3, 3, 3, [(31, 45), (64, 64), (97, 128), (140, 77)]),
+    (1, 6, 11, 3, [(173, 211), (96, 70), (512, 509)]),
+])
+def test_uneven_large_odd_and_prime_sizes_match_oracle(csc, J, K, s, iters, sizes):
+    """Images outside the one-map-per-CTA sweep (multi-pass transforms through HBM, Bluestein's
+    chirp z-transform for lengths with prime factors above 7) mixed with images it holds: the state
+    and the codes of every image against the oracle run image by image, and the objective."""
+    import torch
+    beta, rho = 0.3, 1.0
+    xs, d = batch(500 + K, sizes, K, J, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    with csc.Solver(J=J, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho) as sv:
+        v = torch.zeros(n_v, device="cuda")
+        z = torch.empty_like(v)
+        sv.code(flat(xs), flat([d]), v, z, iters)
+        torch.cuda.synchronize()
+        info = json.loads(sv.describe())
+        f = sv.objective(flat(xs), flat([d]), z)
+    assert info["large_images"] > 0
+    fo = 0.0
+    for xo, vg, zg in zip(xs, split(v, sizes, K), split(z, sizes, K)):
+        vo, zo = O.code_admm(xo, d, beta, rho, iters)
+        assert rel(vg, vo) <= REL_TOL and maxrel(vg, vo) <= REL_TOL
+        if np.any(zo != 0):
+            assert rel(zg, zo) <= REL_TOL
+        fo += O.objective(xo, d, zg, beta)
+    assert abs(f - fo) <= 1e-5 * fo
+
+
+def test_uneven_all_large_with_graph_replay(csc):
+    """A batch with no image for the one-map-per-CTA sweep; CSC_FLAG_GRAPH replay equals eager."""
+    import torch
+    sizes = [(131, 67), (150, 150), (77, 301)]
+    K, s, beta, rho = 3, 5, 0.3, 1.0
+    xs, d = batch(700, sizes, K, 1, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    out = {}
+    for flags in (0, csc.CSC_FLAG_GRAPH):
+        with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho, flags=flags) as sv:
+            v = torch.zeros(n_v, device="cuda")
+            z = torch.empty_like(v)
+            for _ in range(2):
+                sv.code(flat(xs), flat([d]), v, z, 3)
+            torch.cuda.synchronize()
+            out[flags] = v.cpu().numpy()
+    np.testing.assert_array_equal(out[0], out[csc.CSC_FLAG_GRAPH])
+    vo = np.concatenate([O.code_admm(xo, d, beta, rho, 6)[0].reshape(-1) for xo in xs])
+    assert rel(out[0].astype(np.float64), vo) <= REL_TOL
 
 
 def test_uneven_bf16_contractions_against_oracle(csc):
