@@ -322,8 +322,8 @@ cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
     const UnevenLayout& U = c->U;
     cudaError_t e = launch_big_setup(big_args(*c, nullptr, nullptr), U.d_bsetup, U.n_bsetup_rows,
                                      U.d_bsetup + U.n_bsetup_rows, U.n_bsetup_cols, d, x, c->dhat, c->xhat, c->fh,
-                                     c->fw, c->stream);
-    c->launches += 2;
+                                     c->fw, (int)U.bcls.size(), c->stream);
+    c->launches += 3;
     for (int ci = 0; ci < (int)U.bcls.size() && solve && e == cudaSuccess; ++ci) {
       const BigCls& bc = U.bcls[ci];
       Ctx v;

@@ -102,6 +102,7 @@ struct BigPlan {          // a length-n complex DFT
   Radices rad;            // radices of n, or of M
   long long tw;           // twiddles exp(-2 pi i t / L), L = n or M: element offset into the tables
   long long chirp, bhat;  // Bluestein: w_j = exp(-pi i j^2 / n) (n), FFT_M of the conjugate chirp / M (M)
+  long long twn;          // exp(-2 pi i t / n), t < n (direct DFTs of the filters)
 };
 struct BigCls {
   int H, W, Wc;           // Wc = W/2 + 1 stored columns (both parities)
@@ -148,7 +149,7 @@ constexpr int kBigMaxSide = 1024;
 cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st);
 cudaError_t launch_big_setup(const BigArgs& a, const BigSetupItem* row_items, int n_rows,
                              const BigSetupItem* col_items, int n_cols, const float* d, const float* x,
-                             float2* dhat, float2* xhat, int fh, int fw, cudaStream_t st);
+                             float2* dhat, float2* xhat, int fh, int fw, int n_classes, cudaStream_t st);
 struct UnevenLayout;
 // plans (and their tables, appended to L.btabs) of a new H x W class; false if a side is out of range
 bool big_add_class(UnevenLayout& L, int H, int W);

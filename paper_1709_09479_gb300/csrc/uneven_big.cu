@@ -30,6 +30,7 @@ namespace csc {
 namespace big {
 
 constexpr int NT = 256;
+constexpr int kMinCtas = 3;   // resident CTAs per SM the transform kernels are compiled for
 
 __device__ __forceinline__ float bclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
@@ -77,7 +78,7 @@ __device__ void fft1(float2* buf, int nlines, int ls, const BigPlan& pl, const f
 // BUILD: the inverse transform of w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j; else the forward
 // transform of the stored row spectra
 template <bool BUILD>
-__global__ void __launch_bounds__(NT) k_big_cols(BigArgs a) {
+__global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   extern __shared__ float2 sm[];
   __shared__ BigPlan pl;
   const BigItem it = a.col_items[blockIdx.x];
@@ -113,8 +114,19 @@ __global__ void __launch_bounds__(NT) k_big_cols(BigArgs a) {
 }
 
 // ---- row pass: item = (image, map, first row, rows) ----------------------------------------------
+// Two real rows a, b share one complex transform: the inverse transforms Z = X_a + i X_b (each row
+// spectrum completed by Hermitian symmetry, the imaginary parts of its DC and Nyquist bins dropped,
+// as a real inverse transform does) into z = x_a + i x_b; the forward transform of u_a + i u_b gives
+// U_a(k) = (Z(k) + conj Z(-k)) / 2 and U_b(k) = (Z(k) - conj Z(-k)) / 2i.
+__device__ __forceinline__ float2 half_bin(const float2* row, int kw, int W, int Wc) {
+  float2 v = kw < Wc ? row[kw] : row[W - kw];
+  if (kw >= Wc) v.y = -v.y;
+  if (kw == 0 || 2 * kw == W) v.y = 0.f;
+  return v;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(NT) k_big_rows(BigArgs a) {
+__global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   extern __shared__ float2 sm[];
   __shared__ BigPlan pl;
   __shared__ double red[NT / 32];
@@ -124,54 +136,61 @@ __global__ void __launch_bounds__(NT) k_big_rows(BigArgs a) {
   if (threadIdx.x == 0) pl = bc.prow;
   __syncthreads();
   const int H = bc.H, W = bc.W, Wc = bc.Wc, Om = H * Wc, nr = it.count, h0 = it.first;
+  const int np = (nr + 1) / 2;
   const int ls = bc.row_ls;
   const size_t moff = im.v + (size_t)it.map * H * W;
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
+  float* smf = reinterpret_cast<float*>(sm);
   const float beta = a.beta;
   double l1 = 0.0;
   if (MODE == kIter || MODE == kLast) {
-    // the row spectra of w, completed by Hermitian symmetry, to the rows of w
-    for (int i = threadIdx.x; i < nr * W; i += NT) {
-      const int r = i / W, kw = i - r * W;
-      const float2* src = Y + (size_t)(h0 + r) * Wc;
-      float2 v = kw < Wc ? src[kw] : src[W - kw];
-      if (kw >= Wc) v.y = -v.y;
-      sm[(size_t)r * ls + kw] = v;
+    for (int i = threadIdx.x; i < np * W; i += NT) {
+      const int q = i / W, kw = i - q * W;
+      const float2 xa = half_bin(Y + (size_t)(h0 + 2 * q) * Wc, kw, W, Wc);
+      const float2 xb = (2 * q + 1 < nr) ? half_bin(Y + (size_t)(h0 + 2 * q + 1) * Wc, kw, W, Wc) : make_float2(0.f, 0.f);
+      sm[(size_t)q * ls + kw] = make_float2(xa.x - xb.y, xa.y + xb.x);
     }
     __syncthreads();
-    fft1<true>(sm, nr, ls, pl, a.tabs);
+    fft1<true>(sm, np, ls, pl, a.tabs);
     for (int i = threadIdx.x; i < nr * W; i += NT) {
       const int r = i / W, x = i - r * W;
+      float* cell = smf + 2 * ((size_t)(r >> 1) * ls + x) + (r & 1);
       const size_t p = moff + (size_t)(h0 + r) * W + x;
       const float vo = a.v[p];
-      const float vn = sm[(size_t)r * ls + x].x - (bclamp(vo, beta) - vo);
+      const float vn = *cell - (bclamp(vo, beta) - vo);
       a.v[p] = vn;
       const float cn = bclamp(vn, beta);
       if (MODE == kLast) {
         if (a.z) a.z[p] = a.rho * (cn - vn);
       } else {
-        sm[(size_t)r * ls + x] = make_float2(2.f * cn - vn, 0.f);
+        *cell = 2.f * cn - vn;
+        if ((nr & 1) && r == nr - 1) cell[1] = 0.f;
       }
     }
   } else {
     const float* src = (MODE == kPrologue) ? a.v : a.z;
-    for (int i = threadIdx.x; i < nr * W; i += NT) {
+    for (int i = threadIdx.x; i < 2 * np * W; i += NT) {
       const int r = i / W, x = i - r * W;
-      const float t = src[moff + (size_t)(h0 + r) * W + x];
-      if (MODE == kPrologue) {
-        sm[(size_t)r * ls + x] = make_float2(2.f * bclamp(t, beta) - t, 0.f);
-      } else {
-        l1 += fabs((double)t);
-        sm[(size_t)r * ls + x] = make_float2(t, 0.f);
+      float t = 0.f;
+      if (r < nr) {
+        t = src[moff + (size_t)(h0 + r) * W + x];
+        if (MODE == kPrologue) t = 2.f * bclamp(t, beta) - t;
+        else l1 += fabs((double)t);
       }
+      smf[2 * ((size_t)(r >> 1) * ls + x) + (r & 1)] = t;
     }
   }
   if (MODE != kLast) {
     __syncthreads();
-    fft1<false>(sm, nr, ls, pl, a.tabs);
+    fft1<false>(sm, np, ls, pl, a.tabs);
     for (int i = threadIdx.x; i < nr * Wc; i += NT) {
       const int r = i / Wc, kw = i - r * Wc;
-      Y[(size_t)(h0 + r) * Wc + kw] = sm[(size_t)r * ls + kw];
+      const float2* zq = sm + (size_t)(r >> 1) * ls;
+      const float2 z1 = zq[kw], z2 = zq[kw == 0 ? 0 : W - kw];
+      float2 u;
+      if (r & 1) u = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+      else u = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+      Y[(size_t)(h0 + r) * Wc + kw] = u;
     }
   }
   if (MODE == kObjective) {
@@ -251,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_big_freq(BigArgs a) {
 
 // ---- spectra for the setup: the forward row transform of real maps (images, or filters placed with
 // their taps centred: tap (ta, tb) at ((ta - (fh-1)/2) mod H, (tb - (fw-1)/2) mod W)) -----------------
-__global__ void __launch_bounds__(NT) k_big_setup_rows(BigArgs a, const BigSetupItem* items, const float* d,
+__global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_rows(BigArgs a, const BigSetupItem* items, const float* d,
                                                        const float* x, float2* dhat, float2* xhat, int fh, int fw) {
   extern __shared__ float2 sm[];
   __shared__ BigPlan pl;
@@ -283,8 +302,48 @@ __global__ void __launch_bounds__(NT) k_big_setup_rows(BigArgs a, const BigSetup
   }
 }
 
+// filter spectra by direct DFT over the taps (fh x fw nonzero entries of an H x W grid): the row DFTs of
+// the tap rows, R(ta, kw) = sum_tb f(ta, tb) e^{-2 pi i kw (tb - cw) / W}, kept in shared memory (TA tap
+// rows at a time), then d_hat(h, kw) = sum_ta R(ta, kw) e^{-2 pi i h (ta - ch) / H}. One CTA per
+// (class, map).
+__global__ void __launch_bounds__(NT) k_big_filter_spectra(BigArgs a, const float* d, float2* dhat, int fh, int fw,
+                                                          int KJ, int TA) {
+  extern __shared__ float2 sm[];
+  const int ci = blockIdx.x / KJ, m = blockIdx.x - ci * KJ;
+  const BigCls& bc = a.cls[ci];
+  const int H = bc.H, W = bc.W, Wc = bc.Wc;
+  const int ch = (fh - 1) / 2, cw = (fw - 1) / 2;
+  const float* f = d + (size_t)m * fh * fw;
+  const float2* twW = a.tabs + bc.prow.twn;
+  const float2* twH = a.tabs + bc.pcol.twn;
+  float2* out = dhat + bc.dhat + (size_t)m * H * Wc;
+  for (int t0 = 0; t0 < fh; t0 += TA) {
+    const int tn = min(TA, fh - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < tn * Wc; i += NT) {
+      const int ta = i / Wc, kw = i - ta * Wc;
+      float2 s = make_float2(0.f, 0.f);
+      for (int tb = 0; tb < fw; ++tb) {
+        const float2 t = twW[(int)(((long long)(tb - cw + W) * kw) % W)];
+        const float fv = f[(t0 + ta) * fw + tb];
+        s.x = fmaf(fv, t.x, s.x);
+        s.y = fmaf(fv, t.y, s.y);
+      }
+      sm[i] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < H * Wc; o += NT) {
+      const int h = o / Wc, kw = o - h * Wc;
+      float2 s = t0 == 0 ? make_float2(0.f, 0.f) : out[o];
+      for (int ta = 0; ta < tn; ++ta)
+        s = cfma(sm[ta * Wc + kw], twH[(int)(((long long)(t0 + ta - ch + H) * h) % H)], s);
+      out[o] = s;
+    }
+  }
+}
+
 // the forward column transform of the setup's row spectra, in place
-__global__ void __launch_bounds__(NT) k_big_setup_cols(BigArgs a, const BigSetupItem* items, float2* dhat,
+__global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_cols(BigArgs a, const BigSetupItem* items, float2* dhat,
                                                        float2* xhat) {
   extern __shared__ float2 sm[];
   __shared__ BigPlan pl;
@@ -352,11 +411,16 @@ cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st) {
 
 cudaError_t launch_big_setup(const BigArgs& a, const BigSetupItem* row_items, int n_rows,
                              const BigSetupItem* col_items, int n_cols, const float* d, const float* x,
-                             float2* dhat, float2* xhat, int fh, int fw, cudaStream_t st) {
+                             float2* dhat, float2* xhat, int fh, int fw, int n_classes, cudaStream_t st) {
   using namespace big;
   cudaError_t e;
   if ((e = big_attr((const void*)k_big_setup_rows, a.row_smem)) != cudaSuccess) return e;
   if ((e = big_attr((const void*)k_big_setup_cols, a.col_smem)) != cudaSuccess) return e;
+  const int wmax = kBigMaxSide / 2 + 1;
+  const int TA = std::min(fh, std::max(1, (int)((64 * 1024) / (wmax * sizeof(float2)))));
+  const size_t fsm = (size_t)TA * wmax * sizeof(float2);
+  if ((e = big_attr((const void*)k_big_filter_spectra, fsm)) != cudaSuccess) return e;
+  k_big_filter_spectra<<<n_classes * a.K * a.J, NT, fsm, st>>>(a, d, dhat, fh, fw, a.K * a.J, TA);
   if (n_rows > 0) k_big_setup_rows<<<n_rows, NT, a.row_smem, st>>>(a, row_items, d, x, dhat, xhat, fh, fw);
   if (n_cols > 0) k_big_setup_cols<<<n_cols, NT, a.col_smem, st>>>(a, col_items, dhat, xhat);
   return cudaGetLastError();
@@ -410,9 +474,11 @@ const BigPlan& plan_of(UnevenLayout& L, int n) {
   if (smooth7(n)) {
     p.M = 0;
     p.rad = factorize(n);
-    p.tw = (long long)L.btabs.size();
+    p.tw = p.twn = (long long)L.btabs.size();
     push_twiddles(L.btabs, n);
   } else {
+    p.twn = (long long)L.btabs.size();
+    push_twiddles(L.btabs, n);
     int M = 2 * n - 1;
     while (!smooth7(M)) ++M;
     p.M = M;
@@ -476,7 +542,7 @@ void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<
   for (size_t ci = 0; ci < L.bcls.size(); ++ci) {
     const BigCls& bc = L.bcls[ci];
     nc[ci] = lines_per_item(bc.col_ls, bc.Wc);
-    nr[ci] = lines_per_item(bc.row_ls, bc.H);
+    nr[ci] = lines_per_item(bc.row_ls, bc.H);   // transform lines: 2 rows each in the sweeps
     L.bcol_smem = std::max(L.bcol_smem, (size_t)nc[ci] * bc.col_ls * sizeof(float2));
     L.brow_smem = std::max(L.brow_smem, (size_t)nr[ci] * bc.row_ls * sizeof(float2));
   }
@@ -486,23 +552,12 @@ void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<
     const int Om = bc.H * bc.Wc;
     for (int k = 0; k < K; ++k) {
       for (int c0 = 0; c0 < bc.Wc; c0 += nc[ci]) L.bcol.push_back({i, k, c0, std::min(nc[ci], bc.Wc - c0)});
-      for (int h0 = 0; h0 < bc.H; h0 += nr[ci]) L.brow.push_back({i, k, h0, std::min(nr[ci], bc.H - h0)});
+      for (int h0 = 0; h0 < bc.H; h0 += 2 * nr[ci]) L.brow.push_back({i, k, h0, std::min(2 * nr[ci], bc.H - h0)});
     }
     for (int o0 = 0; o0 < Om; o0 += big::NT) L.bfreq.push_back({i, 0, o0, std::min(big::NT, Om - o0)});
   }
-  // setup: rows of every filter of every class and of every image, then their columns
+  // setup: rows of every image, then their columns (the filter spectra are direct DFTs)
   for (int pass = 0; pass < 2; ++pass) {
-    for (int ci = 0; ci < (int)L.bcls.size(); ++ci) {
-      const BigCls& bc = L.bcls[ci];
-      const int Om = bc.H * bc.Wc;
-      for (int m = 0; m < K * J; ++m) {
-        const long long src = (long long)m * fh * fw, dst = bc.dhat + (long long)m * Om;
-        if (pass == 0)
-          for (int h0 = 0; h0 < bc.H; h0 += nr[ci]) setup.push_back({ci, h0, std::min(nr[ci], bc.H - h0), 1, src, dst});
-        else
-          for (int c0 = 0; c0 < bc.Wc; c0 += nc[ci]) setup.push_back({ci, c0, std::min(nc[ci], bc.Wc - c0), 1, src, dst});
-      }
-    }
     for (int i = 0; i < (int)L.bimg.size(); ++i) {
       const BigImg& im = L.bimg[i];
       const BigCls& bc = L.bcls[im.cls];
