@@ -239,9 +239,6 @@ def time_to_target(csc, torch, dev, precision=None, graph=False):
     return out
 
 
-UNEVEN_SIDES = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
-
-
 def measure_extensions(csc, torch, dev, hbm_peak):
     """The spec extensions, each on its own workload, device-timed with CUDA events:
     uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
@@ -253,10 +250,10 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    # --- uneven256: sides drawn independently from the even 7-smooth sizes in [64, 128] ----------
+    # --- uneven256: H and W drawn independently and uniformly from [64, 512] ------------------------
     rng = np.random.default_rng(3)
-    sizes = [(int(rng.choice(UNEVEN_SIDES)), int(rng.choice(UNEVEN_SIDES))) for _ in range(256)]
-    K, s, iters = 64, 11, 10
+    sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(256)]
+    K, s, iters = 64, 11, 5
     xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
     x = torch.from_numpy(xs.astype(np.float32)).to(dev)
     d = torch.from_numpy(inputs.unit_filters(30, K, 1, (s, s)).astype(np.float32)).to(dev)
@@ -285,10 +282,11 @@ def measure_extensions(csc, torch, dev, hbm_peak):
         tm = sv2.timing_read()
     sweep_s = tm["sweep_ms"] / max(tm["sweep_launches"], 1) / 1e3
     alg = 8.0 * K * npx + 8.0 * nom
-    out["uneven256"] = {"workload": "256 grey images, H and W drawn independently from the even 7-smooth sizes in "
-                                    "[64, 128] (seed 3), K=64 filters 11x11, beta=1, rho=0.1, float32",
-                        "pixels": npx, "size_classes": desc["size_classes"], "launch": desc,
-                        "coding_iters_per_s": iters / (ms / 1e3), "ms_per_call_of_10_iters": ms,
+    out["uneven256"] = {"workload": "256 grey images, H and W drawn independently and uniformly from [64, 512] "
+                                    "(seed 3), K=64 filters 11x11, beta=1, rho=0.1, float32",
+                        "pixels": npx, "size_classes": desc["size_classes"] + desc["large_size_classes"],
+                        "images_on_multi_pass_engine": desc["large_images"], "launch": desc,
+                        "coding_iters_per_s": iters / (ms / 1e3), f"ms_per_call_of_{iters}_iters": ms,
                         "sweep_us": sweep_s * 1e6, "sweep_hbm_frac": alg / sweep_s / 1e9 / hbm_peak}
     # the same batch with the per-frequency contractions in bfloat16 (float32 accumulation)
     with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1,

@@ -135,6 +135,7 @@ struct BigArgs {
   size_t col_smem, row_smem;
   const float2* tabs;
   const float2* dhat;
+  const __nv_bfloat162* dhat16;   // mixed precision: bf16 copy of dhat (contraction operands), else null
   const float* pdiag;
   const float2* pmat;
   const float2* xhat;

@@ -33,45 +33,48 @@ constexpr int NT = 256;
 constexpr int kMinCtas = 3;   // resident CTAs per SM the transform kernels are compiled for
 
 __device__ __forceinline__ float bclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
+// a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
+__device__ __forceinline__ float2 bbf16(float2 v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
 
-// nlines lines of length pl.n at buf + line * ls; the Bluestein path needs ls >= pl.M. Ends synchronised.
+// A transform of nlines lines of length pl.n at buf + line * ls (ls >= pl.M) is: each element j < n
+// stored through fin (Bluestein: the chirp w_j, after conjugation for the inverse), the padding [n, M)
+// zeroed by fpad, a synchronisation, fcore, and each result element read through fout (Bluestein: the
+// chirp again, and the conjugation for the inverse). Without Bluestein, fin and fout are the identity.
 template <bool INV>
-__device__ void fft1(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs) {
+__device__ __forceinline__ float2 fin(float2 v, int j, const BigPlan& pl, const float2* tabs) {
+  if (pl.M == 0) return v;
+  if (INV) v.y = -v.y;
+  return cmul(v, __ldg(tabs + pl.chirp + j));
+}
+template <bool INV>
+__device__ __forceinline__ float2 fout(float2 v, int j, const BigPlan& pl, const float2* tabs) {
+  if (pl.M == 0) return v;
+  v = cmul(v, __ldg(tabs + pl.chirp + j));
+  if (INV) v.y = -v.y;
+  return v;
+}
+__device__ __forceinline__ void fpad(float2* buf, int nlines, int ls, const BigPlan& pl) {
+  if (pl.M == 0) return;
+  const int pad = pl.M - pl.n;
+  for (int line = 0; line < nlines; ++line)
+    for (int j = threadIdx.x; j < pad; j += NT) buf[(size_t)line * ls + pl.n + j] = make_float2(0.f, 0.f);
+}
+// ends synchronised
+template <bool INV>
+__device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs) {
   if (pl.M == 0) {
     stages_rt<INV, NT>(buf, nlines, ls, 1, pl.n, pl.rad, tabs + pl.tw);
     return;
   }
-  const int n = pl.n, M = pl.M;
-  const float2* w = tabs + pl.chirp;
+  const int M = pl.M;
   const float2* bh = tabs + pl.bhat;
-  for (int i = threadIdx.x; i < nlines * M; i += NT) {
-    const int line = i / M, j = i - line * M;
-    float2* p = buf + (size_t)line * ls + j;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < n) {
-      v = *p;
-      if (INV) v.y = -v.y;
-      v = cmul(v, w[j]);
-    }
-    *p = v;
-  }
-  __syncthreads();
   stages_rt<false, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
-  for (int i = threadIdx.x; i < nlines * M; i += NT) {
-    const int line = i / M, j = i - line * M;
-    float2* p = buf + (size_t)line * ls + j;
-    *p = cmul(*p, bh[j]);
+  for (int line = 0; line < nlines; ++line) {
+    float2* b = buf + (size_t)line * ls;
+    for (int j = threadIdx.x; j < M; j += NT) b[j] = cmul(b[j], __ldg(bh + j));
   }
   __syncthreads();
   stages_rt<true, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
-  for (int i = threadIdx.x; i < nlines * n; i += NT) {
-    const int line = i / n, j = i - line * n;
-    float2* p = buf + (size_t)line * ls + j;
-    float2 v = cmul(*p, w[j]);
-    if (INV) v.y = -v.y;
-    *p = v;
-  }
-  __syncthreads();
 }
 
 // ---- column pass: item = (image, map, first column, columns) ------------------------------------
@@ -91,25 +94,30 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
   if (BUILD) {
     const float2* lam = a.lam + im.lam;
-    const float2* dk = a.dhat + bc.dhat + (size_t)it.map * a.J * Om;
+    const size_t dbase = bc.dhat + (size_t)it.map * a.J * Om;
     for (int i = threadIdx.x; i < nc * H; i += NT) {
       const int c = i % nc, h = i / nc;
       const int o = h * Wc + kw0 + c;
       float2 s = make_float2(0.f, 0.f);
-      for (int j = 0; j < a.J; ++j) s = cfmac(dk[(size_t)j * Om + o], lam[(size_t)j * Om + o], s);
-      sm[(size_t)c * ls + h] = s;
+      for (int j = 0; j < a.J; ++j) {
+        const size_t q = dbase + (size_t)j * Om + o;
+        const float2 l = lam[(size_t)j * Om + o];
+        s = a.dhat16 ? cfmac(__bfloat1622float2(a.dhat16[q]), bbf16(l), s) : cfmac(a.dhat[q], l, s);
+      }
+      sm[(size_t)c * ls + h] = fin<true>(s, h, pl, a.tabs);
     }
   } else {
     for (int i = threadIdx.x; i < nc * H; i += NT) {
       const int c = i % nc, h = i / nc;
-      sm[(size_t)c * ls + h] = Y[(size_t)h * Wc + kw0 + c];
+      sm[(size_t)c * ls + h] = fin<false>(Y[(size_t)h * Wc + kw0 + c], h, pl, a.tabs);
     }
   }
+  fpad(sm, nc, ls, pl);
   __syncthreads();
-  fft1<BUILD>(sm, nc, ls, pl, a.tabs);
+  fcore<BUILD>(sm, nc, ls, pl, a.tabs);
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int c = i % nc, h = i / nc;
-    Y[(size_t)h * Wc + kw0 + c] = sm[(size_t)c * ls + h];
+    Y[(size_t)h * Wc + kw0 + c] = fout<BUILD>(sm[(size_t)c * ls + h], h, pl, a.tabs);
   }
 }
 
@@ -140,53 +148,64 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   const int ls = bc.row_ls;
   const size_t moff = im.v + (size_t)it.map * H * W;
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
-  float* smf = reinterpret_cast<float*>(sm);
   const float beta = a.beta;
+  const bool pair_last = !(nr & 1);   // the last transform line holds two rows
   double l1 = 0.0;
   if (MODE == kIter || MODE == kLast) {
     for (int i = threadIdx.x; i < np * W; i += NT) {
       const int q = i / W, kw = i - q * W;
       const float2 xa = half_bin(Y + (size_t)(h0 + 2 * q) * Wc, kw, W, Wc);
       const float2 xb = (2 * q + 1 < nr) ? half_bin(Y + (size_t)(h0 + 2 * q + 1) * Wc, kw, W, Wc) : make_float2(0.f, 0.f);
-      sm[(size_t)q * ls + kw] = make_float2(xa.x - xb.y, xa.y + xb.x);
+      sm[(size_t)q * ls + kw] = fin<true>(make_float2(xa.x - xb.y, xa.y + xb.x), kw, pl, a.tabs);
     }
+    fpad(sm, np, ls, pl);
     __syncthreads();
-    fft1<true>(sm, np, ls, pl, a.tabs);
-    for (int i = threadIdx.x; i < nr * W; i += NT) {
-      const int r = i / W, x = i - r * W;
-      float* cell = smf + 2 * ((size_t)(r >> 1) * ls + x) + (r & 1);
-      const size_t p = moff + (size_t)(h0 + r) * W + x;
-      const float vo = a.v[p];
-      const float vn = *cell - (bclamp(vo, beta) - vo);
-      a.v[p] = vn;
-      const float cn = bclamp(vn, beta);
+    fcore<true>(sm, np, ls, pl, a.tabs);
+    for (int i = threadIdx.x; i < np * W; i += NT) {
+      const int q = i / W, x = i - q * W;
+      const bool has_b = (q < np - 1) || pair_last;
+      const float2 w = fout<true>(sm[(size_t)q * ls + x], x, pl, a.tabs);
+      const size_t pa = moff + (size_t)(h0 + 2 * q) * W + x, pb = pa + W;
+      const float va = a.v[pa], vb = has_b ? a.v[pb] : 0.f;
+      const float na = w.x - (bclamp(va, beta) - va), nb = w.y - (bclamp(vb, beta) - vb);
+      const float ca = bclamp(na, beta), cb = bclamp(nb, beta);
+      a.v[pa] = na;
+      if (has_b) a.v[pb] = nb;
       if (MODE == kLast) {
-        if (a.z) a.z[p] = a.rho * (cn - vn);
+        if (a.z) {
+          a.z[pa] = a.rho * (ca - na);
+          if (has_b) a.z[pb] = a.rho * (cb - nb);
+        }
       } else {
-        *cell = 2.f * cn - vn;
-        if ((nr & 1) && r == nr - 1) cell[1] = 0.f;
+        sm[(size_t)q * ls + x] = fin<false>(make_float2(2.f * ca - na, has_b ? 2.f * cb - nb : 0.f), x, pl, a.tabs);
       }
     }
+    if (MODE != kLast) fpad(sm, np, ls, pl);
   } else {
     const float* src = (MODE == kPrologue) ? a.v : a.z;
-    for (int i = threadIdx.x; i < 2 * np * W; i += NT) {
-      const int r = i / W, x = i - r * W;
-      float t = 0.f;
-      if (r < nr) {
-        t = src[moff + (size_t)(h0 + r) * W + x];
-        if (MODE == kPrologue) t = 2.f * bclamp(t, beta) - t;
-        else l1 += fabs((double)t);
+    for (int i = threadIdx.x; i < np * W; i += NT) {
+      const int q = i / W, x = i - q * W;
+      const bool has_b = (q < np - 1) || pair_last;
+      const size_t pa = moff + (size_t)(h0 + 2 * q) * W + x;
+      float ta = src[pa], tb = has_b ? src[pa + W] : 0.f;
+      if (MODE == kPrologue) {
+        ta = 2.f * bclamp(ta, beta) - ta;
+        tb = 2.f * bclamp(tb, beta) - tb;
+      } else {
+        l1 += fabs((double)ta) + fabs((double)tb);
       }
-      smf[2 * ((size_t)(r >> 1) * ls + x) + (r & 1)] = t;
+      sm[(size_t)q * ls + x] = fin<false>(make_float2(ta, tb), x, pl, a.tabs);
     }
+    fpad(sm, np, ls, pl);
   }
   if (MODE != kLast) {
     __syncthreads();
-    fft1<false>(sm, np, ls, pl, a.tabs);
+    fcore<false>(sm, np, ls, pl, a.tabs);
     for (int i = threadIdx.x; i < nr * Wc; i += NT) {
       const int r = i / Wc, kw = i - r * Wc;
       const float2* zq = sm + (size_t)(r >> 1) * ls;
-      const float2 z1 = zq[kw], z2 = zq[kw == 0 ? 0 : W - kw];
+      const int km = kw == 0 ? 0 : W - kw;
+      const float2 z1 = fout<false>(zq[kw], kw, pl, a.tabs), z2 = fout<false>(zq[km], km, pl, a.tabs);
       float2 u;
       if (r & 1) u = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
       else u = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
@@ -228,11 +247,20 @@ __global__ void __launch_bounds__(NT) k_big_freq(BigArgs a) {
     }
     const float2* Yb = a.Y + im.y;
     const float2* db = a.dhat + bc.dhat;
+    // mixed precision (not the objective): both operands of every product in bfloat16
+    const __nv_bfloat162* db16 = (MODE != kObjective && a.dhat16) ? a.dhat16 + bc.dhat : nullptr;
     for (int k = 0; k < K; ++k) {
       const float2 u = Yb[(size_t)k * Om + o];
+      if (db16) {
+        const float2 ub = bbf16(u);
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j)
-        if (j < J) r[j] = cfma(db[((size_t)k * J + j) * Om + o], u, r[j]);
+        for (int j = 0; j < kMaxJ; ++j)
+          if (j < J) r[j] = cfma(__bfloat1622float2(db16[((size_t)k * J + j) * Om + o]), ub, r[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kMaxJ; ++j)
+          if (j < J) r[j] = cfma(db[((size_t)k * J + j) * Om + o], u, r[j]);
+      }
     }
     if (MODE == kObjective) {
       const int kw = o % Wc;
@@ -292,13 +320,14 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_rows(BigArgs a, cons
     } else {
       v = src[(size_t)h * W + col];
     }
-    sm[(size_t)r * ls + col] = make_float2(v, 0.f);
+    sm[(size_t)r * ls + col] = fin<false>(make_float2(v, 0.f), col, pl, a.tabs);
   }
+  fpad(sm, nr, ls, pl);
   __syncthreads();
-  fft1<false>(sm, nr, ls, pl, a.tabs);
+  fcore<false>(sm, nr, ls, pl, a.tabs);
   for (int i = threadIdx.x; i < nr * Wc; i += NT) {
     const int r = i / Wc, kw = i - r * Wc;
-    dst[(size_t)(h0 + r) * Wc + kw] = sm[(size_t)r * ls + kw];
+    dst[(size_t)(h0 + r) * Wc + kw] = fout<false>(sm[(size_t)r * ls + kw], kw, pl, a.tabs);
   }
 }
 
@@ -356,13 +385,14 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_cols(BigArgs a, cons
   float2* dst = (it.filter ? dhat : xhat) + it.dst;
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int c = i % nc, h = i / nc;
-    sm[(size_t)c * ls + h] = dst[(size_t)h * Wc + kw0 + c];
+    sm[(size_t)c * ls + h] = fin<false>(dst[(size_t)h * Wc + kw0 + c], h, pl, a.tabs);
   }
+  fpad(sm, nc, ls, pl);
   __syncthreads();
-  fft1<false>(sm, nc, ls, pl, a.tabs);
+  fcore<false>(sm, nc, ls, pl, a.tabs);
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int c = i % nc, h = i / nc;
-    dst[(size_t)h * Wc + kw0 + c] = sm[(size_t)c * ls + h];
+    dst[(size_t)h * Wc + kw0 + c] = fout<false>(sm[(size_t)c * ls + h], h, pl, a.tabs);
   }
 }
 

@@ -7,7 +7,7 @@
 coding: csc_code with `iters` ADMM iterations (launch order: 2 spectra, solve setup, spectra,
 prologue sweep, then `iters` sweeps). learning: one csc_code of `iters` iterations, then csc_learn
 with `steps` learning steps. uneven: the 256-image batch of bench.py's uneven256 workload (sides uniform
-in [64, 512], K = 64), one csc_code of `iters` iterations (launch order: the setup transforms and the
+in [64, 512], K = 64; `--images` takes its first images only), one csc_code of `iters` iterations (launch order: the setup transforms and the
 per-class solve setup, the autotuner's sweeps when some images fit one map per CTA, then the call's
 prologue and sweeps). Inputs are
 the seeded 1/f^2 fields and Gaussian dictionaries of bench.py.
@@ -28,13 +28,14 @@ def main():
     ap.add_argument("--s", type=int, default=11)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--images", type=int, default=256, help="uneven: number of images")
     a = ap.parse_args()
     import torch
 
     from paper_1709_09479_gb300 import csc, inputs
     if a.what == "uneven":
         rng = np.random.default_rng(3)
-        sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(256)]
+        sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(a.images)]
         K = 64
         xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
         x = torch.from_numpy(xs.astype(np.float32)).cuda()

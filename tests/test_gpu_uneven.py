@@ -169,14 +169,15 @@ def test_uneven_all_large_with_graph_replay(csc):
     assert rel(out[0].astype(np.float64), vo) <= REL_TOL
 
 
-def test_uneven_bf16_contractions_against_oracle(csc):
+@pytest.mark.parametrize("sizes", [SIZES, [(67, 131), (64, 64), (150, 97), (200, 128)]])
+def test_uneven_bf16_contractions_against_oracle(csc, sizes):
     """The uneven batch in CSC_MIXED_BF16 (bfloat16 operands of the per-frequency contractions,
-    float32 accumulation): a stated error bound against the float64 oracle, the float32 run on the
-    same batch within the float32 bar, and the objective float32 in both modes."""
+    float32 accumulation), with and without images for the multi-pass engine: a stated error bound
+    against the float64 oracle, the float32 run on the same batch within the float32 bar, and the
+    objective float32 in both modes."""
     import torch
     from tests.test_gpu_precision import CODE_BF16_TOL
     K, s, iters, beta, rho = 6, 5, 6, 0.3, 1.0
-    sizes = SIZES
     xs, d = batch(400, sizes, K, 1, s)
     n_v = sum(K * H * W for H, W in sizes)
     out = {}
