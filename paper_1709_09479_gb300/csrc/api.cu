@@ -272,7 +272,7 @@ BigArgs big_args(const Ctx& c, float* v, float* z) {
   a.cls = U.d_bcls; a.img = U.d_bimg;
   a.col_items = U.d_bcol; a.row_items = U.d_brow; a.freq_items = U.d_bfreq;
   a.n_col_items = (int)U.bcol.size(); a.n_row_items = (int)U.brow.size(); a.n_freq_items = (int)U.bfreq.size();
-  a.col_smem = U.bcol_smem; a.row_smem = U.brow_smem;
+  a.col_smem = U.bcol_smem; a.row_smem = U.brow_smem; a.tw_max = U.btw_max;
   a.tabs = U.d_btabs; a.dhat = c.dhat; a.pdiag = c.pdiag; a.pmat = c.pmat; a.xhat = c.xhat;
   a.dhat16 = c.p.precision == CSC_MIXED_BF16 ? c.dhat16 : nullptr;
   a.Y = U.d_by; a.lam = U.d_blam; a.v = v; a.z = z; a.e_items = U.d_be; a.l1_items = U.d_bl1;

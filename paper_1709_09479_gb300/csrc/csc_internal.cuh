@@ -132,7 +132,8 @@ struct BigArgs {
   const BigItem* row_items;
   const BigItem* freq_items;
   int n_col_items, n_row_items, n_freq_items;
-  size_t col_smem, row_smem;
+  size_t col_smem, row_smem;   // bytes of the lines of a column / row work item; the twiddles follow
+  int tw_max;                   // longest twiddle table of the plans
   const float2* tabs;
   const float2* dhat;
   const __nv_bfloat162* dhat16;   // mixed precision: bf16 copy of dhat (contraction operands), else null
@@ -172,6 +173,7 @@ struct UnevenLayout {
   std::vector<BigPlan> bplans;   // one per transform length, shared by the classes
   std::vector<BigItem> bcol, brow, bfreq;
   size_t bcol_smem = 0, brow_smem = 0;
+  int btw_max = 0;
   long long n_by = 0, n_blam = 0;
   BigCls* d_bcls = nullptr;
   BigImg* d_bimg = nullptr;

@@ -59,22 +59,29 @@ __device__ __forceinline__ void fpad(float2* buf, int nlines, int ls, const BigP
   for (int line = 0; line < nlines; ++line)
     for (int j = threadIdx.x; j < pad; j += NT) buf[(size_t)line * ls + pl.n + j] = make_float2(0.f, 0.f);
 }
-// ends synchronised
+// the plan's twiddle table (length M, or n without Bluestein) copied to shared memory; no synchronisation
+__device__ __forceinline__ const float2* stage_tw(float2* dst, const BigPlan& pl, const float2* tabs) {
+  const int L = pl.M ? pl.M : pl.n;
+  for (int t = threadIdx.x; t < L; t += NT) dst[t] = __ldg(tabs + pl.tw + t);
+  return dst;
+}
+
+// tw: the plan's twiddle table (in shared memory); ends synchronised
 template <bool INV>
-__device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs) {
+__device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs, const float2* tw) {
   if (pl.M == 0) {
-    stages_rt<INV, NT>(buf, nlines, ls, 1, pl.n, pl.rad, tabs + pl.tw);
+    stages_rt<INV, NT>(buf, nlines, ls, 1, pl.n, pl.rad, tw);
     return;
   }
   const int M = pl.M;
   const float2* bh = tabs + pl.bhat;
-  stages_rt<false, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
+  stages_rt<false, NT>(buf, nlines, ls, 1, M, pl.rad, tw);
   for (int line = 0; line < nlines; ++line) {
     float2* b = buf + (size_t)line * ls;
     for (int j = threadIdx.x; j < M; j += NT) b[j] = cmul(b[j], __ldg(bh + j));
   }
   __syncthreads();
-  stages_rt<true, NT>(buf, nlines, ls, 1, M, pl.rad, tabs + pl.tw);
+  stages_rt<true, NT>(buf, nlines, ls, 1, M, pl.rad, tw);
 }
 
 // ---- column pass: item = (image, map, first column, columns) ------------------------------------
@@ -89,6 +96,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   const BigCls& bc = a.cls[im.cls];
   if (threadIdx.x == 0) pl = bc.pcol;
   __syncthreads();
+  const float2* tw = stage_tw(sm + a.col_smem / sizeof(float2), pl, a.tabs);
   const int H = bc.H, Wc = bc.Wc, Om = H * Wc, nc = it.count, kw0 = it.first;
   const int ls = bc.col_ls;
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   }
   fpad(sm, nc, ls, pl);
   __syncthreads();
-  fcore<BUILD>(sm, nc, ls, pl, a.tabs);
+  fcore<BUILD>(sm, nc, ls, pl, a.tabs, tw);
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int c = i % nc, h = i / nc;
     Y[(size_t)h * Wc + kw0 + c] = fout<BUILD>(sm[(size_t)c * ls + h], h, pl, a.tabs);
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   const BigCls& bc = a.cls[im.cls];
   if (threadIdx.x == 0) pl = bc.prow;
   __syncthreads();
+  const float2* tw = stage_tw(sm + a.row_smem / sizeof(float2), pl, a.tabs);
   const int H = bc.H, W = bc.W, Wc = bc.Wc, Om = H * Wc, nr = it.count, h0 = it.first;
   const int np = (nr + 1) / 2;
   const int ls = bc.row_ls;
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
     }
     fpad(sm, np, ls, pl);
     __syncthreads();
-    fcore<true>(sm, np, ls, pl, a.tabs);
+    fcore<true>(sm, np, ls, pl, a.tabs, tw);
     for (int i = threadIdx.x; i < np * W; i += NT) {
       const int q = i / W, x = i - q * W;
       const bool has_b = (q < np - 1) || pair_last;
@@ -200,7 +209,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   }
   if (MODE != kLast) {
     __syncthreads();
-    fcore<false>(sm, np, ls, pl, a.tabs);
+    fcore<false>(sm, np, ls, pl, a.tabs, tw);
     for (int i = threadIdx.x; i < nr * Wc; i += NT) {
       const int r = i / Wc, kw = i - r * Wc;
       const float2* zq = sm + (size_t)(r >> 1) * ls;
@@ -306,6 +315,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_rows(BigArgs a, cons
   const BigCls& bc = a.cls[it.cls];
   if (threadIdx.x == 0) pl = bc.prow;
   __syncthreads();
+  const float2* tw = stage_tw(sm + a.row_smem / sizeof(float2), pl, a.tabs);
   const int H = bc.H, W = bc.W, Wc = bc.Wc, nr = it.count, h0 = it.first;
   const int ls = bc.row_ls;
   const float* src = (it.filter ? d : x) + it.src;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_rows(BigArgs a, cons
   }
   fpad(sm, nr, ls, pl);
   __syncthreads();
-  fcore<false>(sm, nr, ls, pl, a.tabs);
+  fcore<false>(sm, nr, ls, pl, a.tabs, tw);
   for (int i = threadIdx.x; i < nr * Wc; i += NT) {
     const int r = i / Wc, kw = i - r * Wc;
     dst[(size_t)(h0 + r) * Wc + kw] = fout<false>(sm[(size_t)r * ls + kw], kw, pl, a.tabs);
@@ -380,6 +390,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_cols(BigArgs a, cons
   const BigCls& bc = a.cls[it.cls];
   if (threadIdx.x == 0) pl = bc.pcol;
   __syncthreads();
+  const float2* tw = stage_tw(sm + a.col_smem / sizeof(float2), pl, a.tabs);
   const int H = bc.H, Wc = bc.Wc, nc = it.count, kw0 = it.first;
   const int ls = bc.col_ls;
   float2* dst = (it.filter ? dhat : xhat) + it.dst;
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_setup_cols(BigArgs a, cons
   }
   fpad(sm, nc, ls, pl);
   __syncthreads();
-  fcore<false>(sm, nc, ls, pl, a.tabs);
+  fcore<false>(sm, nc, ls, pl, a.tabs, tw);
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int c = i % nc, h = i / nc;
     dst[(size_t)h * Wc + kw0 + c] = fout<false>(sm[(size_t)c * ls + h], h, pl, a.tabs);
@@ -408,7 +419,8 @@ static cudaError_t big_attr(const void* f, size_t smem) {
 cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st) {
   using namespace big;
   cudaError_t e = cudaSuccess;
-  const size_t csm = a.col_smem, rsm = a.row_smem;
+  const size_t tws = (size_t)a.tw_max * sizeof(float2);
+  const size_t csm = a.col_smem + tws, rsm = a.row_smem + tws;
   if (mode == kIter || mode == kLast) {
     if ((e = big_attr((const void*)k_big_cols<true>, csm)) != cudaSuccess) return e;
     k_big_cols<true><<<a.n_col_items, NT, csm, st>>>(a);
@@ -444,15 +456,16 @@ cudaError_t launch_big_setup(const BigArgs& a, const BigSetupItem* row_items, in
                              float2* dhat, float2* xhat, int fh, int fw, int n_classes, cudaStream_t st) {
   using namespace big;
   cudaError_t e;
-  if ((e = big_attr((const void*)k_big_setup_rows, a.row_smem)) != cudaSuccess) return e;
-  if ((e = big_attr((const void*)k_big_setup_cols, a.col_smem)) != cudaSuccess) return e;
+  const size_t tws = (size_t)a.tw_max * sizeof(float2);
+  if ((e = big_attr((const void*)k_big_setup_rows, a.row_smem + tws)) != cudaSuccess) return e;
+  if ((e = big_attr((const void*)k_big_setup_cols, a.col_smem + tws)) != cudaSuccess) return e;
   const int wmax = kBigMaxSide / 2 + 1;
   const int TA = std::min(fh, std::max(1, (int)((64 * 1024) / (wmax * sizeof(float2)))));
   const size_t fsm = (size_t)TA * wmax * sizeof(float2);
   if ((e = big_attr((const void*)k_big_filter_spectra, fsm)) != cudaSuccess) return e;
   k_big_filter_spectra<<<n_classes * a.K * a.J, NT, fsm, st>>>(a, d, dhat, fh, fw, a.K * a.J, TA);
-  if (n_rows > 0) k_big_setup_rows<<<n_rows, NT, a.row_smem, st>>>(a, row_items, d, x, dhat, xhat, fh, fw);
-  if (n_cols > 0) k_big_setup_cols<<<n_cols, NT, a.col_smem, st>>>(a, col_items, dhat, xhat);
+  if (n_rows > 0) k_big_setup_rows<<<n_rows, NT, a.row_smem + tws, st>>>(a, row_items, d, x, dhat, xhat, fh, fw);
+  if (n_cols > 0) k_big_setup_cols<<<n_cols, NT, a.col_smem + tws, st>>>(a, col_items, dhat, xhat);
   return cudaGetLastError();
 }
 
@@ -541,7 +554,7 @@ const BigPlan& plan_of(UnevenLayout& L, int n) {
 
 int odd_at_least(int n) { return n | 1; }
 
-constexpr size_t kBigLineBudget = 64 * 1024;   // shared memory per work item (bytes)
+constexpr size_t kBigLineBudget = 56 * 1024;   // shared memory of the lines of a work item (bytes)
 
 int lines_per_item(int ls, int total) {
   const int l = (int)(kBigLineBudget / ((size_t)ls * sizeof(float2)));
@@ -568,6 +581,8 @@ void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<
   (void)fh; (void)fw;
   L.bcol.clear(); L.brow.clear(); L.bfreq.clear(); setup.clear();
   L.bcol_smem = L.brow_smem = 0;
+  L.btw_max = 0;
+  for (const BigPlan& p : L.bplans) L.btw_max = std::max(L.btw_max, p.M ? p.M : p.n);
   std::vector<int> nc(L.bcls.size()), nr(L.bcls.size());
   for (size_t ci = 0; ci < L.bcls.size(); ++ci) {
     const BigCls& bc = L.bcls[ci];
