@@ -59,6 +59,84 @@ __device__ __forceinline__ void fpad(float2* buf, int nlines, int ls, const BigP
   for (int line = 0; line < nlines; ++line)
     for (int j = threadIdx.x; j < pad; j += NT) buf[(size_t)line * ls + pl.n + j] = make_float2(0.f, 0.f);
 }
+// x / d and x % d for x * d < 2^32 from m = floor((2^32 - 1) / d) + 1 (d >= 2), by one high multiply
+struct FastDiv {
+  unsigned d, m;
+  __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned x) const { return d > 1 ? __umulhi(x, m) : x; }
+};
+
+// One Stockham stage of radix R over nlines lines (line L element e at buf[L * ls + e]) in place:
+// the butterflies of whole lines per round, read into registers before any is written. The same
+// butterflies as the run-time stages of fft.cuh, with the index divisions by the round's line count
+// and by Ns done as high multiplies.
+template <int R, bool INV, int IPT>
+__device__ __noinline__ void big_stage(float2* buf, int nlines, int ls, int n, int Ns, const float2* tw) {
+  const int nb = n / R;
+  int lpr = (NT * IPT) / nb;
+  lpr = lpr < 1 ? 1 : (lpr > nlines ? nlines : lpr);
+  const int tsu = n / (Ns * R);
+  const FastDiv dns((unsigned)Ns);
+  for (int L0 = 0; L0 < nlines; L0 += lpr) {
+    const int nl = min(lpr, nlines - L0);
+    const FastDiv dnl((unsigned)nl);
+    const int items = nl * nb;
+    float2 v[IPT][R];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int i = threadIdx.x + it * NT;
+      if (i < items) {
+        const int j = (int)dnl.div((unsigned)i);
+        const int line = L0 + i - j * nl;
+        const int k = j - (int)dns.div((unsigned)j) * Ns;
+        const float2* src = buf + line * ls + j;
+        const int ts = k * tsu;
+        v[it][0] = src[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 x = src[r * nb];
+          v[it][r] = ts ? cmul(x, tw_dir<INV>(tw[r * ts])) : x;
+        }
+        dft<R, INV>(v[it], tw, n);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int i = threadIdx.x + it * NT;
+      if (i < items) {
+        const int j = (int)dnl.div((unsigned)i);
+        const int line = L0 + i - j * nl;
+        const int k = j - (int)dns.div((unsigned)j) * Ns;
+        float2* dst = buf + line * ls + (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r * Ns] = v[it][out_slot<R>(r)];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// all stages of a length-n transform (radices of the plan)
+template <bool INV>
+__device__ __noinline__ void big_stages(float2* buf, int nlines, int ls, int n, const Radices& rr, const float2* tw) {
+  int ns = 1;
+  for (int s = 0; s < rr.n_st; ++s) {
+    const int R = rr.r[s];
+    switch (R) {
+      case 2: big_stage<2, INV, 8>(buf, nlines, ls, n, ns, tw); break;
+      case 3: big_stage<3, INV, 5>(buf, nlines, ls, n, ns, tw); break;
+      case 4: big_stage<4, INV, 4>(buf, nlines, ls, n, ns, tw); break;
+      case 5: big_stage<5, INV, 3>(buf, nlines, ls, n, ns, tw); break;
+      case 7: big_stage<7, INV, 2>(buf, nlines, ls, n, ns, tw); break;
+      case 8: big_stage<8, INV, 2>(buf, nlines, ls, n, ns, tw); break;
+      case 16: big_stage<16, INV, 1>(buf, nlines, ls, n, ns, tw); break;
+      default: break;   // host planning only makes radices 2, 3, 4, 5, 7, 8, 16
+    }
+    ns *= R;
+  }
+}
+
 // the plan's twiddle table (length M, or n without Bluestein) copied to shared memory; no synchronisation
 __device__ __forceinline__ const float2* stage_tw(float2* dst, const BigPlan& pl, const float2* tabs) {
   const int L = pl.M ? pl.M : pl.n;
@@ -70,18 +148,18 @@ __device__ __forceinline__ const float2* stage_tw(float2* dst, const BigPlan& pl
 template <bool INV>
 __device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs, const float2* tw) {
   if (pl.M == 0) {
-    stages_rt<INV, NT>(buf, nlines, ls, 1, pl.n, pl.rad, tw);
+    big_stages<INV>(buf, nlines, ls, pl.n, pl.rad, tw);
     return;
   }
   const int M = pl.M;
   const float2* bh = tabs + pl.bhat;
-  stages_rt<false, NT>(buf, nlines, ls, 1, M, pl.rad, tw);
+  big_stages<false>(buf, nlines, ls, M, pl.rad, tw);
   for (int line = 0; line < nlines; ++line) {
     float2* b = buf + (size_t)line * ls;
     for (int j = threadIdx.x; j < M; j += NT) b[j] = cmul(b[j], __ldg(bh + j));
   }
   __syncthreads();
-  stages_rt<true, NT>(buf, nlines, ls, 1, M, pl.rad, tw);
+  big_stages<true>(buf, nlines, ls, M, pl.rad, tw);
 }
 
 // ---- column pass: item = (image, map, first column, columns) ------------------------------------

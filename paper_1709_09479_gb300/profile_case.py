@@ -7,7 +7,8 @@
 coding: csc_code with `iters` ADMM iterations (launch order: 2 spectra, solve setup, spectra,
 prologue sweep, then `iters` sweeps). learning: one csc_code of `iters` iterations, then csc_learn
 with `steps` learning steps. uneven: the 256-image batch of bench.py's uneven256 workload (sides uniform
-in [64, 512], K = 64; `--images` takes its first images only), one csc_code of `iters` iterations (launch order: the setup transforms and the
+in [64, 512], K = 64; `--images` takes its first images only; `--sides smooth64-128` draws the sides
+from the even 7-smooth sizes in [64, 128] instead), one csc_code of `iters` iterations (launch order: the setup transforms and the
 per-class solve setup, the autotuner's sweeps when some images fit one map per CTA, then the call's
 prologue and sweeps). Inputs are
 the seeded 1/f^2 fields and Gaussian dictionaries of bench.py.
@@ -29,13 +30,19 @@ def main():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--images", type=int, default=256, help="uneven: number of images")
+    ap.add_argument("--sides", choices=["64-512", "smooth64-128"], default="64-512",
+                    help="uneven: sides uniform in [64, 512], or drawn from the even 7-smooth sizes in [64, 128]")
     a = ap.parse_args()
     import torch
 
     from paper_1709_09479_gb300 import csc, inputs
     if a.what == "uneven":
         rng = np.random.default_rng(3)
-        sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(a.images)]
+        if a.sides == "64-512":
+            sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(a.images)]
+        else:
+            sides = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
+            sizes = [(int(rng.choice(sides)), int(rng.choice(sides))) for _ in range(a.images)]
         K = 64
         xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
         x = torch.from_numpy(xs.astype(np.float32)).cuda()
