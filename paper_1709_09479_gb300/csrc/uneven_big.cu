@@ -32,6 +32,13 @@ namespace big {
 constexpr int NT = 256;
 constexpr int kMinCtas = 3;   // resident CTAs per SM the transform kernels are compiled for
 
+// x / d and x % d for x * d < 2^32 from m = floor((2^32 - 1) / d) + 1 (d >= 2), by one high multiply
+struct FastDiv {
+  unsigned d, m;
+  __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned x) const { return d > 1 ? __umulhi(x, m) : x; }
+};
+
 __device__ __forceinline__ float bclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
 // a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
 __device__ __forceinline__ float2 bbf16(float2 v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
@@ -59,13 +66,6 @@ __device__ __forceinline__ void fpad(float2* buf, int nlines, int ls, const BigP
   for (int line = 0; line < nlines; ++line)
     for (int j = threadIdx.x; j < pad; j += NT) buf[(size_t)line * ls + pl.n + j] = make_float2(0.f, 0.f);
 }
-// x / d and x % d for x * d < 2^32 from m = floor((2^32 - 1) / d) + 1 (d >= 2), by one high multiply
-struct FastDiv {
-  unsigned d, m;
-  __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
-  __device__ __forceinline__ unsigned div(unsigned x) const { return d > 1 ? __umulhi(x, m) : x; }
-};
-
 // One Stockham stage of radix R over nlines lines (line L element e at buf[L * ls + e]) in place:
 // the butterflies of whole lines per round, read into registers before any is written. The same
 // butterflies as the run-time stages of fft.cuh, with the index divisions by the round's line count
@@ -177,12 +177,13 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   const float2* tw = stage_tw(sm + a.col_smem / sizeof(float2), pl, a.tabs);
   const int H = bc.H, Wc = bc.Wc, Om = H * Wc, nc = it.count, kw0 = it.first;
   const int ls = bc.col_ls;
+  const FastDiv fnc((unsigned)nc);
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
   if (BUILD) {
     const float2* lam = a.lam + im.lam;
     const size_t dbase = bc.dhat + (size_t)it.map * a.J * Om;
     for (int i = threadIdx.x; i < nc * H; i += NT) {
-      const int c = i % nc, h = i / nc;
+      const int h = (int)fnc.div(i), c = i - h * nc;
       const int o = h * Wc + kw0 + c;
       float2 s = make_float2(0.f, 0.f);
       for (int j = 0; j < a.J; ++j) {
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
     }
   } else {
     for (int i = threadIdx.x; i < nc * H; i += NT) {
-      const int c = i % nc, h = i / nc;
+      const int h = (int)fnc.div(i), c = i - h * nc;
       sm[(size_t)c * ls + h] = fin<false>(Y[(size_t)h * Wc + kw0 + c], h, pl, a.tabs);
     }
   }
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   __syncthreads();
   fcore<BUILD>(sm, nc, ls, pl, a.tabs, tw);
   for (int i = threadIdx.x; i < nc * H; i += NT) {
-    const int c = i % nc, h = i / nc;
+    const int h = (int)fnc.div(i), c = i - h * nc;
     Y[(size_t)h * Wc + kw0 + c] = fout<BUILD>(sm[(size_t)c * ls + h], h, pl, a.tabs);
   }
 }
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   const int H = bc.H, W = bc.W, Wc = bc.Wc, Om = H * Wc, nr = it.count, h0 = it.first;
   const int np = (nr + 1) / 2;
   const int ls = bc.row_ls;
+  const FastDiv fW((unsigned)W), fWc((unsigned)Wc);
   const size_t moff = im.v + (size_t)it.map * H * W;
   float2* Y = a.Y + im.y + (size_t)it.map * Om;
   const float beta = a.beta;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   double l1 = 0.0;
   if (MODE == kIter || MODE == kLast) {
     for (int i = threadIdx.x; i < np * W; i += NT) {
-      const int q = i / W, kw = i - q * W;
+      const int q = (int)fW.div(i), kw = i - q * W;
       const float2 xa = half_bin(Y + (size_t)(h0 + 2 * q) * Wc, kw, W, Wc);
       const float2 xb = (2 * q + 1 < nr) ? half_bin(Y + (size_t)(h0 + 2 * q + 1) * Wc, kw, W, Wc) : make_float2(0.f, 0.f);
       sm[(size_t)q * ls + kw] = fin<true>(make_float2(xa.x - xb.y, xa.y + xb.x), kw, pl, a.tabs);
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
     __syncthreads();
     fcore<true>(sm, np, ls, pl, a.tabs, tw);
     for (int i = threadIdx.x; i < np * W; i += NT) {
-      const int q = i / W, x = i - q * W;
+      const int q = (int)fW.div(i), x = i - q * W;
       const bool has_b = (q < np - 1) || pair_last;
       const float2 w = fout<true>(sm[(size_t)q * ls + x], x, pl, a.tabs);
       const size_t pa = moff + (size_t)(h0 + 2 * q) * W + x, pb = pa + W;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   } else {
     const float* src = (MODE == kPrologue) ? a.v : a.z;
     for (int i = threadIdx.x; i < np * W; i += NT) {
-      const int q = i / W, x = i - q * W;
+      const int q = (int)fW.div(i), x = i - q * W;
       const bool has_b = (q < np - 1) || pair_last;
       const size_t pa = moff + (size_t)(h0 + 2 * q) * W + x;
       float ta = src[pa], tb = has_b ? src[pa + W] : 0.f;
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
     __syncthreads();
     fcore<false>(sm, np, ls, pl, a.tabs, tw);
     for (int i = threadIdx.x; i < nr * Wc; i += NT) {
-      const int r = i / Wc, kw = i - r * Wc;
+      const int r = (int)fWc.div(i), kw = i - r * Wc;
       const float2* zq = sm + (size_t)(r >> 1) * ls;
       const int km = kw == 0 ? 0 : W - kw;
       const float2 z1 = fout<false>(zq[kw], kw, pl, a.tabs), z2 = fout<false>(zq[km], km, pl, a.tabs);
