@@ -124,12 +124,12 @@ __device__ __noinline__ void big_stages(float2* buf, int nlines, int ls, int n, 
   for (int s = 0; s < rr.n_st; ++s) {
     const int R = rr.r[s];
     switch (R) {
-      case 2: big_stage<2, INV, 8>(buf, nlines, ls, n, ns, tw); break;
-      case 3: big_stage<3, INV, 5>(buf, nlines, ls, n, ns, tw); break;
-      case 4: big_stage<4, INV, 4>(buf, nlines, ls, n, ns, tw); break;
-      case 5: big_stage<5, INV, 3>(buf, nlines, ls, n, ns, tw); break;
-      case 7: big_stage<7, INV, 2>(buf, nlines, ls, n, ns, tw); break;
-      case 8: big_stage<8, INV, 2>(buf, nlines, ls, n, ns, tw); break;
+      case 2: big_stage<2, INV, 4>(buf, nlines, ls, n, ns, tw); break;
+      case 3: big_stage<3, INV, 3>(buf, nlines, ls, n, ns, tw); break;
+      case 4: big_stage<4, INV, 2>(buf, nlines, ls, n, ns, tw); break;
+      case 5: big_stage<5, INV, 2>(buf, nlines, ls, n, ns, tw); break;
+      case 7: big_stage<7, INV, 1>(buf, nlines, ls, n, ns, tw); break;
+      case 8: big_stage<8, INV, 1>(buf, nlines, ls, n, ns, tw); break;
       case 16: big_stage<16, INV, 1>(buf, nlines, ls, n, ns, tw); break;
       default: break;   // host planning only makes radices 2, 3, 4, 5, 7, 8, 16
     }
