@@ -98,12 +98,17 @@ csc_status csc_init(const csc_params* params, int n_images, const int* dims, voi
 /*
  * Like csc_init for a batch whose images have their own sizes: dims holds n_images (H, W) pairs.
  * Arrays are the per-image arrays of csc_init concatenated in image order: x holds
- * J*H_n*W_n floats for image n, v and z hold K*H_n*W_n. Each size must satisfy csc_init's
- * conditions. Images of one size share one FFT plan, filter spectrum and per-frequency system;
- * one launch per ADMM iteration codes every image, with the maps split over the CTAs by pixel
- * count. On the first coding call the launch shape (threads per CTA, CTAs per SM) is chosen by
- * timing the candidates on this batch. Supports csc_code and csc_objective (csc_learn and the
- * reverse-mode calls return CSC_ERR_UNSUPPORTED on such a context).
+ * J*H_n*W_n floats for image n, v and z hold K*H_n*W_n. Any 8 <= H, W <= 1024 with the filter
+ * inside the image (fh <= H, fw <= W) is accepted; other sizes give CSC_ERR_SHAPE. Images of one
+ * size share one FFT plan, filter spectrum and per-frequency system. Images that satisfy
+ * csc_init's conditions are coded by one launch per ADMM iteration over all of them, with the maps
+ * split over the CTAs by pixel count; on the first coding call that launch's shape (threads per
+ * CTA, CTAs per SM) is chosen by timing the candidates on this batch. Every other image (odd W,
+ * sides with a prime factor above 7, spectra beyond one CTA's shared memory) is coded by four
+ * launches per iteration that stage each 2-D transform through device memory (Bluestein's chirp
+ * z-transform for lengths with a prime factor above 7), with a workspace of K*H_n*(W_n/2+1)
+ * complex values per image. Supports csc_code and csc_objective (csc_learn and the reverse-mode
+ * calls return CSC_ERR_UNSUPPORTED on such a context).
  */
 csc_status csc_init_uneven(const csc_params* params, int n_images, const int* dims, void* stream,
                            csc_ctx** out);

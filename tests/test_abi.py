@@ -54,3 +54,26 @@ def test_version_and_argument_errors_without_gpu(lib):
     assert e.value.status == 1
     assert lib.csc_code(None, None, None, None, None, 1) == 1
 
+
+
+def test_uneven_size_checks_without_gpu(lib):
+    """csc_init_uneven accepts any side in [8, 1024] with the filter inside (odd and prime sides
+    included: the host plans their Bluestein tables before any CUDA call) and rejects the rest with
+    CSC_ERR_SHAPE naming the size; without a GPU an accepted batch then fails with CSC_ERR_CUDA."""
+    from paper_1709_09479_gb300 import csc
+    for bad in [(2000, 64), (64, 6), (9, 4), (1025, 1025)]:
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_init_uneven(1, 2, (5, 5), [(64, 64), bad], 1.0, 1.0)
+        assert e.value.status == 2 and f"{bad[0]}x{bad[1]}" in str(e.value)
+    if not _has_gpu():
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_init_uneven(1, 2, (5, 5), [(67, 131), (64, 64), (509, 1024), (8, 9)], 1.0, 1.0)
+        assert e.value.status == 4
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
