@@ -90,3 +90,52 @@ def test_full_size_learning_solves_normal_equations(csc, workload, gpu_codes):
     assert res <= 1e-4
     # the projection: every filter ends inside the unit ball
     assert np.all(np.sqrt((d_out.reshape(K, -1) ** 2).sum(1)) <= 1 + 1e-5)
+
+
+# ---- uneven256 at full size: 256 images, H and W uniform in [64, 512] (seed 3), K = 64, 11 x 11,
+# beta = 1, rho = 0.1, in bench.py's launch configuration (CSC_FLAG_GRAPH). Images are coded
+# independently, so sampled images are checked element by element against the oracle.
+@pytest.fixture(scope="module")
+def uneven_workload():
+    from paper_1709_09479_gb300 import inputs
+    rng = np.random.default_rng(3)
+    sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(256)]
+    xs = [f32(inputs.powerlaw_field(1000 + i, 1, 1, hw)) for i, hw in enumerate(sizes)]
+    d = f32(inputs.unit_filters(30, 64, 1, (S, S)))
+    return sizes, xs, d
+
+
+def _sampled(sizes):
+    px = [h * w for h, w in sizes]
+    primes = [i for i, (h, w) in enumerate(sizes) if all(h % p for p in range(2, h)) and h > 7]
+    return sorted({int(np.argmin(px)), int(np.argmax(px)), primes[0] if primes else 1})
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_full_size_uneven256_sampled_images(csc, uneven_workload, precision):
+    import torch
+    from tests.test_gpu_precision import CODE_BF16_TOL
+    sizes, xs, d = uneven_workload
+    Ku, iters = 64, 5
+    prec = csc.CSC_FP32 if precision == "fp32" else csc.CSC_MIXED_BF16
+    x = torch.from_numpy(np.concatenate([a.reshape(-1) for a in xs])).cuda()
+    dd = torch.from_numpy(d.reshape(-1).copy()).cuda()
+    npx = sum(h * w for h, w in sizes)
+    v = torch.zeros(Ku * npx, device="cuda")
+    z = torch.empty_like(v)
+    with csc.Solver(J=1, K=Ku, fs=(S, S), dims_list=sizes, beta=BETA, rho=RHO, precision=prec,
+                    flags=csc.CSC_FLAG_GRAPH) as sv:
+        sv.code(x, dd, v, z, iters)
+        torch.cuda.synchronize()
+    offs = np.cumsum([0] + [Ku * h * w for h, w in sizes])
+    tol = REL_TOL if precision == "fp32" else CODE_BF16_TOL
+    for n in _sampled(sizes):
+        h, w = sizes[n]
+        vg = v[offs[n]:offs[n + 1]].cpu().numpy().astype(np.float64).reshape(1, Ku, h, w)
+        zg = z[offs[n]:offs[n + 1]].cpu().numpy().astype(np.float64).reshape(1, Ku, h, w)
+        vo, zo = O.code_admm(xs[n].astype(np.float64), d.astype(np.float64), BETA, RHO, iters)
+        assert rel(vg, vo) <= tol, (n, sizes[n], rel(vg, vo))
+        if np.any(zo != 0):
+            assert rel(zg, zo) <= tol, (n, sizes[n], rel(zg, zo))
+        if precision == "fp32":
+            assert maxrel(vg, vo) <= REL_TOL
