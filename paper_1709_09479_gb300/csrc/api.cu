@@ -107,7 +107,7 @@ void free_all(Ctx* c) {
   c->cap_stream = nullptr;
   void* uptrs[] = {c->U.d_cls, c->U.d_img, c->U.d_mstart, c->U.d_slot, c->U.d_bcls, c->U.d_bimg, c->U.d_bcol,
                    c->U.d_brow, c->U.d_bfreq, c->U.d_btabs, c->U.d_by, c->U.d_blam, c->U.d_be, c->U.d_bl1,
-                   c->U.d_bsetup};
+                   c->U.d_bsetup, c->U.d_bprep};
   for (void* p : uptrs)
     if (p) cudaFree(p);
   for (auto& ep : c->events) {
@@ -289,8 +289,16 @@ csc_status upload_big(Ctx* c, const std::vector<BigSetupItem>& setup) {
     if (cudaMalloc((void**)dptr, std::max<size_t>(vec.size(), 1) * sizeof(T)) != cudaSuccess) return false;
     return cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
   };
+  std::vector<PrepArgs> prep;
+  U.bprep_max_omega = 0;
+  for (const BigCls& bc : U.bcls) {
+    PrepArgs a{c->K, c->J, bc.H * bc.Wc, c->p.rho, 1.0 / ((double)bc.H * bc.W), c->dhat + bc.dhat,
+               c->pdiag + bc.pd, c->pmat + bc.pm};
+    prep.push_back(a);
+    U.bprep_max_omega = std::max(U.bprep_max_omega, a.Omega);
+  }
   if (!put(&U.d_bcls, U.bcls) || !put(&U.d_bimg, U.bimg) || !put(&U.d_bcol, U.bcol) || !put(&U.d_brow, U.brow) ||
-      !put(&U.d_bfreq, U.bfreq) || !put(&U.d_btabs, U.btabs) || !put(&U.d_bsetup, setup) ||
+      !put(&U.d_bfreq, U.bfreq) || !put(&U.d_btabs, U.btabs) || !put(&U.d_bsetup, setup) || !put(&U.d_bprep, prep) ||
       cudaMalloc((void**)&U.d_by, std::max<long long>(U.n_by, 1) * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&U.d_blam, std::max<long long>(U.n_blam, 1) * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&U.d_be, std::max<size_t>(U.bfreq.size(), 1) * sizeof(double)) != cudaSuccess ||
@@ -325,13 +333,8 @@ cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
                                      U.d_bsetup + U.n_bsetup_rows, U.n_bsetup_cols, d, x, c->dhat, c->xhat, c->fh,
                                      c->fw, (int)U.bcls.size(), c->stream);
     c->launches += 3;
-    for (int ci = 0; ci < (int)U.bcls.size() && solve && e == cudaSuccess; ++ci) {
-      const BigCls& bc = U.bcls[ci];
-      Ctx v;
-      v.p = c->p; v.K = c->K; v.J = c->J; v.stream = c->stream;
-      v.g.Omega = bc.H * bc.Wc; v.g.D = bc.H * bc.W;
-      v.dhat = c->dhat + bc.dhat; v.pdiag = c->pdiag + bc.pd; v.pmat = c->pmat + bc.pm;
-      e = launch_solve_prep(v);
+    if (solve && e == cudaSuccess) {
+      e = launch_solve_prep_batch(U.d_bprep, (int)U.bcls.size(), U.bprep_max_omega, c->nsm, c->stream);
       c->launches += 1;
     }
     if (e != cudaSuccess) return e;
@@ -871,7 +874,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
   }
   if (c->uneven && iters > 0 && !c->U.tuned) {
-    CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, true), "uneven setup");
+    if (c->U.n_small > 0) CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, true), "uneven setup");
     if ((s = uneven_autotune(c, vd)) != CSC_OK) return s;
   }
   // the launch sequence of this call

@@ -24,17 +24,7 @@ namespace csc {
 // ---------------------------------------------------------------------------------------------
 // per-frequency system (A(w) + I/rho)^{-1} / D, built in float64 (Sec. 3.2; J x J blocks, Sec. 3.3)
 // ---------------------------------------------------------------------------------------------
-struct PrepArgs {
-  int K, J, Omega;
-  double rho, invD;
-  const float2* dhat;
-  float* pdiag;
-  float2* pmat;
-};
-
-__global__ void k_solve_prep(PrepArgs a) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= a.Omega) return;
+__device__ void solve_prep_at(const PrepArgs& a, int o) {
   if (a.J == 1) {
     double s = 1.0 / a.rho;
     for (int k = 0; k < a.K; ++k) {
@@ -83,6 +73,17 @@ __global__ void k_solve_prep(PrepArgs a) {
   for (int i = 0; i < J; ++i)
     for (int j = 0; j < J; ++j)
       out[i * J + j] = make_float2((float)(re[i][J + j] * a.invD), (float)(im[i][J + j] * a.invD));
+}
+
+__global__ void k_solve_prep(PrepArgs a) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < a.Omega) solve_prep_at(a, o);
+}
+
+// several systems in one launch (the size classes of an uneven batch): system blockIdx.y
+__global__ void k_solve_prep_batch(const PrepArgs* list) {
+  const PrepArgs a = list[blockIdx.y];
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.Omega; o += gridDim.x * blockDim.x) solve_prep_at(a, o);
 }
 
 // z = rho (clamp(v) - v) for every element (zero coding iterations)
@@ -175,6 +176,15 @@ cudaError_t launch_code_spectra(const Ctx& c, const float* in, int nmaps, float2
 cudaError_t launch_solve_prep(const Ctx& c) {
   PrepArgs a{c.K, c.J, c.g.Omega, c.p.rho, 1.0 / ((double)c.g.D), c.dhat, c.pdiag, c.pmat};
   k_solve_prep<<<(c.g.Omega + 255) / 256, 256, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_prep_batch(const PrepArgs* list, int n, int max_omega, int nsm, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  // about four resident blocks per SM over all systems
+  const int gx = std::max(1, std::min((max_omega + 255) / 256, (4 * nsm + n - 1) / n));
+  for (int c0 = 0; c0 < n; c0 += 65535)   // grid y limit
+    k_solve_prep_batch<<<dim3(gx, std::min(65535, n - c0)), 256, 0, st>>>(list + c0);
   return cudaGetLastError();
 }
 

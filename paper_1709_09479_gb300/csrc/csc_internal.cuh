@@ -95,6 +95,16 @@ struct UnevenArgs {
   float* z;
   double* l1;
 };
+// the per-frequency system (A(w) + I/rho)^{-1} / D of one filter spectrum (coding.cu)
+struct PrepArgs {
+  int K, J, Omega;
+  double rho, invD;
+  const float2* dhat;
+  float* pdiag;
+  float2* pmat;
+};
+cudaError_t launch_solve_prep_batch(const PrepArgs* list, int n, int max_omega, int nsm, cudaStream_t st);
+
 // ---- uneven-batch images beyond the one-map-per-CTA sweep (uneven_big.cu) -------------------------
 struct BigPlan {          // a length-n complex DFT
   int n;
@@ -186,6 +196,8 @@ struct UnevenLayout {
   double* d_be = nullptr;
   double* d_bl1 = nullptr;
   BigSetupItem* d_bsetup = nullptr;
+  PrepArgs* d_bprep = nullptr;   // the classes' per-frequency systems, one launch
+  int bprep_max_omega = 0;
   int n_bsetup_rows = 0, n_bsetup_cols = 0;
   long long n_tw = 0, n_dhat = 0, n_pd = 0, n_pm = 0, n_x = 0, n_v = 0, n_xh = 0, n_slot = 0;
   UClass* d_cls = nullptr;

@@ -436,26 +436,34 @@ __global__ void __launch_bounds__(NT) k_big_filter_spectra(BigArgs a, const floa
   const float2* twW = a.tabs + bc.prow.twn;
   const float2* twH = a.tabs + bc.pcol.twn;
   float2* out = dhat + bc.dhat + (size_t)m * H * Wc;
+  const FastDiv fWc((unsigned)Wc);
   for (int t0 = 0; t0 < fh; t0 += TA) {
     const int tn = min(TA, fh - t0);
     __syncthreads();
     for (int i = threadIdx.x; i < tn * Wc; i += NT) {
-      const int ta = i / Wc, kw = i - ta * Wc;
+      const int ta = (int)fWc.div(i), kw = i - ta * Wc;
       float2 s = make_float2(0.f, 0.f);
+      int idx = (int)(((long long)(W - cw) * kw) % W);   // (tb - cw) kw mod W, stepped by kw
       for (int tb = 0; tb < fw; ++tb) {
-        const float2 t = twW[(int)(((long long)(tb - cw + W) * kw) % W)];
+        const float2 t = twW[idx];
         const float fv = f[(t0 + ta) * fw + tb];
         s.x = fmaf(fv, t.x, s.x);
         s.y = fmaf(fv, t.y, s.y);
+        idx += kw;
+        if (idx >= W) idx -= W;
       }
       sm[i] = s;
     }
     __syncthreads();
     for (int o = threadIdx.x; o < H * Wc; o += NT) {
-      const int h = o / Wc, kw = o - h * Wc;
+      const int h = (int)fWc.div(o), kw = o - h * Wc;
       float2 s = t0 == 0 ? make_float2(0.f, 0.f) : out[o];
-      for (int ta = 0; ta < tn; ++ta)
-        s = cfma(sm[ta * Wc + kw], twH[(int)(((long long)(t0 + ta - ch + H) * h) % H)], s);
+      int idx = (int)(((long long)(t0 - ch + H) * h) % H);   // (ta - ch) h mod H, stepped by h
+      for (int ta = 0; ta < tn; ++ta) {
+        s = cfma(sm[ta * Wc + kw], twH[idx], s);
+        idx += h;
+        if (idx >= H) idx -= H;
+      }
       out[o] = s;
     }
   }
