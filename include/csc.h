@@ -177,7 +177,8 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
  *   vbar = (1 - m) vbar' + (2m - 1) ubar,   m = 1[|v| < beta],
  *   dbar_k += G(vbar'_k, lambda) + G(u_k, rbar) - G(w_k, rbar) - G(ubar_k, lambda),
  * with G(a, b)(q) = sum_p b(p) a(p - q) on the filter support and the seed vbar^T = rho (m_T - 1) gz.
- * All arrays must be device memory. Asynchronous on the context's stream.
+ * All arrays must be device memory. Asynchronous on the context's stream. csc_tape_bytes returns 0
+ * for invalid arguments and for uneven-batch and video contexts (no reverse mode there).
  */
 size_t csc_tape_bytes(const csc_ctx* ctx, int iters, int every);
 csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters,

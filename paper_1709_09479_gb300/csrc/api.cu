@@ -655,7 +655,7 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
     delete ctx;
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: the largest image and the largest spectrum do not fit one CTA");
   }
-  if (!geos.empty()) c->g = geos[0];
+  c->g = geos.empty() ? Geometry{} : geos[0];
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
@@ -883,7 +883,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     if (iters == 0) {
       if (!zd) return cudaSuccess;
       c->launches += 1;
-      return launch_codes_from_state(*c, vd, zd);
+      return launch_codes_from_state_n(*c, vd, zd, nv);
     }
     if (c->uneven) {
       e = uneven_setup(c, dd, xd, true);
@@ -1201,7 +1201,7 @@ csc_status ensure_spec(Ctx* c) {
 }  // namespace
 
 size_t csc_tape_bytes(const csc_ctx* ctx, int iters, int every) {
-  if (!ctx || iters < 1 || every < 1) return 0;
+  if (!ctx || iters < 1 || every < 1 || ctx->c.uneven || ctx->c.video) return 0;   // no reverse mode there
   return tape_layout(ctx->c, iters, every).total;
 }
 

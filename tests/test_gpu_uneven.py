@@ -200,3 +200,23 @@ def test_uneven_bf16_contractions_against_oracle(csc, sizes):
     z16 = out[csc.CSC_MIXED_BF16][0]
     fo = sum(O.objective(xo, d, zz, beta) for xo, zz in zip(xs, z16))
     assert abs(out[csc.CSC_MIXED_BF16][1] - fo) <= 1e-5 * fo
+
+
+@pytest.mark.parametrize("sizes", [[(128, 128), (64, 64), (40, 48)], [(67, 131), (64, 64), (200, 181)]])
+def test_uneven_zero_iterations_codes_from_state(csc, sizes):
+    """csc_code with zero iterations turns the state of every image into codes, z = rho (clamp(v) - v),
+    over the whole batch and nothing beyond it."""
+    import torch
+    K, s, beta, rho = 3, 5, 0.3, 2.0
+    xs, d = batch(800, sizes, K, 1, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    v = torch.randn(n_v, device="cuda", generator=g)
+    z = torch.full((n_v + 1024,), 7.0, device="cuda")
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho) as sv:
+        sv.code(flat(xs), flat([d]), v, z[:n_v], 0)
+        torch.cuda.synchronize()
+    vn = v.cpu().numpy()
+    zn = z.cpu().numpy()
+    np.testing.assert_allclose(zn[:n_v], rho * (np.clip(vn, -beta, beta) - vn), rtol=1e-6, atol=1e-6)
+    assert np.all(zn[n_v:] == 7.0)
