@@ -1,12 +1,13 @@
-// Coding of the images of an uneven batch whose maps do not fit the one-map-per-CTA sweep: any side
-// up to 512, odd widths, and lengths with prime factors above 7 (the dual ADMM of
+// Coding of the images of an uneven batch whose maps do not fit the one-map-per-CTA sweep: sides up
+// to kBigMaxSide (1024), odd widths, and lengths with prime factors above 7 (the dual ADMM of
 // Eq. Inference_solution, the same arithmetic as uneven.cu).
 //
 // The map spectra live in HBM ([map][H][W/2+1], the half-spectrum layout of d_hat and x_hat) and each
 // 2-D transform is two batched passes of 1-D transforms through shared memory:
 //   columns (length H, complex) on the W/2+1 stored columns, and
-//   rows (length W, complex on the real row, then the first W/2+1 bins kept; the inverse first
-//   completes the row by Hermitian symmetry, X[W-k] = conj X[k]).
+//   rows (length W; two real rows as the real and imaginary parts of one complex transform, the
+//   first W/2+1 bins of each kept; the inverse first completes each row by Hermitian symmetry,
+//   X[W-k] = conj X[k]).
 // A 1-D transform of a 7-smooth length is the run-time Stockham plan of fft.cuh; any other length n
 // goes through Bluestein's chirp z-transform: with w_j = e^{-pi i j^2/n},
 //     X_k = w_k sum_j (x_j w_j) conj(w_{k-j}),
@@ -32,7 +33,7 @@ namespace big {
 constexpr int NT = 256;
 constexpr int kMinCtas = 3;   // resident CTAs per SM the transform kernels are compiled for
 
-// x / d and x % d for x * d < 2^32 from m = floor((2^32 - 1) / d) + 1 (d >= 2), by one high multiply
+// x / d for x * d < 2^32 from m = floor((2^32 - 1) / d) + 1 (d >= 2), by one high multiply
 struct FastDiv {
   unsigned d, m;
   __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
