@@ -244,7 +244,8 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
     replay), unroll32 (reverse mode through 20 unrolled iterations), video3d (higher-order coding of an
     RGB video with 3-D transforms, and one outer iteration of coding and learning), mixed128 (the benchmark step in the mixed-precision mode,
-    tensor-core Gram)."""
+    tensor-core Gram), cufft128 (cuFFT's forward and inverse transforms of the benchmark's maps, a
+    timed comparison only)."""
     from paper_1709_09479_gb300 import autograd as ag
     from paper_1709_09479_gb300 import inputs
     out = {}
@@ -401,6 +402,29 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     out["mixed128"] = {"workload": "the benchmark step in CSC_MIXED_BF16", "ms_per_step": e0.elapsed_time(e1) / 2,
                        "coding_sweep_us": tm["sweep_ms"] / max(tm["sweep_launches"], 1) * 1e3,
                        "learn_ms_per_step": tm["learn_ms"] / max(tm["learn_calls"], 1)}
+    del x, d, v, z
+
+    # --- cufft128: library transforms as a timed comparison (not on the library's path) ----------
+    # the forward and inverse 2-D real transforms of all N*K maps of powerlaw128 through cuFFT
+    # (torch.fft), i.e. the transforms alone of one coding iteration, each a pass through HBM
+    maps = torch.randn((w["N"] * w["K"], w["H"], w["W"]), device=dev)
+    for _ in range(3):
+        back = torch.fft.irfft2(torch.fft.rfft2(maps), s=(w["H"], w["W"]))
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        back = torch.fft.irfft2(torch.fft.rfft2(maps), s=(w["H"], w["W"]))
+    e1.record()
+    torch.cuda.synchronize()
+    cu_ms = e0.elapsed_time(e1) / reps
+    out["cufft128"] = {"workload": "cuFFT (torch.fft) rfft2 + irfft2 of the 10,000 maps 128x128 of powerlaw128, "
+                                   "float32; a timed comparison, not used by the library",
+                       "rfft2_plus_irfft2_us": cu_ms * 1e3,
+                       "hbm_bytes_min": 2 * (maps.numel() * 4 + w["N"] * w["K"] * w["H"] * (w["W"] // 2 + 1) * 8),
+                       "fused_sweep_us": None}
+    del maps, back
     return out
 
 
@@ -506,6 +530,9 @@ def run_ours(args):
     sv.close()
     del v, z
     ext = measure_extensions(csc, torch, dev, peaks()[0]) if (rank == 0 and not args.no_extensions) else None
+    if ext is not None and "cufft128" in ext:
+        # the fused sweep does both transforms plus the contraction, solve, shrinkage and state update
+        ext["cufft128"]["fused_sweep_us"] = sweep_avg_s * 1e6
 
     line = None
     if rank == 0:
