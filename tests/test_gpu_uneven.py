@@ -220,3 +220,23 @@ def test_uneven_zero_iterations_codes_from_state(csc, sizes):
     zn = z.cpu().numpy()
     np.testing.assert_allclose(zn[:n_v], rho * (np.clip(vn, -beta, beta) - vn), rtol=1e-6, atol=1e-6)
     assert np.all(zn[n_v:] == 7.0)
+
+
+def test_uneven_size_limits_match_oracle(csc):
+    """The largest accepted side (1024; 1021 is prime, so its rows take a 2048-point Bluestein
+    convolution) next to the smallest odd and prime ones, K = 2."""
+    import torch
+    sizes = [(1024, 1021), (8, 11), (13, 8), (9, 9)]
+    K, s, iters, beta, rho = 2, 3, 3, 0.3, 1.0
+    xs, d = batch(900, sizes, K, 1, s)
+    n_v = sum(K * H * W for H, W in sizes)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=beta, rho=rho) as sv:
+        v = torch.zeros(n_v, device="cuda")
+        z = torch.empty_like(v)
+        sv.code(flat(xs), flat([d]), v, z, iters)
+        torch.cuda.synchronize()
+        info = json.loads(sv.describe())
+    assert info["large_images"] == 4
+    for xo, vg in zip(xs, split(v, sizes, K)):
+        vo, _ = O.code_admm(xo, d, beta, rho, iters)
+        assert rel(vg, vo) <= REL_TOL and maxrel(vg, vo) <= REL_TOL
