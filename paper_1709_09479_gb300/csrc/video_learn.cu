@@ -231,7 +231,7 @@ __global__ void k_vl_time(TimeArgs a) {
 struct SpecArgs {
   const float* lags;   // [K][K][Lt][La][Lb]
   int K, Lt, La, Lb, fw, ft, fh;
-  float2* chat;        // [NF][K(K+1)/2], pairs in row order k K - k(k-1)/2 + (k' - k)
+  float2* chat;        // [NF][K][K]: [f][k'][k] = C_hat_kk'(f) (both triangles, the input filter k' major)
 };
 
 __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
@@ -271,14 +271,16 @@ __global__ void __launch_bounds__(256) k_vl_lagspec(SpecArgs a) {
     R2[e] = s;
   }
   __syncthreads();
-  const int np = a.K * (a.K + 1) / 2;
-  const long long pidx = (long long)k * a.K - (long long)k * (k - 1) / 2 + (kp - k);
+  const int K = a.K;
   const float sc = 1.0f / (float)(Lt * La * Lb);
   for (int e = threadIdx.x; e < Lt * La * fw; e += blockDim.x) {
     const int w2 = e % fw, w1 = (e / fw) % La, w0 = e / (fw * La);
     float2 s = make_float2(0.f, 0.f);
     for (int tt = 0; tt < Lt; ++tt) s = cfma(R2[(tt * La + w1) * fw + w2], tt_[imod(w0 * (tt - (a.ft - 1)), Lt)], s);
-    a.chat[(size_t)e * np + pidx] = cscale(s, sc);
+    s = cscale(s, sc);
+    float2* cf = a.chat + (size_t)e * K * K;
+    cf[(size_t)kp * K + k] = s;                                      // C_hat_kk'
+    if (kp != k) cf[(size_t)k * K + kp] = make_float2(s.x, -s.y);    // C_hat_k'k = conj C_hat_kk'
   }
 }
 
@@ -289,7 +291,7 @@ struct OpArgs {
   float2* phat;        // [K][J][NF]
   float2* yhat;        // [K][J][NF]
   float* y;            // [K][J][S3]
-  const float2* chat;  // [NF][K(K+1)/2]
+  const float2* chat;  // [NF][K][K], [f][k'][k] = C_hat_kk'(f)
   const int* done;     // all channels converged: skip
 };
 
@@ -337,25 +339,20 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
   }
 }
 
-// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f), C_hat_kk' = conj C_hat_k'k for k > k'; the lanes of a
-// warp share the bin (p_hat loads are broadcasts) and take consecutive filters
+// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f); the lanes of a warp share the bin (p_hat loads are
+// broadcasts) and take consecutive filters (C_hat loads are contiguous: [f][k'][k])
 __global__ void k_vl_prod(OpArgs a) {
   if (a.done && *a.done) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)a.NF * a.K) return;
   const int f = (int)(e / a.K), k = (int)(e - (long long)f * a.K);
-  const int K = a.K, J = a.J, np = K * (K + 1) / 2;
-  const float2* cf = a.chat + (size_t)f * np;
+  const int K = a.K, J = a.J;
+  const float2* cf = a.chat + (size_t)f * K * K + k;
   float2 acc[kMaxJ];
 #pragma unroll
   for (int j = 0; j < kMaxJ; ++j) acc[j] = make_float2(0.f, 0.f);
   for (int kp = 0; kp < K; ++kp) {
-    float2 c;
-    if (kp >= k) c = cf[(long long)k * K - (long long)k * (k - 1) / 2 + (kp - k)];
-    else {
-      const float2 t = cf[(long long)kp * K - (long long)kp * (kp - 1) / 2 + (k - kp)];
-      c = make_float2(t.x, -t.y);
-    }
+    const float2 c = cf[(size_t)kp * K];
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j)
       if (j < J) acc[j] = cfma(c, a.phat[((size_t)kp * J + j) * a.NF + f], acc[j]);
@@ -721,7 +718,7 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   A((void**)&V.rspecT, (size_t)KJ * O3 * sizeof(float2));
   A((void**)&V.U, (size_t)T * npmax * LLmax * sizeof(float2));
   A((void**)&V.lags, (size_t)K * K * Lt * La * Lb * sizeof(float));
-  A((void**)&V.chat, (size_t)NF * np * sizeof(float2));
+  A((void**)&V.chat, (size_t)NF * K * K * sizeof(float2));
   A((void**)&V.vec, 5 * nvec * sizeof(float));
   A((void**)&V.phat, (size_t)KJ * NF * sizeof(float2));
   A((void**)&V.yhat, (size_t)KJ * NF * sizeof(float2));
@@ -817,15 +814,16 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   const size_t b2t_sm = ((size_t)NF + (size_t)ft * La * fw + (size_t)ft * fh * fw + Lt + La + Lb) * sizeof(float2);
   VL_CHECK(cudaFuncSetAttribute(k_vl_t2b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2b_sm), "attribute");
   VL_CHECK(cudaFuncSetAttribute(k_vl_b2t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2t_sm), "attribute");
-  auto apply = [&](const float* pv, const int* done) -> cudaError_t {
+  auto apply_on = [&](const float* pv, const int* done, cudaStream_t s) -> cudaError_t {
     OpArgs o = oa;
     o.p = pv;
     o.done = done;
-    k_vl_t2b<<<KJ, 256, t2b_sm, st>>>(o);
-    k_vl_prod<<<(unsigned)(((long long)NF * K + 127) / 128), 128, 0, st>>>(o);
-    k_vl_b2t<<<KJ, 256, b2t_sm, st>>>(o);
+    k_vl_t2b<<<KJ, 256, t2b_sm, s>>>(o);
+    k_vl_prod<<<(unsigned)(((long long)NF * K + 127) / 128), 128, 0, s>>>(o);
+    k_vl_b2t<<<KJ, 256, b2t_sm, s>>>(o);
     return cudaGetLastError();
   };
+  auto apply = [&](const float* pv, const int* done) { return apply_on(pv, done, st); };
   VecArgs va{K, J, S3, c->p.cg_max, c->p.cg_tol * c->p.cg_tol, kMuFloor, b, xdev, r, zz, pvec, y, V.mu, V.lags,
              ((ft - 1) * La + (fh - 1)) * Lb + (fw - 1), Lt * La * Lb, V.active, V.fscal,
              reinterpret_cast<CgState*>(V.st), V.iters, 0};
@@ -836,6 +834,39 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   ia.part = V.part;
   ia.part2 = V.part + (size_t)kMaxJ * c->nsm;
   ia.beta = reinterpret_cast<float*>(V.part + (size_t)3 * kMaxJ * c->nsm);
+  // one CG iteration; none of its kernels reads the step index, so a batch of kBatch iterations is
+  // recorded once per call as a CUDA graph (on a private stream) and replayed between the host's
+  // reads of the convergence flag
+  constexpr int kBatch = 8;
+  auto iteration_on = [&](cudaStream_t s) -> cudaError_t {
+    cudaError_t e = apply_on(pvec, done_dev, s);
+    k_vl_it_pap<<<ia.G, kVecNT, 0, s>>>(ia);
+    k_vl_it_upd<<<ia.G, kVecNT, 0, s>>>(ia);
+    k_vl_it_scal<<<1, 32, 0, s>>>(ia);
+    k_vl_it_p<<<ia.G, kVecNT, 0, s>>>(ia);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+  };
+  struct GraphGuard {
+    cudaGraphExec_t g = nullptr;
+    ~GraphGuard() { if (g) cudaGraphExecDestroy(g); }
+  } guard;
+  cudaGraphExec_t& batch_graph = guard.g;
+  if (c->p.cg_max >= kBatch && steps > 0) {
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->cap_stream = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    if (c->cap_stream && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaSuccess;
+      for (int u = 0; u < kBatch && e == cudaSuccess; ++u) e = iteration_on(c->cap_stream);
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &gr);
+      if (e != cudaSuccess || e2 != cudaSuccess || !gr || cudaGraphInstantiate(&batch_graph, gr, 0) != cudaSuccess)
+        batch_graph = nullptr;
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+    }
+  }
   for (int s = 0; s < steps; ++s) {
     va.step = s;
     ia.v = va;
@@ -843,15 +874,12 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     k_vl_cg_init<<<1, kCgNT, 0, st>>>(va);
     VL_CHECK(cudaGetLastError(), "CG init");
     for (int it = 0; it < c->p.cg_max;) {
-      const int batch = std::min(8, c->p.cg_max - it);
-      for (int u = 0; u < batch; ++u) {
-        VL_CHECK(apply(pvec, done_dev), "operator");
-        k_vl_it_pap<<<ia.G, kVecNT, 0, st>>>(ia);
-        k_vl_it_upd<<<ia.G, kVecNT, 0, st>>>(ia);
-        k_vl_it_scal<<<1, 32, 0, st>>>(ia);
-        k_vl_it_p<<<ia.G, kVecNT, 0, st>>>(ia);
+      const int batch = std::min(kBatch, c->p.cg_max - it);
+      if (batch == kBatch && batch_graph) {
+        VL_CHECK(cudaGraphLaunch(batch_graph, st), "CG iterations (graph)");
+      } else {
+        for (int u = 0; u < batch; ++u) VL_CHECK(iteration_on(st), "CG iteration");
       }
-      VL_CHECK(cudaGetLastError(), "CG iteration");
       it += batch;
       int hd = 0;
       VL_CHECK(cudaMemcpyAsync(&hd, done_dev, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
