@@ -16,11 +16,13 @@
 //   4. lag spectra C_hat on the window grid (k_vl_lagspec), separable DFTs;
 //   5. preconditioned CG per learning step, the operator in the Fourier domain of the lag grid:
 //      taps -> bins (k_vl_t2b), y_hat_k = sum_k' C_hat_kk' p_hat_k' (k_vl_prod), bins -> taps
-//      (k_vl_b2t), and the vector updates with float64 dot products over all SMs (k_vl_it_*); Jacobi
+//      (k_vl_b2t; the direction update rides on k_vl_t2b and the p . Ap partials on k_vl_b2t), and the
+//      x, r, z updates with float64 dot products over all SMs (k_vl_it_upd, k_vl_it_scal); Jacobi
 //      preconditioner 1 / (C_kk(0) + 2 mu_k); then mu_k <- max(mu_k ||d_k||, floor) (k_vl_step_end),
 //      and after the last step d_k <- d_k / max(1, ||d_k||).
 // Filters whose codes are all zero keep d_k and mu_k. The host drives the CG iterations in batches
-// of 8 launches and reads the device's convergence flag between batches.
+// of 8 iterations (a CUDA graph recorded once per call) and reads the device's convergence flag
+// between batches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -293,6 +295,15 @@ struct OpArgs {
   float* y;            // [K][J][S3]
   const float2* chat;  // [NF][K][K], [f][k'][k] = C_hat_kk'(f)
   const int* done;     // all channels converged: skip
+  // inside CG iterations (null otherwise): k_vl_t2b first forms p <- beta_j p + z on its (k, j) and
+  // stores it (the direction update of the previous iteration); k_vl_b2t forms the (k, j) partial of
+  // p . Ap with Ap = y + 2 mu_k p
+  float* pw;
+  const float* zv;
+  const float* beta;   // [kMaxJ]
+  const int* active;   // [K]
+  const float* fscal;  // [2][K]: 2 mu_k, Jacobi inverse
+  double* pap;         // [K][J]
 };
 
 // p_hat(f) = sum_q p(q) e^{-2 pi i (w0 qt / Lt + w1 qa / La + w2 qb / Lb)}, separable, one block per (k, j)
@@ -310,7 +321,22 @@ __global__ void __launch_bounds__(256) k_vl_t2b(OpArgs a) {
   build_roots(ta_, La, -1.f);
   build_roots(tt_, Lt, -1.f);
   const size_t kj = blockIdx.x;
-  for (int i = threadIdx.x; i < a.S3; i += blockDim.x) P[i] = a.p[kj * a.S3 + i];
+  if (a.pw) {
+    const int j = (int)(kj % a.J);
+    const bool act = a.active[kj / a.J] != 0;
+    const float bj = a.beta[j];
+    for (int i = threadIdx.x; i < a.S3; i += blockDim.x) {
+      const size_t q = kj * a.S3 + i;
+      float pv = a.pw[q];
+      if (act) {
+        pv = fmaf(bj, pv, a.zv[q]);
+        a.pw[q] = pv;
+      }
+      P[i] = pv;
+    }
+  } else {
+    for (int i = threadIdx.x; i < a.S3; i += blockDim.x) P[i] = a.p[kj * a.S3 + i];
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < ft * fh * fw; e += blockDim.x) {
     const int w2 = e % fw, row = e / fw;
@@ -393,6 +419,10 @@ __global__ void __launch_bounds__(256) k_vl_b2t(OpArgs a) {
     Q1[e] = s;
   }
   __syncthreads();
+  double pap = 0.0;
+  const int k = (int)(kj / a.J);
+  const bool act = a.pap && a.active[k];
+  const float mu2 = a.pap ? a.fscal[k] : 0.f;
   for (int e = threadIdx.x; e < a.S3; e += blockDim.x) {
     const int qb = e % fw, row = e / fw;
     float s = 0.f;
@@ -402,6 +432,21 @@ __global__ void __launch_bounds__(256) k_vl_b2t(OpArgs a) {
       s = fmaf(w2 == 0 ? 1.f : 2.f, v.x * r.x - v.y * r.y, s);
     }
     a.y[kj * a.S3 + e] = s;
+    if (act) {
+      const float pv = a.pw[kj * a.S3 + e];
+      pap += (double)pv * (s + mu2 * pv);
+    }
+  }
+  if (a.pap) {   // block sum in a fixed order: warps, then warp totals in warp order
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) pap += __shfl_down_sync(0xffffffffu, pap, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pap;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      a.pap[kj] = t;
+    }
   }
 }
 
@@ -497,7 +542,7 @@ constexpr int kVecNT = 256;
 struct IterArgs {
   VecArgs v;
   int G;
-  double* part;    // [G][kMaxJ]: p . Ap
+  double* part;    // [K][J]: p . Ap partials of k_vl_b2t
   double* part2;   // [G][2 kMaxJ]: r . z, r . r
   float* beta;     // [kMaxJ]
 };
@@ -523,25 +568,6 @@ __device__ __forceinline__ void block_range(int n, int G, int& i0, int& i1) {
   i1 = (int)((long long)(blockIdx.x + 1) * n / G);
 }
 
-__global__ void __launch_bounds__(kVecNT) k_vl_it_pap(IterArgs a) {
-  const VecArgs& v = a.v;
-  if (v.st->done) return;
-  __shared__ double red[(kVecNT / 32) * kMaxJ];
-  const int JS = v.J * v.S3, n = v.K * JS;
-  int i0, i1;
-  block_range(n, a.G, i0, i1);
-  double pap[kMaxJ] = {};
-  for (int i = i0 + threadIdx.x; i < i1; i += kVecNT) {
-    const int k = i / JS, j = (i - k * JS) / v.S3;
-    if (!v.active[k]) continue;
-    const float apv = v.y[i] + v.fscal[k] * v.p[i];
-    pap[j] += (double)v.p[i] * apv;
-  }
-  block_sum_small<kMaxJ>(pap, red);
-  if (threadIdx.x == 0)
-    for (int j = 0; j < kMaxJ; ++j) a.part[blockIdx.x * kMaxJ + j] = pap[j];
-}
-
 __global__ void __launch_bounds__(kVecNT) k_vl_it_upd(IterArgs a) {
   const VecArgs& v = a.v;
   if (v.st->done) return;
@@ -551,7 +577,8 @@ __global__ void __launch_bounds__(kVecNT) k_vl_it_upd(IterArgs a) {
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j) {
       double t = 0.0;
-      for (int g = threadIdx.x; g < a.G; g += 32) t += a.part[g * kMaxJ + j];
+      if (j < v.J)
+        for (int k = threadIdx.x; k < v.K; k += 32) t += a.part[k * v.J + j];   // p . Ap partials [K][J]
       for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
       if (threadIdx.x == 0)
         s_alpha[j] = (j < v.J && !v.st->done_j[j] && t > 0.0) ? (float)(v.st->rz[j] / t) : 0.f;
@@ -608,19 +635,6 @@ __global__ void k_vl_it_scal(IterArgs a) {   // one warp
   }
   v.st->iters += 1;
   v.st->done = all || v.st->iters >= v.cg_max;
-}
-
-__global__ void __launch_bounds__(kVecNT) k_vl_it_p(IterArgs a) {
-  const VecArgs& v = a.v;
-  if (v.st->done) return;
-  const int JS = v.J * v.S3, n = v.K * JS;
-  int i0, i1;
-  block_range(n, a.G, i0, i1);
-  for (int i = i0 + threadIdx.x; i < i1; i += kVecNT) {
-    const int k = i / JS, j = (i - k * JS) / v.S3;
-    if (!v.active[k]) continue;
-    v.p[i] = fmaf(a.beta[j], v.p[i], v.z[i]);
-  }
 }
 
 // mu_k <- max(mu_k ||d_k||, floor) for active filters (norm over channels and taps); the step's
@@ -725,7 +739,8 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   A((void**)&V.mu, (size_t)K * sizeof(double));
   A((void**)&V.active, (size_t)K * sizeof(int));
   A((void**)&V.fscal, (size_t)2 * K * sizeof(float));
-  A((void**)&V.part, (size_t)3 * kMaxJ * c->nsm * sizeof(double) + kMaxJ * sizeof(float));
+  A((void**)&V.part, (size_t)(std::max(kMaxJ * c->nsm, KJ) + 2 * kMaxJ * c->nsm) * sizeof(double) +
+                        kMaxJ * sizeof(float));
   A((void**)&V.st, sizeof(CgState));
   A((void**)&V.x2, (size_t)N * J * O3 * sizeof(float2));
   A((void**)&V.tab, ((size_t)Wc * 32 + (size_t)H * kMaxL) * sizeof(float2));
@@ -831,20 +846,32 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   IterArgs ia;
   ia.v = va;
   ia.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nsm, (nvec + kVecNT - 1) / kVecNT));
+  const size_t part1 = (size_t)std::max(kMaxJ * c->nsm, KJ);
   ia.part = V.part;
-  ia.part2 = V.part + (size_t)kMaxJ * c->nsm;
-  ia.beta = reinterpret_cast<float*>(V.part + (size_t)3 * kMaxJ * c->nsm);
+  ia.part2 = V.part + part1;
+  ia.beta = reinterpret_cast<float*>(V.part + part1 + (size_t)2 * kMaxJ * c->nsm);
   // one CG iteration; none of its kernels reads the step index, so a batch of kBatch iterations is
   // recorded once per call as a CUDA graph (on a private stream) and replayed between the host's
   // reads of the convergence flag
   constexpr int kBatch = 8;
+  // an iteration: (p <- beta p + z, then the operator on p, with the p . Ap partials), the x, r, z
+  // updates with their partial sums, the scalars
+  OpArgs ob = oa;
+  ob.p = pvec;
+  ob.done = done_dev;
+  ob.pw = pvec;
+  ob.zv = zz;
+  ob.beta = ia.beta;
+  ob.active = V.active;
+  ob.fscal = V.fscal;
+  ob.pap = ia.part;
   auto iteration_on = [&](cudaStream_t s) -> cudaError_t {
-    cudaError_t e = apply_on(pvec, done_dev, s);
-    k_vl_it_pap<<<ia.G, kVecNT, 0, s>>>(ia);
+    k_vl_t2b<<<KJ, 256, t2b_sm, s>>>(ob);
+    k_vl_prod<<<(unsigned)(((long long)NF * K + 127) / 128), 128, 0, s>>>(ob);
+    k_vl_b2t<<<KJ, 256, b2t_sm, s>>>(ob);
     k_vl_it_upd<<<ia.G, kVecNT, 0, s>>>(ia);
     k_vl_it_scal<<<1, 32, 0, s>>>(ia);
-    k_vl_it_p<<<ia.G, kVecNT, 0, s>>>(ia);
-    return e == cudaSuccess ? cudaGetLastError() : e;
+    return cudaGetLastError();
   };
   struct GraphGuard {
     cudaGraphExec_t g = nullptr;
@@ -873,6 +900,8 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     VL_CHECK(apply(xdev, nullptr), "operator");
     k_vl_cg_init<<<1, kCgNT, 0, st>>>(va);
     VL_CHECK(cudaGetLastError(), "CG init");
+    // the first iteration's direction update p <- 0 p + z keeps the initial p = z
+    VL_CHECK(cudaMemsetAsync(ia.beta, 0, kMaxJ * sizeof(float), st), "beta reset");
     for (int it = 0; it < c->p.cg_max;) {
       const int batch = std::min(kBatch, c->p.cg_max - it);
       if (batch == kBatch && batch_graph) {
