@@ -373,15 +373,17 @@ __global__ void k_vl_prod(OpArgs a) {
   if (e >= (long long)a.NF * a.K) return;
   const int f = (int)(e / a.K), k = (int)(e - (long long)f * a.K);
   const int K = a.K, J = a.J;
-  const float2* cf = a.chat + (size_t)f * K * K + k;
+  const float2* __restrict__ cf = a.chat + (size_t)f * K * K + k;
+  const float2* __restrict__ ph = a.phat + f;
   float2 acc[kMaxJ];
 #pragma unroll
   for (int j = 0; j < kMaxJ; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll 8
   for (int kp = 0; kp < K; ++kp) {
-    const float2 c = cf[(size_t)kp * K];
+    const float2 c = __ldg(cf + (size_t)kp * K);
 #pragma unroll
     for (int j = 0; j < kMaxJ; ++j)
-      if (j < J) acc[j] = cfma(c, a.phat[((size_t)kp * J + j) * a.NF + f], acc[j]);
+      if (j < J) acc[j] = cfma(c, __ldg(ph + ((size_t)kp * J + j) * a.NF), acc[j]);
   }
 #pragma unroll
   for (int j = 0; j < kMaxJ; ++j)
