@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <new>
 #include <string>
@@ -378,11 +380,42 @@ cudaError_t uneven_sweeps(Ctx* c, float* v, float* z, int iters) {
   return e;
 }
 
+// launch shapes the autotuner picked, per (sizes, K, J, precision, device): later contexts on the
+// same batch shape reuse them without timing
+struct TuneKey {
+  std::vector<int> dims;
+  int K, J, precision, device;
+  bool operator<(const TuneKey& o) const {
+    if (K != o.K) return K < o.K;
+    if (J != o.J) return J < o.J;
+    if (precision != o.precision) return precision < o.precision;
+    if (device != o.device) return device < o.device;
+    return dims < o.dims;
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // key -> (threads per CTA, CTAs per SM)
+
 // pick threads per CTA and CTAs per SM for this batch by timing two sweeps of each candidate
 csc_status uneven_autotune(Ctx* c, float* v) {
   if (c->U.n_small == 0) {
     c->U.tuned = true;
     return CSC_OK;
+  }
+  const TuneKey key{c->U.dims, c->K, c->J, (int)c->p.precision, c->device};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+      const int G = (int)std::min<long long>((long long)c->nsm * hit->second.second, (long long)c->U.n_small * c->K);
+      uneven_partition(c, G);
+      csc_status st = upload_uneven(c);
+      if (st != CSC_OK) return st;
+      c->U.nt = hit->second.first;
+      c->U.tuned = true;
+      c->U.tune_cached = true;
+      return CSC_OK;
+    }
   }
   struct Cand { int nt, per_sm; };
   const Cand cands[] = {{512, 1}, {256, 1}, {256, 2}, {512, 2}};
@@ -426,6 +459,8 @@ csc_status uneven_autotune(Ctx* c, float* v) {
   if (st != CSC_OK) return st;
   c->U.nt = pick.nt;
   c->U.tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = {pick.nt, pick.per_sm};
   return CSC_OK;
 }
 
@@ -576,6 +611,7 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
     return st;
   };
   UnevenLayout& U = c->U;
+  U.dims.assign(dims, dims + 2 * (size_t)n_images);
   std::vector<Geometry> geos;
   std::vector<float2> tw;
   const double pi2 = 6.283185307179586476925286766559;
@@ -827,11 +863,13 @@ csc_status csc_describe(const csc_ctx* ctx, char* buf, int len) {
   std::snprintf(buf, (size_t)len,
                 "{\"N\": %d, \"K\": %d, \"J\": %d, \"uneven\": %s, \"size_classes\": %d, "
                 "\"large_size_classes\": %d, \"large_images\": %d, \"ctas\": %d, "
-                "\"threads_per_cta\": %d, \"autotuned\": %s, \"graph\": %s, \"graph_recorded\": %s, "
+                "\"threads_per_cta\": %d, \"autotuned\": %s, \"autotune_cached\": %s, \"graph\": %s, "
+                "\"graph_recorded\": %s, "
                 "\"video\": %s, \"T\": %d, \"ft\": %d}",
                 c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, n_big, c.uneven ? (int)c.U.bimg.size() : 0, c.G,
                 c.uneven ? c.U.nt : (int)kNTSweep,
-                (c.uneven && c.U.tuned) ? "true" : "false", (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
+                (c.uneven && c.U.tuned) ? "true" : "false", (c.uneven && c.U.tune_cached) ? "true" : "false",
+                (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
                 c.graph ? "true" : "false", c.video ? "true" : "false", c.T, c.ft);
   return CSC_OK;
 }

@@ -206,6 +206,8 @@ struct UnevenLayout {
   long long* d_slot = nullptr;
   int nt = 512;             // threads per CTA of the sweep (autotuned)
   bool tuned = false;
+  bool tune_cached = false;  // the launch shape came from an earlier batch with the same key
+  std::vector<int> dims;    // (H, W) per image in user order: the autotuner cache key with K, J, precision
 };
 size_t uneven_smem_bytes(const UnevenLayout& L, int J, int mode);
 cudaError_t launch_sweep_uneven(const UnevenArgs& a, int mode, int G, int nt, size_t smem, cudaStream_t st);

@@ -240,3 +240,24 @@ def test_uneven_size_limits_match_oracle(csc):
     for xo, vg in zip(xs, split(v, sizes, K)):
         vo, _ = O.code_admm(xo, d, beta, rho, iters)
         assert rel(vg, vo) <= REL_TOL and maxrel(vg, vo) <= REL_TOL
+
+
+def test_uneven_autotune_cache(csc):
+    """A second context on the same batch shape (sizes, K, J, precision) takes the launch shape the
+    first one timed, without timing, and computes the same state."""
+    import torch
+    K, s, beta, rho = 7, 5, 0.3, 1.0
+    xs, d = batch(950, SIZES, K, 1, s)
+    n_v = sum(K * H * W for H, W in SIZES)
+    out = []
+    for _ in range(2):
+        with csc.Solver(J=1, K=K, fs=(s, s), dims_list=SIZES, beta=beta, rho=rho) as sv:
+            v = torch.zeros(n_v, device="cuda")
+            z = torch.empty_like(v)
+            sv.code(flat(xs), flat([d]), v, z, 3)
+            torch.cuda.synchronize()
+            out.append((json.loads(sv.describe()), v.cpu().numpy()))
+    (da, va), (db, vb) = out
+    assert db["autotuned"] and db["autotune_cached"]
+    assert (db["threads_per_cta"], db["ctas"]) == (da["threads_per_cta"], da["ctas"])
+    np.testing.assert_array_equal(vb, va)
