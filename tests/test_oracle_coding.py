@@ -95,3 +95,30 @@ def test_planted_sign_error_in_multiplier_is_caught(monkeypatch):
     v, z = O.code_admm(x, d, 0.4, 1.7, 5)
     bad = 1.7 * (v - real_clip(v, -0.4, 0.4))
     assert np.max(np.abs(bad - zt)) > 1e-3
+
+
+def test_coding_is_separable_per_image_and_odd_sizes_are_exact_dfts():
+    """The coding of a batch is the coding of each image alone (Eq. Inference_solution couples only
+    the K maps of one image): the sampled-image parity checks at full size rest on this. On an odd,
+    prime-sized grid the oracle's transforms are exact H x W DFTs: its data term equals the spatial
+    circular convolution computed tap by tap."""
+    x, d = tiny(77, dims=(13, 11), K=3, N=3)
+    beta, rho = 0.3, 1.3
+    v, z = O.code_admm(x, d, beta, rho, 4)
+    for n in range(3):
+        vn, zn = O.code_admm(x[n:n + 1], d, beta, rho, 4)
+        np.testing.assert_allclose(v[n:n + 1], vn, atol=1e-13)
+        np.testing.assert_allclose(z[n:n + 1], zn, atol=1e-13)
+    # spatial check of the objective's data term on the prime-sized grid
+    K, J, s = d.shape[0], d.shape[1], d.shape[-1]
+    c = (s - 1) // 2
+    H, W = x.shape[-2:]
+    rec = np.zeros_like(x)
+    for k in range(K):
+        for j in range(J):
+            for ta in range(s):
+                for tb in range(s):
+                    rec[:, j] += d[k, j, ta, tb] * np.roll(z[:, k], (ta - c, tb - c), axis=(-2, -1))
+    data = 0.5 * ((rec - x) ** 2).sum()
+    reg = beta * np.abs(z).sum()
+    assert abs(O.objective(x, d, z, beta) - (data + reg)) <= 1e-10 * (data + reg)
