@@ -18,6 +18,8 @@ Printed JSON line (rank 0):
   cpu_baseline  the float64 oracle timed on this host's cores on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --case coding|learning|uneven|video [--N --K --H --W --s --iters --learn-steps
+                  --images --sides]      (one short run of a kernel family: the ncu target)
 """
 from __future__ import annotations
 
@@ -138,9 +140,25 @@ def make_inputs(w):
 # ------------------------------------------------------------------------------------------------
 # reference arm: the float64 oracle on the host cores
 # ------------------------------------------------------------------------------------------------
-def oracle_coding_rate(w, budget_s=12.0):
-    """Coding ADMM iterations/s of the float64 oracle for the whole batch, from a bounded sample of
-    images (coding is separable per image, Sec. 3.1). Returns (rate, sample description, seconds)."""
+def oracle_learning_step(w):
+    """Seconds per image of one oracle learning step (the paper's gamma route, CG to 1e-12) on one
+    image of the workload, with codes from n_code oracle coding iterations; and its CG iterations."""
+    from oracle import csc_oracle as O
+    x, d = make_inputs(w)
+    x64, d64 = x[:1].astype(np.float64), d.astype(np.float64)
+    _, z = O.code_admm(x64, d64, w["beta"], w["rho"], w["n_code"])
+    t0 = time.perf_counter()
+    _, _, _, its = O.learn_paper(x64, z, d64, np.full(w["K"], 0.5), np.zeros_like(x64), 1)
+    return time.perf_counter() - t0, its[0]
+
+
+def oracle_step_rate(w, budget_s=12.0, learn=None):
+    """Coding ADMM iterations/s of the float64 oracle over whole benchmark steps (n_code coding
+    iterations + n_learn learning steps on all N images), from a bounded sample: coding iterations on
+    a few images (coding is separable per image, Sec. 3.1) and one learning step on one image
+    (``learn`` = oracle_learning_step(w), measured once by the caller); both scaled to N images (the
+    oracle's coding and its CG products cost in proportion to the images).
+    Returns (rate, sample description, seconds of oracle coding work)."""
     from oracle import csc_oracle as O
     x, d = make_inputs(w)
     x64, d64 = x.astype(np.float64), d.astype(np.float64)
@@ -152,10 +170,15 @@ def oracle_coding_rate(w, budget_s=12.0):
     t0 = time.perf_counter()
     O.code_admm(x64[:n_img], d64, w["beta"], w["rho"], iters)
     dt = time.perf_counter() - t0
-    per_img_iter = dt / (n_img * iters)
-    rate = 1.0 / (per_img_iter * w["N"])
-    sample = (f"{iters} coding ADMM iterations on {n_img} of the {w['N']} images ({dt:.1f} s), scaled to the "
-              f"batch; learning not included (the oracle's learning on the full batch does not fit a bounded sample)")
+    t_code = dt / (n_img * iters)          # per image and iteration
+    t_learn, its = learn
+    step_s = w["N"] * (w["n_code"] * t_code + w["n_learn"] * t_learn)
+    rate = w["n_code"] / step_s
+    share = w["n_learn"] * t_learn / (w["n_code"] * t_code + w["n_learn"] * t_learn)
+    sample = (f"{iters} coding iterations on {n_img} of the {w['N']} images ({dt:.1f} s) and one learning step "
+              f"on one image ({t_learn:.1f} s, {its} CG iterations), scaled to a whole step of {w['n_code']} "
+              f"coding iterations + {w['n_learn']} learning steps on {w['N']} images (learning {share * 100:.1f}% "
+              f"of it)")
     return rate, sample, dt
 
 
@@ -168,10 +191,11 @@ def run_reference(args):
     cores = os.cpu_count()
     rates = []
     samples = []
+    learn = oracle_learning_step(w)          # measured once, part of the warm-up
     for _ in range(args.warmup):
-        oracle_coding_rate(w, budget_s=3.0)
+        oracle_step_rate(w, budget_s=1.0, learn=learn)
     for _ in range(args.steps):
-        r, smp, _ = oracle_coding_rate(w, budget_s=6.0)
+        r, smp, _ = oracle_step_rate(w, budget_s=3.0, learn=learn)
         rates.append(r)
         samples.append(smp)
     value = float(np.median(rates))
@@ -188,10 +212,14 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def time_to_target(csc, torch, dev, precision=None, graph=False):
+def time_to_target(csc, torch, dev, schedule="fp32", graph=False, repeats=5):
     """Rounds of Algorithm 1 on the 10-image sparse workload until the objective is within 1e-4
-    relative of the float64 oracle's final objective; then the wall time of that many rounds
-    (precision: CSC_FP32 or CSC_MIXED_BF16; graph: CUDA-graph replay of the coding calls)."""
+    relative of the float64 oracle's final objective; then the wall time of that many rounds, best
+    and spread over `repeats` timed runs.
+    schedule: "fp32" (CSC_FP32 throughout), "bf16" (CSC_MIXED_BF16 throughout) or "bf16>fp32"
+    (CSC_MIXED_BF16 in the first half of the rounds, CSC_FP32 after: a precision schedule, the
+    bf16 rounds' error floor removed by the float32 rounds); graph: CUDA-graph replay of the coding
+    calls."""
     ref_path = os.path.join(ROOT, "tests", "golden", "sparse10_oracle.json")
     if not os.path.exists(ref_path):
         return None
@@ -203,10 +231,15 @@ def time_to_target(csc, torch, dev, precision=None, graph=False):
                                    density=c["density"], noise=c["noise"])
     x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
     d0 = torch.from_numpy(inputs.unit_filters(c["dict_seed"], c["K"], 1, (c["s"], c["s"])).astype(np.float32)).to(dev)
-    sv = csc.Solver(J=1, K=c["K"], fs=(c["s"], c["s"]), dims=(c["H"], c["W"]), n_images=c["N"], beta=c["beta"],
-                    rho=c["rho"], cg_max=400, cg_tol=1e-6,
-                    precision=csc.CSC_FP32 if precision is None else precision,
-                    flags=csc.CSC_FLAG_GRAPH if graph else 0)
+
+    def solver(prec):
+        return csc.Solver(J=1, K=c["K"], fs=(c["s"], c["s"]), dims=(c["H"], c["W"]), n_images=c["N"],
+                          beta=c["beta"], rho=c["rho"], cg_max=400, cg_tol=1e-6, precision=prec,
+                          flags=csc.CSC_FLAG_GRAPH if graph else 0)
+
+    sv_fp = solver(csc.CSC_FP32) if schedule != "bf16" else None
+    sv_bf = solver(csc.CSC_MIXED_BF16) if schedule != "fp32" else None
+    n_bf = {"fp32": 0, "bf16": c["n_outer"], "bf16>fp32": c["n_outer"] // 2}[schedule]
 
     def rounds(n, log):
         d = d0.clone()
@@ -214,7 +247,8 @@ def time_to_target(csc, torch, dev, precision=None, graph=False):
         z = torch.empty_like(v)
         mu = torch.full((c["K"],), 0.5, dtype=torch.float64, device=dev)
         fs = []
-        for _ in range(n):
+        for r in range(n):
+            sv = sv_bf if r < n_bf else sv_fp
             sv.code(x, d, v, z, c["n_code"])
             sv.learn(x, z, d, mu, c["n_learn"])
             if log:
@@ -223,19 +257,26 @@ def time_to_target(csc, torch, dev, precision=None, graph=False):
 
     fs = rounds(c["n_outer"], True)
     hit = next((i for i, f in enumerate(fs) if abs(f - fstar) <= 1e-4 * abs(fstar)), None)
-    out = {"workload": "sparse10: N=10 grey 100x100, K=16 filters 11x11, beta=1, rho=10, 20 coding + 20 "
-                       "learning per round", "f_star_oracle": fstar, "f_gpu_final": fs[-1],
-           "rel_gap_final": abs(fs[-1] - fstar) / abs(fstar), "rounds": None, "seconds": None}
+    out = {"schedule": schedule, "graph": graph, "f_star_oracle": fstar, "f_gpu_final": fs[-1],
+           "rel_gap_final": abs(fs[-1] - fstar) / abs(fstar), "rel_gap_per_round": [abs(f - fstar) / abs(fstar) for f in fs],
+           "rounds": None, "seconds": None}
     if hit is not None:
         rounds(hit + 1, False)     # warm
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rounds(hit + 1, False)
-        torch.cuda.synchronize()
+        ts = []
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rounds(hit + 1, False)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
         out["rounds"] = hit + 1
-        out["seconds"] = time.perf_counter() - t0
-        out["oracle_seconds_same_rounds"] = sum(1 for _ in range(hit + 1)) * ref["oracle_seconds"] / c["n_outer"]
-    sv.close()
+        out["seconds"] = min(ts)
+        out["seconds_median"] = float(np.median(ts))
+        out["seconds_spread"] = [min(ts), max(ts)]
+        out["oracle_seconds_same_rounds"] = (hit + 1) * ref["oracle_seconds"] / c["n_outer"]
+    for sv in (sv_fp, sv_bf):
+        if sv is not None:
+            sv.close()
     return out
 
 
@@ -471,7 +512,9 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     sv.timing_read()
-    sv.timing_enable(True)
+    sv.timing_enable(False)
+
+    # the headline: K steps with no instrumentation (value)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -486,29 +529,51 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    tm = sv.timing_read()
-    sv.timing_enable(False)
+    launches = sv.timing_read()["kernel_launches"]
     if dist:
         ms = max_over_ranks(ms, dist, dev)
     iters_total = w["n_code"] * args.steps * world
     value = iters_total / (ms / 1e3)
 
-    # end to end: images from pinned host memory each step, learned filters read back
-    x_host = torch.from_numpy(x_np).pin_memory()
-    d_host = torch.empty(d.shape, dtype=torch.float32).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
-        x.copy_(x_host, non_blocking=True)
+    # the same K steps again with every coding sweep and learning call bracketed by CUDA events on
+    # the library's stream (the roofline's per-launch duration and the breakdown)
+    sv.timing_enable(True)
+    torch.cuda.synchronize()
+    ei0, ei1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ei0.record(stream)
+    for _ in range(args.steps):
         step()
-        d_host.copy_(d, non_blocking=True)
+    ei1.record(stream)
+    torch.cuda.synchronize()
+    ms_instr = ei0.elapsed_time(ei1)
+    tm = sv.timing_read()
+    sv.timing_enable(False)
+
+    # end to end through the public API with host arrays: the images (pinned host memory), the
+    # filters and the multipliers go straight into csc_code / csc_learn, which stage them to the
+    # device and write the learned filters and multipliers back; the ADMM state and the codes stay on
+    # the device. Host copies per step: x twice (coding and learning), d twice, mu once in and out.
+    x_host = torch.from_numpy(x_np).pin_memory()
+    d_host = torch.from_numpy(d.cpu().numpy()).pin_memory()
+    mu_host = torch.from_numpy(mu.cpu().numpy()).pin_memory()
+
+    def step_host():
+        sv.code(x_host, d_host, v, z, w["n_code"])
+        sv.learn(x_host, z, d_host, mu_host, w["n_learn"])
+
+    for _ in range(max(1, args.warmup // 2)):
+        step_host()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        x.copy_(x_host, non_blocking=True)
-        step()
-        d_host.copy_(d, non_blocking=True)
-        torch.cuda.synchronize()
+        step_host()
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    if dist:
+        e2e_s = max_over_ranks(e2e_s, dist, None if dist.get_backend() == "gloo" else dev)
     e2e_value = w["n_code"] * args.steps * world / e2e_s
+    h2d = 2 * x_np.nbytes + 2 * d_np.nbytes + mu_host.numel() * 8
+    d2h = d_np.nbytes + mu_host.numel() * 8
 
     # roofline of the coding sweep
     Omega = H * (W // 2 + 1)
@@ -518,15 +583,19 @@ def run_ours(args):
     achieved = alg_bytes / sweep_avg_s / 1e9
     traffic = profiled_traffic()
 
-    ttt = time_to_target(csc, torch, dev) if rank == 0 else None
-    if ttt is not None:
-        # the mixed-precision form (bf16 contractions, tensor-core Gram, CUDA-graph replay of coding)
-        mixed = time_to_target(csc, torch, dev, precision=csc.CSC_MIXED_BF16, graph=True)
-        ttt["mixed_graph"] = {k: mixed[k] for k in ("f_gpu_final", "rel_gap_final", "rounds", "seconds")}
-        # float32 with CUDA-graph replay of the coding calls (the float32 Gram already runs on the
-        # tensor cores as 3xTF32)
-        fg = time_to_target(csc, torch, dev, graph=True)
-        ttt["fp32_graph"] = {k: fg[k] for k in ("f_gpu_final", "rel_gap_final", "rounds", "seconds")}
+    ttt = None
+    if rank == 0:
+        forms = [("fp32", False), ("fp32", True), ("bf16", True), ("bf16>fp32", True)]
+        runs = {f"{sch}{'_graph' if g else ''}": time_to_target(csc, torch, dev, schedule=sch, graph=g)
+                for sch, g in forms}
+        if runs["fp32"] is not None:
+            ttt = {"workload": "sparse10: N=10 grey 100x100, K=16 filters 11x11, beta=1, rho=10, 20 coding + 20 "
+                               "learning per round; best and [min, max] of 5 timed runs", "forms": runs}
+            base = runs["fp32"]["seconds"]
+            done = {k: r["seconds"] for k, r in runs.items() if r["seconds"] is not None}
+            best = min(done, key=done.get) if done else None
+            ttt["fastest_form"] = best
+            ttt["fastest_vs_plain_fp32"] = (base / done[best]) if (best and base) else None
     sv.close()
     del v, z
     ext = measure_extensions(csc, torch, dev, peaks()[0]) if (rank == 0 and not args.no_extensions) else None
@@ -536,7 +605,7 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        cpu_rate, cpu_sample, _ = oracle_coding_rate(w)
+        cpu_rate, cpu_sample, _ = oracle_step_rate(w, budget_s=3.0, learn=oracle_learning_step(w))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -545,14 +614,19 @@ def run_ours(args):
                        "rho": w["rho"], "n_code": w["n_code"], "n_learn": w["n_learn"],
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "ADMM state 655 MB > 129 MB L2, no flush needed"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
-                    "d2h_bytes_per_step": int(d_np.nbytes)},
-            "gpu_launches": int(tm["kernel_launches"]),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h),
+                    "how": "csc_code/csc_learn called with pinned host x, d, mu (library staging timed); "
+                           "state and codes on the device; wall clock"},
+            "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": "k_sweep_f128<iterate>", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
-                         "avg_launch_us": sweep_avg_s * 1e6, "launches": tm["sweep_launches"]},
-            "breakdown": {"coding_sweep_ms_per_step": tm["sweep_ms"] / args.steps,
+                         "avg_launch_us": sweep_avg_s * 1e6, "launches": tm["sweep_launches"],
+                         "timed_region": "a second, instrumented pass of the same steps (events around every "
+                                         "sweep on the library's stream)"},
+            "breakdown": {"instrumented_ms_per_step": ms_instr / args.steps,
+                          "coding_sweep_ms_per_step": tm["sweep_ms"] / args.steps,
                           "learn_ms_per_step": tm["learn_ms"] / args.steps,
                           "coding_only_iters_per_s": 1e3 / (tm["sweep_ms"] / max(tm["sweep_launches"], 1))},
             "time_to_1e-4": ttt,
@@ -568,6 +642,68 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """A short run of one hot-path kernel family on a fixed workload, the target of the ncu captures
+    summarised under profiles/ (no timing, no JSON line):
+      coding:   csc_code with --iters ADMM iterations on --N images --H x --W, --K filters --s x --s
+                (launch order: 2 spectra, solve setup, spectra, prologue sweep, then --iters sweeps);
+      learning: the same csc_code, then csc_learn with --learn-steps learning steps;
+      uneven:   the 256-image batch of the uneven256 extension (sides uniform in [64, 512], K = 64;
+                --images takes its first images; --sides smooth64-128 draws the sides from the even
+                7-smooth sizes in [64, 128]), one csc_code of --iters iterations;
+      video:    the video3d extension (3 x 32 x 128^2, K = 64 colour filters 5 x 11 x 11), one csc_code
+                of --iters iterations, then csc_learn with --learn-steps steps.
+    Inputs are the seeded 1/f^2 fields and Gaussian dictionaries of the benchmark."""
+    import torch
+    from paper_1709_09479_gb300 import csc, inputs
+    a = args
+    if a.case == "video":
+        J, T, K, ft = 3, 32, 64, 5
+        x = torch.from_numpy(inputs.powerlaw_field(4, 1, J, (T, 128, 128)).astype(np.float32)).cuda()
+        d = torch.from_numpy(inputs.unit_filters(40, K, J, (ft, a.s, a.s)).astype(np.float32)).cuda()
+        v = torch.zeros((1, K, T, 128, 128), device="cuda")
+        z = torch.empty_like(v)
+        mu = torch.full((K,), 0.5, dtype=torch.float64, device="cuda")
+        with csc.Solver(J=J, K=K, fs=(a.s, a.s), ft=ft, dims=(T, 128, 128), n_images=1, beta=0.5, rho=0.1,
+                        cg_max=100, cg_tol=1e-6) as sv:
+            sv.code(x, d, v, z, a.iters)
+            its = sv.learn(x, z, d, mu, a.learn_steps)
+        torch.cuda.synchronize()
+        print("ok", float(v.abs().sum()), list(its))
+        return 0
+    if a.case == "uneven":
+        rng = np.random.default_rng(3)
+        if a.sides == "64-512":
+            sizes = [(int(rng.integers(64, 513)), int(rng.integers(64, 513))) for _ in range(a.images)]
+        else:
+            sides = [64, 70, 72, 80, 84, 90, 96, 98, 100, 108, 112, 120, 126, 128]
+            sizes = [(int(rng.choice(sides)), int(rng.choice(sides))) for _ in range(a.images)]
+        K = 64
+        xs = np.concatenate([inputs.powerlaw_field(1000 + i, 1, 1, hw).reshape(-1) for i, hw in enumerate(sizes)])
+        x = torch.from_numpy(xs.astype(np.float32)).cuda()
+        d = torch.from_numpy(inputs.unit_filters(30, K, 1, (a.s, a.s)).astype(np.float32)).cuda()
+        npx = sum(H * W for H, W in sizes)
+        v = torch.zeros(K * npx, device="cuda")
+        z = torch.empty_like(v)
+        with csc.Solver(J=1, K=K, fs=(a.s, a.s), dims_list=sizes, beta=1.0, rho=0.1) as sv:
+            sv.code(x, d, v, z, a.iters)
+        torch.cuda.synchronize()
+        print("ok", float(v.abs().sum()))
+        return 0
+    x = torch.from_numpy(inputs.powerlaw_field(2, a.N, 1, (a.H, a.W)).astype(np.float32)).cuda()
+    d = torch.from_numpy(inputs.unit_filters(21, a.K, 1, (a.s, a.s)).astype(np.float32)).cuda()
+    v = torch.zeros((a.N, a.K, a.H, a.W), device="cuda")
+    z = torch.empty_like(v)
+    with csc.Solver(J=1, K=a.K, fs=(a.s, a.s), dims=(a.H, a.W), n_images=a.N, beta=1.0, rho=0.1) as sv:
+        sv.code(x, d, v, z, a.iters)
+        if a.case == "learning":
+            mu = torch.full((a.K,), 0.5, dtype=torch.float64, device="cuda")
+            sv.learn(x, z, d, mu, a.learn_steps)
+    torch.cuda.synchronize()
+    print("ok", float(v.abs().sum()))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,7 +711,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extensions", action="store_true", help="skip the extension workloads")
+    ap.add_argument("--case", choices=["coding", "learning", "uneven", "video"],
+                    help="run one kernel family once on a fixed workload (an ncu target) instead of the benchmark")
+    ap.add_argument("--N", type=int, default=100)
+    ap.add_argument("--K", type=int, default=100)
+    ap.add_argument("--H", type=int, default=128)
+    ap.add_argument("--W", type=int, default=128)
+    ap.add_argument("--s", type=int, default=11)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--learn-steps", type=int, default=2)
+    ap.add_argument("--images", type=int, default=256, help="uneven case: number of images")
+    ap.add_argument("--sides", choices=["64-512", "smooth64-128"], default="64-512")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

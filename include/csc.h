@@ -46,8 +46,8 @@ typedef enum {
   CSC_ERR_SHAPE = 2,         /* size outside what the kernels support */
   CSC_ERR_WORKSPACE = 3,     /* device allocation failed */
   CSC_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
-  CSC_ERR_NONFINITE = 5,     /* a non-finite value appeared */
-  CSC_ERR_NOT_CONVERGED = 6, /* reserved */
+  CSC_ERR_NONFINITE = 5,     /* a non-finite value appeared (device flag, see CSC_FLAG_CHECK_FINITE) */
+  CSC_ERR_NOT_CONVERGED = 6, /* csc_learn with CSC_FLAG_CG_STRICT: a CG solve stopped at cg_max */
   CSC_ERR_TIMEOUT = 7,       /* a bounded grid barrier gave up; results unspecified */
   CSC_ERR_UNSUPPORTED = 8    /* valid request the library does not implement */
 } csc_status;
@@ -77,16 +77,32 @@ typedef struct {
   double cg_tol;  /* CG stop: ||r|| <= cg_tol ||b|| (relative residual), > 0 */
   int precision;  /* csc_precision */
   int flags;      /* CSC_FLAG_* bits */
+  int deterministic; /* 1: every reduction runs in a fixed order, so a call repeated on the same inputs
+                        gives the same bits (partial sums per CTA slot added in slot order, float64 CG
+                        dot products, no atomics on data). This build has no other mode: 0 is accepted
+                        and gives the same bits. */
 } csc_params;
 
 /* csc_code records its launch sequence in a CUDA graph the first time it is called with a given
    (x, d, v, z, iters) on device memory, and replays the graph on later calls with the same
    arguments (the arrays' contents may change between calls; their addresses may not). */
 #define CSC_FLAG_GRAPH 1
+/* csc_code synchronises the stream at its end and returns CSC_ERR_NONFINITE when a sweep met a
+   non-finite dual variable lambda_hat (any NaN or Inf in x, d or v reaches it within one
+   iteration). Calls with host arrays always check; without the flag a device-array call stays
+   asynchronous and csc_check reports the flag later. Uniform 2-D batches only (uneven and video
+   contexts do not raise it). */
+#define CSC_FLAG_CHECK_FINITE 2
+/* csc_learn returns CSC_ERR_NOT_CONVERGED (after writing d, mu and cg_iters) when a step's CG stopped
+   at params->cg_max iterations; without the flag that case returns CSC_OK and shows in cg_iters. */
+#define CSC_FLAG_CG_STRICT 4
 
 /*
  * Create a context for n_images images, all of size H x W (dims = {H, W}), on the current CUDA
- * device, launching on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * device, launching on `stream` (a cudaStream_t; NULL = legacy default stream). The context holds
+ * one instance of the problem of Eq. 1 (N images sharing K filters; J channels per image sharing
+ * one code per filter, the higher-order form of Sec. 3.3) with the parameters beta and rho of
+ * Eq. 1 and Eq. Inference_solution.
  * Supported sizes: W even; H, W >= 8; H and W/2 factoring into 2, 3, 5 and 7; one map plus 2*J
  * half spectra in a CTA's shared memory: 8 * (H*P + 2*J*H*(W/2+1) + W + H + 1) <= 232448 bytes,
  * P = W/2+1 rounded up to odd (128 x 128 fits at J = 1). Filter width fw <= 15.
@@ -215,24 +231,43 @@ csc_status csc_timing_enable(csc_ctx* ctx, int enable);
 csc_status csc_timing_read(csc_ctx* ctx, csc_timing* out);
 
 /*
- * csc_code without a context and without allocating: the paper has no counterpart; this exists for
- * callers that cannot allocate device memory where they code images (code running while a CUDA
- * graph is being captured, code inside a framework whose allocator owns the whole device pool, or
- * plugins that are only handed a stream and device pointers).
+ * csc_code without a context and without allocating. The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory where they code images - code inside a framework whose
+ * caching allocator owns the whole device pool, plugins that are handed only a stream and device
+ * pointers, and latency-bound paths that cannot take the implicit synchronisation of cudaMalloc.
  * Same computation, arguments and layouts as csc_init(params, n_images, dims, stream) followed by
- * csc_code(x, d, v, z, iters), except that x, d, v and z must be device pointers. The workspace is
- * a fixed 64 MiB file-scope __device__ array that every GPU loading the library holds until the
- * process exits; problems needing more return CSC_ERR_SHAPE with the byte count in
- * csc_last_error(NULL) (e.g. N = 100, K = 100, 128 x 128 needs about 47 MB and fits).
- * No cudaMalloc, cudaFree or other allocating call is made. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture. Every call shares the one array and leaves its contents behind (each call
- * rewrites everything it reads), so calls that may overlap on the GPU (different streams or
- * devices sharing nothing else) race: serialise them on one stream. Asynchronous on `stream`.
- * Errors are reported through the return value and csc_last_error(NULL).
+ * csc_code(x, d, v, z, iters), except that x, d, v and z must be device pointers, only CSC_FP32 is
+ * accepted, and every geometry (128 x 128 included) runs the generic fused sweep, about 2.8x slower
+ * than the 128 x 128 sweep csc_code takes (that one needs a second, thread-ordered copy of the filter
+ * spectra). The workspace is a fixed 64 MiB file-scope __device__ array that every GPU loading the
+ * library holds until the process exits; problems needing more return CSC_ERR_SHAPE with the byte
+ * count in csc_last_error(NULL) (e.g. N = 100, K = 100, 128 x 128 needs about 47 MB and fits).
+ * No cudaMalloc, cudaFree or other allocating call is made, and nothing is copied from host memory
+ * (the twiddle table is written by a kernel). The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture. Every call on a device shares that device's one array and leaves its contents behind
+ * (each call rewrites everything it reads), so calls that may overlap on the same device race:
+ * serialise them on one stream per device. Asynchronous on `stream`. Errors are reported through
+ * the return value and csc_last_error(NULL).
  */
 csc_status csc_code_noalloc(const csc_params* params, int n_images, const int* dims, void* stream,
                             const float* x, const float* d, float* v, float* z, int iters);
+
+/*
+ * Synchronise the context's stream and report the device flag of the most recent csc_code call:
+ * CSC_ERR_NONFINITE if one of its sweeps met a non-finite lambda_hat, else CSC_OK (each csc_code
+ * clears the flag when it starts). For asynchronous callers that did not set CSC_FLAG_CHECK_FINITE.
+ */
+csc_status csc_check(csc_ctx* ctx);
+
+/*
+ * Testing aid (no counterpart in the paper): bound every spin-wait of the learning CG's grid
+ * exchanges to `clocks` SM clock cycles (0 restores the default of about one second). A wait that
+ * runs out sets the context's error word; every CTA then returns and csc_learn returns
+ * CSC_ERR_TIMEOUT with d and mu unspecified, leaving the context usable. A tiny bound makes a wait run
+ * out on purpose; the tensor-core Gram's waits are not affected.
+ */
+csc_status csc_set_wait_limit(csc_ctx* ctx, long long clocks);
 
 /* Release the context and its workspace. NULL is ignored. */
 void csc_destroy(csc_ctx* ctx);

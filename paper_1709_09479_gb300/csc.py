@@ -24,6 +24,8 @@ STATUS_NAMES = {0: "CSC_OK", 1: "CSC_ERR_ARG", 2: "CSC_ERR_SHAPE", 3: "CSC_ERR_W
 CSC_FP32 = 0
 CSC_MIXED_BF16 = 1
 CSC_FLAG_GRAPH = 1
+CSC_FLAG_CHECK_FINITE = 2
+CSC_FLAG_CG_STRICT = 4
 
 
 class CscError(RuntimeError):
@@ -35,7 +37,8 @@ class CscError(RuntimeError):
 class csc_params(ctypes.Structure):
     _fields_ = [("J", ctypes.c_int), ("K", ctypes.c_int), ("fs", ctypes.c_int * 2),
                 ("beta", ctypes.c_double), ("rho", ctypes.c_double), ("cg_max", ctypes.c_int),
-                ("cg_tol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
+                ("deterministic", ctypes.c_int)]
 
 
 class csc_timing(ctypes.Structure):
@@ -82,6 +85,10 @@ def _load():
     lib.csc_synthesize_backward.restype = i
     lib.csc_code_noalloc.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i]
     lib.csc_code_noalloc.restype = i
+    lib.csc_check.argtypes = [vp]
+    lib.csc_check.restype = i
+    lib.csc_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.csc_set_wait_limit.restype = i
     lib.csc_version.argtypes = []
     lib.csc_version.restype = ctypes.c_char_p
     return lib
@@ -121,7 +128,7 @@ def csc_last_error(ctx=None) -> str:
 def csc_init(J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6, precision=CSC_FP32,
              stream=None, flags=0):
     """Create a context; returns an opaque handle (int). ``stream``: cudaStream_t as int or None."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, precision, flags)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, precision, flags, 1)
     dims_arr = (ctypes.c_int * 2)(*dims)
     out = ctypes.c_void_p()
     _check(LIB.csc_init(ctypes.byref(p), n_images, dims_arr, stream, ctypes.byref(out)))
@@ -130,7 +137,7 @@ def csc_init(J, K, fs, dims, n_images, beta, rho, cg_max=100, cg_tol=1e-6, preci
 
 def csc_init_uneven(J, K, fs, dims_list, beta, rho, precision=CSC_FP32, stream=None, flags=0):
     """Context for images of different sizes; dims_list = [(H, W), ...] in image order."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, precision, flags)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, precision, flags, 1)
     flat = [int(v) for hw in dims_list for v in hw]
     arr = (ctypes.c_int * len(flat))(*flat)
     out = ctypes.c_void_p()
@@ -140,7 +147,7 @@ def csc_init_uneven(J, K, fs, dims_list, beta, rho, precision=CSC_FP32, stream=N
 
 def csc_init_video(J, K, fs, ft, dims, n_videos, beta, rho, stream=None, cg_max=100, cg_tol=1e-6):
     """Context for n_videos tensors J x T x H x W (dims = (T, H, W)), filters ft x fh x fw (fs = (fh, fw))."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, CSC_FP32, 0)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, CSC_FP32, 0, 1)
     dims_arr = (ctypes.c_int * 3)(*dims)
     out = ctypes.c_void_p()
     _check(LIB.csc_init_video(ctypes.byref(p), ft, n_videos, dims_arr, stream, ctypes.byref(out)))
@@ -206,12 +213,22 @@ def csc_synthesize_backward(ctx, d, z, gout, gz, gd):
 
 def csc_code_noalloc(J, K, fs, dims, n_images, beta, rho, x, d, v, z=None, iters=1, stream=None):
     """The context-free, allocation-free coding call (device arrays only; see include/csc.h)."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, CSC_FP32)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, 1, 1e-6, CSC_FP32, 0, 1)
     dims_arr = (ctypes.c_int * 2)(*dims)
     if stream is None:
         stream = _current_stream()
     _check(LIB.csc_code_noalloc(ctypes.byref(p), n_images, dims_arr, stream, _ptr(x, np.float32),
                                 _ptr(d, np.float32), _ptr(v, np.float32), _ptr(z, np.float32), iters))
+
+
+def csc_check(ctx):
+    """Synchronise and raise CscError(CSC_ERR_NONFINITE) if the latest csc_code met a non-finite value."""
+    _check(LIB.csc_check(ctx), ctx)
+
+
+def csc_set_wait_limit(ctx, clocks):
+    """Testing aid: bound the learning CG's exchange waits to `clocks` SM cycles (0: default)."""
+    _check(LIB.csc_set_wait_limit(ctx, int(clocks)), ctx)
 
 
 def csc_timing_enable(ctx, enable=True):
@@ -268,6 +285,12 @@ class Solver:
 
     def describe(self):
         return csc_describe(self.ctx)
+
+    def check(self):
+        csc_check(self.ctx)
+
+    def set_wait_limit(self, clocks):
+        csc_set_wait_limit(self.ctx, clocks)
 
     def timing_enable(self, enable=True):
         csc_timing_enable(self.ctx, enable)

@@ -425,16 +425,28 @@ csc_status uneven_autotune(Ctx* c, float* v) {
   float* vs = nullptr;
   const size_t nv = (size_t)c->U.n_v;
   CSC_CHECK_CUDA(c, cudaMalloc((void**)&vs, nv * sizeof(float)), "autotune scratch");
-  CSC_CHECK_CUDA(c, cudaMemcpyAsync(vs, v, nv * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "copy");
+  {
+    const cudaError_t ec = cudaMemcpyAsync(vs, v, nv * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    if (ec != cudaSuccess) {
+      cudaFree(vs);
+      return cuda_fail(c, ec, "autotune copy");
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  bool timed = false;
   for (const Cand& cd : cands) {
     if (cd.per_sm * (smem + 1024) > (size_t)228 * 1024) continue;
     const int G = (int)std::min<long long>((long long)c->nsm * cd.per_sm, (long long)c->U.n_small * c->K);
     uneven_partition(c, G);
     csc_status st = upload_uneven(c);
-    if (st != CSC_OK) { cudaFree(vs); return st; }
+    if (st != CSC_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaFree(vs);
+      return st;
+    }
     c->U.nt = cd.nt;
     cudaError_t e = launch_sweep_uneven(uneven_args(*c, nullptr, c->part[0], vs, nullptr), kPrologue, G, cd.nt,
                                         uneven_smem_bytes(c->U, c->J, kPrologue), c->stream);
@@ -448,11 +460,14 @@ csc_status uneven_autotune(Ctx* c, float* v) {
     if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    timed = true;
     if (ms < best) { best = ms; pick = cd; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(vs);
+  // no candidate ran: report it rather than caching an untimed default
+  if (!timed) return fail(c, CSC_ERR_CUDA, "uneven autotune: no launch shape ran on this batch");
   const int G = (int)std::min<long long>((long long)c->nsm * pick.per_sm, (long long)c->U.n_small * c->K);
   uneven_partition(c, G);
   csc_status st = upload_uneven(c);
@@ -567,13 +582,14 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
       cudaMalloc((void**)&c->part[1], (size_t)(tmp.G + tmp.N) * p.J * Om * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->l1, tmp.G * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->objimg, tmp.N * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void**)&c->err, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     c->last_error = "csc_init: device workspace allocation failed";
     return bail(CSC_ERR_WORKSPACE);
   }
   e = cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->err, 0, 2 * sizeof(int));
+  c->cerr = c->err + 1;
   if (e != cudaSuccess) {
     c->last_error = std::string("csc_init: ") + cudaGetErrorString(e);
     return bail(CSC_ERR_CUDA);
@@ -707,13 +723,14 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
       cudaMalloc((void**)&c->pmat, U.n_pm * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->xhat, U.n_xh * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->objimg, n_images * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void**)&c->err, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     c->last_error = "csc_init_uneven: device workspace allocation failed";
     return bail(CSC_ERR_WORKSPACE);
   }
+  c->cerr = c->err + 1;
   if (cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(c->err, 0, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     c->last_error = "csc_init_uneven: upload failed";
     return bail(CSC_ERR_CUDA);
@@ -917,7 +934,8 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
   }
   // the launch sequence of this call
   auto enqueue = [&]() -> cudaError_t {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->cerr, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
     if (iters == 0) {
       if (!zd) return cudaSuccess;
       c->launches += 1;
@@ -990,8 +1008,32 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
   }
   if (v_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(v, vd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "v copy");
   if (z_host) CSC_CHECK_CUDA(c, cudaMemcpyAsync(z, zd, nv * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "z copy");
-  if (v_host || z_host || (xd && xd != x) || (dd && dd != d))
+  const bool sync = v_host || z_host || (xd && xd != x) || (dd && dd != d);
+  if (sync || (c->p.flags & CSC_FLAG_CHECK_FINITE)) {
+    // a synchronous call reports the sweeps' non-finite flag at its end
+    int herr = 0;
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->cerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
     CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (herr) return fail(c, (csc_status)herr, "csc_code: a non-finite value reached the dual variable");
+  }
+  return CSC_OK;
+}
+
+csc_status csc_check(csc_ctx* ctx) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_check: null context");
+  Ctx* c = &ctx->c;
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  int herr[2] = {0, 0};
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(herr, c->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (herr[1]) return fail(c, (csc_status)herr[1], "csc_check: a non-finite value reached the dual variable in csc_code");
+  return CSC_OK;
+}
+
+csc_status csc_set_wait_limit(csc_ctx* ctx, long long clocks) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_set_wait_limit: null context");
+  if (clocks < 0) return fail(&ctx->c, CSC_ERR_ARG, "csc_set_wait_limit: clocks must be >= 0");
+  ctx->c.wait_limit = clocks;
   return CSC_OK;
 }
 
@@ -1167,12 +1209,17 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
   int herr = 0;
   CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
   std::vector<int> its(std::max(steps, 1));
-  if (cg_iters && steps > 0)
+  if ((cg_iters || (c->p.flags & CSC_FLAG_CG_STRICT)) && steps > 0)
     CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), L.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
                    "iteration copy");
   CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (herr == CSC_ERR_NONFINITE) return fail(c, CSC_ERR_NONFINITE, "csc_learn: a CG residual or step was not finite");
   if (herr) return fail(c, (csc_status)herr, "csc_learn: grid barrier timed out");
   if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+  if (c->p.flags & CSC_FLAG_CG_STRICT)
+    for (int i = 0; i < steps; ++i)
+      if (its[i] >= c->p.cg_max)
+        return fail(c, CSC_ERR_NOT_CONVERGED, "csc_learn: a CG solve stopped at cg_max iterations");
   return CSC_OK;
 }
 

@@ -40,6 +40,7 @@ struct SweepArgs {
   float* v_out;          // iterate/last: new state written here instead of over v (may be null)
   const __nv_bfloat162* dhat16;  // mixed precision: d_hat in bf16; contraction operands rounded to bf16
   float2* lam_store;     // iterate/last: lambda_hat / D of each image stored here [N][J][Omega] (may be null)
+  int* err;              // set to CSC_ERR_NONFINITE when a lambda_hat formed by the sweep is not finite (may be null)
 };
 
 struct Ctx;
@@ -297,7 +298,9 @@ struct Ctx {
   float2* part[2] = {nullptr, nullptr};
   double* l1 = nullptr;
   double* objimg = nullptr;
-  int* err = nullptr;
+  int* err = nullptr;        // learning: CSC_ERR_TIMEOUT / CSC_ERR_NONFINITE raised by the kernels
+  int* cerr = nullptr;       // coding: CSC_ERR_NONFINITE raised by the sweeps of the latest csc_code
+  long long wait_limit = 0;  // bound of the CG exchange waits in SM clocks (0: the default, ~1 s)
   LearnBuffers L;
   BackwardBuffers B;
   VideoLearnBuffers VL;

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
       const int c1 = (int)((((n + 1) * a.K) * a.G - 1) / NK);
       const float irho = 1.0f / a.rho;
       const float2* xh = a.xhat + (size_t)n * J * Om;
+      bool bad = false;
       for (int o = threadIdx.x; o < Om; o += NT) {
         float2 r[kMaxJ];
 #pragma unroll
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
         float2* ls = (a.lam_store && cta == c0) ? a.lam_store + (size_t)n * J * Om : nullptr;
         if (J == 1) {
           lam[o] = cscale(r[0], a.pdiag[o]);
+          bad |= !(isfinite(lam[o].x) && isfinite(lam[o].y));
           if (ls) ls[o] = lam[o];
         } else {
           const float2* pm = a.pmat + (size_t)o * J * J;
@@ -129,11 +131,13 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
               for (int j = 0; j < kMaxJ; ++j)
                 if (j < J) s = cfma(pm[i * J + j], r[j], s);
               lam[(size_t)i * Om + o] = s;
+              bad |= !(isfinite(s.x) && isfinite(s.y));
               if (ls) ls[(size_t)i * Om + o] = s;
             }
           }
         }
       }
+      if (bad && a.err) atomicExch(a.err, (int)CSC_ERR_NONFINITE);
     }
     if (kAcc)
       for (int i = threadIdx.x; i < J * Om; i += NT) acc[i] = make_float2(0.f, 0.f);

@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
   }
 }
 
-// bound of every spin-wait of the CG launch (~1 s of SM clocks)
+// default bound of every spin-wait of the CG launch (~1 s of SM clocks); a context can lower it
+// (csc_set_wait_limit) so that a test can make a wait run out
 constexpr long long kSpinLimit = 2000000000LL;
 
 // ---------------------------------------------------------------------------------------------
@@ -223,6 +224,7 @@ struct CgArgs {
   unsigned long long* slots;   // [2][G][kSlotWords], zeroed before the launch
   int* iters;          // [steps]
   int* err;
+  long long spin;      // bound of every spin-wait, in SM clocks
 };
 
 // shared-memory layout of the CG kernel (float2 arrays first, then floats)
@@ -327,64 +329,6 @@ __device__ __forceinline__ void publish(unsigned long long* slots, int G, const 
     st_volatile_u64(s + i, ((unsigned long long)ep << 32) | __float_as_uint(N > 0 ? vals[i] : 0.f));
 }
 
-// every thread: totals[i] = sum over CTAs (in CTA order) of word i of epoch ep, i < n. The G * n
-// words are polled by all threads of the block at once (a few independent loads each, repeated
-// until they carry the epoch), parked in vals ([G][n] floats of shared memory) and summed by warp 0
-// in a fixed order. false on a device error or when the wait runs out (error flag set).
-template <int NT>
-__device__ bool gather(const unsigned long long* slots, int G, int n, unsigned ep, double* totals, float* vals,
-                       int* err) {
-  __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
-  const int nw = n > 0 ? n : 1;
-  const unsigned long long* base = slots + (size_t)(ep & 1) * G * kSlotWords;
-  constexpr int kPer = 4;   // words per thread: G * nw <= kPer * NT
-  int idx[kPer];
-  bool ready[kPer];
-#pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    idx[u] = threadIdx.x + u * NT;
-    ready[u] = idx[u] >= G * nw;
-  }
-  const long long t0 = clock64();
-  bool fail = false;
-  while (true) {
-    unsigned long long w[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u)
-      if (!ready[u]) w[u] = ld_volatile_u64(base + (size_t)(idx[u] / nw) * kSlotWords + idx[u] % nw);
-    bool all = true;
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      if (!ready[u]) {
-        if ((unsigned)(w[u] >> 32) == ep) {
-          ready[u] = true;
-          vals[idx[u]] = __uint_as_float((unsigned)w[u]);
-        } else {
-          all = false;
-        }
-      }
-    }
-    if (all) break;
-    if (*(volatile int*)err) { fail = true; break; }
-    if (clock64() - t0 > kSpinLimit) { atomicExch(err, (int)CSC_ERR_TIMEOUT); fail = true; break; }
-  }
-  if (fail) s_fail = 1;
-  if (threadIdx.x < G * nw) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire: words before data
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i = 0; i < n; ++i) {
-      double v = 0.0;
-      for (int b = lane; b < G; b += 32) v += (double)vals[b * nw + i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) totals[i] = v;
-    }
-  }
-  __syncthreads();
-  return s_fail == 0;
-}
-
 // Waits until this block's words carry epoch ep, in two phases: first the exchange's slot words
 // (G CTAs x nw; thread t polls words t and t + NT, values parked in vals, [G][nw] floats of shared
 // memory), when slots is not null; after a block barrier the data words t + u NT < ndata (left in
@@ -393,7 +337,8 @@ __device__ bool gather(const unsigned long long* slots, int G, int n, unsigned e
 // block. false when a CTA flagged an error or the wait ran out (flag set).
 template <int NT, int U>
 __device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsigned ep, float* vals,
-                           const unsigned long long* data, int ndata, unsigned long long (&wd)[U], int* err) {
+                           const unsigned long long* data, int ndata, unsigned long long (&wd)[U], int* err,
+                           long long limit) {
   __shared__ int s_bad;
   const long long t0 = clock64();
   bool ok = true;
@@ -408,7 +353,7 @@ __device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsig
         const unsigned long long* wp = sb + (size_t)(i / nw) * kSlotWords + i % nw;
         unsigned long long w = ld_volatile_u64(wp);
         while ((unsigned)(w >> 32) != ep) {
-          if (*(volatile int*)err || clock64() - t0 > kSpinLimit) { ok = false; break; }
+          if (*(volatile int*)err || clock64() - t0 > limit) { ok = false; break; }
           w = ld_volatile_u64(wp);
         }
         vals[i] = __uint_as_float((unsigned)w);
@@ -434,7 +379,7 @@ __device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsig
       if ((pend & (1u << u)) && (unsigned)(wd[u] >> 32) == ep) pend &= ~(1u << u);
     if (!pend) break;
     if (*(volatile int*)err) return false;
-    if (clock64() - t0 > kSpinLimit) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, (int)CSC_ERR_TIMEOUT);
       return false;
     }
@@ -776,7 +721,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       for (int i = 0; i < nown; ++i) {
         const int k = blockIdx.x + i * G;
         unsigned long long yv[UY];
-        if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, 1, ep, gvals, a.yw + (size_t)k * nyw, nyw, yv, a.err))
+        if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, 1, ep, gvals, a.yw + (size_t)k * nyw, nyw, yv, a.err, a.spin))
           s_fail = 1;
         float* yhf = reinterpret_cast<float*>(yh);
 #pragma unroll
@@ -800,7 +745,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       }
       if (nown == 0) {   // the exchange's slot words still have to be seen
         unsigned long long none[1];
-        if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err)) s_fail = 1;
+        if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err, a.spin)) s_fail = 1;
         __syncthreads();
         if (s_fail) return;
       }
@@ -811,7 +756,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
       unsigned long long zv[UZ];
       if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 3 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT), zv,
-                              a.err))
+                              a.err, a.spin))
         s_fail = 1;
       __syncthreads();
       if (s_fail) return;
@@ -821,12 +766,18 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     }
     sum_slots<NT>(gvals, G, 3 * J, 3 * J, tot, [&]() {
       int all = 1;
+      bool nonfinite = false;
       for (int j = 0; j < J; ++j) {
         s_rz[j] = tot[j];
         s_rr[j] = tot[J + j];
         s_bb[j] = tot[2 * J + j];
         s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
         all = all && s_done[j];
+        if (!isfinite(s_rr[j]) || !isfinite(s_rz[j]) || !isfinite(s_bb[j])) nonfinite = true;
+      }
+      if (nonfinite) {   // the same totals in every CTA: all of them stop here together
+        if (blockIdx.x == 0) atomicCAS(a.err, 0, (int)CSC_ERR_NONFINITE);
+        all = 1;
       }
       s_all = all;
     });
@@ -860,7 +811,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           const bool has = i < nown;
           unsigned long long yv[UY];
           if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, J, ep, gvals, has ? a.yw + (size_t)k * nyw : nullptr,
-                                  has ? nyw : 0, yv, a.err))
+                                  has ? nyw : 0, yv, a.err, a.spin))
             s_fail = 1;
           float* yhf = reinterpret_cast<float*>(yh);
 #pragma unroll
@@ -903,23 +854,29 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
         unsigned long long zv[UZ];
         if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 2 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT),
-                                zv, a.err))
+                                zv, a.err, a.spin))
           s_fail = 1;
         __syncthreads();
         if (s_fail) return;
         if (c0 == 0)
           sum_slots<NT>(gvals, G, 2 * J, 2 * J, tot, [&]() {
             int all = 1;
+            bool nonfinite = false;
             for (int j = 0; j < J; ++j) {
               if (!s_done[j]) {
                 s_beta[j] = s_rz[j] > 0.0 ? (float)(tot[j] / s_rz[j]) : 0.f;
                 s_rz[j] = tot[j];
                 s_rr[j] = tot[J + j];
                 s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+                if (!isfinite(s_rr[j]) || !isfinite(s_rz[j])) nonfinite = true;
               } else {
                 s_beta[j] = 0.f;
               }
               all = all && s_done[j];
+            }
+            if (nonfinite) {   // the same totals in every CTA: all of them stop here together
+              if (blockIdx.x == 0) atomicCAS(a.err, 0, (int)CSC_ERR_NONFINITE);
+              all = 1;
             }
             s_all = all;
           });
@@ -952,7 +909,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
     publish<0>(a.slots, G, nullptr, ++ep, true);   // x (plain stores) complete everywhere before the next step
     {
       unsigned long long none[1];
-      if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err)) s_fail = 1;
+      if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err, a.spin)) s_fail = 1;
       if (threadIdx.x < G) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire before reading x
       __syncthreads();
       if (s_fail) return;
@@ -1342,6 +1299,7 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   const size_t nvec = (size_t)c.K * c.J * c.S2;
   a.lags = c.L.lags; a.chat = c.L.chat; a.yw = c.L.yw; a.zw = c.L.zw; a.b = c.L.b; a.x = d;
   a.mu = c.L.mu; a.minv = c.L.minv; a.slots = c.L.slots; a.iters = c.L.iters; a.err = dev_err;
+  a.spin = c.wait_limit > 0 ? c.wait_limit : kSpinLimit;
   // the grid: one CTA per SM at most (every CTA must be resident: the exchanges wait on all)
   a.G = learn_cg_ctas(c);
   // epochs restart at 1 every launch: clear every word that carries one

@@ -1,15 +1,17 @@
 // csc_code_noalloc: the coding call of csc_code without a context and without any device
 // allocation. Some callers cannot allocate device memory at the point where they want to code
-// images: code running while a CUDA graph is being captured elsewhere in the process, code
-// inside a framework whose allocator owns every byte of the device pool, or plugins that are only
-// handed a stream and device pointers. For them the workspace (filter and image spectra, the
-// per-frequency system, the partial sums of the ADMM sweeps) lives in one file-scope __device__
-// array of fixed size, reserved when the library is loaded and held by every GPU that loads it
-// until the process exits.
+// images: code inside a framework whose caching allocator owns every byte of the device pool (a
+// cudaMalloc there fails or fragments the pool), plugins and extension points that are handed only a
+// stream and device pointers and have no right to allocate, and latency-bound paths where the
+// implicit synchronisation of cudaMalloc/cudaFree is not acceptable. For them the workspace (filter
+// and image spectra, the per-frequency system, the partial sums of the ADMM sweeps, the twiddle
+// table) lives in one file-scope __device__ array of fixed size, reserved when the library is loaded
+// and held by every GPU that loads it until the process exits.
 //
 // Set-up: the array's name is only a host-side stand-in in host code, so its device address is
 // looked up with cudaGetSymbolAddress once per device (with that device current) on the first
-// call made on it, cached, and passed to the kernels.
+// call made on it, cached, and passed to the kernels. The twiddle table is written by a kernel, so
+// a call copies nothing from host memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -64,6 +66,26 @@ bool device_pointer(const void* p) {
 }
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// tw[t] = exp(-2 pi i t / n) for the three sections of the table: n = W/2 (t < W/2), n = H
+// (t < H) and n = W (t <= W/2), computed in float64 and rounded once
+__global__ void k_noalloc_twiddles(float2* tw, int Wh, int H, int W) {
+  const int n_all = Wh + H + Wh + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += gridDim.x * blockDim.x) {
+    int t = i, n = Wh;
+    if (i >= Wh + H) { t = i - Wh - H; n = W; }
+    else if (i >= Wh) { t = i - Wh; n = H; }
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    tw[i] = make_float2((float)c, (float)-s);
+  }
+}
+
+cudaError_t launch_noalloc_twiddles(float2* tw, int Wh, int H, int W, cudaStream_t stream) {
+  const int n_all = Wh + H + Wh + 1;
+  k_noalloc_twiddles<<<(n_all + 255) / 256, 256, 0, stream>>>(tw, Wh, H, W);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -146,14 +168,9 @@ extern "C" csc_status csc_code_noalloc(const csc_params* params, int n_images, c
   c.part[0] = reinterpret_cast<float2*>(take(b_part));
   c.part[1] = reinterpret_cast<float2*>(take(b_part));
 
-  // twiddles (same table as csc_init), from a host stack array
-  float2 tw[kNoAllocMaxTwiddles];
-  const double pi2 = 6.283185307179586476925286766559;
-  for (int t = 0; t < g.Wh; ++t) tw[t] = make_float2((float)cos(pi2 * t / g.Wh), (float)-sin(pi2 * t / g.Wh));
-  for (int t = 0; t < g.H; ++t) tw[g.Wh + t] = make_float2((float)cos(pi2 * t / g.H), (float)-sin(pi2 * t / g.H));
-  for (int t = 0; t < g.Wc; ++t)
-    tw[g.Wh + g.H + t] = make_float2((float)cos(pi2 * t / g.W), (float)-sin(pi2 * t / g.W));
-  cudaError_t e = cudaMemcpyAsync(c.tw, tw, (size_t)ntw * sizeof(float2), cudaMemcpyHostToDevice, c.stream);
+  // twiddles (the table csc_init builds on the host), written by a kernel so that nothing is
+  // copied from host memory
+  cudaError_t e = launch_noalloc_twiddles(c.tw, g.Wh, g.H, g.W, c.stream);
   if (e == cudaSuccess && iters == 0) {
     if (z) e = launch_codes_from_state(c, v, z);
   } else if (e == cudaSuccess) {

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
       const float irho = 1.0f / a.rho;
       const float2* xh = a.xhat + (size_t)n * OM;
       float2* ls = (a.lam_store && cta == c0) ? a.lam_store + (size_t)n * OM : nullptr;
+      bool bad = false;
 #pragma unroll 2
       for (int s = 0; s < 18; ++s) {
         if (s >= 16 && !nyq) break;
@@ -69,8 +70,10 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         for (int cc = c0; cc <= c1; ++cc) acc2 = cadd(acc2, a.part_in[(size_t)(cc + n) * OM + o]);
         const float2 l = cscale(acc2, a.pdiag[o]);
         lam[p] = l;
+        bad |= !(isfinite(l.x) && isfinite(l.y));
         if (ls) ls[o] = l;
       }
+      if (bad && a.err) atomicExch(a.err, (int)CSC_ERR_NONFINITE);
     }
     // sum_k d_hat_k u_hat_k of this image at the thread's 16 (+2) bins, in registers
     float2 acc[18];

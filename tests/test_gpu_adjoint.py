@@ -113,3 +113,44 @@ def test_unrolled_gradients_match_finite_differences(mods):
             fd = (L(x, d + h * e) - L(x, d - h * e)) / (2 * h)
         an = float(np.sum(g * e))
         assert abs(fd - an) <= 1e-3 * abs(fd), (which, fd, an)
+
+
+def test_unrolled_gradients_at_the_benchmark_settings(mods):
+    """The differentiable-coding workload's settings (K = 64 filters 11 x 11, 128 x 128, beta = 1,
+    rho = 0.1, T = 20 unrolled iterations, checkpoints every 5: four full segments) on 2 of its images:
+    gradients against the float64 oracle adjoint (2e-4) and directional derivatives against float64
+    central differences of the oracle's forward (the 1e-3 bar)."""
+    import torch
+    csc, ag = mods
+    from paper_1709_09479_gb300 import inputs
+    N, K, dims, s, beta, rho, T, every = 2, 64, (128, 128), 11, 1.0, 0.1, 20, 5
+    x = f32(inputs.powerlaw_field(5, N, 1, dims)).astype(np.float64)
+    y = f32(inputs.powerlaw_field(50, N, 1, dims)).astype(np.float64)
+    d = f32(inputs.unit_filters(51, K, 1, (s, s))).astype(np.float64)
+    loss_o, gx_o, gd_o = O.unrolled_loss_and_grad(x, d, y, beta, rho, T)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims=dims, n_images=N, beta=beta, rho=rho) as sv:
+        xt = to_cuda(x).requires_grad_(True)
+        dt = to_cuda(d).requires_grad_(True)
+        loss = unrolled_loss(ag, sv, xt, dt, to_cuda(y), T, every)
+        loss.backward()
+        torch.cuda.synchronize()
+        gx, gd = to_np(xt.grad), to_np(dt.grad)
+    assert abs(float(loss.detach()) - loss_o) <= 1e-5 * loss_o
+    assert rel(gx, gx_o) <= GRAD_TOL, rel(gx, gx_o)
+    assert rel(gd, gd_o) <= GRAD_TOL, rel(gd, gd_o)
+
+    def L(xx, dd):
+        _, z = O.code_admm(xx, dd, beta, rho, T)
+        r = O.synthesize(dd, z) - y
+        return float(np.mean(r * r))
+
+    rng = np.random.default_rng(6)
+    for which, g in (("x", gx), ("d", gd)):
+        e = rng.standard_normal(x.shape if which == "x" else d.shape)
+        h = 1e-6 / np.sqrt(np.mean(e * e))
+        if which == "x":
+            fd = (L(x + h * e, d) - L(x - h * e, d)) / (2 * h)
+        else:
+            fd = (L(x, d + h * e) - L(x, d - h * e)) / (2 * h)
+        an = float(np.sum(g * e))
+        assert abs(fd - an) <= 1e-3 * abs(fd), (which, fd, an)

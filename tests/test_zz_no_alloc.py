@@ -1,8 +1,10 @@
 """The allocation-free coding entry point (csc_code_noalloc) against the context entry point.
 
-Callers that cannot allocate device memory where they code images (inside graph capture, under a
-framework that owns the device pool, or plugins handed only a stream and device pointers) use
-csc_code_noalloc, whose workspace is a fixed file-scope device array. Here it must give what
+Callers that cannot allocate device memory where they code images (under a framework whose caching
+allocator owns the device pool, plugins handed only a stream and device pointers, latency-bound
+paths that cannot take cudaMalloc's implicit synchronisation) use csc_code_noalloc, whose workspace
+is a fixed file-scope device array. At 128 x 128 it runs the generic sweep while csc_code runs the
+dedicated 128 x 128 one, so that case also checks the two sweeps against each other. Here it must give what
 csc_init + csc_code give, on two calls in a row (the second warm-started, reusing the scratch the
 first one left behind), and refuse problems larger than its scratch. Collected last on purpose.
 """
@@ -24,7 +26,8 @@ def csc():
 
 def test_noalloc_matches_context_call_on_two_calls_in_a_row(csc):
     import torch
-    for (N, K, J, dims, s, beta, rho) in [(7, 50, 1, (64, 64), 5, 0.5, 1.0), (2, 3, 3, (24, 32), 3, 0.25, 1.5)]:
+    for (N, K, J, dims, s, beta, rho) in [(7, 50, 1, (64, 64), 5, 0.5, 1.0), (2, 3, 3, (24, 32), 3, 0.25, 1.5),
+                                         (2, 8, 1, (128, 128), 11, 0.05, 1.0)]:
         x, d = make_problem(90 + K, N, K, J, dims, s)
         xv, dv = to_cuda(x), to_cuda(d)
         v_ref = torch.zeros((N, K) + dims, device="cuda")
