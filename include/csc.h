@@ -175,6 +175,29 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
                      int* cg_iters);
 
 /*
+ * The learning subproblem split at its one reduction over images, for data-parallel learning over
+ * several contexts (one per GPU, each holding its own images; Sec. 3.2: the dictionary d is shared,
+ * the images only enter through sums over n). csc_learn is csc_learn_stats followed by
+ * csc_learn_solve on the same context.
+ *
+ * csc_learn_stats writes this context's two sums for codes z:
+ *   C [K][K][2fh-1][2fw-1]  the code cross-correlations on the lag window:
+ *                           C[k][k'][ta + fh-1][tb + fw-1] = sum_n sum_p z_nk(p) z_nk'(p + (ta, tb))
+ *                           (circular in p), i.e. the matrix S Z^T Z S^T of Eq. Learning_new in
+ *                           block-Toeplitz form;
+ *   b [K][J][fh][fw]        the right-hand side S Z^T x = sum_n S (z_nk correlated with x_nj).
+ * Both are sums over images: the sums of several contexts' C and b (an all-reduce) are the C and b of
+ * their images together. csc_learn_solve then runs `steps` learning steps (the CG of csc_learn
+ * warm-started from d, the mu update, the final projection) from a given C and b: every context
+ * given the same reduced C, b, d and mu computes the same d and mu. Arrays may be host or device
+ * memory (float32; mu float64); csc_learn_stats synchronises and returns after C and b are written.
+ * Uniform 2-D contexts only (CSC_ERR_UNSUPPORTED on uneven and video contexts).
+ */
+csc_status csc_learn_stats(csc_ctx* ctx, const float* x, const float* z, float* C, float* b);
+csc_status csc_learn_solve(csc_ctx* ctx, const float* C, const float* b, float* d, double* mu, int steps,
+                           int* cg_iters);
+
+/*
  * Objective of Eq. 1 summed over images: *out (host) = 1/2 sum_n ||x_n - sum_k d_k * z_nk||^2
  * + beta sum |z|. Reductions run in float64 in a fixed order. Synchronises the stream.
  */

@@ -85,6 +85,10 @@ def _load():
     lib.csc_synthesize_backward.restype = i
     lib.csc_code_noalloc.argtypes = [ctypes.POINTER(csc_params), i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i]
     lib.csc_code_noalloc.restype = i
+    lib.csc_learn_stats.argtypes = [vp, vp, vp, vp, vp]
+    lib.csc_learn_stats.restype = i
+    lib.csc_learn_solve.argtypes = [vp, vp, vp, vp, vp, i, ctypes.POINTER(i)]
+    lib.csc_learn_solve.restype = i
     lib.csc_check.argtypes = [vp]
     lib.csc_check.restype = i
     lib.csc_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
@@ -173,6 +177,20 @@ def csc_learn(ctx, x, z, d, mu, steps):
     its = (ctypes.c_int * max(steps, 1))()
     _check(LIB.csc_learn(ctx, _ptr(x, np.float32), _ptr(z, np.float32), _ptr(d, np.float32),
                          _ptr(mu, np.float64), steps, its), ctx)
+    return list(its)[:steps]
+
+
+def csc_learn_stats(ctx, x, z, C, b):
+    """This context's sums over its images: lags C [K][K][2fh-1][2fw-1] and right-hand side b [K][J][fh][fw]."""
+    _check(LIB.csc_learn_stats(ctx, _ptr(x, np.float32), _ptr(z, np.float32), _ptr(C, np.float32),
+                               _ptr(b, np.float32)), ctx)
+
+
+def csc_learn_solve(ctx, C, b, d, mu, steps):
+    """Learning steps from given (reduced) C and b; returns the CG iterations of each step."""
+    its = (ctypes.c_int * max(steps, 1))()
+    _check(LIB.csc_learn_solve(ctx, _ptr(C, np.float32), _ptr(b, np.float32), _ptr(d, np.float32),
+                               _ptr(mu, np.float64), steps, its), ctx)
     return list(its)[:steps]
 
 
@@ -279,6 +297,17 @@ class Solver:
 
     def learn(self, x, z, d, mu, steps):
         return csc_learn(self.ctx, x, z, d, mu, steps)
+
+    def learn_stats(self, x, z, C, b):
+        csc_learn_stats(self.ctx, x, z, C, b)
+
+    def learn_solve(self, C, b, d, mu, steps):
+        return csc_learn_solve(self.ctx, C, b, d, mu, steps)
+
+    def stats_shapes(self):
+        """Shapes of csc_learn_stats' outputs: C (K, K, 2fh-1, 2fw-1) and b (K, J, fh, fw)."""
+        fh, fw = self.fs
+        return (self.K, self.K, 2 * fh - 1, 2 * fw - 1), (self.K, self.J, fh, fw)
 
     def objective(self, x, d, z):
         return csc_objective(self.ctx, x, d, z)

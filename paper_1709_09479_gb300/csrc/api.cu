@@ -1102,6 +1102,101 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   return CSC_OK;
 }
 
+// workspace of the 2-D learning path (allocated on first use) and the per-step iteration buffer
+static csc_status learn_prepare(Ctx* c, int steps, const char* who) {
+  const int K = c->K, J = c->J;
+  const size_t nd = (size_t)K * J * c->S2, Om = c->g.Omega;
+  const size_t npairs = (size_t)K * (K + 1) / 2;
+  const int La = 2 * c->fh - 1, Lb = 2 * c->fw - 1;
+  LearnBuffers& L = c->L;
+  if (!L.ready) {
+    if (ensure_alloc(&L.zhat, (size_t)c->N * K * Om) != cudaSuccess ||
+        ensure_alloc(&L.gram, npairs * Om) != cudaSuccess ||
+        ensure_alloc(&L.lags, (size_t)K * K * La * Lb) != cudaSuccess ||
+        ensure_alloc(&L.chat, (size_t)La * c->fw * K * (K + 1) / 2) != cudaSuccess ||
+        ensure_alloc(&L.yw, (size_t)2 * K * J * La * c->fw) != cudaSuccess ||
+        ensure_alloc(&L.zw, nd) != cudaSuccess ||
+        ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
+        ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
+        (gram_tc_applies(*c) && (ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess ||
+                                 ensure_alloc(&L.zt, (size_t)c->N * K * Om) != cudaSuccess ||
+                                 ensure_alloc(&L.lagT, lag_sep_T_count(*c)) != cudaSuccess)) ||
+        (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||
+        ensure_alloc(&L.slots, (size_t)2 * c->nsm * 4 * kMaxJ) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CSC_ERR_WORKSPACE, std::string(who) + ": device workspace allocation failed");
+    }
+    L.ready = true;
+  }
+  if (steps > L.steps_cap) {
+    if (L.iters) cudaFree(L.iters);
+    L.iters = nullptr;
+    CSC_CHECK_CUDA(c, ensure_alloc(&L.iters, (size_t)steps), "iteration buffer");
+    L.steps_cap = steps;
+  }
+  return CSC_OK;
+}
+
+// the sums over this context's images: code Gram -> lags L.lags (and their spectra L.chat), and the
+// right-hand side L.b = S Z^T x
+static csc_status learn_stats_enqueue(Ctx* c, const float* xd, const float* zd) {
+  const int K = c->K, J = c->J;
+  LearnBuffers& L = c->L;
+  CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
+  // the per-frequency Gram on the tensor cores (3xTF32 in float32, BF16 in the mixed mode), with the
+  // right-hand-side spectra as J extra columns, when K + J <= 128; otherwise on the CUDA cores
+  if (gram_tc_applies(*c)) {
+    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
+    CSC_CHECK_CUDA(c, launch_spectra_transpose(*c, L.zhat, c->N * K, L.zt), "code spectra transpose");
+    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, c->p.precision == CSC_MIXED_BF16, L.rspec, c->err),
+                   "code Gram (tensor cores)");
+    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, L.rspec), "learning right-hand side");
+    CSC_CHECK_CUDA(c, launch_learn_lags_sep(*c), "code lags");
+    c->launches += 4;
+  } else {
+    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
+    CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
+    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, nullptr), "learning right-hand side");
+    CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
+    c->launches += 3;
+  }
+  c->launches += 1;   // image spectra (the lag kernels count themselves)
+  return CSC_OK;
+}
+
+// the CG steps from L.lags / L.chat / L.b, then d, mu and the iteration counts back to the caller
+static csc_status learn_solve_finish(Ctx* c, float* dd, float* d, double* mu, int steps, int* cg_iters, int br) {
+  const int K = c->K;
+  const size_t nd = (size_t)K * c->J * c->S2;
+  LearnBuffers& L = c->L;
+  const bool mu_dev = is_device_ptr(mu);
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(L.mu, mu, K * sizeof(double),
+                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+                 "mu copy");
+  CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
+  bracket_close(c, br);
+  c->launches += 1;
+  if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, nd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(mu, L.mu, K * sizeof(double),
+                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+                 "mu copy");
+  int herr = 0;
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
+  std::vector<int> its(std::max(steps, 1));
+  if ((cg_iters || (c->p.flags & CSC_FLAG_CG_STRICT)) && steps > 0)
+    CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), L.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                   "iteration copy");
+  CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (herr == CSC_ERR_NONFINITE) return fail(c, CSC_ERR_NONFINITE, "csc_learn: a code, CG residual or step was not finite");
+  if (herr) return fail(c, (csc_status)herr, "csc_learn: grid barrier timed out");
+  if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+  if (c->p.flags & CSC_FLAG_CG_STRICT)
+    for (int i = 0; i < steps; ++i)
+      if (its[i] >= c->p.cg_max)
+        return fail(c, CSC_ERR_NOT_CONVERGED, "csc_learn: a CG solve stopped at cg_max iterations");
+  return CSC_OK;
+}
+
 csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, double* mu, int steps,
                      int* cg_iters) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn: null context");
@@ -1138,89 +1233,67 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
     if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
     return CSC_OK;
   }
-  const int K = c->K, J = c->J;
-  const size_t nx = (size_t)c->N * J * c->g.D, nd = (size_t)K * J * c->S2;
-  const size_t nz = (size_t)c->N * K * c->g.D, Om = c->g.Omega;
-  const size_t npairs = (size_t)K * (K + 1) / 2;
-  const int La = 2 * c->fh - 1, Lb = 2 * c->fw - 1;
-  LearnBuffers& L = c->L;
-  if (!L.ready) {
-    if (ensure_alloc(&L.zhat, (size_t)c->N * K * Om) != cudaSuccess ||
-        ensure_alloc(&L.gram, npairs * Om) != cudaSuccess ||
-        ensure_alloc(&L.lags, (size_t)K * K * La * Lb) != cudaSuccess ||
-        ensure_alloc(&L.chat, (size_t)La * c->fw * K * (K + 1) / 2) != cudaSuccess ||
-        ensure_alloc(&L.yw, (size_t)2 * K * J * La * c->fw) != cudaSuccess ||
-        ensure_alloc(&L.zw, nd) != cudaSuccess ||
-        ensure_alloc(&L.b, nd) != cudaSuccess || ensure_alloc(&L.vec, 4 * nd) != cudaSuccess ||
-        ensure_alloc(&L.mu, (size_t)K) != cudaSuccess ||
-        (gram_tc_applies(*c) && (ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess ||
-                                 ensure_alloc(&L.zt, (size_t)c->N * K * Om) != cudaSuccess ||
-                                 ensure_alloc(&L.lagT, lag_sep_T_count(*c)) != cudaSuccess)) ||
-        (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||
-        ensure_alloc(&L.slots, (size_t)2 * c->nsm * 4 * kMaxJ) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, CSC_ERR_WORKSPACE, "csc_learn: device workspace allocation failed");
-    }
-    L.ready = true;
-  }
-  if (steps > L.steps_cap) {
-    if (L.iters) cudaFree(L.iters);
-    L.iters = nullptr;
-    CSC_CHECK_CUDA(c, ensure_alloc(&L.iters, (size_t)steps), "iteration buffer");
-    L.steps_cap = steps;
-  }
-  const float *xd, *zd, *dd_c;
   csc_status s;
+  if ((s = learn_prepare(c, steps, "csc_learn")) != CSC_OK) return s;
+  const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
+  const size_t nz = (size_t)c->N * c->K * c->g.D;
+  const float *xd, *zd, *dd_c;
   if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
   if ((s = stage_in(c, (const float*)d, &c->st_d, nd, &dd_c, true)) != CSC_OK) return s;
-  float* dd = const_cast<float*>(dd_c);
-  const bool mu_dev = is_device_ptr(mu);
-  CSC_CHECK_CUDA(c, cudaMemcpyAsync(L.mu, mu, K * sizeof(double),
-                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
-                 "mu copy");
   CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
   const int br = bracket_open(c, 1);
-  CSC_CHECK_CUDA(c, launch_fft_maps(*c, xd, c->N * J, 0, c->xhat), "image spectra");
-  // the per-frequency Gram on the tensor cores (3xTF32 in float32, BF16 in the mixed mode), with the
-  // right-hand-side spectra as J extra columns, when K + J <= 128; otherwise on the CUDA cores
-  if (gram_tc_applies(*c)) {
-    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
-    CSC_CHECK_CUDA(c, launch_spectra_transpose(*c, L.zhat, c->N * K, L.zt), "code spectra transpose");
-    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, c->p.precision == CSC_MIXED_BF16, L.rspec, c->err),
-                   "code Gram (tensor cores)");
-    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, L.rspec), "learning right-hand side");
-    CSC_CHECK_CUDA(c, launch_learn_lags_sep(*c), "code lags");
-    c->launches += 4;
-  } else {
-    CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
-    CSC_CHECK_CUDA(c, launch_learn_gram(*c), "code Gram");
-    CSC_CHECK_CUDA(c, launch_learn_rhs(*c, nullptr), "learning right-hand side");
-    CSC_CHECK_CUDA(c, launch_learn_lags(*c), "code lags");
-    c->launches += 3;
-  }
-  CSC_CHECK_CUDA(c, launch_learn_cg(*c, dd, steps, c->err), "learning CG");
-  bracket_close(c, br);
-  c->launches += 2;   // image spectra, CG (the lag kernels count themselves)
-  if (dd != d) CSC_CHECK_CUDA(c, cudaMemcpyAsync(d, dd, nd * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "d copy");
-  CSC_CHECK_CUDA(c, cudaMemcpyAsync(mu, L.mu, K * sizeof(double),
-                                    mu_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
-                 "mu copy");
+  if ((s = learn_stats_enqueue(c, xd, zd)) != CSC_OK) return s;
+  return learn_solve_finish(c, const_cast<float*>(dd_c), d, mu, steps, cg_iters, br);
+}
+
+csc_status csc_learn_stats(csc_ctx* ctx, const float* x, const float* z, float* C, float* b) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn_stats: null context");
+  Ctx* c = &ctx->c;
+  if (c->uneven || c->video)
+    return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn_stats: uniform 2-D batches only");
+  if (!x || !z || !C || !b) return fail(c, CSC_ERR_ARG, "csc_learn_stats: null argument");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s;
+  if ((s = learn_prepare(c, 0, "csc_learn_stats")) != CSC_OK) return s;
+  const size_t nx = (size_t)c->N * c->J * c->g.D, nz = (size_t)c->N * c->K * c->g.D;
+  const size_t nd = (size_t)c->K * c->J * c->S2;
+  const size_t nC = (size_t)c->K * c->K * (2 * c->fh - 1) * (2 * c->fw - 1);
+  const float *xd, *zd;
+  if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
+  if ((s = stage_in(c, z, &c->st_z, nz, &zd, true)) != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
+  if ((s = learn_stats_enqueue(c, xd, zd)) != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(C, c->L.lags, nC * sizeof(float), cudaMemcpyDefault, c->stream), "C copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(b, c->L.b, nd * sizeof(float), cudaMemcpyDefault, c->stream), "b copy");
   int herr = 0;
   CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
-  std::vector<int> its(std::max(steps, 1));
-  if ((cg_iters || (c->p.flags & CSC_FLAG_CG_STRICT)) && steps > 0)
-    CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), L.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
-                   "iteration copy");
   CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-  if (herr == CSC_ERR_NONFINITE) return fail(c, CSC_ERR_NONFINITE, "csc_learn: a CG residual or step was not finite");
-  if (herr) return fail(c, (csc_status)herr, "csc_learn: grid barrier timed out");
-  if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
-  if (c->p.flags & CSC_FLAG_CG_STRICT)
-    for (int i = 0; i < steps; ++i)
-      if (its[i] >= c->p.cg_max)
-        return fail(c, CSC_ERR_NOT_CONVERGED, "csc_learn: a CG solve stopped at cg_max iterations");
+  if (herr) return fail(c, (csc_status)herr, "csc_learn_stats: tensor-core Gram wait timed out");
   return CSC_OK;
+}
+
+csc_status csc_learn_solve(csc_ctx* ctx, const float* C, const float* b, float* d, double* mu, int steps,
+                           int* cg_iters) {
+  if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_learn_solve: null context");
+  Ctx* c = &ctx->c;
+  if (c->uneven || c->video)
+    return fail(c, CSC_ERR_UNSUPPORTED, "csc_learn_solve: uniform 2-D batches only");
+  if (!C || !b || !d || !mu) return fail(c, CSC_ERR_ARG, "csc_learn_solve: null argument");
+  if (steps < 0) return fail(c, CSC_ERR_ARG, "csc_learn_solve: steps must be >= 0");
+  CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  csc_status s;
+  if ((s = learn_prepare(c, steps, "csc_learn_solve")) != CSC_OK) return s;
+  const size_t nd = (size_t)c->K * c->J * c->S2;
+  const size_t nC = (size_t)c->K * c->K * (2 * c->fh - 1) * (2 * c->fw - 1);
+  const float* dd_c;
+  if ((s = stage_in(c, (const float*)d, &c->st_d, nd, &dd_c, true)) != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(c->L.lags, C, nC * sizeof(float), cudaMemcpyDefault, c->stream), "C copy");
+  CSC_CHECK_CUDA(c, cudaMemcpyAsync(c->L.b, b, nd * sizeof(float), cudaMemcpyDefault, c->stream), "b copy");
+  CSC_CHECK_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "memset");
+  const int br = bracket_open(c, 1);
+  CSC_CHECK_CUDA(c, launch_lag_spectra(*c), "lag spectra");
+  return learn_solve_finish(c, const_cast<float*>(dd_c), d, mu, steps, cg_iters, br);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -408,6 +408,7 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
 bool video_learn_shape_ok(const Ctx& c);
 cudaError_t launch_learn_lags(const Ctx& c);       // from gram [npairs][Omega] (CUDA-core Gram)
 cudaError_t launch_learn_lags_sep(const Ctx& c);   // from the tensor-core Gram's gramT [Omega][npairs]
+cudaError_t launch_lag_spectra(const Ctx& c);      // L.chat from L.lags (both lag launchers end with it)
 size_t lag_sep_T_count(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
 bool learn_cg_shape_ok(const Ctx& c);   // filters per CTA <= 8 and 2 J NF <= 6 NT

@@ -634,7 +634,9 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   // the CTA's filters: activity, x, b
   if (threadIdx.x < nown) {
     const int k = blockIdx.x + threadIdx.x * G;
-    s_act[threadIdx.x] = a.lags[((size_t)k * K + k) * La * Lb + ctr] > 0.f;
+    const float c0 = a.lags[((size_t)k * K + k) * La * Lb + ctr];   // sum of z_k^2 over all images
+    s_act[threadIdx.x] = c0 > 0.f;
+    if (!isfinite(c0)) atomicCAS(a.err, 0, (int)CSC_ERR_NONFINITE);   // a code was not finite
   }
   for (int i = 0; i < nown; ++i) {
     const int k = blockIdx.x + i * G;
@@ -1224,7 +1226,6 @@ size_t lag_sep_T_count(const Ctx& c) {
   return (size_t)c.g.H * (2 * c.fw - 1) * ((size_t)c.K * (c.K + 1) / 2);
 }
 
-static cudaError_t launch_lag_spectra(const Ctx& c);
 
 cudaError_t launch_learn_lags_sep(const Ctx& c) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
@@ -1259,7 +1260,7 @@ cudaError_t launch_learn_lags(const Ctx& c) {
   return launch_lag_spectra(c);
 }
 
-static cudaError_t launch_lag_spectra(const Ctx& c) {
+cudaError_t launch_lag_spectra(const Ctx& c) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
   LagSpecArgs a{c.K, c.fh, c.fw, La, Lb, La * c.fw, c.L.lags, c.L.chat};
   const size_t smem = (size_t)(La * c.fw + La + Lb) * sizeof(float2) + (size_t)La * Lb * sizeof(float);
