@@ -10,13 +10,16 @@
 //
 // Per-thread frequency data (d_hat, lambda_hat, the accumulator) use the thread-major slot order
 // of f128_common.cuh; d_hat is copied into that order once per set of filter spectra
-// (k_permute_dhat).
+// (k_permute_dhat), scaled by 1/2, and lambda_hat is held scaled by 2: the products
+// conj(d_hat) lambda_hat are unchanged and the forward split's 1/2 is absorbed (all exact). The
+// passes are the packed-pair versions of f128x2.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "csc_internal.cuh"
 #include "f128_common.cuh"
+#include "f128x2.cuh"
 
 namespace csc {
 namespace f128 {
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         float2 acc2 = make_float2(-x.x * irho, -x.y * irho);
         for (int cc = c0; cc <= c1; ++cc) acc2 = cadd(acc2, a.part_in[(size_t)(cc + n) * OM + o]);
         const float2 l = cscale(acc2, a.pdiag[o]);
-        lam[p] = l;
+        lam[p] = make_float2(2.f * l.x, 2.f * l.y);
         bad |= !(isfinite(l.x) && isfinite(l.y));
         if (ls) ls[o] = l;
       }
@@ -93,38 +96,38 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
       if (kLam) {
         if (!kAcc) __syncthreads();   // the previous map's column reads precede these writes
         // w_hat = conj(d_hat_k) lambda_hat at this thread's bins, inverse split, first row pass
-        inv_rows1(buf, T, R, [&](int s) {
+        inv_rows1_x2(buf, T, R, [&](int s) {
           const int p = slot_pos(s, t);
           return cmulc(BF ? to_bf16(lam[p]) : lam[p], dval(p));
         });
         __syncthreads();
-        inv_rows2(buf, R);
+        inv_rows2_x2(buf, R);
         __syncthreads();
-        inv_cols1(buf, T, R);
+        inv_cols1_x2(buf, T, R);
         __syncthreads();
+        inv_cols2_x2(buf, R, zc);
         float2 vv[16];
         const float* vk = a.v + map * D;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
           vv[j] = __ldcs(reinterpret_cast<const float2*>(vk + (g + 8 * j) * W + 2 * wc));
-        inv_cols2(buf, R, zc);
-        // zc[out_slot<16>(j)] is w at rows h = g + 8 j: state update (and codes on the last sweep)
+        // zc[out_slot<16>(j)] is w at rows h = g + 8 j: state update (and codes on the last sweep),
+        // two pixels per packed operation
         float* vw = (a.v_out ? a.v_out : a.v) + map * D;
         float* zk = (MODE == kLast && a.z) ? a.z + map * D : nullptr;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 w = zc[out_slot<16>(j)];
           const float2 vo = vv[j];
-          float2 vn;
-          vn.x = w.x - (clampb(vo.x, beta) - vo.x);
-          vn.y = w.y - (clampb(vo.y, beta) - vo.y);
+          const float2 vn = pk_sub(w, pk_sub(pk_clamp(vo, beta), vo));   // w - (clamp(v) - v)
           __stcs(reinterpret_cast<float2*>(vw + (g + 8 * j) * W + 2 * wc), vn);
+          const float2 cn = pk_clamp(vn, beta);
           if (MODE == kLast) {
             if (zk)
               __stcs(reinterpret_cast<float2*>(zk + (g + 8 * j) * W + 2 * wc),
-                     make_float2(a.rho * (clampb(vn.x, beta) - vn.x), a.rho * (clampb(vn.y, beta) - vn.y)));
+                     pk_mul(make_float2(a.rho, a.rho), pk_sub(cn, vn)));
           } else {
-            vv[j] = make_float2(2.f * clampb(vn.x, beta) - vn.x, 2.f * clampb(vn.y, beta) - vn.y);   // u
+            vv[j] = pk_fma(vn, make_float2(-1.f, -1.f), pk_add(cn, cn));   // u = 2 clamp(v) - v
           }
         }
         if (kAcc) {
@@ -144,7 +147,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         for (int j = 0; j < 16; ++j) {
           const float2 x = zc[j];
           if (MODE == kPrologue) {
-            zc[j] = make_float2(2.f * clampb(x.x, beta) - x.x, 2.f * clampb(x.y, beta) - x.y);
+            const float2 cx = pk_clamp(x, beta);
+            zc[j] = pk_fma(x, make_float2(-1.f, -1.f), pk_add(cx, cx));
           } else {
             l1f += fabsf(x.x) + fabsf(x.y);
           }
@@ -153,22 +157,20 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
       }
 
       if (kAcc) {
-        fwd_cols1(buf, T, R, zc);
+        fwd_cols1_x2(buf, T, R, zc);
         __syncthreads();
-        fwd_cols2(buf, R);
+        fwd_cols2_x2(buf, R);
         __syncthreads();
-        fwd_rows1(buf, T, R);
+        fwd_rows1_x2(buf, T, R);
         __syncthreads();
-        // second forward row pass, split, accumulate d_hat_k u_hat (d_hat loads issued first)
-        float2 dv[18];
-#pragma unroll
-        for (int s = 0; s < 16; ++s) dv[s] = dval(s * NT + t);
-        dv[16] = dv[17] = make_float2(0.f, 0.f);
-        if (nyq) {
-          dv[16] = dval(16 * NT + t);
-          dv[17] = dval(16 * NT + NQ + t);
-        }
-        fwd_rows2_split(buf, T, R, [&](int s, float2 x) { acc[s] = cfma(dv[s], BF ? to_bf16(x) : x, acc[s]); });
+        // second forward row pass, split, accumulate d_hat_k u_hat (d_hat read where it is used)
+        fwd_rows2_split_x2(buf, T, R, [&](int s, float2 x, bool cj) {
+          const float2 xx = BF ? to_bf16(x) : x;
+          const float2 dv = dval(slot_pos(s, t));
+          acc[s] = cj ? make_float2(fmaf(dv.x, xx.x, fmaf(dv.y, xx.y, acc[s].x)),
+                                    fmaf(dv.y, xx.x, fmaf(-dv.x, xx.y, acc[s].y)))   // + d conj(x)
+                      : cfma(dv, xx, acc[s]);
+        });
       }
     }
     if (kAcc) {
@@ -191,12 +193,14 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
   }
 }
 
-__global__ void k_permute_dhat(const float2* __restrict__ in, float2* __restrict__ out, int K) {
+// out[k][p] = scale * in[k][canonical_of(p)]: spectra into the sweep's thread order
+__global__ void k_permute_dhat(const float2* __restrict__ in, float2* __restrict__ out, int K, float scale) {
   const size_t n = (size_t)K * OM;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t k = i / OM;
     const int p = (int)(i - k * OM);
-    out[i] = in[k * OM + canonical_of(p)];
+    const float2 v = in[k * OM + canonical_of(p)];
+    out[i] = make_float2(scale * v.x, scale * v.y);
   }
 }
 
@@ -235,7 +239,7 @@ cudaError_t launch_sweep_fused128(const Ctx& c, int mode, const SweepArgs& a) {
 cudaError_t launch_permute_f128(const float2* in, float2* out, int nmaps, const Ctx& c) {
   const size_t n = (size_t)nmaps * f128::OM;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);
-  f128::k_permute_dhat<<<grid, 256, 0, c.stream>>>(in, out, nmaps);
+  f128::k_permute_dhat<<<grid, 256, 0, c.stream>>>(in, out, nmaps, 1.0f);
   c.launches += 1;
   return cudaGetLastError();
 }
@@ -243,7 +247,7 @@ cudaError_t launch_permute_f128(const float2* in, float2* out, int nmaps, const 
 cudaError_t launch_permute_dhat128(const Ctx& c) {
   const size_t n = (size_t)c.K * f128::OM;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);
-  f128::k_permute_dhat<<<grid, 256, 0, c.stream>>>(c.dhat, c.dhatp, c.K);
+  f128::k_permute_dhat<<<grid, 256, 0, c.stream>>>(c.dhat, c.dhatp, c.K, 0.5f);   // d_hat / 2 (exact)
   c.launches += 1;
   return cudaGetLastError();
 }

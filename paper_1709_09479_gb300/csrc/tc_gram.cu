@@ -151,8 +151,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // round to the nearest TF32 value (10 explicit mantissa bits; ties away from zero), kept in a
 // float32 container with the 13 low bits clear
+// v rounded to the nearest TF32 value (10-bit mantissa, ties away from zero), as a float32 bit
+// pattern with the low 13 bits clear; NaN and Inf pass through unchanged
 __device__ __forceinline__ float round_tf32(float v) {
-  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r & 0xFFFFE000u);
 }
 
 struct TcGramArgs {
