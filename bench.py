@@ -732,6 +732,89 @@ def run_case(args):
     return 0
 
 
+def run_sweeps(args):
+    """Scaling and convergence sweeps on synthetic data (the paper's convergence-vs-beta and
+    scalability-in-K-and-N experiments, without the comparison systems), one JSON line:
+      beta:  Algorithm 1 on the 10-image sparse workload (N=10 grey 100x100, K=16 filters 11x11,
+             rho=10) for several beta, rounds of 20 coding + 20 learning steps until the objective's
+             relative change falls below 1e-3 (the paper's stopping threshold), at most 30 rounds:
+             rounds, wall seconds, final objective, fraction of non-zero codes, and the CG iterations of
+             every learning step (warm-started CG);
+      K, N:  one outer round (20 coding iterations + 20 learning steps) on 128x128 1/f^2 images
+             (beta=1, rho=0.1) for several K at N=100 and several N at K=100: milliseconds per round,
+             coding iterations per second, the coding sweep's device time per iteration."""
+    import torch
+    from paper_1709_09479_gb300 import csc, inputs
+    dev = torch.device("cuda", 0)
+    out = {"kind": "sweeps"}
+    # ---- beta sweep ------------------------------------------------------------------------------
+    N, H, W, K, s, rho = 10, 100, 100, 16, 11, 10.0
+    data = inputs.sparse_synthetic(seed=0, N=N, dims=(H, W), K=K, s=s, density=0.01, noise=0.01)
+    x = torch.from_numpy(data["x"].astype(np.float32)).to(dev)
+    d0 = torch.from_numpy(inputs.unit_filters(1, K, 1, (s, s)).astype(np.float32)).to(dev)
+    rows = []
+    for beta in (0.1, 0.3, 1.0, 3.0):
+        with csc.Solver(J=1, K=K, fs=(s, s), dims=(H, W), n_images=N, beta=beta, rho=rho, cg_max=400,
+                        cg_tol=1e-6) as sv:
+            d = d0.clone()
+            v = torch.zeros((N, K, H, W), device=dev)
+            z = torch.empty_like(v)
+            mu = torch.full((K,), 0.5, dtype=torch.float64, device=dev)
+            fs, cg, prev = [], [], None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rounds = 0
+            for rounds in range(1, 31):
+                sv.code(x, d, v, z, 20)
+                cg.append(sv.learn(x, z, d, mu, 20))
+                f = sv.objective(x, d, z)
+                fs.append(f)
+                if prev is not None and abs(prev - f) <= 1e-3 * abs(prev):
+                    break
+                prev = f
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            rows.append({"beta": beta, "rounds": rounds, "seconds": secs, "f_final": fs[-1], "objective": fs,
+                         "nonzero_code_fraction": float((z != 0).float().mean()),
+                         "cg_iterations_per_step": cg})
+    out["beta"] = {"workload": "sparse10: N=10 grey 100x100, K=16 filters 11x11, rho=10, stop at relative "
+                               "objective change 1e-3 (<= 30 rounds of 20 coding + 20 learning)", "runs": rows}
+
+    # ---- K and N sweeps ----------------------------------------------------------------------------
+    def one_round(N, K):
+        x = torch.from_numpy(inputs.powerlaw_field(2, N, 1, (128, 128)).astype(np.float32)).to(dev)
+        d = torch.from_numpy(inputs.unit_filters(21, K, 1, (11, 11)).astype(np.float32)).to(dev)
+        v = torch.zeros((N, K, 128, 128), device=dev)
+        z = torch.empty_like(v)
+        mu = torch.full((K,), 0.5, dtype=torch.float64, device=dev)
+        with csc.Solver(J=1, K=K, fs=(11, 11), dims=(128, 128), n_images=N, beta=1.0, rho=0.1, cg_max=100,
+                        cg_tol=1e-6) as sv:
+            for _ in range(2):
+                sv.code(x, d, v, z, 20)
+                sv.learn(x, z, d, mu, 20)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                sv.code(x, d, v, z, 20)
+                sv.learn(x, z, d, mu, 20)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            sv.timing_read()
+            sv.timing_enable(True)
+            sv.code(x, d, v, z, 20)
+            tm = sv.timing_read()
+        sweep_us = tm["sweep_ms"] / max(tm["sweep_launches"], 1) * 1e3
+        return {"N": N, "K": K, "ms_per_round": ms, "coding_iters_per_s": 20.0 / (ms / 1e3),
+                "sweep_us": sweep_us, "sweep_us_per_map": sweep_us / (N * K)}
+
+    out["K"] = [one_round(100, K) for K in (16, 32, 64, 100, 128)]
+    out["N"] = [one_round(N, 100) for N in (10, 25, 50, 100, 200)]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,6 +822,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extensions", action="store_true", help="skip the extension workloads")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="convergence-vs-beta and K/N scaling sweeps (one JSON line) instead of the benchmark")
     ap.add_argument("--case", choices=["coding", "learning", "uneven", "video"],
                     help="run one kernel family once on a fixed workload (an ncu target) instead of the benchmark")
     ap.add_argument("--N", type=int, default=100)
@@ -753,6 +838,8 @@ def main():
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.sweeps:
+        return run_sweeps(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

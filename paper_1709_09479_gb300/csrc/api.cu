@@ -589,6 +589,7 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
   }
   e = cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, 2 * sizeof(int));
+  if (e == cudaSuccess && c->dhatp) e = upload_f128_twiddles();
   c->cerr = c->err + 1;
   if (e != cudaSuccess) {
     c->last_error = std::string("csc_init: ") + cudaGetErrorString(e);

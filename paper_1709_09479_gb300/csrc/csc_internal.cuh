@@ -381,6 +381,7 @@ cudaError_t launch_fft_maps(const Ctx& c, const float* in, int nmaps, int filter
 bool fused128_applies(const Ctx& c, const SweepArgs& a);
 cudaError_t launch_sweep_fused128(const Ctx& c, int mode, const SweepArgs& a);
 cudaError_t launch_permute_dhat128(const Ctx& c);
+cudaError_t upload_f128_twiddles();   // the fused sweep's constant twiddle tables, current device
 cudaError_t launch_solve_prep(const Ctx& c);
 cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                          float* z);

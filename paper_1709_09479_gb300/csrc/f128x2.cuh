@@ -11,7 +11,9 @@
 //     one sum, one difference and one twiddle product (w^(64 - kw) = -conj(w^kw)): for the 12 of 16
 //     warps whose items are not self-paired (class c >= 1) the split costs half the scalar form.
 //     The forward split's factor 1/2 is left out (the sweep stores d_hat / 2 in thread order and
-//     scales lambda_hat by 2, which is exact).
+//     scales lambda_hat by 2, which is exact);
+//   * the twiddle tables sit in constant memory: every pass reads them at warp-uniform indices, so
+//     they come through the constant cache and leave the shared-memory pipe to the spectrum.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -19,6 +21,27 @@
 
 namespace csc {
 namespace f128 {
+
+// The tables of f128_common.cuh's build_tw in 16-byte pairs: c_twq4[8 a + i] holds q entries
+// 16 a + 2 i and 16 a + 2 i + 1 (w^(a m mod 128)), c_tws4[4 k + i] holds s entries 8 k + 2 i and
+// 8 k + 2 i + 1 (w^(k + 8 j)); w = exp(-2 pi i / 128). Written once per device by
+// upload_f128_twiddles (sweep128.cu).
+__constant__ float4 c_twq4[128];
+__constant__ float4 c_tws4[32];
+CSC_D void twc_split(float4 v, float2& w0, float2& w1) {
+  w0 = make_float2(v.x, v.y);
+  w1 = make_float2(v.z, v.w);
+}
+// the first 8 entries of q row a, all 8 entries of s row k, and q entries 16 a + 2 i, 16 a + 2 i + 1
+CSC_D void twc_row8_q(int a, float2 (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) twc_split(c_twq4[8 * a + i], w[2 * i], w[2 * i + 1]);
+}
+CSC_D void twc_row8_s(int k, float2 (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) twc_split(c_tws4[4 * k + i], w[2 * i], w[2 * i + 1]);
+}
+CSC_D void twc_pair_q(int a, int i, float2& w0, float2& w1) { twc_split(c_twq4[8 * a + i], w0, w1); }
 
 CSC_D float2 pk_add(float2 a, float2 b) { return __ffma2_rn(b, make_float2(1.f, 1.f), a); }
 CSC_D float2 pk_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
@@ -113,7 +136,7 @@ CSC_D void inv_rows1_x2(float2* buf, const Tw& T, const Roles& R, GET get) {
     za[j] = get(j);
     zb[j] = get(8 + j);
   }
-  tw_row8(T.s + 8 * it.kA, wa);
+  twc_row8_s(it.kA, wa);
   if (R.c != 0) {
     // pairs (A_j, B_{7-j}), j < 4, and (A_{7-j}, B_j), split in place
 #pragma unroll
@@ -133,7 +156,7 @@ CSC_D void inv_rows1_x2(float2* buf, const Tw& T, const Roles& R, GET get) {
       na = get(16);
       nb = get(17);
     }
-    tw_row8(T.s + 8 * it.kB, wb);
+    twc_row8_s(it.kB, wb);
     const bool sf = it.self, cls0 = R.cls0;
     float2 xa[8], xb[8];
 #pragma unroll
@@ -156,8 +179,8 @@ CSC_D void inv_rows1_x2(float2* buf, const Tw& T, const Roles& R, GET get) {
   x2_dft8<true>(zb);
   float2* ra = buf + it.rowA * P + 8 * it.kA;
   float2* rb = buf + it.rowB * P + 8 * it.kB;
-  tw_row8(T.q + 16 * (2 * it.kA), wa);
-  tw_row8(T.q + 16 * (2 * it.kB), wb);
+  twc_row8_q(2 * it.kA, wa);
+  twc_row8_q(2 * it.kB, wb);
   ra[0] = za[0];
   rb[0] = zb[0];
 #pragma unroll
@@ -190,7 +213,7 @@ CSC_D void inv_cols1_x2(float2* buf, const Tw& T, const Roles& R) {
     float2 y[8], w[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = buf[(16 * q + n2) * P + R.wc];
-    tw_row8(T.q + 16 * n2, w);
+    twc_row8_q(n2, w);
     x2_dft8<true>(y);
     buf[n2 * P + R.wc] = y[0];
 #pragma unroll
@@ -212,7 +235,7 @@ CSC_D void fwd_cols1_x2(float2* buf, const Tw& T, const Roles& R, float2 (&zc)[1
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     float2 w0, w1;
-    tw_pair(T.q + 16 * R.g, i, w0, w1);
+    twc_pair_q(R.g, i, w0, w1);
     if (i > 0) buf[(16 * R.g + 2 * i) * P + R.wc] = cmul(zc[out_slot<16>(2 * i)], w0);
     buf[(16 * R.g + 2 * i + 1) * P + R.wc] = cmul(zc[out_slot<16>(2 * i + 1)], w1);
   }
@@ -241,7 +264,7 @@ CSC_D void fwd_rows1_x2(float2* buf, const Tw& T, const Roles& R) {
     float2 y[8], w[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = row[8 * q + n2];
-    tw_row8(T.q + 16 * (2 * n2), w);
+    twc_row8_q(2 * n2, w);
     x2_dft8<false>(y);
     row[n2] = y[0];
 #pragma unroll
@@ -267,7 +290,7 @@ CSC_D void fwd_rows2_split_x2(const float2* buf, const Tw& T, const Roles& R, PU
   x2_dft8<false>(ya);
   x2_dft8<false>(yb);
   float2 wa[8];
-  tw_row8(T.s + 8 * it.kA, wa);
+  twc_row8_s(it.kA, wa);
   if (R.c != 0) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -281,7 +304,7 @@ CSC_D void fwd_rows2_split_x2(const float2* buf, const Tw& T, const Roles& R, PU
     return;
   }
   float2 wb[8];
-  tw_row8(T.s + 8 * it.kB, wb);
+  twc_row8_s(it.kB, wb);
   const bool sf = it.self, cls0 = R.cls0;
 #define CSC_F128X2_SPLIT(J)                                                                       \
   {                                                                                               \

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "csc_internal.cuh"
 #include "f128_common.cuh"
@@ -37,9 +38,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
   constexpr bool kAcc = (MODE != kLast);
   float2* buf = sm;                                   // [128][P]
   float2* lam = buf + H * P;                          // [OM] thread-major
-  float2* twt = lam + (kLam ? OM : 0);                // twiddle tables (kTwEntries)
   const int t = threadIdx.x;
-  const Tw T = build_tw<NT>(twt, a.tw + W / 2);
+  const Tw T{nullptr, nullptr};   // the passes read their twiddles from constant memory
 
   const Roles R = roles_of(t);
   const int wc = R.wc, g = R.g;
@@ -206,7 +206,7 @@ __global__ void k_permute_dhat(const float2* __restrict__ in, float2* __restrict
 
 size_t smem_bytes(int mode) {
   const bool lam = (mode == kIter || mode == kLast);
-  return ((size_t)H * P + (lam ? OM : 0) + kTwEntries) * sizeof(float2);
+  return ((size_t)H * P + (lam ? OM : 0)) * sizeof(float2);
 }
 
 template <int MODE, bool BF>
@@ -220,6 +220,29 @@ cudaError_t launch_mode(const Ctx& c, const SweepArgs& a) {
 }
 
 }  // namespace f128
+
+// the constant-memory twiddle tables of the 128 x 128 sweep on the current device (float64 then
+// rounded once); every 128 x 128 context writes the same values
+cudaError_t upload_f128_twiddles() {
+  const double pi2 = 6.283185307179586476925286766559;
+  auto w = [&](int m) {
+    return make_float2((float)std::cos(pi2 * m / 128.0), (float)-std::sin(pi2 * m / 128.0));
+  };
+  float4 q4[128], s4[32];
+  for (int a = 0; a < 16; ++a)
+    for (int i = 0; i < 8; ++i) {
+      const float2 w0 = w((a * (2 * i)) & 127), w1 = w((a * (2 * i + 1)) & 127);
+      q4[8 * a + i] = make_float4(w0.x, w0.y, w1.x, w1.y);
+    }
+  for (int k = 0; k < 8; ++k)
+    for (int i = 0; i < 4; ++i) {
+      const float2 w0 = w(k + 8 * (2 * i)), w1 = w(k + 8 * (2 * i + 1));
+      s4[4 * k + i] = make_float4(w0.x, w0.y, w1.x, w1.y);
+    }
+  cudaError_t e = cudaMemcpyToSymbol(f128::c_twq4, q4, sizeof(q4));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(f128::c_tws4, s4, sizeof(s4));
+  return e;
+}
 
 bool fused128_applies(const Ctx& c, const SweepArgs& a) {
   return c.dhatp && c.g.ct_id == 1 && c.J == 1 && a.vec4 && (a.dhat16 == nullptr || c.dhatp16 != nullptr);
