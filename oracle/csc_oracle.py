@@ -20,7 +20,9 @@ Parity pins for every function are in tests/test_oracle_*.py. The entry points:
 ``code_admm`` (v-state form) and ``code_admm_textbook`` (the three-variable update of Sec. 3.2);
 ``learn_paper`` (Sec. 3.2, learning: gamma by CG, d recovery, mu fixed point, final projection);
 ``csc_alternate`` (Algorithm 1); ``objective`` (Eq. 1); ``duality_gap``; ``fista_code``;
-``unrolled_loss_and_grad`` (adjoint of T unrolled coding iterations, not in the paper).
+``unrolled_loss_and_grad`` (adjoint of T unrolled coding iterations, not in the paper);
+``code_admm_symmetric`` and ``code_admm_dct`` (reflected image boundaries: the DCT variant the paper
+mentions at the start of Sec. 3).
 """
 from __future__ import annotations
 
@@ -102,6 +104,62 @@ def objective(x, d, z, beta):
     """Eq. 1 summed over images: 1/2 ||x - sum_k d_k * z_k||^2 + beta * sum ||z_k||_1."""
     r = x - synthesize(d, z)
     return 0.5 * float(np.sum(r * r)) + beta * float(np.sum(np.abs(z)))
+
+
+# --------------------------------------------------------------------------------------------
+# Symmetric boundary: the DCT variant mentioned at the start of Sec. 3
+# --------------------------------------------------------------------------------------------
+
+def symmetric_extend(a):
+    """Half-sample symmetric extension of the last two axes, (..., H, W) -> (..., 2H, 2W):
+    rows H..2H-1 repeat rows H-1..0 and columns likewise. Circular convolution on the extension is
+    convolution with reflected boundaries on the image."""
+    a = np.concatenate([a, a[..., ::-1, :]], axis=-2)
+    return np.concatenate([a, a[..., :, ::-1]], axis=-1)
+
+
+def code_admm_symmetric(x, d, beta, rho, iters, v0=None):
+    """Coding with reflected (symmetric) image boundaries: the dual ADMM of ``code_admm`` on the
+    symmetric extension of the images (2H x 2W), whose circular boundary is the image's reflection.
+    Returns (v, z) on the extended grid (N, K, 2H, 2W)."""
+    return code_admm(symmetric_extend(x), d, beta, rho, iters, v0)
+
+
+def dct_eigenvalues(d, dims):
+    """delta_k(u, v) = sum_(a, b) d_k(a, b) cos(pi u a / H) cos(pi v b / W) over the centred tap offsets
+    (a, b): for a filter symmetric about its centre, d(-a, -b) = d(a, b), convolution with reflected
+    boundaries is diagonal in the type-II DCT with these eigenvalues. d (K, fh, fw) -> (K, H, W)."""
+    H, W = dims
+    K, fh, fw = d.shape
+    oa = np.arange(fh) - (fh - 1) // 2
+    ob = np.arange(fw) - (fw - 1) // 2
+    ca = np.cos(np.pi * np.outer(np.arange(H), oa) / H)     # (H, fh)
+    cb = np.cos(np.pi * np.outer(np.arange(W), ob) / W)     # (W, fw)
+    return np.einsum("ua,kab,vb->kuv", ca, d, cb)
+
+
+def code_admm_dct(x, d, beta, rho, iters):
+    """The dual ADMM of Eq. Inference_solution with the type-II DCT in place of the DFT (grey images,
+    filters symmetric about their centre): D_k = C^T diag(delta_k) C with C the orthonormal 2-D DCT,
+    so the lambda system is diagonal with entries sum_k delta_k^2 + 1/rho. x (N, 1, H, W),
+    d (K, 1, fh, fw). Returns (v, z), each (N, K, H, W)."""
+    dims = x.shape[2:]
+    N, K = x.shape[0], d.shape[0]
+    delta = dct_eigenvalues(d[:, 0], dims)                           # (K, H, W)
+    C = lambda a: sfft.dctn(a, type=2, axes=(-2, -1), norm="ortho")
+    Ci = lambda a: sfft.idctn(a, type=2, axes=(-2, -1), norm="ortho")
+    xc = C(x[:, 0])                                                  # (N, H, W)
+    denom = np.sum(delta ** 2, axis=0) + 1.0 / rho
+    v = np.zeros((N, K) + tuple(dims))
+    for _ in range(iters):
+        c = np.clip(v, -beta, beta)
+        u = 2.0 * c - v
+        r = np.einsum("kuv,nkuv->nuv", delta, C(u)) - xc / rho
+        lam = r / denom
+        w = Ci(delta[None] * lam[:, None])
+        v = w - (c - v)
+    z = rho * (np.clip(v, -beta, beta) - v)
+    return v, z
 
 
 # --------------------------------------------------------------------------------------------
