@@ -96,6 +96,17 @@ typedef struct {
 /* csc_learn returns CSC_ERR_NOT_CONVERGED (after writing d, mu and cg_iters) when a step's CG stopped
    at params->cg_max iterations; without the flag that case returns CSC_OK and shows in cg_iters. */
 #define CSC_FLAG_CG_STRICT 4
+/* csc_init only: reflected image boundaries instead of circular ones - the DCT variant the paper
+   mentions at the start of Sec. 3. dims = {H, W} is the size of the caller's images x [N][J][H][W];
+   the context codes their half-sample symmetric extension (2H x 2W: rows H..2H-1 repeat rows
+   H-1..0, columns likewise), whose circular convolution is convolution with reflected boundaries
+   on the image, so v and z are [N][K][2H][2W] and csc_objective is the objective of the extended
+   problem. For filters symmetric about their centre this is exactly the dual ADMM in the type-II DCT
+   domain of the H x W images, and the extended codes are mirror symmetric (their [0, H) x [0, W)
+   block holds all of them). 2H x 2W must satisfy csc_init's size conditions. csc_code, csc_learn,
+   csc_learn_stats and csc_objective take x at H x W; the reverse-mode calls return
+   CSC_ERR_UNSUPPORTED. */
+#define CSC_FLAG_SYMMETRIC_BOUNDARY 8
 
 /*
  * Create a context for n_images images, all of size H x W (dims = {H, W}), on the current CUDA

@@ -117,7 +117,7 @@ void free_all(Ctx* c) {
     cudaEventDestroy(ep.b);
   }
   c->events.clear();
-  void* ptrs[] = {c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->L.zt, c->L.lagT, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
+  void* ptrs[] = {c->xext, c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->L.zt, c->L.lagT, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
                   c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
@@ -521,11 +521,20 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
   if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter support must be odd and >= 1");
   if (fw > 15) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter width must be <= 15");
-  const int H = dims[0], W = dims[1];
+  // symmetric boundary: the context codes the half-sample symmetric extension (2H x 2W)
+  const bool sym = !video && (p.flags & CSC_FLAG_SYMMETRIC_BOUNDARY);
+  if (video && (p.flags & CSC_FLAG_SYMMETRIC_BOUNDARY))
+    return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_video: no symmetric boundary on video contexts");
+  const int H0 = dims[0], W0 = dims[1];
+  if (sym && (H0 < 4 || W0 < 4)) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: symmetric boundary needs H, W >= 4");
+  const int H = sym ? 2 * H0 : H0, W = sym ? 2 * W0 : W0;
   if (H < 8 || W < 8 || (W & 1)) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: need H, W >= 8 and W even");
   if (fh > H || fw > W) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: filter larger than the image");
 
   Ctx tmp;
+  tmp.sym = sym;
+  tmp.H0 = H0;
+  tmp.W0 = W0;
   tmp.p = p;
   tmp.N = n_images; tmp.J = p.J; tmp.K = p.K; tmp.fh = fh; tmp.fw = fw; tmp.S2 = fh * fw;
   Geometry& g = tmp.g;
@@ -582,7 +591,8 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
       cudaMalloc((void**)&c->part[1], (size_t)(tmp.G + tmp.N) * p.J * Om * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&c->l1, tmp.G * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->objimg, tmp.N * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&c->err, 2 * sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void**)&c->err, 2 * sizeof(int)) != cudaSuccess ||
+      (sym && cudaMalloc((void**)&c->xext, (size_t)tmp.N * p.J * g.D * sizeof(float)) != cudaSuccess)) {
     cudaGetLastError();
     c->last_error = "csc_init: device workspace allocation failed";
     return bail(CSC_ERR_WORKSPACE);
@@ -900,12 +910,29 @@ void csc_destroy(csc_ctx* ctx) {
   delete ctx;
 }
 
+// symmetric-boundary contexts: stage the caller's H x W images (host or device) and write their
+// half-sample symmetric extension into the context's 2H x 2W image buffer, which the call then uses
+static csc_status sym_images(Ctx* c, const float** x) {
+  if (!c->sym) return CSC_OK;
+  const float* xd = nullptr;
+  csc_status s = stage_in(c, *x, &c->st_x, (size_t)c->N * c->J * c->H0 * c->W0, &xd, true);
+  if (s != CSC_OK) return s;
+  CSC_CHECK_CUDA(c, launch_symmetric_extend(*c, xd, c->xext), "symmetric extension");
+  c->launches += 1;
+  *x = c->xext;
+  return CSC_OK;
+}
+
 csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, float* z, int iters) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code: null context");
   Ctx* c = &ctx->c;
   if (!x || !d || !v) return fail(c, CSC_ERR_ARG, "csc_code: x, d and v must be non-null");
   if (iters < 0) return fail(c, CSC_ERR_ARG, "csc_code: iters must be >= 0");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  {
+    const csc_status s0 = (iters > 0) ? sym_images(c, &x) : CSC_OK;
+    if (s0 != CSC_OK) return s0;
+  }
   if (c->video) return video_code(c, x, d, v, z, iters);
   const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
   const size_t nd = (size_t)c->K * c->J * c->S2;
@@ -1043,6 +1070,10 @@ csc_status csc_objective(csc_ctx* ctx, const float* x, const float* d, const flo
   Ctx* c = &ctx->c;
   if (!x || !d || !z || !out) return fail(c, CSC_ERR_ARG, "csc_objective: null argument");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  {
+    const csc_status s0 = sym_images(c, &x);
+    if (s0 != CSC_OK) return s0;
+  }
   if (c->video) return video_objective(c, x, d, z, out);
   const size_t nx = c->uneven ? (size_t)c->U.n_x : (size_t)c->N * c->J * c->g.D;
   const size_t nd = (size_t)c->K * c->J * c->S2;
@@ -1235,6 +1266,7 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
     return CSC_OK;
   }
   csc_status s;
+  if ((s = sym_images(c, &x)) != CSC_OK) return s;
   if ((s = learn_prepare(c, steps, "csc_learn")) != CSC_OK) return s;
   const size_t nx = (size_t)c->N * c->J * c->g.D, nd = (size_t)c->K * c->J * c->S2;
   const size_t nz = (size_t)c->N * c->K * c->g.D;
@@ -1256,6 +1288,7 @@ csc_status csc_learn_stats(csc_ctx* ctx, const float* x, const float* z, float* 
   if (!x || !z || !C || !b) return fail(c, CSC_ERR_ARG, "csc_learn_stats: null argument");
   CSC_CHECK_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   csc_status s;
+  if ((s = sym_images(c, &x)) != CSC_OK) return s;
   if ((s = learn_prepare(c, 0, "csc_learn_stats")) != CSC_OK) return s;
   const size_t nx = (size_t)c->N * c->J * c->g.D, nz = (size_t)c->N * c->K * c->g.D;
   const size_t nd = (size_t)c->K * c->J * c->S2;
@@ -1360,7 +1393,7 @@ csc_status ensure_spec(Ctx* c) {
 }  // namespace
 
 size_t csc_tape_bytes(const csc_ctx* ctx, int iters, int every) {
-  if (!ctx || iters < 1 || every < 1 || ctx->c.uneven || ctx->c.video) return 0;   // no reverse mode there
+  if (!ctx || iters < 1 || every < 1 || ctx->c.uneven || ctx->c.video || ctx->c.sym) return 0;   // no reverse mode there
   return tape_layout(ctx->c, iters, every).total;
 }
 
@@ -1368,7 +1401,8 @@ csc_status csc_code_unrolled(csc_ctx* ctx, const float* x, const float* d, float
                              int every, void* tape) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_unrolled: null context");
   Ctx* c = &ctx->c;
-  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on an uneven-batch context");
+  if (c->uneven || c->sym)
+    return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on uneven-batch or symmetric-boundary contexts");
   if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_unrolled: not available on a video context");
   if (!x || !d || !v || !tape || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_unrolled: null array, iters < 1 or every < 1");
@@ -1406,7 +1440,8 @@ csc_status csc_code_backward(csc_ctx* ctx, const float* x, const float* d, const
                              const float* gz, float* gx, float* gd) {
   if (!ctx) return fail(nullptr, CSC_ERR_ARG, "csc_code_backward: null context");
   Ctx* c = &ctx->c;
-  if (c->uneven) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on an uneven-batch context");
+  if (c->uneven || c->sym)
+    return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on uneven-batch or symmetric-boundary contexts");
   if (c->video) return fail(c, CSC_ERR_UNSUPPORTED, "csc_code_backward: not available on a video context");
   if (!x || !d || !tape || !gz || !gx || !gd || iters < 1 || every < 1)
     return fail(c, CSC_ERR_ARG, "csc_code_backward: null array, iters < 1 or every < 1");

@@ -229,6 +229,29 @@ cudaError_t launch_sum_slots(const Ctx& c, const float2* part, float2* out) {
   return cudaGetLastError();
 }
 
+// the half-sample symmetric extension of each H0 x W0 plane: pixel (h, w) of the 2 H0 x 2 W0 plane
+// reads (m(h, H0), m(w, W0)) with m(i, n) = i for i < n and 2 n - 1 - i otherwise
+__global__ void k_symmetric_extend(const float* __restrict__ in, float* __restrict__ out, long long planes, int H0,
+                                   int W0) {
+  const int W = 2 * W0;
+  const long long per = 4LL * H0 * W0, n = planes * per;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long pl = i / per;
+    const int r = (int)(i - pl * per);
+    const int h = r / W, w = r - h * W;
+    const int hs = h < H0 ? h : 2 * H0 - 1 - h, ws = w < W0 ? w : 2 * W0 - 1 - w;
+    out[i] = in[pl * H0 * W0 + (long long)hs * W0 + ws];
+  }
+}
+
+cudaError_t launch_symmetric_extend(const Ctx& c, const float* in, float* out) {
+  const long long planes = (long long)c.N * c.J;
+  const long long n = planes * 4LL * c.H0 * c.W0;
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)c.nsm * 8);
+  k_symmetric_extend<<<grid, 256, 0, c.stream>>>(in, out, planes, c.H0, c.W0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_codes_from_state_n(const Ctx& c, const float* v, float* z, size_t n) {
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)c.nsm * 8);
   k_codes_from_state<<<grid, 256, 0, c.stream>>>(v, z, n, (float)c.p.beta, (float)c.p.rho);

@@ -281,6 +281,11 @@ struct BackwardBuffers {
 struct Ctx {
   csc_params p;
   int N, J, K, fh, fw, S2;
+  // symmetric image boundary (CSC_FLAG_SYMMETRIC_BOUNDARY): the caller's images are H0 x W0, the
+  // context codes their half-sample symmetric extension (g = 2 H0 x 2 W0) from xext
+  bool sym = false;
+  int H0 = 0, W0 = 0;
+  float* xext = nullptr;
   Geometry g;
   cudaStream_t stream;
   int device = 0, nsm = 0;
@@ -386,6 +391,8 @@ cudaError_t launch_solve_prep(const Ctx& c);
 cudaError_t launch_sweep(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
                          float* z);
 cudaError_t launch_codes_from_state(const Ctx& c, const float* v, float* z);
+// out [N J][2 H0][2 W0] = half-sample symmetric extension of in [N J][H0][W0] (symmetric boundary)
+cudaError_t launch_symmetric_extend(const Ctx& c, const float* in, float* out);
 cudaError_t launch_codes_from_state_n(const Ctx& c, const float* v, float* z, size_t n);
 cudaError_t launch_objective_final(const Ctx& c, const float2* part, double* out_img);
 cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float2* part_out, float* v,
