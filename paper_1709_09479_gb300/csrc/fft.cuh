@@ -101,6 +101,24 @@ template <bool INV> CSC_D float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// init + sum of the partial sums p[c * stride] over slots c = c0..c1 (the CTAs that covered an
+// image), in a fixed order: four running sums over c = c0 + 4 i + r, added as (s0 + s1) + (s2 + s3),
+// so that four loads are in flight at a time when an image spans many CTAs
+CSC_D float2 sum_slots_at(const float2* __restrict__ p, size_t stride, int c0, int c1, float2 init) {
+  float2 s0 = init, s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+  int c = c0;
+  for (; c + 3 <= c1; c += 4) {
+    const float2 v0 = p[(size_t)c * stride], v1 = p[(size_t)(c + 1) * stride];
+    const float2 v2 = p[(size_t)(c + 2) * stride], v3 = p[(size_t)(c + 3) * stride];
+    s0 = cadd(s0, v0);
+    s1 = cadd(s1, v1);
+    s2 = cadd(s2, v2);
+    s3 = cadd(s3, v3);
+  }
+  for (; c <= c1; ++c) s0 = cadd(s0, p[(size_t)c * stride]);
+  return cadd(cadd(s0, s1), cadd(s2, s3));
+}
+
 // ---------------------------------------------------------------------------------------------
 // small DFTs in registers (outputs in natural order)
 // ---------------------------------------------------------------------------------------------

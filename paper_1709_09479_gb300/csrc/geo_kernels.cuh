@@ -111,9 +111,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
         for (int j = 0; j < kMaxJ; ++j) {
           if (j < J) {
             const float2 x = xh[(size_t)j * Om + o];
-            float2 s = make_float2(-x.x * irho, -x.y * irho);
-            for (int c = c0; c <= c1; ++c) s = cadd(s, a.part_in[((size_t)(c + n) * J + j) * Om + o]);
-            r[j] = s;
+            r[j] = sum_slots_at(a.part_in + ((size_t)n * J + j) * Om + o, (size_t)J * Om, c0, c1,
+                                make_float2(-x.x * irho, -x.y * irho));
           }
         }
         float2* ls = (a.lam_store && cta == c0) ? a.lam_store + (size_t)n * J * Om : nullptr;

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         const int p = slot_pos(s, t);
         const int o = canonical_of(p);
         const float2 x = xh[o];
-        float2 acc2 = make_float2(-x.x * irho, -x.y * irho);
-        for (int cc = c0; cc <= c1; ++cc) acc2 = cadd(acc2, a.part_in[(size_t)(cc + n) * OM + o]);
+        const float2 acc2 = sum_slots_at(a.part_in + (size_t)n * OM + o, OM, c0, c1,
+                                         make_float2(-x.x * irho, -x.y * irho));
         const float2 l = cscale(acc2, a.pdiag[o]);
         lam[p] = make_float2(2.f * l.x, 2.f * l.y);
         bad |= !(isfinite(l.x) && isfinite(l.y));
