@@ -163,10 +163,19 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         __syncthreads();
         fwd_rows1_x2(buf, T, R);
         __syncthreads();
-        // second forward row pass, split, accumulate d_hat_k u_hat (d_hat read where it is used)
+        // second forward row pass, split, accumulate d_hat_k u_hat. The d_hat values of the first
+        // three bin pairs (slots 0-2 and 13-15) are loaded before the row transforms, the rest where
+        // they are used (registers allow no more in flight)
+        constexpr int kPre = 3;
+        float2 dpre[2 * kPre];
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+          dpre[i] = dval(i * NT + t);
+          dpre[kPre + i] = dval((15 - i) * NT + t);
+        }
         fwd_rows2_split_x2(buf, T, R, [&](int s, float2 x, bool cj) {
           const float2 xx = BF ? to_bf16(x) : x;
-          const float2 dv = dval(slot_pos(s, t));
+          const float2 dv = (s < kPre) ? dpre[s] : (s > 15 - kPre && s < 16) ? dpre[kPre + 15 - s] : dval(slot_pos(s, t));
           acc[s] = cj ? make_float2(fmaf(dv.x, xx.x, fmaf(dv.y, xx.y, acc[s].x)),
                                     fmaf(dv.y, xx.x, fmaf(-dv.x, xx.y, acc[s].y)))   // + d conj(x)
                       : cfma(dv, xx, acc[s]);
