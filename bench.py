@@ -216,10 +216,10 @@ def time_to_target(csc, torch, dev, schedule="fp32", graph=False, repeats=5):
     """Rounds of Algorithm 1 on the 10-image sparse workload until the objective is within 1e-4
     relative of the float64 oracle's final objective; then the wall time of that many rounds, best
     and spread over `repeats` timed runs.
-    schedule: "fp32" (CSC_FP32 throughout), "bf16" (CSC_MIXED_BF16 throughout) or "bf16>fp32"
-    (CSC_MIXED_BF16 in the first half of the rounds, CSC_FP32 after: a precision schedule, the
-    bf16 rounds' error floor removed by the float32 rounds); graph: CUDA-graph replay of the coding
-    calls."""
+    schedule: "fp32" (CSC_FP32 throughout), "bf16" / "tf32" (CSC_MIXED_BF16 / CSC_MIXED_TF32
+    throughout) or "bf16>fp32" / "tf32>fp32" (the reduced precision in the first half of the rounds,
+    CSC_FP32 after: a precision schedule, the low-precision rounds' error floor removed by the float32
+    rounds); graph: CUDA-graph replay of the coding calls."""
     ref_path = os.path.join(ROOT, "tests", "golden", "sparse10_oracle.json")
     if not os.path.exists(ref_path):
         return None
@@ -237,9 +237,11 @@ def time_to_target(csc, torch, dev, schedule="fp32", graph=False, repeats=5):
                           beta=c["beta"], rho=c["rho"], cg_max=400, cg_tol=1e-6, precision=prec,
                           flags=csc.CSC_FLAG_GRAPH if graph else 0)
 
-    sv_fp = solver(csc.CSC_FP32) if schedule != "bf16" else None
-    sv_bf = solver(csc.CSC_MIXED_BF16) if schedule != "fp32" else None
-    n_bf = {"fp32": 0, "bf16": c["n_outer"], "bf16>fp32": c["n_outer"] // 2}[schedule]
+    lo = csc.CSC_MIXED_TF32 if schedule.startswith("tf32") else csc.CSC_MIXED_BF16
+    sv_fp = solver(csc.CSC_FP32) if schedule not in ("bf16", "tf32") else None
+    sv_bf = solver(lo) if schedule != "fp32" else None
+    n_bf = {"fp32": 0, "bf16": c["n_outer"], "tf32": c["n_outer"], "bf16>fp32": c["n_outer"] // 2,
+            "tf32>fp32": c["n_outer"] // 2}[schedule]
 
     def rounds(n, log):
         d = d0.clone()
@@ -646,7 +648,7 @@ def run_ours(args):
 
     ttt = None
     if rank == 0:
-        forms = [("fp32", False), ("fp32", True), ("bf16", True), ("bf16>fp32", True)]
+        forms = [("fp32", False), ("fp32", True), ("tf32", False), ("tf32", True), ("bf16", True), ("bf16>fp32", True)]
         runs = {f"{sch}{'_graph' if g else ''}": time_to_target(csc, torch, dev, schedule=sch, graph=g)
                 for sch, g in forms}
         if runs["fp32"] is not None:

@@ -54,7 +54,7 @@ typedef enum {
 
 typedef enum {
   CSC_FP32 = 0,        /* everything in float32 */
-  CSC_MIXED_BF16 = 1   /* FFTs, shrinkage and CG in float32; the per-frequency contractions with
+  CSC_MIXED_BF16 = 1,  /* FFTs, shrinkage and CG in float32; the per-frequency contractions with
                           bfloat16 operands and float32 accumulation: sum_k d_hat_k u_hat_k and
                           conj(d_hat_k) lambda_hat in the coding sweep (CUDA cores), and the code Gram
                           Z(w)^H Z(w) of csc_learn on the tensor cores (tcgen05 kind::f16). In
@@ -65,6 +65,11 @@ typedef enum {
                           it; video contexts,
                           csc_code_unrolled, csc_code_backward and the synthesis calls accept
                           CSC_FP32 only. */
+  CSC_MIXED_TF32 = 2   /* as CSC_MIXED_BF16 with TF32 operands (10 explicit mantissa bits, rounded to
+                          nearest, ties away from zero): both operands of sum_k d_hat_k u_hat_k and of
+                          conj(d_hat_k) lambda_hat rounded to TF32 in the coding sweeps, float32
+                          accumulation; the code Gram as one TF32 tensor-core product (kind::tf32)
+                          instead of CSC_FP32's three. Uniform batches only (csc_init). */
 } csc_precision;
 
 typedef struct {

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "CSC_OK", 1: "CSC_ERR_ARG", 2: "CSC_ERR_SHAPE", 3: "CSC_ERR_W
                 8: "CSC_ERR_UNSUPPORTED"}
 CSC_FP32 = 0
 CSC_MIXED_BF16 = 1
+CSC_MIXED_TF32 = 2
 CSC_FLAG_GRAPH = 1
 CSC_FLAG_CHECK_FINITE = 2
 CSC_FLAG_CG_STRICT = 4

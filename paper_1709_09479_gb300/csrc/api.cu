@@ -512,7 +512,7 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
   if (!(p.beta > 0) || !(p.rho > 0) || !std::isfinite(p.beta) || !std::isfinite(p.rho))
     return fail(nullptr, CSC_ERR_ARG, "csc_init: beta and rho must be finite and > 0");
   if (p.cg_max < 1 || !(p.cg_tol > 0)) return fail(nullptr, CSC_ERR_ARG, "csc_init: cg_max >= 1, cg_tol > 0");
-  if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16)
+  if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16 && p.precision != CSC_MIXED_TF32)
     return fail(nullptr, CSC_ERR_ARG, "csc_init: unknown precision");
   if (p.precision == CSC_MIXED_BF16) {
     if (p.K > 128) return fail(nullptr, CSC_ERR_SHAPE, "csc_init: CSC_MIXED_BF16 needs K <= 128");
@@ -619,6 +619,8 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   if (p.K < 1) return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: K must be >= 1");
   if (!(p.beta > 0) || !(p.rho > 0) || !std::isfinite(p.beta) || !std::isfinite(p.rho))
     return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: beta and rho must be finite and > 0");
+  if (p.precision == CSC_MIXED_TF32)
+    return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: CSC_MIXED_TF32 is for uniform batches");
   if (p.precision != CSC_FP32 && p.precision != CSC_MIXED_BF16)
     return fail(nullptr, CSC_ERR_ARG, "csc_init_uneven: unknown precision");
   const int fh = p.fs[0], fw = p.fs[1];
@@ -1180,7 +1182,7 @@ static csc_status learn_stats_enqueue(Ctx* c, const float* xd, const float* zd) 
   if (gram_tc_applies(*c)) {
     CSC_CHECK_CUDA(c, launch_code_spectra(*c, zd, c->N * K, L.zhat), "code spectra");
     CSC_CHECK_CUDA(c, launch_spectra_transpose(*c, L.zhat, c->N * K, L.zt), "code spectra transpose");
-    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, c->p.precision == CSC_MIXED_BF16, L.rspec, c->err),
+    CSC_CHECK_CUDA(c, launch_learn_gram_tc(*c, c->p.precision, L.rspec, c->err),
                    "code Gram (tensor cores)");
     CSC_CHECK_CUDA(c, launch_learn_rhs(*c, L.rspec), "learning right-hand side");
     CSC_CHECK_CUDA(c, launch_learn_lags_sep(*c), "code lags");

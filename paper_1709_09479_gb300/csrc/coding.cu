@@ -203,6 +203,7 @@ cudaError_t launch_sweep_ex(const Ctx& c, int mode, const float2* part_in, float
   a.v_out = v_out;
   a.lam_store = lam_store;
   a.err = c.cerr;
+  a.tf32 = (c.p.precision == CSC_MIXED_TF32 && mode != kObjective) ? 1 : 0;
   // the bf16 copy of d_hat is refreshed by csc_code only; the objective stays float32
   a.dhat16 = (c.p.precision == CSC_MIXED_BF16 && mode != kObjective) ? c.dhat16 : nullptr;
   const bool al = ((uintptr_t)v % 16 == 0) && ((uintptr_t)z % 16 == 0) && ((uintptr_t)v_out % 16 == 0);

@@ -41,6 +41,7 @@ struct SweepArgs {
   const __nv_bfloat162* dhat16;  // mixed precision: d_hat in bf16; contraction operands rounded to bf16
   float2* lam_store;     // iterate/last: lambda_hat / D of each image stored here [N][J][Omega] (may be null)
   int* err;              // set to CSC_ERR_NONFINITE when a lambda_hat formed by the sweep is not finite (may be null)
+  int tf32;              // CSC_MIXED_TF32: contraction operands rounded to TF32 (float32 accumulation)
 };
 
 struct Ctx;
@@ -427,9 +428,10 @@ cudaError_t launch_code_spectra(const Ctx& c, const float* in, int nmaps, float2
 cudaError_t launch_spectra_f128(const Ctx& c, const float* in, long long nmaps, float2* out);
 // out[o][m] = in[m][o] for nmaps spectra (frequency-major copy for the tensor-core Gram)
 cudaError_t launch_spectra_transpose(const Ctx& c, const float2* in, int nmaps, float2* out);
-// tensor-core Gram (K + J <= 128): 3xTF32 (float32-accurate) or BF16 operands, reading the
-// frequency-major code spectra L.zt; also writes the right-hand-side spectra [K][J][Omega]
-cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err);
+// tensor-core Gram (K + J <= 128), reading the frequency-major code spectra L.zt; also writes the
+// right-hand-side spectra [K][J][Omega]. prec: CSC_FP32 (3xTF32, float32-accurate), CSC_MIXED_BF16
+// (BF16 operands) or CSC_MIXED_TF32 (one TF32 product)
+cudaError_t launch_learn_gram_tc(const Ctx& c, int prec, float2* rspec, int* dev_err);
 bool gram_tc_applies(const Ctx& c);
 cudaError_t launch_to_bf16(const Ctx& c, const float2* in, __nv_bfloat162* out, size_t n);
 

@@ -101,6 +101,15 @@ template <bool INV> CSC_D float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// v rounded to the nearest TF32 value (10 explicit mantissa bits, ties away from zero) and back to
+// float32 (operands of the TF32 contractions); NaN and Inf pass through
+CSC_D float tf32r(float v) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r & 0xFFFFE000u);
+}
+CSC_D float2 tf32r2(float2 v) { return make_float2(tf32r(v.x), tf32r(v.y)); }
+
 // init + sum of the partial sums p[c * stride] over slots c = c0..c1 (the CTAs that covered an
 // image), in a fixed order: four running sums over c = c0 + 4 i + r, added as (s0 + s1) + (s2 + s3),
 // so that four loads are in flight at a time when an image spans many CTAs

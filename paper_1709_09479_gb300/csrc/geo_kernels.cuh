@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
       float* vw = a.v_out ? a.v_out + map * D : vk;   // where the new state goes
       const float2* dk = a.dhat + (size_t)k * J * Om;
       const __nv_bfloat162* dk16 = a.dhat16 ? a.dhat16 + (size_t)k * J * Om : nullptr;
+      const bool tf = a.tf32 != 0;   // TF32 contraction operands
       // pull the next map's state (or codes) into L2 while this one is transformed
       if (a.vec4 && threadIdx.x < 4 && (long long)map + 1 < m1) {
         const float* nxt = (MODE == kObjective) ? a.z + (map + 1) * D : a.v + (map + 1) * D;
@@ -162,7 +163,8 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             if (o < Om)
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
-                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o]) : __ldg(dk + (size_t)j * Om + o);
+                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o])
+                                 : (tf ? tf32r2(__ldg(dk + (size_t)j * Om + o)) : __ldg(dk + (size_t)j * Om + o));
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
               for (int j = 0; j < kMaxJ; ++j)
                 if (j < J) {
                   const float2 l = lam[(size_t)j * Om + o];
-                  s = cfmac(dv[u][j], dk16 ? round_bf16(l) : l, s);
+                  s = cfmac(dv[u][j], dk16 ? round_bf16(l) : (tf ? tf32r2(l) : l), s);
                 }
               const int h = o / Wc, c = o - h * Wc;
               buf[h * P + c] = s;
@@ -296,14 +298,15 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(SweepArgs a, G g) {
             if (o < Om)
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
-                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o]) : __ldg(dk + (size_t)j * Om + o);
+                if (j < J) dv[u][j] = dk16 ? __bfloat1622float2(dk16[(size_t)j * Om + o])
+                                 : (tf ? tf32r2(__ldg(dk + (size_t)j * Om + o)) : __ldg(dk + (size_t)j * Om + o));
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int o = o0 + u * NT;
             if (o < Om) {
               const int h = o / Wc, c = o - h * Wc;
-              const float2 uh = dk16 ? round_bf16(buf[h * P + c]) : buf[h * P + c];
+              const float2 uh = dk16 ? round_bf16(buf[h * P + c]) : (tf ? tf32r2(buf[h * P + c]) : buf[h * P + c]);
 #pragma unroll
               for (int j = 0; j < kMaxJ; ++j)
                 if (j < J) acc[(size_t)j * Om + o] = cfma(dv[u][j], uh, acc[(size_t)j * Om + o]);

@@ -28,12 +28,14 @@ namespace f128 {
 // a complex value rounded to bfloat16 and back (operands of the mixed-precision contractions)
 __device__ __forceinline__ float2 to_bf16(float2 v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
 
-// BF: mixed precision. d_hat comes in bfloat16 (dhatp16, thread-major) and both operands of every
-// complex product of the contractions are bfloat16 values, accumulated in float32.
-template <int MODE, bool BF>
+// PREC 0: float32. PREC 1 (CSC_MIXED_BF16): d_hat comes in bfloat16 (dhatp16, thread-major) and both
+// operands of every complex product of the contractions are bfloat16 values, accumulated in float32.
+// PREC 2 (CSC_MIXED_TF32): both operands rounded to TF32, accumulated in float32.
+template <int MODE, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2* __restrict__ dhatp,
                                                       const __nv_bfloat162* __restrict__ dhatp16) {
   extern __shared__ float2 sm[];
+  constexpr bool BF = (PREC == 1), TF = (PREC == 2);
   constexpr bool kLam = (MODE == kIter || MODE == kLast);
   constexpr bool kAcc = (MODE != kLast);
   float2* buf = sm;                                   // [128][P]
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
       const size_t map = (size_t)n * a.K + k;
       const float2* dk = dhatp + (size_t)k * OM;
       const __nv_bfloat162* dk16 = BF ? dhatp16 + (size_t)k * OM : nullptr;
-      auto dval = [&](int p) { return BF ? __bfloat1622float2(dk16[p]) : __ldg(dk + p); };
+      auto dval = [&](int p) { return BF ? __bfloat1622float2(dk16[p]) : TF ? tf32r2(__ldg(dk + p)) : __ldg(dk + p); };
       if (threadIdx.x < 4 && (long long)map + 1 < m1) {
         const float* nxt = (MODE == kObjective) ? a.z + (map + 1) * D : a.v + (map + 1) * D;
         prefetch_l2_f128(nxt + threadIdx.x * (D / 4), (unsigned)D);
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         // w_hat = conj(d_hat_k) lambda_hat at this thread's bins, inverse split, first row pass
         inv_rows1_x2(buf, T, R, [&](int s) {
           const int p = slot_pos(s, t);
-          return cmulc(BF ? to_bf16(lam[p]) : lam[p], dval(p));
+          return cmulc(BF ? to_bf16(lam[p]) : TF ? tf32r2(lam[p]) : lam[p], dval(p));
         });
         __syncthreads();
         inv_rows2_x2(buf, R);
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
           dpre[kPre + i] = dval((15 - i) * NT + t);
         }
         fwd_rows2_split_x2(buf, T, R, [&](int s, float2 x, bool cj) {
-          const float2 xx = BF ? to_bf16(x) : x;
+          const float2 xx = BF ? to_bf16(x) : TF ? tf32r2(x) : x;
           const float2 dv = (s < kPre) ? dpre[s] : (s > 15 - kPre && s < 16) ? dpre[kPre + 15 - s] : dval(slot_pos(s, t));
           acc[s] = cj ? make_float2(fmaf(dv.x, xx.x, fmaf(dv.y, xx.y, acc[s].x)),
                                     fmaf(dv.y, xx.x, fmaf(-dv.x, xx.y, acc[s].y)))   // + d conj(x)
@@ -218,9 +220,9 @@ size_t smem_bytes(int mode) {
   return ((size_t)H * P + (lam ? OM : 0)) * sizeof(float2);
 }
 
-template <int MODE, bool BF>
+template <int MODE, int PREC>
 cudaError_t launch_mode(const Ctx& c, const SweepArgs& a) {
-  auto kern = k_sweep_f128<MODE, BF>;
+  auto kern = k_sweep_f128<MODE, PREC>;
   const size_t smem = smem_bytes(MODE);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -257,14 +259,21 @@ bool fused128_applies(const Ctx& c, const SweepArgs& a) {
   return c.dhatp && c.g.ct_id == 1 && c.J == 1 && a.vec4 && (a.dhat16 == nullptr || c.dhatp16 != nullptr);
 }
 
-// a.dhat16 set: mixed precision, with the context's thread-major bf16 copy of d_hat
+// a.dhat16 set: mixed precision, with the context's thread-major bf16 copy of d_hat; a.tf32: TF32
+// contraction operands
 cudaError_t launch_sweep_fused128(const Ctx& c, int mode, const SweepArgs& a) {
-  const bool bf = a.dhat16 != nullptr && c.dhatp16 != nullptr;
+  const int prec = (a.dhat16 != nullptr && c.dhatp16 != nullptr) ? 1 : a.tf32 ? 2 : 0;
   switch (mode) {
-    case kPrologue: return bf ? f128::launch_mode<kPrologue, true>(c, a) : f128::launch_mode<kPrologue, false>(c, a);
-    case kIter: return bf ? f128::launch_mode<kIter, true>(c, a) : f128::launch_mode<kIter, false>(c, a);
-    case kLast: return bf ? f128::launch_mode<kLast, true>(c, a) : f128::launch_mode<kLast, false>(c, a);
-    default: return f128::launch_mode<kObjective, false>(c, a);
+    case kPrologue:
+      return prec == 1 ? f128::launch_mode<kPrologue, 1>(c, a)
+                       : prec == 2 ? f128::launch_mode<kPrologue, 2>(c, a) : f128::launch_mode<kPrologue, 0>(c, a);
+    case kIter:
+      return prec == 1 ? f128::launch_mode<kIter, 1>(c, a)
+                       : prec == 2 ? f128::launch_mode<kIter, 2>(c, a) : f128::launch_mode<kIter, 0>(c, a);
+    case kLast:
+      return prec == 1 ? f128::launch_mode<kLast, 1>(c, a)
+                       : prec == 2 ? f128::launch_mode<kLast, 2>(c, a) : f128::launch_mode<kLast, 0>(c, a);
+    default: return f128::launch_mode<kObjective, 0>(c, a);
   }
 }
 

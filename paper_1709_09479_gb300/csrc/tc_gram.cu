@@ -22,7 +22,8 @@
 // later chunks run while the MMAs of chunk i execute; each buffer is released by a tcgen05.commit.
 //
 // Two operand precisions:
-//   X3 = true   float32-accurate 3xTF32: v = hi + lo with hi, lo rounded to TF32 (10 explicit mantissa
+//   X3 = true   float32-accurate 3xTF32 (a.passes = 3), or one TF32 product (a.passes = 1: the
+//               CSC_MIXED_TF32 mode): v = hi + lo with hi, lo rounded to TF32 (10 explicit mantissa
 //               bits); G accumulates hi.hi + hi.lo + lo.hi in FP32 (kind::tf32). The dropped lo.lo term
 //               and the rounding of lo are below 2^-21 relative per product.
 //   X3 = false  BF16 operands, FP32 accumulation (kind::f16), the mixed-precision mode.
@@ -169,6 +170,7 @@ struct TcGramArgs {
   int np;                   // K (K + 1) / 2
   float2* rspec;            // [K][J][Omega]
   int* err;
+  int passes;               // TF32 kernel: 3 (hi.hi + hi.lo + lo.hi, float32-accurate) or 1 (hi.hi: TF32 operands)
 };
 
 template <bool X3>
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(TcGramArgs a) {
         const int kb = ks < kTcKSteps / 2 ? ks + kTcKSteps / 2 : ks - kTcKSteps / 2;
         const uint32_t idi = ks < kTcKSteps / 2 ? id_pos : id_neg;
 #pragma unroll
-        for (int c = 0; c < (X3 ? 3 : 1); ++c) {
+        for (int c = 0; c < (X3 ? a.passes : 1); ++c) {
           const uint32_t pa = (c == 2) ? kTcPieceBytes : 0u;   // hi.hi, hi.lo, lo.hi
           const uint32_t pb = (c == 1) ? kTcPieceBytes : 0u;
           const uint64_t ad = smem_desc(base + pa + (uint32_t)ks * 2u * kTcLbo);
@@ -390,10 +392,11 @@ cudaError_t launch_spectra_transpose(const Ctx& c, const float2* in, int nmaps, 
 bool gram_tc_applies(const Ctx& c) { return c.K + c.J <= 128; }
 
 template <bool X3>
-static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err) {
+static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err, int passes) {
   const int rows = c.K + c.J;
   const int ntile = (rows + 15) / 16 * 16;
-  TcGramArgs a{c.N, c.K, c.J, c.g.Omega, ntile, rows, c.L.zt, c.xhat, c.L.gram, c.K * (c.K + 1) / 2, rspec, dev_err};
+  TcGramArgs a{c.N, c.K, c.J, c.g.Omega, ntile, rows, c.L.zt, c.xhat, c.L.gram, c.K * (c.K + 1) / 2, rspec, dev_err,
+               passes};
   // at least 80 KB per CTA keeps at most two CTAs (2 x 256 TMEM columns) per SM
   const int smem = (int)std::max<size_t>(gram_tc_smem<X3>(rows), 80 * 1024);
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -403,9 +406,10 @@ static cudaError_t launch_gram_tc_t(const Ctx& c, float2* rspec, int* dev_err) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_learn_gram_tc(const Ctx& c, bool bf16, float2* rspec, int* dev_err) {
+cudaError_t launch_learn_gram_tc(const Ctx& c, int prec, float2* rspec, int* dev_err) {
   if (!gram_tc_applies(c) || !rspec) return cudaErrorInvalidValue;
-  return bf16 ? launch_gram_tc_t<false>(c, rspec, dev_err) : launch_gram_tc_t<true>(c, rspec, dev_err);
+  if (prec == CSC_MIXED_BF16) return launch_gram_tc_t<false>(c, rspec, dev_err, 1);
+  return launch_gram_tc_t<true>(c, rspec, dev_err, prec == CSC_MIXED_TF32 ? 1 : 3);
 }
 
 }  // namespace csc

@@ -782,7 +782,7 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     v.L.gram = V.gram;
     v.xhat = V.x3;
     VL_CHECK(launch_spectra_transpose(v, V.z3, N * K, V.zt), "code spectra transpose");
-    VL_CHECK(launch_learn_gram_tc(v, false, V.rspec, c->err), "code Gram (tensor cores)");
+    VL_CHECK(launch_learn_gram_tc(v, CSC_FP32, V.rspec, c->err), "code Gram (tensor cores)");
     // right-hand-side spectra frequency-major: [O3][K J]
     Ctx vr = *c;
     vr.g.Omega = (int)O3;

@@ -1,4 +1,4 @@
-"""The mixed-precision mode (CSC_MIXED_BF16): per-frequency contractions with bfloat16 operands and
+"""The mixed-precision modes (CSC_MIXED_BF16, and CSC_MIXED_TF32 at the end of the file): per-frequency contractions with bfloat16 operands and
 float32 accumulation — the coding sweep's sum_k d_hat_k u_hat_k and conj(d_hat_k) lambda_hat on the
 CUDA cores, and the learning step's code Gram Z(w)^H Z(w) on the tensor cores (tcgen05) — against
 the float64 oracle. bfloat16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3), so the errors
@@ -83,3 +83,51 @@ def test_objective_stays_float32_in_mixed_mode(csc):
         f = sv.objective(to_cuda(x), to_cuda(d), to_cuda(z))
     fo = O.objective(x, d, z, 0.7)
     assert abs(f - fo) <= 1e-5 * fo
+
+
+#: CSC_MIXED_TF32 (10 explicit mantissa bits, unit roundoff 2^-11 ~ 4.9e-4): measured on GB300 and
+#: printed by the tests; bounds leave a factor of ~3
+CODE_TF32_TOL = 3e-3
+LEARN_TF32_TOL = 1e-2
+
+
+@pytest.mark.parametrize("case", [(3, 5, (100, 100), 11, 1.0, 0.1, 10), (4, 40, (64, 64), 5, 0.3, 1.0, 8),
+                                  (2, 24, (128, 128), 11, 0.3, 1.0, 8)])
+def test_tf32_coding_error_against_oracle(csc, case):
+    """TF32 contraction operands in the generic sweep (100 x 100, 64 x 64) and the fused 128 x 128 one."""
+    import torch
+    N, K, dims, s, beta, rho, iters = case
+    x, d = make_problem(140 + K, N, K, 1, dims, s)
+    _, zo = O.code_admm(x, d, beta, rho, iters)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims=dims, n_images=N, beta=beta, rho=rho,
+                    precision=csc.CSC_MIXED_TF32) as sv:
+        v = torch.zeros((N, K) + dims, device="cuda")
+        z = torch.empty_like(v)
+        sv.code(to_cuda(x), to_cuda(d), v, z, iters)
+        torch.cuda.synchronize()
+    e = rel(to_np(z), zo)
+    print(f"coding rel err vs oracle: tf32 {e:.2e}")
+    assert np.abs(zo).max() > 0
+    assert e <= CODE_TF32_TOL
+
+
+@pytest.mark.parametrize("case", [(3, 6, (64, 64), 5, 0.3), (16, 100, (64, 64), 5, 0.3)])
+def test_tf32_tensor_core_gram_learning_against_oracle(csc, case):
+    import torch
+    N, K, dims, s, beta = case
+    x, d = make_problem(150 + K, N, K, 1, dims, s)
+    _, z = O.code_admm(x, d, beta, 1.0, 30)
+    z = f32(z).astype(np.float64)
+    mu0 = np.full(K, 0.5)
+    do, muo, _, _ = O.learn_paper(x, z, d, mu0, np.zeros_like(x), 2)
+    with csc.Solver(J=1, K=K, fs=(s, s), dims=dims, n_images=N, beta=beta, rho=1.0,
+                    precision=csc.CSC_MIXED_TF32, cg_tol=1e-6, cg_max=400) as sv:
+        dv = to_cuda(d)
+        mu = torch.tensor(mu0, device="cuda")
+        sv.learn(to_cuda(x), to_cuda(z), dv, mu, 2)
+        torch.cuda.synchronize()
+    e = rel(to_np(dv), do)
+    m = float(np.max(np.abs(mu.cpu().numpy() - muo) / muo))
+    print(f"learned filters rel err vs oracle: tf32 tensor-core Gram {e:.2e} (mu {m:.2e})")
+    assert e <= LEARN_TF32_TOL
+    assert m <= LEARN_TF32_TOL
