@@ -811,7 +811,9 @@ def run_sweeps(args):
             conv = None
             if moved is not None:
                 conv = next((i + 1 for i in range(moved, len(rel_ch)) if all(r <= 1e-3 for r in rel_ch[i:])), None)
-            rows.append({"beta": beta, "rounds_to_1e-3": None if conv is None else conv + 1,
+            first = None if moved is None else next((i + 1 for i in range(moved, len(rel_ch)) if rel_ch[i] <= 1e-3), None)
+            rows.append({"beta": beta, "first_round_change_below_1e-3": None if first is None else first + 1,
+                         "rounds_to_1e-3": None if conv is None else conv + 1,
                          "seconds_to_1e-3": None if conv is None else ts[conv],
                          "f_final": fs[-1], "objective": fs, "seconds_per_round": ts[-1] / len(ts),
                          "nonzero_code_fraction": float((z != 0).float().mean()),

@@ -88,7 +88,7 @@ def test_objective_stays_float32_in_mixed_mode(csc):
 #: CSC_MIXED_TF32 (10 explicit mantissa bits, unit roundoff 2^-11 ~ 4.9e-4): measured on GB300 and
 #: printed by the tests; bounds leave a factor of ~3
 CODE_TF32_TOL = 3e-3
-LEARN_TF32_TOL = 1e-2
+LEARN_TF32_TOL = 2e-3
 
 
 @pytest.mark.parametrize("case", [(3, 5, (100, 100), 11, 1.0, 0.1, 10), (4, 40, (64, 64), 5, 0.3, 1.0, 8),
