@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         __syncthreads();
         inv_cols1_x2(buf, T, R);
         __syncthreads();
-        inv_cols2_x2(buf, R, zc);
-        float2 vv[16];
+        float2 vv[16];   // the state, loaded while the last inverse column pass runs
         const float* vk = a.v + map * D;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
           vv[j] = __ldcs(reinterpret_cast<const float2*>(vk + (g + 8 * j) * W + 2 * wc));
+        inv_cols2_x2(buf, R, zc);
         // zc[out_slot<16>(j)] is w at rows h = g + 8 j: state update (and codes on the last sweep),
         // two pixels per packed operation
         float* vw = (a.v_out ? a.v_out : a.v) + map * D;
@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f128(SweepArgs a, const float2*
         fwd_rows1_x2(buf, T, R);
         __syncthreads();
         // second forward row pass, split, accumulate d_hat_k u_hat. The d_hat values of the first
-        // three bin pairs (slots 0-2 and 13-15) are loaded before the row transforms, the rest where
-        // they are used (registers allow no more in flight)
-        constexpr int kPre = 3;
+        // bin pairs (three in float32: slots 0-2 and 13-15) are loaded before the row transforms,
+        // the rest where they are used (registers allow no more in flight)
+        constexpr int kPre = (PREC == 0) ? 3 : 1;   // the rounding modes need the registers
         float2 dpre[2 * kPre];
 #pragma unroll
         for (int i = 0; i < kPre; ++i) {
