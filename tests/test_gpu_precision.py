@@ -25,8 +25,10 @@ def csc():
     return lib
 
 
-@pytest.mark.parametrize("case", [(3, 5, (100, 100), 11, 1.0, 0.1, 10), (4, 40, (64, 64), 5, 0.3, 1.0, 8)])
+@pytest.mark.parametrize("case", [(3, 5, (100, 100), 11, 1.0, 0.1, 10), (4, 40, (64, 64), 5, 0.3, 1.0, 8),
+                                  (2, 24, (128, 128), 11, 0.3, 1.0, 8)])
 def test_bf16_coding_error_against_oracle(csc, case):
+    """bf16 contraction operands in the generic sweep (100 x 100, 64 x 64) and the fused 128 x 128 one."""
     import torch
     N, K, dims, s, beta, rho, iters = case
     x, d = make_problem(110 + K, N, K, 1, dims, s)
