@@ -150,11 +150,14 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
  * coded with K filters of support ft x fh x fw per channel (params->fs = {fh, fw}; ft odd, taps at
  * time offsets -(ft-1)/2 .. (ft-1)/2, circular like the spatial ones), 3-D DFTs: the higher-order
  * extension of Sec. 3.3 with a time axis. Arrays: x [N][J][T][H][W], d [K][J][ft][fh][fw],
- * v and z [N][K][T][H][W]. Supported: H = W = 128, 1 <= T <= 64, ft <= 7 and <= T, CSC_FP32.
+ * v and z [N][K][T][H][W]. Supported: H = W = 128, 1 <= T <= 64, ft <= 7 and <= T, CSC_FP32; the
+ * flags of csc_params but CSC_FLAG_SYMMETRIC_BOUNDARY (CSC_ERR_UNSUPPORTED).
  * Supports csc_code, csc_objective, csc_learn (fh <= 12, fw <= 16, K + J <= 128; the 3-D lag window
- * (2ft-1) x (2fh-1) x (2fw-1), Jacobi-preconditioned CG driven from the host, params->cg_max and
- * cg_tol as for csc_init), csc_describe and csc_destroy; the reverse-mode calls return
- * CSC_ERR_UNSUPPORTED on such a context.
+ * (2ft-1) x (2fh-1) x (2fw-1), Jacobi-preconditioned CG, params->cg_max, cg_tol and
+ * CSC_FLAG_CG_STRICT as for csc_init; all learning steps in one persistent launch whose exchange
+ * waits follow csc_set_wait_limit, where the shape fits the shared memory of an SM, else a
+ * host-driven CG), csc_describe and csc_destroy; the reverse-mode calls return CSC_ERR_UNSUPPORTED
+ * on such a context.
  */
 csc_status csc_init_video(const csc_params* params, int ft, int n_videos, const int* dims, void* stream,
                           csc_ctx** out);

@@ -151,9 +151,9 @@ def csc_init_uneven(J, K, fs, dims_list, beta, rho, precision=CSC_FP32, stream=N
     return out.value
 
 
-def csc_init_video(J, K, fs, ft, dims, n_videos, beta, rho, stream=None, cg_max=100, cg_tol=1e-6):
+def csc_init_video(J, K, fs, ft, dims, n_videos, beta, rho, stream=None, cg_max=100, cg_tol=1e-6, flags=0):
     """Context for n_videos tensors J x T x H x W (dims = (T, H, W)), filters ft x fh x fw (fs = (fh, fw))."""
-    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, CSC_FP32, 0, 1)
+    p = csc_params(J, K, (ctypes.c_int * 2)(*fs), beta, rho, cg_max, cg_tol, CSC_FP32, flags, 1)
     dims_arr = (ctypes.c_int * 3)(*dims)
     out = ctypes.c_void_p()
     _check(LIB.csc_init_video(ctypes.byref(p), ft, n_videos, dims_arr, stream, ctypes.byref(out)))
@@ -285,7 +285,7 @@ class Solver:
             stream = _current_stream()
         if ft is not None:
             self.dims, self.N, self.ft = tuple(dims), n_images, ft
-            self.ctx = csc_init_video(J, K, fs, ft, dims, n_images, beta, rho, stream, cg_max, cg_tol)
+            self.ctx = csc_init_video(J, K, fs, ft, dims, n_images, beta, rho, stream, cg_max, cg_tol, flags)
         elif dims_list is not None:
             self.dims_list = [tuple(hw) for hw in dims_list]
             self.N, self.dims = len(self.dims_list), None

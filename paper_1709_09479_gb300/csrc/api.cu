@@ -123,7 +123,8 @@ void free_all(Ctx* c) {
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
                   c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1,
                   c->VL.z3, c->VL.zt, c->VL.x2, c->VL.x3, c->VL.gram, c->VL.rspec, c->VL.rspecT, c->VL.U, c->VL.tab, c->VL.lags,
-                  c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.fscal, c->VL.part, c->VL.st, c->VL.iters};
+                  c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.fscal, c->VL.part, c->VL.st, c->VL.iters,
+                  c->VL.words};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -766,6 +767,8 @@ csc_status csc_init_video(const csc_params* params, int ft, int n_videos, const 
   if (ft < 1 || !(ft & 1) || ft > 7 || ft > T)
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_video: time support must be odd, <= 7 and <= T");
   if (params->precision != CSC_FP32) return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_video: CSC_FP32 only");
+  if (params->flags & CSC_FLAG_SYMMETRIC_BOUNDARY)
+    return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_video: the symmetric boundary is for 2-D batches");
   const int hw[2] = {H, W};
   csc_status s = init_ctx(params, n_videos, hw, stream, out, true);
   if (s != CSC_OK) return s;
@@ -1259,12 +1262,17 @@ csc_status csc_learn(csc_ctx* ctx, const float* x, const float* z, float* d, dou
     int herr = 0;
     CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
     std::vector<int> its(std::max(steps, 1));
-    if (cg_iters && steps > 0)
+    if (steps > 0)
       CSC_CHECK_CUDA(c, cudaMemcpyAsync(its.data(), c->VL.iters, steps * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
                      "iteration copy");
     CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    if (herr) return fail(c, (csc_status)herr, "csc_learn: tensor-core Gram wait timed out");
+    if (herr == CSC_ERR_NONFINITE) return fail(c, CSC_ERR_NONFINITE, "csc_learn: a code or image value was not finite");
+    if (herr) return fail(c, (csc_status)herr, "csc_learn: a device wait (tensor-core Gram or CG exchange) timed out");
     if (cg_iters && steps > 0) std::memcpy(cg_iters, its.data(), steps * sizeof(int));
+    if (c->p.flags & CSC_FLAG_CG_STRICT)
+      for (int i = 0; i < steps; ++i)
+        if (its[i] >= c->p.cg_max)
+          return fail(c, CSC_ERR_NOT_CONVERGED, "csc_learn: a CG solve stopped at cg_max iterations");
     return CSC_OK;
   }
   csc_status s;

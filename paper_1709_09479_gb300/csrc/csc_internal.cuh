@@ -266,6 +266,7 @@ struct VideoLearnBuffers {
   void* st = nullptr;        // CG scalars and flags
   int* iters = nullptr;
   int iters_cap = 0;
+  unsigned long long* words = nullptr;   // exchange words of the persistent CG (video_cg.cu)
 };
 
 struct BackwardBuffers {
@@ -415,6 +416,12 @@ cudaError_t launch_learn_gram(const Ctx& c);
 // steps' CG iteration counts in c->VL.iters
 csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double* mu, int steps);
 bool video_learn_shape_ok(const Ctx& c);
+// the persistent cooperative CG of the video learning (video_cg.cu): whether the context's shape fits
+// it, the exchange words it needs, and the launch (all learning steps, mu on the device)
+bool video_cg_applies(const Ctx& c);
+size_t video_cg_words(const Ctx& c);
+cudaError_t launch_video_cg(const Ctx& c, unsigned long long* words, const float* lags, const float2* chat,
+                            const float* b, float* x, double* mu, const int* active, int* iters, int steps);
 cudaError_t launch_learn_lags(const Ctx& c);       // from gram [npairs][Omega] (CUDA-core Gram)
 cudaError_t launch_learn_lags_sep(const Ctx& c);   // from the tensor-core Gram's gramT [Omega][npairs]
 cudaError_t launch_lag_spectra(const Ctx& c);      // L.chat from L.lags (both lag launchers end with it)

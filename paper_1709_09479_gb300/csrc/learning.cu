@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "csc_internal.cuh"
+#include "cg_exchange.cuh"
 
 namespace csc {
 
@@ -122,10 +123,6 @@ __global__ void __launch_bounds__(kGramNT) k_learn_gram(GramArgs a) {
   }
 }
 
-// default bound of every spin-wait of the CG launch (~1 s of SM clocks); a context can lower it
-// (csc_set_wait_limit) so that a test can make a wait run out
-constexpr long long kSpinLimit = 2000000000LL;
-
 // ---------------------------------------------------------------------------------------------
 // lag spectra: the normal-equation product in the Fourier domain of the (2fh-1) x (2fw-1) lag grid
 //
@@ -207,8 +204,6 @@ __global__ void __launch_bounds__(kLagSpecNT) k_lag_spectra(LagSpecArgs a) {
 // banks by epoch parity (a CTA one exchange ahead never overwrites words a slower CTA still
 // reads) and are summed in CTA order, so every CTA gets the same totals.
 // ---------------------------------------------------------------------------------------------
-constexpr int kSlotWords = 4 * kMaxJ;
-
 struct CgArgs {
   int K, J, fh, fw, S2, La, Lb, NF, G, steps, cg_max;
   double tol2, mu_floor;
@@ -270,142 +265,6 @@ __device__ __forceinline__ void axpy_from_l2(float* dst, const float* src, int n
       if (i < n) dst[i] = overwrite ? v[u] : fmaf((float)beta[JS == S2 ? 0 : (i % JS) / S2], dst[i], v[u]);
     }
   }
-}
-
-// Sums vals[0..N) over the block in float32 (the device's float64 rate is a few operations per
-// clock per SM, so per-thread float64 work is kept out of the CG loop); the totals are valid in
-// thread 0 only. scratch: [NT/32][kSlotWords] floats, free on entry.
-template <int NT, int N>
-__device__ __forceinline__ void block_reduce_to0(float (&vals)[N], float* scratch) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float v = vals[i];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) scratch[(threadIdx.x >> 5) * kSlotWords + i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float v = (threadIdx.x < NT / 32) ? scratch[threadIdx.x * kSlotWords + i] : 0.f;
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      vals[i] = v;
-    }
-  }
-}
-
-// vals[idx] += v for a run-time idx with every slot kept in registers
-template <int N>
-__device__ __forceinline__ void add_at(float (&vals)[N], int idx, float v) {
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (i == idx) vals[i] += v;
-}
-
-// 64-bit words exchanged between CTAs: relaxed, GPU scope (single-copy atomic; no fences implied)
-__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long tag(float v, unsigned ep) {
-  return ((unsigned long long)ep << 32) | __float_as_uint(v);
-}
-
-// thread 0: make the CTA's earlier global writes visible, then publish vals[0..N) with epoch ep.
-// The caller has synchronised the block since those writes. N == 0: one word without a sum.
-template <int N>
-__device__ __forceinline__ void publish(unsigned long long* slots, int G, const float* vals, unsigned ep,
-                                        bool fence = false) {
-  if (threadIdx.x != 0) return;
-  if (fence) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release: plain stores before the words
-  unsigned long long* s = slots + ((size_t)(ep & 1) * G + blockIdx.x) * kSlotWords;
-#pragma unroll
-  for (int i = 0; i < (N > 0 ? N : 1); ++i)
-    st_volatile_u64(s + i, ((unsigned long long)ep << 32) | __float_as_uint(N > 0 ? vals[i] : 0.f));
-}
-
-// Waits until this block's words carry epoch ep, in two phases: first the exchange's slot words
-// (G CTAs x nw; thread t polls words t and t + NT, values parked in vals, [G][nw] floats of shared
-// memory), when slots is not null; after a block barrier the data words t + u NT < ndata (left in
-// wd[u]; the value is the low half), which the publishers wrote before their slot words and so are
-// almost always complete by then (any that are not are polled again). Must be called by the whole
-// block. false when a CTA flagged an error or the wait ran out (flag set).
-template <int NT, int U>
-__device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsigned ep, float* vals,
-                           const unsigned long long* data, int ndata, unsigned long long (&wd)[U], int* err,
-                           long long limit) {
-  __shared__ int s_bad;
-  const long long t0 = clock64();
-  bool ok = true;
-  if (slots) {
-    if (threadIdx.x == 0) s_bad = 0;
-    const unsigned long long* sb = slots + (size_t)(ep & 1) * G * kSlotWords;
-    const int nsw = G * nw;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = threadIdx.x + u * NT;
-      if (i < nsw) {
-        const unsigned long long* wp = sb + (size_t)(i / nw) * kSlotWords + i % nw;
-        unsigned long long w = ld_volatile_u64(wp);
-        while ((unsigned)(w >> 32) != ep) {
-          if (*(volatile int*)err || clock64() - t0 > limit) { ok = false; break; }
-          w = ld_volatile_u64(wp);
-        }
-        vals[i] = __uint_as_float((unsigned)w);
-      }
-    }
-    if (!ok) s_bad = 1;
-    __syncthreads();
-    if (s_bad) {
-      if (!*(volatile int*)err) atomicExch(err, (int)CSC_ERR_TIMEOUT);
-      return false;
-    }
-  }
-  unsigned pend = 0;
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-    if ((int)threadIdx.x + u * NT < ndata) pend |= 1u << u;
-  while (pend) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (pend & (1u << u)) wd[u] = ld_volatile_u64(data + threadIdx.x + u * NT);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if ((pend & (1u << u)) && (unsigned)(wd[u] >> 32) == ep) pend &= ~(1u << u);
-    if (!pend) break;
-    if (*(volatile int*)err) return false;
-    if (clock64() - t0 > limit) {
-      atomicExch(err, (int)CSC_ERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ float word_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
-
-// totals[i] = sum over CTAs in CTA order of vals[b * nw + i], i < n (warp 0, float64). Call after a
-// barrier that follows wait_words; ends with a barrier. then() runs on thread 0 once the totals are
-// known: the scalars of the iteration are formed there, in float64, and broadcast through shared
-// memory (the device's float64 rate is low).
-template <int NT, class F>
-__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, double* totals, F then) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i = 0; i < n; ++i) {
-      double v = 0.0;
-      for (int b = lane; b < G; b += 32) v += (double)vals[b * nw + i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) totals[i] = v;
-    }
-    if (lane == 0) then();
-  }
-  __syncthreads();
 }
 
 // Lag-grid half spectrum of S Z^T Z S^T p at this CTA's bins, p (all filters) in shared memory:

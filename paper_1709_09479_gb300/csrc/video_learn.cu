@@ -826,6 +826,16 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   k_vl_active<<<K, 256, 0, st>>>(z, (long long)T * H * W, N, K, V.active);
   VL_CHECK(cudaGetLastError(), "activity");
   float* xdev = d;   // staged by the caller: device filters [K][J][ft][fh][fw]
+  if (steps >= 0 && video_cg_applies(*c)) {
+    // all learning steps in one persistent cooperative launch (video_cg.cu)
+    A((void**)&V.words, video_cg_words(*c) * sizeof(unsigned long long));
+    if (e != cudaSuccess) { cudaGetLastError(); return vl_fail(c, CSC_ERR_WORKSPACE, "csc_learn: video workspace allocation failed"); }
+    VL_CHECK(launch_video_cg(*c, V.words, V.lags, V.chat, b, xdev, V.mu, V.active, V.iters, steps), "video CG");
+    VL_CHECK(cudaMemcpyAsync(mu, V.mu, K * sizeof(double), vl_is_device_ptr(mu) ? cudaMemcpyDeviceToDevice
+                                                                              : cudaMemcpyDeviceToHost, st), "mu copy");
+    c->launches += 14;
+    return CSC_OK;
+  }
   OpArgs oa{K, J, ft, fh, fw, Lt, La, Lb, S3, NF, nullptr, V.phat, V.yhat, y, V.chat, nullptr};
   const size_t t2b_sm = ((size_t)(S3 + 1) / 2 + (size_t)ft * fh * fw + (size_t)ft * La * fw + Lt + La + Lb) * sizeof(float2);
   const size_t b2t_sm = ((size_t)NF + (size_t)ft * La * fw + (size_t)ft * fh * fw + Lt + La + Lb) * sizeof(float2);

@@ -187,3 +187,69 @@ def test_video_full_size_matches_oracle(csc):
     assert np.count_nonzero(z_o) > 0
     assert rel(v_g, v_o) <= REL_TOL
     assert rel(z_g, z_o) <= REL_TOL
+
+
+def video_learn_case():
+    """A small video learning problem (N=1, K=3 grey filters 3 x 5 x 5, 6 frames) and its oracle codes."""
+    from paper_1709_09479_gb300 import inputs
+    N, K, J, T, ft, s = 1, 3, 1, 6, 3, 5
+    x = f32(inputs.powerlaw_field(86, N, J, (T, 128, 128))).astype(np.float64)
+    d = f32(inputs.unit_filters(87, K, J, (ft, s, s))).astype(np.float64)
+    _, z = O.code_admm(x, d, 0.3, 1.0, 20)
+    return x, f32(z).astype(np.float64), d
+
+
+def video_solver(csc, x, d, **kw):
+    N, J, T = x.shape[:3]
+    K, ft, s = d.shape[0], d.shape[2], d.shape[3]
+    args = dict(J=J, K=K, fs=(s, s), ft=ft, dims=(T, 128, 128), n_images=N, beta=0.3, rho=1.0, cg_tol=1e-7,
+                cg_max=400)
+    args.update(kw)
+    return csc.Solver(**args)
+
+
+def test_video_cg_wait_limit_times_out_then_context_learns_normally(csc):
+    """The persistent video CG's exchange waits honour csc_set_wait_limit: with a one-clock bound a
+    wait gives up, every CTA returns and csc_learn reports CSC_ERR_TIMEOUT; the same context then
+    learns normally and matches the oracle."""
+    import torch
+    x, z, d = video_learn_case()
+    K = d.shape[0]
+    mu0 = np.full(K, 0.5)
+    d_o, mu_o, _, _ = O.learn_paper(x, z, d, mu0, np.zeros_like(x), 2)
+    with video_solver(csc, x, d) as sv:
+        sv.set_wait_limit(1)
+        with pytest.raises(csc.CscError) as e:
+            sv.learn(to_cuda(x), to_cuda(z), to_cuda(d), torch.tensor(mu0, device="cuda"), 2)
+        assert e.value.status == 7
+        sv.set_wait_limit(0)
+        dv, mu = to_cuda(d), torch.tensor(mu0, device="cuda")
+        sv.learn(to_cuda(x), to_cuda(z), dv, mu, 2)
+        assert rel(to_np(dv), d_o) <= REL_TOL
+        np.testing.assert_allclose(mu.cpu().numpy(), mu_o, rtol=REL_TOL)
+
+
+def test_video_nan_codes_stop_the_cg_with_nonfinite(csc):
+    import torch
+    x, z, d = video_learn_case()
+    zb = z.copy()
+    zb[0, 1, 2, 5, 5] = np.nan
+    with video_solver(csc, x, d) as sv:
+        with pytest.raises(csc.CscError) as e:
+            sv.learn(to_cuda(x), to_cuda(zb), to_cuda(d), torch.full((d.shape[0],), 0.5, dtype=torch.float64,
+                                                                        device="cuda"), 2)
+        assert e.value.status == 5
+
+
+def test_video_cg_stopped_at_its_cap(csc):
+    """cg_max = 1: one CG iteration per learning step is reported; with CSC_FLAG_CG_STRICT the call
+    returns CSC_ERR_NOT_CONVERGED."""
+    import torch
+    x, z, d = video_learn_case()
+    mu = lambda: torch.full((d.shape[0],), 0.5, dtype=torch.float64, device="cuda")
+    with video_solver(csc, x, d, cg_max=1, cg_tol=1e-9) as sv:
+        assert sv.learn(to_cuda(x), to_cuda(z), to_cuda(d), mu(), 3) == [1, 1, 1]
+    with video_solver(csc, x, d, cg_max=1, cg_tol=1e-9, flags=csc.CSC_FLAG_CG_STRICT) as sv:
+        with pytest.raises(csc.CscError) as e:
+            sv.learn(to_cuda(x), to_cuda(z), to_cuda(d), mu(), 3)
+        assert e.value.status == 6
