@@ -133,22 +133,22 @@ __device__ bool wait_words(const unsigned long long* slots, int G, int nw, unsig
 
 __device__ __forceinline__ float word_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
 
-// totals[i] = sum over CTAs in CTA order of vals[b * nw + i], i < n (warp 0, float64). Call after a
-// barrier that follows wait_words; ends with a barrier. then() runs on thread 0 once the totals are
-// known: the scalars of the iteration are formed there, in float64, and broadcast through shared
-// memory (the device's float64 rate is low).
+// totals[i] = sum over CTAs of vals[b * nw + i], i < n, in a fixed order (one warp per value, float32).
+// Call after a barrier that follows wait_words; ends with a barrier. then() runs on thread 0 once the
+// totals are known: the scalars of the iteration are formed there and broadcast through shared memory.
+// All of it stays in float32: the device's float64 rate is a few operations per clock per SM, and
+// float64 on the path of every exchange cost microseconds.
 template <int NT, class F>
-__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, double* totals, F then) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i = 0; i < n; ++i) {
-      double v = 0.0;
-      for (int b = lane; b < G; b += 32) v += (double)vals[b * nw + i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) totals[i] = v;
-    }
-    if (lane == 0) then();
+__device__ __forceinline__ void sum_slots(const float* vals, int G, int nw, int n, float* totals, F then) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < n; i += NT / 32) {
+    float v = 0.f;
+    for (int b = lane; b < G; b += 32) v += vals[b * nw + i];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) totals[i] = v;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) then();
   __syncthreads();
 }
 

@@ -440,13 +440,13 @@ template <int NT, int JT>
 __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   extern __shared__ float smf[];
   __shared__ float scratch[(NT / 32) * kSlotWords];
-  __shared__ double tot[kSlotWords];
+  __shared__ float tot[kSlotWords];
   __shared__ float gvals[2 * NT];   // slot words of the current exchange [G][nw]
   __shared__ int s_fail;
   if (threadIdx.x == 0) s_fail = 0;
   __shared__ float s_twomu[8], s_jac[8];
   // scalars of the CG iteration, formed by thread 0 in float64
-  __shared__ double s_rz[kMaxJ], s_rr[kMaxJ], s_bb[kMaxJ];
+  __shared__ float s_rz[kMaxJ], s_rr[kMaxJ], s_bb[kMaxJ];
   __shared__ float s_alpha[kMaxJ], s_beta[kMaxJ];
   __shared__ int s_done[kMaxJ], s_all;
   __shared__ int s_act[8];
@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   const int La = a.La, Lb = a.Lb, ctr = (a.fh - 1) * Lb + (a.fw - 1);   // lag tau = 0
   const int f0 = (int)((long long)blockIdx.x * a.NF / G), f1 = (int)((long long)(blockIdx.x + 1) * a.NF / G);
   const int nbc = f1 - f0;
+  const float tol2f = (float)a.tol2;
   unsigned ep = 0;
 
   for (int i = threadIdx.x; i < La; i += NT) twa[i] = unit_root(i, La);
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         s_rz[j] = tot[j];
         s_rr[j] = tot[J + j];
         s_bb[j] = tot[2 * J + j];
-        s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+        s_done[j] = !(s_rr[j] > tol2f * s_bb[j]) || !(s_rz[j] > 0.f);
         all = all && s_done[j];
         if (!isfinite(s_rr[j]) || !isfinite(s_rz[j]) || !isfinite(s_bb[j])) nonfinite = true;
       }
@@ -683,8 +684,8 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           if (i == 0)
             sum_slots<NT>(gvals, G, J, J, tot, [&]() {
               for (int j = 0; j < J; ++j) {
-                const double pap = tot[j];
-                s_alpha[j] = (!s_done[j] && pap > 0.0) ? (float)(s_rz[j] / pap) : 0.f;
+                const float pap = tot[j];
+                s_alpha[j] = (!s_done[j] && pap > 0.f) ? s_rz[j] / pap : 0.f;
               }
             });
           if (!has) continue;
@@ -725,10 +726,10 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             bool nonfinite = false;
             for (int j = 0; j < J; ++j) {
               if (!s_done[j]) {
-                s_beta[j] = s_rz[j] > 0.0 ? (float)(tot[j] / s_rz[j]) : 0.f;
+                s_beta[j] = s_rz[j] > 0.f ? tot[j] / s_rz[j] : 0.f;
                 s_rz[j] = tot[j];
                 s_rr[j] = tot[J + j];
-                s_done[j] = !(s_rr[j] > a.tol2 * s_bb[j]) || !(s_rz[j] > 0.0);
+                s_done[j] = !(s_rr[j] > tol2f * s_bb[j]) || !(s_rz[j] > 0.f);
                 if (!isfinite(s_rr[j]) || !isfinite(s_rz[j])) nonfinite = true;
               } else {
                 s_beta[j] = 0.f;

@@ -170,6 +170,135 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows(RowsArgs a) {
   }
 }
 
+// The same partial inverse DFTs with the per-frequency products formed on the fly from the 3-D
+// spectra instead of read from a materialised Gram (for the video workload the Gram is [T x 8320
+// frequencies][2080 pairs]: 4.4 GB written and read again): per (tau, kh) the block stages the rows
+// z_hat_nk(tau, kh, .) it needs (the distinct k of its items, all n) and forms
+//     g[kw][q] = sum_n conj(A_nq(tau, kh, kw)) B_nq(tau, kh, kw)
+// with (A, B) = (z_hat_k, z_hat_k') for the pair items of the lag window (column order
+// k'(k'+1)/2 + k, mode 0) or (z_hat_k, x_hat_j) for the right-hand-side items k J + j (mode 1).
+struct RowsZArgs {
+  const float2* z3;    // [N][K][T][OM]
+  const float2* x3;    // [N][J][T][OM]
+  int N, K, J, np, T, La, Lb, offa, offb, mode;
+  float2* U;           // [T][np][La * Lb]
+  const float2* tab;   // as RowsArgs
+};
+constexpr int kRowsZMaxN = 2, kRowsZRows = 2 * kRowsPairs;
+
+__host__ __device__ inline size_t rowsz_smem(int N, int La, int Lb) {
+  return ((size_t)Wc * Lb + (size_t)H * La + (size_t)kRowsStages * kRowsZRows * N * Wc + (size_t)Wc * kRowsPairs) *
+         sizeof(float2);
+}
+
+__global__ void __launch_bounds__(kRowsNT) k_vl_rows_z(RowsZArgs a) {
+  extern __shared__ float2 sm[];
+  __shared__ const float2* rowp[kRowsZRows];   // row r: its map at n = 0 (tau and kh added per stage)
+  __shared__ size_t rown[kRowsZRows];          // row r: the map stride of n
+  __shared__ int qa[kRowsPairs], qb[kRowsPairs], s_nr;
+  float2* e1 = sm;                                  // [Wc][Lb]
+  float2* e2 = e1 + Wc * a.Lb;                      // [H][La]
+  float2* ring = e2 + H * a.La;                     // [kRowsStages][nr][N][Wc]
+  float2* gt = ring + kRowsStages * kRowsZRows * a.N * Wc;   // [Wc][kRowsPairs]
+  for (int i = threadIdx.x; i < Wc * a.Lb + H * a.La; i += kRowsNT) e1[i] = a.tab[i];   // e1 then e2
+  const int tau = blockIdx.y;
+  const int p0 = blockIdx.x * kRowsPairs;
+  const size_t map = (size_t)a.T * OM;
+  if (threadIdx.x == 0) {   // the distinct rows of the block's items
+    int nr = 0;
+    auto slot = [&](const float2* base, size_t nstride) {
+      for (int r = 0; r < nr; ++r)
+        if (rowp[r] == base) return r;
+      rowp[nr] = base;
+      rown[nr] = nstride;
+      return nr++;
+    };
+    for (int q = 0; q < kRowsPairs; ++q) {
+      const int p = min(p0 + q, a.np - 1);
+      int ka, kb;
+      if (a.mode == 0) {
+        int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+        while (kp * (kp + 1) / 2 > p) --kp;
+        while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
+        ka = p - kp * (kp + 1) / 2;
+        kb = kp;
+        qa[q] = slot(a.z3 + (size_t)ka * map, (size_t)a.K * map);
+        qb[q] = slot(a.z3 + (size_t)kb * map, (size_t)a.K * map);
+      } else {
+        ka = p / a.J;
+        kb = p - ka * a.J;
+        qa[q] = slot(a.z3 + (size_t)ka * map, (size_t)a.K * map);
+        qb[q] = slot(a.x3 + (size_t)kb * map, (size_t)a.J * map);
+      }
+    }
+    s_nr = nr;
+  }
+  __syncthreads();
+  const int nr = s_nr, NW = a.N * Wc, stage = nr * NW;
+  const int q = threadIdx.x / kRowsSub, sub = threadIdx.x % kRowsSub;
+  auto issue = [&](int kh) {
+    if (kh < H) {
+      float2* dst = ring + (kh % kRowsStages) * kRowsZRows * NW;
+      const size_t off = (size_t)tau * OM + (size_t)kh * Wc;
+      for (int i = threadIdx.x; i < stage; i += kRowsNT) {
+        const int r = i / NW, rem = i - r * NW, n = rem / Wc, kw = rem - n * Wc;
+        cp_async8(dst + i, rowp[r] + n * rown[r] + off + kw, true);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  for (int r = 0; r < kRowsStages - 1; ++r) issue(r);
+  float2 acc[2][kMaxL];
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+#pragma unroll
+    for (int h = 0; h < kMaxL; ++h) acc[w][h] = make_float2(0.f, 0.f);
+  for (int kh = 0; kh < H; ++kh) {
+    issue(kh + kRowsStages - 1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRowsStages - 1) : "memory");
+    __syncthreads();
+    const float2* rs = ring + (kh % kRowsStages) * kRowsZRows * NW;
+    for (int i = threadIdx.x; i < Wc * kRowsPairs; i += kRowsNT) {   // g[kw][qq], n in order
+      const int kw = i / kRowsPairs, qq = i - kw * kRowsPairs;
+      const float2* A = rs + qa[qq] * NW + kw;
+      const float2* B = rs + qb[qq] * NW + kw;
+      float2 g = make_float2(0.f, 0.f);
+      for (int n = 0; n < a.N; ++n) g = cfmac(A[n * Wc], B[n * Wc], g);
+      gt[i] = g;
+    }
+    __syncthreads();
+    const float2* g = gt + q;
+    float2 t[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int kw = 0; kw < Wc; ++kw) {
+      const float2 gv = g[kw * kRowsPairs];
+      const float2* e = e1 + kw * a.Lb + sub;
+#pragma unroll
+      for (int w = 0; w < 2; ++w)
+        if (sub + kRowsSub * w < a.Lb) t[w] = cfma(gv, e[kRowsSub * w], t[w]);
+    }
+    const float2* e = e2 + kh * a.La;
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int h = 0; h < kMaxL; ++h)
+        if (h < a.La) acc[w][h] = cfma(t[w], e[h], acc[w][h]);
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  const int p = p0 + q;
+  if (p >= a.np) return;
+  const int LL = a.La * a.Lb;
+  float2* out = a.U + ((size_t)tau * a.np + p) * LL;
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const int wi = sub + kRowsSub * w;
+    if (wi >= a.Lb) continue;
+#pragma unroll
+    for (int h = 0; h < kMaxL; ++h)
+      if (h < a.La) out[h * a.Lb + wi] = acc[w][h];
+  }
+}
+
 // C(ti, i) = (1/D) sum_tau Re(U[tau][p][i] e^{2 pi i tau (ti - offt) / T}); the same operations in the
 // same order for every (p, ti, i), so C(tau) is bitwise the same whichever thread forms it
 __device__ __forceinline__ float time_sum(const float2* U, const float2* twT, int np, int LL, int T, int p, int i,
@@ -726,12 +855,17 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   const int npmax = std::max(np, KJ);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = vl_alloc(p, bytes); };
+  // few videos: the per-frequency products are formed inside the partial inverse DFTs (k_vl_rows_z);
+  // else the frequency-major Gram on the tensor cores and the right-hand-side spectra are materialised
+  const bool fused = N <= kRowsZMaxN;
   A((void**)&V.z3, (size_t)N * K * O3 * sizeof(float2));
-  A((void**)&V.zt, (size_t)N * K * O3 * sizeof(float2));
   A((void**)&V.x3, (size_t)N * J * O3 * sizeof(float2));
-  A((void**)&V.gram, O3 * np * sizeof(float2));
-  A((void**)&V.rspec, (size_t)KJ * O3 * sizeof(float2));
-  A((void**)&V.rspecT, (size_t)KJ * O3 * sizeof(float2));
+  if (!fused) {
+    A((void**)&V.zt, (size_t)N * K * O3 * sizeof(float2));
+    A((void**)&V.gram, O3 * np * sizeof(float2));
+    A((void**)&V.rspec, (size_t)KJ * O3 * sizeof(float2));
+    A((void**)&V.rspecT, (size_t)KJ * O3 * sizeof(float2));
+  }
   A((void**)&V.U, (size_t)T * npmax * LLmax * sizeof(float2));
   A((void**)&V.lags, (size_t)K * K * Lt * La * Lb * sizeof(float));
   A((void**)&V.chat, (size_t)NF * K * K * sizeof(float2));
@@ -774,7 +908,7 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   k_dft_time<<<gx, 128, 0, st>>>(V.x2, V.x3, T);
   VL_CHECK(cudaGetLastError(), "time DFT");
   // 2. frequency-major codes and the Gram over the 3-D frequencies
-  {
+  if (!fused) {
     Ctx v = *c;
     v.g.Omega = (int)O3;
     v.L.zhat = V.z3;
@@ -792,10 +926,18 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   const size_t rsm = ((size_t)Wc * Lb + (size_t)H * La + (size_t)kRowsStages * Wc * kRowsPairs) * sizeof(float2);
   VL_CHECK(cudaFuncSetAttribute(k_vl_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm), "attribute");
   const float invD = 1.0f / (float)(O3 / Wc * W);   // 1 / (T H W)
+  const size_t zsm = rowsz_smem(N, std::max(La, fh), std::max(Lb, fw));
+  if (fused)
+    VL_CHECK(cudaFuncSetAttribute(k_vl_rows_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm), "attribute");
   {
     RowsArgs ra{V.gram, np, T, La, Lb, fh - 1, fw - 1, V.U, V.tab};
     k_vl_tables<<<(Wc * Lb + H * La + 255) / 256, 256, 0, st>>>(ra, V.tab);
-    k_vl_rows<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
+    if (fused) {
+      RowsZArgs rz{V.z3, V.x3, N, K, J, np, T, La, Lb, fh - 1, fw - 1, 0, V.U, V.tab};
+      k_vl_rows_z<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, zsm, st>>>(rz);
+    } else {
+      k_vl_rows<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
+    }
     VL_CHECK(cudaGetLastError(), "lag window rows");
     TimeArgs ta{V.U, np, T, Lt, La * Lb, ft - 1, K, J, invD, 1, V.lags};
     const long long nt = (long long)np * La * Lb;
@@ -805,7 +947,12 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   {
     RowsArgs ra{V.rspecT, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, V.U, V.tab};
     k_vl_tables<<<(Wc * fw + H * fh + 255) / 256, 256, 0, st>>>(ra, V.tab);
-    k_vl_rows<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
+    if (fused) {
+      RowsZArgs rz{V.z3, V.x3, N, K, J, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, 1, V.U, V.tab};
+      k_vl_rows_z<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, zsm, st>>>(rz);
+    } else {
+      k_vl_rows<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
+    }
     VL_CHECK(cudaGetLastError(), "right-hand side rows");
     TimeArgs ta{V.U, KJ, T, ft, fh * fw, (ft - 1) / 2, K, J, invD, 0, b};
     const long long nt = (long long)KJ * fh * fw;

@@ -106,9 +106,12 @@ def test_video_rejects_unsupported_shapes(csc):
 
 
 LEARN_CASES = [
-    # (N, K, J, T, ft, s, steps)
+    # (N, K, J, T, ft, s, steps); N <= 2 forms the per-frequency products inside the lag window's
+    # partial DFTs, N = 3 goes through the materialised tensor-core Gram
     (1, 3, 1, 6, 3, 5, 2),
     (1, 4, 3, 4, 3, 5, 2),
+    (2, 3, 3, 4, 3, 5, 2),
+    (3, 2, 1, 4, 3, 5, 2),
 ]
 
 
