@@ -177,32 +177,38 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows(RowsArgs a) {
 //     g[kw][q] = sum_n conj(A_nq(tau, kh, kw)) B_nq(tau, kh, kw)
 // with (A, B) = (z_hat_k, z_hat_k') for the pair items of the lag window (column order
 // k'(k'+1)/2 + k, mode 0) or (z_hat_k, x_hat_j) for the right-hand-side items k J + j (mode 1).
+// The first partial DFT pairs the outputs w = offb + m and offb - m: with g = gr + i gi and
+// e = c(kw) e^{2 pi i kw m / W} = ec + i es, the four sums of gr ec, gi es, gr es, gi ec give both,
+//     T(+m) = (A - B) + i (C + D),   T(-m) = (A + B) + i (D - C),
+// so a thread (item q, m = sub) does four FMAs and two shared-memory reads per kw for two outputs.
 struct RowsZArgs {
   const float2* z3;    // [N][K][T][OM]
   const float2* x3;    // [N][J][T][OM]
   int N, K, J, np, T, La, Lb, offa, offb, mode;
+  int ns, ni;          // threads per item (m = 0 .. ns - 1), items per block
   float2* U;           // [T][np][La * Lb]
   const float2* tab;   // as RowsArgs
 };
-constexpr int kRowsZMaxN = 2, kRowsZRows = 2 * kRowsPairs;
+// items per block, staged rows (each item needs at most two), ring depth; the twiddles of both partial
+// DFTs come from one 128-entry table (H = W = 128): 41 KB of shared memory for one video, four blocks
+// per SM
+constexpr int kRowsZMaxN = 2, kRowsZItems = 11, kRowsZRows = 2 * kRowsZItems, kRowsZStages = 3;
 
-__host__ __device__ inline size_t rowsz_smem(int N, int La, int Lb) {
-  return ((size_t)Wc * Lb + (size_t)H * La + (size_t)kRowsStages * kRowsZRows * N * Wc + (size_t)Wc * kRowsPairs) *
-         sizeof(float2);
+__host__ __device__ inline size_t rowsz_smem(int N) {
+  return ((size_t)W + (size_t)kRowsZStages * kRowsZRows * N * Wc + (size_t)Wc * kRowsZItems) * sizeof(float2);
 }
 
-__global__ void __launch_bounds__(kRowsNT) k_vl_rows_z(RowsZArgs a) {
+__global__ void __launch_bounds__(kRowsNT, 4) k_vl_rows_z(RowsZArgs a) {
   extern __shared__ float2 sm[];
   __shared__ const float2* rowp[kRowsZRows];   // row r: its map at n = 0 (tau and kh added per stage)
   __shared__ size_t rown[kRowsZRows];          // row r: the map stride of n
-  __shared__ int qa[kRowsPairs], qb[kRowsPairs], s_nr;
-  float2* e1 = sm;                                  // [Wc][Lb]
-  float2* e2 = e1 + Wc * a.Lb;                      // [H][La]
-  float2* ring = e2 + H * a.La;                     // [kRowsStages][nr][N][Wc]
-  float2* gt = ring + kRowsStages * kRowsZRows * a.N * Wc;   // [Wc][kRowsPairs]
-  for (int i = threadIdx.x; i < Wc * a.Lb + H * a.La; i += kRowsNT) e1[i] = a.tab[i];   // e1 then e2
-  const int tau = blockIdx.y;
-  const int p0 = blockIdx.x * kRowsPairs;
+  __shared__ int qa[kRowsZItems], qb[kRowsZItems], s_nr;
+  float2* w128 = sm;                                // e^{2 pi i m / 128}
+  float2* ring = w128 + W;                          // [kRowsZStages][nr][N][Wc]
+  float2* gt = ring + kRowsZStages * kRowsZRows * a.N * Wc;   // [Wc][ni]
+  for (int i = threadIdx.x; i < W; i += kRowsNT) w128[i] = root(i, W, 1.f);
+  const int tau = blockIdx.y, ni = a.ni, ns = a.ns;
+  const int p0 = blockIdx.x * ni;
   const size_t map = (size_t)a.T * OM;
   if (threadIdx.x == 0) {   // the distinct rows of the block's items
     int nr = 0;
@@ -213,32 +219,31 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows_z(RowsZArgs a) {
       rown[nr] = nstride;
       return nr++;
     };
-    for (int q = 0; q < kRowsPairs; ++q) {
+    for (int q = 0; q < ni; ++q) {
       const int p = min(p0 + q, a.np - 1);
-      int ka, kb;
       if (a.mode == 0) {
         int kp = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
         while (kp * (kp + 1) / 2 > p) --kp;
         while ((kp + 1) * (kp + 2) / 2 <= p) ++kp;
-        ka = p - kp * (kp + 1) / 2;
-        kb = kp;
-        qa[q] = slot(a.z3 + (size_t)ka * map, (size_t)a.K * map);
-        qb[q] = slot(a.z3 + (size_t)kb * map, (size_t)a.K * map);
+        qa[q] = slot(a.z3 + (size_t)(p - kp * (kp + 1) / 2) * map, (size_t)a.K * map);
+        qb[q] = slot(a.z3 + (size_t)kp * map, (size_t)a.K * map);
       } else {
-        ka = p / a.J;
-        kb = p - ka * a.J;
-        qa[q] = slot(a.z3 + (size_t)ka * map, (size_t)a.K * map);
-        qb[q] = slot(a.x3 + (size_t)kb * map, (size_t)a.J * map);
+        const int k = p / a.J;
+        qa[q] = slot(a.z3 + (size_t)k * map, (size_t)a.K * map);
+        qb[q] = slot(a.x3 + (size_t)(p - k * a.J) * map, (size_t)a.J * map);
       }
     }
     s_nr = nr;
   }
   __syncthreads();
   const int nr = s_nr, NW = a.N * Wc, stage = nr * NW;
-  const int q = threadIdx.x / kRowsSub, sub = threadIdx.x % kRowsSub;
+  const int q = threadIdx.x / ns, sub = threadIdx.x - q * ns;
+  const bool live = q < ni;
+  const int wp = a.offb + sub, wm = a.offb - sub;   // the thread's outputs w = offb + m, offb - m
+  const bool hp = live && wp < a.Lb, hm = live && sub > 0 && wm >= 0;
   auto issue = [&](int kh) {
     if (kh < H) {
-      float2* dst = ring + (kh % kRowsStages) * kRowsZRows * NW;
+      float2* dst = ring + (kh % kRowsZStages) * kRowsZRows * NW;
       const size_t off = (size_t)tau * OM + (size_t)kh * Wc;
       for (int i = threadIdx.x; i < stage; i += kRowsNT) {
         const int r = i / NW, rem = i - r * NW, n = rem / Wc, kw = rem - n * Wc;
@@ -247,19 +252,19 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows_z(RowsZArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  for (int r = 0; r < kRowsStages - 1; ++r) issue(r);
+  for (int r = 0; r < kRowsZStages - 1; ++r) issue(r);
   float2 acc[2][kMaxL];
 #pragma unroll
   for (int w = 0; w < 2; ++w)
 #pragma unroll
     for (int h = 0; h < kMaxL; ++h) acc[w][h] = make_float2(0.f, 0.f);
   for (int kh = 0; kh < H; ++kh) {
-    issue(kh + kRowsStages - 1);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRowsStages - 1) : "memory");
+    issue(kh + kRowsZStages - 1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRowsZStages - 1) : "memory");
     __syncthreads();
-    const float2* rs = ring + (kh % kRowsStages) * kRowsZRows * NW;
-    for (int i = threadIdx.x; i < Wc * kRowsPairs; i += kRowsNT) {   // g[kw][qq], n in order
-      const int kw = i / kRowsPairs, qq = i - kw * kRowsPairs;
+    const float2* rs = ring + (kh % kRowsZStages) * kRowsZRows * NW;
+    for (int i = threadIdx.x; i < Wc * ni; i += kRowsNT) {   // g[kw][qq], n in order
+      const int kw = i / ni, qq = i - kw * ni;
       const float2* A = rs + qa[qq] * NW + kw;
       const float2* B = rs + qb[qq] * NW + kw;
       float2 g = make_float2(0.f, 0.f);
@@ -267,36 +272,52 @@ __global__ void __launch_bounds__(kRowsNT) k_vl_rows_z(RowsZArgs a) {
       gt[i] = g;
     }
     __syncthreads();
-    const float2* g = gt + q;
-    float2 t[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (int kw = 0; kw < Wc; ++kw) {
-      const float2 gv = g[kw * kRowsPairs];
-      const float2* e = e1 + kw * a.Lb + sub;
-#pragma unroll
-      for (int w = 0; w < 2; ++w)
-        if (sub + kRowsSub * w < a.Lb) t[w] = cfma(gv, e[kRowsSub * w], t[w]);
-    }
-    const float2* e = e2 + kh * a.La;
-#pragma unroll
-    for (int w = 0; w < 2; ++w)
+    if (live) {
+      const float2* g = gt + q;
+      // c(kw) e^{2 pi i kw m / W} (c = 1 at kw = 0 and W / 2, else 2)
+      float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f;
+      int m = 0;
+      for (int kw = 0; kw < Wc; ++kw) {
+        const float2 gv = g[kw * ni];
+        const float cw = (kw == 0 || 2 * kw == W) ? 1.f : 2.f;
+        const float2 ev = make_float2(cw * w128[m].x, cw * w128[m].y);
+        m = (m + sub) & (W - 1);
+        sA = fmaf(gv.x, ev.x, sA);
+        sB = fmaf(gv.y, ev.y, sB);
+        sC = fmaf(gv.x, ev.y, sC);
+        sD = fmaf(gv.y, ev.x, sD);
+      }
+      const float2 t[2] = {make_float2(sA - sB, sC + sD), make_float2(sA + sB, sD - sC)};
+      // e^{2 pi i kh (h - offa) / H}
+      int m2 = (int)(((long long)kh * (H - a.offa)) & (H - 1));
 #pragma unroll
       for (int h = 0; h < kMaxL; ++h)
-        if (h < a.La) acc[w][h] = cfma(t[w], e[h], acc[w][h]);
+        if (h < a.La) {
+          const float2 e = w128[m2];
+          m2 = (m2 + kh) & (H - 1);
+#pragma unroll
+          for (int w = 0; w < 2; ++w) acc[w][h] = cfma(t[w], e, acc[w][h]);
+        }
+    }
     __syncthreads();
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   const int p = p0 + q;
-  if (p >= a.np) return;
+  if (!live || p >= a.np) return;
   const int LL = a.La * a.Lb;
   float2* out = a.U + ((size_t)tau * a.np + p) * LL;
 #pragma unroll
-  for (int w = 0; w < 2; ++w) {
-    const int wi = sub + kRowsSub * w;
-    if (wi >= a.Lb) continue;
-#pragma unroll
-    for (int h = 0; h < kMaxL; ++h)
-      if (h < a.La) out[h * a.Lb + wi] = acc[w][h];
+  for (int h = 0; h < kMaxL; ++h) {
+    if (h >= a.La) continue;
+    if (hp) out[h * a.Lb + wp] = acc[0][h];
+    if (hm) out[h * a.Lb + wm] = acc[1][h];
   }
+}
+
+// block shape of k_vl_rows_z for an output window of Lb columns around offb
+static void rowsz_shape(int Lb, int offb, int& ns, int& ni) {
+  ns = std::max(offb, Lb - 1 - offb) + 1;
+  ni = std::min(kRowsZItems, kRowsNT / ns);
 }
 
 // C(ti, i) = (1/D) sum_tau Re(U[tau][p][i] e^{2 pi i tau (ti - offt) / T}); the same operations in the
@@ -926,15 +947,16 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
   const size_t rsm = ((size_t)Wc * Lb + (size_t)H * La + (size_t)kRowsStages * Wc * kRowsPairs) * sizeof(float2);
   VL_CHECK(cudaFuncSetAttribute(k_vl_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm), "attribute");
   const float invD = 1.0f / (float)(O3 / Wc * W);   // 1 / (T H W)
-  const size_t zsm = rowsz_smem(N, std::max(La, fh), std::max(Lb, fw));
+  const size_t zsm = rowsz_smem(N);
   if (fused)
     VL_CHECK(cudaFuncSetAttribute(k_vl_rows_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm), "attribute");
   {
     RowsArgs ra{V.gram, np, T, La, Lb, fh - 1, fw - 1, V.U, V.tab};
     k_vl_tables<<<(Wc * Lb + H * La + 255) / 256, 256, 0, st>>>(ra, V.tab);
     if (fused) {
-      RowsZArgs rz{V.z3, V.x3, N, K, J, np, T, La, Lb, fh - 1, fw - 1, 0, V.U, V.tab};
-      k_vl_rows_z<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, zsm, st>>>(rz);
+      RowsZArgs rz{V.z3, V.x3, N, K, J, np, T, La, Lb, fh - 1, fw - 1, 0, 0, 0, V.U, V.tab};
+      rowsz_shape(Lb, fw - 1, rz.ns, rz.ni);
+      k_vl_rows_z<<<dim3((np + rz.ni - 1) / rz.ni, T), kRowsNT, zsm, st>>>(rz);
     } else {
       k_vl_rows<<<dim3((np + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
     }
@@ -948,8 +970,9 @@ csc_status video_learn(Ctx* c, const float* x, const float* z, float* d, double*
     RowsArgs ra{V.rspecT, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, V.U, V.tab};
     k_vl_tables<<<(Wc * fw + H * fh + 255) / 256, 256, 0, st>>>(ra, V.tab);
     if (fused) {
-      RowsZArgs rz{V.z3, V.x3, N, K, J, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, 1, V.U, V.tab};
-      k_vl_rows_z<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, zsm, st>>>(rz);
+      RowsZArgs rz{V.z3, V.x3, N, K, J, KJ, T, fh, fw, (fh - 1) / 2, (fw - 1) / 2, 1, 0, 0, V.U, V.tab};
+      rowsz_shape(fw, (fw - 1) / 2, rz.ns, rz.ni);
+      k_vl_rows_z<<<dim3((KJ + rz.ni - 1) / rz.ni, T), kRowsNT, zsm, st>>>(rz);
     } else {
       k_vl_rows<<<dim3((KJ + kRowsPairs - 1) / kRowsPairs, T), kRowsNT, rsm, st>>>(ra);
     }
