@@ -195,14 +195,13 @@ __global__ void __launch_bounds__(kLagSpecNT) k_lag_spectra(LagSpecArgs a) {
 //
 // One cooperative launch; CTA b owns the lag-grid bins [f0, f1) for the product and the filters
 // k = b, b + G, ... for everything else. An iteration has two grid-wide exchanges:
-//   A: after the product at its bins (y_hat to global) a CTA publishes its partial p . A p;
-//   B: after x, r and z = M^-1 r of its filters (z to global) it publishes partial r . z, r . r.
-// Exchanges carry no atomics and, but for the one at the end of a learning step, no fences: every
-// value that crosses CTAs (partial sums, y_hat, z) is stored as a 64-bit word (float bits |
-// epoch << 32), so a reader polls exactly the words it needs until they carry the current epoch:
-// one round trip to L2 per exchange. Partial sums go to per-CTA slots that alternate between two
-// banks by epoch parity (a CTA one exchange ahead never overwrites words a slower CTA still
-// reads) and are summed in CTA order, so every CTA gets the same totals.
+//   A: after the product at its bins (y_hat to global) a CTA contributes its partial p . A p;
+//   B: after x, r and z = M^-1 r of its filters (z to global) it contributes partial r . z, r . r.
+// An exchange is a counter that every CTA increments with release semantics once its data (plain
+// stores) and its partial sums (one slot per CTA, two banks alternating by exchange parity) are out;
+// a reader polls the counter with acquire loads (bounded by the context's wait limit), then reads the
+// slots and the data through L2 and sums the slots in a fixed order, so every CTA forms the same
+// scalars (in float32: the device's float64 rate is a few operations per clock per SM).
 // ---------------------------------------------------------------------------------------------
 struct CgArgs {
   int K, J, fh, fw, S2, La, Lb, NF, G, steps, cg_max;
@@ -210,13 +209,14 @@ struct CgArgs {
   const float* lags;   // [K][K][La*Lb]: the zero lag of C_kk (activity) and the preconditioner blocks
   const float2* chat;  // [NF][K(K+1)/2] lag spectra / (La Lb), pairs k <= k'
   int chat_smem;       // the CTA's bins of chat are staged in shared memory
-  unsigned long long* yw;   // [K][J][NF][2] words of y_hat (re, im), the product being formed
-  unsigned long long* zw;   // [K][J][S2] words of z = M^-1 r
+  float2* yv;          // [K][J][NF] y_hat, the product (written by the bins' CTAs)
+  float* zv;           // [K][J][S2] z = M^-1 r (written by the filters' CTAs)
   const float* b;      // [K][J][S2]
   float* x;            // [K][J][S2]  d (in/out)
   double* mu;          // [K]
   float* minv;         // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
-  unsigned long long* slots;   // [2][G][kSlotWords], zeroed before the launch
+  float* slots;        // [2][G][kSlotWords] partial sums of the exchanges (bank = exchange parity)
+  unsigned* arrivals;  // exchange counter: G arrivals per exchange, zeroed before the launch
   int* iters;          // [steps]
   int* err;
   long long spin;      // bound of every spin-wait, in SM clocks
@@ -267,14 +267,54 @@ __device__ __forceinline__ void axpy_from_l2(float* dst, const float* src, int n
   }
 }
 
+// thread 0: vals[0..n) into the CTA's slot of bank ep & 1, then release and count the arrival. The
+// caller has synchronised the block since its data stores.
+__device__ __forceinline__ void cg_arrive(const CgArgs& a, const float* vals, int n, unsigned ep) {
+  if (threadIdx.x != 0) return;
+  float* sl = a.slots + ((size_t)(ep & 1) * a.G + blockIdx.x) * kSlotWords;
+  for (int i = 0; i < n; ++i) sl[i] = vals[i];
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");   // release
+  atomicAdd(a.arrivals, 1u);
+}
+
+// Waits (thread 0, acquire, bounded) for the G arrivals of exchange ep, then loads the G x nw slot
+// values into gv (one round trip, all threads) and forms their totals in a fixed order (one warp per
+// value) into tot; then() runs on thread 0. Ends synchronised; false when the wait ran out or a CTA
+// flagged an error (error word set).
+template <int NT, class F>
+__device__ bool cg_wait(const CgArgs& a, unsigned ep, int nw, float* gv, float* tot, int* fail, F then) {
+  if (threadIdx.x == 0) {
+    const unsigned target = ep * (unsigned)a.G;
+    const long long t0 = clock64();
+    unsigned v;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.arrivals) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (*(volatile int*)a.err) { *fail = 1; break; }
+      if (clock64() - t0 > a.spin) {
+        atomicCAS(a.err, 0, (int)CSC_ERR_TIMEOUT);
+        *fail = 1;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (*fail) return false;
+  const float* sb = a.slots + (size_t)(ep & 1) * a.G * kSlotWords;
+  for (int i = threadIdx.x; i < a.G * nw; i += NT) gv[i] = __ldcg(sb + (size_t)(i / nw) * kSlotWords + i % nw);
+  __syncthreads();
+  sum_slots<NT>(gv, a.G, nw, nw, tot, then);
+  return true;
+}
+
 // Lag-grid half spectrum of S Z^T Z S^T p at this CTA's bins, p (all filters) in shared memory:
-// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yw with epoch ep (C_hat_kk' = conj C_hat_k'k for k > k'),
+// y_hat_kj(f) = sum_k' C_hat_kk'(f) p_hat_k'j(f) to a.yv (C_hat_kk' = conj C_hat_k'k for k > k'),
 // and the partial Parseval sums of p . S Z^T Z S^T p over these bins (weight 2 for w2 > 0) into
 // part[j]. ew[i][q] holds the tap twiddles of the CTA's bin f0 + i, cch the CTA's bins of chat (or
 // null: read from global), both in pair_index order. Does not end synchronised.
 template <int NT, int JT>
 __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, const float2* ew, float2* phat,
-                             float2* red, const float2* cch, float (&part)[JT], unsigned ep) {
+                             float2* red, const float2* cch, float (&part)[JT]) {
   constexpr int J = JT;
   const int K = a.K, S2 = a.S2, fw = a.fw, NF = a.NF;
   const int KJ = K * J;
@@ -349,9 +389,7 @@ __device__ void product_bins(const CgArgs& a, int f0, int nbc, const float* pp, 
     const int f = f0 + bi, w2 = f % fw;
     float2 s = make_float2(0.f, 0.f);
     for (int pi = 0; pi < PS; ++pi) s = cadd(s, red[(((size_t)bi * PS + pi) * K + k) * J + j]);
-    unsigned long long* w = a.yw + 2 * ((size_t)i * NF + f);
-    st_volatile_u64(w, tag(s.x, ep));
-    st_volatile_u64(w + 1, tag(s.y, ep));
+    a.yv[(size_t)i * NF + f] = s;
     const float2 p = phat[e];
     add_at(part, j, (w2 == 0 ? 1.f : 2.f) * (p.x * s.x + p.y * s.y));
   }
@@ -402,12 +440,12 @@ __device__ void product_taps(const CgArgs& a, const float2* yh, float2* sc, cons
   }
 }
 
-// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zw (epoch ep); the
+// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zv; the
 // partial r . z into part[j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the CTA owns
 // one filter, else global), else the diagonal. Four lanes of a warp share one tap.
 template <int NT, int N>
 __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc,
-                                               const float* r, float* zo, float (&part)[N], unsigned ep) {
+                                               const float* r, float* zo, float (&part)[N]) {
   const int S2 = a.S2, JS = a.J * S2;
   const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
   const int sub = threadIdx.x & 3;
@@ -430,7 +468,7 @@ __device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act,
     zv += __shfl_xor_sync(0xffffffffu, zv, 2);
     if (sub == 0 && o0 < JS) {
       zo[o] = zv;
-      st_volatile_u64(a.zw + (size_t)k * JS + o, tag(zv, ep));
+      a.zv[(size_t)k * JS + o] = zv;
       add_at(part, j, r[o] * zv);
     }
   }
@@ -556,9 +594,12 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   }
   const float* mk = own_one ? mloc : nullptr;
 
-  constexpr int UY = 6;    // y_hat words per thread: 2 J NF <= UY NT
-  constexpr int UZ = 12;   // z words per thread and pass
-  const int nyw = 2 * J * a.NF, nz = K * JS;
+  const int NF = a.NF, nz = K * JS;
+  // y_hat of the CTA's filter k into yh (read through L2 after an exchange)
+  auto load_y = [&](int k) {
+    const float2* src = a.yv + (size_t)k * J * NF;
+    for (int i = threadIdx.x; i < J * NF; i += NT) yh[i] = __ldcg(src + i);
+  };
   for (int step = 0; step < a.steps; ++step) {
     if (threadIdx.x < nown) {
       const int k = blockIdx.x + threadIdx.x * G;
@@ -573,24 +614,19 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       float pa[J];
 #pragma unroll
       for (int j = 0; j < J; ++j) pa[j] = 0.f;
-      product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa, ep + 1);
+      product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
     }
-    publish<0>(a.slots, G, nullptr, ++ep);   // no sums: an exchange of y_hat only
+    __syncthreads();
+    cg_arrive(a, nullptr, 0, ++ep);   // no sums: an exchange of y_hat only
+    if (!cg_wait<NT>(a, ep, 0, gvals, tot, &s_fail, [] {})) return;
     {
       float w3[3 * J];   // r . z, r . r, b . b
 #pragma unroll
       for (int u = 0; u < 3 * J; ++u) w3[u] = 0.f;
       for (int i = 0; i < nown; ++i) {
         const int k = blockIdx.x + i * G;
-        unsigned long long yv[UY];
-        if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, 1, ep, gvals, a.yw + (size_t)k * nyw, nyw, yv, a.err, a.spin))
-          s_fail = 1;
-        float* yhf = reinterpret_cast<float*>(yh);
-#pragma unroll
-        for (int u = 0; u < UY; ++u)
-          if ((int)threadIdx.x + u * NT < nyw) yhf[threadIdx.x + u * NT] = word_value(yv[u]);
+        load_y(k);
         __syncthreads();
-        if (s_fail) return;
         float* r = orr + (size_t)i * JS;
         product_taps<NT>(a, yh, sc, twa, twb, r);   // r <- (S Z^T Z S^T x)_k
         const bool act = s_act[i];
@@ -603,46 +639,32 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           if (act) add_at(w3, 2 * J + j, bv * bv);
         }
         __syncthreads();
-        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3, ep + 1);
-      }
-      if (nown == 0) {   // the exchange's slot words still have to be seen
-        unsigned long long none[1];
-        if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err, a.spin)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) return;
+        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3);
       }
       block_reduce_to0<NT>(w3, scratch);
-      publish<3 * J>(a.slots, G, w3, ++ep);
+      cg_arrive(a, w3, 3 * J, ++ep);
     }
     // all z (and the sums) of exchange ep: p = z
-    for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
-      unsigned long long zv[UZ];
-      if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 3 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT), zv,
-                              a.err, a.spin))
-        s_fail = 1;
-      __syncthreads();
-      if (s_fail) return;
-#pragma unroll
-      for (int u = 0; u < UZ; ++u)
-        if (c0 + (int)threadIdx.x + u * NT < nz) pp[c0 + threadIdx.x + u * NT] = word_value(zv[u]);
-    }
-    sum_slots<NT>(gvals, G, 3 * J, 3 * J, tot, [&]() {
-      int all = 1;
-      bool nonfinite = false;
-      for (int j = 0; j < J; ++j) {
-        s_rz[j] = tot[j];
-        s_rr[j] = tot[J + j];
-        s_bb[j] = tot[2 * J + j];
-        s_done[j] = !(s_rr[j] > tol2f * s_bb[j]) || !(s_rz[j] > 0.f);
-        all = all && s_done[j];
-        if (!isfinite(s_rr[j]) || !isfinite(s_rz[j]) || !isfinite(s_bb[j])) nonfinite = true;
-      }
-      if (nonfinite) {   // the same totals in every CTA: all of them stop here together
-        if (blockIdx.x == 0) atomicCAS(a.err, 0, (int)CSC_ERR_NONFINITE);
-        all = 1;
-      }
-      s_all = all;
-    });
+    if (!cg_wait<NT>(a, ep, 3 * J, gvals, tot, &s_fail, [&]() {
+          int all = 1;
+          bool nonfinite = false;
+          for (int j = 0; j < J; ++j) {
+            s_rz[j] = tot[j];
+            s_rr[j] = tot[J + j];
+            s_bb[j] = tot[2 * J + j];
+            s_done[j] = !(s_rr[j] > tol2f * s_bb[j]) || !(s_rz[j] > 0.f);
+            all = all && s_done[j];
+            if (!isfinite(s_rr[j]) || !isfinite(s_rz[j]) || !isfinite(s_bb[j])) nonfinite = true;
+          }
+          if (nonfinite) {   // the same totals in every CTA: all of them stop here together
+            if (blockIdx.x == 0) atomicCAS(a.err, 0, (int)CSC_ERR_NONFINITE);
+            all = 1;
+          }
+          s_all = all;
+        }))
+      return;
+    axpy_from_l2<NT>(pp, a.zv, nz, JS, S2, nullptr, true);
+    __syncthreads();
     int it = 0;
     for (; it < a.cg_max; ++it) {
       if (s_all) break;   // the same totals in every CTA
@@ -651,7 +673,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
         float pa[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) pa[j] = 0.f;
-        product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa, ep + 1);
+        product_bins<NT, J>(a, f0, nbc, pp, ew, phat, red, cch, pa);
         for (int i = 0; i < nown; ++i) {
           if (!s_act[i]) continue;
           const int k = blockIdx.x + i * G;
@@ -661,38 +683,25 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           }
         }
         block_reduce_to0<NT>(pa, scratch);
-        publish<J>(a.slots, G, pa, ++ep);
+        cg_arrive(a, pa, J, ++ep);
       }
       // ---- x += alpha p, r -= alpha A p, z = M^{-1} r (exchange B) ---------------------------
+      if (!cg_wait<NT>(a, ep, J, gvals, tot, &s_fail, [&]() {
+            for (int j = 0; j < J; ++j) {
+              const float pap = tot[j];
+              s_alpha[j] = (!s_done[j] && pap > 0.f) ? s_rz[j] / pap : 0.f;
+            }
+          }))
+        return;
       {
         float w2[2 * J];   // r . z, r . r
 #pragma unroll
         for (int u = 0; u < 2 * J; ++u) w2[u] = 0.f;
-        for (int i = 0; i < nown + (nown == 0 ? 1 : 0); ++i) {
+        for (int i = 0; i < nown; ++i) {
           const int k = blockIdx.x + i * G;
-          const bool has = i < nown;
-          unsigned long long yv[UY];
-          if (!wait_words<NT, UY>(i == 0 ? a.slots : nullptr, G, J, ep, gvals, has ? a.yw + (size_t)k * nyw : nullptr,
-                                  has ? nyw : 0, yv, a.err, a.spin))
-            s_fail = 1;
-          float* yhf = reinterpret_cast<float*>(yh);
-#pragma unroll
-          for (int u = 0; u < UY; ++u)
-            if (has && (int)threadIdx.x + u * NT < nyw) yhf[threadIdx.x + u * NT] = word_value(yv[u]);
+          if (!s_act[i]) continue;   // z_k stays 0
+          load_y(k);
           __syncthreads();
-          if (s_fail) return;
-          if (i == 0)
-            sum_slots<NT>(gvals, G, J, J, tot, [&]() {
-              for (int j = 0; j < J; ++j) {
-                const float pap = tot[j];
-                s_alpha[j] = (!s_done[j] && pap > 0.f) ? s_rz[j] / pap : 0.f;
-              }
-            });
-          if (!has) continue;
-          if (!s_act[i]) {   // z_k stays 0, but its words carry every exchange's epoch
-            for (int o = threadIdx.x; o < JS; o += NT) st_volatile_u64(a.zw + (size_t)k * JS + o, tag(0.f, ep + 1));
-            continue;
-          }
           float* r = orr + (size_t)i * JS;
           float* yk = oz + (size_t)i * JS;   // A p of the filter, then z
           product_taps<NT>(a, yh, sc, twa, twb, yk);
@@ -707,21 +716,13 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             add_at(w2, J + j, rv * rv);
           }
           __syncthreads();
-          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2, ep + 1);
+          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2);
         }
         block_reduce_to0<NT>(w2, scratch);
-        publish<2 * J>(a.slots, G, w2, ++ep);
+        cg_arrive(a, w2, 2 * J, ++ep);
       }
       // ---- p = z + beta p: every CTA keeps the whole search direction ------------------------
-      for (int c0 = 0; c0 < nz; c0 += UZ * NT) {
-        unsigned long long zv[UZ];
-        if (!wait_words<NT, UZ>(c0 == 0 ? a.slots : nullptr, G, 2 * J, ep, gvals, a.zw + c0, min(nz - c0, UZ * NT),
-                                zv, a.err, a.spin))
-          s_fail = 1;
-        __syncthreads();
-        if (s_fail) return;
-        if (c0 == 0)
-          sum_slots<NT>(gvals, G, 2 * J, 2 * J, tot, [&]() {
+      if (!cg_wait<NT>(a, ep, 2 * J, gvals, tot, &s_fail, [&]() {
             int all = 1;
             bool nonfinite = false;
             for (int j = 0; j < J; ++j) {
@@ -741,13 +742,18 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
               all = 1;
             }
             s_all = all;
-          });
+          }))
+        return;
+      {
+        constexpr int U = 24;   // z values per thread in flight
+        for (int i0 = threadIdx.x; i0 < nz; i0 += U * NT) {
+          float v[U];
 #pragma unroll
-        for (int u = 0; u < UZ; ++u) {
-          const int idx = c0 + threadIdx.x + u * NT;
-          if (idx < nz) {
-            const float bt = s_beta[J == 1 ? 0 : (idx % JS) / S2];
-            pp[idx] = fmaf(bt, pp[idx], word_value(zv[u]));
+          for (int u = 0; u < U; ++u) v[u] = (i0 + u * NT < nz) ? __ldcg(a.zv + i0 + u * NT) : 0.f;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int idx = i0 + u * NT;
+            if (idx < nz) pp[idx] = fmaf(s_beta[J == 1 ? 0 : (idx % JS) / S2], pp[idx], v[u]);
           }
         }
       }
@@ -768,14 +774,8 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
       __syncthreads();
     }
     __syncthreads();
-    publish<0>(a.slots, G, nullptr, ++ep, true);   // x (plain stores) complete everywhere before the next step
-    {
-      unsigned long long none[1];
-      if (!wait_words<NT, 1>(a.slots, G, 1, ep, gvals, nullptr, 0, none, a.err, a.spin)) s_fail = 1;
-      if (threadIdx.x < G) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire before reading x
-      __syncthreads();
-      if (s_fail) return;
-    }
+    cg_arrive(a, nullptr, 0, ++ep);   // x (plain stores) complete everywhere before the next step
+    if (!cg_wait<NT>(a, ep, 0, gvals, tot, &s_fail, [] {})) return;
   }
   // ---- d_k <- d_k / max(1, ||d_k||) ---------------------------------------------------------
   for (int i = 0; i < nown; ++i) {
@@ -1157,16 +1157,18 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   a.La = 2 * c.fh - 1; a.Lb = 2 * c.fw - 1; a.NF = a.La * c.fw;
   a.G = 0; a.steps = steps; a.cg_max = c.p.cg_max;
   a.tol2 = c.p.cg_tol * c.p.cg_tol; a.mu_floor = kMuFloor;
-  const size_t nvec = (size_t)c.K * c.J * c.S2;
-  a.lags = c.L.lags; a.chat = c.L.chat; a.yw = c.L.yw; a.zw = c.L.zw; a.b = c.L.b; a.x = d;
-  a.mu = c.L.mu; a.minv = c.L.minv; a.slots = c.L.slots; a.iters = c.L.iters; a.err = dev_err;
+  a.lags = c.L.lags; a.chat = c.L.chat; a.b = c.L.b; a.x = d;
+  a.yv = reinterpret_cast<float2*>(c.L.yw);   // the words buffers hold the plain values
+  a.zv = reinterpret_cast<float*>(c.L.zw);
+  a.mu = c.L.mu; a.minv = c.L.minv; a.iters = c.L.iters; a.err = dev_err;
   a.spin = c.wait_limit > 0 ? c.wait_limit : kSpinLimit;
   // the grid: one CTA per SM at most (every CTA must be resident: the exchanges wait on all)
   a.G = learn_cg_ctas(c);
-  // epochs restart at 1 every launch: clear every word that carries one
-  cudaError_t e = cudaMemsetAsync(c.L.slots, 0, (size_t)2 * a.G * kSlotWords * sizeof(unsigned long long), c.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c.L.yw, 0, (size_t)2 * c.K * c.J * a.NF * sizeof(unsigned long long), c.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c.L.zw, 0, nvec * sizeof(unsigned long long), c.stream);
+  // the exchange counter restarts at 0 every launch; the slots (floats, then the counter) live in
+  // the slot buffer
+  a.slots = reinterpret_cast<float*>(c.L.slots);
+  a.arrivals = reinterpret_cast<unsigned*>(a.slots + (size_t)2 * a.G * kSlotWords);
+  cudaError_t e = cudaMemsetAsync(a.arrivals, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
   auto kern = c.J == 1 ? k_learn_cg<NT, 1> : c.J == 2 ? k_learn_cg<NT, 2> : k_learn_cg<NT, 3>;
   // the CTA's bins of the lag spectra stay in shared memory when they fit
