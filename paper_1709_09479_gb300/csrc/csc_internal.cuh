@@ -229,13 +229,13 @@ struct LearnBuffers {
                             // column order k'(k'+1)/2 + k (tensor-core Gram)
   float* lags = nullptr;    // [K][K][L*L]
   float2* chat = nullptr;   // [NF][K(K+1)/2] lag spectra / (La Lb), NF = La * fw
-  unsigned long long* yw = nullptr;   // [K][J][NF][2] epoch-tagged words of the CG product spectrum
-  unsigned long long* zw = nullptr;   // [K][J][S2] epoch-tagged words of z = M^-1 r
+  unsigned long long* yw = nullptr;   // the CG product spectrum, [K][J][NF] c64 (allocated as 2x that)
+  unsigned long long* zw = nullptr;   // the CG's z = M^-1 r, [K][J][S2] f32 (allocated as 2x that)
   float* b = nullptr;       // [K][J][S2]
   float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
   double* mu = nullptr;     // [K]
   float* minv = nullptr;    // [K][S2][S2] block-Jacobi inverses (S2 <= kMaxBlockJacobi)
-  unsigned long long* slots = nullptr;   // [2][G][4 kMaxJ] CG exchange words (sum | epoch)
+  unsigned long long* slots = nullptr;   // CG partial sums [2][G][4 kMaxJ] f32, then the arrival counter
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
   float2* rspec = nullptr;  // [K][J][Omega] right-hand-side spectra from the tensor-core Gram
