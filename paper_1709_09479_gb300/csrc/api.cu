@@ -118,7 +118,7 @@ void free_all(Ctx* c) {
   }
   c->events.clear();
   void* ptrs[] = {c->xext, c->tw, c->dhat, c->dhatp, c->dhatp16, c->dhat16, c->L.rspec, c->L.zt, c->L.lagT, c->xhat, c->pdiag, c->pmat, c->part[0], c->part[1], c->l1, c->objimg,
-                  c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.minv, c->L.slots,
+                  c->err, c->L.zhat, c->L.gram, c->L.lags, c->L.chat, c->L.yw, c->L.zw, c->L.b, c->L.vec, c->L.mu, c->L.slots,
                   c->L.iters, c->st_x, c->st_d, c->st_v, c->st_z, c->st_mu, c->B.seg, c->B.vbar,
                   c->B.gspec, c->B.S, c->B.Xb, c->B.part[0], c->B.part[1], c->B.spec,
                   c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1,
@@ -553,7 +553,7 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
   if (cudaGetDevice(&tmp.device) != cudaSuccess) return cuda_fail(nullptr, cudaGetLastError(), "cudaGetDevice");
   cudaError_t e = cudaDeviceGetAttribute(&tmp.nsm, cudaDevAttrMultiProcessorCount, tmp.device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
-  const size_t cg_smem = learn_cg_smem_bytes(tmp, tmp.S2 <= kMaxBlockJacobi, false);
+  const size_t cg_smem = learn_cg_smem_bytes(tmp, false);
   if (!video && (cg_smem > kSmemLimit || !learn_cg_shape_ok(tmp)))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init: K * J * fh * fw too large for the learning kernel");
   const long long NK = (long long)tmp.N * tmp.K;
@@ -1158,7 +1158,6 @@ static csc_status learn_prepare(Ctx* c, int steps, const char* who) {
         (gram_tc_applies(*c) && (ensure_alloc(&L.rspec, (size_t)K * J * Om) != cudaSuccess ||
                                  ensure_alloc(&L.zt, (size_t)c->N * K * Om) != cudaSuccess ||
                                  ensure_alloc(&L.lagT, lag_sep_T_count(*c)) != cudaSuccess)) ||
-        (c->S2 <= kMaxBlockJacobi && ensure_alloc(&L.minv, (size_t)K * c->S2 * c->S2) != cudaSuccess) ||
         ensure_alloc(&L.slots, (size_t)2 * c->nsm * 4 * kMaxJ) != cudaSuccess) {
       cudaGetLastError();
       return fail(c, CSC_ERR_WORKSPACE, std::string(who) + ": device workspace allocation failed");

@@ -18,7 +18,6 @@ constexpr int kNTSweep = 512;         // threads of the coding sweep
 constexpr int kMaxJ = 3;
 constexpr size_t kSmemLimit = 232448; // 227 KB opt-in shared memory per CTA
 constexpr double kMuFloor = 1e-8;
-constexpr int kMaxBlockJacobi = 128;  // filters with more taps use the scalar Jacobi preconditioner
 
 enum SweepMode { kPrologue = 0, kIter = 1, kLast = 2, kObjective = 3 };
 
@@ -234,7 +233,6 @@ struct LearnBuffers {
   float* b = nullptr;       // [K][J][S2]
   float* vec = nullptr;     // r, z, p, Ap: 4 x [K][J][S2]
   double* mu = nullptr;     // [K]
-  float* minv = nullptr;    // [K][S2][S2] block-Jacobi inverses (S2 <= kMaxBlockJacobi)
   unsigned long long* slots = nullptr;   // CG partial sums [2][G][4 kMaxJ] f32, then the arrival counter
   int* iters = nullptr;     // [steps_cap]
   int steps_cap = 0;
@@ -428,7 +426,7 @@ cudaError_t launch_lag_spectra(const Ctx& c);      // L.chat from L.lags (both l
 size_t lag_sep_T_count(const Ctx& c);
 cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err);
 bool learn_cg_shape_ok(const Ctx& c);   // filters per CTA <= 8 and 2 J NF <= 6 NT
-size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem);
+size_t learn_cg_smem_bytes(const Ctx& c, bool chat_smem);
 // spectra of nmaps real maps (codes), out[m][Omega]: the fused-sweep passes for 128 x 128 maps,
 // else the generic FFT
 cudaError_t launch_code_spectra(const Ctx& c, const float* in, int nmaps, float2* out);

@@ -214,7 +214,6 @@ struct CgArgs {
   const float* b;      // [K][J][S2]
   float* x;            // [K][J][S2]  d (in/out)
   double* mu;          // [K]
-  float* minv;         // [K][S2][S2] block-Jacobi inverses (null: scalar Jacobi)
   float* slots;        // [2][G][kSlotWords] partial sums of the exchanges (bank = exchange parity)
   unsigned* arrivals;  // exchange counter: G arrivals per exchange, zeroed before the launch
   int* iters;          // [steps]
@@ -224,11 +223,11 @@ struct CgArgs {
 
 // shared-memory layout of the CG kernel (float2 arrays first, then floats)
 struct CgSmem {
-  size_t ew, phat, red, yh, sc, twa, twb, cch, pp, own, mloc, total_floats;
+  size_t ew, phat, red, yh, sc, twa, twb, cch, pp, own, total_floats;
   int nb, nown;
 };
 CSC_HD CgSmem cg_smem_layout(int K, int J, int S2, int NF, int fh, int fw, int La, int Lb, int NT, int G,
-                             bool minv, bool chat_smem) {
+                             bool chat_smem) {
   CgSmem L;
   L.nb = (NF + G - 1) / G;        // bins per CTA (at most)
   L.nown = (K + G - 1) / G;       // filters per CTA (at most)
@@ -244,7 +243,6 @@ CSC_HD CgSmem cg_smem_layout(int K, int J, int S2, int NF, int fh, int fw, int L
   L.cch = o;  o += chat_smem ? 2 * (size_t)L.nb * (K * (K + 1) / 2) : 0;
   L.pp = o;   o += (size_t)K * J * S2;
   L.own = o;  o += 4 * (size_t)L.nown * J * S2;   // x, r, b, z of the CTA's filters
-  L.mloc = o; o += minv ? (size_t)S2 * S2 + 2 * S2 : 0;
   L.total_floats = o;
   return L;
 }
@@ -440,37 +438,20 @@ __device__ void product_taps(const CgArgs& a, const float2* yh, float2* sc, cons
   }
 }
 
-// z = M_k^{-1} r for one filter (r complete in shared memory), written to zo and to a.zv; the
-// partial r . z into part[j]. M_k^{-1}: the block-Jacobi inverse (shared memory when the CTA owns
-// one filter, else global), else the diagonal. Four lanes of a warp share one tap.
+// z = M_k^{-1} r for one filter (r complete in shared memory) with the Jacobi preconditioner
+// M_k^{-1} = 1 / (C_kk(0) + 2 mu_k) of the current step, written to zo and to a.zv; the partial r . z
+// into part[j]. (A block-Jacobi inverse of the filter's Toeplitz block, formed once per call, was
+// tried: it goes stale as mu grows from step to step, and took more CG iterations than this one.)
 template <int NT, int N>
-__device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* mloc,
-                                               const float* r, float* zo, float (&part)[N]) {
+__device__ __forceinline__ void precondition_k(const CgArgs& a, int k, bool act, float sjac, const float* r,
+                                               float* zo, float (&part)[N]) {
   const int S2 = a.S2, JS = a.J * S2;
-  const float* m = mloc ? mloc : (a.minv ? a.minv + (size_t)k * S2 * S2 : nullptr);
-  const int sub = threadIdx.x & 3;
-  for (int o0 = threadIdx.x >> 2; o0 < ((JS + 7) / 8) * 8; o0 += NT / 4) {
-    const int o = o0 < JS ? o0 : JS - 1;
-    const int j = o / S2, q = o - j * S2;
-    float zv = 0.f;
-    if (act) {
-      if (m) {
-        // M_k^{-1} is symmetric: column q
-        const float* rj = r + (size_t)j * S2;
-        float sacc = 0.f;
-        for (int q2 = sub; q2 < S2; q2 += 4) sacc = fmaf(m[(size_t)q2 * S2 + q], rj[q2], sacc);
-        zv = sacc;
-      } else if (sub == 0) {
-        zv = r[o] * sjac;
-      }
-    }
-    zv += __shfl_xor_sync(0xffffffffu, zv, 1);
-    zv += __shfl_xor_sync(0xffffffffu, zv, 2);
-    if (sub == 0 && o0 < JS) {
-      zo[o] = zv;
-      a.zv[(size_t)k * JS + o] = zv;
-      add_at(part, j, r[o] * zv);
-    }
+  for (int o = threadIdx.x; o < JS; o += NT) {
+    const int j = o / S2;
+    const float zv = act ? r[o] * sjac : 0.f;
+    zo[o] = zv;
+    a.zv[(size_t)k * JS + o] = zv;
+    add_at(part, j, r[o] * zv);
   }
 }
 
@@ -491,7 +472,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   constexpr int J = JT;
   const int K = a.K, S2 = a.S2, G = a.G;
   const int JS = J * S2;
-  const CgSmem Ls = cg_smem_layout(K, J, S2, a.NF, a.fh, a.fw, a.La, a.Lb, NT, G, a.minv != nullptr, a.chat_smem);
+  const CgSmem Ls = cg_smem_layout(K, J, S2, a.NF, a.fh, a.fw, a.La, a.Lb, NT, G, a.chat_smem);
   float2* ew = reinterpret_cast<float2*>(smf + Ls.ew);
   float2* phat = reinterpret_cast<float2*>(smf + Ls.phat);
   float2* red = reinterpret_cast<float2*>(smf + Ls.red);
@@ -505,9 +486,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   float* orr = ox + (size_t)Ls.nown * JS;
   float* ob = orr + (size_t)Ls.nown * JS;
   float* oz = ob + (size_t)Ls.nown * JS;
-  float* mloc = smf + Ls.mloc;                   // [S2][S2] (+ 2 [S2] during the inversion)
   const int nown = (blockIdx.x < K) ? (K - 1 - blockIdx.x) / G + 1 : 0;
-  const bool own_one = (G >= K) && a.minv;       // at most one filter per CTA: keep its inverse
   const int La = a.La, Lb = a.Lb, ctr = (a.fh - 1) * Lb + (a.fw - 1);   // lag tau = 0
   const int f0 = (int)((long long)blockIdx.x * a.NF / G), f1 = (int)((long long)(blockIdx.x + 1) * a.NF / G);
   const int nbc = f1 - f0;
@@ -545,54 +524,6 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
   }
   __syncthreads();
 
-  // ---- block-Jacobi preconditioner for this call: inverse of (C_kk Toeplitz + 2 mu_k I) -------
-  // (the mu at entry; the preconditioner need not track the later mu updates exactly)
-  if (a.minv) {
-    float* A = mloc;                    // [S2][S2]
-    float* colv = A + (size_t)S2 * S2;  // [S2] pivot column, then [S2] pivot row
-    const int fh = a.fh, fw = a.fw;
-    for (int i = 0; i < nown; ++i) {
-      const int k = blockIdx.x + i * G;
-      const bool act = s_act[i];
-      const float tm = (float)(2.0 * a.mu[k]);
-      const float* C = a.lags + ((size_t)k * K + k) * La * Lb;
-      for (int e = threadIdx.x; e < S2 * S2; e += NT) {
-        const int q = e / S2, q2 = e - q * S2;
-        const int qa = q / fw, qb = q - qa * fw, qa2 = q2 / fw, qb2 = q2 - qa2 * fw;
-        const float diag = (q == q2) ? 1.f : 0.f;
-        A[e] = act ? C[(qa - qa2 + fh - 1) * Lb + (qb - qb2 + fw - 1)] + tm * diag : diag;
-      }
-      __syncthreads();
-      // in-place Gauss-Jordan inversion (symmetric positive definite: no pivoting); per pivot the
-      // pivot column and row are copied out, then every thread updates its elements
-      float* prow = colv + S2;
-      for (int pv = 0; pv < S2; ++pv) {
-        for (int r = threadIdx.x; r < S2; r += NT) {
-          colv[r] = A[(size_t)r * S2 + pv];
-          prow[r] = A[(size_t)pv * S2 + r];
-        }
-        __syncthreads();
-        const float inv = 1.f / colv[pv];
-        int i = threadIdx.x / S2, j = threadIdx.x - (threadIdx.x / S2) * S2;
-        const int di = NT / S2, dj = NT - (NT / S2) * S2;
-        for (int e = threadIdx.x; e < S2 * S2; e += NT) {
-          float* el = A + (size_t)i * S2 + j;
-          if (i == pv) *el = (j == pv) ? inv : prow[j] * inv;
-          else *el = (j == pv) ? -colv[i] * inv : fmaf(-colv[i] * inv, prow[j], *el);
-          i += di;
-          j += dj;
-          if (j >= S2) { j -= S2; ++i; }
-        }
-        __syncthreads();
-      }
-      if (!own_one) {
-        float* dst = a.minv + (size_t)k * S2 * S2;
-        for (int e = threadIdx.x; e < S2 * S2; e += NT) dst[e] = A[e];
-      }
-      __syncthreads();
-    }
-  }
-  const float* mk = own_one ? mloc : nullptr;
 
   const int NF = a.NF, nz = K * JS;
   // y_hat of the CTA's filter k into yh (read through L2 after an exchange)
@@ -639,7 +570,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
           if (act) add_at(w3, 2 * J + j, bv * bv);
         }
         __syncthreads();
-        precondition_k<NT>(a, k, act, s_jac[i], mk, r, oz + (size_t)i * JS, w3);
+        precondition_k<NT>(a, k, act, s_jac[i], r, oz + (size_t)i * JS, w3);
       }
       block_reduce_to0<NT>(w3, scratch);
       cg_arrive(a, w3, 3 * J, ++ep);
@@ -716,7 +647,7 @@ __global__ void __launch_bounds__(NT, 1) k_learn_cg(CgArgs a) {
             add_at(w2, J + j, rv * rv);
           }
           __syncthreads();
-          precondition_k<NT>(a, k, true, s_jac[i], mk, r, yk, w2);
+          precondition_k<NT>(a, k, true, s_jac[i], r, yk, w2);
         }
         block_reduce_to0<NT>(w2, scratch);
         cg_arrive(a, w2, 2 * J, ++ep);
@@ -1143,10 +1074,10 @@ bool learn_cg_shape_ok(const Ctx& c) {
   return (c.K + G - 1) / G <= 8 && 2 * c.J * NF <= 6 * kNT;
 }
 
-size_t learn_cg_smem_bytes(const Ctx& c, bool minv, bool chat_smem) {
+size_t learn_cg_smem_bytes(const Ctx& c, bool chat_smem) {
   const int La = 2 * c.fh - 1, Lb = 2 * c.fw - 1;
   const int G = learn_cg_ctas(c);
-  return cg_smem_layout(c.K, c.J, c.S2, La * c.fw, c.fh, c.fw, La, Lb, kNT, G, minv, chat_smem).total_floats *
+  return cg_smem_layout(c.K, c.J, c.S2, La * c.fw, c.fh, c.fw, La, Lb, kNT, G, chat_smem).total_floats *
          sizeof(float);
 }
 
@@ -1160,7 +1091,7 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   a.lags = c.L.lags; a.chat = c.L.chat; a.b = c.L.b; a.x = d;
   a.yv = reinterpret_cast<float2*>(c.L.yw);   // the words buffers hold the plain values
   a.zv = reinterpret_cast<float*>(c.L.zw);
-  a.mu = c.L.mu; a.minv = c.L.minv; a.iters = c.L.iters; a.err = dev_err;
+  a.mu = c.L.mu; a.iters = c.L.iters; a.err = dev_err;
   a.spin = c.wait_limit > 0 ? c.wait_limit : kSpinLimit;
   // the grid: one CTA per SM at most (every CTA must be resident: the exchanges wait on all)
   a.G = learn_cg_ctas(c);
@@ -1172,8 +1103,8 @@ cudaError_t launch_learn_cg(const Ctx& c, float* d, int steps, int* dev_err) {
   if (e != cudaSuccess) return e;
   auto kern = c.J == 1 ? k_learn_cg<NT, 1> : c.J == 2 ? k_learn_cg<NT, 2> : k_learn_cg<NT, 3>;
   // the CTA's bins of the lag spectra stay in shared memory when they fit
-  a.chat_smem = learn_cg_smem_bytes(c, a.minv != nullptr, true) <= kSmemLimit ? 1 : 0;
-  const size_t smem = learn_cg_smem_bytes(c, a.minv != nullptr, a.chat_smem != 0);
+  a.chat_smem = learn_cg_smem_bytes(c, true) <= kSmemLimit ? 1 : 0;
+  const size_t smem = learn_cg_smem_bytes(c, a.chat_smem != 0);
   if (smem > kSmemLimit) return cudaErrorInvalidValue;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
