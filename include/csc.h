@@ -112,6 +112,20 @@ typedef struct {
    csc_learn_stats and csc_objective take x at H x W; the reverse-mode calls return
    CSC_ERR_UNSUPPORTED. */
 #define CSC_FLAG_SYMMETRIC_BOUNDARY 8
+/* csc_init only: csc_code applies D and D^T as direct spatial convolutions on the tensor cores
+   (tcgen05, float32 operands split into two TF32 parts, three products per pair: float32-accurate;
+   one TF32 product under CSC_MIXED_TF32) instead of per-frequency products of K map spectra. The
+   Fourier domain is kept only for the per-frequency solve lambda = (D D^T + I/rho)^{-1} r of one
+   channel per image (Eq. Inference_solution; the complexity table of Sec. 4.2 counts the Fourier
+   route's transforms, about log(H W) operations per pixel and filter, where the spatial products take
+   fh fw multiply-adds on the tensor pipe). One iteration is three launches:
+   r = D u with u = 2 clamp(v) - v, lambda from r - x/rho by two 2-D FFTs, and D^T lambda with the state
+   update. Same state v and codes z as the Fourier route, equal up to rounding. Needs H = W = 128,
+   J = 1, K <= 128, fh fw <= 128, fh <= 15, precision CSC_FP32 or CSC_MIXED_TF32, no symmetric
+   boundary (CSC_ERR_UNSUPPORTED otherwise). Only csc_code's iterations change; the other calls run as
+   on any context. Every wait of the tensor-core kernels is bounded by csc_set_wait_limit's bound (or
+   about one second); a wait that gives up makes a synchronising csc_code return CSC_ERR_TIMEOUT. */
+#define CSC_FLAG_SPATIAL 16
 
 /*
  * Create a context for n_images images, all of size H x W (dims = {H, W}), on the current CUDA

@@ -28,6 +28,7 @@ CSC_FLAG_GRAPH = 1
 CSC_FLAG_CHECK_FINITE = 2
 CSC_FLAG_CG_STRICT = 4
 CSC_FLAG_SYMMETRIC_BOUNDARY = 8
+CSC_FLAG_SPATIAL = 16
 
 
 class CscError(RuntimeError):

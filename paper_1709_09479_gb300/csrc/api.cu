@@ -124,7 +124,7 @@ void free_all(Ctx* c) {
                   c->vS, c->vd2, c->vx3, c->vp3, c->vtmp, c->vobj, c->vl1,
                   c->VL.z3, c->VL.zt, c->VL.x2, c->VL.x3, c->VL.gram, c->VL.rspec, c->VL.rspecT, c->VL.U, c->VL.tab, c->VL.lags,
                   c->VL.chat, c->VL.vec, c->VL.phat, c->VL.yhat, c->VL.mu, c->VL.active, c->VL.fscal, c->VL.part, c->VL.st, c->VL.iters,
-                  c->VL.words};
+                  c->VL.words, c->sp_bt, c->sp_bc, c->sp_r, c->sp_lam};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -598,6 +598,21 @@ static csc_status init_ctx(const csc_params* params, int n_images, const int* di
     c->last_error = "csc_init: device workspace allocation failed";
     return bail(CSC_ERR_WORKSPACE);
   }
+  if (p.flags & CSC_FLAG_SPATIAL) {
+    std::string why;
+    if (video || !spatial_applies(*c, &why)) {
+      c->last_error = "csc_init: " + (video ? std::string("direct spatial coding is for 2-D images") : why);
+      return bail(CSC_ERR_UNSUPPORTED);
+    }
+    const size_t ob = spatial_operand_bytes(*c), plane = (size_t)tmp.N * g.D * sizeof(float);
+    if (cudaMalloc((void**)&c->sp_bt, ob) != cudaSuccess || cudaMalloc((void**)&c->sp_bc, ob) != cudaSuccess ||
+        cudaMalloc((void**)&c->sp_r, plane) != cudaSuccess || cudaMalloc((void**)&c->sp_lam, plane) != cudaSuccess) {
+      cudaGetLastError();
+      c->last_error = "csc_init: device workspace allocation failed";
+      return bail(CSC_ERR_WORKSPACE);
+    }
+    c->spatial = true;
+  }
   e = cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, 2 * sizeof(int));
   if (e == cudaSuccess && c->dhatp) e = upload_f128_twiddles();
@@ -898,12 +913,12 @@ csc_status csc_describe(const csc_ctx* ctx, char* buf, int len) {
                 "\"large_size_classes\": %d, \"large_images\": %d, \"ctas\": %d, "
                 "\"threads_per_cta\": %d, \"autotuned\": %s, \"autotune_cached\": %s, \"graph\": %s, "
                 "\"graph_recorded\": %s, "
-                "\"video\": %s, \"T\": %d, \"ft\": %d}",
+                "\"video\": %s, \"T\": %d, \"ft\": %d, \"spatial\": %s}",
                 c.N, c.K, c.J, c.uneven ? "true" : "false", n_cls, n_big, c.uneven ? (int)c.U.bimg.size() : 0, c.G,
                 c.uneven ? c.U.nt : (int)kNTSweep,
                 (c.uneven && c.U.tuned) ? "true" : "false", (c.uneven && c.U.tune_cached) ? "true" : "false",
                 (c.p.flags & CSC_FLAG_GRAPH) ? "true" : "false",
-                c.graph ? "true" : "false", c.video ? "true" : "false", c.T, c.ft);
+                c.graph ? "true" : "false", c.video ? "true" : "false", c.T, c.ft, c.spatial ? "true" : "false");
   return CSC_OK;
 }
 
@@ -982,6 +997,21 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     e = launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat);
     if (e == cudaSuccess) e = launch_solve_prep(*c);
     if (e == cudaSuccess) e = launch_fft_maps(*c, xd, c->N * c->J, 0, c->xhat);
+    if (c->spatial) {
+      // direct spatial D and D^T on the tensor cores; P from the filter spectra as above
+      if (e == cudaSuccess) e = launch_spatial_operands(*c, dd);
+      c->launches += 4;
+      for (int t = 0; t < iters && e == cudaSuccess; ++t) {
+        const bool last = (t == iters - 1);
+        const int br = last ? -1 : bracket_open(c, 0);
+        e = launch_spatial_conv(*c, vd);
+        if (e == cudaSuccess) e = launch_spatial_lambda(*c, xd);
+        if (e == cudaSuccess) e = launch_spatial_corr(*c, vd, zd, last);
+        bracket_close(c, br);
+        c->launches += 3;
+      }
+      return e;
+    }
     if (e == cudaSuccess && c->p.precision == CSC_MIXED_BF16) {
       e = launch_to_bf16(*c, c->dhat, c->dhat16, (size_t)c->K * c->J * c->g.Omega);
       // and the copy in the thread order of the fused 128 x 128 sweep
@@ -1047,6 +1077,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     int herr = 0;
     CSC_CHECK_CUDA(c, cudaMemcpyAsync(&herr, c->cerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
     CSC_CHECK_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (herr == CSC_ERR_TIMEOUT) return fail(c, CSC_ERR_TIMEOUT, "csc_code: a bounded wait of the spatial products gave up");
     if (herr) return fail(c, (csc_status)herr, "csc_code: a non-finite value reached the dual variable");
   }
   return CSC_OK;

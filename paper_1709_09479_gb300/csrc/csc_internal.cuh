@@ -321,6 +321,12 @@ struct Ctx {
   float2* vtmp = nullptr;   // canonical 2-D spectra scratch [max(K J ft, N J T)][Omega]
   double* vobj = nullptr;   // [N][bin blocks]
   double* vl1 = nullptr;    // [frame CTAs]
+  // direct spatial coding (CSC_FLAG_SPATIAL, spatial.cu)
+  bool spatial = false;
+  uint8_t* sp_bt = nullptr;   // filter operand of D^T, TF32 hi | lo
+  uint8_t* sp_bc = nullptr;   // filter operand of D, TF32 hi | lo
+  float* sp_r = nullptr;      // [N][128][128] sum_k d_k * u_k
+  float* sp_lam = nullptr;    // [N][128][128] dual variable
   // CUDA graph of the last csc_code launch sequence (flag CSC_FLAG_GRAPH)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -403,6 +409,17 @@ inline size_t bwd_smem_bytes(const Geometry& g, bool rb, bool acc) {
   return ((size_t)g.H * g.P + (rb ? (size_t)g.Omega : 0) + (acc ? (size_t)g.Omega : 0) +
           (size_t)(g.Wh + g.H + g.Wc)) * sizeof(float2);
 }
+
+// direct spatial coding of 128 x 128 grey images on the tensor cores (spatial.cu): whether the
+// context qualifies (else *why says what is missing), the bytes of each filter operand, the operand
+// build from d, and the three launches of one iteration (D, the per-frequency solve of lambda, D^T with
+// the state update; z written by the last iteration's D^T when non-null)
+bool spatial_applies(const Ctx& c, std::string* why);
+size_t spatial_operand_bytes(const Ctx& c);
+cudaError_t launch_spatial_operands(const Ctx& c, const float* d);
+cudaError_t launch_spatial_conv(const Ctx& c, const float* v);
+cudaError_t launch_spatial_lambda(const Ctx& c, const float* x);
+cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last);
 
 // message returned by csc_last_error(NULL) (api.cu)
 void set_global_error(const char* msg);

@@ -1,0 +1,623 @@
+// Direct spatial D and D^T on the 5th-generation tensor cores: the coding iteration of
+// Eq. Inference_solution with the two filter products taken as convolutions on the pixel grid, and
+// the Fourier domain kept only for the per-frequency solve of the dual variable (one channel per
+// image instead of K maps per image).
+//
+// With the state v of the dual ADMM and u = 2 clamp(v) - v, one iteration is
+//   r      = sum_k d_k * u_k                       convolution, K maps -> one channel      (k_sp_conv)
+//   lambda = F^-1( P(w) F(r - x / rho) )           P = (sum_k |d_hat_k|^2 + 1/rho)^-1      (k_sp_lambda)
+//   w_k    = d_k (x) lambda                        correlation (D^T), one channel -> K maps
+//   v     <- w - (clamp(v) - v)                                                            (k_sp_corr)
+// which is the Fourier-domain sweep's iteration (its products sum_k d_hat_k u_hat_k and
+// conj(d_hat_k) lambda_hat are these convolutions by the convolution theorem), so the two routes
+// agree up to rounding. Filter tap (ta, tb) acts at offset (ta - ch, tb - cw), ch = (fh-1)/2,
+// cw = (fw-1)/2, circularly on the 128 x 128 grid.
+//
+// Both filter products are dense contractions over one image row of 128 pixels (the MMA's M = 128
+// rows = TMEM lanes):
+//   D^T   Wr[p][k] = sum_t A[p][t] d_k[t],   A[p][t] = lambda(h + ta - ch, p + tb - cw):
+//         the taps t = ta fw + tb of the row's pixels, gathered from fh rows of lambda;
+//   D     Yr[p][t] = sum_k u_k(h, p) d_k[t], then r(h + ta - ch, p + tb - cw) += Yr[p][t]:
+//         every input row scatters its products over fh output rows (a shift-add over the taps,
+//         done by the thread of each output column in a fixed order).
+// Operands are float32 values split as hi + lo, both rounded to TF32, and multiplied as
+// hi.hi + hi.lo + lo.hi (kind::tf32, FP32 accumulation in TMEM): float32-accurate, the dropped lo.lo
+// term and the rounding of lo below 2^-21 relative per product. The TF32 mode takes hi.hi alone.
+//
+// Kernel shape (both products): one CTA per SM, persistent over its range of rows; warps 4-7 are the
+// producers (they stage the row's operand chunks of 16 contraction elements through a two-stage ring
+// in the canonical no-swizzle K-major layout, and thread 128 issues the MMAs), warps 0-3 the epilogue
+// (TMEM lane p = pixel p). The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory
+// for the whole launch. Two TMEM accumulators let the epilogue of row i run under the MMAs of row
+// i + 1. The state v streams through a six-stage ring of 4-byte cp.async copies, each thread copying
+// exactly the values it later reads (no barrier between copy and use). Every mbarrier wait is bounded:
+// on timeout the CTA records CSC_ERR_TIMEOUT, stops issuing work, drains its MMAs (bounded) and frees
+// its TMEM.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "csc_internal.cuh"
+
+namespace csc {
+namespace sp {
+
+constexpr int kThreads = 256;
+constexpr int kPix = 128;                        // pixels of a row: MMA M, TMEM lanes
+constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
+constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
+constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
+constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo) of an A chunk
+constexpr int kVStages = 6;                      // state stages in flight
+constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
+constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [128 pixels][17]
+constexpr int kTmemCols = 256;                   // two accumulators of up to 128 columns
+constexpr long long kDefaultSpin = 2000000000LL; // ~1 s of SM clocks
+
+// byte offset of (row, contraction element kk < 16) in a chunk block: core matrices of 8 rows x 4
+// elements, kLbo apart along the contraction, kSbo apart along the rows
+__host__ __device__ __forceinline__ uint32_t cm_off(int row, int kk) {
+  return (uint32_t)((row >> 3) * kSbo + (kk >> 2) * kLbo + (row & 7) * 16 + (kk & 3) * 4);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// shared-memory matrix descriptor: start, leading (contraction) and stride (8-row) byte offsets,
+// descriptor version 1 (bit 46), no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t a) {
+  return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)(kLbo >> 4) << 16) | ((uint64_t)(kSbo >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+// instruction descriptor: D f32, A and B TF32, both K-major, N >> 3 at bits 17-22, M = 128
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(bar)) : "memory");
+}
+// bounded wait for the completion of phase `parity`; false on timeout
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
+
+struct SpArgs {
+  int N, K, T, fh, fw;    // images, filters, taps (fh fw), filter support
+  int Kp, Tp;             // K and T rounded up to 16
+  int passes;             // 3: hi.hi + hi.lo + lo.hi; 1: hi.hi (TF32 operands)
+  float beta, rho;
+  const uint8_t* bop;     // the launch's filter operand, hi then lo (chunk-major, see k_sp_operands)
+  float* v;               // [N][K][128][128] ADMM state
+  float* z;               // corr, last iteration: codes (may be null)
+  const float* lam;       // corr: [N][128][128] dual variable
+  float* r;               // conv: [N][128][128] sum_k d_k * u_k
+  int* err;
+  long long spin;
+};
+
+// the two filter operands from d [K][fh fw]: bt for D^T (rows = filters k < Kp, contraction over
+// taps: chunk t / 16 is a [Kp][16] block) and bc for D (rows = taps t < Tp, contraction over
+// filters: chunk k / 16 is a [Tp][16] block); each as the hi split followed by the lo split
+__global__ void k_sp_operands(const float* __restrict__ d, int K, int T, int Kp, int Tp, uint8_t* bt, uint8_t* bc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Kp * Tp) return;
+  const int k = i / Tp, t = i - k * Tp;
+  const float x = (k < K && t < T) ? d[(size_t)k * T + t] : 0.f;
+  const float hi = tf32r(x), lo = tf32r(x - hi);
+  const size_t split = (size_t)Kp * Tp * 4;
+  const size_t ot = (size_t)(t >> 4) * Kp * 64 + cm_off(k, t & 15);
+  const size_t oc = (size_t)(k >> 4) * Tp * 64 + cm_off(t, k & 15);
+  *reinterpret_cast<float*>(bt + ot) = hi;
+  *reinterpret_cast<float*>(bt + split + ot) = lo;
+  *reinterpret_cast<float*>(bc + oc) = hi;
+  *reinterpret_cast<float*>(bc + split + oc) = lo;
+}
+
+// shared start of both product kernels: the filter operand into shared memory, the mbarriers, TMEM
+struct Sync {
+  uint64_t a_empty[2];    // A stage s free again (MMA commit)
+  uint64_t acc_full[2];   // accumulator b complete (MMA commit)
+  uint64_t acc_empty[2];  // accumulator b read by the epilogue (128 arrivals)
+  uint64_t drain;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_t bbytes, Sync& s) {
+  const int4* src = reinterpret_cast<const int4*>(a.bop);
+  int4* dst = reinterpret_cast<int4*>(sb);
+  for (size_t i = threadIdx.x; i < bbytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&s.tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&s.a_empty[i], 1);
+      bar_init(&s.acc_full[i], 1);
+      bar_init(&s.acc_empty[i], 128);
+    }
+    bar_init(&s.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// every MMA of the CTA has completed before its TMEM is released; a timeout anywhere is recorded
+__device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
+  // the drain keeps the default bound whatever the context's wait limit: TMEM is never released
+  // under MMAs in flight
+  if (threadIdx.x == 128) commit(&s.drain);
+  if (!bar_wait(&s.drain, 0u, kDefaultSpin)) ok = false;
+  if (!ok) atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s.tmem), "r"(kTmemCols));
+}
+
+// thread 128: the MMAs of one chunk (2 K-steps x passes) into accumulator acc; the commit frees the
+// A stage, and after the row's last chunk marks the accumulator complete
+__device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, uint32_t acc, uint32_t astage,
+                                            uint32_t bchunk, uint32_t bsplit, uint32_t id, bool first, int st,
+                                            bool last, int accb) {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok) {
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      for (int ps = 0; ps < a.passes; ++ps) {
+        const uint32_t pa = (ps == 2) ? (uint32_t)kAChunk : 0u;   // hi.hi, hi.lo, lo.hi
+        const uint32_t pb = (ps == 1) ? bsplit : 0u;
+        mma_tf32(acc, sdesc(astage + pa + (uint32_t)ks * 2u * kLbo), sdesc(bchunk + pb + (uint32_t)ks * 2u * kLbo), id,
+                 (first && ks == 0 && ps == 0) ? 0u : 1u);
+      }
+    }
+  }
+  commit(&s.a_empty[st]);
+  if (last) commit(&s.acc_full[accb]);
+}
+
+// ---- D^T and the state update: one tile = one image row (n, h) -----------------------------------
+// shared memory: filter operand bt | A stages [2][hi | lo] | lambda rows [fh][128] | state ring
+template <bool LAST>
+__global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Sync s;
+  const int warp = threadIdx.x >> 5;
+  const int nch = a.Tp / kCh, NG = a.Kp / kCh;
+  const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
+  uint8_t* sb = smem;
+  uint8_t* sa = sb + bbytes;
+  float* lam_s = reinterpret_cast<float*>(sa + 4 * kAChunk);
+  float* vring = lam_s + a.fh * kPix;
+  kernel_begin(a, sb, bbytes, s);
+  const uint32_t tmem = s.tmem;
+  const int NH = a.N * kPix;
+  const int t0 = (int)((long long)blockIdx.x * NH / gridDim.x);
+  const int t1 = (int)((long long)(blockIdx.x + 1) * NH / gridDim.x);
+  const int ntiles = t1 - t0;
+  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
+  const size_t plane = (size_t)kPix * kPix;
+  bool ok = true;
+
+  if (warp >= 4) {
+    // producers: thread p builds row p (pixel p) of every A chunk
+    const int p = threadIdx.x - 128;
+    const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
+    const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
+    const uint32_t id = idesc_tf32(a.Kp);
+    for (int i = 0; i < ntiles; ++i) {
+      const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
+      const float* lam_n = a.lam + (size_t)n * plane;
+      for (int ta = 0; ta < a.fh; ++ta) lam_s[ta * kPix + p] = lam_n[((h + ta - ch) & (kPix - 1)) * kPix + p];
+      named_sync(1, 128);
+      int ta = 0, tb = 0;   // tap of element 16 c + kk
+      for (int c = 0; c < nch; ++c) {
+        const int q = i * nch + c, st = q & 1;
+        if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
+        uint8_t* stage = sa + st * 2 * kAChunk;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float hv[4], lv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = c * kCh + 4 * j + e;
+            float x = 0.f;
+            if (t < a.T) {
+              x = lam_s[ta * kPix + ((p + tb - cw) & (kPix - 1))];
+              if (++tb == a.fw) { tb = 0; ++ta; }
+            }
+            hv[e] = tf32r(x);
+            lv[e] = tf32r(x - hv[e]);
+          }
+          const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
+          *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        named_sync(1, 128);
+        if (p == 0) {
+          if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+          issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
+                      sb0 + (uint32_t)(c * a.Kp * 64), bsplit, id, c == 0, st, c == nch - 1, i & 1);
+        }
+      }
+    }
+  } else {
+    // epilogue: thread p = TMEM lane p = pixel p
+    const int p = threadIdx.x;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const int nitems = ntiles * NG;   // item q = (tile q / NG, filter group q % NG)
+    auto issue = [&](int q) {
+      if (q < nitems) {
+        const int i = q / NG, g = q - i * NG;
+        const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
+        float* dst = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+        const float* src = a.v + ((size_t)n * a.K * kPix + h) * kPix + p;
+        for (int e = 0; e < kCh; ++e) {
+          const int k = g * kCh + e;
+          if (k < a.K) cp4(dst + e * kPix, src + (size_t)k * plane);
+        }
+      }
+      cp_commit();
+    };
+    for (int q = 0; q < kVStages - 1; ++q) issue(q);
+    const float beta = a.beta, rho = a.rho;
+    for (int i = 0; i < ntiles; ++i) {
+      const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
+      if (ok) ok = bar_wait(&s.acc_full[i & 1], (uint32_t)((i >> 1) & 1), a.spin);
+      ok = __all_sync(0xFFFFFFFFu, ok);   // tcgen05.ld below is warp-collective: one decision per warp
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
+      const size_t base = ((size_t)n * a.K * kPix + h) * kPix + p;
+      for (int g = 0; g < NG; ++g) {
+        const int q = i * NG + g;
+        issue(q + kVStages - 1);
+        cp_wait<kVStages - 1>();
+        float w[16] = {};
+        if (ok) tmem_ld16(acc + (uint32_t)(g * 16), w);   // after a timeout: no TMEM read, results void
+        const float* vs = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int k = g * kCh + e;
+          if (k < a.K) {
+            const float old = vs[e * kPix];
+            const float nv = w[e] - (clampb(old, beta) - old);
+            a.v[base + (size_t)k * plane] = nv;
+            if (LAST && a.z) a.z[base + (size_t)k * plane] = rho * (clampb(nv, beta) - nv);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      bar_arrive(&s.acc_empty[i & 1]);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
+  kernel_end(a, s, ok);
+}
+
+// ---- D: r = sum_k d_k * u_k ------------------------------------------------------------------------
+// The CTA owns the output rows [o0, o1) of the N x 128 rows, split into one segment [h0, h1) per
+// image it meets. A segment's input rows run from h0 - (fh - 1 - ch) to h1 - 1 + ch (unwrapped,
+// taken mod 128), each a tile: its Yr is scattered to the output rows h + ta - ch that lie in the
+// segment. Output row o receives its fh contributions from consecutive input rows, the first
+// (ta = fh - 1) stored and the others added, so every r value is written by one thread in a fixed
+// order.
+struct ConvTile {
+  int n, hu, h0, h1;
+};
+__device__ __forceinline__ ConvTile conv_tile(int i, int o0, int o1, int fh) {
+  int n = o0 / kPix;
+  while (true) {
+    const int h0 = max(o0 - n * kPix, 0), h1 = min(o1 - n * kPix, kPix);
+    const int cnt = h1 - h0 + fh - 1;
+    if (i < cnt) return ConvTile{n, h0 - (fh - 1 - (fh - 1) / 2) + i, h0, h1};
+    i -= cnt;
+    ++n;
+  }
+}
+__device__ __forceinline__ int conv_tiles(int o0, int o1, int fh) {
+  if (o1 <= o0) return 0;
+  const int nseg = (o1 - 1) / kPix - o0 / kPix + 1;
+  return (o1 - o0) + nseg * (fh - 1);
+}
+
+// shared memory: filter operand bc | A stages [2][hi | lo] | state ring | epilogue exchange
+__global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Sync s;
+  const int warp = threadIdx.x >> 5;
+  const int nch = a.Kp / kCh, ntc = a.Tp / kCh;
+  const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
+  uint8_t* sb = smem;
+  uint8_t* sa = sb + bbytes;
+  float* vring = reinterpret_cast<float*>(sa + 4 * kAChunk);
+  float* ys = vring + kVStages * kCh * kPix;
+  kernel_begin(a, sb, bbytes, s);
+  const uint32_t tmem = s.tmem;
+  const int NH = a.N * kPix;
+  const int o0 = (int)((long long)blockIdx.x * NH / gridDim.x);
+  const int o1 = (int)((long long)(blockIdx.x + 1) * NH / gridDim.x);
+  const int ntiles = conv_tiles(o0, o1, a.fh);
+  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
+  const size_t plane = (size_t)kPix * kPix;
+  bool ok = true;
+
+  if (warp >= 4) {
+    // producers: thread p stages u_k(h, p) of every filter chunk as row p of the A chunk
+    const int p = threadIdx.x - 128;
+    const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
+    const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
+    const uint32_t id = idesc_tf32(a.Tp);
+    const int nitems = ntiles * nch;   // item q = (tile q / nch, filter chunk q % nch)
+    auto issue = [&](int q) {
+      if (q < nitems) {
+        const int i = q / nch, c = q - i * nch;
+        const ConvTile tl = conv_tile(i, o0, o1, a.fh);
+        const int h = tl.hu & (kPix - 1);
+        float* dst = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+        const float* src = a.v + ((size_t)tl.n * a.K * kPix + h) * kPix + p;
+        for (int e = 0; e < kCh; ++e) {
+          const int k = c * kCh + e;
+          if (k < a.K) cp4(dst + e * kPix, src + (size_t)k * plane);
+        }
+      }
+      cp_commit();
+    };
+    for (int q = 0; q < kVStages - 1; ++q) issue(q);
+    const float beta = a.beta;
+    for (int i = 0; i < ntiles; ++i) {
+      for (int c = 0; c < nch; ++c) {
+        const int q = i * nch + c, st = q & 1;
+        issue(q + kVStages - 1);
+        cp_wait<kVStages - 1>();
+        if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
+        uint8_t* stage = sa + st * 2 * kAChunk;
+        const float* vs = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float hv[4], lv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = c * kCh + 4 * j + e;
+            float u = 0.f;
+            if (k < a.K) {
+              const float x = vs[(4 * j + e) * kPix];
+              u = 2.f * clampb(x, beta) - x;
+            }
+            hv[e] = tf32r(u);
+            lv[e] = tf32r(u - hv[e]);
+          }
+          const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
+          *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        named_sync(1, 128);
+        if (p == 0) {
+          if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+          issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
+                      sb0 + (uint32_t)(c * a.Tp * 64), bsplit, id, c == 0, st, c == nch - 1, i & 1);
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    // epilogue: thread p reads TMEM lane p (input pixel p), then acts for output column p
+    const int p = threadIdx.x;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    for (int i = 0; i < ntiles; ++i) {
+      const ConvTile tl = conv_tile(i, o0, o1, a.fh);
+      if (ok) ok = bar_wait(&s.acc_full[i & 1], (uint32_t)((i >> 1) & 1), a.spin);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
+      float* rn = a.r + (size_t)tl.n * plane + p;
+      float cur = 0.f;
+      int ta = 0, tb = 0;
+      for (int tc = 0; tc < ntc; ++tc) {
+        float y[16] = {};
+        if (ok) tmem_ld16(acc + (uint32_t)(tc * 16), y);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) ys[p * kYsPitch + e] = y[e];
+        named_sync(2, 128);
+#pragma unroll 4
+        for (int e = 0; e < 16; ++e) {
+          if (tc * kCh + e < a.T) {
+            cur += ys[((p - tb + cw) & (kPix - 1)) * kYsPitch + e];
+            if (++tb == a.fw) {
+              // taps (ta, 0 .. fw-1) of this input row, for output row hu + ta - ch
+              const int ho = tl.hu + ta - ch;
+              if (ho >= tl.h0 && ho < tl.h1) {
+                float* dst = rn + (size_t)ho * kPix;
+                *dst = (ta == a.fh - 1) ? cur : *dst + cur;
+              }
+              cur = 0.f;
+              tb = 0;
+              ++ta;
+            }
+          }
+        }
+        named_sync(2, 128);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      bar_arrive(&s.acc_empty[i & 1]);
+    }
+  }
+  kernel_end(a, s, ok);
+}
+
+// ---- lambda = F^-1( P F(r - x / rho) ): one CTA per image, the 2-D real FFTs in shared memory ------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sp_lambda(const float* __restrict__ r, const float* __restrict__ x,
+                                                  const float* __restrict__ pdiag, const float2* __restrict__ tw_g,
+                                                  float irho, float* __restrict__ lam, int* err) {
+  using G = GeoCT<128, 128>;
+  extern __shared__ float2 sm[];
+  const G g;
+  float2* buf = sm;
+  const Twiddles tw = stage_twiddles<G, NT>(g, buf + G::H * G::P, tw_g);
+  float* bf = reinterpret_cast<float*>(buf);
+  const size_t off = (size_t)blockIdx.x * G::D;
+  for (int q = threadIdx.x; q < G::D; q += NT) {
+    const int h = q >> 7, w = q & 127;
+    bf[2 * G::P * h + w] = r[off + q] - x[off + q] * irho;
+  }
+  __syncthreads();
+  rfft2<G, NT>(g, buf, tw);
+  // P / D: the inverse below is unnormalised
+  for (int o = threadIdx.x; o < G::Omega; o += NT) {
+    const int h = o / G::Wc, c = o - h * G::Wc;
+    const float s = pdiag[o];
+    float2 b = buf[h * G::P + c];
+    buf[h * G::P + c] = make_float2(b.x * s, b.y * s);
+  }
+  __syncthreads();
+  irfft2<G, NT>(g, buf, tw);
+  __syncthreads();
+  bool bad = false;
+  for (int q = threadIdx.x; q < G::D; q += NT) {
+    const int h = q >> 7, w = q & 127;
+    const float v = bf[2 * G::P * h + w];
+    lam[off + q] = v;
+    bad |= !isfinite(v);
+  }
+  if (bad) atomicExch(err, (int)CSC_ERR_NONFINITE);
+}
+
+}  // namespace sp
+
+// ---- host side ---------------------------------------------------------------------------------------
+static int round16(int v) { return (v + 15) / 16 * 16; }
+
+bool spatial_applies(const Ctx& c, std::string* why) {
+  auto no = [&](const char* m) {
+    if (why) *why = m;
+    return false;
+  };
+  if (c.video || c.uneven || c.sym) return no("direct spatial coding is for uniform 2-D batches");
+  if (c.J != 1) return no("direct spatial coding needs J = 1");
+  if (c.g.H != 128 || c.g.W != 128) return no("direct spatial coding needs 128 x 128 images");
+  if (c.K > 128) return no("direct spatial coding needs K <= 128");
+  if (c.fh * c.fw > 128 || c.fh > 15) return no("direct spatial coding needs fh * fw <= 128 and fh <= 15");
+  if (c.p.precision != CSC_FP32 && c.p.precision != CSC_MIXED_TF32)
+    return no("direct spatial coding runs in CSC_FP32 (3xTF32) or CSC_MIXED_TF32");
+  return true;
+}
+
+size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * round16(c.fh * c.fw) * 4; }
+
+static size_t corr_smem(const Ctx& c) {
+  return spatial_operand_bytes(c) + 4 * sp::kAChunk + (size_t)c.fh * sp::kPix * 4 + sp::kVStages * sp::kVStage;
+}
+static size_t conv_smem(const Ctx& c) {
+  return spatial_operand_bytes(c) + 4 * sp::kAChunk + sp::kVStages * sp::kVStage +
+         (size_t)sp::kPix * sp::kYsPitch * 4;
+}
+static constexpr int kLamThreads = 512;
+static size_t lambda_smem() { return ((size_t)128 * odd_pitch(65) + 64 + 128 + 65) * sizeof(float2); }
+
+static sp::SpArgs sp_args(const Ctx& c, const uint8_t* bop, float* v, float* z) {
+  sp::SpArgs a{};
+  a.N = c.N; a.K = c.K; a.T = c.fh * c.fw; a.fh = c.fh; a.fw = c.fw;
+  a.Kp = round16(c.K); a.Tp = round16(a.T);
+  a.passes = (c.p.precision == CSC_MIXED_TF32) ? 1 : 3;
+  a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
+  a.bop = bop; a.v = v; a.z = z; a.lam = c.sp_lam; a.r = c.sp_r;
+  a.err = c.cerr;   // read at the end of csc_code like the sweeps' flag
+  a.spin = c.wait_limit > 0 ? c.wait_limit : sp::kDefaultSpin;
+  return a;
+}
+
+cudaError_t launch_spatial_operands(const Ctx& c, const float* d) {
+  const int Kp = round16(c.K), Tp = round16(c.fh * c.fw);
+  const int n = Kp * Tp;
+  sp::k_sp_operands<<<(n + 255) / 256, 256, 0, c.stream>>>(d, c.K, c.fh * c.fw, Kp, Tp, c.sp_bt, c.sp_bc);
+  return cudaGetLastError();
+}
+
+static int sp_grid(const Ctx& c) { return std::min(c.nsm, c.N * sp::kPix); }
+
+cudaError_t launch_spatial_conv(const Ctx& c, const float* v) {
+  const sp::SpArgs a = sp_args(c, c.sp_bc, const_cast<float*>(v), nullptr);
+  const int smem = (int)conv_smem(c);
+  cudaError_t e = cudaFuncSetAttribute(sp::k_sp_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  sp::k_sp_conv<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spatial_lambda(const Ctx& c, const float* x) {
+  auto kern = sp::k_sp_lambda<kLamThreads>;
+  const int smem = (int)lambda_smem();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<c.N, kLamThreads, smem, c.stream>>>(c.sp_r, x, c.pdiag, c.tw, (float)(1.0 / c.p.rho), c.sp_lam, c.cerr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last) {
+  const sp::SpArgs a = sp_args(c, c.sp_bt, v, z);
+  const int smem = (int)corr_smem(c);
+  auto kern = last ? sp::k_sp_corr<true> : sp::k_sp_corr<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace csc
