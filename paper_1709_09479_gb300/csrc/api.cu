@@ -976,6 +976,8 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
     if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
   }
+  if (c->spatial && iters > 0 && (reinterpret_cast<uintptr_t>(vd) & 15))
+    return fail(c, CSC_ERR_ARG, "csc_code: direct spatial coding needs v 16-byte aligned (its rows are bulk copies)");
   if (c->uneven && iters > 0 && !c->U.tuned) {
     if (c->U.n_small > 0) CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, true), "uneven setup");
     if ((s = uneven_autotune(c, vd)) != CSC_OK) return s;

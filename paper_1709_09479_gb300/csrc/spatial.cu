@@ -24,15 +24,18 @@
 // hi.hi + hi.lo + lo.hi (kind::tf32, FP32 accumulation in TMEM): float32-accurate, the dropped lo.lo
 // term and the rounding of lo below 2^-21 relative per product. The TF32 mode takes hi.hi alone.
 //
-// Kernel shape (both products): one CTA per SM, persistent over its range of rows; warps 4-7 are the
-// producers (they stage the row's operand chunks of 16 contraction elements through a two-stage ring
-// in the canonical no-swizzle K-major layout, and thread 128 issues the MMAs), warps 0-3 the epilogue
-// (TMEM lane p = pixel p). The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory
-// for the whole launch. Two TMEM accumulators let the epilogue of row i run under the MMAs of row
-// i + 1. The state v streams through a six-stage ring of 4-byte cp.async copies, each thread copying
-// exactly the values it later reads (no barrier between copy and use). Every mbarrier wait is bounded:
-// on timeout the CTA records CSC_ERR_TIMEOUT, stops issuing work, drains its MMAs (bounded) and frees
-// its TMEM.
+// Kernel shape (both products): one CTA per SM, persistent over its range of rows, five roles:
+//   warps 4-7  producers: stage the row's operand chunks of 16 contraction elements (split into TF32
+//              hi and lo) through a two-stage ring in the canonical no-swizzle K-major layout; thread
+//              128 issues the MMAs;
+//   warps 0-3  epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs under
+//              the MMAs of row i + 1);
+//   warp 8     loader of the state v: one TMA bulk copy per 512-byte row v[n][k][h][.] into a
+//              six-stage ring (16 maps a stage), with full/empty mbarriers;
+//   warp 9     loader of the lambda rows of D^T's tiles (double-buffered).
+// The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory for the whole launch.
+// Every mbarrier wait is bounded: on timeout the CTA records CSC_ERR_TIMEOUT, stops issuing work,
+// waits (under the default bound) for its MMAs and copies in flight and frees its TMEM.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,7 +46,7 @@
 namespace csc {
 namespace sp {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 320;                  // epilogue warps 0-3, producers 4-7, loaders 8-9
 constexpr int kPix = 128;                        // pixels of a row: MMA M, TMEM lanes
 constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
 constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
@@ -163,15 +166,32 @@ __global__ void k_sp_operands(const float* __restrict__ d, int K, int T, int Kp,
   *reinterpret_cast<float*>(bc + split + oc) = lo;
 }
 
-// shared start of both product kernels: the filter operand into shared memory, the mbarriers, TMEM
+// TMA bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared memory,
+// counted on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
 struct Sync {
-  uint64_t a_empty[2];    // A stage s free again (MMA commit)
-  uint64_t acc_full[2];   // accumulator b complete (MMA commit)
-  uint64_t acc_empty[2];  // accumulator b read by the epilogue (128 arrivals)
+  uint64_t a_empty[2];          // A stage free again (MMA commit)
+  uint64_t acc_full[2];         // accumulator complete (MMA commit)
+  uint64_t acc_empty[2];        // accumulator read by the 128 epilogue threads
+  uint64_t v_full[kVStages];    // state stage landed (the loader's expected bytes)
+  uint64_t v_empty[kVStages];   // state stage read by its 128 consumers
+  uint64_t l_full[2];           // lambda rows of a tile landed (D^T)
+  uint64_t l_empty[2];          // lambda rows read by the 128 producers
   uint64_t drain;
   uint32_t tmem;
 };
 
+// start of both product kernels: the filter operand into shared memory (the caller has written
+// its own tables before), the mbarriers, TMEM
 __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_t bbytes, Sync& s) {
   const int4* src = reinterpret_cast<const int4*>(a.bop);
   int4* dst = reinterpret_cast<int4*>(sb);
@@ -186,6 +206,12 @@ __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_
       bar_init(&s.a_empty[i], 1);
       bar_init(&s.acc_full[i], 1);
       bar_init(&s.acc_empty[i], 128);
+      bar_init(&s.l_full[i], 1);
+      bar_init(&s.l_empty[i], 128);
+    }
+    for (int i = 0; i < kVStages; ++i) {
+      bar_init(&s.v_full[i], 1);
+      bar_init(&s.v_empty[i], 128);
     }
     bar_init(&s.drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -196,12 +222,13 @@ __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
 
-// every MMA of the CTA has completed before its TMEM is released; a timeout anywhere is recorded
+// every MMA of the CTA has completed before its TMEM is released (the drain keeps the default bound
+// whatever the context's wait limit); a timeout anywhere is recorded
 __device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
-  // the drain keeps the default bound whatever the context's wait limit: TMEM is never released
-  // under MMAs in flight
-  if (threadIdx.x == 128) commit(&s.drain);
-  if (!bar_wait(&s.drain, 0u, kDefaultSpin)) ok = false;
+  if (threadIdx.x == 128) {
+    commit(&s.drain);
+    if (!bar_wait(&s.drain, 0u, kDefaultSpin)) ok = false;
+  }
   if (!ok) atomicExch(a.err, (int)CSC_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -231,8 +258,33 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
   if (last) commit(&s.acc_full[accb]);
 }
 
+// warp 8, lane 0: the state rows v[n][k][h][0..127] of every item, in item order, into the ring
+// (item q = row tile q / groups, filters 16 (q % groups) ..; tile_row(i) gives the tile's n and h).
+// Before returning it waits for the copies of the last stages, so that none is in flight when the
+// CTA ends.
+template <class TileRow>
+__device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, float* vring, int nitems, int groups,
+                                            TileRow tile_row, bool& ok) {
+  const size_t plane = (size_t)kPix * kPix;
+  for (int q = 0; q < nitems; ++q) {
+    const int st = q % kVStages;
+    if (q >= kVStages && ok) ok = bar_wait(&s.v_empty[st], (uint32_t)(((q / kVStages) - 1) & 1), a.spin);
+    const int i = q / groups, k0 = (q - i * groups) * kCh;
+    const int nk = min(kCh, a.K - k0);
+    int n, h;
+    tile_row(i, n, h);
+    float* dst = vring + (size_t)st * kCh * kPix;
+    const float* src = a.v + (((size_t)n * a.K + k0) * kPix + h) * kPix;
+    bar_expect(&s.v_full[st], (uint32_t)(nk * kPix * 4));
+    for (int e = 0; e < nk; ++e) bulk_g2s(dst + e * kPix, src + (size_t)e * plane, kPix * 4, &s.v_full[st]);
+  }
+  for (int q = max(nitems - kVStages, 0); q < nitems; ++q)
+    bar_wait(&s.v_full[q % kVStages], (uint32_t)((q / kVStages) & 1), kDefaultSpin);
+}
+
 // ---- D^T and the state update: one tile = one image row (n, h) -----------------------------------
-// shared memory: filter operand bt | A stages [2][hi | lo] | lambda rows [fh][128] | state ring
+// shared memory: filter operand bt | A stages [2][hi | lo] | state ring | lambda rows [2][fh + 1][128]
+// (row fh stays zero: the padding taps read it) | tap table (row offset, column shift)
 template <bool LAST>
 __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -242,30 +294,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   uint8_t* sa = sb + bbytes;
-  float* lam_s = reinterpret_cast<float*>(sa + 4 * kAChunk);
-  float* vring = lam_s + a.fh * kPix;
+  float* vring = reinterpret_cast<float*>(sa + 4 * kAChunk);
+  float* lbuf = vring + kVStages * kCh * kPix;
+  const int lrows = a.fh + 1;
+  int* tap_a = reinterpret_cast<int*>(lbuf + 2 * lrows * kPix);
+  int* tap_b = tap_a + a.Tp;
+  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
+  for (int t = threadIdx.x; t < a.Tp; t += kThreads) {
+    const int ta = t / a.fw, tb = t - ta * a.fw;
+    tap_a[t] = t < a.T ? ta * kPix : a.fh * kPix;
+    tap_b[t] = t < a.T ? tb - cw : 0;
+  }
+  for (int i = threadIdx.x; i < 2 * kPix; i += kThreads) lbuf[((i >> 7) * lrows + a.fh) * kPix + (i & 127)] = 0.f;
   kernel_begin(a, sb, bbytes, s);
   const uint32_t tmem = s.tmem;
   const int NH = a.N * kPix;
   const int t0 = (int)((long long)blockIdx.x * NH / gridDim.x);
   const int t1 = (int)((long long)(blockIdx.x + 1) * NH / gridDim.x);
   const int ntiles = t1 - t0;
-  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
   const size_t plane = (size_t)kPix * kPix;
+  auto tile_row = [&](int i, int& n, int& h) {
+    const int tile = t0 + i;
+    n = tile / kPix;
+    h = tile - n * kPix;
+  };
   bool ok = true;
 
-  if (warp >= 4) {
-    // producers: thread p builds row p (pixel p) of every A chunk
+  if (warp >= 4 && warp < 8) {
+    // producers: thread p builds row p (pixel p) of every A chunk from the tile's lambda rows
     const int p = threadIdx.x - 128;
     const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
     const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
     const uint32_t id = idesc_tf32(a.Kp);
     for (int i = 0; i < ntiles; ++i) {
-      const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
-      const float* lam_n = a.lam + (size_t)n * plane;
-      for (int ta = 0; ta < a.fh; ++ta) lam_s[ta * kPix + p] = lam_n[((h + ta - ch) & (kPix - 1)) * kPix + p];
-      named_sync(1, 128);
-      int ta = 0, tb = 0;   // tap of element 16 c + kk
+      const int b = i & 1;
+      if (ok) ok = bar_wait(&s.l_full[b], (uint32_t)((i >> 1) & 1), a.spin);
+      const float* lb = lbuf + b * lrows * kPix;
       for (int c = 0; c < nch; ++c) {
         const int q = i * nch + c, st = q & 1;
         if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
@@ -276,11 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int t = c * kCh + 4 * j + e;
-            float x = 0.f;
-            if (t < a.T) {
-              x = lam_s[ta * kPix + ((p + tb - cw) & (kPix - 1))];
-              if (++tb == a.fw) { tb = 0; ++ta; }
-            }
+            const float x = lb[tap_a[t] + ((p + tap_b[t]) & (kPix - 1))];
             hv[e] = tf32r(x);
             lv[e] = tf32r(x - hv[e]);
           }
@@ -288,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
           *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
+        if (c == nch - 1) bar_arrive(&s.l_empty[b]);   // the tile's lambda rows are read
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         named_sync(1, 128);
         if (p == 0) {
@@ -297,46 +358,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
         }
       }
     }
+  } else if (warp == 8) {
+    if ((threadIdx.x & 31) == 0) load_states(a, s, vring, ntiles * NG, NG, tile_row, ok);
+    __syncwarp();
+  } else if (warp == 9) {
+    // warp 9, lane 0: the fh lambda rows of every tile (rows h + ta - ch, circularly)
+    if ((threadIdx.x & 31) == 0) {
+      for (int i = 0; i < ntiles; ++i) {
+        const int b = i & 1;
+        if (i >= 2 && ok) ok = bar_wait(&s.l_empty[b], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+        int n, h;
+        tile_row(i, n, h);
+        float* dst = lbuf + b * lrows * kPix;
+        const float* src = a.lam + (size_t)n * plane;
+        bar_expect(&s.l_full[b], (uint32_t)(a.fh * kPix * 4));
+        for (int ta = 0; ta < a.fh; ++ta)
+          bulk_g2s(dst + ta * kPix, src + (size_t)((h + ta - ch) & (kPix - 1)) * kPix, kPix * 4, &s.l_full[b]);
+      }
+      for (int i = max(ntiles - 2, 0); i < ntiles; ++i) bar_wait(&s.l_full[i & 1], (uint32_t)((i >> 1) & 1), kDefaultSpin);
+    }
+    __syncwarp();
   } else {
     // epilogue: thread p = TMEM lane p = pixel p
     const int p = threadIdx.x;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    const int nitems = ntiles * NG;   // item q = (tile q / NG, filter group q % NG)
-    auto issue = [&](int q) {
-      if (q < nitems) {
-        const int i = q / NG, g = q - i * NG;
-        const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
-        float* dst = vring + (size_t)(q % kVStages) * kCh * kPix + p;
-        const float* src = a.v + ((size_t)n * a.K * kPix + h) * kPix + p;
-        for (int e = 0; e < kCh; ++e) {
-          const int k = g * kCh + e;
-          if (k < a.K) cp4(dst + e * kPix, src + (size_t)k * plane);
-        }
-      }
-      cp_commit();
-    };
-    for (int q = 0; q < kVStages - 1; ++q) issue(q);
+    const int warp_lane0 = 32 * warp;
+    const uint32_t lane_off = (uint32_t)warp_lane0 << 16;
     const float beta = a.beta, rho = a.rho;
     for (int i = 0; i < ntiles; ++i) {
-      const int tile = t0 + i, n = tile / kPix, h = tile - n * kPix;
+      int n, h;
+      tile_row(i, n, h);
       if (ok) ok = bar_wait(&s.acc_full[i & 1], (uint32_t)((i >> 1) & 1), a.spin);
       ok = __all_sync(0xFFFFFFFFu, ok);   // tcgen05.ld below is warp-collective: one decision per warp
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
       const size_t base = ((size_t)n * a.K * kPix + h) * kPix + p;
       for (int g = 0; g < NG; ++g) {
-        const int q = i * NG + g;
-        issue(q + kVStages - 1);
-        cp_wait<kVStages - 1>();
+        const int q = i * NG + g, st = q % kVStages;
+        if (ok) ok = bar_wait(&s.v_full[st], (uint32_t)((q / kVStages) & 1), a.spin);
+        ok = __all_sync(0xFFFFFFFFu, ok);
         float w[16] = {};
         if (ok) tmem_ld16(acc + (uint32_t)(g * 16), w);   // after a timeout: no TMEM read, results void
-        const float* vs = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+        const float* vs = vring + (size_t)st * kCh * kPix + p;
+        float old[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) old[e] = vs[e * kPix];
+        bar_arrive(&s.v_empty[st]);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int k = g * kCh + e;
           if (k < a.K) {
-            const float old = vs[e * kPix];
-            const float nv = w[e] - (clampb(old, beta) - old);
+            const float nv = w[e] - (clampb(old[e], beta) - old[e]);
             a.v[base + (size_t)k * plane] = nv;
             if (LAST && a.z) a.z[base + (size_t)k * plane] = rho * (clampb(nv, beta) - nv);
           }
@@ -345,7 +416,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       bar_arrive(&s.acc_empty[i & 1]);
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   kernel_end(a, s, ok);
 }
@@ -353,10 +423,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
 // ---- D: r = sum_k d_k * u_k ------------------------------------------------------------------------
 // The CTA owns the output rows [o0, o1) of the N x 128 rows, split into one segment [h0, h1) per
 // image it meets. A segment's input rows run from h0 - (fh - 1 - ch) to h1 - 1 + ch (unwrapped,
-// taken mod 128), each a tile: its Yr is scattered to the output rows h + ta - ch that lie in the
-// segment. Output row o receives its fh contributions from consecutive input rows, the first
-// (ta = fh - 1) stored and the others added, so every r value is written by one thread in a fixed
-// order.
+// taken mod 128), each a tile whose Yr is scattered to the output rows h + ta - ch. Output row o
+// receives its fh contributions from consecutive input rows (tap row ta = fh - 1 first, ta = 0 last);
+// the thread of column p keeps the partial sums of the fh rows in flight in a ring (slot o mod fh, a
+// column of its own), stores the first contribution, adds the others in that order, and writes the
+// row of r when its last contribution is in: every r value is formed by one thread in a fixed order.
 struct ConvTile {
   int n, hu, h0, h1;
 };
@@ -377,6 +448,7 @@ __device__ __forceinline__ int conv_tiles(int o0, int o1, int fh) {
 }
 
 // shared memory: filter operand bc | A stages [2][hi | lo] | state ring | epilogue exchange
+// [128][17] | output ring [fh][128]
 __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
@@ -387,6 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
   uint8_t* sa = sb + bbytes;
   float* vring = reinterpret_cast<float*>(sa + 4 * kAChunk);
   float* ys = vring + kVStages * kCh * kPix;
+  float* oring = ys + kPix * kYsPitch;
   kernel_begin(a, sb, bbytes, s);
   const uint32_t tmem = s.tmem;
   const int NH = a.N * kPix;
@@ -397,48 +470,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
   const size_t plane = (size_t)kPix * kPix;
   bool ok = true;
 
-  if (warp >= 4) {
+  if (warp >= 4 && warp < 8) {
     // producers: thread p stages u_k(h, p) of every filter chunk as row p of the A chunk
     const int p = threadIdx.x - 128;
     const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
     const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
     const uint32_t id = idesc_tf32(a.Tp);
-    const int nitems = ntiles * nch;   // item q = (tile q / nch, filter chunk q % nch)
-    auto issue = [&](int q) {
-      if (q < nitems) {
-        const int i = q / nch, c = q - i * nch;
-        const ConvTile tl = conv_tile(i, o0, o1, a.fh);
-        const int h = tl.hu & (kPix - 1);
-        float* dst = vring + (size_t)(q % kVStages) * kCh * kPix + p;
-        const float* src = a.v + ((size_t)tl.n * a.K * kPix + h) * kPix + p;
-        for (int e = 0; e < kCh; ++e) {
-          const int k = c * kCh + e;
-          if (k < a.K) cp4(dst + e * kPix, src + (size_t)k * plane);
-        }
-      }
-      cp_commit();
-    };
-    for (int q = 0; q < kVStages - 1; ++q) issue(q);
     const float beta = a.beta;
     for (int i = 0; i < ntiles; ++i) {
       for (int c = 0; c < nch; ++c) {
-        const int q = i * nch + c, st = q & 1;
-        issue(q + kVStages - 1);
-        cp_wait<kVStages - 1>();
+        const int q = i * nch + c, st = q & 1, vst = q % kVStages;
+        if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)((q / kVStages) & 1), a.spin);
         if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
-        const float* vs = vring + (size_t)(q % kVStages) * kCh * kPix + p;
+        const float* vs = vring + (size_t)vst * kCh * kPix + p;
+        float x[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) x[e] = vs[e * kPix];
+        bar_arrive(&s.v_empty[vst]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           float hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int k = c * kCh + 4 * j + e;
-            float u = 0.f;
-            if (k < a.K) {
-              const float x = vs[(4 * j + e) * kPix];
-              u = 2.f * clampb(x, beta) - x;
-            }
+            const float u = k < a.K ? 2.f * clampb(x[4 * j + e], beta) - x[4 * j + e] : 0.f;
             hv[e] = tf32r(u);
             lv[e] = tf32r(u - hv[e]);
           }
@@ -455,8 +511,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
         }
       }
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-  } else {
+  } else if (warp == 8) {
+    if ((threadIdx.x & 31) == 0) {
+      auto tile_row = [&](int i, int& n, int& h) {
+        const ConvTile tl = conv_tile(i, o0, o1, a.fh);
+        n = tl.n;
+        h = tl.hu & (kPix - 1);
+      };
+      load_states(a, s, vring, ntiles * nch, nch, tile_row, ok);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
     // epilogue: thread p reads TMEM lane p (input pixel p), then acts for output column p
     const int p = threadIdx.x;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
@@ -482,10 +547,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
             if (++tb == a.fw) {
               // taps (ta, 0 .. fw-1) of this input row, for output row hu + ta - ch
               const int ho = tl.hu + ta - ch;
-              if (ho >= tl.h0 && ho < tl.h1) {
-                float* dst = rn + (size_t)ho * kPix;
-                *dst = (ta == a.fh - 1) ? cur : *dst + cur;
-              }
+              float* slot = oring + (((ho % a.fh) + a.fh) % a.fh) * kPix + p;
+              const float val = (ta == a.fh - 1) ? cur : *slot + cur;
+              *slot = val;
+              if (ta == 0 && ho >= tl.h0 && ho < tl.h1) rn[(size_t)ho * kPix] = val;   // row complete
               cur = 0.f;
               tb = 0;
               ++ta;
@@ -562,11 +627,12 @@ bool spatial_applies(const Ctx& c, std::string* why) {
 size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * round16(c.fh * c.fw) * 4; }
 
 static size_t corr_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 4 * sp::kAChunk + (size_t)c.fh * sp::kPix * 4 + sp::kVStages * sp::kVStage;
+  return spatial_operand_bytes(c) + 4 * sp::kAChunk + sp::kVStages * sp::kVStage +
+         (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * round16(c.fh * c.fw) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
   return spatial_operand_bytes(c) + 4 * sp::kAChunk + sp::kVStages * sp::kVStage +
-         (size_t)sp::kPix * sp::kYsPitch * 4;
+         (size_t)sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4;
 }
 static constexpr int kLamThreads = 512;
 static size_t lambda_smem() { return ((size_t)128 * odd_pitch(65) + 64 + 128 + 65) * sizeof(float2); }

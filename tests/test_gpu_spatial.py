@@ -159,3 +159,18 @@ def test_spatial_wait_limit_times_out_then_codes_normally(csc):
         sv.code(f32(x), f32(d), v, z, iters)
         assert rel(v, vo) <= REL_TOL
         assert rel(z, zo) <= REL_TOL
+
+
+def test_spatial_needs_an_aligned_state(csc):
+    """The state's rows are moved by TMA bulk copies (16-byte aligned addresses): a v that starts 4
+    bytes into an allocation is refused before any launch."""
+    import torch
+    N, K, fs = 1, 4, (5, 5)
+    x, d = make_problem(1, N, K, fs)
+    with csc.Solver(J=1, K=K, fs=fs, dims=(H, H), n_images=N, beta=0.5, rho=1.0,
+                    flags=csc.CSC_FLAG_SPATIAL) as sv:
+        buf = torch.zeros(N * K * H * H + 1, device="cuda")
+        v = buf[1:].view(N, K, H, H)
+        with pytest.raises(csc.CscError) as e:
+            sv.code(to_cuda(x), to_cuda(d), v, None, 2)
+        assert e.value.status == 1
