@@ -24,18 +24,23 @@
 // hi.hi + hi.lo + lo.hi (kind::tf32, FP32 accumulation in TMEM): float32-accurate, the dropped lo.lo
 // term and the rounding of lo below 2^-21 relative per product. The TF32 mode takes hi.hi alone.
 //
-// Kernel shape (both products): one CTA per SM, persistent over its range of rows, five roles:
-//   warps 4-7  producers: stage the row's operand chunks of 16 contraction elements (split into TF32
-//              hi and lo) through a two-stage ring in the canonical no-swizzle K-major layout; thread
-//              128 issues the MMAs;
-//   warps 0-3  epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs under
-//              the MMAs of row i + 1);
-//   warp 8     loader of the state v: one TMA bulk copy per 512-byte row v[n][k][h][.] into a
-//              six-stage ring (16 maps a stage), with full/empty mbarriers;
-//   warp 9     loader of the lambda rows of D^T's tiles (double-buffered).
+// Kernel shape (both products): one CTA per SM, persistent over its range of rows, four roles:
+//   warps 4-11  producers: stage the row's operand chunks of 16 contraction elements (split into
+//               TF32 hi and lo) through a two-stage ring in the canonical no-swizzle K-major layout,
+//               two threads per pixel row (two warps per scheduler, so that one's shared-memory
+//               latency hides under the other's conversions);
+//   warp 14     lane 0 issues the MMAs of each filled stage (an issuing thread waits for the tensor
+//               pipe, so it must not be a producer: the next chunk is built meanwhile);
+//   warps 0-3   epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs
+//               under the MMAs of row i + 1);
+//   warp 12     loader of the state v: one TMA tile load (16 maps x 1 row x 128 pixels, 8 KB) per
+//               stage of a five-stage ring, with full/empty mbarriers;
+//   warp 13     loader of the lambda rows of D^T's tiles (double-buffered).
 // The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory for the whole launch.
 // Every mbarrier wait is bounded: on timeout the CTA records CSC_ERR_TIMEOUT, stops issuing work,
 // waits (under the default bound) for its MMAs and copies in flight and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,17 +51,23 @@
 namespace csc {
 namespace sp {
 
-constexpr int kThreads = 320;                  // epilogue warps 0-3, producers 4-7, loaders 8-9
+constexpr int kThreads = 480;                  // epilogue 0-3, producers 4-11, loaders 12-13, MMA 14
+constexpr int kProd = 256;                     // producer threads: two per pixel row of a chunk
+constexpr int kWarpV = 12, kWarpL = 13;        // loader warps (state, lambda rows)
+constexpr int kWarpMma = 14;                   // lane 0 issues every MMA of the CTA
+constexpr int kMmaThread = 32 * kWarpMma;
 constexpr int kPix = 128;                        // pixels of a row: MMA M, TMEM lanes
 constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
 constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
 constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
 constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo) of an A chunk
-constexpr int kVStages = 6;                      // state stages in flight
+constexpr int kAStages = 2;                      // A operand stages (16 KB each)
+constexpr int kVStages = 5;                      // state stages in flight
 constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
-constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [128 pixels][17]
+constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
 constexpr int kTmemCols = 256;                   // two accumulators of up to 128 columns
 constexpr long long kDefaultSpin = 2000000000LL; // ~1 s of SM clocks
+constexpr uint32_t kSuspendHintNs = 100000;      // longest suspension of one mbarrier try_wait
 
 // byte offset of (row, contraction element kk < 16) in a chunk block: core matrices of 8 rows x 4
 // elements, kLbo apart along the contraction, kSbo apart along the rows
@@ -94,17 +105,25 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(bar)) : "memory");
 }
-// bounded wait for the completion of phase `parity`; false on timeout
+// one arrival per warp once all its lanes are past this point (the consumer barriers count warps:
+// 32 arrivals of one warp on one mbarrier would be serialised in the shared-memory unit)
+__device__ __forceinline__ void warp_arrive(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) bar_arrive(bar);
+}
+// bounded wait for the completion of phase `parity`; false on timeout. The waiting thread is
+// suspended by the hardware until the phase completes (or the hint expires) rather than spinning, so
+// that the warps that wait do not take issue slots from the ones that work
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(saddr(bar)), "r"(parity)
+        : "r"(saddr(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > limit) return false;
@@ -174,25 +193,34 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(saddr(bar))
                : "memory");
 }
+// TMA tile load of one box of the 3-D tensor map at coordinates (x, y, z) into shared memory
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+      : "memory");
+}
 __device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
 }
 
 struct Sync {
-  uint64_t a_empty[2];          // A stage free again (MMA commit)
+  uint64_t a_full[kAStages];    // A stage built by the producer warps
+  uint64_t a_empty[kAStages];   // A stage free again (MMA commit)
   uint64_t acc_full[2];         // accumulator complete (MMA commit)
-  uint64_t acc_empty[2];        // accumulator read by the 128 epilogue threads
+  uint64_t acc_empty[2];        // accumulator read by the 4 epilogue warps
   uint64_t v_full[kVStages];    // state stage landed (the loader's expected bytes)
-  uint64_t v_empty[kVStages];   // state stage read by its 128 consumers
+  uint64_t v_empty[kVStages];   // state stage read by its consumers (epilogue of D^T, producers of D)
   uint64_t l_full[2];           // lambda rows of a tile landed (D^T)
-  uint64_t l_empty[2];          // lambda rows read by the 128 producers
+  uint64_t l_empty[2];          // lambda rows read by the producers
   uint64_t drain;
   uint32_t tmem;
 };
 
 // start of both product kernels: the filter operand into shared memory (the caller has written
 // its own tables before), the mbarriers, TMEM
-__device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_t bbytes, Sync& s) {
+__device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_t bbytes, Sync& s, unsigned v_consumers) {
   const int4* src = reinterpret_cast<const int4*>(a.bop);
   int4* dst = reinterpret_cast<int4*>(sb);
   for (size_t i = threadIdx.x; i < bbytes / 16; i += kThreads) dst[i] = __ldg(src + i);
@@ -203,15 +231,18 @@ __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_
   }
   if (threadIdx.x == 32) {
     for (int i = 0; i < 2; ++i) {
-      bar_init(&s.a_empty[i], 1);
       bar_init(&s.acc_full[i], 1);
-      bar_init(&s.acc_empty[i], 128);
+      bar_init(&s.acc_empty[i], 4);        // epilogue warps
       bar_init(&s.l_full[i], 1);
-      bar_init(&s.l_empty[i], 128);
+      bar_init(&s.l_empty[i], kProd / 32);  // producer warps
+    }
+    for (int i = 0; i < kAStages; ++i) {
+      bar_init(&s.a_full[i], kProd / 32);   // producer warps
+      bar_init(&s.a_empty[i], 1);
     }
     for (int i = 0; i < kVStages; ++i) {
       bar_init(&s.v_full[i], 1);
-      bar_init(&s.v_empty[i], 128);
+      bar_init(&s.v_empty[i], v_consumers);   // consumer warps
     }
     bar_init(&s.drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -225,7 +256,7 @@ __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_
 // every MMA of the CTA has completed before its TMEM is released (the drain keeps the default bound
 // whatever the context's wait limit); a timeout anywhere is recorded
 __device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
-  if (threadIdx.x == 128) {
+  if (threadIdx.x == kMmaThread) {
     commit(&s.drain);
     if (!bar_wait(&s.drain, 0u, kDefaultSpin)) ok = false;
   }
@@ -237,8 +268,8 @@ __device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s.tmem), "r"(kTmemCols));
 }
 
-// thread 128: the MMAs of one chunk (2 K-steps x passes) into accumulator acc; the commit frees the
-// A stage, and after the row's last chunk marks the accumulator complete
+// the MMAs of one chunk (2 K-steps x passes) into accumulator acc; the commit frees the A stage, and
+// after the row's last chunk marks the accumulator complete
 __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, uint32_t acc, uint32_t astage,
                                             uint32_t bchunk, uint32_t bsplit, uint32_t id, bool first, int st,
                                             bool last, int accb) {
@@ -258,27 +289,47 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
   if (last) commit(&s.acc_full[accb]);
 }
 
-// warp 8, lane 0: the state rows v[n][k][h][0..127] of every item, in item order, into the ring
-// (item q = row tile q / groups, filters 16 (q % groups) ..; tile_row(i) gives the tile's n and h).
-// Before returning it waits for the copies of the last stages, so that none is in flight when the
-// CTA ends.
+// lane 0 of the MMA warp: every chunk of every row tile once the producers have filled its A stage
+// (and, for a row's first chunk, once the epilogue has emptied the accumulator it reuses); the B
+// chunk c starts bchunk * c bytes into the filter operand
+__device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uint32_t tmem, uint32_t sa0,
+                                         uint32_t sb0, uint32_t bchunk, uint32_t id, int ntiles, int nch) {
+  const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
+  for (int i = 0; i < ntiles; ++i) {
+    for (int c = 0; c < nch; ++c) {
+      const int q = i * nch + c, st = q % kAStages;
+      if (ok) ok = bar_wait(&s.a_full[st], (uint32_t)((q / kAStages) & 1), a.spin);
+      if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
+                  sb0 + (uint32_t)c * bchunk, bsplit, id, c == 0, st, c == nch - 1, i & 1);
+    }
+  }
+}
+
+// lane 0 of the state loader warp: the state rows of every item, in item order, into the ring (item
+// q = row tile q / groups, filters 16 (q % groups) ..; tile_row(i) gives the tile's image n and row
+// h): one TMA box of 16 maps x 1 row x 128 pixels of the tensor map vmap over v viewed as
+// [N K][128][128] (maps past the image's K belong to the next image, or lie past the end and read as
+// zeros; their values are never used). A stage is refilled only after its consumers released it, so
+// every copy lands in a free stage and completes the phase it was counted in; when a wait gives up
+// the loader issues nothing more. Before returning it waits (under the default bound) for the copies
+// of the last stages it filled, so that none is in flight when the CTA ends.
 template <class TileRow>
-__device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, float* vring, int nitems, int groups,
-                                            TileRow tile_row, bool& ok) {
-  const size_t plane = (size_t)kPix * kPix;
+__device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUtensorMap* vmap, float* vring,
+                                            int nitems, int groups, TileRow tile_row, bool& ok) {
+  int issued = 0;
   for (int q = 0; q < nitems; ++q) {
     const int st = q % kVStages;
-    if (q >= kVStages && ok) ok = bar_wait(&s.v_empty[st], (uint32_t)(((q / kVStages) - 1) & 1), a.spin);
+    if (q >= kVStages) ok = ok && bar_wait(&s.v_empty[st], (uint32_t)(((q / kVStages) - 1) & 1), a.spin);
+    if (!ok) break;
     const int i = q / groups, k0 = (q - i * groups) * kCh;
-    const int nk = min(kCh, a.K - k0);
     int n, h;
     tile_row(i, n, h);
-    float* dst = vring + (size_t)st * kCh * kPix;
-    const float* src = a.v + (((size_t)n * a.K + k0) * kPix + h) * kPix;
-    bar_expect(&s.v_full[st], (uint32_t)(nk * kPix * 4));
-    for (int e = 0; e < nk; ++e) bulk_g2s(dst + e * kPix, src + (size_t)e * plane, kPix * 4, &s.v_full[st]);
+    bar_expect(&s.v_full[st], (uint32_t)kVStage);
+    tma_load_3d(vring + (size_t)st * kCh * kPix, vmap, 0, h, n * a.K + k0, &s.v_full[st]);
+    issued = q + 1;
   }
-  for (int q = max(nitems - kVStages, 0); q < nitems; ++q)
+  for (int q = max(issued - kVStages, 0); q < issued; ++q)
     bar_wait(&s.v_full[q % kVStages], (uint32_t)((q / kVStages) & 1), kDefaultSpin);
 }
 
@@ -286,7 +337,7 @@ __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, float* vri
 // shared memory: filter operand bt | A stages [2][hi | lo] | state ring | lambda rows [2][fh + 1][128]
 // (row fh stays zero: the padding taps read it) | tap table (row offset, column shift)
 template <bool LAST>
-__global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_constant__ CUtensorMap vmap) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
@@ -294,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   uint8_t* sa = sb + bbytes;
-  float* vring = reinterpret_cast<float*>(sa + 4 * kAChunk);
+  float* vring = reinterpret_cast<float*>(sa + 2 * kAStages * kAChunk);
   float* lbuf = vring + kVStages * kCh * kPix;
   const int lrows = a.fh + 1;
   int* tap_a = reinterpret_cast<int*>(lbuf + 2 * lrows * kPix);
@@ -306,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
     tap_b[t] = t < a.T ? tb - cw : 0;
   }
   for (int i = threadIdx.x; i < 2 * kPix; i += kThreads) lbuf[((i >> 7) * lrows + a.fh) * kPix + (i & 127)] = 0.f;
-  kernel_begin(a, sb, bbytes, s);
+  kernel_begin(a, sb, bbytes, s, 4);
   const uint32_t tmem = s.tmem;
   const int NH = a.N * kPix;
   const int t0 = (int)((long long)blockIdx.x * NH / gridDim.x);
@@ -320,22 +371,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
   };
   bool ok = true;
 
-  if (warp >= 4 && warp < 8) {
-    // producers: thread p builds row p (pixel p) of every A chunk from the tile's lambda rows
-    const int p = threadIdx.x - 128;
-    const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
-    const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
-    const uint32_t id = idesc_tf32(a.Kp);
+  if (warp >= 4 && warp < kWarpV) {
+    // producers: threads p and p + 128 build row p (pixel p) of every A chunk from the tile's lambda
+    // rows, elements 8 half .. 8 half + 7 each
+    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), half = pp >> 7;
     for (int i = 0; i < ntiles; ++i) {
       const int b = i & 1;
       if (ok) ok = bar_wait(&s.l_full[b], (uint32_t)((i >> 1) & 1), a.spin);
       const float* lb = lbuf + b * lrows * kPix;
       for (int c = 0; c < nch; ++c) {
-        const int q = i * nch + c, st = q & 1;
-        if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
+        const int q = i * nch + c, st = q % kAStages;
+        if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = 2 * half + jj;
           float hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -348,25 +398,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
           *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
-        if (c == nch - 1) bar_arrive(&s.l_empty[b]);   // the tile's lambda rows are read
+        if (c == nch - 1) warp_arrive(&s.l_empty[b]);   // the tile's lambda rows are read
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        named_sync(1, 128);
-        if (p == 0) {
-          if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
-          issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
-                      sb0 + (uint32_t)(c * a.Kp * 64), bsplit, id, c == 0, st, c == nch - 1, i & 1);
-        }
+        warp_arrive(&s.a_full[st]);
       }
     }
-  } else if (warp == 8) {
-    if ((threadIdx.x & 31) == 0) load_states(a, s, vring, ntiles * NG, NG, tile_row, ok);
+  } else if (warp == kWarpMma) {
+    if ((threadIdx.x & 31) == 0)
+      mma_loop(a, s, ok, tmem, saddr(sa), saddr(sb), (uint32_t)(a.Kp * 64), idesc_tf32(a.Kp), ntiles, nch);
     __syncwarp();
-  } else if (warp == 9) {
-    // warp 9, lane 0: the fh lambda rows of every tile (rows h + ta - ch, circularly)
+  } else if (warp == kWarpV) {
+    if ((threadIdx.x & 31) == 0) load_states(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
+    __syncwarp();
+  } else if (warp == kWarpL) {
+    // lane 0: the fh lambda rows of every tile (rows h + ta - ch, circularly)
     if ((threadIdx.x & 31) == 0) {
+      int issued = 0;   // as for the state loader: nothing more after a wait gave up
       for (int i = 0; i < ntiles; ++i) {
         const int b = i & 1;
-        if (i >= 2 && ok) ok = bar_wait(&s.l_empty[b], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+        if (i >= 2) ok = ok && bar_wait(&s.l_empty[b], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
+        if (!ok) break;
         int n, h;
         tile_row(i, n, h);
         float* dst = lbuf + b * lrows * kPix;
@@ -374,11 +425,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
         bar_expect(&s.l_full[b], (uint32_t)(a.fh * kPix * 4));
         for (int ta = 0; ta < a.fh; ++ta)
           bulk_g2s(dst + ta * kPix, src + (size_t)((h + ta - ch) & (kPix - 1)) * kPix, kPix * 4, &s.l_full[b]);
+        issued = i + 1;
       }
-      for (int i = max(ntiles - 2, 0); i < ntiles; ++i) bar_wait(&s.l_full[i & 1], (uint32_t)((i >> 1) & 1), kDefaultSpin);
+      for (int i = max(issued - 2, 0); i < issued; ++i) bar_wait(&s.l_full[i & 1], (uint32_t)((i >> 1) & 1), kDefaultSpin);
     }
     __syncwarp();
-  } else {
+  } else if (warp < 4) {
     // epilogue: thread p = TMEM lane p = pixel p
     const int p = threadIdx.x;
     const int warp_lane0 = 32 * warp;
@@ -402,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
         float old[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) old[e] = vs[e * kPix];
-        bar_arrive(&s.v_empty[st]);
+        warp_arrive(&s.v_empty[st]);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int k = g * kCh + e;
@@ -414,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a) {
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      bar_arrive(&s.acc_empty[i & 1]);
+      warp_arrive(&s.acc_empty[i & 1]);
     }
   }
   kernel_end(a, s, ok);
@@ -448,8 +500,8 @@ __device__ __forceinline__ int conv_tiles(int o0, int o1, int fh) {
 }
 
 // shared memory: filter operand bc | A stages [2][hi | lo] | state ring | epilogue exchange
-// [128][17] | output ring [fh][128]
-__global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
+// [2][128][17] (alternating, one barrier per chunk) | output ring [fh][128] | tap table
+__global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_constant__ CUtensorMap vmap) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
@@ -457,44 +509,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   uint8_t* sa = sb + bbytes;
-  float* vring = reinterpret_cast<float*>(sa + 4 * kAChunk);
+  float* vring = reinterpret_cast<float*>(sa + 2 * kAStages * kAChunk);
   float* ys = vring + kVStages * kCh * kPix;
-  float* oring = ys + kPix * kYsPitch;
-  kernel_begin(a, sb, bbytes, s);
+  float* oring = ys + 2 * kPix * kYsPitch;
+  int* tap_i = reinterpret_cast<int*>(oring + a.fh * kPix);
+  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
+  // tap t of the scatter: source row shift cw - tb (low byte, signed), last tap of its filter row
+  // (bit 8), filter row ta (bits 16..); the padding taps t >= T carry zero products and no flag
+  for (int t = threadIdx.x; t < a.Tp; t += kThreads) {
+    const int ta = t / a.fw, tb = t - ta * a.fw;
+    tap_i[t] = t < a.T ? (((cw - tb) & 0xFF) | ((tb == a.fw - 1) ? 0x100 : 0) | (ta << 16)) : 0;
+  }
+  kernel_begin(a, sb, bbytes, s, kProd / 32);
   const uint32_t tmem = s.tmem;
   const int NH = a.N * kPix;
   const int o0 = (int)((long long)blockIdx.x * NH / gridDim.x);
   const int o1 = (int)((long long)(blockIdx.x + 1) * NH / gridDim.x);
   const int ntiles = conv_tiles(o0, o1, a.fh);
-  const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
   const size_t plane = (size_t)kPix * kPix;
   bool ok = true;
 
-  if (warp >= 4 && warp < 8) {
-    // producers: thread p stages u_k(h, p) of every filter chunk as row p of the A chunk
-    const int p = threadIdx.x - 128;
-    const uint32_t sa0 = saddr(sa), sb0 = saddr(sb);
-    const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
-    const uint32_t id = idesc_tf32(a.Tp);
+  if (warp >= 4 && warp < kWarpV) {
+    // producers: threads p and p + 128 stage u_k(h, p) of every filter chunk as row p of the A chunk,
+    // filters 8 half .. 8 half + 7 of the chunk each
+    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), half = pp >> 7;
     const float beta = a.beta;
     for (int i = 0; i < ntiles; ++i) {
       for (int c = 0; c < nch; ++c) {
-        const int q = i * nch + c, st = q & 1, vst = q % kVStages;
+        const int q = i * nch + c, st = q % kAStages, vst = q % kVStages;
         if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)((q / kVStages) & 1), a.spin);
-        if (q >= 2 && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q >> 1) - 1) & 1), a.spin);
+        if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
-        const float* vs = vring + (size_t)vst * kCh * kPix + p;
-        float x[16];
+        const float* vs = vring + (size_t)vst * kCh * kPix + 8 * half * kPix + p;
+        float x[8];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) x[e] = vs[e * kPix];
-        bar_arrive(&s.v_empty[vst]);
+        for (int e = 0; e < 8; ++e) x[e] = vs[e * kPix];
+        warp_arrive(&s.v_empty[vst]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = 2 * half + jj;
           float hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int k = c * kCh + 4 * j + e;
-            const float u = k < a.K ? 2.f * clampb(x[4 * j + e], beta) - x[4 * j + e] : 0.f;
+            const float u = k < a.K ? 2.f * clampb(x[4 * jj + e], beta) - x[4 * jj + e] : 0.f;
             hv[e] = tf32r(u);
             lv[e] = tf32r(u - hv[e]);
           }
@@ -503,28 +561,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
           *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        named_sync(1, 128);
-        if (p == 0) {
-          if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
-          issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
-                      sb0 + (uint32_t)(c * a.Tp * 64), bsplit, id, c == 0, st, c == nch - 1, i & 1);
-        }
+        warp_arrive(&s.a_full[st]);
       }
     }
-  } else if (warp == 8) {
+  } else if (warp == kWarpMma) {
+    if ((threadIdx.x & 31) == 0)
+      mma_loop(a, s, ok, tmem, saddr(sa), saddr(sb), (uint32_t)(a.Tp * 64), idesc_tf32(a.Tp), ntiles, nch);
+    __syncwarp();
+  } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) {
       auto tile_row = [&](int i, int& n, int& h) {
         const ConvTile tl = conv_tile(i, o0, o1, a.fh);
         n = tl.n;
         h = tl.hu & (kPix - 1);
       };
-      load_states(a, s, vring, ntiles * nch, nch, tile_row, ok);
+      load_states(a, s, &vmap, vring, ntiles * nch, nch, tile_row, ok);
     }
     __syncwarp();
   } else if (warp < 4) {
     // epilogue: thread p reads TMEM lane p (input pixel p), then acts for output column p
     const int p = threadIdx.x;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    int gc = 0;   // chunks exchanged so far: the exchange buffer alternates with it
     for (int i = 0; i < ntiles; ++i) {
       const ConvTile tl = conv_tile(i, o0, o1, a.fh);
       if (ok) ok = bar_wait(&s.acc_full[i & 1], (uint32_t)((i >> 1) & 1), a.spin);
@@ -532,35 +590,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
       float* rn = a.r + (size_t)tl.n * plane + p;
+      // ring slot of output row hu - ch (tap row 0); tap row ta uses the next slots, circularly
+      const int s0 = (((tl.hu - ch) % a.fh) + a.fh) % a.fh;
       float cur = 0.f;
-      int ta = 0, tb = 0;
-      for (int tc = 0; tc < ntc; ++tc) {
+      for (int tc = 0; tc < ntc; ++tc, ++gc) {
         float y[16] = {};
         if (ok) tmem_ld16(acc + (uint32_t)(tc * 16), y);
+        // a buffer is rewritten two chunks later, after every thread has passed the barrier of the
+        // chunk between, i.e. finished its reads of it
+        float* yb = ys + (gc & 1) * kPix * kYsPitch;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) ys[p * kYsPitch + e] = y[e];
+        for (int e = 0; e < 16; ++e) yb[p * kYsPitch + e] = y[e];
         named_sync(2, 128);
-#pragma unroll 4
+        float yv[16];
+#pragma unroll
         for (int e = 0; e < 16; ++e) {
-          if (tc * kCh + e < a.T) {
-            cur += ys[((p - tb + cw) & (kPix - 1)) * kYsPitch + e];
-            if (++tb == a.fw) {
-              // taps (ta, 0 .. fw-1) of this input row, for output row hu + ta - ch
-              const int ho = tl.hu + ta - ch;
-              float* slot = oring + (((ho % a.fh) + a.fh) % a.fh) * kPix + p;
-              const float val = (ta == a.fh - 1) ? cur : *slot + cur;
-              *slot = val;
-              if (ta == 0 && ho >= tl.h0 && ho < tl.h1) rn[(size_t)ho * kPix] = val;   // row complete
-              cur = 0.f;
-              tb = 0;
-              ++ta;
-            }
+          const int inf = tap_i[tc * kCh + e];
+          yv[e] = yb[((p + (int)(signed char)(inf & 0xFF)) & (kPix - 1)) * kYsPitch + e];
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int inf = tap_i[tc * kCh + e];
+          cur += yv[e];
+          if (inf & 0x100) {
+            // taps (ta, 0 .. fw-1) of this input row are in: output row hu + ta - ch
+            const int ta = inf >> 16;
+            const int sl = s0 + ta < a.fh ? s0 + ta : s0 + ta - a.fh;
+            float* slot = oring + sl * kPix + p;
+            const float val = (ta == a.fh - 1) ? cur : *slot + cur;
+            *slot = val;
+            const int ho = tl.hu + ta - ch;
+            if (ta == 0 && ho >= tl.h0 && ho < tl.h1) rn[(size_t)ho * kPix] = val;   // row complete
+            cur = 0.f;
           }
         }
-        named_sync(2, 128);
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      bar_arrive(&s.acc_empty[i & 1]);
+      warp_arrive(&s.acc_empty[i & 1]);
     }
   }
   kernel_end(a, s, ok);
@@ -627,12 +693,12 @@ bool spatial_applies(const Ctx& c, std::string* why) {
 size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * round16(c.fh * c.fw) * 4; }
 
 static size_t corr_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 4 * sp::kAChunk + sp::kVStages * sp::kVStage +
+  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::kVStages * sp::kVStage +
          (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * round16(c.fh * c.fw) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 4 * sp::kAChunk + sp::kVStages * sp::kVStage +
-         (size_t)sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4;
+  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::kVStages * sp::kVStage +
+         (size_t)2 * sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4 + (size_t)round16(c.fh * c.fw) * 4;
 }
 static constexpr int kLamThreads = 512;
 static size_t lambda_smem() { return ((size_t)128 * odd_pitch(65) + 64 + 128 + 65) * sizeof(float2); }
@@ -658,12 +724,37 @@ cudaError_t launch_spatial_operands(const Ctx& c, const float* d) {
 
 static int sp_grid(const Ctx& c) { return std::min(c.nsm, c.N * sp::kPix); }
 
+// the tensor map of the state v as [N K][128][128] float32 with boxes of 16 maps x 1 row x 128
+// pixels (the loader's stage); the encoder comes from the driver through the runtime
+static cudaError_t state_map(const Ctx& c, const float* v, CUtensorMap* m) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)sp::kPix, (cuuint64_t)sp::kPix, (cuuint64_t)c.N * c.K};
+  const cuuint64_t strides[2] = {(cuuint64_t)sp::kPix * 4, (cuuint64_t)sp::kPix * sp::kPix * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)sp::kPix, 1u, (cuuint32_t)sp::kCh};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(v), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_spatial_conv(const Ctx& c, const float* v) {
   const sp::SpArgs a = sp_args(c, c.sp_bc, const_cast<float*>(v), nullptr);
-  const int smem = (int)conv_smem(c);
-  cudaError_t e = cudaFuncSetAttribute(sp::k_sp_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  CUtensorMap vmap;
+  cudaError_t e = state_map(c, v, &vmap);
   if (e != cudaSuccess) return e;
-  sp::k_sp_conv<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a);
+  const int smem = (int)conv_smem(c);
+  e = cudaFuncSetAttribute(sp::k_sp_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  sp::k_sp_conv<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a, vmap);
   return cudaGetLastError();
 }
 
@@ -678,11 +769,14 @@ cudaError_t launch_spatial_lambda(const Ctx& c, const float* x) {
 
 cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last) {
   const sp::SpArgs a = sp_args(c, c.sp_bt, v, z);
+  CUtensorMap vmap;
+  cudaError_t e = state_map(c, v, &vmap);
+  if (e != cudaSuccess) return e;
   const int smem = (int)corr_smem(c);
   auto kern = last ? sp::k_sp_corr<true> : sp::k_sp_corr<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a);
+  kern<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a, vmap);
   return cudaGetLastError();
 }
 
