@@ -63,6 +63,7 @@ constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chun
 constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo) of an A chunk
 constexpr int kAStages = 2;                      // A operand stages (16 KB each)
 constexpr int kVStages = 5;                      // state stages in flight
+constexpr int kPrefetch = 24;                    // state boxes fetched into L2 ahead of the ring
 constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
 constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
 constexpr int kTmemCols = 256;                   // two accumulators of up to 128 columns
@@ -153,6 +154,20 @@ __device__ __forceinline__ void cp_wait() {
 }
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
+// the taps of a filter support known at compile time (FW > 0): tap t = ta fw + tb, padding taps
+// t >= fh fw up to the next multiple of 16
+template <int FH, int FW>
+struct Taps {
+  static constexpr int T = FH * FW, TP = (T + 15) / 16 * 16, NCH = TP / 16, CH = (FH - 1) / 2, CW = (FW - 1) / 2;
+  // D^T gather: lambda row offset (row fh is the zero row) and column shift of tap t
+  __host__ __device__ static constexpr int row(int t) { return t < T ? (t / FW) * kPix : FH * kPix; }
+  __host__ __device__ static constexpr int shift(int t) { return t < T ? t % FW - CW : 0; }
+  // D scatter: source pixel shift, whether t closes its filter row, its filter row
+  __host__ __device__ static constexpr int src(int t) { return t < T ? CW - t % FW : 0; }
+  __host__ __device__ static constexpr bool closes(int t) { return t < T && t % FW == FW - 1; }
+  __host__ __device__ static constexpr int ta(int t) { return t / FW; }
+};
+
 struct SpArgs {
   int N, K, T, fh, fw;    // images, filters, taps (fh fw), filter support
   int Kp, Tp;             // K and T rounded up to 16
@@ -201,6 +216,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
       : "memory");
 }
+// the same box fetched into L2 only (no shared memory, no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
 }
@@ -237,7 +259,7 @@ __device__ __forceinline__ void kernel_begin(const SpArgs& a, uint8_t* sb, size_
       bar_init(&s.l_empty[i], kProd / 32);  // producer warps
     }
     for (int i = 0; i < kAStages; ++i) {
-      bar_init(&s.a_full[i], kProd / 32);   // producer warps
+      bar_init(&s.a_full[i], kProd / 64);   // the warps of one producer group
       bar_init(&s.a_empty[i], 1);
     }
     for (int i = 0; i < kVStages; ++i) {
@@ -312,22 +334,38 @@ __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uin
 // [N K][128][128] (maps past the image's K belong to the next image, or lie past the end and read as
 // zeros; their values are never used). A stage is refilled only after its consumers released it, so
 // every copy lands in a free stage and completes the phase it was counted in; when a wait gives up
-// the loader issues nothing more. Before returning it waits (under the default bound) for the copies
-// of the last stages it filled, so that none is in flight when the CTA ends.
+// the loader issues nothing more. The boxes kPrefetch items ahead are fetched into L2 meanwhile (the
+// ring alone holds too few bytes to cover the latency of HBM). Before returning it waits (under the
+// default bound) for the copies of the last stages it filled, so that none is in flight when the CTA
+// ends.
 template <class TileRow>
 __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUtensorMap* vmap, float* vring,
                                             int nitems, int groups, TileRow tile_row, bool& ok) {
+  auto box = [&](int q, int& h, int& z) {
+    const int i = q / groups, k0 = (q - i * groups) * kCh;
+    int n;
+    tile_row(i, n, h);
+    z = n * a.K + k0;
+  };
+  for (int q = 0; q < min(kPrefetch, nitems); ++q) {
+    int h, z;
+    box(q, h, z);
+    tma_prefetch_3d(vmap, 0, h, z);
+  }
   int issued = 0;
   for (int q = 0; q < nitems; ++q) {
     const int st = q % kVStages;
     if (q >= kVStages) ok = ok && bar_wait(&s.v_empty[st], (uint32_t)(((q / kVStages) - 1) & 1), a.spin);
     if (!ok) break;
-    const int i = q / groups, k0 = (q - i * groups) * kCh;
-    int n, h;
-    tile_row(i, n, h);
+    int h, z;
+    box(q, h, z);
     bar_expect(&s.v_full[st], (uint32_t)kVStage);
-    tma_load_3d(vring + (size_t)st * kCh * kPix, vmap, 0, h, n * a.K + k0, &s.v_full[st]);
+    tma_load_3d(vring + (size_t)st * kCh * kPix, vmap, 0, h, z, &s.v_full[st]);
     issued = q + 1;
+    if (q + kPrefetch < nitems) {
+      box(q + kPrefetch, h, z);
+      tma_prefetch_3d(vmap, 0, h, z);
+    }
   }
   for (int q = max(issued - kVStages, 0); q < issued; ++q)
     bar_wait(&s.v_full[q % kVStages], (uint32_t)((q / kVStages) & 1), kDefaultSpin);
@@ -336,8 +374,9 @@ __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUte
 // ---- D^T and the state update: one tile = one image row (n, h) -----------------------------------
 // shared memory: filter operand bt | A stages [2][hi | lo] | state ring | lambda rows [2][fh + 1][128]
 // (row fh stays zero: the padding taps read it) | tap table (row offset, column shift)
-template <bool LAST>
+template <bool LAST, int FH, int FW>
 __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_constant__ CUtensorMap vmap) {
+  using CT = Taps<FH, FW>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
@@ -372,25 +411,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
   bool ok = true;
 
   if (warp >= 4 && warp < kWarpV) {
-    // producers: threads p and p + 128 build row p (pixel p) of every A chunk from the tile's lambda
-    // rows, elements 8 half .. 8 half + 7 each
-    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), half = pp >> 7;
+    // producers: group g (warps 4-7: g = 0, warps 8-11: g = 1) builds the chunks of A stage g (every
+    // other chunk); thread p of a group builds row p (pixel p) of its chunks from the tile's lambda rows
+    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), grp = pp >> 7;
     for (int i = 0; i < ntiles; ++i) {
       const int b = i & 1;
       if (ok) ok = bar_wait(&s.l_full[b], (uint32_t)((i >> 1) & 1), a.spin);
       const float* lb = lbuf + b * lrows * kPix;
-      for (int c = 0; c < nch; ++c) {
+      auto chunk = [&](int c, auto tap) {
         const int q = i * nch + c, st = q % kAStages;
+        if (st != grp) return;
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const int j = 2 * half + jj;
+        for (int j = 0; j < 4; ++j) {
           float hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int t = c * kCh + 4 * j + e;
-            const float x = lb[tap_a[t] + ((p + tap_b[t]) & (kPix - 1))];
+            const float x = tap(c * kCh + 4 * j + e);
             hv[e] = tf32r(x);
             lv[e] = tf32r(x - hv[e]);
           }
@@ -398,10 +436,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
           *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
-        if (c == nch - 1) warp_arrive(&s.l_empty[b]);   // the tile's lambda rows are read
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         warp_arrive(&s.a_full[st]);
+      };
+      if constexpr (FW > 0) {
+        // compile-time taps: every gather address is p plus constants
+#pragma unroll
+        for (int c = 0; c < CT::NCH; ++c)
+          chunk(c, [&](int t) { return lb[CT::row(t) + ((p + CT::shift(t)) & (kPix - 1))]; });
+      } else {
+        for (int c = 0; c < nch; ++c) chunk(c, [&](int t) { return lb[tap_a[t] + ((p + tap_b[t]) & (kPix - 1))]; });
       }
+      warp_arrive(&s.l_empty[b]);   // this group's reads of the tile's lambda rows are done
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
@@ -501,7 +547,9 @@ __device__ __forceinline__ int conv_tiles(int o0, int o1, int fh) {
 
 // shared memory: filter operand bc | A stages [2][hi | lo] | state ring | epilogue exchange
 // [2][128][17] (alternating, one barrier per chunk) | output ring [fh][128] | tap table
+template <int FH, int FW>
 __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_constant__ CUtensorMap vmap) {
+  using CT = Taps<FH, FW>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
@@ -520,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
     const int ta = t / a.fw, tb = t - ta * a.fw;
     tap_i[t] = t < a.T ? (((cw - tb) & 0xFF) | ((tb == a.fw - 1) ? 0x100 : 0) | (ta << 16)) : 0;
   }
-  kernel_begin(a, sb, bbytes, s, kProd / 32);
+  kernel_begin(a, sb, bbytes, s, kProd / 64);
   const uint32_t tmem = s.tmem;
   const int NH = a.N * kPix;
   const int o0 = (int)((long long)blockIdx.x * NH / gridDim.x);
@@ -530,29 +578,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
   bool ok = true;
 
   if (warp >= 4 && warp < kWarpV) {
-    // producers: threads p and p + 128 stage u_k(h, p) of every filter chunk as row p of the A chunk,
-    // filters 8 half .. 8 half + 7 of the chunk each
-    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), half = pp >> 7;
+    // producers: group g builds the chunks of A stage g (every other chunk); thread p of a group
+    // stages u_k(h, p) of the chunk's 16 filters as row p
+    const int pp = threadIdx.x - 128, p = pp & (kPix - 1), grp = pp >> 7;
     const float beta = a.beta;
     for (int i = 0; i < ntiles; ++i) {
       for (int c = 0; c < nch; ++c) {
         const int q = i * nch + c, st = q % kAStages, vst = q % kVStages;
+        if (st != grp) continue;
         if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)((q / kVStages) & 1), a.spin);
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
-        const float* vs = vring + (size_t)vst * kCh * kPix + 8 * half * kPix + p;
-        float x[8];
+        const float* vs = vring + (size_t)vst * kCh * kPix + p;
+        float x[16];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = vs[e * kPix];
+        for (int e = 0; e < 16; ++e) x[e] = vs[e * kPix];
         warp_arrive(&s.v_empty[vst]);
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const int j = 2 * half + jj;
+        for (int j = 0; j < 4; ++j) {
           float hv[4], lv[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int k = c * kCh + 4 * j + e;
-            const float u = k < a.K ? 2.f * clampb(x[4 * jj + e], beta) - x[4 * jj + e] : 0.f;
+            const float u = k < a.K ? 2.f * clampb(x[4 * j + e], beta) - x[4 * j + e] : 0.f;
             hv[e] = tf32r(u);
             lv[e] = tf32r(u - hv[e]);
           }
@@ -581,6 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
   } else if (warp < 4) {
     // epilogue: thread p reads TMEM lane p (input pixel p), then acts for output column p
     const int p = threadIdx.x;
+    const int fh = FH > 0 ? FH : a.fh;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     int gc = 0;   // chunks exchanged so far: the exchange buffer alternates with it
     for (int i = 0; i < ntiles; ++i) {
@@ -591,39 +640,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
       const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
       float* rn = a.r + (size_t)tl.n * plane + p;
       // ring slot of output row hu - ch (tap row 0); tap row ta uses the next slots, circularly
-      const int s0 = (((tl.hu - ch) % a.fh) + a.fh) % a.fh;
+      const int s0 = (((tl.hu - ch) % fh) + fh) % fh;
       float cur = 0.f;
-      for (int tc = 0; tc < ntc; ++tc, ++gc) {
+      // the taps of chunk tc: scatter source shift, whether the tap closes its filter row, the row
+      auto chunk = [&](int tc, auto src, auto closes, auto row) {
         float y[16] = {};
         if (ok) tmem_ld16(acc + (uint32_t)(tc * 16), y);
         // a buffer is rewritten two chunks later, after every thread has passed the barrier of the
         // chunk between, i.e. finished its reads of it
         float* yb = ys + (gc & 1) * kPix * kYsPitch;
+        ++gc;
 #pragma unroll
         for (int e = 0; e < 16; ++e) yb[p * kYsPitch + e] = y[e];
         named_sync(2, 128);
         float yv[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int inf = tap_i[tc * kCh + e];
-          yv[e] = yb[((p + (int)(signed char)(inf & 0xFF)) & (kPix - 1)) * kYsPitch + e];
-        }
+        for (int e = 0; e < 16; ++e) yv[e] = yb[((p + src(tc * kCh + e)) & (kPix - 1)) * kYsPitch + e];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int inf = tap_i[tc * kCh + e];
+          const int t = tc * kCh + e;
           cur += yv[e];
-          if (inf & 0x100) {
+          if (closes(t)) {
             // taps (ta, 0 .. fw-1) of this input row are in: output row hu + ta - ch
-            const int ta = inf >> 16;
-            const int sl = s0 + ta < a.fh ? s0 + ta : s0 + ta - a.fh;
+            const int ta = row(t);
+            const int sl = s0 + ta < fh ? s0 + ta : s0 + ta - fh;
             float* slot = oring + sl * kPix + p;
-            const float val = (ta == a.fh - 1) ? cur : *slot + cur;
+            const float val = (ta == fh - 1) ? cur : *slot + cur;
             *slot = val;
             const int ho = tl.hu + ta - ch;
             if (ta == 0 && ho >= tl.h0 && ho < tl.h1) rn[(size_t)ho * kPix] = val;   // row complete
             cur = 0.f;
           }
         }
+      };
+      if constexpr (FW > 0) {
+#pragma unroll
+        for (int tc = 0; tc < CT::NCH; ++tc)
+          chunk(tc, [](int t) { return CT::src(t); }, [](int t) { return CT::closes(t); }, [](int t) { return CT::ta(t); });
+      } else {
+        for (int tc = 0; tc < ntc; ++tc)
+          chunk(tc, [&](int t) { return (int)(signed char)(tap_i[t] & 0xFF); }, [&](int t) { return (tap_i[t] & 0x100) != 0; },
+                [&](int t) { return tap_i[t] >> 16; });
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       warp_arrive(&s.acc_empty[i & 1]);
@@ -752,9 +809,11 @@ cudaError_t launch_spatial_conv(const Ctx& c, const float* v) {
   cudaError_t e = state_map(c, v, &vmap);
   if (e != cudaSuccess) return e;
   const int smem = (int)conv_smem(c);
-  e = cudaFuncSetAttribute(sp::k_sp_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // 11 x 11 (the benchmark's support) with compile-time taps; every other support reads tap tables
+  auto kern = (c.fh == 11 && c.fw == 11) ? sp::k_sp_conv<11, 11> : sp::k_sp_conv<0, 0>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  sp::k_sp_conv<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a, vmap);
+  kern<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a, vmap);
   return cudaGetLastError();
 }
 
@@ -773,7 +832,9 @@ cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last) {
   cudaError_t e = state_map(c, v, &vmap);
   if (e != cudaSuccess) return e;
   const int smem = (int)corr_smem(c);
-  auto kern = last ? sp::k_sp_corr<true> : sp::k_sp_corr<false>;
+  const bool t11 = (c.fh == 11 && c.fw == 11);
+  auto kern = last ? (t11 ? sp::k_sp_corr<true, 11, 11> : sp::k_sp_corr<true, 0, 0>)
+                   : (t11 ? sp::k_sp_corr<false, 11, 11> : sp::k_sp_corr<false, 0, 0>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<sp_grid(c), sp::kThreads, smem, c.stream>>>(a, vmap);
