@@ -27,6 +27,7 @@ CASES = [
     (2, 7, (7, 3), 0.2, 1.0, 5),        # rectangular support
     (1, 1, (1, 1), 0.1, 1.0, 4),        # one filter, one tap
     (5, 33, (9, 9), 0.4, 3.0, 4),       # 81 taps -> 96, K = 33 -> 48
+    (1, 128, (11, 11), 0.5, 1.0, 3),    # K = 128: the largest filter operand, two A stages
 ]
 
 
