@@ -45,12 +45,20 @@ METRIC = "coding ADMM iters/s"
 UNIT = "iters/s"
 
 
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)).get("bf16_tflops") if os.path.exists(p) else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+MEASURED_BF16 = _bf16_peak()
 
 
 def kernel_source_hash():
@@ -301,7 +309,8 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     uneven256 (batched coding of 256 images of different sizes, one launch per iteration, CUDA-graph
     replay), unroll32 (reverse mode through 20 unrolled iterations), video3d (higher-order coding of an
     RGB video with 3-D transforms, and one outer iteration of coding and learning), mixed128 (the benchmark step in the mixed-precision mode,
-    tensor-core Gram), cufft128 (cuFFT's forward and inverse transforms of the benchmark's maps, a
+    tensor-core Gram), spatial128 (the coding iteration with direct spatial D and D^T on the tensor
+    cores), cufft128 (cuFFT's forward and inverse transforms of the benchmark's maps, a
     timed comparison only)."""
     from paper_1709_09479_gb300 import autograd as ag
     from paper_1709_09479_gb300 import inputs
@@ -460,6 +469,57 @@ def measure_extensions(csc, torch, dev, hbm_peak):
                        "coding_sweep_us": tm["sweep_ms"] / max(tm["sweep_launches"], 1) * 1e3,
                        "learn_ms_per_step": tm["learn_ms"] / max(tm["learn_calls"], 1)}
     del x, d, v, z
+
+    # --- spatial128: the coding iteration with D and D^T as direct spatial products on tcgen05 ------
+    x = torch.from_numpy(x_np).to(dev)
+    d = torch.from_numpy(d_np).to(dev)
+    N, K, H, W, s = w["N"], w["K"], w["H"], w["W"], w["s"]
+    forms = {}
+    for name, prec, passes in (("fp32_3xtf32", csc.CSC_FP32, 3), ("tf32", csc.CSC_MIXED_TF32, 1)):
+        with csc.Solver(J=1, K=K, fs=(s, s), dims=(H, W), n_images=N, beta=w["beta"], rho=w["rho"],
+                        precision=prec, flags=csc.CSC_FLAG_SPATIAL) as sv:
+            v = torch.zeros((N, K, H, W), device=dev)
+            z = torch.empty_like(v)
+            sv.code(x, d, v, z, 3)
+            torch.cuda.synchronize()
+            per = []
+            for iters in (1, 21):
+                ts = []
+                for _ in range(3):
+                    e0, e1 = ev(), ev()
+                    e0.record()
+                    sv.code(x, d, v, z, iters)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                per.append(min(ts))
+            forms[name] = {"us_per_iteration": (per[1] - per[0]) / 20 * 1e3, "passes": passes}
+            del v, z
+    # tensor work per iteration: useful multiply-adds (two products of N H W K s^2) and the issued ones
+    # (operands padded to 16: taps 121 -> 128, filters 100 -> 112; the convolution's halo rows: fh - 1
+    # extra input rows per image segment of a CTA)
+    G = min(torch.cuda.get_device_properties(dev).multi_processor_count, N * H)
+    conv_tiles = 0
+    for b in range(G):
+        o0, o1 = b * N * H // G, (b + 1) * N * H // G
+        if o1 > o0:
+            conv_tiles += (o1 - o0) + ((o1 - 1) // H - o0 // H + 1) * (s - 1)
+    Tp, Kp = (s * s + 15) // 16 * 16, (K + 15) // 16 * 16
+    useful = 2.0 * 2 * N * H * W * K * s * s
+    tf32_peak = MEASURED_BF16 * 0.5 if MEASURED_BF16 else None
+    for name, f in forms.items():
+        issued = 2.0 * W * Tp * Kp * (N * H + conv_tiles) * f["passes"]
+        t = f["us_per_iteration"] * 1e-6
+        f["tensor_tflops_useful"] = useful / t / 1e12
+        f["tensor_tflops_issued"] = issued / t / 1e12
+        f["issued_frac_of_tf32_peak"] = (issued / t / 1e12 / tf32_peak) if tf32_peak else None
+    out["spatial128"] = {"workload": "powerlaw128 coding (N=100, K=100, 11x11, beta=1, rho=0.1) with CSC_FLAG_SPATIAL: "
+                                     "D and D^T as row-tiled tcgen05 products, lambda by per-image 2-D FFTs",
+                         "forms": forms, "fourier_sweep_us": None,
+                         "useful_gflop_per_iteration": useful / 1e9,
+                         "tf32_peak_tflops": tf32_peak,
+                         "tf32_peak_kind": "measured bf16 burst x 0.5 (the nominal TF32:BF16 ratio 1.1:2.25)"}
+    del x, d
 
     # --- cufft128: library transforms as a timed comparison (not on the library's path) ----------
     # the forward and inverse 2-D real transforms of all N*K maps of powerlaw128 through cuFFT
@@ -665,6 +725,8 @@ def run_ours(args):
     if ext is not None and "cufft128" in ext:
         # the fused sweep does both transforms plus the contraction, solve, shrinkage and state update
         ext["cufft128"]["fused_sweep_us"] = sweep_avg_s * 1e6
+    if ext is not None and "spatial128" in ext:
+        ext["spatial128"]["fourier_sweep_us"] = sweep_avg_s * 1e6
 
     line = None
     if rank == 0:
@@ -710,7 +772,9 @@ def run_case(args):
     """A short run of one hot-path kernel family on a fixed workload, the target of the ncu captures
     summarised under profiles/ (no timing, no JSON line):
       coding:   csc_code with --iters ADMM iterations on --N images --H x --W, --K filters --s x --s
-                (launch order: 2 spectra, solve setup, spectra, prologue sweep, then --iters sweeps);
+                (launch order: 2 spectra, solve setup, spectra, prologue sweep, then --iters sweeps;
+                with --spatial: 2 spectra, solve setup, operands, then per iteration the spatial D,
+                the lambda solve and the spatial D^T);
       learning: the same csc_code, then csc_learn with --learn-steps learning steps;
       uneven:   the 256-image batch of the uneven256 extension (sides uniform in [64, 512], K = 64;
                 --images takes its first images; --sides smooth64-128 draws the sides from the even
@@ -758,7 +822,8 @@ def run_case(args):
     d = torch.from_numpy(inputs.unit_filters(21, a.K, 1, (a.s, a.s)).astype(np.float32)).cuda()
     v = torch.zeros((a.N, a.K, a.H, a.W), device="cuda")
     z = torch.empty_like(v)
-    with csc.Solver(J=1, K=a.K, fs=(a.s, a.s), dims=(a.H, a.W), n_images=a.N, beta=1.0, rho=0.1) as sv:
+    flags = csc.CSC_FLAG_SPATIAL if a.spatial else 0
+    with csc.Solver(J=1, K=a.K, fs=(a.s, a.s), dims=(a.H, a.W), n_images=a.N, beta=1.0, rho=0.1, flags=flags) as sv:
         sv.code(x, d, v, z, a.iters)
         if a.case == "learning":
             mu = torch.full((a.K,), 0.5, dtype=torch.float64, device="cuda")
@@ -877,6 +942,8 @@ def main():
     ap.add_argument("--learn-steps", type=int, default=2)
     ap.add_argument("--images", type=int, default=256, help="uneven case: number of images")
     ap.add_argument("--sides", choices=["64-512", "smooth64-128"], default="64-512")
+    ap.add_argument("--spatial", action="store_true",
+                    help="coding case: CSC_FLAG_SPATIAL (D and D^T as direct spatial products on the tensor cores)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
