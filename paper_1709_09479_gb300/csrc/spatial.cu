@@ -20,9 +20,10 @@
 //   D     Yr[p][t] = sum_k u_k(h, p) d_k[t], then r(h + ta - ch, p + tb - cw) += Yr[p][t]:
 //         every input row scatters its products over fh output rows (a shift-add over the taps,
 //         done by the thread of each output column in a fixed order).
-// Operands are float32 values split as hi + lo, both rounded to TF32, and multiplied as
-// hi.hi + hi.lo + lo.hi (kind::tf32, FP32 accumulation in TMEM): float32-accurate, the dropped lo.lo
-// term and the rounding of lo below 2^-21 relative per product. The TF32 mode takes hi.hi alone.
+// Operands are float32 values split as hi + lo (hi rounded to TF32, lo = v - hi read by the MMA as
+// TF32) and multiplied as hi.hi + hi.lo + lo.hi (kind::tf32, FP32 accumulation in TMEM):
+// float32-accurate, the dropped lo.lo term and the truncation of lo below 2^-20 relative per product.
+// The TF32 mode takes hi.hi alone.
 //
 // Kernel shape (both products): one CTA per SM, persistent over its range of rows, four roles:
 //   warps 4-11  producers: stage the row's operand chunks of 16 contraction elements (split into
@@ -153,6 +154,14 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
+// the TF32 hi part of the streamed operands: v rounded to 10 explicit mantissa bits, half-way cases
+// away from zero, by integer arithmetic on the bit pattern (add half of the lowest kept bit, clear
+// the 13 dropped bits; a carry moves into the exponent as it should, Inf and NaN keep their class).
+// The lo part v - hi is exact in float32 and is passed as is: the MMA reads its TF32 bits, i.e.
+// truncates it, an error below 2^-10 of lo, itself below 2^-11 of v.
+__device__ __forceinline__ float tf32_hi(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
 
 // the taps of a filter support known at compile time (FW > 0): tap t = ta fw + tb, padding taps
 // t >= fh fw up to the next multiple of 16
@@ -429,8 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const float x = tap(c * kCh + 4 * j + e);
-            hv[e] = tf32r(x);
-            lv[e] = tf32r(x - hv[e]);
+            hv[e] = tf32_hi(x);
+            lv[e] = x - hv[e];
           }
           const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
           *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
@@ -601,8 +610,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
           for (int e = 0; e < 4; ++e) {
             const int k = c * kCh + 4 * j + e;
             const float u = k < a.K ? 2.f * clampb(x[4 * j + e], beta) - x[4 * j + e] : 0.f;
-            hv[e] = tf32r(u);
-            lv[e] = tf32r(u - hv[e]);
+            hv[e] = tf32_hi(u);
+            lv[e] = u - hv[e];
           }
           const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
           *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
