@@ -35,7 +35,8 @@
 //   warps 0-3   epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs
 //               under the MMAs of row i + 1);
 //   warp 12     loader of the state v: one TMA tile load (16 maps x 1 row x 128 pixels, 8 KB) per
-//               stage of a five-stage ring, with full/empty mbarriers;
+//               stage (five stages for D^T; for D two rings of two, one per producer group), with
+//               full/empty mbarriers; boxes further ahead are prefetched into L2;
 //   warp 13     loader of the lambda rows of D^T's tiles (double-buffered).
 // The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory for the whole launch.
 // Every mbarrier wait is bounded: on timeout the CTA records CSC_ERR_TIMEOUT, stops issuing work,
@@ -63,7 +64,7 @@ constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 1
 constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
 constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo) of an A chunk
 constexpr int kAStages = 2;                      // A operand stages (16 KB each)
-constexpr int kVStages = 5;                      // state stages in flight
+constexpr int kVStages = 5;                      // state stages in flight (D^T; D has 2 rings of 2)
 constexpr int kPrefetch = 24;                    // state boxes fetched into L2 ahead of the ring
 constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
 constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
@@ -337,6 +338,19 @@ __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uin
   }
 }
 
+// The state ring as RINGS rings of PER stages: item q goes to ring q % RINGS, which one consumer group
+// reads in item order. A consumer must never wait for a stage's next phase before it has waited for
+// the current one (an mbarrier parity wait cannot tell the two apart, and the loads of different
+// items may land out of order), so consumer groups that take alternate items get a ring each.
+template <int RINGS, int PER>
+struct Ring {
+  static constexpr int STAGES = RINGS * PER;
+  __device__ static int stage(int q) { return (q % RINGS) * PER + (q / RINGS) % PER; }
+  __device__ static int phase(int q) { return (q / RINGS) / PER; }
+};
+using RingDt = Ring<1, kVStages>;   // D^T: the four epilogue warps read every item
+using RingD = Ring<2, 2>;           // D: producer group g reads the items of parity g
+
 // lane 0 of the state loader warp: the state rows of every item, in item order, into the ring (item
 // q = row tile q / groups, filters 16 (q % groups) ..; tile_row(i) gives the tile's image n and row
 // h): one TMA box of 16 maps x 1 row x 128 pixels of the tensor map vmap over v viewed as
@@ -347,7 +361,7 @@ __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uin
 // ring alone holds too few bytes to cover the latency of HBM). Before returning it waits (under the
 // default bound) for the copies of the last stages it filled, so that none is in flight when the CTA
 // ends.
-template <class TileRow>
+template <class R, class TileRow>
 __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUtensorMap* vmap, float* vring,
                                             int nitems, int groups, TileRow tile_row, bool& ok) {
   auto box = [&](int q, int& h, int& z) {
@@ -363,8 +377,8 @@ __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUte
   }
   int issued = 0;
   for (int q = 0; q < nitems; ++q) {
-    const int st = q % kVStages;
-    if (q >= kVStages) ok = ok && bar_wait(&s.v_empty[st], (uint32_t)(((q / kVStages) - 1) & 1), a.spin);
+    const int st = R::stage(q), ph = R::phase(q);
+    if (ph >= 1) ok = ok && bar_wait(&s.v_empty[st], (uint32_t)((ph - 1) & 1), a.spin);
     if (!ok) break;
     int h, z;
     box(q, h, z);
@@ -376,8 +390,8 @@ __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUte
       tma_prefetch_3d(vmap, 0, h, z);
     }
   }
-  for (int q = max(issued - kVStages, 0); q < issued; ++q)
-    bar_wait(&s.v_full[q % kVStages], (uint32_t)((q / kVStages) & 1), kDefaultSpin);
+  for (int q = max(issued - R::STAGES, 0); q < issued; ++q)
+    bar_wait(&s.v_full[R::stage(q)], (uint32_t)(R::phase(q) & 1), kDefaultSpin);
 }
 
 // ---- D^T and the state update: one tile = one image row (n, h) -----------------------------------
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
       mma_loop(a, s, ok, tmem, saddr(sa), saddr(sb), (uint32_t)(a.Kp * 64), idesc_tf32(a.Kp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
-    if ((threadIdx.x & 31) == 0) load_states(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
+    if ((threadIdx.x & 31) == 0) load_states<RingDt>(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
     __syncwarp();
   } else if (warp == kWarpL) {
     // lane 0: the fh lambda rows of every tile (rows h + ta - ch, circularly)
@@ -500,8 +514,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
       const uint32_t acc = tmem + (uint32_t)((i & 1) * 128) + lane_off;
       const size_t base = ((size_t)n * a.K * kPix + h) * kPix + p;
       for (int g = 0; g < NG; ++g) {
-        const int q = i * NG + g, st = q % kVStages;
-        if (ok) ok = bar_wait(&s.v_full[st], (uint32_t)((q / kVStages) & 1), a.spin);
+        const int q = i * NG + g, st = RingDt::stage(q);
+        if (ok) ok = bar_wait(&s.v_full[st], (uint32_t)(RingDt::phase(q) & 1), a.spin);
         ok = __all_sync(0xFFFFFFFFu, ok);
         float w[16] = {};
         if (ok) tmem_ld16(acc + (uint32_t)(g * 16), w);   // after a timeout: no TMEM read, results void
@@ -567,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
   uint8_t* sb = smem;
   uint8_t* sa = sb + bbytes;
   float* vring = reinterpret_cast<float*>(sa + 2 * kAStages * kAChunk);
-  float* ys = vring + kVStages * kCh * kPix;
+  float* ys = vring + RingD::STAGES * kCh * kPix;
   float* oring = ys + 2 * kPix * kYsPitch;
   int* tap_i = reinterpret_cast<int*>(oring + a.fh * kPix);
   const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
@@ -593,9 +607,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
     const float beta = a.beta;
     for (int i = 0; i < ntiles; ++i) {
       for (int c = 0; c < nch; ++c) {
-        const int q = i * nch + c, st = q % kAStages, vst = q % kVStages;
-        if (st != grp) continue;
-        if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)((q / kVStages) & 1), a.spin);
+        const int q = i * nch + c, st = q % kAStages, vst = RingD::stage(q);
+        if (st != grp) continue;   // with two A stages, also the state ring of this group
+        if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)(RingD::phase(q) & 1), a.spin);
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
         uint8_t* stage = sa + st * 2 * kAChunk;
         const float* vs = vring + (size_t)vst * kCh * kPix + p;
@@ -632,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
         n = tl.n;
         h = tl.hu & (kPix - 1);
       };
-      load_states(a, s, &vmap, vring, ntiles * nch, nch, tile_row, ok);
+      load_states<RingD>(a, s, &vmap, vring, ntiles * nch, nch, tile_row, ok);
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -763,7 +777,7 @@ static size_t corr_smem(const Ctx& c) {
          (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * round16(c.fh * c.fw) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::kVStages * sp::kVStage +
+  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::RingD::STAGES * sp::kVStage +
          (size_t)2 * sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4 + (size_t)round16(c.fh * c.fw) * 4;
 }
 static constexpr int kLamThreads = 512;
