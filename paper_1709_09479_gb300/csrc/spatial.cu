@@ -68,7 +68,8 @@ constexpr int kVStages = 5;                      // state stages in flight (D^T;
 constexpr int kPrefetch = 24;                    // state boxes fetched into L2 ahead of the ring
 constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
 constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
-constexpr int kTmemCols = 256;                   // two accumulators of up to 128 columns
+constexpr int kTmemCols = 512;                   // two accumulators of up to 128 columns, then the A stages
+constexpr uint32_t kAColBase = 256;              // A stage s at columns kAColBase + 32 s: hi 0-15, lo 16-31
 constexpr long long kDefaultSpin = 2000000000LL; // ~1 s of SM clocks
 constexpr uint32_t kSuspendHintNs = 100000;      // longest suspension of one mbarrier try_wait
 
@@ -90,6 +91,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t a) {
 // instruction descriptor: D f32, A and B TF32, both K-major, N >> 3 at bits 17-22, M = 128
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+// A from TMEM (lane = row, one column per TF32 element), B from shared memory
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc));
 }
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   asm volatile(
@@ -145,6 +154,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// 16 consecutive TMEM columns of the warp's 32 lanes from registers (no wait)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+// an A stage's row (16 contraction elements, hi then lo) into TMEM lane threadIdx.x % 128 by its
+// producer thread; visible to the MMA issuer after the mbarrier arrival that follows
+__device__ __forceinline__ void stage_row(uint32_t tmem, int st, const uint32_t* hv, const uint32_t* lv) {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");   // the MMAs that read the stage are done
+  const uint32_t ta = tmem + ((uint32_t)(threadIdx.x & 96) << 16) + kAColBase + 32u * (uint32_t)st;
+  tmem_st16(ta, hv);
+  tmem_st16(ta + 16u, lv);
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 __device__ __forceinline__ void cp4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr(dst)), "l"(src) : "memory");
@@ -310,10 +338,10 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
       for (int ps = 0; ps < a.passes; ++ps) {
-        const uint32_t pa = (ps == 2) ? (uint32_t)kAChunk : 0u;   // hi.hi, hi.lo, lo.hi
+        const uint32_t pa = (ps == 2) ? 16u : 0u;   // hi.hi, hi.lo, lo.hi (A columns: hi 0-15, lo 16-31)
         const uint32_t pb = (ps == 1) ? bsplit : 0u;
-        mma_tf32(acc, sdesc(astage + pa + (uint32_t)ks * 2u * kLbo), sdesc(bchunk + pb + (uint32_t)ks * 2u * kLbo), id,
-                 (first && ks == 0 && ps == 0) ? 0u : 1u);
+        mma_tf32_ta(acc, astage + pa + (uint32_t)ks * 8u, sdesc(bchunk + pb + (uint32_t)ks * 2u * kLbo), id,
+                    (first && ks == 0 && ps == 0) ? 0u : 1u);
       }
     }
   }
@@ -324,15 +352,15 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
 // lane 0 of the MMA warp: every chunk of every row tile once the producers have filled its A stage
 // (and, for a row's first chunk, once the epilogue has emptied the accumulator it reuses); the B
 // chunk c starts bchunk * c bytes into the filter operand
-__device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uint32_t tmem, uint32_t sa0,
-                                         uint32_t sb0, uint32_t bchunk, uint32_t id, int ntiles, int nch) {
+__device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uint32_t tmem, uint32_t sb0,
+                                         uint32_t bchunk, uint32_t id, int ntiles, int nch) {
   const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
   for (int i = 0; i < ntiles; ++i) {
     for (int c = 0; c < nch; ++c) {
       const int q = i * nch + c, st = q % kAStages;
       if (ok) ok = bar_wait(&s.a_full[st], (uint32_t)((q / kAStages) & 1), a.spin);
       if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
-      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), sa0 + (uint32_t)(st * 2 * kAChunk),
+      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), tmem + kAColBase + 32u * (uint32_t)st,
                   sb0 + (uint32_t)c * bchunk, bsplit, id, c == 0, st, c == nch - 1, i & 1);
     }
   }
@@ -406,8 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
   const int nch = a.Tp / kCh, NG = a.Kp / kCh;
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
-  uint8_t* sa = sb + bbytes;
-  float* vring = reinterpret_cast<float*>(sa + 2 * kAStages * kAChunk);
+  float* vring = reinterpret_cast<float*>(sb + bbytes);
   float* lbuf = vring + kVStages * kCh * kPix;
   const int lrows = a.fh + 1;
   int* tap_a = reinterpret_cast<int*>(lbuf + 2 * lrows * kPix);
@@ -445,21 +472,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
         const int q = i * nch + c, st = q % kAStages;
         if (st != grp) return;
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
-        uint8_t* stage = sa + st * 2 * kAChunk;
+        uint32_t hv[16], lv[16];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float hv[4], lv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float x = tap(c * kCh + 4 * j + e);
-            hv[e] = tf32_hi(x);
-            lv[e] = x - hv[e];
-          }
-          const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
-          *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-          *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        for (int e = 0; e < 16; ++e) {
+          const float x = tap(c * kCh + e);
+          const float h = tf32_hi(x);
+          hv[e] = __float_as_uint(h);
+          lv[e] = __float_as_uint(x - h);
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        stage_row(tmem, st, hv, lv);
         warp_arrive(&s.a_full[st]);
       };
       if constexpr (FW > 0) {
@@ -474,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sa), saddr(sb), (uint32_t)(a.Kp * 64), idesc_tf32(a.Kp), ntiles, nch);
+      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Kp * 64), idesc_tf32(a.Kp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) load_states<RingDt>(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
@@ -579,8 +600,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
   const int nch = a.Kp / kCh, ntc = a.Tp / kCh;
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
-  uint8_t* sa = sb + bbytes;
-  float* vring = reinterpret_cast<float*>(sa + 2 * kAStages * kAChunk);
+  float* vring = reinterpret_cast<float*>(sb + bbytes);
   float* ys = vring + RingD::STAGES * kCh * kPix;
   float* oring = ys + 2 * kPix * kYsPitch;
   int* tap_i = reinterpret_cast<int*>(oring + a.fh * kPix);
@@ -611,33 +631,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
         if (st != grp) continue;   // with two A stages, also the state ring of this group
         if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)(RingD::phase(q) & 1), a.spin);
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
-        uint8_t* stage = sa + st * 2 * kAChunk;
         const float* vs = vring + (size_t)vst * kCh * kPix + p;
         float x[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) x[e] = vs[e * kPix];
         warp_arrive(&s.v_empty[vst]);
+        uint32_t hv[16], lv[16];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float hv[4], lv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = c * kCh + 4 * j + e;
-            const float u = k < a.K ? 2.f * clampb(x[4 * j + e], beta) - x[4 * j + e] : 0.f;
-            hv[e] = tf32_hi(u);
-            lv[e] = u - hv[e];
-          }
-          const uint32_t o = (uint32_t)((p >> 3) * kSbo + j * kLbo + (p & 7) * 16);
-          *reinterpret_cast<float4*>(stage + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-          *reinterpret_cast<float4*>(stage + kAChunk + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        for (int e = 0; e < 16; ++e) {
+          const int k = c * kCh + e;
+          const float u = k < a.K ? 2.f * clampb(x[e], beta) - x[e] : 0.f;
+          const float h = tf32_hi(u);
+          hv[e] = __float_as_uint(h);
+          lv[e] = __float_as_uint(u - h);
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        stage_row(tmem, st, hv, lv);
         warp_arrive(&s.a_full[st]);
       }
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sa), saddr(sb), (uint32_t)(a.Tp * 64), idesc_tf32(a.Tp), ntiles, nch);
+      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Tp * 64), idesc_tf32(a.Tp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) {
@@ -773,11 +787,11 @@ bool spatial_applies(const Ctx& c, std::string* why) {
 size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * round16(c.fh * c.fw) * 4; }
 
 static size_t corr_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::kVStages * sp::kVStage +
+  return spatial_operand_bytes(c) + sp::kVStages * sp::kVStage +
          (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * round16(c.fh * c.fw) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + 2 * sp::kAStages * sp::kAChunk + sp::RingD::STAGES * sp::kVStage +
+  return spatial_operand_bytes(c) + sp::RingD::STAGES * sp::kVStage +
          (size_t)2 * sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4 + (size_t)round16(c.fh * c.fw) * 4;
 }
 static constexpr int kLamThreads = 512;
@@ -831,7 +845,8 @@ cudaError_t launch_spatial_conv(const Ctx& c, const float* v) {
   CUtensorMap vmap;
   cudaError_t e = state_map(c, v, &vmap);
   if (e != cudaSuccess) return e;
-  const int smem = (int)conv_smem(c);
+  // at least 116 KB, so that one CTA holds an SM and its 512 TMEM columns
+  const int smem = (int)std::max<size_t>(conv_smem(c), 116 * 1024);
   // 11 x 11 (the benchmark's support) with compile-time taps; every other support reads tap tables
   auto kern = (c.fh == 11 && c.fw == 11) ? sp::k_sp_conv<11, 11> : sp::k_sp_conv<0, 0>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -854,7 +869,7 @@ cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last) {
   CUtensorMap vmap;
   cudaError_t e = state_map(c, v, &vmap);
   if (e != cudaSuccess) return e;
-  const int smem = (int)corr_smem(c);
+  const int smem = (int)std::max<size_t>(corr_smem(c), 116 * 1024);
   const bool t11 = (c.fh == 11 && c.fw == 11);
   auto kern = last ? (t11 ? sp::k_sp_corr<true, 11, 11> : sp::k_sp_corr<true, 0, 0>)
                    : (t11 ? sp::k_sp_corr<false, 11, 11> : sp::k_sp_corr<false, 0, 0>);
