@@ -26,10 +26,11 @@
 // The TF32 mode takes hi.hi alone.
 //
 // Kernel shape (both products): one CTA per SM, persistent over its range of rows, four roles:
-//   warps 4-11  producers: stage the row's operand chunks of 16 contraction elements (split into
-//               TF32 hi and lo) through a two-stage ring in the canonical no-swizzle K-major layout,
-//               two threads per pixel row (two warps per scheduler, so that one's shared-memory
-//               latency hides under the other's conversions);
+//   warps 4-11  producers, two groups of four warps: stage the row's operand chunks of 16
+//               contraction elements, split into TF32 hi and lo, in TMEM (the MMA's A operand: lane p =
+//               pixel p, one column per element; group g fills the stage of parity g, thread p of a
+//               group writes lane p with tcgen05.st), so that shared memory carries only the filter
+//               operand (the MMA's B), the state ring and the exchanges;
 //   warp 14     lane 0 issues the MMAs of each filled stage (an issuing thread waits for the tensor
 //               pipe, so it must not be a producer: the next chunk is built meanwhile);
 //   warps 0-3   epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs
