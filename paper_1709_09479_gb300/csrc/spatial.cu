@@ -60,6 +60,7 @@ constexpr int kWarpV = 12, kWarpL = 13;        // loader warps (state, lambda ro
 constexpr int kWarpMma = 14;                   // lane 0 issues every MMA of the CTA
 constexpr int kMmaThread = 32 * kWarpMma;
 constexpr int kPix = 128;                        // pixels of a row: MMA M, TMEM lanes
+constexpr int kAK = 32;                          // contraction elements of an A chunk (one hand-off, 4 K-steps)
 constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
 constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
 constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
@@ -67,10 +68,11 @@ constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo
 constexpr int kAStages = 2;                      // A operand stages (16 KB each)
 constexpr int kVStages = 5;                      // state stages in flight (D^T; D has 2 rings of 2)
 constexpr int kPrefetch = 24;                    // state boxes fetched into L2 ahead of the ring
-constexpr int kVStage = kCh * kPix * 4;          // 16 maps x 128 pixels
+constexpr int kVStage = kCh * kPix * 4;          // D^T's state box: 16 maps x 128 pixels
+constexpr int kVStageD = kAK * kPix * 4;         // D's state box: 32 maps x 128 pixels (one A chunk)
 constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
 constexpr int kTmemCols = 512;                   // two accumulators of up to 128 columns, then the A stages
-constexpr uint32_t kAColBase = 256;              // A stage s at columns kAColBase + 32 s: hi 0-15, lo 16-31
+constexpr uint32_t kAColBase = 256;              // A stage s at columns kAColBase + 2 kAK s: hi 0-31, lo 32-63
 constexpr long long kDefaultSpin = 2000000000LL; // ~1 s of SM clocks
 constexpr uint32_t kSuspendHintNs = 100000;      // longest suspension of one mbarrier try_wait
 
@@ -165,13 +167,19 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
-// an A stage's row (16 contraction elements, hi then lo) into TMEM lane threadIdx.x % 128 by its
-// producer thread; visible to the MMA issuer after the mbarrier arrival that follows
-__device__ __forceinline__ void stage_row(uint32_t tmem, int st, const uint32_t* hv, const uint32_t* lv) {
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");   // the MMAs that read the stage are done
-  const uint32_t ta = tmem + ((uint32_t)(threadIdx.x & 96) << 16) + kAColBase + 32u * (uint32_t)st;
-  tmem_st16(ta, hv);
-  tmem_st16(ta + 16u, lv);
+// The producer thread of TMEM lane threadIdx.x % 128 writes its row of an A stage: stage_begin after
+// the stage is free (the MMAs that read it have completed), 16 elements at a time with stage_put
+// (hi at columns e0.., lo at kAK + e0..), stage_end before the mbarrier arrival that hands the stage
+// to the MMA issuer
+__device__ __forceinline__ uint32_t stage_begin(uint32_t tmem, int st) {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  return tmem + ((uint32_t)(threadIdx.x & 96) << 16) + kAColBase + (uint32_t)(2 * kAK) * (uint32_t)st;
+}
+__device__ __forceinline__ void stage_put(uint32_t ta, int e0, const uint32_t* hv, const uint32_t* lv) {
+  tmem_st16(ta + (uint32_t)e0, hv);
+  tmem_st16(ta + (uint32_t)(kAK + e0), lv);
+}
+__device__ __forceinline__ void stage_end() {
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
@@ -197,7 +205,8 @@ __device__ __forceinline__ float tf32_hi(float v) {
 // t >= fh fw up to the next multiple of 16
 template <int FH, int FW>
 struct Taps {
-  static constexpr int T = FH * FW, TP = (T + 15) / 16 * 16, NCH = TP / 16, CH = (FH - 1) / 2, CW = (FW - 1) / 2;
+  static constexpr int T = FH * FW, TP = (T + 15) / 16 * 16, NCH = TP / 16, NCHA = (TP + kAK - 1) / kAK,
+                       CH = (FH - 1) / 2, CW = (FW - 1) / 2;
   // D^T gather: lambda row offset (row fh is the zero row) and column shift of tap t
   __host__ __device__ static constexpr int row(int t) { return t < T ? (t / FW) * kPix : FH * kPix; }
   __host__ __device__ static constexpr int shift(int t) { return t < T ? t % FW - CW : 0; }
@@ -329,20 +338,22 @@ __device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s.tmem), "r"(kTmemCols));
 }
 
-// the MMAs of one chunk (2 K-steps x passes) into accumulator acc; the commit frees the A stage, and
-// after the row's last chunk marks the accumulator complete
+// the MMAs of one A chunk (nks K-steps of 8 elements x passes) into accumulator acc; B's K-step ks of
+// the chunk lies in its 16-element block bblk0 + ks / 2 (blocks blk bytes apart). The commit frees
+// the A stage, and after the row's last chunk marks the accumulator complete
 __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, uint32_t acc, uint32_t astage,
-                                            uint32_t bchunk, uint32_t bsplit, uint32_t id, bool first, int st,
-                                            bool last, int accb) {
+                                            uint32_t bblk0, uint32_t blk, int nks, uint32_t bsplit, uint32_t id,
+                                            bool first, int st, bool last, int accb) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (ok) {
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
+    for (int ks = 0; ks < kAK / 8; ++ks) {
+      if (ks >= nks) break;
+      const uint32_t b = bblk0 + (uint32_t)(ks >> 1) * blk + (uint32_t)(ks & 1) * 2u * kLbo;
       for (int ps = 0; ps < a.passes; ++ps) {
-        const uint32_t pa = (ps == 2) ? 16u : 0u;   // hi.hi, hi.lo, lo.hi (A columns: hi 0-15, lo 16-31)
+        const uint32_t pa = (ps == 2) ? (uint32_t)kAK : 0u;   // hi.hi, hi.lo, lo.hi
         const uint32_t pb = (ps == 1) ? bsplit : 0u;
-        mma_tf32_ta(acc, astage + pa + (uint32_t)ks * 8u, sdesc(bchunk + pb + (uint32_t)ks * 2u * kLbo), id,
-                    (first && ks == 0 && ps == 0) ? 0u : 1u);
+        mma_tf32_ta(acc, astage + pa + (uint32_t)ks * 8u, sdesc(b + pb), id, (first && ks == 0 && ps == 0) ? 0u : 1u);
       }
     }
   }
@@ -350,19 +361,21 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
   if (last) commit(&s.acc_full[accb]);
 }
 
-// lane 0 of the MMA warp: every chunk of every row tile once the producers have filled its A stage
-// (and, for a row's first chunk, once the epilogue has emptied the accumulator it reuses); the B
-// chunk c starts bchunk * c bytes into the filter operand
+// lane 0 of the MMA warp: every A chunk of every row tile once the producers have filled its stage
+// (and, for a row's first chunk, once the epilogue has emptied the accumulator it reuses). The
+// contraction has kdim elements (a multiple of 16): chunk c covers kAK of them from kAK c; the filter
+// operand's 16-element blocks are blk bytes apart from sb0
 __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uint32_t tmem, uint32_t sb0,
-                                         uint32_t bchunk, uint32_t id, int ntiles, int nch) {
+                                         uint32_t blk, int kdim, uint32_t id, int ntiles, int nch) {
   const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
   for (int i = 0; i < ntiles; ++i) {
     for (int c = 0; c < nch; ++c) {
       const int q = i * nch + c, st = q % kAStages;
       if (ok) ok = bar_wait(&s.a_full[st], (uint32_t)((q / kAStages) & 1), a.spin);
       if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
-      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), tmem + kAColBase + 32u * (uint32_t)st,
-                  sb0 + (uint32_t)c * bchunk, bsplit, id, c == 0, st, c == nch - 1, i & 1);
+      const int nks = min(kAK, kdim - kAK * c) / 8;
+      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), tmem + kAColBase + (uint32_t)(2 * kAK) * (uint32_t)st,
+                  sb0 + (uint32_t)(c * (kAK / kCh)) * blk, blk, nks, bsplit, id, c == 0, st, c == nch - 1, i & 1);
     }
   }
 }
@@ -381,8 +394,8 @@ using RingDt = Ring<1, kVStages>;   // D^T: the four epilogue warps read every i
 using RingD = Ring<2, 2>;           // D: producer group g reads the items of parity g
 
 // lane 0 of the state loader warp: the state rows of every item, in item order, into the ring (item
-// q = row tile q / groups, filters 16 (q % groups) ..; tile_row(i) gives the tile's image n and row
-// h): one TMA box of 16 maps x 1 row x 128 pixels of the tensor map vmap over v viewed as
+// q = row tile q / groups, maps MAPS (q % groups) ..; tile_row(i) gives the tile's image n and row
+// h): one TMA box of MAPS maps x 1 row x 128 pixels of the tensor map vmap over v viewed as
 // [N K][128][128] (maps past the image's K belong to the next image, or lie past the end and read as
 // zeros; their values are never used). A stage is refilled only after its consumers released it, so
 // every copy lands in a free stage and completes the phase it was counted in; when a wait gives up
@@ -390,11 +403,11 @@ using RingD = Ring<2, 2>;           // D: producer group g reads the items of pa
 // ring alone holds too few bytes to cover the latency of HBM). Before returning it waits (under the
 // default bound) for the copies of the last stages it filled, so that none is in flight when the CTA
 // ends.
-template <class R, class TileRow>
+template <class R, int MAPS, class TileRow>
 __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUtensorMap* vmap, float* vring,
                                             int nitems, int groups, TileRow tile_row, bool& ok) {
   auto box = [&](int q, int& h, int& z) {
-    const int i = q / groups, k0 = (q - i * groups) * kCh;
+    const int i = q / groups, k0 = (q - i * groups) * MAPS;
     int n;
     tile_row(i, n, h);
     z = n * a.K + k0;
@@ -411,8 +424,8 @@ __device__ __forceinline__ void load_states(const SpArgs& a, Sync& s, const CUte
     if (!ok) break;
     int h, z;
     box(q, h, z);
-    bar_expect(&s.v_full[st], (uint32_t)kVStage);
-    tma_load_3d(vring + (size_t)st * kCh * kPix, vmap, 0, h, z, &s.v_full[st]);
+    bar_expect(&s.v_full[st], (uint32_t)(MAPS * kPix * 4));
+    tma_load_3d(vring + (size_t)st * MAPS * kPix, vmap, 0, h, z, &s.v_full[st]);
     issued = q + 1;
     if (q + kPrefetch < nitems) {
       box(q + kPrefetch, h, z);
@@ -432,16 +445,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
-  const int nch = a.Tp / kCh, NG = a.Kp / kCh;
+  const int nch = (a.Tp + kAK - 1) / kAK, NG = a.Kp / kCh, TA = nch * kAK;
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   float* vring = reinterpret_cast<float*>(sb + bbytes);
   float* lbuf = vring + kVStages * kCh * kPix;
   const int lrows = a.fh + 1;
   int* tap_a = reinterpret_cast<int*>(lbuf + 2 * lrows * kPix);
-  int* tap_b = tap_a + a.Tp;
+  int* tap_b = tap_a + TA;
   const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
-  for (int t = threadIdx.x; t < a.Tp; t += kThreads) {
+  for (int t = threadIdx.x; t < TA; t += kThreads) {
     const int ta = t / a.fw, tb = t - ta * a.fw;
     tap_a[t] = t < a.T ? ta * kPix : a.fh * kPix;
     tap_b[t] = t < a.T ? tb - cw : 0;
@@ -473,21 +486,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
         const int q = i * nch + c, st = q % kAStages;
         if (st != grp) return;
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
-        uint32_t hv[16], lv[16];
+        const uint32_t ta = stage_begin(tmem, st);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float x = tap(c * kCh + e);
-          const float h = tf32_hi(x);
-          hv[e] = __float_as_uint(h);
-          lv[e] = __float_as_uint(x - h);
+        for (int e0 = 0; e0 < kAK; e0 += 16) {
+          uint32_t hv[16], lv[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float x = tap(c * kAK + e0 + e);
+            const float h = tf32_hi(x);
+            hv[e] = __float_as_uint(h);
+            lv[e] = __float_as_uint(x - h);
+          }
+          stage_put(ta, e0, hv, lv);
         }
-        stage_row(tmem, st, hv, lv);
+        stage_end();
         warp_arrive(&s.a_full[st]);
       };
       if constexpr (FW > 0) {
         // compile-time taps: every gather address is p plus constants
 #pragma unroll
-        for (int c = 0; c < CT::NCH; ++c)
+        for (int c = 0; c < CT::NCHA; ++c)
           chunk(c, [&](int t) { return lb[CT::row(t) + ((p + CT::shift(t)) & (kPix - 1))]; });
       } else {
         for (int c = 0; c < nch; ++c) chunk(c, [&](int t) { return lb[tap_a[t] + ((p + tap_b[t]) & (kPix - 1))]; });
@@ -496,10 +514,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Kp * 64), idesc_tf32(a.Kp), ntiles, nch);
+      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Kp * 64), a.Tp, idesc_tf32(a.Kp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
-    if ((threadIdx.x & 31) == 0) load_states<RingDt>(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
+    if ((threadIdx.x & 31) == 0) load_states<RingDt, kCh>(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
     __syncwarp();
   } else if (warp == kWarpL) {
     // lane 0: the fh lambda rows of every tile (rows h + ta - ch, circularly)
@@ -598,11 +616,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
-  const int nch = a.Kp / kCh, ntc = a.Tp / kCh;
+  const int nch = (a.Kp + kAK - 1) / kAK, ntc = a.Tp / kCh;
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   float* vring = reinterpret_cast<float*>(sb + bbytes);
-  float* ys = vring + RingD::STAGES * kCh * kPix;
+  float* ys = vring + RingD::STAGES * kAK * kPix;
   float* oring = ys + 2 * kPix * kYsPitch;
   int* tap_i = reinterpret_cast<int*>(oring + a.fh * kPix);
   const int ch = (a.fh - 1) / 2, cw = (a.fw - 1) / 2;
@@ -632,27 +650,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
         if (st != grp) continue;   // with two A stages, also the state ring of this group
         if (ok) ok = bar_wait(&s.v_full[vst], (uint32_t)(RingD::phase(q) & 1), a.spin);
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
-        const float* vs = vring + (size_t)vst * kCh * kPix + p;
-        float x[16];
+        const float* vs = vring + (size_t)vst * kAK * kPix + p;
+        float x[kAK];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) x[e] = vs[e * kPix];
+        for (int e = 0; e < kAK; ++e) x[e] = vs[e * kPix];
         warp_arrive(&s.v_empty[vst]);
-        uint32_t hv[16], lv[16];
+        const uint32_t ta = stage_begin(tmem, st);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int k = c * kCh + e;
-          const float u = k < a.K ? 2.f * clampb(x[e], beta) - x[e] : 0.f;
-          const float h = tf32_hi(u);
-          hv[e] = __float_as_uint(h);
-          lv[e] = __float_as_uint(u - h);
+        for (int e0 = 0; e0 < kAK; e0 += 16) {
+          uint32_t hv[16], lv[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int k = c * kAK + e0 + e;
+            const float u = k < a.K ? 2.f * clampb(x[e0 + e], beta) - x[e0 + e] : 0.f;
+            const float h = tf32_hi(u);
+            hv[e] = __float_as_uint(h);
+            lv[e] = __float_as_uint(u - h);
+          }
+          stage_put(ta, e0, hv, lv);
         }
-        stage_row(tmem, st, hv, lv);
+        stage_end();
         warp_arrive(&s.a_full[st]);
       }
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Tp * 64), idesc_tf32(a.Tp), ntiles, nch);
+      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Tp * 64), a.Kp, idesc_tf32(a.Tp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) {
@@ -661,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
         n = tl.n;
         h = tl.hu & (kPix - 1);
       };
-      load_states<RingD>(a, s, &vmap, vring, ntiles * nch, nch, tile_row, ok);
+      load_states<RingD, kAK>(a, s, &vmap, vring, ntiles * nch, nch, tile_row, ok);
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -789,10 +812,10 @@ size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * r
 
 static size_t corr_smem(const Ctx& c) {
   return spatial_operand_bytes(c) + sp::kVStages * sp::kVStage +
-         (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * round16(c.fh * c.fw) * 4;
+         (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * ((round16(c.fh * c.fw) + sp::kAK - 1) / sp::kAK * sp::kAK) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
-  return spatial_operand_bytes(c) + sp::RingD::STAGES * sp::kVStage +
+  return spatial_operand_bytes(c) + sp::RingD::STAGES * sp::kVStageD +
          (size_t)2 * sp::kPix * sp::kYsPitch * 4 + (size_t)c.fh * sp::kPix * 4 + (size_t)round16(c.fh * c.fw) * 4;
 }
 static constexpr int kLamThreads = 512;
@@ -819,9 +842,9 @@ cudaError_t launch_spatial_operands(const Ctx& c, const float* d) {
 
 static int sp_grid(const Ctx& c) { return std::min(c.nsm, c.N * sp::kPix); }
 
-// the tensor map of the state v as [N K][128][128] float32 with boxes of 16 maps x 1 row x 128
+// the tensor map of the state v as [N K][128][128] float32 with boxes of `maps` maps x 1 row x 128
 // pixels (the loader's stage); the encoder comes from the driver through the runtime
-static cudaError_t state_map(const Ctx& c, const float* v, CUtensorMap* m) {
+static cudaError_t state_map(const Ctx& c, const float* v, int maps, CUtensorMap* m) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -833,7 +856,7 @@ static cudaError_t state_map(const Ctx& c, const float* v, CUtensorMap* m) {
   }
   const cuuint64_t dims[3] = {(cuuint64_t)sp::kPix, (cuuint64_t)sp::kPix, (cuuint64_t)c.N * c.K};
   const cuuint64_t strides[2] = {(cuuint64_t)sp::kPix * 4, (cuuint64_t)sp::kPix * sp::kPix * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)sp::kPix, 1u, (cuuint32_t)sp::kCh};
+  const cuuint32_t box[3] = {(cuuint32_t)sp::kPix, 1u, (cuuint32_t)maps};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(v), dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -844,7 +867,7 @@ static cudaError_t state_map(const Ctx& c, const float* v, CUtensorMap* m) {
 cudaError_t launch_spatial_conv(const Ctx& c, const float* v) {
   const sp::SpArgs a = sp_args(c, c.sp_bc, const_cast<float*>(v), nullptr);
   CUtensorMap vmap;
-  cudaError_t e = state_map(c, v, &vmap);
+  cudaError_t e = state_map(c, v, sp::kAK, &vmap);
   if (e != cudaSuccess) return e;
   // at least 116 KB, so that one CTA holds an SM and its 512 TMEM columns
   const int smem = (int)std::max<size_t>(conv_smem(c), 116 * 1024);
@@ -868,7 +891,7 @@ cudaError_t launch_spatial_lambda(const Ctx& c, const float* x) {
 cudaError_t launch_spatial_corr(const Ctx& c, float* v, float* z, bool last) {
   const sp::SpArgs a = sp_args(c, c.sp_bt, v, z);
   CUtensorMap vmap;
-  cudaError_t e = state_map(c, v, &vmap);
+  cudaError_t e = state_map(c, v, sp::kCh, &vmap);
   if (e != cudaSuccess) return e;
   const int smem = (int)std::max<size_t>(corr_smem(c), 116 * 1024);
   const bool t11 = (c.fh == 11 && c.fw == 11);
