@@ -60,7 +60,8 @@ constexpr int kWarpV = 12, kWarpL = 13;        // loader warps (state, lambda ro
 constexpr int kWarpMma = 14;                   // lane 0 issues every MMA of the CTA
 constexpr int kMmaThread = 32 * kWarpMma;
 constexpr int kPix = 128;                        // pixels of a row: MMA M, TMEM lanes
-constexpr int kAK = 32;                          // contraction elements of an A chunk (one hand-off, 4 K-steps)
+constexpr int kAK = 32;                          // contraction elements of D's A chunks (one hand-off, 4 K-steps)
+constexpr int kAKDt = 64;                        // ... of D^T's A chunks (its producers read no state: 8 K-steps)
 constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
 constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
 constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
@@ -72,7 +73,7 @@ constexpr int kVStage = kCh * kPix * 4;          // D^T's state box: 16 maps x 1
 constexpr int kVStageD = kAK * kPix * 4;         // D's state box: 32 maps x 128 pixels (one A chunk)
 constexpr int kYsPitch = kCh + 1;                // epilogue exchange of the conv: [2][128 pixels][17]
 constexpr int kTmemCols = 512;                   // two accumulators of up to 128 columns, then the A stages
-constexpr uint32_t kAColBase = 256;              // A stage s at columns kAColBase + 2 kAK s: hi 0-31, lo 32-63
+constexpr uint32_t kAColBase = 256;              // A stage s at columns kAColBase + 2 AK s: hi 0..AK-1, lo AK..
 constexpr long long kDefaultSpin = 2000000000LL; // ~1 s of SM clocks
 constexpr uint32_t kSuspendHintNs = 100000;      // longest suspension of one mbarrier try_wait
 
@@ -169,15 +170,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
 }
 // The producer thread of TMEM lane threadIdx.x % 128 writes its row of an A stage: stage_begin after
 // the stage is free (the MMAs that read it have completed), 16 elements at a time with stage_put
-// (hi at columns e0.., lo at kAK + e0..), stage_end before the mbarrier arrival that hands the stage
+// (hi at columns e0.., lo at AK + e0..), stage_end before the mbarrier arrival that hands the stage
 // to the MMA issuer
+template <int AK>
 __device__ __forceinline__ uint32_t stage_begin(uint32_t tmem, int st) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  return tmem + ((uint32_t)(threadIdx.x & 96) << 16) + kAColBase + (uint32_t)(2 * kAK) * (uint32_t)st;
+  return tmem + ((uint32_t)(threadIdx.x & 96) << 16) + kAColBase + (uint32_t)(2 * AK) * (uint32_t)st;
 }
+template <int AK>
 __device__ __forceinline__ void stage_put(uint32_t ta, int e0, const uint32_t* hv, const uint32_t* lv) {
   tmem_st16(ta + (uint32_t)e0, hv);
-  tmem_st16(ta + (uint32_t)(kAK + e0), lv);
+  tmem_st16(ta + (uint32_t)(AK + e0), lv);
 }
 __device__ __forceinline__ void stage_end() {
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
@@ -205,7 +208,7 @@ __device__ __forceinline__ float tf32_hi(float v) {
 // t >= fh fw up to the next multiple of 16
 template <int FH, int FW>
 struct Taps {
-  static constexpr int T = FH * FW, TP = (T + 15) / 16 * 16, NCH = TP / 16, NCHA = (TP + kAK - 1) / kAK,
+  static constexpr int T = FH * FW, TP = (T + 15) / 16 * 16, NCH = TP / 16, NCHA = (TP + kAKDt - 1) / kAKDt,
                        CH = (FH - 1) / 2, CW = (FW - 1) / 2;
   // D^T gather: lambda row offset (row fh is the zero row) and column shift of tap t
   __host__ __device__ static constexpr int row(int t) { return t < T ? (t / FW) * kPix : FH * kPix; }
@@ -341,17 +344,18 @@ __device__ __forceinline__ void kernel_end(const SpArgs& a, Sync& s, bool ok) {
 // the MMAs of one A chunk (nks K-steps of 8 elements x passes) into accumulator acc; B's K-step ks of
 // the chunk lies in its 16-element block bblk0 + ks / 2 (blocks blk bytes apart). The commit frees
 // the A stage, and after the row's last chunk marks the accumulator complete
+template <int AK>
 __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, uint32_t acc, uint32_t astage,
                                             uint32_t bblk0, uint32_t blk, int nks, uint32_t bsplit, uint32_t id,
                                             bool first, int st, bool last, int accb) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (ok) {
 #pragma unroll
-    for (int ks = 0; ks < kAK / 8; ++ks) {
+    for (int ks = 0; ks < AK / 8; ++ks) {
       if (ks >= nks) break;
       const uint32_t b = bblk0 + (uint32_t)(ks >> 1) * blk + (uint32_t)(ks & 1) * 2u * kLbo;
       for (int ps = 0; ps < a.passes; ++ps) {
-        const uint32_t pa = (ps == 2) ? (uint32_t)kAK : 0u;   // hi.hi, hi.lo, lo.hi
+        const uint32_t pa = (ps == 2) ? (uint32_t)AK : 0u;   // hi.hi, hi.lo, lo.hi
         const uint32_t pb = (ps == 1) ? bsplit : 0u;
         mma_tf32_ta(acc, astage + pa + (uint32_t)ks * 8u, sdesc(b + pb), id, (first && ks == 0 && ps == 0) ? 0u : 1u);
       }
@@ -363,8 +367,9 @@ __device__ __forceinline__ void issue_chunk(const SpArgs& a, Sync& s, bool ok, u
 
 // lane 0 of the MMA warp: every A chunk of every row tile once the producers have filled its stage
 // (and, for a row's first chunk, once the epilogue has emptied the accumulator it reuses). The
-// contraction has kdim elements (a multiple of 16): chunk c covers kAK of them from kAK c; the filter
+// contraction has kdim elements (a multiple of 16): chunk c covers AK of them from AK c; the filter
 // operand's 16-element blocks are blk bytes apart from sb0
+template <int AK>
 __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uint32_t tmem, uint32_t sb0,
                                          uint32_t blk, int kdim, uint32_t id, int ntiles, int nch) {
   const uint32_t bsplit = (uint32_t)(a.Kp * a.Tp * 4);
@@ -373,9 +378,9 @@ __device__ __forceinline__ void mma_loop(const SpArgs& a, Sync& s, bool& ok, uin
       const int q = i * nch + c, st = q % kAStages;
       if (ok) ok = bar_wait(&s.a_full[st], (uint32_t)((q / kAStages) & 1), a.spin);
       if (c == 0 && i >= 2 && ok) ok = bar_wait(&s.acc_empty[i & 1], (uint32_t)(((i >> 1) - 1) & 1), a.spin);
-      const int nks = min(kAK, kdim - kAK * c) / 8;
-      issue_chunk(a, s, ok, tmem + (uint32_t)((i & 1) * 128), tmem + kAColBase + (uint32_t)(2 * kAK) * (uint32_t)st,
-                  sb0 + (uint32_t)(c * (kAK / kCh)) * blk, blk, nks, bsplit, id, c == 0, st, c == nch - 1, i & 1);
+      const int nks = min(AK, kdim - AK * c) / 8;
+      issue_chunk<AK>(a, s, ok, tmem + (uint32_t)((i & 1) * 128), tmem + kAColBase + (uint32_t)(2 * AK) * (uint32_t)st,
+                      sb0 + (uint32_t)(c * (AK / kCh)) * blk, blk, nks, bsplit, id, c == 0, st, c == nch - 1, i & 1);
     }
   }
 }
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Sync s;
   const int warp = threadIdx.x >> 5;
-  const int nch = (a.Tp + kAK - 1) / kAK, NG = a.Kp / kCh, TA = nch * kAK;
+  const int nch = (a.Tp + kAKDt - 1) / kAKDt, NG = a.Kp / kCh, TA = nch * kAKDt;
   const size_t bbytes = (size_t)2 * a.Kp * a.Tp * 4;
   uint8_t* sb = smem;
   float* vring = reinterpret_cast<float*>(sb + bbytes);
@@ -486,18 +491,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
         const int q = i * nch + c, st = q % kAStages;
         if (st != grp) return;
         if (q >= kAStages && ok) ok = bar_wait(&s.a_empty[st], (uint32_t)(((q / kAStages) - 1) & 1), a.spin);
-        const uint32_t ta = stage_begin(tmem, st);
+        const uint32_t ta = stage_begin<kAKDt>(tmem, st);
 #pragma unroll
-        for (int e0 = 0; e0 < kAK; e0 += 16) {
+        for (int e0 = 0; e0 < kAKDt; e0 += 16) {
           uint32_t hv[16], lv[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            const float x = tap(c * kAK + e0 + e);
+            const float x = tap(c * kAKDt + e0 + e);
             const float h = tf32_hi(x);
             hv[e] = __float_as_uint(h);
             lv[e] = __float_as_uint(x - h);
           }
-          stage_put(ta, e0, hv, lv);
+          stage_put<kAKDt>(ta, e0, hv, lv);
         }
         stage_end();
         warp_arrive(&s.a_full[st]);
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_corr(SpArgs a, const __grid_
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Kp * 64), a.Tp, idesc_tf32(a.Kp), ntiles, nch);
+      mma_loop<kAKDt>(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Kp * 64), a.Tp, idesc_tf32(a.Kp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) load_states<RingDt, kCh>(a, s, &vmap, vring, ntiles * NG, NG, tile_row, ok);
@@ -655,7 +660,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
 #pragma unroll
         for (int e = 0; e < kAK; ++e) x[e] = vs[e * kPix];
         warp_arrive(&s.v_empty[vst]);
-        const uint32_t ta = stage_begin(tmem, st);
+        const uint32_t ta = stage_begin<kAK>(tmem, st);
 #pragma unroll
         for (int e0 = 0; e0 < kAK; e0 += 16) {
           uint32_t hv[16], lv[16];
@@ -667,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
             hv[e] = __float_as_uint(h);
             lv[e] = __float_as_uint(u - h);
           }
-          stage_put(ta, e0, hv, lv);
+          stage_put<kAK>(ta, e0, hv, lv);
         }
         stage_end();
         warp_arrive(&s.a_full[st]);
@@ -675,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sp_conv(SpArgs a, const __grid_
     }
   } else if (warp == kWarpMma) {
     if ((threadIdx.x & 31) == 0)
-      mma_loop(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Tp * 64), a.Kp, idesc_tf32(a.Tp), ntiles, nch);
+      mma_loop<kAK>(a, s, ok, tmem, saddr(sb), (uint32_t)(a.Tp * 64), a.Kp, idesc_tf32(a.Tp), ntiles, nch);
     __syncwarp();
   } else if (warp == kWarpV) {
     if ((threadIdx.x & 31) == 0) {
@@ -812,7 +817,7 @@ size_t spatial_operand_bytes(const Ctx& c) { return (size_t)2 * round16(c.K) * r
 
 static size_t corr_smem(const Ctx& c) {
   return spatial_operand_bytes(c) + sp::kVStages * sp::kVStage +
-         (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * ((round16(c.fh * c.fw) + sp::kAK - 1) / sp::kAK * sp::kAK) * 4;
+         (size_t)2 * (c.fh + 1) * sp::kPix * 4 + (size_t)2 * ((round16(c.fh * c.fw) + sp::kAKDt - 1) / sp::kAKDt * sp::kAKDt) * 4;
 }
 static size_t conv_smem(const Ctx& c) {
   return spatial_operand_bytes(c) + sp::RingD::STAGES * sp::kVStageD +
