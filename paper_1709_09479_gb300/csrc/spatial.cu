@@ -26,17 +26,18 @@
 // The TF32 mode takes hi.hi alone.
 //
 // Kernel shape (both products): one CTA per SM, persistent over its range of rows, four roles:
-//   warps 4-11  producers, two groups of four warps: stage the row's operand chunks of 16
-//               contraction elements, split into TF32 hi and lo, in TMEM (the MMA's A operand: lane p =
-//               pixel p, one column per element; group g fills the stage of parity g, thread p of a
-//               group writes lane p with tcgen05.st), so that shared memory carries only the filter
-//               operand (the MMA's B), the state ring and the exchanges;
+//   warps 4-11  producers, two groups of four warps: stage the row's operand chunks (32 contraction
+//               elements for D, 64 taps for D^T: every chunk is one hand-off to the MMA warp, the
+//               cost that bounds these kernels), split into TF32 hi and lo, in TMEM (the MMA's A
+//               operand: lane p = pixel p, one column per element; group g fills the stage of parity
+//               g, thread p of a group writes lane p with tcgen05.st), so that shared memory carries
+//               only the filter operand (the MMA's B), the state ring and the exchanges;
 //   warp 14     lane 0 issues the MMAs of each filled stage (an issuing thread waits for the tensor
 //               pipe, so it must not be a producer: the next chunk is built meanwhile);
 //   warps 0-3   epilogue: TMEM lane p = pixel p (two accumulators, so the epilogue of row i runs
 //               under the MMAs of row i + 1);
-//   warp 12     loader of the state v: one TMA tile load (16 maps x 1 row x 128 pixels, 8 KB) per
-//               stage (five stages for D^T; for D two rings of two, one per producer group), with
+//   warp 12     loader of the state v: one TMA tile load of 1 row x 128 pixels per stage (D^T: 16
+//               maps, five stages; D: 32 maps, two rings of two, one per producer group), with
 //               full/empty mbarriers; boxes further ahead are prefetched into L2;
 //   warp 13     loader of the lambda rows of D^T's tiles (double-buffered).
 // The filter operand (up to 128 x 128 hi + lo, 128 KB) stays in shared memory for the whole launch.
