@@ -109,7 +109,7 @@ cudaError_t launch_solve_prep_batch(const PrepArgs* list, int n, int max_omega, 
 // ---- uneven-batch images beyond the one-map-per-CTA sweep (uneven_big.cu) -------------------------
 struct BigPlan {          // a length-n complex DFT
   int n;
-  int M;                  // 0: Stockham plan of n (7-smooth); else Bluestein length M >= 2n - 1 (7-smooth)
+  int M;                  // 0: Stockham plan of n (7-smooth); else Bluestein length M >= 2n - 1 (a power of two)
   Radices rad;            // radices of n, or of M
   long long tw;           // twiddles exp(-2 pi i t / L), L = n or M: element offset into the tables
   long long chirp, bhat;  // Bluestein: w_j = exp(-pi i j^2 / n) (n), FFT_M of the conjugate chirp / M (M)

@@ -11,7 +11,7 @@
 // A 1-D transform of a 7-smooth length is the run-time Stockham plan of fft.cuh; any other length n
 // goes through Bluestein's chirp z-transform: with w_j = e^{-pi i j^2/n},
 //     X_k = w_k sum_j (x_j w_j) conj(w_{k-j}),
-// a circular convolution of length M >= 2n - 1 (M 7-smooth) done with two length-M transforms; the
+// a circular convolution of length M >= 2n - 1 (M a power of two) done with two length-M transforms; the
 // inverse transform is conj(DFT(conj x)).
 // One ADMM iteration over all such images is four launches: the inverse column pass (building
 // w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j as it loads), the row pass (inverse row transform, the
@@ -72,7 +72,7 @@ __device__ __forceinline__ void fpad(float2* buf, int nlines, int ls, const BigP
 // butterflies as the run-time stages of fft.cuh, with the index divisions by the round's line count
 // and by Ns done as high multiplies.
 template <int R, bool INV, int IPT>
-__device__ __noinline__ void big_stage(float2* buf, int nlines, int ls, int n, int Ns, const float2* tw) {
+__device__ __forceinline__ void big_stage_body(float2* buf, int nlines, int ls, int n, int Ns, const float2* tw) {
   const int nb = n / R;
   int lpr = (NT * IPT) / nb;
   lpr = lpr < 1 ? 1 : (lpr > nlines ? nlines : lpr);
@@ -117,6 +117,36 @@ __device__ __noinline__ void big_stage(float2* buf, int nlines, int ls, int n, i
   }
   __syncthreads();
 }
+template <int R, bool INV, int IPT>
+__device__ __noinline__ void big_stage(float2* buf, int nlines, int ls, int n, int Ns, const float2* tw) {
+  big_stage_body<R, INV, IPT>(buf, nlines, ls, n, Ns, tw);
+}
+
+// the stages of a power-of-two length L >= 128 with compile-time radices (16 first, then what is
+// left: 8, 16, 2 or 4), inlined one after the other: no calls, so no registers saved to local memory
+// around them as for the run-time plans
+template <int L, bool INV>
+__device__ __forceinline__ void pow2_stages(float2* buf, int nlines, int ls, const float2* tw) {
+  big_stage_body<16, INV, 1>(buf, nlines, ls, L, 1, tw);
+  if constexpr (L == 128) {
+    big_stage_body<8, INV, 1>(buf, nlines, ls, L, 16, tw);
+  } else {
+    big_stage_body<16, INV, 1>(buf, nlines, ls, L, 16, tw);
+    if constexpr (L == 512) big_stage_body<2, INV, 4>(buf, nlines, ls, L, 256, tw);
+    if constexpr (L == 1024) big_stage_body<4, INV, 2>(buf, nlines, ls, L, 256, tw);
+  }
+}
+template <bool INV>
+__device__ __forceinline__ bool pow2_dispatch(float2* buf, int nlines, int ls, int L, const float2* tw) {
+  switch (L) {
+    case 128: pow2_stages<128, INV>(buf, nlines, ls, tw); return true;
+    case 256: pow2_stages<256, INV>(buf, nlines, ls, tw); return true;
+    case 512: pow2_stages<512, INV>(buf, nlines, ls, tw); return true;
+    case 1024: pow2_stages<1024, INV>(buf, nlines, ls, tw); return true;
+    default: return false;
+  }
+}
+
 
 // all stages of a length-n transform (radices of the plan)
 template <bool INV>
@@ -149,18 +179,18 @@ __device__ __forceinline__ const float2* stage_tw(float2* dst, const BigPlan& pl
 template <bool INV>
 __device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const float2* tabs, const float2* tw) {
   if (pl.M == 0) {
-    big_stages<INV>(buf, nlines, ls, pl.n, pl.rad, tw);
+    if (!pow2_dispatch<INV>(buf, nlines, ls, pl.n, tw)) big_stages<INV>(buf, nlines, ls, pl.n, pl.rad, tw);
     return;
   }
   const int M = pl.M;
   const float2* bh = tabs + pl.bhat;
-  big_stages<false>(buf, nlines, ls, M, pl.rad, tw);
+  if (!pow2_dispatch<false>(buf, nlines, ls, M, tw)) big_stages<false>(buf, nlines, ls, M, pl.rad, tw);
   for (int line = 0; line < nlines; ++line) {
     float2* b = buf + (size_t)line * ls;
     for (int j = threadIdx.x; j < M; j += NT) b[j] = cmul(b[j], __ldg(bh + j));
   }
   __syncthreads();
-  big_stages<true>(buf, nlines, ls, M, pl.rad, tw);
+  if (!pow2_dispatch<true>(buf, nlines, ls, M, tw)) big_stages<true>(buf, nlines, ls, M, pl.rad, tw);
 }
 
 // ---- column pass: item = (image, map, first column, columns) ------------------------------------
@@ -611,8 +641,10 @@ const BigPlan& plan_of(UnevenLayout& L, int n) {
   } else {
     p.twn = (long long)L.btabs.size();
     push_twiddles(L.btabs, n);
-    int M = 2 * n - 1;
-    while (!smooth7(M)) ++M;
+    // a power of two: its transforms run with compile-time radices (pow2_stages), which pays for the
+    // longer circle (measured on 256 images with sides in [64, 512])
+    int M = 1;
+    while (M < 2 * n - 1) M *= 2;
     p.M = M;
     p.rad = factorize(M);
     p.tw = (long long)L.btabs.size();
