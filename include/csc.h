@@ -123,7 +123,10 @@ typedef struct {
    update. Same state v and codes z as the Fourier route, equal up to rounding. Needs H = W = 128,
    J = 1, K <= 128, fh fw <= 128, fh <= 15, precision CSC_FP32 or CSC_MIXED_TF32, no symmetric
    boundary (CSC_ERR_UNSUPPORTED otherwise); csc_code needs v 16-byte aligned (CSC_ERR_ARG otherwise:
-   its rows are moved by TMA bulk copies). Only csc_code's iterations change; the other calls run as
+   its rows are moved by TMA tensor copies). On a GB300 at 100 images of 128 x 128 and 100 filters of
+   11 x 11 an iteration takes about 1.25 times the Fourier route's (1.04 times with CSC_MIXED_TF32):
+   it is a second route to the same iterates, not the faster one there. Only csc_code's iterations
+   change; the other calls run as
    on any context. Every wait of the tensor-core kernels is bounded by csc_set_wait_limit's bound (or
    about one second); a wait that gives up makes a synchronising csc_code return CSC_ERR_TIMEOUT. */
 #define CSC_FLAG_SPATIAL 16
