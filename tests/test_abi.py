@@ -77,3 +77,17 @@ def _has_gpu():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's flag, precision and status constants are the values include/csc.h
+    defines (the binding passes them through the C ABI as plain integers)."""
+    from paper_1709_09479_gb300 import csc
+    text = open(os.path.join(ROOT, "include", "csc.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(CSC_FLAG_\w+)\s+(\d+)", text)}
+    assert defines, "no CSC_FLAG_* defines found"
+    for name, value in defines.items():
+        assert getattr(csc, name) == value, name
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(CSC_(?:FP32|MIXED_\w+))\s*=\s*(\d+)", text)}
+    for name, value in enums.items():
+        assert getattr(csc, name) == value, name
