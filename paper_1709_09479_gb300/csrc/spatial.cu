@@ -66,7 +66,6 @@ constexpr int kAKDt = 64;                        // ... of D^T's A chunks (its p
 constexpr int kCh = 16;                          // contraction elements of an operand chunk (2 K-steps)
 constexpr uint32_t kLbo = 128;                   // next core matrix (8 rows x 16 bytes) along the contraction
 constexpr uint32_t kSbo = 512;                   // next group of 8 rows: a chunk row is 64 bytes
-constexpr int kAChunk = kPix * kCh * 4;          // bytes of one split (hi or lo) of an A chunk
 constexpr int kAStages = 2;                      // A operand stages (16 KB each)
 constexpr int kVStages = 5;                      // state stages in flight (D^T; D has 2 rings of 2)
 constexpr int kPrefetch = 24;                    // state boxes fetched into L2 ahead of the ring
@@ -104,13 +103,6 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, 
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
       "r"(a), "l"(b), "r"(id), "r"(acc));
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
@@ -186,14 +178,6 @@ __device__ __forceinline__ void stage_put(uint32_t ta, int e0, const uint32_t* h
 __device__ __forceinline__ void stage_end() {
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ float clampb(float v, float b) { return fminf(fmaxf(v, -b), b); }
 // the TF32 hi part of the streamed operands: v rounded to 10 explicit mantissa bits, half-way cases
