@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcsc.so")
 SOURCES = ["api.cu", "coding.cu", "learning.cu", "geo_128.cu", "geo_100.cu", "geo_64.cu", "geo_rt.cu", "noalloc.cu", "tc_gram.cu", "uneven.cu", "uneven_big.cu",
-           "sweep128.cu", "video.cu", "spectra128.cu", "video_learn.cu", "video_cg.cu", "spatial.cu"]
+           "sweep128.cu", "video.cu", "spectra128.cu", "video_learn.cu", "video_cg.cu", "spatial.cu", "uneven_spatial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

@@ -109,7 +109,7 @@ void free_all(Ctx* c) {
   c->cap_stream = nullptr;
   void* uptrs[] = {c->U.d_cls, c->U.d_img, c->U.d_mstart, c->U.d_slot, c->U.d_bcls, c->U.d_bimg, c->U.d_bcol,
                    c->U.d_brow, c->U.d_bfreq, c->U.d_btabs, c->U.d_by, c->U.d_blam, c->U.d_be, c->U.d_bl1,
-                   c->U.d_bsetup, c->U.d_bprep};
+                   c->U.d_bsetup, c->U.d_bprep, c->U.d_scol, c->U.d_srow, c->U.d_stile, c->U.d_sy, c->U.d_sq};
   for (void* p : uptrs)
     if (p) cudaFree(p);
   for (auto& ep : c->events) {
@@ -312,6 +312,23 @@ csc_status upload_big(Ctx* c, const std::vector<BigSetupItem>& setup) {
   return CSC_OK;
 }
 
+// the spatial route's work items and buffers: one half spectrum and one plane per image
+csc_status upload_usp(Ctx* c) {
+  UnevenLayout& U = c->U;
+  auto put = [&](auto** dptr, const auto& vec) {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    if (cudaMalloc((void**)dptr, std::max<size_t>(vec.size(), 1) * sizeof(T)) != cudaSuccess) return false;
+    return cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!put(&U.d_scol, U.scol) || !put(&U.d_srow, U.srow) || !put(&U.d_stile, U.stile) ||
+      cudaMalloc((void**)&U.d_sy, std::max<long long>(U.n_xh, 1) * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&U.d_sq, std::max<long long>(U.n_x, 1) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CSC_ERR_WORKSPACE, "uneven batch: allocation of the spatial route's workspace failed");
+  }
+  return CSC_OK;
+}
+
 // spectra of the filters (per class) and of the images (per image) of an uneven batch
 cudaError_t uneven_setup(Ctx* c, const float* d, const float* x, bool solve) {
   for (int ci = 0; ci < (int)c->U.cls.size(); ++ci) {
@@ -375,6 +392,46 @@ cudaError_t uneven_sweeps(Ctx* c, float* v, float* z, int iters) {
     if (big && e == cudaSuccess) {
       e = launch_big_sweep(ba, mode, c->stream);
       c->launches += big_launches(mode);
+    }
+    bracket_close(c, br);
+  }
+  return e;
+}
+
+// the direct spatial route on an uneven batch (CSC_FLAG_SPATIAL): per iteration D on the tiles
+// (q = sum_k d_k * u_k - x / rho), lambda = F^-1(P F(q)) by the one-channel transforms, then D^T and the
+// state update on the tiles; P and the spectra of the setup as for the Fourier route
+UspArgs usp_args(const Ctx& c, const float* x, const float* d, float* v, float* z) {
+  const UnevenLayout& U = c.U;
+  UspArgs a{};
+  a.K = c.K; a.fh = c.fh; a.fw = c.fw;
+  a.beta = (float)c.p.beta; a.rho = (float)c.p.rho;
+  a.cls = U.d_bcls; a.img = U.d_bimg; a.tiles = U.d_stile; a.n_tiles = (int)U.stile.size();
+  a.d = d; a.x = x; a.q = U.d_sq; a.v = v; a.z = z;
+  return a;
+}
+
+cudaError_t uneven_spatial_sweeps(Ctx* c, const float* x, const float* d, float* v, float* z, int iters) {
+  const UnevenLayout& U = c->U;
+  BigArgs la = big_args(*c, U.d_sq, nullptr);
+  la.one = 1;
+  la.K = 1;
+  la.col_items = U.d_scol; la.row_items = U.d_srow;
+  la.n_col_items = (int)U.scol.size(); la.n_row_items = (int)U.srow.size();
+  la.Y = U.d_sy;
+  const UspArgs ua = usp_args(*c, x, d, v, z);
+  cudaError_t e = launch_usp_conv(ua, c->stream);
+  if (e == cudaSuccess) e = launch_big_lambda1(la, c->stream);
+  c->launches += 4;
+  for (int t = 0; t < iters && e == cudaSuccess; ++t) {
+    const bool last = (t == iters - 1);
+    const int br = last ? -1 : bracket_open(c, 0);
+    e = launch_usp_corr(ua, last, c->stream);
+    c->launches += 1;
+    if (!last && e == cudaSuccess) {
+      e = launch_usp_conv(ua, c->stream);
+      if (e == cudaSuccess) e = launch_big_lambda1(la, c->stream);
+      c->launches += 4;
     }
     bracket_close(c, br);
   }
@@ -642,12 +699,24 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   const int fh = p.fs[0], fw = p.fs[1];
   if (fh < 1 || fw < 1 || !(fh & 1) || !(fw & 1))
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: filter support must be odd and >= 1");
+  const bool spatial = (p.flags & CSC_FLAG_SPATIAL) != 0;
+  if (spatial) {
+    if (p.J != 1 || p.precision != CSC_FP32)
+      return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: direct spatial coding is for grey images in CSC_FP32");
+    if (fh > kUspF || fw > kUspF)
+      return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: direct spatial coding needs fh, fw <= 11");
+    if (usp_smem_bytes(p.K) > kSmemLimit)
+      return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: direct spatial coding: K filters do not fit shared memory");
+    if (p.flags & CSC_FLAG_SYMMETRIC_BOUNDARY)
+      return fail(nullptr, CSC_ERR_UNSUPPORTED, "csc_init_uneven: direct spatial coding takes circular boundaries");
+  }
   csc_ctx* ctx = new (std::nothrow) csc_ctx;
   if (!ctx) return fail(nullptr, CSC_ERR_WORKSPACE, "csc_init_uneven: out of host memory");
   Ctx* c = &ctx->c;
   c->p = p;
   c->N = n_images; c->J = p.J; c->K = p.K; c->fh = fh; c->fw = fw; c->S2 = fh * fw;
   c->uneven = true;
+  c->spatial = spatial;
   c->stream = (cudaStream_t)stream;
   auto bail = [&](csc_status st) {
     if (c->last_error.size()) g_init_error = c->last_error;
@@ -668,8 +737,9 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
     for (int q = 0; ci < 0 && q < (int)U.bcls.size(); ++q)
       if (U.bcls_H[q] == H && U.bcls_W[q] == W) { bi = q; break; }
     Geometry g;
-    if (ci < 0 && bi < 0 && check_size(p, H, W, g, "csc_init_uneven") != CSC_OK) {
-      // not one map per CTA: the multi-pass engine (any side up to kBigMaxSide, any factorisation)
+    if (ci < 0 && bi < 0 && (spatial || check_size(p, H, W, g, "csc_init_uneven") != CSC_OK)) {
+      // not one map per CTA (or the direct spatial route, whose lambda transforms are the engine's):
+      // the multi-pass engine (any side up to kBigMaxSide, any factorisation)
       if (H < 8 || W < 8 || fh > H || fw > W || !big_add_class(U, H, W)) {
         char msg[160];
         std::snprintf(msg, sizeof(msg), "csc_init_uneven: image %dx%d: need 8 <= H, W <= %d and the filter inside",
@@ -732,6 +802,7 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   U.n_small = (int)U.img.size();
   std::vector<BigSetupItem> bsetup;
   if (!U.bimg.empty()) big_build_items(U, p.K, p.J, fh, fw, bsetup);
+  if (spatial) big_build_one_channel(U);
   if (uneven_smem_bytes(U, p.J, kIter) > kSmemLimit) {
     delete ctx;
     return fail(nullptr, CSC_ERR_SHAPE, "csc_init_uneven: the largest image and the largest spectrum do not fit one CTA");
@@ -766,6 +837,7 @@ csc_status csc_init_uneven(const csc_params* params, int n_images, const int* di
   }
   if (upload_uneven(c) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
   if (!U.bimg.empty() && upload_big(c, bsetup) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
+  if (spatial && upload_usp(c) != CSC_OK) return bail(CSC_ERR_WORKSPACE);
   *out = ctx;
   return CSC_OK;
 }
@@ -976,7 +1048,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     if ((s = stage_in(c, x, &c->st_x, nx, &xd, true)) != CSC_OK) return s;
     if ((s = stage_in(c, d, &c->st_d, nd, &dd, true)) != CSC_OK) return s;
   }
-  if (c->spatial && iters > 0 && (reinterpret_cast<uintptr_t>(vd) & 15))
+  if (c->spatial && !c->uneven && iters > 0 && (reinterpret_cast<uintptr_t>(vd) & 15))
     return fail(c, CSC_ERR_ARG, "csc_code: direct spatial coding needs v 16-byte aligned (its rows are bulk copies)");
   if (c->uneven && iters > 0 && !c->U.tuned) {
     if (c->U.n_small > 0) CSC_CHECK_CUDA(c, uneven_setup(c, dd, xd, true), "uneven setup");
@@ -993,7 +1065,7 @@ csc_status csc_code(csc_ctx* ctx, const float* x, const float* d, float* v, floa
     }
     if (c->uneven) {
       e = uneven_setup(c, dd, xd, true);
-      if (e == cudaSuccess) e = uneven_sweeps(c, vd, zd, iters);
+      if (e == cudaSuccess) e = c->spatial ? uneven_spatial_sweeps(c, xd, dd, vd, zd, iters) : uneven_sweeps(c, vd, zd, iters);
       return e;
     }
     e = launch_fft_maps(*c, dd, c->K * c->J, 1, c->dhat);

@@ -157,6 +157,8 @@ struct BigArgs {
   float* z;
   double* e_items;        // [n_freq_items] residual energy (objective)
   double* l1_items;       // [n_row_items] sum |z| (objective)
+  int one;                // one-channel item lists (direct spatial route): Y at the image's x_hat offset,
+                          // the spatial plane (v) at its x offset
 };
 constexpr int kBigMaxSide = 1024;
 cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st);
@@ -168,6 +170,34 @@ struct UnevenLayout;
 bool big_add_class(UnevenLayout& L, int H, int W);
 // the work-item lists of the sweeps and of the setup, from L.bcls / L.bimg
 void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<BigSetupItem>& setup);
+
+// ---- direct spatial coding of an uneven batch (uneven_spatial.cu, CSC_FLAG_SPATIAL, J = 1) -------
+// D and D^T as correlations on the CUDA cores over output tiles of kUspTileH x kUspTileW pixels,
+// filters zero-padded to kUspF x kUspF about their centre; lambda by the engine's one-channel transforms
+constexpr int kUspTileH = 32, kUspTileW = 64, kUspF = 11;
+struct UspTile {
+  int img, y0, x0, pad;
+};
+struct UspArgs {
+  int K, fh, fw;
+  float beta, rho;
+  const BigCls* cls;
+  const BigImg* img;
+  const UspTile* tiles;
+  int n_tiles;
+  const float* d;     // [K][fh][fw] filters
+  const float* x;     // images (offset im.x)
+  float* q;           // conv: q = sum_k d_k * u_k - x / rho (offset im.x); then lambda, in place
+  float* v;           // [K][H][W] per image (offset im.v) ADMM state
+  float* z;           // corr, last iteration: codes (may be null)
+};
+size_t usp_smem_bytes(int K);
+cudaError_t launch_usp_conv(const UspArgs& a, cudaStream_t st);
+cudaError_t launch_usp_corr(const UspArgs& a, bool last, cudaStream_t st);
+// lambda = F^-1(P F(q)) per image in place on q: the one-channel row and column passes (3 launches)
+cudaError_t launch_big_lambda1(const BigArgs& a, cudaStream_t st);
+// the one-channel column and row work items and the output tiles of the spatial route, from L.bimg
+void big_build_one_channel(UnevenLayout& L);
 
 struct UnevenLayout {
   std::vector<UClass> cls;
@@ -200,6 +230,14 @@ struct UnevenLayout {
   PrepArgs* d_bprep = nullptr;   // the classes' per-frequency systems, one launch
   int bprep_max_omega = 0;
   int n_bsetup_rows = 0, n_bsetup_cols = 0;
+  // direct spatial route (CSC_FLAG_SPATIAL): one-channel transform items, output tiles, buffers
+  std::vector<BigItem> scol, srow;
+  std::vector<UspTile> stile;
+  BigItem* d_scol = nullptr;
+  BigItem* d_srow = nullptr;
+  UspTile* d_stile = nullptr;
+  float2* d_sy = nullptr;     // one half spectrum per image (x_hat offsets)
+  float* d_sq = nullptr;      // q, then lambda, one plane per image (x offsets)
   long long n_tw = 0, n_dhat = 0, n_pd = 0, n_pm = 0, n_x = 0, n_v = 0, n_xh = 0, n_slot = 0;
   UClass* d_cls = nullptr;
   UImage* d_img = nullptr;

@@ -194,10 +194,12 @@ __device__ void fcore(float2* buf, int nlines, int ls, const BigPlan& pl, const 
 }
 
 // ---- column pass: item = (image, map, first column, columns) ------------------------------------
-// BUILD: the inverse transform of w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j; else the forward
-// transform of the stored row spectra
-template <bool BUILD>
+// B = 1: the inverse transform of w_hat_k = sum_j conj(d_hat_jk) lambda_hat_j; B = 0: the forward
+// transform of the stored row spectra; B = 2 (one-channel items, J = 1): the forward transform, the
+// product with P and the inverse transform, in shared memory (lambda_hat = P F(q), then back)
+template <int B>
 __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
+  constexpr bool BUILD = (B == 1);
   extern __shared__ float2 sm[];
   __shared__ BigPlan pl;
   const BigItem it = a.col_items[blockIdx.x];
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   const int H = bc.H, Wc = bc.Wc, Om = H * Wc, nc = it.count, kw0 = it.first;
   const int ls = bc.col_ls;
   const FastDiv fnc((unsigned)nc);
-  float2* Y = a.Y + im.y + (size_t)it.map * Om;
+  float2* Y = a.Y + (a.one ? im.xh : im.y + (size_t)it.map * Om);
   if (BUILD) {
     const float2* lam = a.lam + im.lam;
     const size_t dbase = bc.dhat + (size_t)it.map * a.J * Om;
@@ -233,9 +235,22 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_cols(BigArgs a) {
   fpad(sm, nc, ls, pl);
   __syncthreads();
   fcore<BUILD>(sm, nc, ls, pl, a.tabs, tw);
+  if (B == 2) {
+    // each element is read and rewritten by the same thread; the padding [n, M) is not read
+    const float* pd = a.pdiag + bc.pd;
+    for (int i = threadIdx.x; i < nc * H; i += NT) {
+      const int h = (int)fnc.div(i), c = i - h * nc;
+      const float p = pd[h * Wc + kw0 + c];
+      const float2 X = fout<false>(sm[(size_t)c * ls + h], h, pl, a.tabs);
+      sm[(size_t)c * ls + h] = fin<true>(make_float2(X.x * p, X.y * p), h, pl, a.tabs);
+    }
+    fpad(sm, nc, ls, pl);
+    __syncthreads();
+    fcore<true>(sm, nc, ls, pl, a.tabs, tw);
+  }
   for (int i = threadIdx.x; i < nc * H; i += NT) {
     const int h = (int)fnc.div(i), c = i - h * nc;
-    Y[(size_t)h * Wc + kw0 + c] = fout<BUILD>(sm[(size_t)c * ls + h], h, pl, a.tabs);
+    Y[(size_t)h * Wc + kw0 + c] = fout<(B != 0)>(sm[(size_t)c * ls + h], h, pl, a.tabs);
   }
 }
 
@@ -250,6 +265,10 @@ __device__ __forceinline__ float2 half_bin(const float2* row, int kw, int W, int
   if (kw == 0 || 2 * kw == W) v.y = 0.f;
   return v;
 }
+
+// one-channel items (the direct spatial route): the forward row transform of q (read raw from a.v),
+// and the inverse row transform written to a.v as a real plane (lambda), with no state update
+constexpr int kRawFwd = 4, kRawInv = 5;
 
 template <int MODE>
 __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
@@ -266,12 +285,12 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
   const int np = (nr + 1) / 2;
   const int ls = bc.row_ls;
   const FastDiv fW((unsigned)W), fWc((unsigned)Wc);
-  const size_t moff = im.v + (size_t)it.map * H * W;
-  float2* Y = a.Y + im.y + (size_t)it.map * Om;
+  const size_t moff = a.one ? (size_t)im.x : im.v + (size_t)it.map * H * W;
+  float2* Y = a.Y + (a.one ? im.xh : im.y + (size_t)it.map * Om);
   const float beta = a.beta;
   const bool pair_last = !(nr & 1);   // the last transform line holds two rows
   double l1 = 0.0;
-  if (MODE == kIter || MODE == kLast) {
+  if (MODE == kIter || MODE == kLast || MODE == kRawInv) {
     for (int i = threadIdx.x; i < np * W; i += NT) {
       const int q = (int)fW.div(i), kw = i - q * W;
       const float2 xa = half_bin(Y + (size_t)(h0 + 2 * q) * Wc, kw, W, Wc);
@@ -286,6 +305,11 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
       const bool has_b = (q < np - 1) || pair_last;
       const float2 w = fout<true>(sm[(size_t)q * ls + x], x, pl, a.tabs);
       const size_t pa = moff + (size_t)(h0 + 2 * q) * W + x, pb = pa + W;
+      if (MODE == kRawInv) {
+        a.v[pa] = w.x;
+        if (has_b) a.v[pb] = w.y;
+        continue;
+      }
       const float va = a.v[pa], vb = has_b ? a.v[pb] : 0.f;
       const float na = w.x - (bclamp(va, beta) - va), nb = w.y - (bclamp(vb, beta) - vb);
       const float ca = bclamp(na, beta), cb = bclamp(nb, beta);
@@ -300,9 +324,9 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
         sm[(size_t)q * ls + x] = fin<false>(make_float2(2.f * ca - na, has_b ? 2.f * cb - nb : 0.f), x, pl, a.tabs);
       }
     }
-    if (MODE != kLast) fpad(sm, np, ls, pl);
+    if (MODE != kLast && MODE != kRawInv) fpad(sm, np, ls, pl);
   } else {
-    const float* src = (MODE == kPrologue) ? a.v : a.z;
+    const float* src = (MODE == kPrologue || MODE == kRawFwd) ? a.v : a.z;
     for (int i = threadIdx.x; i < np * W; i += NT) {
       const int q = (int)fW.div(i), x = i - q * W;
       const bool has_b = (q < np - 1) || pair_last;
@@ -311,14 +335,14 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_big_rows(BigArgs a) {
       if (MODE == kPrologue) {
         ta = 2.f * bclamp(ta, beta) - ta;
         tb = 2.f * bclamp(tb, beta) - tb;
-      } else {
+      } else if (MODE == kObjective) {
         l1 += fabs((double)ta) + fabs((double)tb);
       }
       sm[(size_t)q * ls + x] = fin<false>(make_float2(ta, tb), x, pl, a.tabs);
     }
     fpad(sm, np, ls, pl);
   }
-  if (MODE != kLast) {
+  if (MODE != kLast && MODE != kRawInv) {
     __syncthreads();
     fcore<false>(sm, np, ls, pl, a.tabs, tw);
     for (int i = threadIdx.x; i < nr * Wc; i += NT) {
@@ -541,8 +565,8 @@ cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st) {
   const size_t tws = (size_t)a.tw_max * sizeof(float2);
   const size_t csm = a.col_smem + tws, rsm = a.row_smem + tws;
   if (mode == kIter || mode == kLast) {
-    if ((e = big_attr((const void*)k_big_cols<true>, csm)) != cudaSuccess) return e;
-    k_big_cols<true><<<a.n_col_items, NT, csm, st>>>(a);
+    if ((e = big_attr((const void*)k_big_cols<1>, csm)) != cudaSuccess) return e;
+    k_big_cols<1><<<a.n_col_items, NT, csm, st>>>(a);
   }
   switch (mode) {
     case kPrologue:
@@ -563,10 +587,24 @@ cudaError_t launch_big_sweep(const BigArgs& a, int mode, cudaStream_t st) {
       break;
   }
   if (mode == kLast) return cudaGetLastError();
-  if ((e = big_attr((const void*)k_big_cols<false>, csm)) != cudaSuccess) return e;
-  k_big_cols<false><<<a.n_col_items, NT, csm, st>>>(a);
+  if ((e = big_attr((const void*)k_big_cols<0>, csm)) != cudaSuccess) return e;
+  k_big_cols<0><<<a.n_col_items, NT, csm, st>>>(a);
   if (mode == kObjective) k_big_freq<kObjective><<<a.n_freq_items, NT, 0, st>>>(a);
   else k_big_freq<kIter><<<a.n_freq_items, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_big_lambda1(const BigArgs& a, cudaStream_t st) {
+  using namespace big;
+  cudaError_t e;
+  const size_t tws = (size_t)a.tw_max * sizeof(float2);
+  const size_t csm = a.col_smem + tws, rsm = a.row_smem + tws;
+  if ((e = big_attr((const void*)k_big_rows<kRawFwd>, rsm)) != cudaSuccess) return e;
+  if ((e = big_attr((const void*)k_big_cols<2>, csm)) != cudaSuccess) return e;
+  if ((e = big_attr((const void*)k_big_rows<kRawInv>, rsm)) != cudaSuccess) return e;
+  k_big_rows<kRawFwd><<<a.n_row_items, NT, rsm, st>>>(a);
+  k_big_cols<2><<<a.n_col_items, NT, csm, st>>>(a);
+  k_big_rows<kRawInv><<<a.n_row_items, NT, rsm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -696,6 +734,18 @@ bool big_add_class(UnevenLayout& L, int H, int W) {
   L.bcls_H.push_back(H);
   L.bcls_W.push_back(W);
   return true;
+}
+
+void big_build_one_channel(UnevenLayout& L) {
+  L.scol.clear(); L.srow.clear(); L.stile.clear();
+  for (int i = 0; i < (int)L.bimg.size(); ++i) {
+    const BigCls& bc = L.bcls[L.bimg[i].cls];
+    const int nc = lines_per_item(bc.col_ls, bc.Wc), nr = lines_per_item(bc.row_ls, bc.H);
+    for (int c0 = 0; c0 < bc.Wc; c0 += nc) L.scol.push_back({i, 0, c0, std::min(nc, bc.Wc - c0)});
+    for (int h0 = 0; h0 < bc.H; h0 += 2 * nr) L.srow.push_back({i, 0, h0, std::min(2 * nr, bc.H - h0)});
+    for (int y0 = 0; y0 < bc.H; y0 += kUspTileH)
+      for (int x0 = 0; x0 < bc.W; x0 += kUspTileW) L.stile.push_back({i, y0, x0, 0});
+  }
 }
 
 void big_build_items(UnevenLayout& L, int K, int J, int fh, int fw, std::vector<BigSetupItem>& setup) {
