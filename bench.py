@@ -778,7 +778,9 @@ def run_case(args):
       learning: the same csc_code, then csc_learn with --learn-steps learning steps;
       uneven:   the 256-image batch of the uneven256 extension (sides uniform in [64, 512], K = 64;
                 --images takes its first images; --sides smooth64-128 draws the sides from the even
-                7-smooth sizes in [64, 128]), one csc_code of --iters iterations;
+                7-smooth sizes in [64, 128]), one csc_code of --iters iterations (with --spatial: the
+                direct spatial route, per iteration D on the tiles, the three one-channel lambda
+                passes and D^T);
       video:    the video3d extension (3 x 32 x 128^2, K = 64 colour filters 5 x 11 x 11), one csc_code
                 of --iters iterations, then csc_learn with --learn-steps steps.
     Inputs are the seeded 1/f^2 fields and Gaussian dictionaries of the benchmark."""
@@ -813,7 +815,8 @@ def run_case(args):
         npx = sum(H * W for H, W in sizes)
         v = torch.zeros(K * npx, device="cuda")
         z = torch.empty_like(v)
-        with csc.Solver(J=1, K=K, fs=(a.s, a.s), dims_list=sizes, beta=1.0, rho=0.1) as sv:
+        flags = csc.CSC_FLAG_SPATIAL if a.spatial else 0
+        with csc.Solver(J=1, K=K, fs=(a.s, a.s), dims_list=sizes, beta=1.0, rho=0.1, flags=flags) as sv:
             sv.code(x, d, v, z, a.iters)
         torch.cuda.synchronize()
         print("ok", float(v.abs().sum()))
@@ -943,7 +946,8 @@ def main():
     ap.add_argument("--images", type=int, default=256, help="uneven case: number of images")
     ap.add_argument("--sides", choices=["64-512", "smooth64-128"], default="64-512")
     ap.add_argument("--spatial", action="store_true",
-                    help="coding case: CSC_FLAG_SPATIAL (D and D^T as direct spatial products on the tensor cores)")
+                    help="coding and uneven cases: CSC_FLAG_SPATIAL (D and D^T as direct spatial products: on "
+                         "the tensor cores for 128 x 128, on the CUDA cores for uneven batches)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
