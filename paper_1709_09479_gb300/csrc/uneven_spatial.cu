@@ -86,6 +86,9 @@ __device__ __forceinline__ void correlate(const float* __restrict__ tile, const 
     const float4 t = g4[q];
     g[4 * q] = t.x; g[4 * q + 1] = t.y; g[4 * q + 2] = t.z; g[4 * q + 3] = t.w;
   }
+  // the taps stay in registers for the whole filter (not re-read from shared memory at each use)
+#pragma unroll
+  for (int t = 0; t < F * F; ++t) asm volatile("" : "+f"(g[t]));
 #pragma unroll
   for (int r = 0; r < 4 + F - 1; ++r) {
     const float4* row = reinterpret_cast<const float4*>(tile + (4 * ty + r) * IP + 4 * tx);
@@ -108,7 +111,9 @@ __device__ __forceinline__ void correlate(const float* __restrict__ tile, const 
   }
 }
 
-// q = sum_k d_k * u_k - x / rho on one tile
+// q = sum_k d_k * u_k - x / rho on one tile. The tile of v_{k+1} is loaded into registers while
+// filter k's products run, and stored as u_{k+1} once every thread has finished reading tile k.
+constexpr int NPRE = (IH * IW + NT - 1) / NT;   // tile elements per thread
 __global__ void __launch_bounds__(NT, 2) k_usp_conv(UspArgs a) {
   extern __shared__ __align__(16) float sm[];
   const UspTile tl = a.tiles[blockIdx.x];
@@ -120,15 +125,32 @@ __global__ void __launch_bounds__(NT, 2) k_usp_conv(UspArgs a) {
   const float beta = a.beta;
   float acc[4][4] = {};
   const size_t plane = (size_t)H * W;
-  for (int k = 0; k < a.K; ++k) {
-    __syncthreads();   // the halo tables, and every thread's reads of the previous tile
+  float pre[NPRE];
+  auto fetch = [&](int k) {
     const float* vk = a.v + im.v + (size_t)k * plane;
-    for (int i = threadIdx.x; i < IH * IW; i += NT) {
-      const int r = i / IW, c = i - r * IW;
-      const float v = __ldg(vk + s.roff[r] + s.cidx[c]);
-      s.tile[r * IP + c] = 2.f * uclamp(v, beta) - v;
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int i = threadIdx.x + j * NT;
+      if (i < IH * IW) {
+        const int r = i / IW, c = i - r * IW;
+        pre[j] = __ldg(vk + s.roff[r] + s.cidx[c]);
+      }
+    }
+  };
+  __syncthreads();   // the halo tables
+  fetch(0);
+  for (int k = 0; k < a.K; ++k) {
+    if (k > 0) __syncthreads();   // every thread's reads of tile k - 1
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int i = threadIdx.x + j * NT;
+      if (i < IH * IW) {
+        const int r = i / IW, c = i - r * IW;
+        s.tile[r * IP + c] = 2.f * uclamp(pre[j], beta) - pre[j];
+      }
     }
     __syncthreads();
+    if (k + 1 < a.K) fetch(k + 1);
     correlate(s.tile, s.g + (size_t)k * GS, ty, tx, acc);
   }
   const float irho = 1.0f / a.rho;
