@@ -367,6 +367,40 @@ def measure_extensions(csc, torch, dev, hbm_peak):
     sweep3 = tm3["sweep_ms"] / max(tm3["sweep_launches"], 1) / 1e3
     out["uneven256"]["bf16"] = {"sweep_us": sweep3 * 1e6, "sweep_hbm_frac": alg / sweep3 / 1e9 / hbm_peak,
                                 "coding_iters_per_s_sweeps_only": 1.0 / sweep3}
+    # the same batch on the direct spatial route (D and D^T as tiled correlations on the CUDA cores,
+    # lambda by one-channel transforms): graph replay of whole calls, and one iteration from the
+    # eager call's event brackets (D^T + state update, D, the three lambda passes)
+    fl = csc.CSC_FLAG_SPATIAL
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1, flags=fl | csc.CSC_FLAG_GRAPH) as sv4:
+        v.zero_()
+        sv4.code(x, d, v, z, iters)
+        sv4.code(x, d, v, z, iters)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(3):
+            sv4.code(x, d, v, z, iters)
+        e1.record()
+        torch.cuda.synchronize()
+        ms4 = e0.elapsed_time(e1) / 3
+    with csc.Solver(J=1, K=K, fs=(s, s), dims_list=sizes, beta=1.0, rho=0.1, flags=fl) as sv5:
+        sv5.code(x, d, v, z, 3)
+        sv5.timing_read()
+        sv5.timing_enable(True)
+        sv5.code(x, d, v, z, iters)
+        tm5 = sv5.timing_read()
+    it5 = tm5["sweep_ms"] / max(tm5["sweep_launches"], 1) / 1e3
+    flops = 2.0 * 2.0 * K * s * s * npx           # D and D^T, one multiply-add = 2 flops
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12    # TFLOP/s: SMs x FP32 lanes x 2 x maximum SM clock
+    out["uneven256"]["spatial"] = {
+        "route": "direct spatial D and D^T (CUDA cores, 32 x 64 output tiles), lambda by one-channel transforms",
+        f"ms_per_call_of_{iters}_iters": ms4, "coding_iters_per_s": iters / (ms4 / 1e3),
+        "iteration_us": it5 * 1e6, "coding_iters_per_s_iterations_only": 1.0 / it5,
+        "roofline": {"bound": "alu", "achieved": flops / it5 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": flops / it5 / 1e12 / fp32_peak,
+                     "note": "useful products of D and D^T per iteration over the whole iteration's time "
+                             "(lambda passes included); peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "hbm_frac_of_state_traffic": 12.0 * K * npx / it5 / 1e9 / hbm_peak}
     del x, v, z
 
     # --- unroll32: batch 32, 128x128, K=64, T=20, checkpoints every 5 --------------------------

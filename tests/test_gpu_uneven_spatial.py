@@ -156,3 +156,22 @@ def test_uneven_spatial_full_batch_sampled_images(csc):
         if np.any(zo != 0):
             assert rel(zi, zo) <= REL_TOL
     del torch
+
+
+def test_uneven_spatial_graph_replay_equals_eager(csc):
+    """With CSC_FLAG_GRAPH the launches of a call are recorded once and replayed: the replayed calls
+    give the eager call's bits."""
+    sizes = [(67, 131), (100, 100), (37, 53)]
+    K, fs, beta, rho, iters = 8, (11, 11), 0.5, 1.0, 4
+    xs, d = batch(23, sizes, K, fs)
+    ve, ze = code(csc, xs, d, sizes, beta, rho, iters, csc.CSC_FLAG_SPATIAL)
+    import torch
+    n_v = sum(K * H * W for H, W in sizes)
+    with csc.Solver(J=1, K=K, fs=fs, dims_list=sizes, beta=beta, rho=rho,
+                    flags=csc.CSC_FLAG_SPATIAL | csc.CSC_FLAG_GRAPH) as sv:
+        for _ in range(3):
+            v = torch.zeros(n_v, device="cuda")
+            z = torch.empty_like(v)
+            sv.code(flat(xs), flat([d]), v, z, iters)
+            torch.cuda.synchronize()
+            assert bool((v == ve).all()) and bool((z == ze).all())
