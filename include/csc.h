@@ -134,8 +134,8 @@ typedef struct {
    their centre, circular boundaries on each image's own H x W grid) and lambda by one 2-D transform
    pair per image and iteration (the multi-pass transforms, Bluestein for sides with a prime factor
    above 7). One iteration is five launches: D^T with the state update, D (q = D u - x/rho), and three
-   passes for lambda = F^-1(P F(q)). Needs J = 1, CSC_FP32, fh, fw <= 11, 496 K + 13 400 bytes of
-   shared memory <= 232448 (K <= 441), no symmetric boundary (CSC_ERR_UNSUPPORTED otherwise); any
+   passes for lambda = F^-1(P F(q)). Needs J = 1, CSC_FP32, fh, fw <= 11, 496 K + 26 168 bytes of
+   shared memory <= 232448 (K <= 415), no symmetric boundary (CSC_ERR_UNSUPPORTED otherwise); any
    alignment of v. On a GB300, 256 images with sides uniform in [64, 512] and 64 filters of 11 x 11
    take about 16 ms per iteration against 84 ms on the Fourier route. The objective on such a context
    is the Fourier engine's (its workspace is kept). */

@@ -42,11 +42,13 @@ static_assert(IP >= 4 * 15 + 16, "the last thread's four loads stay inside the r
 __device__ __forceinline__ float uclamp(float v, float b) { return fminf(fmaxf(v, -b), b); }
 
 // shared memory: padded filters [K][GS] | input tile [IH][IP] | halo row offsets [IH] | columns [IW]
+// | the in-plane offset of every tile element [IH][IP] (0 for the pad columns IW..IP-1)
 struct Smem {
   float* g;
   float* tile;
   long long* roff;
   int* cidx;
+  int* gofs;
 };
 __device__ __forceinline__ Smem carve(float* sm, int K) {
   Smem s;
@@ -54,6 +56,7 @@ __device__ __forceinline__ Smem carve(float* sm, int K) {
   s.tile = sm + (size_t)K * GS;
   s.roff = reinterpret_cast<long long*>(s.tile + IH * IP);
   s.cidx = reinterpret_cast<int*>(s.roff + IH);
+  s.gofs = s.cidx + IW;
   return s;
 }
 
@@ -113,7 +116,9 @@ __device__ __forceinline__ void correlate(const float* __restrict__ tile, const 
 
 // q = sum_k d_k * u_k - x / rho on one tile. The tile of v_{k+1} is loaded into registers while
 // filter k's products run, and stored as u_{k+1} once every thread has finished reading tile k.
-constexpr int NPRE = (IH * IW + NT - 1) / NT;   // tile elements per thread
+// Elements are taken in the tile's own order (pitch IP), their in-plane offsets from the table
+// built once per tile (a plane is at most 1024 x 1024: int offsets).
+constexpr int NPRE = (IH * IP + NT - 1) / NT;   // tile elements per thread
 __global__ void __launch_bounds__(NT, 2) k_usp_conv(UspArgs a) {
   extern __shared__ __align__(16) float sm[];
   const UspTile tl = a.tiles[blockIdx.x];
@@ -125,29 +130,28 @@ __global__ void __launch_bounds__(NT, 2) k_usp_conv(UspArgs a) {
   const float beta = a.beta;
   float acc[4][4] = {};
   const size_t plane = (size_t)H * W;
+  __syncthreads();   // the halo tables
+  for (int i = threadIdx.x; i < IH * IP; i += NT) {
+    const int r = i / IP, c = i - r * IP;
+    s.gofs[i] = c < IW ? (int)(s.roff[r] + s.cidx[c]) : 0;
+  }
+  __syncthreads();
   float pre[NPRE];
   auto fetch = [&](int k) {
     const float* vk = a.v + im.v + (size_t)k * plane;
 #pragma unroll
     for (int j = 0; j < NPRE; ++j) {
       const int i = threadIdx.x + j * NT;
-      if (i < IH * IW) {
-        const int r = i / IW, c = i - r * IW;
-        pre[j] = __ldg(vk + s.roff[r] + s.cidx[c]);
-      }
+      if (i < IH * IP) pre[j] = __ldg(vk + s.gofs[i]);
     }
   };
-  __syncthreads();   // the halo tables
   fetch(0);
   for (int k = 0; k < a.K; ++k) {
     if (k > 0) __syncthreads();   // every thread's reads of tile k - 1
 #pragma unroll
     for (int j = 0; j < NPRE; ++j) {
       const int i = threadIdx.x + j * NT;
-      if (i < IH * IW) {
-        const int r = i / IW, c = i - r * IW;
-        s.tile[r * IP + c] = 2.f * uclamp(pre[j], beta) - pre[j];
-      }
+      if (i < IH * IP) s.tile[i] = 2.f * uclamp(pre[j], beta) - pre[j];
     }
     __syncthreads();
     if (k + 1 < a.K) fetch(k + 1);
@@ -224,7 +228,8 @@ __global__ void __launch_bounds__(NT, 2) k_usp_corr(UspArgs a) {
 
 size_t usp_smem_bytes(int K) {
   using namespace usp;
-  return ((size_t)K * GS + (size_t)IH * IP) * sizeof(float) + (size_t)IH * sizeof(long long) + (size_t)IW * sizeof(int);
+  return ((size_t)K * GS + (size_t)IH * IP) * sizeof(float) + (size_t)IH * sizeof(long long) +
+         (size_t)(IW + IH * IP) * sizeof(int);
 }
 
 cudaError_t launch_usp_conv(const UspArgs& a, cudaStream_t st) {
