@@ -91,3 +91,20 @@ def test_binding_constants_match_the_header():
     enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(CSC_(?:FP32|MIXED_\w+))\s*=\s*(\d+)", text)}
     for name, value in enums.items():
         assert getattr(csc, name) == value, name
+
+
+def test_uneven_spatial_refusals_without_gpu():
+    """CSC_FLAG_SPATIAL on an uneven batch is checked on the host before any CUDA call: colour
+    images, reduced precision, supports above 11 x 11 and filter sets beyond one CTA's shared memory
+    give CSC_ERR_UNSUPPORTED; an accepted batch then needs the device (CSC_ERR_CUDA without one)."""
+    from paper_1709_09479_gb300 import csc
+    dims = [(64, 64), (67, 131)]
+    for J, K, fs, prec in [(3, 4, (3, 3), csc.CSC_FP32), (1, 4, (13, 13), csc.CSC_FP32),
+                           (1, 4, (5, 5), csc.CSC_MIXED_BF16), (1, 416, (5, 5), csc.CSC_FP32)]:
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_init_uneven(J, K, fs, dims, 1.0, 1.0, precision=prec, flags=csc.CSC_FLAG_SPATIAL)
+        assert e.value.status == 8, (J, K, fs, prec)
+    if not _has_gpu():
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_init_uneven(1, 415, (11, 11), dims, 1.0, 1.0, flags=csc.CSC_FLAG_SPATIAL)
+        assert e.value.status == 4
